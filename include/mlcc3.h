@@ -1,0 +1,140 @@
+/*
+ * mlcc3.h -- C ABI of the MLCC3 triples library (GB300, sm_103a).
+ *
+ * The library computes the triples (T3, R3, L3) contributions of multilevel
+ * CC3 (arXiv 2202.08612, Sec. 3 "Implementation" and the SI equations):
+ * the ground-state residual, the right and transpose Jacobian
+ * transformations, the transition densities and the oscillator strength.
+ * The triples amplitudes are built on the fly per batch of active occupied
+ * indices i >= j >= k and never stored as a whole.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Orbitals: occupied first, then virtual (n_mo = N_O + N_V).  Active occupied
+ *   orbitals are occupied indices [0, n_o), active virtual orbitals are
+ *   virtual indices [0, n_v).
+ * Arrays: C row-major, IEEE double, dense.  Every array argument may be a
+ *   device pointer or a host pointer (detected per call with
+ *   cudaPointerGetAttributes); host arrays are staged through buffers the
+ *   context owns.  The caller keeps ownership of all arrays.
+ * Singles: X[A][I] = X^A_I, shape [N_V][N_O].
+ * Doubles: the active-pair block X[i][a][L][D] = X^{aD}_{iL}, shape
+ *   [n_o][n_v][N_O][N_V] (the paper's N_V N_O n_v n_o sub-block, Sec. 3).
+ *   Elements whose two pairs are both active appear twice and must be equal.
+ *   Vectors (R, L, rho, sigma, Omega) hold one number per unique excitation,
+ *   the bra <mu| being biorthonormal to E_ai E_bj |HF>; the trial vector's
+ *   doubles operator is 1/2 sum Rbar E E with Rbar = (1 + delta_ij delta_ab) R.
+ * Densities: [n_mo][n_mo], D_pq pairs with the operator element A_pq of the
+ *   T1-transformed one-electron operator, sum_pq D_pq A_pq.
+ * Outputs are overwritten with the triples contribution only; the caller adds
+ *   it to its CCSD-level quantity.
+ * Errors: every function returns MLCC3_OK (0) or a negative MLCC3_ERR_* code;
+ *   mlcc3_last_error() returns a message for the calling thread.  Nothing is
+ *   thrown or aborted across the ABI.  Calls on one context are serialised on
+ *   the context's stream and are not thread safe.
+ */
+#ifndef MLCC3_H
+#define MLCC3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLCC3_OK 0
+#define MLCC3_ERR_ARG (-1)            /* bad dimension, null pointer, bad mode */
+#define MLCC3_ERR_CUDA (-2)           /* a CUDA call failed */
+#define MLCC3_ERR_OOM (-3)            /* device allocation failed */
+#define MLCC3_ERR_SINGULAR_DENOM (-4) /* |eps^{abc}_{ijk} - omega| < 1e-3 */
+#define MLCC3_ERR_TIMEOUT (-5)        /* a device wait gave up */
+#define MLCC3_ERR_STATE (-6)          /* call order: integrals not built */
+
+/* Arithmetic of the contractions.  MLCC3_FP64: every product and sum in
+ * IEEE double.  MLCC3_SPLIT_BF16X3: integral-amplitude products on the
+ * tensor cores from hi/lo bfloat16 splits with FP32 accumulation;
+ * denominators and final reductions stay in FP64. */
+#define MLCC3_FP64 0
+#define MLCC3_SPLIT_BF16X3 1
+
+typedef struct mlcc3_ctx mlcc3_ctx;
+
+typedef struct {
+  int64_t n_occ;     /* N_O */
+  int64_t n_vir;     /* N_V */
+  int64_t n_act_occ; /* n_o, 0 <= n_o <= N_O */
+  int64_t n_act_vir; /* n_v, 0 <= n_v <= N_V */
+  int64_t n_chol;    /* N_J, number of Cholesky vectors */
+  /* [N_O] host array, 1 = core orbital; NULL = no core-valence separation.
+   * With a mask, the Jacobian transformations and the densities skip every
+   * batch i,j,k without a core index (Sec. 3, CVS). Copied at create. */
+  const uint8_t *core_mask;
+} mlcc3_dims;
+
+/* Create a context on the current device.  `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream) on which every later call runs. */
+int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *dims, int precision, void *cuda_stream);
+void mlcc3_destroy(mlcc3_ctx *ctx);
+const char *mlcc3_last_error(void);
+
+/* Set the ground-state amplitudes and build the T1-transformed integral
+ * blocks (Sec. 2: H = exp(-T1) H exp(T1); SI: g_PQRS = sum_J L^J_PQ L^J_RS).
+ *   chol [N_J][n_mo][n_mo]  Cholesky vectors of (pq|rs), symmetric in p,q
+ *   t1   [N_V][N_O]         singles amplitudes t^A_I
+ *   eps  [n_mo]             orbital energies (canonical, Sec. 2 eps^{abc}_{ijk})
+ *   t2c  [n_o][n_v][N_O][N_V]  t^{aD}_{iL}
+ *   t2x  [n_o][n_v][N_O][N_V]  t^{aD}_{Li} (only the transition density reads it)
+ * Must precede every other compute call; may be repeated. */
+int mlcc3_build_integrals(mlcc3_ctx *ctx, const double *chol, const double *t1,
+                          const double *eps, const double *t2c, const double *t2x);
+
+/* Triples contributions to the ground-state residual (Sec. 3, Eq. tau3, SI):
+ *   omega1 [N_V][N_O], omega2 [n_o][n_v][N_O][N_V]. */
+int mlcc3_triples_omega(mlcc3_ctx *ctx, double *omega1, double *omega2);
+
+/* Right Jacobian transformation rho = A R, triples part (Sec. 3, Eq. R3,
+ * Eqs. ups_v/ups_o, SI), for n_vec trial vectors at frequencies omega[n_vec]
+ * (host array).  R1 [n_vec][N_V][N_O], R2 [n_vec][n_o][n_v][N_O][N_V];
+ * rho1, rho2 the same shapes. */
+int mlcc3_jacobian_right(mlcc3_ctx *ctx, int n_vec, const double *omega, const double *R1,
+                         const double *R2, double *rho1, double *rho2);
+
+/* Transpose Jacobian transformation sigma = L^T A, triples part (Sec. 3, SI
+ * L3 and sigma equations); the exact adjoint of mlcc3_jacobian_right under
+ * the unique-element inner product. Shapes as for mlcc3_jacobian_right. */
+int mlcc3_jacobian_left(mlcc3_ctx *ctx, int n_vec, const double *omega, const double *L1,
+                        const double *L2, double *sigma1, double *sigma2);
+
+/* Triples parts of the ground-state density D^{0-0} and of the left and
+ * right transition densities D^{m-0}, D^{0-m} of one state (Sec. 3,
+ * Eq. DL_oo, SI densities).  lam1/lam2 are the ground-state multipliers
+ * (lambda3 is built from them with omega = 0); D00_in [n_mo][n_mo] is the
+ * caller's CCSD-level ground-state density including the reference
+ * (2 delta_IJ), used by the normalisation term of D^{0-m}.
+ * Outputs D00_T, Dm0_T, D0m_T [n_mo][n_mo]. */
+int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
+                             const double *lam2, const double *R1, const double *R2,
+                             const double *L1, const double *L2, const double *D00_in,
+                             double *D00_T, double *Dm0_T, double *D0m_T);
+
+/* Length-gauge oscillator strength of one state from its full (CCSD-level +
+ * triples) transition densities (Sec. 2 transition moments):
+ *   f = 2/3 omega sum_x (sum_pq D0m_pq mu~^x_pq)(sum_pq Dm0_pq mu~^x_pq),
+ *   mu~ = (1 - t1) mu (1 + t1).  mu [3][n_mo][n_mo]; f is a host scalar. */
+int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
+                              const double *Dm0, const double *mu, double *f);
+
+/* Diagnostics (used by the test-suite).  mlcc3_debug_fetch copies the first
+ * n doubles of a named device buffer of the context into `host` (integral
+ * blocks "Lt", "Gv", "Gb", "Go", "Gx", "Govov", "F", or a named scratch
+ * buffer such as "tau"); MLCC3_ERR_ARG for an unknown name or n too large.
+ * mlcc3_debug_nbatches returns the number of unique batches i >= j >= k
+ * (i = j = k excluded), or -1 for a null context. */
+int mlcc3_debug_fetch(mlcc3_ctx *ctx, const char *name, double *host, size_t n);
+long long mlcc3_debug_nbatches(mlcc3_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLCC3_H */

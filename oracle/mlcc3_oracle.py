@@ -203,6 +203,25 @@ def tau3(ctx):
     return -sym3(W) / eps3(ctx)
 
 
+def tau3_block(ctx, i, j, k):
+    """Eq. tau3 for one ordered occupied triple (i, j, k): the n_v^3 block
+    tau^{abc}_{ijk}, summing W over the six pair permutations explicitly."""
+    tA, tB = ctx.views(ctx.t2)
+    gv, go = ctx.gn("vVvo"), ctx.gn("Oovo")
+    occ = (i, j, k)
+    out = np.zeros((ctx.nv, ctx.nv, ctx.nv))
+    # W^{abc}_{ijk}, W^{acb}_{ikj}, W^{bac}_{jik}, W^{bca}_{jki}, W^{cab}_{kij}, W^{cba}_{kji}
+    for perm, virt in (((0, 1, 2), "abc"), ((0, 2, 1), "acb"), ((1, 0, 2), "bac"),
+                       ((1, 2, 0), "bca"), ((2, 0, 1), "cab"), ((2, 1, 0), "cba")):
+        x, y, z = (occ[p] for p in perm)
+        W = (_es('aD,bDc->abc', tA[x, y], gv[:, :, :, z])
+             - _es('abL,Lc->abc', tB[x], go[:, y, :, z]))
+        out += _es(virt + '->abc', W)
+    eo, ev = ctx.eo, ctx.ev[:ctx.nv]
+    den = ev[:, None, None] + ev[None, :, None] + ev[None, None, :] - eo[i] - eo[j] - eo[k]
+    return -out / den
+
+
 def _back_contract(ctx, Xt, F):
     """Contributions of a contravariant triples tensor Xt to the singles and
     (unsymmetrised) doubles of the residual (SI, Omega terms):

@@ -1,0 +1,156 @@
+"""Thin ctypes binding of the MLCC3 C ABI (include/mlcc3.h).
+
+Argument marshalling only: every array is passed as a raw pointer (a torch
+CUDA tensor's device pointer, or a contiguous float64 numpy array's host
+pointer) and all arithmetic happens in the CUDA library.  Loading fails
+loudly when libmlcc3.so is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmlcc3.so")
+
+MLCC3_FP64 = 0
+MLCC3_SPLIT_BF16X3 = 1
+
+ERRORS = {-1: "MLCC3_ERR_ARG", -2: "MLCC3_ERR_CUDA", -3: "MLCC3_ERR_OOM",
+          -4: "MLCC3_ERR_SINGULAR_DENOM", -5: "MLCC3_ERR_TIMEOUT", -6: "MLCC3_ERR_STATE"}
+
+# Every symbol include/mlcc3.h declares.
+EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_integrals",
+           "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
+           "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
+           "mlcc3_debug_nbatches")
+
+
+class MLCC3Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Dims(ctypes.Structure):
+    _fields_ = [("n_occ", ctypes.c_int64), ("n_vir", ctypes.c_int64),
+                ("n_act_occ", ctypes.c_int64), ("n_act_vir", ctypes.c_int64),
+                ("n_chol", ctypes.c_int64), ("core_mask", ctypes.POINTER(ctypes.c_uint8))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_2202_08612_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    lib.mlcc3_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_Dims), I, P]
+    lib.mlcc3_destroy.argtypes = [P]
+    lib.mlcc3_destroy.restype = None
+    lib.mlcc3_last_error.restype = ctypes.c_char_p
+    lib.mlcc3_build_integrals.argtypes = [P] * 6
+    lib.mlcc3_triples_omega.argtypes = [P, P, P]
+    lib.mlcc3_jacobian_right.argtypes = [P, I, P, P, P, P, P]
+    lib.mlcc3_jacobian_left.argtypes = [P, I, P, P, P, P, P]
+    lib.mlcc3_transition_density.argtypes = [P, D] + [P] * 10
+    lib.mlcc3_oscillator_strength.argtypes = [P, D, P, P, P, P]
+    lib.mlcc3_debug_fetch.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t]
+    lib.mlcc3_debug_nbatches.argtypes = [P]
+    lib.mlcc3_debug_nbatches.restype = ctypes.c_longlong
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor (device or host) or a numpy float64 array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("numpy arrays must be contiguous float64")
+        return x.ctypes.data
+    # torch.Tensor
+    if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+        raise ValueError("tensors must be contiguous float64")
+    return x.data_ptr()
+
+
+class Context:
+    """One library context (mlcc3_create .. mlcc3_destroy)."""
+
+    def __init__(self, n_occ, n_vir, n_act_occ, n_act_vir, n_chol, precision=MLCC3_FP64,
+                 core_mask=None, stream=None):
+        self.lib = load()
+        self._core = None
+        if core_mask is not None:
+            self._core = np.ascontiguousarray(core_mask, dtype=np.uint8)
+        dims = _Dims(n_occ, n_vir, n_act_occ, n_act_vir, n_chol,
+                     self._core.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                     if self._core is not None else None)
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream)
+        self._check(self.lib.mlcc3_create(ctypes.byref(h), ctypes.byref(dims), precision, s))
+        self.h = h
+        self.dims = (n_occ, n_vir, n_act_occ, n_act_vir, n_chol)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MLCC3Error(rc, self.lib.mlcc3_last_error().decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mlcc3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_integrals(self, chol, t1, eps, t2c, t2x):
+        self._check(self.lib.mlcc3_build_integrals(self.h, _ptr(chol), _ptr(t1), _ptr(eps),
+                                                   _ptr(t2c), _ptr(t2x)))
+
+    def triples_omega(self, omega1, omega2):
+        self._check(self.lib.mlcc3_triples_omega(self.h, _ptr(omega1), _ptr(omega2)))
+
+    def jacobian_right(self, omega, R1, R2, rho1, rho2):
+        w = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+        self._check(self.lib.mlcc3_jacobian_right(self.h, len(w), w.ctypes.data, _ptr(R1),
+                                                  _ptr(R2), _ptr(rho1), _ptr(rho2)))
+
+    def jacobian_left(self, omega, L1, L2, sigma1, sigma2):
+        w = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+        self._check(self.lib.mlcc3_jacobian_left(self.h, len(w), w.ctypes.data, _ptr(L1),
+                                                 _ptr(L2), _ptr(sigma1), _ptr(sigma2)))
+
+    def transition_density(self, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T):
+        self._check(self.lib.mlcc3_transition_density(
+            self.h, float(omega), _ptr(lam1), _ptr(lam2), _ptr(R1), _ptr(R2), _ptr(L1), _ptr(L2),
+            _ptr(D00_in), _ptr(D00_T), _ptr(Dm0_T), _ptr(D0m_T)))
+
+    def oscillator_strength(self, omega, D0m, Dm0, mu) -> float:
+        f = ctypes.c_double()
+        self._check(self.lib.mlcc3_oscillator_strength(self.h, float(omega), _ptr(D0m), _ptr(Dm0),
+                                                       _ptr(mu), ctypes.byref(f)))
+        return f.value
+
+    def debug_fetch(self, name: str, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.float64)
+        self._check(self.lib.mlcc3_debug_fetch(self.h, name.encode(), out.ctypes.data, n))
+        return out
+
+    def nbatches(self) -> int:
+        return int(self.lib.mlcc3_debug_nbatches(self.h))

@@ -1,0 +1,99 @@
+// Host-side engine of the MLCC3 triples library: context, buffers, and the
+// launch helpers every stage uses.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstdint>
+#include <functional>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels_fp64.cuh"
+#include "mlcc3.h"
+
+namespace mlcc3 {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void check_cuda(cudaError_t e, const char *what);
+
+// Shapes of a batched strided contraction: m = (M1,M2), n = (N1,N2), k = (K1,K2,K3).
+struct Shape {
+  long long M1 = 1, M2 = 1, N1 = 1, N2 = 1, K1 = 1, K2 = 1, K3 = 1;
+};
+
+inline BstcItem mk_item(long long oA, long long oB, long long oC, std::array<long long, 5> sA,
+                        std::array<long long, 5> sB, std::array<long long, 4> sC) {
+  BstcItem it;
+  it.offA = oA;
+  it.offB = oB;
+  it.offC = oC;
+  for (int i = 0; i < 5; ++i) it.sA[i] = sA[i];
+  for (int i = 0; i < 5; ++i) it.sB[i] = sB[i];
+  for (int i = 0; i < 4; ++i) it.sC[i] = sC[i];
+  return it;
+}
+
+// An ordered occupied triple (p,q,r) = sigma(i,j,k) of unique batch u, with
+// the strides of the view X_{pqr}[x1][x2][x3] into the canonical block of u.
+struct Ord {
+  int u;
+  int p, q, r;
+  long long off;      // canonical block offset (elements)
+  long long vs[3];    // strides of x1, x2, x3
+};
+
+}  // namespace mlcc3
+
+struct mlcc3_ctx {
+  // sizes
+  long long NO, NV, no, nv, NJ, nmo;
+  int precision;
+  cudaStream_t stream;
+  int device;
+  std::vector<uint8_t> core;
+  bool built = false;
+
+  // persistent device arrays (FP64)
+  double *eps = nullptr, *t1 = nullptr, *Lt = nullptr, *t2c = nullptr, *t2x = nullptr;
+  double *Tl = nullptr;              // t^{ab}_{iL} as [i][a][b][L]
+  double *Gv = nullptr, *Gb = nullptr;  // g_bDck, g_Dbkc as [k][b][c][D]
+  double *Go = nullptr, *Gx = nullptr;  // g_Ljck, g_jLkc as [j][k][c][L]
+  double *Govov = nullptr;           // g_jbkc as [j][b][k][c]
+  double *F = nullptr;               // F_kc [k][c]
+  int *status = nullptr;             // device error word
+  double *dscal = nullptr;           // device scalars
+
+  std::vector<mlcc3::TripItem> batches;       // unique i >= j >= k, not i = j = k
+  std::vector<mlcc3::TripItem> batches_cvs;   // those with a core index
+  std::vector<mlcc3::Ord> ords, ords_cvs;     // distinct orderings
+
+  // named scratch buffers, reused across calls (stream ordered)
+  std::map<std::string, std::pair<void *, size_t>> scratch;
+  // item lists on the device, built once per pattern
+  std::map<std::string, std::pair<void *, int>> items;
+  // output copies back to host pointers at the end of a call
+  std::vector<std::array<void *, 3>> pending_out;
+
+  double *buf(const std::string &name, size_t n);
+  void *raw(const std::string &name, size_t bytes);
+  const mlcc3::BstcItem *dev_items(const std::string &key,
+                                   const std::function<std::vector<mlcc3::BstcItem>()> &make,
+                                   int *n);
+  const double *in(const double *p, size_t n, const std::string &name);
+  double *out(double *p, size_t n, const std::string &name);
+  void finish();
+
+  void bstc(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,
+            const mlcc3::BstcItem *items, int nitems, bool atomic);
+  void bstc1(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,
+             const mlcc3::BstcItem &item, const std::string &key);
+  void dot(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,
+           const mlcc3::BstcItem *items, int nitems);
+  void zero(double *p, size_t n);
+};

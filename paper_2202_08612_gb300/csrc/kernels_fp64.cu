@@ -1,0 +1,453 @@
+// FP64 kernels of the MLCC3 triples path (sm_103a).
+//
+// * bstc_kernel: batched strided tensor contraction, C += alpha A B with
+//   per-item strides (any permuted view of a triples block is a stride set).
+// * triples_build_kernel: one n_v^3 block per unique batch i >= j >= k,
+//   X^{abc}_{ijk} = -(eps^{abc}_{ijk} - omega)^{-1} P^{abc}_{ijk} V^{abc}_{ijk}
+//   (Eq. tau3, Eq. R3, SI L3), the six pair permutations summed in registers.
+// * contra3_kernel: contravariant triples (Eq. contra_3, virtual permutations).
+// * finalize_doubles_kernel / c2_block_kernel / delta_block_kernel /
+//   transpose_tl_kernel: doubles bookkeeping on the active-pair block.
+#include <cuda_runtime.h>
+
+#include "kernels_fp64.cuh"
+
+namespace mlcc3 {
+
+__constant__ int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// ---------------------------------------------------------------------------
+// Batched strided tensor contraction.
+// Tile 64 x 64 of C per CTA, K chunks of 16, 256 threads with 4 x 4 outputs.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16;
+}
+
+__global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ long long rowA[BM], rowC[BM], colB[BN], colC[BN];
+  __shared__ long long kA[BK], kB[BK];
+
+  const BstcItem &it = p.items[blockIdx.y];
+  const int tid = threadIdx.x;
+  const long long M = (long long)p.M1 * p.M2, N = (long long)p.N1 * p.N2;
+  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  const long long ntn = (N + BN - 1) / BN;
+  const long long m0 = ((long long)blockIdx.x / ntn) * BM, n0 = ((long long)blockIdx.x % ntn) * BN;
+
+  if (tid < BM) {
+    long long m = m0 + tid;
+    if (m < M) {
+      long long m1 = m / p.M2, m2 = m % p.M2;
+      rowA[tid] = m1 * it.sA[0] + m2 * it.sA[1];
+      rowC[tid] = m1 * it.sC[0] + m2 * it.sC[1];
+    } else {
+      rowA[tid] = -1;
+      rowC[tid] = -1;
+    }
+  } else if (tid < BM + BN) {
+    int t = tid - BM;
+    long long n = n0 + t;
+    if (n < N) {
+      long long n1 = n / p.N2, n2 = n % p.N2;
+      colB[t] = n1 * it.sB[3] + n2 * it.sB[4];
+      colC[t] = n1 * it.sC[2] + n2 * it.sC[3];
+    } else {
+      colB[t] = -1;
+      colC[t] = -1;
+    }
+  }
+  const bool kfastA = (it.sA[4] == 1 && p.K3 > 1) || (p.K3 == 1 && it.sA[3] == 1 && p.K2 > 1) ||
+                      (p.K3 == 1 && p.K2 == 1 && it.sA[2] == 1);
+  const bool kfastB = (it.sB[2] == 1 && p.K3 > 1) || (p.K3 == 1 && it.sB[1] == 1 && p.K2 > 1) ||
+                      (p.K3 == 1 && p.K2 == 1 && it.sB[0] == 1);
+  const double *A = p.A + it.offA;
+  const double *B = p.B + it.offB;
+
+  const int ty = tid / 16, tx = tid % 16;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (long long k0 = 0; k0 < K; k0 += BK) {
+    if (tid < BK) {
+      long long k = k0 + tid;
+      if (k < K) {
+        long long k3 = k % p.K3, k12 = k / p.K3;
+        long long k2 = k12 % p.K2, k1 = k12 / p.K2;
+        kA[tid] = k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4];
+        kB[tid] = k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2];
+      } else {
+        kA[tid] = -1;
+        kB[tid] = -1;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < BK * BM; e += 256) {
+      int kk, mm;
+      if (kfastA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+      double v = 0.0;
+      if (rowA[mm] >= 0 && kA[kk] >= 0) v = A[rowA[mm] + kA[kk]];
+      As[kk][mm] = v;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      int kk, nn;
+      if (kfastB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
+      double v = 0.0;
+      if (colB[nn] >= 0 && kB[kk] >= 0) v = B[kB[kk] + colB[nn]];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *C = p.C + it.offC;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    long long rc = rowC[ty * 4 + i];
+    if (rc < 0) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      long long cc = colC[tx * 4 + j];
+      if (cc < 0) continue;
+      double v = p.alpha * acc[i][j];
+      if (p.atomic) atomicAdd(C + rc + cc, v);
+      else C[rc + cc] += v;
+    }
+  }
+}
+
+// Dot-product form (M = N = 1, large K): one CTA per item reduces over K.
+__global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
+  __shared__ double red[256];
+  const BstcItem &it = p.items[blockIdx.x];
+  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  double s = 0.0;
+  for (long long k = threadIdx.x; k < K; k += 256) {
+    long long k3 = k % p.K3, k12 = k / p.K3;
+    long long k2 = k12 % p.K2, k1 = k12 / p.K2;
+    s += p.A[it.offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] *
+         p.B[it.offB + k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(p.C + it.offC, p.alpha * red[0]);
+}
+
+// Strided copy: C[offC + k] = A(view k) with k = (k1,k2,k3) row-major.
+__global__ void bstc_copy_kernel(BstcParams p) {
+  const BstcItem &it = p.items[blockIdx.y];
+  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  for (long long k = blockIdx.x * 256LL + threadIdx.x; k < K; k += 256LL * gridDim.x) {
+    long long k3 = k % p.K3, k12 = k / p.K3;
+    long long k2 = k12 % p.K2, k1 = k12 / p.K2;
+    p.C[it.offC + k] = p.A[it.offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Triples block build, cube tile 8 x 8 x 8 of (a, b, c) per CTA.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int TT = 8;
+constexpr int TR = 32;
+}
+
+__global__ void __launch_bounds__(256) triples_build_kernel(const TripTerms terms,
+                                                            const TripItem *__restrict__ items,
+                                                            const double *__restrict__ eps, int NO,
+                                                            int nv, double omega,
+                                                            double *__restrict__ out,
+                                                            int *__restrict__ status) {
+  __shared__ double Ps[TT][TR + 1];
+  __shared__ double Qs[TT * TT][TR + 1];
+  const TripTerm *sterm = terms.t;
+  const int nterms = terms.n;
+  const int tid = threadIdx.x;
+  const TripItem it = items[blockIdx.y];
+  const int ntile = (nv + TT - 1) / TT;
+  int tile = blockIdx.x;
+  int base[3];
+  base[2] = (tile % ntile) * TT;
+  tile /= ntile;
+  base[1] = (tile % ntile) * TT;
+  tile /= ntile;
+  base[0] = tile * TT;
+  const int I[3] = {it.i, it.j, it.k};
+  int loc[2][3];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = tid + q * 256;
+    loc[q][0] = e / (TT * TT);
+    loc[q][1] = (e / TT) % TT;
+    loc[q][2] = e % TT;
+  }
+  double acc[2] = {0.0, 0.0};
+  __syncthreads();
+
+  for (int sg = 0; sg < 6; ++sg) {
+    const int s0 = kPerm[sg][0], s1 = kPerm[sg][1], s2 = kPerm[sg][2];
+    const long long x = I[s0], y = I[s1], z = I[s2];
+    for (int t = 0; t < nterms; ++t) {
+      const TripTerm &tm = sterm[t];
+      if (tm.kind == 0 || tm.kind == 1) {
+        // kind 0: single index u (dim s0) from A[x][y][u][r], pair (v, w) (dims s1, s2) from B[z][v][w][r]
+        // kind 1: single index w (dim s2) from B[y][z][w][r], pair (u, v) (dims s0, s1) from A[x][u][v][r]
+        const int ds = (tm.kind == 0) ? s0 : s2;
+        const int dp1 = (tm.kind == 0) ? s1 : s0;
+        const int dp2 = (tm.kind == 0) ? s2 : s1;
+        const double *S;
+        long long sS, sSr;
+        const double *Pp;
+        long long sP1, sP2, sPr;
+        if (tm.kind == 0) {
+          S = tm.A + x * tm.sA[0] + y * tm.sA[1];
+          sS = tm.sA[2];
+          sSr = tm.sA[3];
+          Pp = tm.B + z * tm.sB[0];
+          sP1 = tm.sB[1];
+          sP2 = tm.sB[2];
+          sPr = tm.sB[3];
+        } else {
+          S = tm.B + y * tm.sB[0] + z * tm.sB[1];
+          sS = tm.sB[2];
+          sSr = tm.sB[3];
+          Pp = tm.A + x * tm.sA[0];
+          sP1 = tm.sA[1];
+          sP2 = tm.sA[2];
+          sPr = tm.sA[3];
+        }
+        for (int r0 = 0; r0 < tm.R; r0 += TR) {
+          {
+            int row = tid / TR, rr = tid % TR;
+            int g = base[ds] + row;
+            double v = 0.0;
+            if (g < nv && r0 + rr < tm.R) v = S[g * sS + (long long)(r0 + rr) * sSr];
+            Ps[row][rr] = v;
+          }
+#pragma unroll
+          for (int q = 0; q < (TT * TT * TR) / 256; ++q) {
+            int e = tid + q * 256;
+            int row = e / TR, rr = e % TR;
+            int g1 = base[dp1] + row / TT, g2 = base[dp2] + row % TT;
+            double v = 0.0;
+            if (g1 < nv && g2 < nv && r0 + rr < tm.R)
+              v = Pp[g1 * sP1 + g2 * sP2 + (long long)(r0 + rr) * sPr];
+            Qs[row][rr] = v;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const double *ps = Ps[loc[q][ds]];
+            const double *qs = Qs[loc[q][dp1] * TT + loc[q][dp2]];
+            double s = 0.0;
+#pragma unroll 8
+            for (int rr = 0; rr < TR; ++rr) s = fma(ps[rr], qs[rr], s);
+            acc[q] = fma(tm.coef, s, acc[q]);
+          }
+          __syncthreads();
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const long long u = base[s0] + loc[q][s0], v = base[s1] + loc[q][s1],
+                          w = base[s2] + loc[q][s2];
+          if (u >= nv || v >= nv || w >= nv) continue;
+          double val;
+          if (tm.kind == 2)
+            val = tm.A[x * tm.sA[0] + u * tm.sA[1]] *
+                  tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+          else
+            val = tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]] *
+                  tm.B[z * tm.sB[0] + w * tm.sB[1]];
+          acc[q] = fma(tm.coef, val, acc[q]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int a = base[0] + loc[q][0], b = base[1] + loc[q][1], c = base[2] + loc[q][2];
+    if (a >= nv || b >= nv || c >= nv) continue;
+    const double den = eps[NO + a] + eps[NO + b] + eps[NO + c] - eps[it.i] - eps[it.j] -
+                       eps[it.k] - omega;
+    double val;
+    if (fabs(den) < 1e-3) {
+      atomicOr(status, 1);
+      val = 0.0;
+    } else {
+      val = -acc[q] / den;
+    }
+    out[it.off + ((long long)a * nv + b) * nv + c] = val;
+  }
+}
+
+// Contravariant triples, virtual permutations with ijk fixed (Eq. contra_3):
+// Xt^{abc} = 4X^{abc} - 2X^{bac} - 2X^{cba} - 2X^{acb} + X^{cab} + X^{bca}.
+__global__ void contra3_kernel(const double *__restrict__ X, double *__restrict__ Xt,
+                               long long nblocks, int nv) {
+  const long long nv3 = (long long)nv * nv * nv;
+  const long long total = nblocks * nv3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long blk = e / nv3;
+    const long long r = e % nv3;
+    const int a = (int)(r / ((long long)nv * nv)), b = (int)((r / nv) % nv), c = (int)(r % nv);
+    const double *B = X + blk * nv3;
+    auto at = [&](int x, int y, int z) { return B[((long long)x * nv + y) * nv + z]; };
+    Xt[e] = 4.0 * at(a, b, c) - 2.0 * at(b, a, c) - 2.0 * at(c, b, a) - 2.0 * at(a, c, b) +
+            at(c, a, b) + at(b, c, a);
+  }
+}
+
+// Doubles element X(A,I,B,J) of a pair-symmetric quantity stored as the
+// active-pair block Xb[i][a][L][D]: found at [I][A][J][B] or [J][B][I][A].
+__device__ __forceinline__ double blk_get(const double *Xb, int I, int A, int J, int B, int no,
+                                          int nv, int NO, int NV) {
+  if (I < no && A < nv) return Xb[(((long long)I * nv + A) * NO + J) * NV + B];
+  if (J < no && B < nv) return Xb[(((long long)J * nv + B) * NO + I) * NV + A];
+  return 0.0;
+}
+
+// Unsymmetrised accumulator Z(A,I,B,J), nonzero only for an active first pair.
+__device__ __forceinline__ double z_get(const double *Zb, int I, int A, int J, int B, int no,
+                                        int nv, int NO, int NV) {
+  if (I < no && A < nv) return Zb[(((long long)I * nv + A) * NO + J) * NV + B];
+  return 0.0;
+}
+
+// mode 0: out = covariant(Delta^{-1} P Z)   (residual and rho doubles)
+// mode 1: out = P Z                          (sigma doubles)
+// P Z(A,I,B,J) = Z(A,I,B,J) + Z(B,J,A,I); covariant: (2 Y^{AB}_{IJ} + Y^{BA}_{IJ}) / 3.
+__global__ void finalize_doubles_kernel(const double *__restrict__ Zb, double *__restrict__ out,
+                                        int no, int nv, int NO, int NV, int mode) {
+  const long long total = (long long)no * nv * NO * NV;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int D = (int)(e % NV);
+    const int L = (int)((e / NV) % NO);
+    const int a = (int)((e / ((long long)NV * NO)) % nv);
+    const int i = (int)(e / ((long long)NV * NO * nv));
+    auto P = [&](int A, int I, int B, int J) {
+      return z_get(Zb, I, A, J, B, no, nv, NO, NV) + z_get(Zb, J, B, I, A, no, nv, NO, NV);
+    };
+    if (mode == 1) {
+      out[e] = P(a, i, D, L);
+    } else {
+      auto Y = [&](int A, int I, int B, int J) {
+        double v = P(A, I, B, J);
+        return (A == B && I == J) ? 0.5 * v : v;
+      };
+      out[e] = (2.0 * Y(a, i, D, L) + Y(D, i, a, L)) / 3.0;
+    }
+  }
+}
+
+// out = (2 X^{aD}_{iL} + X^{Da}_{iL}) / 3 on the block (covariant combination).
+__global__ void c2_block_kernel(const double *__restrict__ X, double *__restrict__ out, int no,
+                                int nv, int NO, int NV) {
+  const long long total = (long long)no * nv * NO * NV;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int D = (int)(e % NV);
+    const int L = (int)((e / NV) % NO);
+    const int a = (int)((e / ((long long)NV * NO)) % nv);
+    const int i = (int)(e / ((long long)NV * NO * nv));
+    out[e] = (2.0 * blk_get(X, i, a, L, D, no, nv, NO, NV) +
+              blk_get(X, i, D, L, a, no, nv, NO, NV)) / 3.0;
+  }
+}
+
+// Rbar = Delta R: double the diagonal elements X[i][a][i][a].
+__global__ void delta_block_kernel(const double *__restrict__ X, double *__restrict__ out, int no,
+                                   int nv, int NO, int NV) {
+  const long long total = (long long)no * nv * NO * NV;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int D = (int)(e % NV);
+    const int L = (int)((e / NV) % NO);
+    const int a = (int)((e / ((long long)NV * NO)) % nv);
+    const int i = (int)(e / ((long long)NV * NO * nv));
+    out[e] = (L == i && D == a) ? 2.0 * X[e] : X[e];
+  }
+}
+
+// T[i][a][b][L] = X[i][a][L][b], b < n_v (X^{ab}_{iL} with L contiguous).
+__global__ void transpose_tl_kernel(const double *__restrict__ X, double *__restrict__ T, int no,
+                                    int nv, int NO, int NV) {
+  const long long total = (long long)no * nv * nv * NO;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int L = (int)(e % NO);
+    const int b = (int)((e / NO) % nv);
+    const long long ia = e / ((long long)NO * nv);
+    T[e] = X[(ia * NO + L) * NV + b];
+  }
+}
+
+// sum_AI x1 y1 + sum over unique doubles: block weights 1/2 where both pairs
+// are active and not diagonal.
+__global__ void sd_dot_kernel(const double *__restrict__ x1, const double *__restrict__ x2,
+                              const double *__restrict__ y1, const double *__restrict__ y2,
+                              int no, int nv, int NO, int NV, double *__restrict__ out) {
+  __shared__ double red[256];
+  const long long n1 = (long long)NV * NO, n2 = (long long)no * nv * NO * NV;
+  double s = 0.0;
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n1 + n2; e += 256LL * gridDim.x) {
+    if (e < n1) {
+      s += x1[e] * y1[e];
+    } else {
+      long long f = e - n1;
+      const int D = (int)(f % NV);
+      const int L = (int)((f / NV) % NO);
+      const int a = (int)((f / ((long long)NV * NO)) % nv);
+      const int i = (int)(f / ((long long)NV * NO * nv));
+      double w = (L < no && D < nv && !(L == i && D == a)) ? 0.5 : 1.0;
+      s += w * x2[f] * y2[f];
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+// D += alpha * D0 (+ diag on the first n_diag diagonal elements), alpha and
+// diag read from device scalars: D_pq -= (lambda.R) D00_pq, D_LL += 2 lambda3.R3.
+__global__ void density_norm_kernel(double *__restrict__ D, const double *__restrict__ D00a,
+                                    const double *__restrict__ D00b, const double *__restrict__ s,
+                                    int nmo, int NO) {
+  // s[0] = lambda3.R3, s[1] = lambda_SD.R_SD
+  const long long total = (long long)nmo * nmo;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / nmo), q = (int)(e % nmo);
+    double v = D[e] - s[0] * (D00a[e] + D00b[e]) - s[1] * D00b[e];
+    if (p == q && p < NO) v += 2.0 * s[0];
+    D[e] = v;
+  }
+}
+
+}  // namespace mlcc3

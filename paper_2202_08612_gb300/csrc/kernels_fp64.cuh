@@ -1,0 +1,60 @@
+// Device-side data structures shared by the FP64 kernels and the host engine.
+#pragma once
+#include <cstdint>
+
+namespace mlcc3 {
+
+// One item of a batched strided tensor contraction
+//   C[m][n] += alpha * sum_k A(m,k) B(k,n),
+// m = (m1, m2), n = (n1, n2), k = (k1, k2, k3) (row-major decompositions).
+// Strides are per item so that a permuted view of a triples block
+// (X_{pqr}[x1][x2][x3] = X_{ijk}[...], i >= j >= k) is a plain stride set.
+struct BstcItem {
+  long long offA, offB, offC;
+  long long sA[5];  // m1, m2, k1, k2, k3
+  long long sB[5];  // k1, k2, k3, n1, n2
+  long long sC[4];  // m1, m2, n1, n2
+};
+
+struct BstcParams {
+  const double *A, *B;
+  double *C;
+  int M1, M2, N1, N2, K1, K2, K3;
+  double alpha;
+  const BstcItem *items;
+  int nitems;
+  int atomic;  // 1: accumulate with atomicAdd (items may overlap in C)
+};
+
+// One additive term of the pre-permutation triples expression V^{abc}_{ijk}
+// (Eq. tau3, Eq. R3, SI L3), evaluated for an ordered occupied triple
+// (x, y, z) and virtual triple (u, v, w):
+//   kind 0 (D-type): sum_r A[x][y][u][r] B[z][v][w][r]
+//   kind 1 (L-type): sum_r A[x][u][v][r] B[y][z][w][r]
+//   kind 2:          A[x][u] B[y][z][v][w]
+//   kind 3:          A[x][y][u][v] B[z][w]
+// Strides in the order the indices are listed; r is the last.
+struct TripTerm {
+  int kind;
+  int R;
+  double coef;
+  const double *A, *B;
+  long long sA[4];
+  long long sB[4];
+};
+
+// A unique batch i >= j >= k with its output block offset (in elements).
+struct TripItem {
+  int i, j, k, pad;
+  long long off;
+};
+
+constexpr int kMaxTerms = 6;
+
+// Terms passed by value as a kernel parameter.
+struct TripTerms {
+  TripTerm t[kMaxTerms];
+  int n;
+};
+
+}  // namespace mlcc3

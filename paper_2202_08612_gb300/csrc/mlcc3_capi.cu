@@ -1,0 +1,1366 @@
+// C ABI and host orchestration of the MLCC3 triples path.
+//
+// Every contraction of the paper's equations is expressed as a batched
+// strided contraction (bstc_kernel) over the unique batches i >= j >= k:
+// the block X_{ijk} of a batch is computed once (triples_build_kernel) and
+// each distinct ordering (p,q,r) of (i,j,k) reads it through a permuted
+// stride set (pair symmetry X^{abc}_{ijk} = X^{sigma(abc)}_{sigma(ijk)},
+// Eq. tau3).  Sums over all ordered occupied triples in the SI equations
+// become sums over (batch, distinct ordering).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "engine.cuh"
+#include "kernels_fp64.cuh"
+#include "mlcc3.h"
+
+namespace mlcc3 {
+__global__ void bstc_kernel(BstcParams p);
+__global__ void bstc_dot_kernel(BstcParams p);
+__global__ void bstc_copy_kernel(BstcParams p);
+__global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
+                                     double, double *, int *);
+__global__ void contra3_kernel(const double *, double *, long long, int);
+__global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
+__global__ void c2_block_kernel(const double *, double *, int, int, int, int);
+__global__ void delta_block_kernel(const double *, double *, int, int, int, int);
+__global__ void transpose_tl_kernel(const double *, double *, int, int, int, int);
+__global__ void sd_dot_kernel(const double *, const double *, const double *, const double *, int,
+                              int, int, int, double *);
+__global__ void density_norm_kernel(double *, const double *, const double *, const double *,
+                                    int, int);
+
+static thread_local std::string g_last_error;
+
+void check_cuda(cudaError_t e, const char *what) {
+  if (e != cudaSuccess)
+    throw Error{e == cudaErrorMemoryAllocation ? MLCC3_ERR_OOM : MLCC3_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+static int grid1d(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152LL * 64) g = 152LL * 64;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace mlcc3
+
+using namespace mlcc3;
+
+// ---------------------------------------------------------------------------
+// Context helpers
+// ---------------------------------------------------------------------------
+void *mlcc3_ctx::raw(const std::string &name, size_t bytes) {
+  auto it = scratch.find(name);
+  if (it != scratch.end() && it->second.second >= bytes) return it->second.first;
+  if (it != scratch.end()) {
+    check_cuda(cudaStreamSynchronize(stream), "sync before realloc");
+    cudaFree(it->second.first);
+    scratch.erase(it);
+  }
+  void *p = nullptr;
+  check_cuda(cudaMalloc(&p, bytes < 256 ? 256 : bytes), ("cudaMalloc " + name).c_str());
+  scratch[name] = {p, bytes};
+  return p;
+}
+
+double *mlcc3_ctx::buf(const std::string &name, size_t n) {
+  return static_cast<double *>(raw(name, n * sizeof(double)));
+}
+
+void mlcc3_ctx::zero(double *p, size_t n) {
+  check_cuda(cudaMemsetAsync(p, 0, n * sizeof(double), stream), "memset");
+}
+
+const BstcItem *mlcc3_ctx::dev_items(const std::string &key,
+                                     const std::function<std::vector<BstcItem>()> &make, int *n) {
+  auto it = items.find(key);
+  if (it != items.end()) {
+    *n = it->second.second;
+    return static_cast<const BstcItem *>(it->second.first);
+  }
+  std::vector<BstcItem> v = make();
+  void *p = nullptr;
+  size_t bytes = std::max<size_t>(1, v.size()) * sizeof(BstcItem);
+  check_cuda(cudaMalloc(&p, bytes), "cudaMalloc items");
+  if (!v.empty())
+    check_cuda(cudaMemcpy(p, v.data(), v.size() * sizeof(BstcItem), cudaMemcpyHostToDevice),
+               "upload items");
+  items[key] = {p, (int)v.size()};
+  *n = (int)v.size();
+  return static_cast<const BstcItem *>(p);
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+const double *mlcc3_ctx::in(const double *p, size_t n, const std::string &name) {
+  if (p == nullptr) throw Error{MLCC3_ERR_ARG, "null input array: " + name};
+  if (is_device_ptr(p)) return p;
+  double *d = buf("in:" + name, n);
+  check_cuda(cudaMemcpyAsync(d, p, n * sizeof(double), cudaMemcpyHostToDevice, stream),
+             "stage input");
+  return d;
+}
+
+double *mlcc3_ctx::out(double *p, size_t n, const std::string &name) {
+  if (p == nullptr) throw Error{MLCC3_ERR_ARG, "null output array: " + name};
+  if (is_device_ptr(p)) return p;
+  double *d = buf("out:" + name, n);
+  pending_out.push_back({(void *)p, (void *)d, (void *)(n * sizeof(double))});
+  return d;
+}
+
+void mlcc3_ctx::finish() {
+  for (auto &o : pending_out)
+    check_cuda(cudaMemcpyAsync(o[0], o[1], (size_t)o[2], cudaMemcpyDeviceToHost, stream),
+               "copy output");
+  pending_out.clear();
+  int st = 0;
+  check_cuda(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream),
+             "read status");
+  check_cuda(cudaStreamSynchronize(stream), "synchronize");
+  check_cuda(cudaGetLastError(), "kernel launch");
+  if (st & 1) {
+    check_cuda(cudaMemsetAsync(status, 0, sizeof(int), stream), "reset status");
+    throw Error{MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk} - omega| < 1e-3 in a triples block"};
+  }
+}
+
+void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &sh, double alpha,
+                     const BstcItem *it, int nitems, bool atomic) {
+  if (nitems == 0) return;
+  BstcParams p;
+  p.A = A;
+  p.B = B;
+  p.C = C;
+  p.M1 = (int)sh.M1;
+  p.M2 = (int)sh.M2;
+  p.N1 = (int)sh.N1;
+  p.N2 = (int)sh.N2;
+  p.K1 = (int)sh.K1;
+  p.K2 = (int)sh.K2;
+  p.K3 = (int)sh.K3;
+  p.alpha = alpha;
+  p.items = it;
+  p.nitems = nitems;
+  p.atomic = atomic ? 1 : 0;
+  long long M = sh.M1 * sh.M2, N = sh.N1 * sh.N2;
+  if (M == 0 || N == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
+  const long long tiles = ((N + 63) / 64) * ((M + 63) / 64);
+  for (int z0 = 0; z0 < nitems; z0 += 65535) {
+    p.items = it + z0;
+    int nz = std::min(65535, nitems - z0);
+    dim3 grid((unsigned)tiles, (unsigned)nz);
+    bstc_kernel<<<grid, 256, 0, stream>>>(p);
+  }
+  check_cuda(cudaGetLastError(), "bstc launch");
+}
+
+void mlcc3_ctx::bstc1(const double *A, const double *B, double *C, const Shape &sh, double alpha,
+                      const BstcItem &item, const std::string &key) {
+  int n = 0;
+  const BstcItem *d = dev_items(key, [&] { return std::vector<BstcItem>{item}; }, &n);
+  bstc(A, B, C, sh, alpha, d, n, false);
+}
+
+void mlcc3_ctx::dot(const double *A, const double *B, double *C, const Shape &sh, double alpha,
+                    const BstcItem *it, int nitems) {
+  if (nitems == 0) return;
+  BstcParams p{};
+  p.A = A;
+  p.B = B;
+  p.C = C;
+  p.K1 = (int)sh.K1;
+  p.K2 = (int)sh.K2;
+  p.K3 = (int)sh.K3;
+  p.alpha = alpha;
+  p.items = it;
+  p.nitems = nitems;
+  bstc_dot_kernel<<<nitems, 256, 0, stream>>>(p);
+  check_cuda(cudaGetLastError(), "dot launch");
+}
+
+// ---------------------------------------------------------------------------
+// Engine: stride bookkeeping and the stages of the path
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPermH[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+struct S {
+  long long NO, NV, no, nv, NJ, nmo;
+  long long bi, ba, bL;      // active-pair block [i][a][L][D]
+  long long gk, gb, gc;      // [k][b][c][D]
+  long long oj, ok, oc;      // [j][k][c][L]
+  long long vj, vb, vk;      // [j][b][k][c]
+  long long ti, ta, tb;      // [i][a][b][L]
+  long long lJ;              // Lt [J][p][q]
+  long long nv3;
+  explicit S(const mlcc3_ctx *c) {
+    NO = c->NO; NV = c->NV; no = c->no; nv = c->nv; NJ = c->NJ; nmo = c->nmo;
+    bi = nv * NO * NV; ba = NO * NV; bL = NV;
+    gk = nv * nv * NV; gb = nv * NV; gc = NV;
+    oj = no * nv * NO; ok = nv * NO; oc = NO;
+    vj = nv * no * nv; vb = no * nv; vk = nv;
+    ti = nv * nv * NO; ta = nv * NO; tb = NO;
+    lJ = nmo * nmo;
+    nv3 = nv * nv * nv;
+  }
+  size_t blk() const { return (size_t)(no * nv * NO * NV); }
+  size_t gvsz() const { return (size_t)(no * nv * nv * NV); }
+  size_t gosz() const { return (size_t)(no * no * nv * NO); }
+};
+
+void make_batches(mlcc3_ctx *c) {
+  c->batches.clear();
+  c->batches_cvs.clear();
+  long long nv3 = c->nv * c->nv * c->nv;
+  for (int i = 0; i < c->no; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k) {
+        if (i == j && j == k) continue;  // contravariant block vanishes
+        TripItem t{i, j, k, 0, 0};
+        t.off = (long long)c->batches.size() * nv3;
+        c->batches.push_back(t);
+      }
+  for (auto t : c->batches) {
+    bool core = !c->core.empty() && (c->core[t.i] || c->core[t.j] || c->core[t.k]);
+    if (core) c->batches_cvs.push_back(t);  // keeps the full-list block offset
+  }
+  auto ords_of = [&](const std::vector<TripItem> &bs) {
+    std::vector<Ord> v;
+    const long long cs[3] = {c->nv * c->nv, c->nv, 1};
+    for (size_t u = 0; u < bs.size(); ++u) {
+      const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
+      std::set<std::tuple<int, int, int>> seen;
+      for (int sg = 0; sg < 6; ++sg) {
+        int p = I[kPermH[sg][0]], q = I[kPermH[sg][1]], r = I[kPermH[sg][2]];
+        if (!seen.insert({p, q, r}).second) continue;
+        Ord o;
+        o.u = (int)u;
+        o.p = p;
+        o.q = q;
+        o.r = r;
+        o.off = bs[u].off;
+        for (int t = 0; t < 3; ++t) o.vs[t] = cs[kPermH[sg][t]];
+        v.push_back(o);
+      }
+    }
+    return v;
+  };
+  c->ords = ords_of(c->batches);
+  c->ords_cvs = ords_of(c->batches_cvs);
+}
+
+void launch_1d(mlcc3_ctx *c, long long n, const char *what,
+               const std::function<void(int)> &launch) {
+  if (n <= 0) return;
+  launch(grid1d(n));
+  check_cuda(cudaGetLastError(), what);
+}
+
+// sum_{LD} (2 g_kcLD - g_kDLc) x^D_L for active k, c, through the Cholesky
+// factors (SI Upsilon_kc; with x = t1 the T1-transformed Fock block F_kc).
+void fock_ov(mlcc3_ctx *c, const double *x1, double *out, const std::string &tag) {
+  S s(c);
+  double *xs = c->buf("fov_xs", s.NJ);
+  double *PA = c->buf("fov_PA", s.NJ * s.no * s.NO);
+  c->zero(xs, s.NJ);
+  c->zero(PA, s.NJ * s.no * s.NO);
+  c->zero(out, s.no * s.nv);
+  const double *LtV = c->Lt + s.NO;  // column offset to the virtual block
+  Shape sh;
+  // xs[J] = sum_{L,D} Lt[J][L][NO+D] x[D][L]
+  sh = Shape{};
+  sh.M1 = s.NJ; sh.K1 = s.NO; sh.K2 = s.NV;
+  c->bstc1(LtV, x1, xs, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 0, s.nmo, 1, 0}, {1, s.NO, 0, 0, 0}, {1, 0, 0, 0}), "fov1");
+  // out[k][c] = 2 sum_J Lt[J][k][NO+c] xs[J]
+  sh = Shape{};
+  sh.M1 = s.no; sh.M2 = s.nv; sh.K1 = s.NJ;
+  c->bstc1(LtV, xs, out, sh, 2.0, mk_item(0, 0, 0, {s.nmo, 1, s.lJ, 0, 0}, {1, 0, 0, 0, 0}, {s.nv, 1, 0, 0}), "fov2");
+  // PA[J][k][L] = sum_D Lt[J][k][NO+D] x[D][L]
+  sh = Shape{};
+  sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
+  c->bstc1(LtV, x1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, s.nmo, 1, 0, 0}, {s.NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "fov3");
+  // out[k][c] -= sum_{J,L} PA[J][k][L] Lt[J][L][NO+c]
+  sh = Shape{};
+  sh.M1 = s.no; sh.N1 = s.nv; sh.K1 = s.NJ; sh.K2 = s.NO;
+  c->bstc1(PA, LtV, out, sh, -1.0, mk_item(0, 0, 0, {s.NO, 0, s.no * s.NO, 1, 0}, {s.lJ, s.nmo, 0, 1, 0}, {s.nv, 0, 1, 0}), "fov4");
+  (void)tag;
+}
+
+// Triples blocks X_u for every batch of `bs`, written at bs[u].off of `out`.
+void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string &bkey,
+             const std::vector<TripItem> &bs, double omega, double *out) {
+  if (bs.empty() || c->nv == 0) return;
+  if (terms.size() > (size_t)kMaxTerms) throw Error{MLCC3_ERR_ARG, "too many triples terms"};
+  TripTerms tt{};
+  for (size_t t = 0; t < terms.size(); ++t) tt.t[t] = terms[t];
+  tt.n = (int)terms.size();
+  int n = 0;
+  // batch list on the device (cached per key)
+  auto it = c->items.find(bkey);
+  const TripItem *db;
+  if (it == c->items.end()) {
+    void *p = nullptr;
+    check_cuda(cudaMalloc(&p, bs.size() * sizeof(TripItem)), "cudaMalloc batches");
+    check_cuda(cudaMemcpy(p, bs.data(), bs.size() * sizeof(TripItem), cudaMemcpyHostToDevice),
+               "upload batches");
+    c->items[bkey] = {p, (int)bs.size()};
+    db = static_cast<const TripItem *>(p);
+  } else {
+    db = static_cast<const TripItem *>(it->second.first);
+  }
+  n = (int)bs.size();
+  long long nt = (c->nv + 7) / 8;
+  dim3 grid((unsigned)(nt * nt * nt), (unsigned)n);
+  triples_build_kernel<<<grid, 256, 0, c->stream>>>(tt, db, c->eps, (int)c->NO, (int)c->nv,
+                                                    omega, out, c->status);
+  check_cuda(cudaGetLastError(), "triples_build launch");
+}
+
+void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
+  long long n = nblocks * c->nv * c->nv * c->nv;
+  launch_1d(c, n, "contra3", [&](int g) {
+    contra3_kernel<<<g, 256, 0, c->stream>>>(X, Xt, nblocks, (int)c->nv);
+  });
+}
+
+TripTerm term(int kind, int R, double coef, const double *A, std::array<long long, 4> sA,
+              const double *B, std::array<long long, 4> sB) {
+  TripTerm t;
+  t.kind = kind;
+  t.R = R;
+  t.coef = coef;
+  t.A = A;
+  t.B = B;
+  for (int i = 0; i < 4; ++i) t.sA[i] = sA[i];
+  for (int i = 0; i < 4; ++i) t.sB[i] = sB[i];
+  return t;
+}
+
+// tau3 (Eq. tau3): D-type  t^{aD}_{ij} g_bDck, L-type -t^{ab}_{iL} g_Ljck.
+std::vector<TripTerm> tau_terms(mlcc3_ctx *c) {
+  S s(c);
+  return {term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
+          term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1})};
+}
+
+// Contravariant back-contraction of the blocks of `ords` into singles s1[A][I]
+// and the unsymmetrised doubles accumulator Zb (active-pair block layout):
+//   s^a_p          += cs  sum_{bc} X_{pqr}[a][b][c] Gs[q][b][r][c]
+//   Z[p][a][q][b]  += cF  sum_c  X_{pqr}[a][b][c] F[r][c]
+//   Z[p][a][L][b]  += cL  sum_c  X_{pqr}[a][b][c] GL[q][r][c][L]
+//   Z[p][a][q][D]  += cD  sum_{bc} X_{pqr}[a][b][c] GD[r][b][c][D]
+struct BackSet {
+  double cs = 0;
+  const double *Gs = nullptr;
+  double cF = 0;
+  const double *F = nullptr;
+  double cL = 0;
+  const double *GL = nullptr;
+  double cD = 0;
+  const double *GD = nullptr;
+};
+
+void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
+                   const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
+  S s(c);
+  int n = 0;
+  const BstcItem *it;
+  Shape sh;
+  if (bset.Gs) {
+    it = c->dev_items(okey + ":bs", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ords)
+        v.push_back(mk_item(o.off, o.q * s.vj + o.r * s.vk, o.p,
+                            {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.vb, 1, 0, 0, 0}, {s.NO, 0, 0, 0}));
+      return v;
+    }, &n);
+    sh = Shape{};
+    sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true);
+  }
+  if (bset.F) {
+    it = c->dev_items(okey + ":bF", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ords)
+        v.push_back(mk_item(o.off, o.r * s.nv, o.p * s.bi + o.q * s.bL,
+                            {o.vs[0], o.vs[1], o.vs[2], 0, 0}, {1, 0, 0, 0, 0}, {s.ba, 1, 0, 0}));
+      return v;
+    }, &n);
+    sh = Shape{};
+    sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
+    c->bstc(X, bset.F, Zb, sh, bset.cF, it, n, true);
+  }
+  if (bset.GL) {
+    it = c->dev_items(okey + ":bL", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ords)
+        v.push_back(mk_item(o.off, o.q * s.oj + o.r * s.ok, o.p * s.bi,
+                            {o.vs[0], o.vs[1], o.vs[2], 0, 0}, {s.oc, 0, 0, 1, 0}, {s.ba, 1, s.bL, 0}));
+      return v;
+    }, &n);
+    sh = Shape{};
+    sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NO;
+    c->bstc(X, bset.GL, Zb, sh, bset.cL, it, n, true);
+  }
+  if (bset.GD) {
+    it = c->dev_items(okey + ":bD", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ords)
+        v.push_back(mk_item(o.off, o.r * s.gk, o.p * s.bi + o.q * s.bL,
+                            {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.gb, s.gc, 0, 1, 0}, {s.ba, 0, 1, 0}));
+      return v;
+    }, &n);
+    sh = Shape{};
+    sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NV;
+    c->bstc(X, bset.GD, Zb, sh, bset.cD, it, n, true);
+  }
+}
+
+void finalize(mlcc3_ctx *c, const double *Zb, double *out, int mode) {
+  S s(c);
+  launch_1d(c, (long long)s.blk(), "finalize", [&](int g) {
+    finalize_doubles_kernel<<<g, 256, 0, c->stream>>>(Zb, out, (int)s.no, (int)s.nv, (int)s.NO,
+                                                      (int)s.NV, mode);
+  });
+}
+
+void transpose_tl(mlcc3_ctx *c, const double *X, double *T) {
+  S s(c);
+  launch_1d(c, s.no * s.nv * s.nv * s.NO, "transpose_tl", [&](int g) {
+    transpose_tl_kernel<<<g, 256, 0, c->stream>>>(X, T, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+  });
+}
+
+// tau and its contravariant form for all unique batches.
+void build_tau(mlcc3_ctx *c, double **tau, double **taut) {
+  S s(c);
+  size_t nb = c->batches.size();
+  *tau = c->buf("tau", nb * s.nv3);
+  *taut = c->buf("taut", nb * s.nv3);
+  triples(c, tau_terms(c), "batches", c->batches, 0.0, *tau);
+  contra3(c, *tau, *taut, (long long)nb);
+}
+
+// Upsilon blocks for one trial vector (Eqs. ups_v, ups_o) and the rho tau-term
+// intermediates H1[j][k][c][L] = sum_D g_jDkc R^D_L, H2[k][b][c][D] = -sum_L g_Lbkc R^D_L.
+struct Ups {
+  double *Uv, *Uo, *Ukc, *H1, *H2;
+};
+
+Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
+  S s(c);
+  Ups u;
+  u.Uv = c->buf("Uv", s.gvsz());
+  u.Uo = c->buf("Uo", s.gosz());
+  u.Ukc = c->buf("Ukc", s.no * s.nv);
+  u.H1 = c->buf("H1", s.gosz());
+  u.H2 = c->buf("H2", s.gvsz());
+  double *LRvV = c->buf("LRvV", s.NJ * s.nv * s.NV);
+  double *LRvo = c->buf("LRvo", s.NJ * s.nv * s.no);
+  double *LROo = c->buf("LROo", s.NJ * s.NO * s.no);
+  double *PA = c->buf("PA", s.NJ * s.no * s.NO);
+  double *PB = c->buf("PB", s.NJ * s.nv * s.NV);
+  for (double *p : {u.Uv, u.H2}) c->zero(p, s.gvsz());
+  for (double *p : {u.Uo, u.H1}) c->zero(p, s.gosz());
+  c->zero(LRvV, s.NJ * s.nv * s.NV);
+  c->zero(LRvo, s.NJ * s.nv * s.no);
+  c->zero(LROo, s.NJ * s.NO * s.no);
+  c->zero(PA, s.NJ * s.no * s.NO);
+  c->zero(PB, s.NJ * s.nv * s.NV);
+  const double *Lt = c->Lt;
+  const long long nmo = s.nmo, NO = s.NO;
+  Shape sh;
+  // LR = [Lt, R1] blocks: LRvV[J][b][D] = -sum_M R^b_M Lt[J][M][NO+D]
+  sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NJ; sh.N2 = s.NV; sh.K1 = s.NO;
+  c->bstc1(R1, Lt + NO, LRvV, sh, -1.0, mk_item(0, 0, 0, {NO, 0, 1, 0, 0}, {nmo, 0, 0, s.lJ, 1}, {s.NV, 0, s.nv * s.NV, 1}), "ups1");
+  // LRvo[J][c][k] = sum_E Lt[J][NO+c][NO+E] R^E_k - sum_M R^c_M Lt[J][M][k]
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.no; sh.K1 = s.NV;
+  c->bstc1(Lt + NO * nmo + NO, R1, LRvo, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.nv * s.no, s.no, 1, 0}), "ups2");
+  sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NJ; sh.N2 = s.no; sh.K1 = s.NO;
+  c->bstc1(R1, Lt, LRvo, sh, -1.0, mk_item(0, 0, 0, {NO, 0, 1, 0, 0}, {nmo, 0, 0, s.lJ, 1}, {s.no, 0, s.nv * s.no, 1}), "ups3");
+  // LROo[J][L][j] = sum_E Lt[J][L][NO+E] R^E_j
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.NO; sh.N1 = s.no; sh.K1 = s.NV;
+  c->bstc1(Lt + NO, R1, LROo, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.NO * s.no, s.no, 1, 0}), "ups4");
+  // Uv[k][b][c][D] = sum_J (LRvV[J][b][D] Lt[J][NO+c][k] + Lt[J][NO+b][NO+D] LRvo[J][c][k])
+  sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
+  c->bstc1(Lt + NO * nmo, LRvV, u.Uv, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.nv * s.NV, 0, 0, s.NV, 1}, {s.gk, s.gc, s.gb, 1}), "ups5");
+  c->bstc1(LRvo, Lt + NO * nmo + NO, u.Uv, sh, 1.0, mk_item(0, 0, 0, {1, s.no, s.nv * s.no, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.gk, s.gc, s.gb, 1}), "ups6");
+  // Uo[j][k][c][L] = sum_J (LROo[J][L][j] Lt[J][NO+c][k] + Lt[J][L][j] LRvo[J][c][k])
+  sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
+  c->bstc1(Lt + NO * nmo, LROo, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.NO * s.no, 0, 0, 1, s.no}, {s.ok, s.oc, s.oj, 1}), "ups7");
+  c->bstc1(LRvo, Lt, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, s.no, s.nv * s.no, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.ok, s.oc, s.oj, 1}), "ups8");
+  // Upsilon_kc
+  fock_ov(c, R1, u.Ukc, "ups");
+  // H1[j][k][c][L] = sum_J PA[J][j][L] Lt[J][k][NO+c], PA[J][j][L] = sum_D Lt[J][j][NO+D] R^D_L
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
+  c->bstc1(Lt + NO, R1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "ups9");
+  sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
+  c->bstc1(Lt + NO, PA, u.H1, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.no * s.NO, 0, 0, s.NO, 1}, {s.ok, s.oc, s.oj, 1}), "ups10");
+  // H2[k][b][c][D] = -sum_J PB[J][b][D] Lt[J][k][NO+c], PB[J][b][D] = sum_L Lt[J][L][NO+b] R^D_L
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.NV; sh.K1 = s.NO;
+  c->bstc1(Lt + NO, R1, PB, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 1, nmo, 0, 0}, {1, 0, 0, NO, 0}, {s.nv * s.NV, s.NV, 1, 0}), "ups11");
+  sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
+  c->bstc1(Lt + NO, PB, u.H2, sh, -1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.nv * s.NV, 0, 0, s.NV, 1}, {s.gk, s.gc, s.gb, 1}), "ups12");
+  return u;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Stages
+// ---------------------------------------------------------------------------
+static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double *t1_in,
+                               const double *eps_in, const double *t2c_in, const double *t2x_in) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const double *chol = c->in(chol_in, s.NJ * s.lJ, "chol");
+  check_cuda(cudaMemcpyAsync(c->eps, c->in(eps_in, nmo, "eps"), nmo * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->stream), "eps");
+  check_cuda(cudaMemcpyAsync(c->t1, c->in(t1_in, s.NV * NO, "t1"), s.NV * NO * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->stream), "t1");
+  check_cuda(cudaMemcpyAsync(c->t2c, c->in(t2c_in, s.blk(), "t2c"), s.blk() * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->stream), "t2c");
+  check_cuda(cudaMemcpyAsync(c->t2x, c->in(t2x_in, s.blk(), "t2x"), s.blk() * sizeof(double),
+                             cudaMemcpyDeviceToDevice, c->stream), "t2x");
+  // Lt = (1 - t1) L (1 + t1) (Sec. 2, T1-transformed Hamiltonian):
+  // X = L + L t (occupied columns), then Lt[NO+A][q] = X[NO+A][q] - sum_I t[A][I] X[I][q].
+  check_cuda(cudaMemcpyAsync(c->Lt, chol, s.NJ * s.lJ * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream), "Lt copy");
+  Shape sh;
+  sh.M1 = s.NJ; sh.M2 = nmo; sh.N1 = NO; sh.K1 = s.NV;
+  c->bstc1(chol + NO, c->t1, c->Lt, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.lJ, nmo, 1, 0}), "t1a");
+  sh = Shape{};
+  sh.M1 = s.NV; sh.N1 = s.NJ; sh.N2 = nmo; sh.K1 = NO;
+  c->bstc1(c->t1, c->Lt, c->Lt + NO * nmo, sh, -1.0, mk_item(0, 0, 0, {NO, 0, 1, 0, 0}, {nmo, 0, 0, s.lJ, 1}, {nmo, 0, s.lJ, 1}), "t1b");
+  // Integral blocks g_PQRS = sum_J Lt^J_PQ Lt^J_RS (SI).
+  const double *Lt = c->Lt;
+  for (double *p : {c->Gv, c->Gb}) c->zero(p, s.gvsz());
+  for (double *p : {c->Go, c->Gx}) c->zero(p, s.gosz());
+  c->zero(c->Govov, s.no * s.nv * s.no * s.nv);
+  sh = Shape{};
+  sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
+  // Gv[k][b][c][D] = g_bDck: A(k,c;J) = Lt[J][NO+c][k], B(J;b,D) = Lt[J][NO+b][NO+D]
+  c->bstc1(Lt + NO * nmo, Lt + NO * nmo + NO, c->Gv, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.gk, s.gc, s.gb, 1}), "Gv");
+  // Gb[k][b][c][D] = g_Dbkc: A(k,c;J) = Lt[J][k][NO+c], B(J;b,D) = Lt[J][NO+D][NO+b]
+  c->bstc1(Lt + NO, Lt + NO * nmo + NO, c->Gb, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.gk, s.gc, s.gb, 1}), "Gb");
+  sh = Shape{};
+  sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = NO; sh.K1 = s.NJ;
+  // Go[j][k][c][L] = g_Ljck: A(k,c;J) = Lt[J][NO+c][k], B(J;j,L) = Lt[J][L][j]
+  c->bstc1(Lt + NO * nmo, Lt, c->Go, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.ok, s.oc, s.oj, 1}), "Go");
+  // Gx[j][k][c][L] = g_jLkc: A(k,c;J) = Lt[J][k][NO+c], B(J;j,L) = Lt[J][j][L]
+  c->bstc1(Lt + NO, Lt, c->Gx, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.ok, s.oc, s.oj, 1}), "Gx");
+  sh = Shape{};
+  sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.nv; sh.K1 = s.NJ;
+  // Govov[j][b][k][c] = g_jbkc: A(k,c;J) = Lt[J][k][NO+c], B(J;j,b) = Lt[J][j][NO+b]
+  c->bstc1(Lt + NO, Lt + NO, c->Govov, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.vk, 1, s.vj, s.vb}), "Govov");
+  fock_ov(c, c->t1, c->F, "F");
+  transpose_tl(c, c->t2c, c->Tl);
+  c->built = true;
+}
+
+static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_out) {
+  S s(c);
+  double *o1 = c->out(omega1_out, s.NV * s.NO, "omega1");
+  double *o2 = c->out(omega2_out, s.blk(), "omega2");
+  double *tau, *taut;
+  build_tau(c, &tau, &taut);
+  double *Zb = c->buf("Zb", s.blk());
+  c->zero(Zb, s.blk());
+  c->zero(o1, s.NV * s.NO);
+  BackSet b;
+  b.cs = 0.5; b.Gs = c->Govov;
+  b.cF = 0.5; b.F = c->F;
+  b.cL = -1.0; b.GL = c->Gx;
+  b.cD = 1.0; b.GD = c->Gb;
+  back_contract(c, taut, c->ords, "ords", b, o1, Zb);
+  finalize(c, Zb, o2, 0);
+}
+
+static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, const double *R1_in,
+                              const double *R2_in, double *rho1_out, double *rho2_out) {
+  S s(c);
+  const bool cvs = !c->core.empty();
+  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
+  const std::vector<Ord> &os = cvs ? c->ords_cvs : c->ords;
+  const std::string bkey = cvs ? "batches_cvs" : "batches";
+  const std::string okey = cvs ? "ords_cvs" : "ords";
+  const double *R1all = c->in(R1_in, (size_t)n_vec * s.NV * s.NO, "R1");
+  const double *R2all = c->in(R2_in, (size_t)n_vec * s.blk(), "R2");
+  double *rho1all = c->out(rho1_out, (size_t)n_vec * s.NV * s.NO, "rho1");
+  double *rho2all = c->out(rho2_out, (size_t)n_vec * s.blk(), "rho2");
+  double *tau, *taut;
+  build_tau(c, &tau, &taut);
+  size_t nb = c->batches.size();
+  double *R3 = c->buf("R3", nb * s.nv3);
+  double *R3t = c->buf("R3t", nb * s.nv3);
+  double *Rbar = c->buf("Rbar", s.blk());
+  double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * s.NO);
+  double *Zb = c->buf("Zb", s.blk());
+  for (int v = 0; v < n_vec; ++v) {
+    const double *R1 = R1all + (size_t)v * s.NV * s.NO;
+    const double *R2 = R2all + (size_t)v * s.blk();
+    double *rho1 = rho1all + (size_t)v * s.NV * s.NO;
+    double *rho2 = rho2all + (size_t)v * s.blk();
+    if (!(std::fabs(omega[v]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
+    launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
+      delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+    });
+    transpose_tl(c, Rbar, Rbl);
+    Ups u = build_upsilon(c, R1);
+    // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, Rbar, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, Rbl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1}),
+        term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
+    triples(c, terms, bkey, bs, omega[v], R3);
+    contra3(c, R3, R3t, (long long)nb);
+    c->zero(Zb, s.blk());
+    c->zero(rho1, s.NV * s.NO);
+    BackSet b;
+    b.cs = 0.5; b.Gs = c->Govov;
+    b.cF = 0.5; b.F = c->F;
+    b.cL = -1.0; b.GL = c->Gx;
+    b.cD = 1.0; b.GD = c->Gb;
+    back_contract(c, R3t, os, okey, b, rho1, Zb);
+    BackSet bt;  // tau terms: 1/2 taut Upsilon_kc, -taut H1, +taut H2 (H2 carries the minus)
+    bt.cF = 0.5; bt.F = u.Ukc;
+    bt.cL = -1.0; bt.GL = u.H1;
+    bt.cD = 1.0; bt.GD = u.H2;
+    back_contract(c, taut, os, okey, bt, nullptr, Zb);
+    finalize(c, Zb, rho2, 0);
+  }
+}
+
+static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const double *L1_in,
+                             const double *L2_in, double *sig1_out, double *sig2_out) {
+  S s(c);
+  const bool cvs = !c->core.empty();
+  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
+  const std::vector<Ord> &os = cvs ? c->ords_cvs : c->ords;
+  const std::string bkey = cvs ? "batches_cvs" : "batches";
+  const std::string okey = cvs ? "ords_cvs" : "ords";
+  const double *L1all = c->in(L1_in, (size_t)n_vec * s.NV * s.NO, "L1");
+  const double *L2all = c->in(L2_in, (size_t)n_vec * s.blk(), "L2");
+  double *sig1all = c->out(sig1_out, (size_t)n_vec * s.NV * s.NO, "sigma1");
+  double *sig2all = c->out(sig2_out, (size_t)n_vec * s.blk(), "sigma2");
+  double *tau, *taut;
+  build_tau(c, &tau, &taut);
+  size_t nb = c->batches.size();
+  double *L3 = c->buf("L3", nb * s.nv3);
+  double *L3t = c->buf("L3t", nb * s.nv3);
+  double *Lc = c->buf("Lc", s.blk());
+  double *LcT = c->buf("LcT", s.no * s.nv * s.nv * s.NO);
+  double *Sb = c->buf("Zb", s.blk());
+  double *Y1 = c->buf("Y1", s.gvsz());
+  double *Y2 = c->buf("Y2", s.gosz());
+  double *P1 = c->buf("Pq", s.gosz());
+  double *P2 = c->buf("P2", s.gvsz());
+  double *Y3 = c->buf("Y3", s.no * s.nv);
+  double *W = c->buf("Wz", s.NJ * s.no * s.nv);
+  double *Z2 = c->buf("Z2", s.NJ * s.nv * s.NV);
+  double *Z4 = c->buf("Z4", s.NJ * s.no * s.NO);
+  double *yv = c->buf("yv", s.NJ);
+  double *Q = c->buf("Q", s.NJ * s.no * s.NO);
+  double *Q2 = c->buf("Q2", s.NJ * s.nv * s.NV);
+  const double *Lt = c->Lt;
+  const long long nmo = s.nmo, NO = s.NO;
+  for (int v = 0; v < n_vec; ++v) {
+    const double *L1 = L1all + (size_t)v * s.NV * s.NO;
+    const double *L2 = L2all + (size_t)v * s.blk();
+    double *sig1 = sig1all + (size_t)v * s.NV * s.NO;
+    double *sig2 = sig2all + (size_t)v * s.blk();
+    launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
+      c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+    });
+    transpose_tl(c, Lc, LcT);
+    // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, LcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
+        term(2, 0, 0.5, L1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
+        term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
+    triples(c, terms, bkey, bs, omega[v], L3);
+    contra3(c, L3, L3t, (long long)nb);
+    // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
+    c->zero(Sb, s.blk());
+    BackSet b;
+    b.cL = -1.0; b.GL = c->Go;
+    b.cD = 1.0; b.GD = c->Gv;
+    back_contract(c, L3t, os, okey, b, nullptr, Sb);
+    finalize(c, Sb, sig2, 1);
+    // singles intermediates
+    for (double *p : {Y1, P2}) c->zero(p, s.gvsz());
+    for (double *p : {Y2, P1}) c->zero(p, s.gosz());
+    c->zero(Y3, s.no * s.nv);
+    int n = 0;
+    const BstcItem *it;
+    Shape sh;
+    // Y1[r][b][c][D] += sum_a Lt3_{pqr}[a][b][c] t2c[p][a][q][D]  (and P2 with taut, Lc)
+    it = c->dev_items(okey + ":y1", [&] {
+      std::vector<BstcItem> vv;
+      for (auto &o : os)
+        vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.gk,
+                             {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {s.ba, 0, 0, 1, 0}, {s.gb, s.gc, 1, 0}));
+      return vv;
+    }, &n);
+    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NV;
+    c->bstc(L3t, c->t2c, Y1, sh, 1.0, it, n, true);
+    c->bstc(taut, Lc, P2, sh, 1.0, it, n, true);
+    // Y2[q][r][c][L] += sum_{ab} Lt3_{pqr}[a][b][c] Tl[p][a][b][L]  (and P1 with taut, LcT)
+    it = c->dev_items(okey + ":y2", [&] {
+      std::vector<BstcItem> vv;
+      for (auto &o : os)
+        vv.push_back(mk_item(o.off, o.p * s.ti, o.q * s.oj + o.r * s.ok,
+                             {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
+      return vv;
+    }, &n);
+    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
+    c->bstc(L3t, c->Tl, Y2, sh, 1.0, it, n, true);
+    c->bstc(taut, LcT, P1, sh, 1.0, it, n, true);
+    // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
+    it = c->dev_items(okey + ":y3", [&] {
+      std::vector<BstcItem> vv;
+      for (auto &o : os)
+        vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
+                             {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
+      return vv;
+    }, &n);
+    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+    c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true);
+    // --- singles through the Cholesky factors ---
+    c->zero(sig1, s.NV * NO);
+    for (double *p : {W, Z2, Z4, yv, Q, Q2}) (void)p;
+    c->zero(W, s.NJ * s.no * s.nv);
+    c->zero(Z2, s.NJ * s.nv * s.NV);
+    c->zero(Z4, s.NJ * s.no * NO);
+    c->zero(yv, s.NJ);
+    // W[J][k][c] = sum_{b,D} Y1[k][b][c][D] Lt[J][NO+b][NO+D] - sum_{L,j} Y2[j][k][c][L] Lt[J][L][j]
+    sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.NV;
+    c->bstc1(Y1, Lt + NO * nmo + NO, W, sh, 1.0, mk_item(0, 0, 0, {s.gk, s.gc, s.gb, 1, 0}, {nmo, 1, 0, s.lJ, 0}, {s.nv, 1, s.no * s.nv, 0}), "sg1");
+    sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.NJ; sh.K1 = NO; sh.K2 = s.no;
+    c->bstc1(Y2, Lt, W, sh, -1.0, mk_item(0, 0, 0, {s.ok, s.oc, 1, s.oj, 0}, {nmo, 1, 0, s.lJ, 0}, {s.nv, 1, s.no * s.nv, 0}), "sg2");
+    // sigma[E][k] += sum_{J,c} W[J][k][c] Lt[J][NO+c][NO+E]
+    sh = Shape{}; sh.M1 = s.NV; sh.N1 = s.no; sh.K1 = s.NJ; sh.K2 = s.nv;
+    c->bstc1(Lt + NO * nmo + NO, W, sig1, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.lJ, nmo, 0}, {s.no * s.nv, 1, 0, s.nv, 0}, {NO, 0, 1, 0}), "sg3");
+    // sigma[c][M] -= sum_{J,k} W[J][k][c] Lt[J][M][k]
+    sh = Shape{}; sh.M1 = s.nv; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.no;
+    c->bstc1(W, Lt, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv, s.nv, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg4");
+    // Z2[J][b][D] = sum_{c,k} Y1[k][b][c][D] Lt[J][NO+c][k];  sigma[b][M] -= sum_{J,D} Z2 Lt[J][M][NO+D]
+    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
+    c->bstc1(Y1, Lt + NO * nmo, Z2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {nmo, 1, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg5");
+    sh = Shape{}; sh.M1 = s.nv; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.NV;
+    c->bstc1(Z2, Lt + NO, sig1, sh, -1.0, mk_item(0, 0, 0, {s.NV, 0, s.nv * s.NV, 1, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg6");
+    // Z4[J][j][L] = sum_{c,k} Y2[j][k][c][L] Lt[J][NO+c][k];  sigma[E][j] -= sum_{J,L} Lt[J][L][NO+E] Z4
+    sh = Shape{}; sh.M1 = s.no; sh.M2 = NO; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
+    c->bstc1(Y2, Lt + NO * nmo, Z4, sh, 1.0, mk_item(0, 0, 0, {s.oj, 1, s.oc, s.ok, 0}, {nmo, 1, 0, s.lJ, 0}, {NO, 1, s.no * NO, 0}), "sg7");
+    sh = Shape{}; sh.M1 = s.NV; sh.N1 = s.no; sh.K1 = s.NJ; sh.K2 = NO;
+    c->bstc1(Lt + NO, Z4, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.lJ, nmo, 0}, {s.no * NO, 1, 0, NO, 0}, {NO, 0, 1, 0}), "sg8");
+    // Y3 terms: sigma[D][L] += sum_{kc} Y3[k][c] (2 g_kcLD - g_kDLc)
+    sh = Shape{}; sh.M1 = s.NJ; sh.K1 = s.no; sh.K2 = s.nv;
+    c->bstc1(Lt + NO, Y3, yv, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 0, nmo, 1, 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}), "sg9");
+    sh = Shape{}; sh.M1 = s.NV; sh.M2 = NO; sh.K1 = s.NJ;
+    c->bstc1(Lt + NO, yv, sig1, sh, 2.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {1, 0, 0, 0, 0}, {NO, 1, 0, 0}), "sg10");
+    // Q[J][k][L] = sum_c Y3[k][c] Lt[J][L][NO+c]; sigma[D][L] -= sum_{J,k} Lt[J][k][NO+D] Q[J][k][L]
+    c->zero(Q, s.NJ * s.no * NO);
+    sh = Shape{}; sh.M1 = s.no; sh.N1 = s.NJ; sh.N2 = NO; sh.K1 = s.nv;
+    c->bstc1(Y3, Lt + NO, Q, sh, 1.0, mk_item(0, 0, 0, {s.nv, 0, 1, 0, 0}, {1, 0, 0, s.lJ, nmo}, {NO, 0, s.no * NO, 1}), "sg11");
+    sh = Shape{}; sh.M1 = s.NV; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.no;
+    c->bstc1(Lt + NO, Q, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.lJ, nmo, 0}, {s.no * NO, NO, 0, 1, 0}, {NO, 0, 1, 0}), "sg12");
+    // P1 term: Q[J][j][L] = sum_{k,c} Lt[J][k][NO+c] P1[j][k][c][L]; sigma[D][L] -= sum_{J,j} Lt[J][j][NO+D] Q
+    c->zero(Q, s.NJ * s.no * NO);
+    sh = Shape{}; sh.M1 = s.no; sh.M2 = NO; sh.N1 = s.NJ; sh.K1 = s.no; sh.K2 = s.nv;
+    c->bstc1(P1, Lt + NO, Q, sh, 1.0, mk_item(0, 0, 0, {s.oj, 1, s.ok, s.oc, 0}, {nmo, 1, 0, s.lJ, 0}, {NO, 1, s.no * NO, 0}), "sg13");
+    sh = Shape{}; sh.M1 = s.NV; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.no;
+    c->bstc1(Lt + NO, Q, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.lJ, nmo, 0}, {s.no * NO, NO, 0, 1, 0}, {NO, 0, 1, 0}), "sg14");
+    // P2 term: Q2[J][b][D] = sum_{c,k} P2[k][b][c][D] Lt[J][k][NO+c]; sigma[D][L] -= sum_{J,b} Q2 Lt[J][L][NO+b]
+    c->zero(Q2, s.NJ * s.nv * s.NV);
+    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
+    c->bstc1(P2, Lt + NO, Q2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {1, nmo, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg15");
+    sh = Shape{}; sh.M1 = s.NV; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.nv;
+    c->bstc1(Q2, Lt + NO, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.nv * s.NV, s.NV, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg16");
+  }
+}
+
+static void do_oscillator(mlcc3_ctx *c, double omega, const double *D0m_in, const double *Dm0_in,
+                          const double *mu_in, double *f) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const double *D0m = c->in(D0m_in, nmo * nmo, "D0m");
+  const double *Dm0 = c->in(Dm0_in, nmo * nmo, "Dm0");
+  const double *mu = c->in(mu_in, 3 * nmo * nmo, "mu");
+  // mu~ = (1 - t1) mu (1 + t1), as for the Cholesky vectors.
+  double *mut = c->buf("mut", 3 * nmo * nmo);
+  check_cuda(cudaMemcpyAsync(mut, mu, 3 * nmo * nmo * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream), "mu copy");
+  Shape sh;
+  sh.M1 = 3; sh.M2 = nmo; sh.N1 = NO; sh.K1 = s.NV;
+  c->bstc1(mu + NO, c->t1, mut, sh, 1.0, mk_item(0, 0, 0, {nmo * nmo, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {nmo * nmo, nmo, 1, 0}), "mu1");
+  sh = Shape{};
+  sh.M1 = s.NV; sh.N1 = 3; sh.N2 = nmo; sh.K1 = NO;
+  c->bstc1(c->t1, mut, mut + NO * nmo, sh, -1.0, mk_item(0, 0, 0, {NO, 0, 1, 0, 0}, {nmo, 0, 0, nmo * nmo, 1}, {nmo, 0, nmo * nmo, 1}), "mu2");
+  double *T = c->buf("Tmom", 6);
+  c->zero(T, 6);
+  int n = 0;
+  const BstcItem *it = c->dev_items("fdot", [&] {
+    std::vector<BstcItem> v;
+    for (int x = 0; x < 3; ++x) {
+      v.push_back(mk_item(0, x * nmo * nmo, x, {0, 0, nmo, 1, 0}, {nmo, 1, 0, 0, 0}, {0, 0, 0, 0}));
+    }
+    return v;
+  }, &n);
+  Shape dsh;
+  dsh.K1 = nmo; dsh.K2 = nmo;
+  c->dot(D0m, mut, T, dsh, 1.0, it, n);
+  c->dot(Dm0, mut, T + 3, dsh, 1.0, it, n);
+  double h[6];
+  check_cuda(cudaMemcpyAsync(h, T, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "T");
+  c->finish();
+  *f = 2.0 / 3.0 * omega * (h[0] * h[3] + h[1] * h[4] + h[2] * h[5]);
+}
+
+// ---------------------------------------------------------------------------
+// Transition densities (SI, D^{m-0}, D^{0-0}, D^{0-m}; Eq. DL_oo)
+// ---------------------------------------------------------------------------
+namespace {
+
+// View of the block of an ordered triple (p,q,r) (not all equal).
+struct ViewMap {
+  long long n;
+  std::vector<long long> off, s0, s1, s2;
+  std::vector<char> have;
+  explicit ViewMap(const std::vector<Ord> &os, long long no) : n(no) {
+    off.assign(no * no * no, 0);
+    s0 = s1 = s2 = off;
+    have.assign(no * no * no, 0);
+    for (auto &o : os) {
+      long long x = (o.p * no + o.q) * no + o.r;
+      off[x] = o.off;
+      s0[x] = o.vs[0];
+      s1[x] = o.vs[1];
+      s2[x] = o.vs[2];
+      have[x] = 1;
+    }
+  }
+  long long idx(long long p, long long q, long long r) const { return (p * n + q) * n + r; }
+};
+
+// out[k][l] (or [l][k]) += alpha sum_{ij} sum_{abc} X_{ijl}[abc] Y_{ijk}[abc]
+// over all ordered (i,j,k), (i,j,l) with stored blocks.
+void pair_dots(mlcc3_ctx *c, const ViewMap &vm, const double *X, const double *Y, double *out,
+               long long ldo, bool kl, double alpha, const std::string &key) {
+  S s(c);
+  int n = 0;
+  const BstcItem *it = c->dev_items(key, [&] {
+    std::vector<BstcItem> v;
+    for (long long i = 0; i < s.no; ++i)
+      for (long long j = 0; j < s.no; ++j)
+        for (long long k = 0; k < s.no; ++k) {
+          long long y = vm.idx(i, j, k);
+          if (!vm.have[y]) continue;
+          for (long long l = 0; l < s.no; ++l) {
+            long long x = vm.idx(i, j, l);
+            if (!vm.have[x]) continue;
+            long long o = kl ? k * ldo + l : l * ldo + k;
+            v.push_back(mk_item(vm.off[x], vm.off[y], o, {0, 0, vm.s0[x], vm.s1[x], vm.s2[x]},
+                                {vm.s0[y], vm.s1[y], vm.s2[y], 0, 0}, {0, 0, 0, 0}));
+          }
+        }
+    return v;
+  }, &n);
+  Shape sh;
+  sh.K1 = s.nv; sh.K2 = s.nv; sh.K3 = s.nv;
+  c->dot(X, Y, out, sh, alpha, it, n);
+}
+
+// out[c][d] += alpha sum_{pqr} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
+void vv_block(mlcc3_ctx *c, const double *X, const double *Y, double *out, long long ldo,
+              double alpha) {
+  S s(c);
+  int n = 0;
+  const BstcItem *it = c->dev_items("ords:vv:" + std::to_string(ldo), [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.off, 0, {o.vs[2], 0, o.vs[0], o.vs[1], 0},
+                          {o.vs[0], o.vs[1], 0, o.vs[2], 0}, {ldo, 0, 1, 0}));
+    return v;
+  }, &n);
+  Shape sh;
+  sh.M1 = s.nv; sh.N1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+  c->bstc(X, Y, out, sh, alpha, it, n, true);
+}
+
+// out[r][c] (row stride ldo, col stride 1) += alpha sum_{ab} X_{pqr}[a][b][c] B[p][a][q][b]
+// with B in the active-pair block layout.
+void y3_like(mlcc3_ctx *c, const double *X, const double *B, double *out, long long ldo,
+             double alpha, const std::string &key) {
+  S s(c);
+  int n = 0;
+  const BstcItem *it = c->dev_items(key, [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * ldo,
+                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
+    return v;
+  }, &n);
+  Shape sh;
+  sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+  c->bstc(X, B, out, sh, alpha, it, n, true);
+}
+
+// V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
+void v_like(mlcc3_ctx *c, const double *X, const double *T, double *V) {
+  S s(c);
+  int n = 0;
+  const BstcItem *it = c->dev_items("ords:vlike", [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.p * s.ti, o.q * s.oj + o.r * s.ok,
+                          {o.vs[1], 0, o.vs[0], o.vs[2], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
+    return v;
+  }, &n);
+  Shape sh;
+  sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
+  c->bstc(X, T, V, sh, 1.0, it, n, true);
+}
+
+// D[L][NO+D] += alpha sum_{q,r,b} V[q][r][b][L] X[q][b][r][D]   (X in block layout)
+void d_LD_from_v(mlcc3_ctx *c, const double *V, const double *X, double *D, double alpha,
+                 const std::string &key) {
+  S s(c);
+  Shape sh;
+  sh.M1 = s.NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
+  c->bstc1(V, X, D + s.NO, sh, alpha,
+           mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {s.nmo, 0, 1, 0}),
+           key);
+}
+
+// Triples part of the left density from (contravariant left triples Xt3,
+// covariant-combined doubles Lc, tau, contravariant tau).
+void density_left_gpu(mlcc3_ctx *c, const ViewMap &vm, const double *Xt3, const double *Lc,
+                      const double *tau, const double *taut, double *D, const std::string &tag) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  // D_kl -= 1/2 sum Xt_{ijl} tau_{ijk}
+  pair_dots(c, vm, Xt3, tau, D, nmo, true, -0.5, "pd:kl");
+  // D_ld += 1/2 sum Lc^{ab}_{ij} taut^{abd}_{ijl}
+  y3_like(c, taut, Lc, D + NO, nmo, 0.5, "ords:y3d");
+  // D_LD -= sum Xt^{abc}_{ijk} t^{ac}_{iL} t^{bD}_{jk}
+  double *V = c->buf("dV", s.gosz());
+  c->zero(V, s.gosz());
+  v_like(c, Xt3, c->Tl, V);
+  d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
+  // D_cd += 1/2 sum Xt^{abc}_{ijk} tau^{abd}_{ijk}
+  vv_block(c, Xt3, tau, D + NO * nmo + NO, nmo, 0.5);
+  (void)tag;
+}
+
+}  // namespace
+
+static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1_in,
+                                  const double *lam2_in, const double *R1_in, const double *R2_in,
+                                  const double *L1_in, const double *L2_in,
+                                  const double *D00_in_in, double *D00_out, double *Dm0_out,
+                                  double *D0m_out) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const bool cvs = !c->core.empty();
+  const double *lam1 = c->in(lam1_in, s.NV * NO, "lam1");
+  const double *lam2 = c->in(lam2_in, s.blk(), "lam2");
+  const double *R1 = c->in(R1_in, s.NV * NO, "R1");
+  const double *R2 = c->in(R2_in, s.blk(), "R2");
+  const double *L1 = c->in(L1_in, s.NV * NO, "L1");
+  const double *L2 = c->in(L2_in, s.blk(), "L2");
+  const double *D00_in = c->in(D00_in_in, nmo * nmo, "D00_in");
+  double *D00 = c->out(D00_out, nmo * nmo, "D00");
+  double *Dm0 = c->out(Dm0_out, nmo * nmo, "Dm0");
+  double *D0m = c->out(D0m_out, nmo * nmo, "D0m");
+  for (double *p : {D00, Dm0, D0m}) c->zero(p, nmo * nmo);
+  const size_t nb = c->batches.size();
+  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
+  const std::string bkey = cvs ? "batches_cvs" : "batches";
+  ViewMap vm(c->ords, s.no);
+
+  double *tau, *taut;
+  build_tau(c, &tau, &taut);
+  // lambda3 (omega = 0) and its contravariant form
+  double *lc = c->buf("lamc", s.blk());
+  double *lcT = c->buf("lamcT", s.no * s.nv * s.nv * NO);
+  launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
+    c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+  });
+  transpose_tl(c, lc, lcT);
+  double *lam3 = c->buf("lam3", nb * s.nv3);
+  double *lt3 = c->buf("lam3t", nb * s.nv3);
+  {
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, lcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
+        term(2, 0, 0.5, lam1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
+        term(3, 0, 0.5, lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
+    triples(c, terms, "batches", c->batches, 0.0, lam3);
+    contra3(c, lam3, lt3, (long long)nb);
+  }
+  // L3 (omega) and its contravariant form
+  double *Lc = c->buf("Lc", s.blk());
+  double *LcT = c->buf("LcT", s.no * s.nv * s.nv * NO);
+  launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
+    c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+  });
+  transpose_tl(c, Lc, LcT);
+  double *L3 = c->buf("L3", nb * s.nv3);
+  double *L3t = c->buf("L3t", nb * s.nv3);
+  if (cvs) c->zero(L3, nb * s.nv3);
+  {
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, LcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
+        term(2, 0, 0.5, L1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
+        term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
+    triples(c, terms, bkey, bs, omega, L3);
+    contra3(c, L3, L3t, (long long)nb);
+  }
+  // R3 (omega) and its contravariant form
+  double *Rbar = c->buf("Rbar", s.blk());
+  double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * NO);
+  launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
+    delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+  });
+  transpose_tl(c, Rbar, Rbl);
+  double *R3 = c->buf("R3", nb * s.nv3);
+  double *R3t = c->buf("R3t", nb * s.nv3);
+  if (cvs) c->zero(R3, nb * s.nv3);
+  {
+    Ups u = build_upsilon(c, R1);
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, Rbar, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, Rbl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1}),
+        term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
+    triples(c, terms, bkey, bs, omega, R3);
+    contra3(c, R3, R3t, (long long)nb);
+  }
+  // D^{0-0} and D^{m-0}
+  density_left_gpu(c, vm, lt3, lc, tau, taut, D00, "00");
+  density_left_gpu(c, vm, L3t, Lc, tau, taut, Dm0, "m0");
+
+  // D^{0-m}
+  double *D = D0m;
+  int n = 0;
+  const BstcItem *it;
+  Shape sh;
+  // U[q][r][b][c] = sum_{p,a} lt_{pqr}[a][b][c] R^a_p
+  double *U = c->buf("dU", s.no * s.no * s.nv * s.nv);
+  c->zero(U, s.no * s.no * s.nv * s.nv);
+  it = c->dev_items("ords:U", [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.p, (o.q * s.no + o.r) * s.nv * s.nv,
+                          {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {NO, 0, 0, 0, 0}, {s.nv, 1, 0, 0}));
+    return v;
+  }, &n);
+  sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
+  c->bstc(lt3, R1, U, sh, 1.0, it, n, true);
+  // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
+  sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
+  c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
+  // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
+  pair_dots(c, vm, lt3, R3, D, nmo, true, -0.5, "pd:kl");
+  // D_ld += sum U[j][k][b][c] (tau^{bcd}_{jkl} - tau^{bcd}_{jlk})
+  it = c->dev_items("ords:ld1", [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
+                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
+    return v;
+  }, &n);
+  sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+  c->bstc(tau, U, D + NO, sh, 1.0, it, n, true);
+  it = c->dev_items("ords:ld2", [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, (o.p * s.no + o.r) * s.nv * s.nv, o.q * nmo,
+                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
+    return v;
+  }, &n);
+  c->bstc(tau, U, D + NO, sh, -1.0, it, n, true);
+  //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
+  y3_like(c, R3t, lc, D + NO, nmo, 0.5, "ords:y3d");
+  // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}
+  double *W3 = c->buf("dW3", s.no * s.nv);
+  c->zero(W3, s.no * s.nv);
+  y3_like(c, lt3, Rbar, W3, s.nv, 0.5, "ords:y3w");
+  //   D_LD += sum_{kc} W3[k][c] (2 t^{cD}_{kL} - t^{cD}_{Lk})
+  sh = Shape{}; sh.M1 = NO; sh.M2 = s.NV; sh.K1 = s.no; sh.K2 = s.nv;
+  c->bstc1(c->t2c, W3, D + NO, sh, 2.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
+  c->bstc1(c->t2x, W3, D + NO, sh, -1.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
+  //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}
+  double *V = c->buf("dV", s.gosz());
+  c->zero(V, s.gosz());
+  v_like(c, lt3, Rbl, V);
+  d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
+  //   D_LD -= sum lt^{abc}_{ijk} Rbar^{aD}_{ik} t^{bc}_{jL}
+  double *V3 = c->buf("dV3", s.gosz());
+  c->zero(V3, s.gosz());
+  it = c->dev_items("ords:v3", [&] {
+    std::vector<BstcItem> v;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.q * s.ti, o.p * s.oj + o.r * s.ok,
+                          {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
+    return v;
+  }, &n);
+  sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = NO;
+  c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true);
+  sh = Shape{}; sh.M1 = NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
+  c->bstc1(V3, Rbar, D + NO, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dLD3");
+  // D_lD -= 1/2 sum_k E[l][k] R^D_k,  E[l][k] = sum lt_{ijk} tau_{ijl}
+  double *E = c->buf("dE", s.no * s.no + s.nv * s.nv);
+  c->zero(E, s.no * s.no + s.nv * s.nv);
+  pair_dots(c, vm, tau, lt3, E, s.no, false, 1.0, "pd:E");
+  sh = Shape{}; sh.M1 = s.no; sh.N1 = s.NV; sh.K1 = s.no;
+  c->bstc1(E, R1, D + NO, sh, -0.5, mk_item(0, 0, 0, {s.no, 0, 1, 0, 0}, {1, 0, 0, NO, 0}, {nmo, 0, 1, 0}), "dlD");
+  // D_Ld -= 1/2 sum_c E2[c][d] R^c_L,  E2[c][d] = sum lt^{abc}_{ijk} tau^{abd}_{ijk}
+  double *E2 = E + s.no * s.no;
+  vv_block(c, lt3, tau, E2, s.nv, 1.0);
+  sh = Shape{}; sh.M1 = NO; sh.N1 = s.nv; sh.K1 = s.nv;
+  c->bstc1(R1, E2, D + NO, sh, -0.5, mk_item(0, 0, 0, {1, 0, NO, 0, 0}, {s.nv, 0, 0, 1, 0}, {nmo, 0, 1, 0}), "dLd");
+  // D_ck += W3[k][c]
+  double *one = c->dscal;
+  {
+    double h1 = 1.0;
+    check_cuda(cudaMemcpyAsync(one, &h1, sizeof(double), cudaMemcpyHostToDevice, c->stream), "one");
+    check_cuda(cudaStreamSynchronize(c->stream), "one sync");
+  }
+  sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.no;
+  c->bstc1(W3, one, D + NO * nmo, sh, 1.0, mk_item(0, 0, 0, {1, s.nv, 0, 0, 0}, {0, 0, 0, 0, 0}, {nmo, 1, 0, 0}), "dck");
+  // D_cD += sum_{j,k,b} U[j][k][b][c] t^{bD}_{jk}
+  sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
+  c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dcD");
+  // D_cd += 1/2 sum lt^{abc}_{ijk} R^{abd}_{ijk}
+  vv_block(c, lt3, R3, D + NO * nmo + NO, nmo, 0.5);
+  // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings), lambda_SD.R_SD
+  double *sc = c->dscal + 1;
+  c->zero(sc, 2);
+  it = c->dev_items("bdots", [&] {
+    std::vector<BstcItem> v;
+    std::map<int, int> mult;
+    for (auto &o : c->ords) mult[o.u]++;
+    (void)mult;
+    for (auto &o : c->ords)
+      v.push_back(mk_item(o.off, o.off, 0, {0, 0, 0, 0, 1}, {0, 0, 1, 0, 0}, {0, 0, 0, 0}));
+    return v;
+  }, &n);
+  sh = Shape{}; sh.K3 = s.nv3;
+  c->dot(lt3, R3, sc, sh, 1.0 / 6.0, it, n);
+  launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
+    sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, R1, R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1);
+  });
+  launch_1d(c, nmo * nmo, "density_norm", [&](int g) {
+    density_norm_kernel<<<g, 256, 0, c->stream>>>(D, D00_in, D00, sc, (int)nmo, (int)NO);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+template <class F>
+static int guarded(F &&f) {
+  try {
+    f();
+    return MLCC3_OK;
+  } catch (const Error &e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return MLCC3_ERR_CUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return MLCC3_ERR_CUDA;
+  }
+}
+
+extern "C" const char *mlcc3_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *d, int precision,
+                            void *cuda_stream) {
+  return guarded([&] {
+    if (!out || !d) throw Error{MLCC3_ERR_ARG, "null argument"};
+    *out = nullptr;
+    if (d->n_occ < 1 || d->n_vir < 1 || d->n_act_occ < 0 || d->n_act_vir < 0 ||
+        d->n_act_occ > d->n_occ || d->n_act_vir > d->n_vir || d->n_chol < 1)
+      throw Error{MLCC3_ERR_ARG, "invalid dimensions"};
+    if (d->n_occ + d->n_vir > 46340) throw Error{MLCC3_ERR_ARG, "n_mo too large"};
+    if (precision != MLCC3_FP64 && precision != MLCC3_SPLIT_BF16X3)
+      throw Error{MLCC3_ERR_ARG, "unknown precision mode"};
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    auto *c = new mlcc3_ctx();
+    c->NO = d->n_occ;
+    c->NV = d->n_vir;
+    c->no = d->n_act_occ;
+    c->nv = d->n_act_vir;
+    c->NJ = d->n_chol;
+    c->nmo = c->NO + c->NV;
+    c->precision = precision;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->device = dev;
+    if (d->core_mask) c->core.assign(d->core_mask, d->core_mask + d->n_occ);
+    try {
+      S s(c);
+      auto alloc = [&](double **p, size_t n) {
+        check_cuda(cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(double)), "cudaMalloc");
+      };
+      alloc(&c->eps, s.nmo);
+      alloc(&c->t1, s.NV * s.NO);
+      alloc(&c->Lt, s.NJ * s.lJ);
+      alloc(&c->t2c, s.blk());
+      alloc(&c->t2x, s.blk());
+      alloc(&c->Tl, s.no * s.nv * s.nv * s.NO);
+      alloc(&c->Gv, s.gvsz());
+      alloc(&c->Gb, s.gvsz());
+      alloc(&c->Go, s.gosz());
+      alloc(&c->Gx, s.gosz());
+      alloc(&c->Govov, s.no * s.nv * s.no * s.nv);
+      alloc(&c->F, s.no * s.nv);
+      alloc(&c->dscal, 16);
+      check_cuda(cudaMalloc(&c->status, sizeof(int)), "cudaMalloc status");
+      check_cuda(cudaMemset(c->status, 0, sizeof(int)), "memset status");
+      make_batches(c);
+    } catch (...) {
+      mlcc3_destroy(c);
+      throw;
+    }
+    *out = c;
+  });
+}
+
+extern "C" void mlcc3_destroy(mlcc3_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (double *p : {c->eps, c->t1, c->Lt, c->t2c, c->t2x, c->Tl, c->Gv, c->Gb, c->Go, c->Gx,
+                    c->Govov, c->F, c->dscal})
+    if (p) cudaFree(p);
+  if (c->status) cudaFree(c->status);
+  for (auto &kv : c->scratch) cudaFree(kv.second.first);
+  for (auto &kv : c->items) cudaFree(kv.second.first);
+  delete c;
+}
+
+static void require_built(mlcc3_ctx *c) {
+  if (!c) throw Error{MLCC3_ERR_ARG, "null context"};
+  if (!c->built) throw Error{MLCC3_ERR_STATE, "mlcc3_build_integrals has not been called"};
+}
+
+extern "C" int mlcc3_build_integrals(mlcc3_ctx *c, const double *chol, const double *t1,
+                                     const double *eps, const double *t2c, const double *t2x) {
+  return guarded([&] {
+    if (!c) throw Error{MLCC3_ERR_ARG, "null context"};
+    do_build_integrals(c, chol, t1, eps, t2c, t2x);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_triples_omega(mlcc3_ctx *c, double *omega1, double *omega2) {
+  return guarded([&] {
+    require_built(c);
+    do_triples_omega(c, omega1, omega2);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega,
+                                    const double *R1, const double *R2, double *rho1,
+                                    double *rho2) {
+  return guarded([&] {
+    require_built(c);
+    if (n_vec < 0 || (n_vec > 0 && !omega)) throw Error{MLCC3_ERR_ARG, "bad n_vec/omega"};
+    if (n_vec == 0) return;
+    do_jacobian_right(c, n_vec, omega, R1, R2, rho1, rho2);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega,
+                                   const double *L1, const double *L2, double *sigma1,
+                                   double *sigma2) {
+  return guarded([&] {
+    require_built(c);
+    if (n_vec < 0 || (n_vec > 0 && !omega)) throw Error{MLCC3_ERR_ARG, "bad n_vec/omega"};
+    if (n_vec == 0) return;
+    do_jacobian_left(c, n_vec, omega, L1, L2, sigma1, sigma2);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_transition_density(mlcc3_ctx *c, double omega, const double *lam1,
+                                        const double *lam2, const double *R1, const double *R2,
+                                        const double *L1, const double *L2, const double *D00_in,
+                                        double *D00_T, double *Dm0_T, double *D0m_T) {
+  return guarded([&] {
+    require_built(c);
+    do_transition_density(c, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_oscillator_strength(mlcc3_ctx *c, double omega, const double *D0m,
+                                         const double *Dm0, const double *mu, double *f) {
+  return guarded([&] {
+    require_built(c);
+    if (!f) throw Error{MLCC3_ERR_ARG, "null f"};
+    do_oscillator(c, omega, D0m, Dm0, mu, f);
+  });
+}
+
+extern "C" int mlcc3_debug_fetch(mlcc3_ctx *c, const char *name, double *host, size_t n) {
+  return guarded([&] {
+    if (!c || !name || !host) throw Error{MLCC3_ERR_ARG, "null argument"};
+    S s(c);
+    const double *src = nullptr;
+    size_t have = 0;
+    std::string nm(name);
+    if (nm == "Lt") { src = c->Lt; have = s.NJ * s.lJ; }
+    else if (nm == "Gv") { src = c->Gv; have = s.gvsz(); }
+    else if (nm == "Gb") { src = c->Gb; have = s.gvsz(); }
+    else if (nm == "Go") { src = c->Go; have = s.gosz(); }
+    else if (nm == "Gx") { src = c->Gx; have = s.gosz(); }
+    else if (nm == "Govov") { src = c->Govov; have = s.no * s.nv * s.no * s.nv; }
+    else if (nm == "F") { src = c->F; have = s.no * s.nv; }
+    else {
+      auto it = c->scratch.find(nm);
+      if (it == c->scratch.end()) throw Error{MLCC3_ERR_ARG, "unknown buffer " + nm};
+      src = static_cast<const double *>(it->second.first);
+      have = it->second.second / sizeof(double);
+    }
+    if (n > have) throw Error{MLCC3_ERR_ARG, "fetch larger than buffer"};
+    check_cuda(cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "fetch");
+    check_cuda(cudaStreamSynchronize(c->stream), "fetch sync");
+  });
+}
+
+extern "C" long long mlcc3_debug_nbatches(mlcc3_ctx *c) {
+  return c ? (long long)c->batches.size() : -1;
+}
