@@ -1,0 +1,330 @@
+"""Benchmark of the MLCC3 triples hot path (one JSON line on rank 0).
+
+A step is one pass of the whole path on one synthetic system: integral
+build, triples residual, right and transpose Jacobian transformations of the
+state vectors, the three transition densities and the oscillator strength.
+The metric is the algorithmic throughput of the step (the paper's leading
+flop counts, Sec. 3: Omega 4, rho 8, sigma 8, D^{0-0} 10, D^{m-0} 10,
+D^{0-m} 16, in units of N_V n_v^3 n_o^3) divided by the measured step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "triples sweep TFLOP/s & s/Davidson-iter vs FP64 GPU path at 1e-6 error in f"
+WORKLOADS = {
+    # name: (N_O, N_V, n_o, n_v, N_J, states)
+    "guanine_like_small": (20, 200, 12, 60, 600, 1),
+    "tiny": (6, 24, 4, 8, 72, 1),
+}
+UNITS_PER_STEP = 4 + 8 + 8 + 10 + 10 + 16      # per state
+FP64_PEAK_TFLOPS = 1.25                        # nominal GB300 FP64 (ALU bound)
+
+
+def algorithmic_flops(NO, NV, no, nv, nstates):
+    return UNITS_PER_STEP * NV * nv ** 3 * no ** 3 * nstates
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace('.', '', 1).isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace('.', '', 1).isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2202_08612_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel sources changed since it was captured."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t[kernel]
+        return e["bytes_per_launch"] if e.get("source_digest") == source_digest() else None
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------------------
+def oracle_sample(workload, seed):
+    """The oracle on a bounded sample of the workload: the same system with the
+    active occupied space cut to n_o = 4 (every stage of the step)."""
+    import oracle as O
+    from paper_2202_08612_gb300 import synth
+    NO, NV, no, nv, NJ, ns = WORKLOADS[workload]
+    no_s = min(no, 4)
+    s = synth.make_system(NO, NV, no_s, nv, NJ, seed=seed)
+    st = synth.make_states(s, 1, seed=seed + 1)
+    lam1, lam2 = synth.make_multipliers(s, seed=seed + 2)
+    mu = synth.make_dipole(s, seed=seed + 3)
+    D00_in = synth.reference_density(s)
+    t = time.perf_counter()
+    oc = O.make_ctx(s)
+    O.triples_omega(oc)
+    w = float(st.omega[0])
+    O.jacobian_right(oc, w, st.R1[0], O.to_full(oc, st.R2[0]))
+    O.jacobian_left(oc, w, st.L1[0], O.to_full(oc, st.L2[0]))
+    d00, dm0, d0m = O.transition_densities(oc, w, lam1, O.to_full(oc, lam2), st.R1[0],
+                                           O.to_full(oc, st.R2[0]), st.L1[0],
+                                           O.to_full(oc, st.L2[0]), D00_in)
+    O.oscillator_strength(oc, w, d0m, dm0, mu)
+    dt = time.perf_counter() - t
+    fl = algorithmic_flops(NO, NV, no_s, nv, 1)
+    return fl / dt / 1e12, dt, f"same system with n_o cut to {no_s} (all stages of one step)"
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, sample = oracle_sample(args.workload, 1000 + i)
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = statistics.mean(dt for _, dt in vals) * 1e3
+    NO, NV, no, nv, NJ, ns = WORKLOADS[args.workload]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.workload)},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(w):
+    NO, NV, no, nv, NJ, ns = WORKLOADS[w]
+    return f"{w}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}, {ns} state(s)"
+
+
+# --------------------------------------------------------------------------------------
+class Problem:
+    def __init__(self, workload, seed, device):
+        import torch
+        from paper_2202_08612_gb300 import synth
+        NO, NV, no, nv, NJ, ns = WORKLOADS[workload]
+        self.dims = (NO, NV, no, nv, NJ)
+        self.ns = ns
+        s = synth.make_system(NO, NV, no, nv, NJ, seed=seed)
+        st = synth.make_states(s, ns, seed=seed + 1)
+        lam1, lam2 = synth.make_multipliers(s, seed=seed + 2)
+        self.host = dict(chol=s.chol, t1=s.t1, eps=s.eps, t2c=s.t2c, t2x=s.t2x, R1=st.R1, R2=st.R2,
+                         L1=st.L1, L2=st.L2, lam1=lam1, lam2=lam2, mu=synth.make_dipole(s, seed=seed + 3),
+                         D00_in=synth.reference_density(s))
+        self.host = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in self.host.items()}
+        self.omega = st.omega
+        self.dev = {k: torch.from_numpy(v).to(device) for k, v in self.host.items()}
+        nmo = NO + NV
+        z = lambda shape: torch.zeros(shape, dtype=torch.float64, device=device)
+        self.out_dev = dict(o1=z((NV, NO)), o2=z(s.t2c.shape), rho1=z(st.R1.shape), rho2=z(st.R2.shape),
+                            sig1=z(st.R1.shape), sig2=z(st.R2.shape), D00=z((nmo, nmo)),
+                            Dm0=z((nmo, nmo)), D0m=z((nmo, nmo)))
+        self.out_host = {k: np.zeros(tuple(v.shape)) for k, v in self.out_dev.items()}
+
+    def step(self, ctx, x, o):
+        """One pass of the whole path; x/o are device tensors or host arrays."""
+        ctx.build_integrals(x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"])
+        ctx.triples_omega(o["o1"], o["o2"])
+        ctx.jacobian_right(self.omega, x["R1"], x["R2"], o["rho1"], o["rho2"])
+        ctx.jacobian_left(self.omega, x["L1"], x["L2"], o["sig1"], o["sig2"])
+        fs = []
+        for n in range(self.ns):
+            w = float(self.omega[n])
+            ctx.transition_density(w, x["lam1"], x["lam2"], x["R1"][n], x["R2"][n], x["L1"][n],
+                                   x["L2"][n], x["D00_in"], o["D00"], o["Dm0"], o["D0m"])
+            fs.append(ctx.oscillator_strength(w, o["D0m"], o["Dm0"], x["mu"]))
+        return fs
+
+    def bytes_io(self):
+        i = sum(v.nbytes for v in self.host.values()) + 8 * self.ns
+        o = sum(v.nbytes for v in self.out_host.values()) + 8 * self.ns
+        return i, o
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2202_08612_gb300 import binding, build
+    build.build()
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    NO, NV, no, nv, NJ, ns = WORKLOADS[args.workload]
+    prob = Problem(args.workload, 2022 + 17 * rank, device)
+    stream = torch.cuda.current_stream(device)
+    ctx = binding.Context(*prob.dims, precision=binding.MLCC3_FP64, stream=stream.cuda_stream)
+    dist = world > 1
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(device)
+
+    for _ in range(args.warmup):
+        prob.step(ctx, prob.dev, prob.out_dev)
+    ctx.profile(True)
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            prob.step(ctx, prob.dev, prob.out_dev)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms_total], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    fl = algorithmic_flops(NO, NV, no, nv, ns)
+    value = fl * world / (ms * 1e-3) / 1e12
+
+    # per-stage time of the Davidson-iteration part (rho + sigma of the state vectors)
+    barrier()
+    t = time.perf_counter()
+    ctx.jacobian_right(prob.omega, prob.dev["R1"], prob.dev["R2"], prob.out_dev["rho1"], prob.out_dev["rho2"])
+    ctx.jacobian_left(prob.omega, prob.dev["L1"], prob.dev["L2"], prob.out_dev["sig1"], prob.out_dev["sig2"])
+    torch.cuda.synchronize(device)
+    s_iter = time.perf_counter() - t
+
+    # end to end through the C ABI with host buffers (staged by the library)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        prob.step(ctx, prob.host, prob.out_host)
+    torch.cuda.synchronize(device)
+    e2e_s = (time.perf_counter() - t) / args.steps
+    bi, bo = prob.bytes_io()
+    e2e = {"value": fl * world / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo}
+
+    # dominant kernel of the timed region
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    name, (launches, kms, kfl) = dom
+    achieved = kfl / (kms * 1e-3) / 1e12 if kms > 0 else None
+    roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": traffic_for(name), "launches_per_step": launches / args.steps,
+                "share_of_step": kms / ms_total,
+                "peak_note": "nominal GB300 FP64 (FP64 FMA on the SIMT pipes; no FP64 tensor path)"}
+    gpu_launches = sum(v[0] for v in stats.values())
+
+    if rank == 0:
+        cpu_v, cpu_dt, sample = oracle_sample(args.workload, 77)
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": workload_name(args.workload), "precision": "fp64",
+                           "parallelism": f"replicas x{world} (independent systems)",
+                           "l2": "inputs larger than L2 (Cholesky vectors "
+                                 f"{prob.host['chol'].nbytes / 2**20:.0f} MiB)"},
+                "s_per_davidson_iter": s_iter,
+                "roofline": roofline,
+                "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                 "kind": "oracle", "sample": sample, "seconds": cpu_dt},
+                "e2e": e2e, "clocks": clk.summary(), "gpu_launches": gpu_launches,
+                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="guanine_like_small", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -134,6 +134,18 @@ int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
 int mlcc3_debug_fetch(mlcc3_ctx *ctx, const char *name, double *host, size_t n);
 long long mlcc3_debug_nbatches(mlcc3_ctx *ctx);
 
+/* Launch accounting.  The context counts every kernel it launches, per
+ * kernel name, with the floating-point operations of the launch.
+ * mlcc3_debug_profile(ctx, 1) clears the counters and additionally brackets
+ * each launch with CUDA events on the context's stream (timings are summed
+ * when a call finishes); mlcc3_debug_profile(ctx, 0) clears and stops timing.
+ * mlcc3_debug_kernel_stats reports entry `index` (0-based, in name order):
+ * its name (NUL-terminated, truncated to name_len), launches, summed event
+ * milliseconds (0 without profiling) and flops; MLCC3_ERR_ARG past the end. */
+int mlcc3_debug_profile(mlcc3_ctx *ctx, int enable);
+int mlcc3_debug_kernel_stats(mlcc3_ctx *ctx, int index, char *name, size_t name_len,
+                             long long *launches, double *ms, double *flops);
+
 #ifdef __cplusplus
 }
 #endif

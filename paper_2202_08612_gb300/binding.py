@@ -25,7 +25,7 @@ ERRORS = {-1: "MLCC3_ERR_ARG", -2: "MLCC3_ERR_CUDA", -3: "MLCC3_ERR_OOM",
 EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_integrals",
            "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
            "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
-           "mlcc3_debug_nbatches")
+           "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats")
 
 
 class MLCC3Error(RuntimeError):
@@ -66,6 +66,10 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_debug_fetch.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t]
     lib.mlcc3_debug_nbatches.argtypes = [P]
     lib.mlcc3_debug_nbatches.restype = ctypes.c_longlong
+    lib.mlcc3_debug_profile.argtypes = [P, I]
+    lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
+                                             ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(D), ctypes.POINTER(D)]
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype
     _lib = lib
@@ -150,6 +154,21 @@ class Context:
     def debug_fetch(self, name: str, n: int) -> np.ndarray:
         out = np.empty(n, dtype=np.float64)
         self._check(self.lib.mlcc3_debug_fetch(self.h, name.encode(), out.ctypes.data, n))
+        return out
+
+    def profile(self, enable: bool):
+        """Clear the launch counters; with enable, time every launch with CUDA events."""
+        self._check(self.lib.mlcc3_debug_profile(self.h, 1 if enable else 0))
+
+    def kernel_stats(self) -> dict:
+        """{kernel name: (launches, summed ms, flops)} since the last profile() call."""
+        out, i = {}, 0
+        name = ctypes.create_string_buffer(128)
+        n, ms, fl = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        while self.lib.mlcc3_debug_kernel_stats(self.h, i, name, 128, ctypes.byref(n),
+                                                 ctypes.byref(ms), ctypes.byref(fl)) == 0:
+            out[name.value.decode()] = (n.value, ms.value, fl.value)
+            i += 1
         return out
 
     def nbatches(self) -> int:

@@ -80,6 +80,39 @@ struct mlcc3_ctx {
   // output copies back to host pointers at the end of a call
   std::vector<std::array<void *, 3>> pending_out;
 
+  // launch accounting: every kernel launch is counted; with profiling on,
+  // CUDA events bracket each launch on the context's stream.
+  struct KStat {
+    long long launches = 0;
+    double ms = 0.0;
+    double flops = 0.0;
+  };
+  struct PendingEvent {
+    std::string name;
+    cudaEvent_t start, stop;
+  };
+  bool prof = false;
+  std::map<std::string, KStat> kstats;
+  std::vector<PendingEvent> pending_ev;
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t get_event();
+  template <class F>
+  void launch(const char *name, double flops, F &&f) {
+    KStat &k = kstats[name];
+    k.launches += 1;
+    k.flops += flops;
+    if (!prof) {
+      f();
+      return;
+    }
+    PendingEvent pe{name, get_event(), get_event()};
+    cudaEventRecord(pe.start, stream);
+    f();
+    cudaEventRecord(pe.stop, stream);
+    pending_ev.push_back(pe);
+  }
+  void collect_events();
+
   double *buf(const std::string &name, size_t n);
   void *raw(const std::string &name, size_t bytes);
   const mlcc3::BstcItem *dev_items(const std::string &key,

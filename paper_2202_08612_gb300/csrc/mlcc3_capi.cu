@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <iterator>
 #include <set>
 #include <stdexcept>
 #include <string>
@@ -79,6 +80,27 @@ double *mlcc3_ctx::buf(const std::string &name, size_t n) {
   return static_cast<double *>(raw(name, n * sizeof(double)));
 }
 
+cudaEvent_t mlcc3_ctx::get_event() {
+  if (!event_pool.empty()) {
+    cudaEvent_t e = event_pool.back();
+    event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+void mlcc3_ctx::collect_events() {
+  for (auto &pe : pending_ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.start, pe.stop) == cudaSuccess) kstats[pe.name].ms += ms;
+    event_pool.push_back(pe.start);
+    event_pool.push_back(pe.stop);
+  }
+  pending_ev.clear();
+}
+
 void mlcc3_ctx::zero(double *p, size_t n) {
   check_cuda(cudaMemsetAsync(p, 0, n * sizeof(double), stream), "memset");
 }
@@ -138,6 +160,7 @@ void mlcc3_ctx::finish() {
              "read status");
   check_cuda(cudaStreamSynchronize(stream), "synchronize");
   check_cuda(cudaGetLastError(), "kernel launch");
+  collect_events();
   if (st & 1) {
     check_cuda(cudaMemsetAsync(status, 0, sizeof(int), stream), "reset status");
     throw Error{MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk} - omega| < 1e-3 in a triples block"};
@@ -169,7 +192,8 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
     p.items = it + z0;
     int nz = std::min(65535, nitems - z0);
     dim3 grid((unsigned)tiles, (unsigned)nz);
-    bstc_kernel<<<grid, 256, 0, stream>>>(p);
+    launch("bstc_kernel", 2.0 * M * N * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
+           [&] { bstc_kernel<<<grid, 256, 0, stream>>>(p); });
   }
   check_cuda(cudaGetLastError(), "bstc launch");
 }
@@ -194,7 +218,8 @@ void mlcc3_ctx::dot(const double *A, const double *B, double *C, const Shape &sh
   p.alpha = alpha;
   p.items = it;
   p.nitems = nitems;
-  bstc_dot_kernel<<<nitems, 256, 0, stream>>>(p);
+  launch("bstc_dot_kernel", 2.0 * (double)(sh.K1 * sh.K2 * sh.K3) * nitems,
+         [&] { bstc_dot_kernel<<<nitems, 256, 0, stream>>>(p); });
   check_cuda(cudaGetLastError(), "dot launch");
 }
 
@@ -332,15 +357,20 @@ void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string
   n = (int)bs.size();
   long long nt = (c->nv + 7) / 8;
   dim3 grid((unsigned)(nt * nt * nt), (unsigned)n);
-  triples_build_kernel<<<grid, 256, 0, c->stream>>>(tt, db, c->eps, (int)c->NO, (int)c->nv,
-                                                    omega, out, c->status);
+  double fl = 0.0;
+  const double nv3 = (double)(c->nv * c->nv * c->nv);
+  for (auto &t : terms) fl += 12.0 * nv3 * (t.kind <= 1 ? (double)t.R : 1.0);
+  c->launch("triples_build_kernel", fl * n, [&] {
+    triples_build_kernel<<<grid, 256, 0, c->stream>>>(tt, db, c->eps, (int)c->NO, (int)c->nv,
+                                                      omega, out, c->status);
+  });
   check_cuda(cudaGetLastError(), "triples_build launch");
 }
 
 void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
   long long n = nblocks * c->nv * c->nv * c->nv;
   launch_1d(c, n, "contra3", [&](int g) {
-    contra3_kernel<<<g, 256, 0, c->stream>>>(X, Xt, nblocks, (int)c->nv);
+    c->launch("contra3_kernel", 0.0, [&] { contra3_kernel<<<g, 256, 0, c->stream>>>(X, Xt, nblocks, (int)c->nv); });
   });
 }
 
@@ -440,15 +470,17 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
 void finalize(mlcc3_ctx *c, const double *Zb, double *out, int mode) {
   S s(c);
   launch_1d(c, (long long)s.blk(), "finalize", [&](int g) {
-    finalize_doubles_kernel<<<g, 256, 0, c->stream>>>(Zb, out, (int)s.no, (int)s.nv, (int)s.NO,
-                                                      (int)s.NV, mode);
+    c->launch("finalize_doubles_kernel", 0.0, [&] {
+      finalize_doubles_kernel<<<g, 256, 0, c->stream>>>(Zb, out, (int)s.no, (int)s.nv, (int)s.NO,
+                                                        (int)s.NV, mode);
+    });
   });
 }
 
 void transpose_tl(mlcc3_ctx *c, const double *X, double *T) {
   S s(c);
   launch_1d(c, s.no * s.nv * s.nv * s.NO, "transpose_tl", [&](int g) {
-    transpose_tl_kernel<<<g, 256, 0, c->stream>>>(X, T, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+    c->launch("transpose_tl_kernel", 0.0, [&] { transpose_tl_kernel<<<g, 256, 0, c->stream>>>(X, T, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV); });
   });
 }
 
@@ -624,7 +656,7 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     double *rho2 = rho2all + (size_t)v * s.blk();
     if (!(std::fabs(omega[v]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
     launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
-      delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+      c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV); });
     });
     transpose_tl(c, Rbar, Rbl);
     Ups u = build_upsilon(c, R1);
@@ -692,7 +724,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     double *sig1 = sig1all + (size_t)v * s.NV * s.NO;
     double *sig2 = sig2all + (size_t)v * s.blk();
     launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
-      c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV);
+      c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV); });
     });
     transpose_tl(c, Lc, LcT);
     // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
@@ -1008,7 +1040,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   double *lc = c->buf("lamc", s.blk());
   double *lcT = c->buf("lamcT", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
-    c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+    c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, lc, lcT);
   double *lam3 = c->buf("lam3", nb * s.nv3);
@@ -1026,7 +1058,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   double *Lc = c->buf("Lc", s.blk());
   double *LcT = c->buf("LcT", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
-    c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+    c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, Lc, LcT);
   double *L3 = c->buf("L3", nb * s.nv3);
@@ -1045,7 +1077,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   double *Rbar = c->buf("Rbar", s.blk());
   double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
-    delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV);
+    c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, Rbar, Rbl);
   double *R3 = c->buf("R3", nb * s.nv3);
@@ -1174,10 +1206,10 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   sh = Shape{}; sh.K3 = s.nv3;
   c->dot(lt3, R3, sc, sh, 1.0 / 6.0, it, n);
   launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
-    sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, R1, R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1);
+    c->launch("sd_dot_kernel", 0.0, [&] { sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, R1, R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1); });
   });
   launch_1d(c, nmo * nmo, "density_norm", [&](int g) {
-    density_norm_kernel<<<g, 256, 0, c->stream>>>(D, D00_in, D00, sc, (int)nmo, (int)NO);
+    c->launch("density_norm_kernel", 0.0, [&] { density_norm_kernel<<<g, 256, 0, c->stream>>>(D, D00_in, D00, sc, (int)nmo, (int)NO); });
   });
 }
 
@@ -1265,6 +1297,11 @@ extern "C" void mlcc3_destroy(mlcc3_ctx *c) {
   if (c->status) cudaFree(c->status);
   for (auto &kv : c->scratch) cudaFree(kv.second.first);
   for (auto &kv : c->items) cudaFree(kv.second.first);
+  for (auto &pe : c->pending_ev) {
+    cudaEventDestroy(pe.start);
+    cudaEventDestroy(pe.stop);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -1358,6 +1395,31 @@ extern "C" int mlcc3_debug_fetch(mlcc3_ctx *c, const char *name, double *host, s
     check_cuda(cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                "fetch");
     check_cuda(cudaStreamSynchronize(c->stream), "fetch sync");
+  });
+}
+
+extern "C" int mlcc3_debug_profile(mlcc3_ctx *c, int enable) {
+  return guarded([&] {
+    if (!c) throw Error{MLCC3_ERR_ARG, "null context"};
+    check_cuda(cudaStreamSynchronize(c->stream), "profile sync");
+    c->collect_events();
+    c->kstats.clear();
+    c->prof = enable != 0;
+  });
+}
+
+extern "C" int mlcc3_debug_kernel_stats(mlcc3_ctx *c, int index, char *name, size_t name_len,
+                                        long long *launches, double *ms, double *flops) {
+  return guarded([&] {
+    if (!c || !name || name_len == 0 || !launches || !ms || !flops)
+      throw Error{MLCC3_ERR_ARG, "null argument"};
+    if (index < 0 || index >= (int)c->kstats.size()) throw Error{MLCC3_ERR_ARG, "index out of range"};
+    auto it = c->kstats.begin();
+    std::advance(it, index);
+    std::snprintf(name, name_len, "%s", it->first.c_str());
+    *launches = it->second.launches;
+    *ms = it->second.ms;
+    *flops = it->second.flops;
   });
 }
 
