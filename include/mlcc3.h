@@ -125,6 +125,30 @@ int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
 int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
                               const double *Dm0, const double *mu, double *f);
 
+/* Triples residual without allocating (no counterpart in the paper).
+ * Some callers cannot allocate device memory at the moment they call: code
+ * that runs while a stream is being captured into a CUDA graph, or a loop
+ * whose host application owns all device memory and forbids (or cannot afford
+ * the stall of) a cudaMalloc.  This entry point returns the same omega1 and
+ * omega2 as mlcc3_triples_omega but takes all of its scratch (the unique-batch
+ * tau blocks, their contravariant copies, the doubles accumulator and the
+ * index tables) from one fixed 32 MiB device array compiled into the
+ * library, which every device that loads the library holds until exit.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ * Requirements: mlcc3_build_integrals has run on `ctx` (that call allocates,
+ * so make it during set-up); omega1/omega2 are device pointers (host arrays
+ * would need staging buffers); the current device is the context's; and
+ * 2 n_batch n_v^3 + n_o n_v N_O N_V doubles plus the index tables fit in
+ * 32 MiB (n_batch = unique i >= j >= k, i = j = k excluded) -- larger systems
+ * get MLCC3_ERR_ARG with the required size in mlcc3_last_error().
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and finds the previous call's contents in it
+ * (the accumulators are cleared on entry); calls that overlap on the GPU
+ * (other streams, other contexts on the same device) race on it and must be
+ * serialised by the caller. */
+int mlcc3_triples_omega_static(mlcc3_ctx *ctx, double *omega1, double *omega2);
+
 /* Diagnostics (used by the test-suite).  mlcc3_debug_fetch copies the first
  * n doubles of a named device buffer of the context into `host` (integral
  * blocks "Lt", "Gv", "Gb", "Go", "Gx", "Govov", "F", or a named scratch

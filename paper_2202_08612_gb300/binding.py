@@ -25,7 +25,8 @@ ERRORS = {-1: "MLCC3_ERR_ARG", -2: "MLCC3_ERR_CUDA", -3: "MLCC3_ERR_OOM",
 EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_integrals",
            "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
            "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
-           "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats")
+           "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
+           "mlcc3_triples_omega_static")
 
 
 class MLCC3Error(RuntimeError):
@@ -59,6 +60,7 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_last_error.restype = ctypes.c_char_p
     lib.mlcc3_build_integrals.argtypes = [P] * 6
     lib.mlcc3_triples_omega.argtypes = [P, P, P]
+    lib.mlcc3_triples_omega_static.argtypes = [P, P, P]
     lib.mlcc3_jacobian_right.argtypes = [P, I, P, P, P, P, P]
     lib.mlcc3_jacobian_left.argtypes = [P, I, P, P, P, P, P]
     lib.mlcc3_transition_density.argtypes = [P, D] + [P] * 10
@@ -129,6 +131,10 @@ class Context:
 
     def triples_omega(self, omega1, omega2):
         self._check(self.lib.mlcc3_triples_omega(self.h, _ptr(omega1), _ptr(omega2)))
+
+    def triples_omega_static(self, omega1, omega2):
+        """mlcc3_triples_omega without allocating: scratch in a fixed device array."""
+        self._check(self.lib.mlcc3_triples_omega_static(self.h, _ptr(omega1), _ptr(omega2)))
 
     def jacobian_right(self, omega, R1, R2, rho1, rho2):
         w = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)

@@ -42,6 +42,8 @@ __global__ void density_norm_kernel(double *, const double *, const double *, co
 
 static thread_local std::string g_last_error;
 
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
 void check_cuda(cudaError_t e, const char *what) {
   if (e != cudaSuccess)
     throw Error{e == cudaErrorMemoryAllocation ? MLCC3_ERR_OOM : MLCC3_ERR_CUDA,
