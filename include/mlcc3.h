@@ -167,6 +167,13 @@ long long mlcc3_debug_nbatches(mlcc3_ctx *ctx);
  * its name (NUL-terminated, truncated to name_len), launches, summed event
  * milliseconds (0 without profiling) and flops; MLCC3_ERR_ARG past the end. */
 int mlcc3_debug_profile(mlcc3_ctx *ctx, int enable);
+
+/* C = A B^T on the split-precision tensor-core path (the contraction kernel
+ * of MLCC3_SPLIT_BF16X3): A [M][K], B [N][K], C [M][N], row-major FP64 device
+ * arrays.  A and B are split into hi/lo bfloat16 pairs; the three products
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32.  Diagnostic: it
+ * allocates temporaries and synchronises the default stream. */
+int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, int M, int N, int K);
 int mlcc3_debug_kernel_stats(mlcc3_ctx *ctx, int index, char *name, size_t name_len,
                              long long *launches, double *ms, double *flops);
 

@@ -26,7 +26,7 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
            "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
            "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
-           "mlcc3_triples_omega_static")
+           "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm")
 
 
 class MLCC3Error(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_debug_nbatches.argtypes = [P]
     lib.mlcc3_debug_nbatches.restype = ctypes.c_longlong
     lib.mlcc3_debug_profile.argtypes = [P, I]
+    lib.mlcc3_debug_tc_gemm.argtypes = [P, P, P, I, I, I]
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -90,6 +91,16 @@ def _ptr(x):
     if not x.is_contiguous() or str(x.dtype) != "torch.float64":
         raise ValueError("tensors must be contiguous float64")
     return x.data_ptr()
+
+
+def tc_gemm(A, B, C):
+    """C = A B^T (torch CUDA float64 tensors) on the split-precision tensor-core kernel."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    rc = lib.mlcc3_debug_tc_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K)
+    if rc != 0:
+        raise MLCC3Error(rc, lib.mlcc3_last_error().decode())
 
 
 class Context:

@@ -1,0 +1,324 @@
+// tcgen05 / TMA kernels of the split-precision path (sm_103a).
+//
+// tc_gemm_kernel: one 128 x BN tile of C = sum_segments A_seg B_seg^T per CTA.
+//   warp 0 lane 0  : TMA producer (A_hi, A_lo, B_hi, B_lo per 64-wide K chunk)
+//   warp 1         : TMEM allocation; lane 0 issues tcgen05.mma
+//   warps 2..5     : epilogue, tcgen05.ld of the FP32 accumulator
+// Every wait on an mbarrier is bounded (about one second of clock); on
+// expiry the kernel records kStatusTimeout in the status word, stops issuing
+// work, drains what it issued, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels_tc.cuh"
+
+namespace mlcc3 {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: about 2^31 clocks (~1 s at 2 GHz).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) {
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                      // LBO (unused for swizzled K-major)
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;  // SBO
+  d |= (uint64_t)1 << 46;                      // version
+  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcItem *__restrict__ items,
+                   const TcEpi epi, int *__restrict__ status) {
+  constexpr int A_BYTES = 128 * 128;
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int NCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = smem_u32(bars + STAGES);
+  const uint32_t done = smem_u32(bars + 2 * STAGES);
+
+  const TcItem &it = items[blockIdx.x];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int total = 0;
+  for (int s = 0; s < it.nseg; ++s) total += it.seg[s].nk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int stage = 0;
+    uint32_t phase = 0;
+    int issued = 0;
+    bool ok = true;
+    for (int s = 0; s < it.nseg && ok; ++s) {
+      const TcSeg &sg = it.seg[s];
+      for (int kc = 0; kc < sg.nk; ++kc) {
+        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = smem + stage * STAGE;
+        const uint32_t fb = full0 + 8 * stage;
+        mbar_expect_tx(fb, STAGE);
+        const int k = sg.ac[0] + 64 * kc, kb = sg.bc[0] + 64 * kc;
+        tma_load_4d(smem_u32(st), &maps.m[sg.amap], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
+        tma_load_4d(smem_u32(st + A_BYTES), &maps.m[sg.amap + 1], k, sg.ac[1], sg.ac[2], sg.ac[3],
+                    fb);
+        tma_load_4d(smem_u32(st + 2 * A_BYTES), &maps.m[sg.bmap], kb, sg.bc[1], sg.bc[2],
+                    sg.bc[3], fb);
+        tma_load_4d(smem_u32(st + 2 * A_BYTES + B_BYTES), &maps.m[sg.bmap + 1], kb, sg.bc[1],
+                    sg.bc[2], sg.bc[3], fb);
+        ++issued;
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (!ok) {
+      // drain: wait (bounded) until every chunk this thread issued has landed
+      int st2 = 0;
+      uint32_t ph2 = 0;
+      for (int c = 0; c < issued; ++c) {
+        if (c >= issued - STAGES) mbar_wait(full0 + 8 * st2, ph2, status);
+        if (++st2 == STAGES) {
+          st2 = 0;
+          ph2 ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int c = 0; c < total; ++c) {
+      if (!mbar_wait(full0 + 8 * stage, phase, status)) break;
+      tc_fence_after();
+      unsigned char *st = smem + stage * STAGE;
+      const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
+      const uint32_t bhi = smem_u32(st + 2 * A_BYTES), blo = smem_u32(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t off = kk * 32;
+        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(bhi + off), IDESC, (c > 0 || kk > 0));
+        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(blo + off), IDESC, 1u);
+        mma_bf16(tmem, smem_desc(alo + off), smem_desc(bhi + off), IDESC, 1u);
+      }
+      mma_commit(empty0 + 8 * stage);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    mma_commit(done);  // arrives once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const bool ok = mbar_wait(done, 0, status);
+    tc_fence_after();
+    const int lg = warp & 3;
+    const int row = lg * 32 + lane;
+    const int r1 = it.r1_0 + row / epi.R2, r2 = it.r2_0 + row % epi.R2;
+    const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
+    const long long base = it.out_off + (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+#pragma unroll 1
+    for (int n0 = 0; n0 < BN; n0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
+      if (!rv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = it.c0 + n0 + j;
+        if (n >= epi.nlim) break;
+        const long long a = base + (long long)n * epi.sn;
+        const float x = epi.alpha * v[j];
+        if (epi.mode == 0) {
+          static_cast<float *>(epi.out)[a] = x;
+        } else if (epi.mode == 1) {
+          static_cast<float *>(epi.out)[a] += x;
+        } else if (epi.mode == 2) {
+          atomicAdd(static_cast<double *>(epi.out) + a, (double)x);
+        } else {
+          static_cast<double *>(epi.out)[a] = (double)x;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS)
+                 : "memory");
+  }
+}
+
+template <int BN, int STAGES>
+constexpr int tc_smem_bytes() {
+  return STAGES * (2 * 128 * 128 + 2 * BN * 128) + 1024 + (2 * STAGES + 1) * 8 + 16;
+}
+
+template <int BN, int STAGES>
+static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, int nitems, const TcEpi &epi,
+                             int *status, cudaStream_t stream) {
+  constexpr int smem = tc_smem_bytes<BN, STAGES>();
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  tc_gemm_kernel<BN, STAGES><<<nitems, 192, smem, stream>>>(maps, items, epi, status);
+  return cudaGetLastError();
+}
+
+// Host launcher: BN is the tile width (columns), one of 64, 128, 160, 256.
+cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
+                           const TcEpi &epi, int *status, cudaStream_t stream) {
+  if (nitems <= 0) return cudaSuccess;
+  switch (BN) {
+    case 64: return launch_bn<64, 4>(maps, items, nitems, epi, status, stream);
+    case 128: return launch_bn<128, 3>(maps, items, nitems, epi, status, stream);
+    case 160: return launch_bn<160, 3>(maps, items, nitems, epi, status, stream);
+    case 256: return launch_bn<256, 2>(maps, items, nitems, epi, status, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int tc_tile_width(long long n) { return n <= 64 ? 64 : n <= 128 ? 128 : n <= 160 ? 160 : 256; }
+
+// Split FP64 -> (hi, lo) bfloat16 with a 4-D permuted gather and K padding:
+// out[o0][o1][o2][o3] (o3 < K3p, zero for o3 >= K3) = scale * in[o0 s0 + o1 s1 + o2 s2 + o3 s3].
+__global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                  long long D2, long long K3, long long K3p, long long s0,
+                                  long long s1, long long s2, long long s3, double scale) {
+  const long long total = D0 * D1 * D2 * K3p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long o3 = e % K3p;
+    long long r = e / K3p;
+    const long long o2 = r % D2;
+    r /= D2;
+    const long long o1 = r % D1;
+    const long long o0 = r / D1;
+    double x = 0.0;
+    if (o3 < K3) x = scale * in[o0 * s0 + o1 * s1 + o2 * s2 + o3 * s3];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    hi[e] = h;
+    lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+  }
+}
+
+}  // namespace mlcc3

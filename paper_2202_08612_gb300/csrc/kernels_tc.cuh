@@ -1,0 +1,54 @@
+// Split-precision tensor-core contraction (sm_103a): operands in global
+// memory as hi/lo bfloat16 pairs, K-major, K padded to a multiple of 64 and
+// read by TMA; tcgen05.mma with FP32 accumulation in TMEM computes
+// A_hi B_hi + A_hi B_lo + A_lo B_hi for every 16-wide K step.
+#pragma once
+#include <cuda.h>
+#include <cstdint>
+
+namespace mlcc3 {
+
+constexpr int kTcMaps = 24;   // tensor maps per launch (hi/lo pairs at even/odd slots)
+constexpr int kTcSegs = 8;    // K segments per item
+
+// Tensor maps of a launch, passed as a __grid_constant__ kernel parameter.
+struct TcMaps {
+  CUtensorMap m[kTcMaps];
+};
+
+// One K segment: A rows from map `amap` (hi) / `amap + 1` (lo) at 4-D
+// coordinates ac (ac[0], the K coordinate, advances by 64 per chunk), and the
+// same for B with `bmap` and bc.
+struct TcSeg {
+  int amap, bmap, nk, pad;
+  int ac[4];
+  int bc[4];
+};
+
+// One 128 x BN output tile.  Rows r of the tile map to global row coordinates
+// (r1_0 + r / R2, r2_0 + r % R2) in the epilogue.
+struct TcItem {
+  int nseg;
+  int r1_0, r2_0;
+  int c0;             // global column of the tile's first column
+  long long out_off;
+  TcSeg seg[kTcSegs];
+};
+
+// Epilogue: out[out_off + r1 s1 + r2 s2 + n sn] (op) alpha * acc for
+// r1 < lim1, r2 < lim2, n < nlim, with n = c0 + the tile column.  mode 0: FP32 store, 1: FP32 add
+// (read-modify-write; one writer per element per launch), 2: FP64 atomicAdd,
+// 3: FP64 store.
+struct TcEpi {
+  void *out;
+  int mode;
+  int R2;
+  long long s1, s2, sn;
+  int lim1, lim2, nlim;
+  float alpha;
+};
+
+// Status bits written by the tensor-core kernels.
+constexpr int kStatusTimeout = 2;
+
+}  // namespace mlcc3
