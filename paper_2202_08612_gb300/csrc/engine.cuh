@@ -1,6 +1,7 @@
 // Host-side engine of the MLCC3 triples library: context, buffers, and the
 // launch helpers every stage uses.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -77,6 +78,13 @@ struct mlcc3_ctx {
   std::map<std::string, std::pair<void *, size_t>> scratch;
   // item lists on the device, built once per pattern
   std::map<std::string, std::pair<void *, int>> items;
+  // hi/lo bfloat16 copies of operands of the tensor-core path, with their
+  // tensor maps (MLCC3_SPLIT_BF16X3)
+  struct SplitOp {
+    void *hi = nullptr, *lo = nullptr;
+    CUtensorMap mhi, mlo;
+  };
+  std::map<std::string, SplitOp> splits;
   // output copies back to host pointers at the end of a call
   std::vector<std::array<void *, 3>> pending_out;
 

@@ -451,3 +451,54 @@ __global__ void density_norm_kernel(double *__restrict__ D, const double *__rest
 }
 
 }  // namespace mlcc3
+
+namespace mlcc3 {
+
+// Finish of the tensor-core triples build: X = -(W + rank-1 terms) / (eps - omega)
+// per element of every block in `items`, W the FP32 sum of the six permuted
+// two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
+// Only kinds 2 and 3 of `terms` are evaluated here (summed over the six pair
+// permutations in FP64).
+__global__ void triples_finish_kernel(const float *__restrict__ W, const TripItem *__restrict__ items,
+                                      int nitems, const TripTerms terms,
+                                      const double *__restrict__ eps, int NO, int nv, double omega,
+                                      double *__restrict__ out, int *__restrict__ status) {
+  const long long nv3 = (long long)nv * nv * nv;
+  const long long total = nv3 * nitems;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const TripItem it = items[e / nv3];
+    const long long r = e % nv3;
+    const int X[3] = {(int)(r / ((long long)nv * nv)), (int)((r / nv) % nv), (int)(r % nv)};
+    const int I[3] = {it.i, it.j, it.k};
+    double acc = (double)W[it.off + r];
+    for (int t = 0; t < terms.n; ++t) {
+      const TripTerm &tm = terms.t[t];
+      if (tm.kind < 2) continue;
+      for (int sg = 0; sg < 6; ++sg) {
+        const long long x = I[kPerm[sg][0]], y = I[kPerm[sg][1]], z = I[kPerm[sg][2]];
+        const long long u = X[kPerm[sg][0]], v = X[kPerm[sg][1]], w = X[kPerm[sg][2]];
+        double val;
+        if (tm.kind == 2)
+          val = tm.A[x * tm.sA[0] + u * tm.sA[1]] *
+                tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+        else
+          val = tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]] *
+                tm.B[z * tm.sB[0] + w * tm.sB[1]];
+        acc = fma(tm.coef, val, acc);
+      }
+    }
+    const double den = eps[NO + X[0]] + eps[NO + X[1]] + eps[NO + X[2]] - eps[it.i] - eps[it.j] -
+                       eps[it.k] - omega;
+    double val;
+    if (fabs(den) < 1e-3) {
+      atomicOr(status, 1);
+      val = 0.0;
+    } else {
+      val = -acc / den;
+    }
+    out[it.off + r] = val;
+  }
+}
+
+}  // namespace mlcc3

@@ -7,6 +7,7 @@
 // stride set (pair symmetry X^{abc}_{ijk} = X^{sigma(abc)}_{sigma(ijk)},
 // Eq. tau3).  Sums over all ordered occupied triples in the SI equations
 // become sums over (batch, distinct ordering).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,7 @@
 
 #include "engine.cuh"
 #include "kernels_fp64.cuh"
+#include "kernels_tc.cuh"
 #include "mlcc3.h"
 
 namespace mlcc3 {
@@ -39,6 +41,16 @@ __global__ void sd_dot_kernel(const double *, const double *, const double *, co
                               int, int, int, double *);
 __global__ void density_norm_kernel(double *, const double *, const double *, const double *,
                                     int, int);
+__global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
+                                      const double *, int, int, double, double *, int *);
+bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
+                const unsigned long long strides[3], const unsigned box[4], std::string *err);
+cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
+                       long long D1, long long D2, long long K3, long long K3p, long long s0,
+                       long long s1, long long s2, long long s3, double scale, cudaStream_t st);
+cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
+                           const TcEpi &epi, int *status, cudaStream_t stream);
+int tc_tile_width(long long n);
 
 static thread_local std::string g_last_error;
 
@@ -486,13 +498,254 @@ void transpose_tl(mlcc3_ctx *c, const double *X, double *T) {
   });
 }
 
+
+// ---- split-precision tensor-core path (MLCC3_SPLIT_BF16X3) ----
+using SplitOp = mlcc3_ctx::SplitOp;
+enum class Box { Pair, Row };
+
+// hi/lo bfloat16 copy out[D0][D1][D2][Kp] of src (strides s0..s3, K innermost,
+// padded with zeros to a multiple of 64) and its two 4-D tensor maps.
+SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, long long D0,
+                    long long D1, long long D2, long long K, long long s0, long long s1,
+                    long long s2, long long s3, double scale, Box box) {
+  const long long Kp = (K + 63) / 64 * 64;
+  SplitOp &op = c->splits[key];
+  const size_t n = (size_t)(D0 * D1 * D2 * Kp);
+  op.hi = c->raw("split:" + key + ":hi", n * 2);
+  op.lo = c->raw("split:" + key + ":lo", n * 2);
+  check_cuda(split_bf16(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
+                        D0, D1, D2, K, Kp, s0, s1, s2, s3, scale, c->stream),
+             "split_bf16");
+  c->kstats["split_bf16_kernel"].launches += 1;
+  const unsigned long long dims[4] = {(unsigned long long)Kp, (unsigned long long)D2,
+                                      (unsigned long long)D1, (unsigned long long)D0};
+  const unsigned long long str[3] = {(unsigned long long)(Kp * 2), (unsigned long long)(Kp * 2 * D2),
+                                     (unsigned long long)(Kp * 2 * D2 * D1)};
+  unsigned bx[4] = {64, 16, 8, 1};
+  if (box == Box::Row) {
+    bx[1] = (unsigned)tc_tile_width(c->nv);
+    bx[2] = 1;
+  }
+  std::string err;
+  if (!encode_map(&op.mhi, op.hi, dims, str, bx, &err) || !encode_map(&op.mlo, op.lo, dims, str, bx, &err))
+    throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
+  return op;
+}
+
+// Operands of one two-index term of the triples expression, as split copies:
+// D-type sum_D X^{uD}_{xy} G_{vDwz}:  amp = X as [x][y][u][D], P/S = G as [z][v][w][D] / [z][w][v][D]
+// L-type -sum_L X^{uv}_{xL} g_{Lywz}:  P/S = X as [x][u][v][L] / [x][v][u][L], amp = -g as [y][z][w][L]
+struct SplitTerm {
+  bool dtype;
+  SplitOp *P, *S, *amp;
+};
+
+// Split copies of a D-type term: amplitude block X[x][u][y][D] and integral Gv-like [z][v][w][D].
+SplitTerm split_d(mlcc3_ctx *c, const std::string &ak, const double *amp, bool convert_a,
+                  const std::string &gk, const double *G, bool convert_g) {
+  S s(c);
+  SplitTerm t{true, nullptr, nullptr, nullptr};
+  if (convert_a)
+    make_split(c, ak + ":B", amp, s.no, s.no, s.nv, s.NV, s.bi, s.bL, s.ba, 1, 1.0, Box::Row);
+  t.amp = &c->splits.at(ak + ":B");
+  if (convert_g) {
+    make_split(c, gk + ":P", G, s.no, s.nv, s.nv, s.NV, s.gk, s.gb, s.gc, 1, 1.0, Box::Pair);
+    make_split(c, gk + ":S", G, s.no, s.nv, s.nv, s.NV, s.gk, s.gc, s.gb, 1, 1.0, Box::Pair);
+  }
+  t.P = &c->splits.at(gk + ":P");
+  t.S = &c->splits.at(gk + ":S");
+  return t;
+}
+
+// Split copies of an L-type term: amplitude Tl-like X[x][u][v][L] and integral Go-like [y][z][w][L].
+SplitTerm split_l(mlcc3_ctx *c, const std::string &ak, const double *ampl, bool convert_a,
+                  const std::string &gk, const double *Gl, bool convert_g) {
+  S s(c);
+  SplitTerm t{false, nullptr, nullptr, nullptr};
+  if (convert_a) {
+    make_split(c, ak + ":P", ampl, s.no, s.nv, s.nv, s.NO, s.ti, s.ta, s.tb, 1, 1.0, Box::Pair);
+    make_split(c, ak + ":S", ampl, s.no, s.nv, s.nv, s.NO, s.ti, s.tb, s.ta, 1, 1.0, Box::Pair);
+  }
+  if (convert_g)
+    make_split(c, gk + ":N", Gl, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
+  t.P = &c->splits.at(ak + ":P");
+  t.S = &c->splits.at(ak + ":S");
+  t.amp = &c->splits.at(gk + ":N");
+  return t;
+}
+
+// Triples blocks on the tensor cores.  For each batch and each pair tile, three
+// launches (single virtual index a, b, c) accumulate the six permuted
+// two-index terms of every D/L term into an FP32 block:
+//   orientation o collects the D-part of each W^{sigma} whose first virtual
+//   index sits at position o and the L-part of each W^{sigma} whose third
+//   virtual index sits at position o (Eq. tau3, P^{abc}_{ijk}).
+// triples_finish_kernel then adds the rank-1 terms and divides by (eps - omega).
+void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
+                   const std::vector<TripTerm> &rank1, const std::string &bkey,
+                   const std::vector<TripItem> &bs, double omega, double *out) {
+  S s(c);
+  if (bs.empty() || s.nv == 0) return;
+  if (terms.size() * 6 > (size_t)kTcMaps) throw Error{MLCC3_ERR_ARG, "too many tensor-core terms"};
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (size_t t = 0; t < terms.size(); ++t) {
+    const SplitTerm &st = terms[t];
+    maps.m[6 * t + 0] = st.P->mhi;
+    maps.m[6 * t + 1] = st.P->mlo;
+    maps.m[6 * t + 2] = st.S->mhi;
+    maps.m[6 * t + 3] = st.S->mlo;
+    maps.m[6 * t + 4] = st.amp->mhi;
+    maps.m[6 * t + 5] = st.amp->mlo;
+  }
+  const long long nb = (long long)bs.size();
+  float *W = static_cast<float *>(c->raw("tcW", sizeof(float) * (size_t)(c->batches.size() * s.nv3)));
+  const long long NVk = (s.NV + 63) / 64, NOk = (s.NO + 63) / 64;
+  const long long nt1 = (s.nv + 7) / 8, nt2 = (s.nv + 15) / 16;
+  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
+  std::string sig;
+  for (auto &t : terms) sig += t.dtype ? 'd' : 'l';
+  const int BN = tc_tile_width(s.nv);
+  for (int o = 0; o < 3; ++o) {
+    const int p1 = o == 0 ? 1 : 0, p2 = o == 2 ? 1 : 2;
+    int n = 0;
+    const BstcItem *raw_items = c->dev_items("tc:" + bkey + ":" + sig + ":" + std::to_string(o), [&] {
+      std::vector<TcItem> v;
+      for (long long u = 0; u < nb; ++u) {
+        const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
+        for (long long t1 = 0; t1 < nt1; ++t1)
+          for (long long t2 = 0; t2 < nt2; ++t2) {
+            TcItem it;
+            std::memset(&it, 0, sizeof(it));
+            it.r1_0 = (int)(8 * t1);
+            it.r2_0 = (int)(16 * t2);
+            it.c0 = 0;
+            it.out_off = bs[u].off;
+            int ns = 0;
+            for (size_t t = 0; t < terms.size(); ++t) {
+              for (int sg = 0; sg < 6; ++sg) {
+                const int s0 = kPermH[sg][0], s1 = kPermH[sg][1], s2 = kPermH[sg][2];
+                TcSeg &g = it.seg[ns];
+                if (terms[t].dtype && s0 == o) {
+                  g.amap = (int)(6 * t) + (s1 < s2 ? 0 : 2);
+                  g.bmap = (int)(6 * t) + 4;
+                  g.nk = (int)NVk;
+                  g.ac[1] = it.r2_0; g.ac[2] = it.r1_0; g.ac[3] = I[s2];
+                  g.bc[2] = I[s1]; g.bc[3] = I[s0];
+                  ++ns;
+                } else if (!terms[t].dtype && s2 == o) {
+                  g.amap = (int)(6 * t) + (s0 < s1 ? 0 : 2);
+                  g.bmap = (int)(6 * t) + 4;
+                  g.nk = (int)NOk;
+                  g.ac[1] = it.r2_0; g.ac[2] = it.r1_0; g.ac[3] = I[s0];
+                  g.bc[2] = I[s2]; g.bc[3] = I[s1];
+                  ++ns;
+                }
+              }
+            }
+            it.nseg = ns;
+            v.push_back(it);
+          }
+      }
+      // reuse the generic item cache: store TcItems as raw bytes
+      std::vector<BstcItem> raw((v.size() * sizeof(TcItem) + sizeof(BstcItem) - 1) / sizeof(BstcItem) + 1);
+      std::memcpy(raw.data(), v.data(), v.size() * sizeof(TcItem));
+      return raw;
+    }, &n);
+    const TcItem *items = reinterpret_cast<const TcItem *>(raw_items);
+    const int nitems = (int)(nb * nt1 * nt2);
+    TcEpi epi;
+    epi.out = W;
+    epi.mode = (o == 0) ? 0 : 1;
+    epi.R2 = 16;
+    epi.s1 = cs[p1];
+    epi.s2 = cs[p2];
+    epi.sn = cs[o];
+    epi.lim1 = (int)s.nv;
+    epi.lim2 = (int)s.nv;
+    epi.nlim = (int)s.nv;
+    epi.alpha = 1.0f;
+    double K = 0.0;
+    for (auto &t : terms) K += 2.0 * (t.dtype ? (double)s.NV : (double)s.NO);
+    const double fl = 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb;
+    c->launch("tc_gemm_kernel", fl, [&] {
+      check_cuda(launch_tc_gemm(BN, maps, items, nitems, epi, c->status, c->stream), "tc_gemm");
+    });
+  }
+  TripTerms tt{};
+  for (auto &t : rank1) tt.t[tt.n++] = t;
+  int n = 0;
+  auto it = c->items.find(bkey);
+  const TripItem *db;
+  if (it == c->items.end()) {
+    void *p = nullptr;
+    check_cuda(cudaMalloc(&p, bs.size() * sizeof(TripItem)), "cudaMalloc batches");
+    check_cuda(cudaMemcpy(p, bs.data(), bs.size() * sizeof(TripItem), cudaMemcpyHostToDevice), "batches");
+    c->items[bkey] = {p, (int)bs.size()};
+    db = static_cast<const TripItem *>(p);
+  } else {
+    db = static_cast<const TripItem *>(it->second.first);
+  }
+  (void)n;
+  launch_1d(c, nb * s.nv3, "triples_finish", [&](int g) {
+    c->launch("triples_finish_kernel", 0.0, [&] {
+      triples_finish_kernel<<<g, 256, 0, c->stream>>>(W, db, (int)nb, tt, c->eps, (int)s.NO,
+                                                      (int)s.nv, omega, out, c->status);
+    });
+  });
+}
+
+bool split_mode(const mlcc3_ctx *c) { return c->precision == MLCC3_SPLIT_BF16X3; }
+
+// Persistent split copies of the ground-state amplitudes and integrals.
+void build_split_persistent(mlcc3_ctx *c) {
+  S s(c);
+  make_split(c, "t:B", c->t2c, s.no, s.no, s.nv, s.NV, s.bi, s.bL, s.ba, 1, 1.0, Box::Row);
+  for (auto kv : {std::make_pair(std::string("Gv"), c->Gv), std::make_pair(std::string("Gb"), c->Gb)}) {
+    make_split(c, kv.first + ":P", kv.second, s.no, s.nv, s.nv, s.NV, s.gk, s.gb, s.gc, 1, 1.0, Box::Pair);
+    make_split(c, kv.first + ":S", kv.second, s.no, s.nv, s.nv, s.NV, s.gk, s.gc, s.gb, 1, 1.0, Box::Pair);
+  }
+  make_split(c, "Tl:P", c->Tl, s.no, s.nv, s.nv, s.NO, s.ti, s.ta, s.tb, 1, 1.0, Box::Pair);
+  make_split(c, "Tl:S", c->Tl, s.no, s.nv, s.nv, s.NO, s.ti, s.tb, s.ta, 1, 1.0, Box::Pair);
+  make_split(c, "Go:N", c->Go, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
+  make_split(c, "Gx:N", c->Gx, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
+}
+
+// tau3 terms on the tensor cores: D (t, Gv), L (Tl, Go).
+std::vector<SplitTerm> tau_split_terms(mlcc3_ctx *c) {
+  return {SplitTerm{true, &c->splits.at("Gv:P"), &c->splits.at("Gv:S"), &c->splits.at("t:B")},
+          SplitTerm{false, &c->splits.at("Tl:P"), &c->splits.at("Tl:S"), &c->splits.at("Go:N")}};
+}
+
+// L3 / lambda3 (SI): D (Lc, Gb), L (LcT, Gx), plus the rank-1 terms in FP64.
+void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const double *Lc,
+                  const double *LcT, const std::string &bkey, const std::vector<TripItem> &bs,
+                  double omega, double *out) {
+  S s(c);
+  std::vector<TripTerm> full = {
+      term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
+      term(1, (int)s.NO, -1.0, LcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
+      term(2, 0, 0.5, L1, {1, s.NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
+      term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
+  if (!split_mode(c)) {
+    triples(c, full, bkey, bs, omega, out);
+    return;
+  }
+  SplitTerm d = split_d(c, tag + "c", Lc, true, "Gb", c->Gb, false);
+  SplitTerm l = split_l(c, tag + "cT", LcT, true, "Gx", c->Gx, false);
+  triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out);
+}
+
 // tau and its contravariant form for all unique batches.
 void build_tau(mlcc3_ctx *c, double **tau, double **taut) {
   S s(c);
   size_t nb = c->batches.size();
   *tau = c->buf("tau", nb * s.nv3);
   *taut = c->buf("taut", nb * s.nv3);
-  triples(c, tau_terms(c), "batches", c->batches, 0.0, *tau);
+  if (split_mode(c))
+    triples_split(c, tau_split_terms(c), {}, "batches", c->batches, 0.0, *tau);
+  else
+    triples(c, tau_terms(c), "batches", c->batches, 0.0, *tau);
   contra3(c, *tau, *taut, (long long)nb);
 }
 
@@ -559,6 +812,27 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
   return u;
 }
 
+// R3 (Eq. R3): D (Rbar, Gv), L (Rbar_l, Go), D (t, Upsilon_v), L (Tl, Upsilon_o).
+void right_triples(mlcc3_ctx *c, const double *Rbar, const double *Rbl, const Ups &u,
+                   const std::string &bkey, const std::vector<TripItem> &bs, double omega,
+                   double *out) {
+  S s(c);
+  if (!split_mode(c)) {
+    std::vector<TripTerm> terms = {
+        term(0, (int)s.NV, 1.0, Rbar, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, Rbl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1}),
+        term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
+        term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
+    triples(c, terms, bkey, bs, omega, out);
+    return;
+  }
+  SplitTerm d1 = split_d(c, "Rbar", Rbar, true, "Gv", c->Gv, false);
+  SplitTerm l1 = split_l(c, "Rbarl", Rbl, true, "Go", c->Go, false);
+  SplitTerm d2 = split_d(c, "t", c->t2c, false, "Uv", u.Uv, true);
+  SplitTerm l2 = split_l(c, "Tl", c->Tl, false, "Uo", u.Uo, true);
+  triples_split(c, {d1, l1, d2, l2}, {}, bkey, bs, omega, out);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -610,6 +884,7 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   c->bstc1(Lt + NO, Lt + NO, c->Govov, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.vk, 1, s.vj, s.vb}), "Govov");
   fock_ov(c, c->t1, c->F, "F");
   transpose_tl(c, c->t2c, c->Tl);
+  if (split_mode(c)) build_split_persistent(c);
   c->built = true;
 }
 
@@ -663,12 +938,7 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     transpose_tl(c, Rbar, Rbl);
     Ups u = build_upsilon(c, R1);
     // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
-    std::vector<TripTerm> terms = {
-        term(0, (int)s.NV, 1.0, Rbar, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, Rbl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1}),
-        term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
-    triples(c, terms, bkey, bs, omega[v], R3);
+    right_triples(c, Rbar, Rbl, u, bkey, bs, omega[v], R3);
     contra3(c, R3, R3t, (long long)nb);
     c->zero(Zb, s.blk());
     c->zero(rho1, s.NV * s.NO);
@@ -730,12 +1000,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     });
     transpose_tl(c, Lc, LcT);
     // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
-    std::vector<TripTerm> terms = {
-        term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, LcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
-        term(2, 0, 0.5, L1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
-        term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
-    triples(c, terms, bkey, bs, omega[v], L3);
+    left_triples(c, "L", L1, Lc, LcT, bkey, bs, omega[v], L3);
     contra3(c, L3, L3t, (long long)nb);
     // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
     c->zero(Sb, s.blk());
@@ -1047,15 +1312,8 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   transpose_tl(c, lc, lcT);
   double *lam3 = c->buf("lam3", nb * s.nv3);
   double *lt3 = c->buf("lam3t", nb * s.nv3);
-  {
-    std::vector<TripTerm> terms = {
-        term(0, (int)s.NV, 1.0, lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, lcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
-        term(2, 0, 0.5, lam1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
-        term(3, 0, 0.5, lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
-    triples(c, terms, "batches", c->batches, 0.0, lam3);
-    contra3(c, lam3, lt3, (long long)nb);
-  }
+  left_triples(c, "lam", lam1, lc, lcT, "batches", c->batches, 0.0, lam3);
+  contra3(c, lam3, lt3, (long long)nb);
   // L3 (omega) and its contravariant form
   double *Lc = c->buf("Lc", s.blk());
   double *LcT = c->buf("LcT", s.no * s.nv * s.nv * NO);
@@ -1066,15 +1324,8 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   double *L3 = c->buf("L3", nb * s.nv3);
   double *L3t = c->buf("L3t", nb * s.nv3);
   if (cvs) c->zero(L3, nb * s.nv3);
-  {
-    std::vector<TripTerm> terms = {
-        term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, LcT, {s.ti, s.ta, s.tb, 1}, c->Gx, {s.oj, s.ok, s.oc, 1}),
-        term(2, 0, 0.5, L1, {1, NO, 0, 0}, c->Govov, {s.vj, s.vk, s.vb, 1}),
-        term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
-    triples(c, terms, bkey, bs, omega, L3);
-    contra3(c, L3, L3t, (long long)nb);
-  }
+  left_triples(c, "L", L1, Lc, LcT, bkey, bs, omega, L3);
+  contra3(c, L3, L3t, (long long)nb);
   // R3 (omega) and its contravariant form
   double *Rbar = c->buf("Rbar", s.blk());
   double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * NO);
@@ -1087,12 +1338,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   if (cvs) c->zero(R3, nb * s.nv3);
   {
     Ups u = build_upsilon(c, R1);
-    std::vector<TripTerm> terms = {
-        term(0, (int)s.NV, 1.0, Rbar, {s.bi, s.bL, s.ba, 1}, c->Gv, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, Rbl, {s.ti, s.ta, s.tb, 1}, c->Go, {s.oj, s.ok, s.oc, 1}),
-        term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
-        term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
-    triples(c, terms, bkey, bs, omega, R3);
+    right_triples(c, Rbar, Rbl, u, bkey, bs, omega, R3);
     contra3(c, R3, R3t, (long long)nb);
   }
   // D^{0-0} and D^{m-0}

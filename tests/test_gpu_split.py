@@ -1,0 +1,114 @@
+"""Split-precision mode (MLCC3_SPLIT_BF16X3) vs the FP64 oracle.
+
+The integral-amplitude products of the triples blocks run on the tensor cores
+from hi/lo bfloat16 operands (about 16 significant bits each) with FP32
+accumulation; denominators and all later contractions stay in FP64.  The bar:
+normwise relative error below 1e-4 on every output, and |f - f_oracle| below
+1e-6 (the target of the paper's oscillator strengths).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import Case, rel_err
+from paper_2202_08612_gb300 import binding
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+CASES = {
+    "ragged": dict(NO=7, NV=30, no=5, nv=13, NJ=40),
+    "tiny": dict(NO=6, NV=24, no=4, nv=8, NJ=72),
+    "wide": dict(NO=9, NV=70, no=6, nv=20, NJ=90),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(**CASES[request.param])
+    c.gctx = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+    c.octx = c.oracle_ctx()
+    return c
+
+
+def test_split_tau_blocks(case):
+    o, g = case.octx, case.gctx
+    NO, NV = o.NO, o.NV
+    o1, o2 = case.empty_dev((NV, NO)), case.empty_dev(case.sys.t2c.shape)
+    g.triples_omega(o1, o2)
+    nb = g.nbatches()
+    tau = g.debug_fetch("tau", nb * o.nv ** 3).reshape(nb, o.nv, o.nv, o.nv)
+    ref = O.tau3(o)
+    u, worst = 0, 0.0
+    for i in range(o.no):
+        for j in range(i + 1):
+            for k in range(j + 1):
+                if i == j == k:
+                    continue
+                worst = max(worst, rel_err(tau[u], ref[i, j, k]))
+                u += 1
+    assert worst < TOL, worst
+    r1, r2 = O.triples_omega(o)
+    assert rel_err(case.host(o1), r1) < TOL
+    assert rel_err(case.host(o2), O.from_full(o, r2)) < TOL
+
+
+def test_split_jacobians(case):
+    o, g, st = case.octx, case.gctx, case.st
+    R1, R2 = case.to_dev(st.R1), case.to_dev(st.R2)
+    L1, L2 = case.to_dev(st.L1), case.to_dev(st.L2)
+    rho1, rho2 = case.empty_dev(st.R1.shape), case.empty_dev(st.R2.shape)
+    sig1, sig2 = case.empty_dev(st.R1.shape), case.empty_dev(st.R2.shape)
+    g.jacobian_right(st.omega, R1, R2, rho1, rho2)
+    g.jacobian_left(st.omega, L1, L2, sig1, sig2)
+    rho1, rho2, sig1, sig2 = map(case.host, (rho1, rho2, sig1, sig2))
+    for v in range(len(st.omega)):
+        w = float(st.omega[v])
+        r1, r2 = O.jacobian_right(o, w, st.R1[v], O.to_full(o, st.R2[v]))
+        s1, s2 = O.jacobian_left(o, w, st.L1[v], O.to_full(o, st.L2[v]))
+        assert rel_err(rho1[v], r1) < TOL
+        assert rel_err(rho2[v], O.from_full(o, r2)) < TOL
+        assert rel_err(sig1[v], s1) < TOL
+        assert rel_err(sig2[v], O.from_full(o, s2)) < TOL
+
+
+def test_split_densities_and_f(case):
+    o, g, st = case.octx, case.gctx, case.st
+    nmo, NO = o.nmo, o.NO
+    w = float(st.omega[0])
+    outs = [case.empty_dev((nmo, nmo)) for _ in range(3)]
+    g.transition_density(w, case.to_dev(case.lam1), case.to_dev(case.lam2),
+                         case.to_dev(st.R1[0]), case.to_dev(st.R2[0]),
+                         case.to_dev(st.L1[0]), case.to_dev(st.L2[0]),
+                         case.to_dev(case.D00_in), *outs)
+    D00, Dm0, D0m = map(case.host, outs)
+    r00, rm0, r0m = O.transition_densities(o, w, case.lam1, O.to_full(o, case.lam2), st.R1[0],
+                                           O.to_full(o, st.R2[0]), st.L1[0],
+                                           O.to_full(o, st.L2[0]), case.D00_in)
+    for got, ref in ((D00, r00), (Dm0, rm0), (D0m, r0m)):
+        assert rel_err(got, ref) < TOL
+    D0m_full, Dm0_full = D0m.copy(), Dm0.copy()
+    D0m_full[NO:, :NO] += st.R1[0]
+    Dm0_full[:NO, NO:] += st.L1[0].T
+    f = g.oscillator_strength(w, case.to_dev(D0m_full), case.to_dev(Dm0_full), case.to_dev(case.mu))
+    r0m[NO:, :NO] += st.R1[0]
+    rm0[:NO, NO:] += st.L1[0].T
+    fo = O.oscillator_strength(o, w, r0m, rm0, case.mu)
+    assert abs(f - fo) < 1e-6, (f, fo)
+
+
+def test_split_cvs():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(NO=6, NV=22, no=4, nv=9, NJ=30, core=True, nstates=1)
+    g, o, st = c.context(precision=binding.MLCC3_SPLIT_BF16X3), c.oracle_ctx(), c.st
+    w = float(st.omega[0])
+    rho1, rho2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    g.jacobian_right(st.omega, c.to_dev(st.R1), c.to_dev(st.R2), rho1, rho2)
+    r1, r2 = O.jacobian_right(o, w, st.R1[0], O.to_full(o, st.R2[0]))
+    assert rel_err(c.host(rho1)[0], r1) < TOL
+    assert rel_err(c.host(rho2)[0], O.from_full(o, r2)) < TOL
