@@ -223,7 +223,9 @@ def run_ours(args, rank, world, local_rank):
     NO, NV, no, nv, NJ, ns = WORKLOADS[args.workload]
     prob = Problem(args.workload, 2022 + 17 * rank, device)
     stream = torch.cuda.current_stream(device)
-    ctx = binding.Context(*prob.dims, precision=binding.MLCC3_FP64, stream=stream.cuda_stream)
+    split = args.precision == "split"
+    prec = binding.MLCC3_SPLIT_BF16X3 if split else binding.MLCC3_FP64
+    ctx = binding.Context(*prob.dims, precision=prec, stream=stream.cuda_stream)
     dist = world > 1
 
     def barrier():
@@ -231,8 +233,9 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(device)
 
+    f_ours = None
     for _ in range(args.warmup):
-        prob.step(ctx, prob.dev, prob.out_dev)
+        f_ours = prob.step(ctx, prob.dev, prob.out_dev)
     ctx.profile(True)
     barrier()
     with ClockSampler(local_rank) as clk:
@@ -275,25 +278,58 @@ def run_ours(args, rank, world, local_rank):
     # dominant kernel of the timed region
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     name, (launches, kms, kfl) = dom
-    achieved = kfl / (kms * 1e-3) / 1e12 if kms > 0 else None
-    roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": traffic_for(name), "launches_per_step": launches / args.steps,
-                "share_of_step": kms / ms_total,
-                "peak_note": "nominal GB300 FP64 (FP64 FMA on the SIMT pipes; no FP64 tensor path)"}
+    alg = kfl / (kms * 1e-3) / 1e12 if kms > 0 else None
+    if name.startswith("tc_gemm"):
+        pk = peaks().get("bf16_tflops_sustained") or 1700.0
+        achieved = 3.0 * alg if alg else None  # three BF16 products per algorithmic product
+        roofline = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": pk,
+                    "unit": "TFLOP/s", "frac": achieved / pk if achieved else None,
+                    "traffic": traffic_for(name), "achieved_algorithmic": alg,
+                    "launches_per_step": launches / args.steps, "share_of_step": kms / ms_total,
+                    "peak_note": "measured sustained dense BF16 (MEASURED_PEAKS.json); achieved "
+                                 "counts the 3 BF16 products (hi*hi, hi*lo, lo*hi) per product"}
+    else:
+        roofline = {"kernel": name, "bound": "alu", "achieved": alg, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": alg / FP64_PEAK_TFLOPS if alg else None,
+                    "traffic": traffic_for(name), "launches_per_step": launches / args.steps,
+                    "share_of_step": kms / ms_total,
+                    "peak_note": "nominal GB300 FP64 (FP64 FMA on the SIMT pipes)"}
     gpu_launches = sum(v[0] for v in stats.values())
+
+    # the plain FP64 GPU path on the same system: its throughput and f
+    fp64 = None
+    if split and not args.no_fp64_compare:
+        ctx64 = binding.Context(*prob.dims, precision=binding.MLCC3_FP64, stream=stream.cuda_stream)
+        out64 = {k: torch.zeros_like(v) for k, v in prob.out_dev.items()}
+        f64 = prob.step(ctx64, prob.dev, out64)
+        barrier()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        f64 = prob.step(ctx64, prob.dev, out64)
+        e3.record(stream)
+        barrier()
+        ms64 = e2.elapsed_time(e3)
+        fp64 = {"value": fl / (ms64 * 1e-3) / 1e12, "ms_per_step": ms64,
+                "speedup_of_split": ms64 / ms,
+                "f_abs_diff": max(abs(a - b) for a, b in zip(f_ours, f64)),
+                "f_fp64": f64}
+        ctx64.close()
 
     if rank == 0:
         cpu_v, cpu_dt, sample = oracle_sample(args.workload, 77)
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x3" if split else "f64",
                 "data": "synthetic",
-                "config": {"workload": workload_name(args.workload), "precision": "fp64",
+                "config": {"workload": workload_name(args.workload),
+                           "precision": "split bf16x3 / fp32 accumulate / fp64 denominators and reductions"
+                           if split else "fp64",
                            "parallelism": f"replicas x{world} (independent systems)",
                            "l2": "inputs larger than L2 (Cholesky vectors "
                                  f"{prob.host['chol'].nbytes / 2**20:.0f} MiB)"},
                 "s_per_davidson_iter": s_iter,
+                "fp64_gpu_path": fp64, "f": f_ours,
                 "roofline": roofline,
                 "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": os.cpu_count(),
                                  "kind": "oracle", "sample": sample, "seconds": cpu_dt},
@@ -310,6 +346,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="guanine_like_small", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="split", choices=("split", "fp64"))
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the untimed FP64-path comparison step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -47,6 +47,7 @@ struct Ord {
   int p, q, r;
   long long off;      // canonical block offset (elements)
   long long vs[3];    // strides of x1, x2, x3
+  int sp[3];          // canonical positions of x1, x2, x3
 };
 
 }  // namespace mlcc3

@@ -322,3 +322,28 @@ __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *
 }
 
 }  // namespace mlcc3
+
+namespace mlcc3 {
+
+// Split with a two-level K: out[o0][o1][k] for k = k1 K2 + k2 < K1 K2 (zero up
+// to Kp) = scale * in[o0 s0 + o1 s1 + k1 sk1 + k2 sk2].
+__global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                     __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                     long long K1, long long K2, long long Kp, long long s0,
+                                     long long s1, long long sk1, long long sk2, double scale) {
+  const long long total = D0 * D1 * Kp;
+  const long long K = K1 * K2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e % Kp;
+    const long long r = e / Kp;
+    const long long o1 = r % D1, o0 = r / D1;
+    double x = 0.0;
+    if (k < K) x = scale * in[o0 * s0 + o1 * s1 + (k / K2) * sk1 + (k % K2) * sk2];
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    hi[e] = h;
+    lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+  }
+}
+
+}  // namespace mlcc3

@@ -51,6 +51,10 @@ cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, l
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
                            const TcEpi &epi, int *status, cudaStream_t stream);
 int tc_tile_width(long long n);
+cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
+                          long long D1, long long K1, long long K2, long long Kp, long long s0,
+                          long long s1, long long sk1, long long sk2, double scale,
+                          cudaStream_t st);
 
 static thread_local std::string g_last_error;
 
@@ -300,6 +304,7 @@ void make_batches(mlcc3_ctx *c) {
         o.r = r;
         o.off = bs[u].off;
         for (int t = 0; t < 3; ++t) o.vs[t] = cs[kPermH[sg][t]];
+        for (int t = 0; t < 3; ++t) o.sp[t] = kPermH[sg][t];
         v.push_back(o);
       }
     }
@@ -423,7 +428,15 @@ struct BackSet {
   const double *GL = nullptr;
   double cD = 0;
   const double *GD = nullptr;
+  std::string gd_key;      // split-mode name of GD's transposed copies
+  bool gd_convert = false; // convert GD now (per-vector operand)
 };
+
+// Tensor-core form of the D slot, defined with the split helpers below.
+void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
+               const BackSet &b, double *Zb);
+bool split_mode(const mlcc3_ctx *c);
+void split_gt(mlcc3_ctx *c, const std::string &key, const double *G);
 
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
@@ -467,7 +480,9 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NO;
     c->bstc(X, bset.GL, Zb, sh, bset.cL, it, n, true);
   }
-  if (bset.GD) {
+  if (bset.GD && split_mode(c)) {
+    tc_back_D(c, X, ords, okey, bset, Zb);
+  } else if (bset.GD) {
     it = c->dev_items(okey + ":bD", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ords)
@@ -709,6 +724,112 @@ void build_split_persistent(mlcc3_ctx *c) {
   make_split(c, "Tl:S", c->Tl, s.no, s.nv, s.nv, s.NO, s.ti, s.tb, s.ta, 1, 1.0, Box::Pair);
   make_split(c, "Go:N", c->Go, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
   make_split(c, "Gx:N", c->Gx, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
+  split_gt(c, "Gb", c->Gb);
+  split_gt(c, "Gv", c->Gv);
+}
+
+// hi/lo split with a two-level K (k = k1 K2 + k2): out[o0][o1][Kp]; tensor maps
+// over (Kp, o1, -, o0) with a box of `rows` rows.
+SplitOp &make_split_k2(mlcc3_ctx *c, const std::string &key, const double *src, long long D0,
+                       long long D1, long long K1, long long K2, long long s0, long long s1,
+                       long long sk1, long long sk2, unsigned rows) {
+  const long long Kp = (K1 * K2 + 63) / 64 * 64;
+  SplitOp &op = c->splits[key];
+  const size_t n = (size_t)(D0 * D1 * Kp);
+  op.hi = c->raw("split:" + key + ":hi", n * 2);
+  op.lo = c->raw("split:" + key + ":lo", n * 2);
+  check_cuda(split_bf16_k2(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
+                           D0, D1, K1, K2, Kp, s0, s1, sk1, sk2, 1.0, c->stream),
+             "split_bf16_k2");
+  c->kstats["split_bf16_kernel"].launches += 1;
+  const unsigned long long dims[4] = {(unsigned long long)Kp, (unsigned long long)D1, 1ULL,
+                                      (unsigned long long)D0};
+  const unsigned long long str[3] = {(unsigned long long)(Kp * 2), (unsigned long long)(Kp * 2 * D1),
+                                     (unsigned long long)(Kp * 2 * D1)};
+  const unsigned bx[4] = {64, rows, 1, 1};
+  std::string err;
+  if (!encode_map(&op.mhi, op.hi, dims, str, bx, &err) || !encode_map(&op.mlo, op.lo, dims, str, bx, &err))
+    throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
+  return op;
+}
+
+// G[k][b][c][D] (Gv-like) transposed to [k][D][(b,c)] and [k][D][(c,b)].
+void split_gt(mlcc3_ctx *c, const std::string &key, const double *G) {
+  S s(c);
+  make_split_k2(c, key + ":T", G, s.no, s.NV, s.nv, s.nv, s.gk, 1, s.gb, s.gc, 128);
+  make_split_k2(c, key + ":Ts", G, s.no, s.NV, s.nv, s.nv, s.gk, 1, s.gc, s.gb, 128);
+}
+
+// Z[p][a][q][D] += cD sum_{bc} X_{pqr}[a][b][c] G_r[b][c][D] on the tensor cores:
+// rows D (128-wide tiles of the transposed G), columns a, K = the pair (b,c).
+// The permuted view X_{pqr} is row a = canonical position s0 of one of three
+// split layouts of the canonical blocks (row = position 0, 1 or 2, K = the
+// other two in ascending order); when s1 > s2 that K order is (c,b) and the
+// (c,b)-ordered copy of G is used.
+void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
+               const BackSet &b, double *Zb) {
+  S s(c);
+  if (ords.empty() || s.nv == 0) return;
+  const long long nb = (long long)c->batches.size();
+  const unsigned BN = (unsigned)tc_tile_width(s.nv);
+  // row = canonical position 0 / 1 / 2; K = the other two (ascending)
+  make_split_k2(c, "XL0", X, nb, s.nv, s.nv, s.nv, s.nv3, s.nv * s.nv, s.nv, 1, BN);
+  make_split_k2(c, "XL1", X, nb, s.nv, s.nv, s.nv, s.nv3, s.nv, s.nv * s.nv, 1, BN);
+  make_split_k2(c, "XL2", X, nb, s.nv, s.nv, s.nv, s.nv3, 1, s.nv * s.nv, s.nv, BN);
+  if (b.gd_convert) split_gt(c, b.gd_key, b.GD);
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  const SplitOp *ops[5] = {&c->splits.at(b.gd_key + ":T"), &c->splits.at(b.gd_key + ":Ts"),
+                           &c->splits.at("XL0"), &c->splits.at("XL1"), &c->splits.at("XL2")};
+  for (int i = 0; i < 5; ++i) {
+    maps.m[2 * i] = ops[i]->mhi;
+    maps.m[2 * i + 1] = ops[i]->mlo;
+  }
+  const long long ntD = (s.NV + 127) / 128;
+  const int nk = (int)((s.nv * s.nv + 63) / 64);
+  int n = 0;
+  const BstcItem *raw_items = c->dev_items("tcD:" + okey, [&] {
+    std::vector<TcItem> v;
+    for (auto &o : ords)
+      for (long long t = 0; t < ntD; ++t) {
+        TcItem it;
+        std::memset(&it, 0, sizeof(it));
+        it.nseg = 1;
+        it.r1_0 = 0;
+        it.r2_0 = (int)(128 * t);
+        it.c0 = 0;
+        it.out_off = o.p * s.bi + o.q * s.bL;
+        TcSeg &g = it.seg[0];
+        g.amap = o.sp[1] < o.sp[2] ? 0 : 2;
+        g.bmap = 4 + 2 * o.sp[0];
+        g.nk = nk;
+        g.ac[1] = (int)(128 * t);
+        g.ac[3] = o.r;
+        g.bc[3] = (int)(o.off / s.nv3);
+        v.push_back(it);
+      }
+    std::vector<BstcItem> raw((v.size() * sizeof(TcItem) + sizeof(BstcItem) - 1) / sizeof(BstcItem) + 1);
+    std::memcpy(raw.data(), v.data(), v.size() * sizeof(TcItem));
+    return raw;
+  }, &n);
+  TcEpi epi;
+  epi.out = Zb;
+  epi.mode = 2;
+  epi.R2 = 128;
+  epi.s1 = 0;
+  epi.s2 = 1;
+  epi.sn = s.ba;
+  epi.lim1 = 1;
+  epi.lim2 = (int)s.NV;
+  epi.nlim = (int)s.nv;
+  epi.alpha = (float)b.cD;
+  const int nitems = (int)(ords.size() * ntD);
+  const double fl = 2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size();
+  c->launch("tc_gemm_kernel", fl, [&] {
+    check_cuda(launch_tc_gemm((int)BN, maps, reinterpret_cast<const TcItem *>(raw_items), nitems,
+                              epi, c->status, c->stream),
+               "tc_gemm back");
+  });
 }
 
 // tau3 terms on the tensor cores: D (t, Gv), L (Tl, Go).
@@ -901,7 +1022,7 @@ static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_ou
   b.cs = 0.5; b.Gs = c->Govov;
   b.cF = 0.5; b.F = c->F;
   b.cL = -1.0; b.GL = c->Gx;
-  b.cD = 1.0; b.GD = c->Gb;
+  b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
   back_contract(c, taut, c->ords, "ords", b, o1, Zb);
   finalize(c, Zb, o2, 0);
 }
@@ -946,12 +1067,12 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     b.cs = 0.5; b.Gs = c->Govov;
     b.cF = 0.5; b.F = c->F;
     b.cL = -1.0; b.GL = c->Gx;
-    b.cD = 1.0; b.GD = c->Gb;
+    b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
     back_contract(c, R3t, os, okey, b, rho1, Zb);
     BackSet bt;  // tau terms: 1/2 taut Upsilon_kc, -taut H1, +taut H2 (H2 carries the minus)
     bt.cF = 0.5; bt.F = u.Ukc;
     bt.cL = -1.0; bt.GL = u.H1;
-    bt.cD = 1.0; bt.GD = u.H2;
+    bt.cD = 1.0; bt.GD = u.H2; bt.gd_key = "H2"; bt.gd_convert = true;
     back_contract(c, taut, os, okey, bt, nullptr, Zb);
     finalize(c, Zb, rho2, 0);
   }
@@ -1006,7 +1127,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     c->zero(Sb, s.blk());
     BackSet b;
     b.cL = -1.0; b.GL = c->Go;
-    b.cD = 1.0; b.GD = c->Gv;
+    b.cD = 1.0; b.GD = c->Gv; b.gd_key = "Gv";
     back_contract(c, L3t, os, okey, b, nullptr, Sb);
     finalize(c, Sb, sig2, 1);
     // singles intermediates

@@ -166,3 +166,22 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
   }
   return MLCC3_OK;
 }
+
+namespace mlcc3 {
+__global__ void split_bf16_k2_kernel(const double *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
+                                     long long, long long, long long, long long, long long,
+                                     long long, long long, long long, double);
+
+cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
+                          long long D1, long long K1, long long K2, long long Kp, long long s0,
+                          long long s1, long long sk1, long long sk2, double scale,
+                          cudaStream_t st) {
+  long long total = D0 * D1 * Kp;
+  if (total <= 0) return cudaSuccess;
+  long long g = (total + 255) / 256;
+  if (g > 152LL * 64) g = 152LL * 64;
+  split_bf16_k2_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2,
+                                                scale);
+  return cudaGetLastError();
+}
+}  // namespace mlcc3

@@ -14,8 +14,9 @@ the shapes below stand in for them:
 * Cholesky vectors  L^J_pq = L^J_qp ~ N(0, 0.05^2), (pq|rs) = sum_J L^J_pq L^J_rs;
 * t1 ~ N(0, 0.01^2);
 * t2 MP2-like, t^{AB}_{IJ} = (AI|BJ) / (eps_I + eps_J - eps_A - eps_B);
-* trial vectors R ~ N(0, 1) on unique elements, unit norm; L = R + 0.3 noise,
-  then biorthonormalised against R;
+* trial vectors R ~ N(0, 1) on unique elements, scaled to a singles weight
+  |R1|^2 = 0.95 and doubles weight |R2|^2 = 0.05 (singly excited states);
+  L = R + 0.3 noise, then biorthonormalised against R;
 * lambda1 ~ N(0, 0.01^2), lambda2 = t2;  dipole integrals symmetric N(0, 0.1^2).
 
 Orbital ordering: occupied orbitals first, then virtual ones (n_mo = N_O + N_V);
@@ -161,8 +162,11 @@ def make_states(sys: System, nstates=1, seed=DEFAULT_SEED, cvs_states=()) -> Sta
             x1, x2 = cvs_project(d, sys.core_mask, x1, x2)
             omega[n] = 10.2
             cvs[n] = True
-        nrm = np.sqrt(sd_dot(d, x1, x2, x1, x2))
-        R1[n], R2[n] = x1 / nrm, x2 / nrm
+        # singles-dominated, like the paper's valence and core states:
+        # |R1|^2 = 0.95, |R2|^2 = 0.05 under the unique-element norm
+        n1 = np.sqrt(np.sum(x1 * x1))
+        n2 = np.sqrt(sd_dot(d, 0 * x1, x2, 0 * x1, x2))
+        R1[n], R2[n] = np.sqrt(0.95) * x1 / n1, np.sqrt(0.05) * x2 / n2
         y1 = R1[n] + 0.3 * r.normal(size=(NV, NO)) / np.sqrt(R1[n].size)
         y2 = R2[n] + symmetrize_block(d, 0.3 * r.normal(size=(no, nv, NO, NV))
                                       / np.sqrt(R2[n].size))

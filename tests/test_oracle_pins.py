@@ -189,7 +189,7 @@ def test_fd_upsilon():
     """Eqs. ups_v, ups_o: Upsilon = d g / dh along t1 -> t1 + h R1."""
     s, ctx = _small()
     R1 = synth.make_states(s, 1, seed=2).R1[0]
-    h = 1e-4
+    h = 2e-5
     up = _with(s, t1=s.t1 + h * R1)
     dn = _with(s, t1=s.t1 - h * R1)
     Uv, Uo = O.upsilon(ctx, R1)
