@@ -275,8 +275,15 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": fl * world / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
            "d2h_bytes_per_step": bo}
 
-    # dominant kernel of the timed region
-    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    # dominant kernel of the timed region (call-site tags "name:site" aggregated by name)
+    agg = {}
+    for k, (nl, kms_, kfl_) in stats.items():
+        base = k.split(":")[0]
+        a = agg.setdefault(base, [0, 0.0, 0.0])
+        a[0] += nl
+        a[1] += kms_
+        a[2] += kfl_
+    dom = max(agg.items(), key=lambda kv: kv[1][1])
     name, (launches, kms, kfl) = dom
     alg = kfl / (kms * 1e-3) / 1e12 if kms > 0 else None
     if name.startswith("tc_gemm"):
@@ -334,7 +341,9 @@ def run_ours(args, rank, world, local_rank):
                 "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": os.cpu_count(),
                                  "kind": "oracle", "sample": sample, "seconds": cpu_dt},
                 "e2e": e2e, "clocks": clk.summary(), "gpu_launches": gpu_launches,
-                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in stats.items()}}
+                "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},
+                "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
+                               sorted(stats.items(), key=lambda kv: -kv[1][1])[:24]}}
         print(json.dumps(line), flush=True)
     ctx.close()
 

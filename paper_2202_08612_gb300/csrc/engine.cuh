@@ -60,6 +60,7 @@ struct mlcc3_ctx {
   int device;
   std::vector<uint8_t> core;
   bool built = false;
+  bool tau_valid = false;   // tau3 / its contravariant blocks match the current build
 
   // persistent device arrays (FP64)
   double *eps = nullptr, *t1 = nullptr, *Lt = nullptr, *t2c = nullptr, *t2x = nullptr;
@@ -132,7 +133,7 @@ struct mlcc3_ctx {
   void finish();
 
   void bstc(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,
-            const mlcc3::BstcItem *items, int nitems, bool atomic);
+            const mlcc3::BstcItem *items, int nitems, bool atomic, const std::string &tag = "");
   void bstc1(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,
              const mlcc3::BstcItem &item, const std::string &key);
   void dot(const double *A, const double *B, double *C, const mlcc3::Shape &sh, double alpha,

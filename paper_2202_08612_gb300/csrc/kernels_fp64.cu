@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-  for (long long k0 = 0; k0 < K; k0 += BK) {
+  const long long kbeg = p.kchunk ? (long long)blockIdx.z * p.kchunk : 0;
+  const long long kend = p.kchunk ? min(K, kbeg + p.kchunk) : K;
+  for (long long k0 = kbeg; k0 < kend; k0 += BK) {
     if (tid < BK) {
       long long k = k0 + tid;
-      if (k < K) {
+      if (k < kend) {
         long long k3 = k % p.K3, k12 = k / p.K3;
         long long k2 = k12 % p.K2, k1 = k12 / p.K2;
         kA[tid] = k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4];
@@ -305,17 +307,16 @@ __global__ void __launch_bounds__(256) triples_build_kernel(const TripTerms term
 // Xt^{abc} = 4X^{abc} - 2X^{bac} - 2X^{cba} - 2X^{acb} + X^{cab} + X^{bca}.
 __global__ void contra3_kernel(const double *__restrict__ X, double *__restrict__ Xt,
                                long long nblocks, int nv) {
-  const long long nv3 = (long long)nv * nv * nv;
-  const long long total = nblocks * nv3;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long blk = e / nv3;
-    const long long r = e % nv3;
-    const int a = (int)(r / ((long long)nv * nv)), b = (int)((r / nv) % nv), c = (int)(r % nv);
-    const double *B = X + blk * nv3;
-    auto at = [&](int x, int y, int z) { return B[((long long)x * nv + y) * nv + z]; };
-    Xt[e] = 4.0 * at(a, b, c) - 2.0 * at(b, a, c) - 2.0 * at(c, b, a) - 2.0 * at(a, c, b) +
-            at(c, a, b) + at(b, c, a);
+  const int nv3 = nv * nv * nv;
+  const long long blk = blockIdx.y;
+  if (blk >= nblocks) return;
+  const double *B = X + blk * (long long)nv3;
+  double *O = Xt + blk * (long long)nv3;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
+    const int a = r / (nv * nv), b = (r / nv) % nv, c = r % nv;
+    auto at = [&](int x, int y, int z) { return B[(x * nv + y) * nv + z]; };
+    O[r] = 4.0 * at(a, b, c) - 2.0 * at(b, a, c) - 2.0 * at(c, b, a) - 2.0 * at(a, c, b) +
+           at(c, a, b) + at(b, c, a);
   }
 }
 
@@ -463,13 +464,11 @@ __global__ void triples_finish_kernel(const float *__restrict__ W, const TripIte
                                       int nitems, const TripTerms terms,
                                       const double *__restrict__ eps, int NO, int nv, double omega,
                                       double *__restrict__ out, int *__restrict__ status) {
-  const long long nv3 = (long long)nv * nv * nv;
-  const long long total = nv3 * nitems;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const TripItem it = items[e / nv3];
-    const long long r = e % nv3;
-    const int X[3] = {(int)(r / ((long long)nv * nv)), (int)((r / nv) % nv), (int)(r % nv)};
+  const int nv3 = nv * nv * nv;
+  if ((int)blockIdx.y >= nitems) return;
+  const TripItem it = items[blockIdx.y];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
+    const int X[3] = {r / (nv * nv), (r / nv) % nv, r % nv};
     const int I[3] = {it.i, it.j, it.k};
     double acc = (double)W[it.off + r];
     for (int t = 0; t < terms.n; ++t) {
@@ -498,6 +497,83 @@ __global__ void triples_finish_kernel(const float *__restrict__ W, const TripIte
       val = -acc / den;
     }
     out[it.off + r] = val;
+  }
+}
+
+}  // namespace mlcc3
+
+namespace mlcc3 {
+
+// Matrix-vector form of the batched strided contraction (N = 1): one warp per
+// output row m, the lanes stride over K, warp reduction, one (atomic) update.
+__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
+  const BstcItem &it = p.items[blockIdx.y];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long M = (long long)p.M1 * p.M2;
+  const long long m = (long long)blockIdx.x * 8 + warp;
+  if (m >= M) return;
+  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  const long long m1 = m / p.M2, m2 = m % p.M2;
+  const double *A = p.A + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
+  const double *B = p.B + it.offB;
+  double s = 0.0;
+  for (long long k = lane; k < K; k += 32) {
+    const long long k3 = k % p.K3, k12 = k / p.K3;
+    const long long k2 = k12 % p.K2, k1 = k12 / p.K2;
+    s += A[k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] * B[k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+    if (p.atomic) atomicAdd(C, p.alpha * s);
+    else *C += p.alpha * s;
+  }
+}
+
+}  // namespace mlcc3
+
+namespace mlcc3 {
+
+// D[k][l] (or [l][k]) += alpha sum_{ij} sum_{abc} X_{ijl}[abc] Y_{ijk}[abc] for
+// one (i,j) pair per blockIdx.y and a chunk of 256 (a,b,c) per blockIdx.x: the
+// chunk of every block X_{ij.} and Y_{ij.} is read once and all n_o^2 partial
+// dot products are formed from shared memory.  Views: off/stride tables per
+// ordered triple (p,q,r) -> canonical block offset and strides of x1, x2, x3
+// (have == 0 marks a triple without a stored block).
+__global__ void __launch_bounds__(256) pair_dots_kernel(const double *__restrict__ X,
+                                                        const double *__restrict__ Y,
+                                                        const long long *__restrict__ voff,
+                                                        const int *__restrict__ vstr,
+                                                        const char *__restrict__ vhave, int no, int nv,
+                                                        double *__restrict__ out, long long ldo, int kl,
+                                                        double alpha) {
+  extern __shared__ double sm[];
+  double *xs = sm;                  // [no][256]
+  double *ys = sm + (size_t)no * 256;  // [no][256]
+  const int i = blockIdx.y / no, j = blockIdx.y % no;
+  const int nv3 = nv * nv * nv;
+  const int r = blockIdx.x * 256 + threadIdx.x;
+  const int a = r / (nv * nv), b = (r / nv) % nv, c = r % nv;
+  for (int k = 0; k < no; ++k) {
+    const int v = (i * no + j) * no + k;
+    double xv = 0.0, yv = 0.0;
+    if (r < nv3 && vhave[v]) {
+      const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
+                          (long long)c * vstr[3 * v + 2];
+      xv = X[o];
+      yv = Y[o];
+    }
+    xs[k * 256 + threadIdx.x] = xv;
+    ys[k * 256 + threadIdx.x] = yv;
+  }
+  __syncthreads();
+  // thread t handles the pairs (k, l) with k*no + l = t, t + 256, ...
+  for (int t = threadIdx.x; t < no * no; t += 256) {
+    const int k = t / no, l = t % no;
+    double s = 0.0;
+    for (int e = 0; e < 256; ++e) s += xs[l * 256 + e] * ys[k * 256 + e];
+    if (s != 0.0) atomicAdd(out + (kl ? k * ldo + l : l * ldo + k), alpha * s);
   }
 }
 

@@ -23,7 +23,8 @@ struct BstcParams {
   double alpha;
   const BstcItem *items;
   int nitems;
-  int atomic;  // 1: accumulate with atomicAdd (items may overlap in C)
+  int atomic;        // 1: accumulate with atomicAdd (items may overlap in C)
+  long long kchunk;  // split-K: grid.z slices of this many K elements (0 = whole K)
 };
 
 // One additive term of the pre-permutation triples expression V^{abc}_{ijk}

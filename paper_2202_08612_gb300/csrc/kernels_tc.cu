@@ -118,7 +118,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcItem *__restrict__ items,
-                   const TcEpi epi, int *__restrict__ status) {
+                   const TcSeg *__restrict__ segs, const TcEpi epi, int *__restrict__ status) {
   constexpr int A_BYTES = 128 * 128;
   constexpr int B_BYTES = BN * 128;
   constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t done = smem_u32(bars + 2 * STAGES);
 
   const TcItem &it = items[blockIdx.x];
+  const TcSeg *seg = segs + it.seg_begin;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int total = 0;
-  for (int s = 0; s < it.nseg; ++s) total += it.seg[s].nk;
+  for (int s = 0; s < it.seg_count; ++s) total += seg[s].nk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t phase = 0;
     int issued = 0;
     bool ok = true;
-    for (int s = 0; s < it.nseg && ok; ++s) {
-      const TcSeg &sg = it.seg[s];
+    for (int s = 0; s < it.seg_count && ok; ++s) {
+      const TcSeg sg = seg[s];
       for (int kc = 0; kc < sg.nk; ++kc) {
         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
           ok = false;
@@ -252,8 +253,10 @@ __global__ void __launch_bounds__(192, 1)
           static_cast<float *>(epi.out)[a] += x;
         } else if (epi.mode == 2) {
           atomicAdd(static_cast<double *>(epi.out) + a, (double)x);
-        } else {
+        } else if (epi.mode == 3) {
           static_cast<double *>(epi.out)[a] = (double)x;
+        } else {
+          static_cast<double *>(epi.out)[a] += (double)x;
         }
       }
     }
@@ -273,25 +276,25 @@ constexpr int tc_smem_bytes() {
 }
 
 template <int BN, int STAGES>
-static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, int nitems, const TcEpi &epi,
-                             int *status, cudaStream_t stream) {
+static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                             int nitems, const TcEpi &epi, int *status, cudaStream_t stream) {
   constexpr int smem = tc_smem_bytes<BN, STAGES>();
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  tc_gemm_kernel<BN, STAGES><<<nitems, 192, smem, stream>>>(maps, items, epi, status);
+  tc_gemm_kernel<BN, STAGES><<<nitems, 192, smem, stream>>>(maps, items, segs, epi, status);
   return cudaGetLastError();
 }
 
 // Host launcher: BN is the tile width (columns), one of 64, 128, 160, 256.
-cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
-                           const TcEpi &epi, int *status, cudaStream_t stream) {
+cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream) {
   if (nitems <= 0) return cudaSuccess;
   switch (BN) {
-    case 64: return launch_bn<64, 4>(maps, items, nitems, epi, status, stream);
-    case 128: return launch_bn<128, 3>(maps, items, nitems, epi, status, stream);
-    case 160: return launch_bn<160, 3>(maps, items, nitems, epi, status, stream);
-    case 256: return launch_bn<256, 2>(maps, items, nitems, epi, status, stream);
+    case 64: return launch_bn<64, 4>(maps, items, segs, nitems, epi, status, stream);
+    case 128: return launch_bn<128, 3>(maps, items, segs, nitems, epi, status, stream);
+    case 160: return launch_bn<160, 3>(maps, items, segs, nitems, epi, status, stream);
+    case 256: return launch_bn<256, 2>(maps, items, segs, nitems, epi, status, stream);
     default: return cudaErrorInvalidValue;
   }
 }

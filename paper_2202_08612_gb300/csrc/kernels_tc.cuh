@@ -9,7 +9,6 @@
 namespace mlcc3 {
 
 constexpr int kTcMaps = 24;   // tensor maps per launch (hi/lo pairs at even/odd slots)
-constexpr int kTcSegs = 8;    // K segments per item
 
 // Tensor maps of a launch, passed as a __grid_constant__ kernel parameter.
 struct TcMaps {
@@ -25,20 +24,21 @@ struct TcSeg {
   int bc[4];
 };
 
-// One 128 x BN output tile.  Rows r of the tile map to global row coordinates
-// (r1_0 + r / R2, r2_0 + r % R2) in the epilogue.
+// One 128 x BN output tile: the K segments seg[seg_begin, seg_begin + seg_count)
+// of the launch's segment array.  Rows r of the tile map to global row
+// coordinates (r1_0 + r / R2, r2_0 + r % R2) in the epilogue.
 struct TcItem {
-  int nseg;
+  int seg_begin, seg_count;
   int r1_0, r2_0;
   int c0;             // global column of the tile's first column
+  int pad;
   long long out_off;
-  TcSeg seg[kTcSegs];
 };
 
 // Epilogue: out[out_off + r1 s1 + r2 s2 + n sn] (op) alpha * acc for
 // r1 < lim1, r2 < lim2, n < nlim, with n = c0 + the tile column.  mode 0: FP32 store, 1: FP32 add
 // (read-modify-write; one writer per element per launch), 2: FP64 atomicAdd,
-// 3: FP64 store.
+// 3: FP64 store, 4: FP64 add (read-modify-write; one writer per element per launch).
 struct TcEpi {
   void *out;
   int mode;

@@ -29,6 +29,9 @@
 namespace mlcc3 {
 __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
+__global__ void bstc_gemv_kernel(BstcParams p);
+__global__ void pair_dots_kernel(const double *, const double *, const long long *, const int *,
+                                 const char *, int, int, double *, long long, int, double);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, double *, int *);
@@ -48,8 +51,8 @@ bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
                        long long s1, long long s2, long long s3, double scale, cudaStream_t st);
-cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
-                           const TcEpi &epi, int *status, cudaStream_t stream);
+cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream);
 int tc_tile_width(long long n);
 cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                           long long D1, long long K1, long long K2, long long Kp, long long s0,
@@ -186,9 +189,9 @@ void mlcc3_ctx::finish() {
 }
 
 void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &sh, double alpha,
-                     const BstcItem *it, int nitems, bool atomic) {
+                     const BstcItem *it, int nitems, bool atomic, const std::string &tag) {
   if (nitems == 0) return;
-  BstcParams p;
+  BstcParams p{};
   p.A = A;
   p.B = B;
   p.C = C;
@@ -205,12 +208,39 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
   p.atomic = atomic ? 1 : 0;
   long long M = sh.M1 * sh.M2, N = sh.N1 * sh.N2;
   if (M == 0 || N == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
+  if (N == 1) {  // matrix-vector form: a warp per output row
+    for (int z0 = 0; z0 < nitems; z0 += 65535) {
+      p.items = it + z0;
+      int nz = std::min(65535, nitems - z0);
+      dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
+      const std::string name = tag.empty() ? std::string("bstc_gemv_kernel") : "bstc_gemv_kernel:" + tag;
+      launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
+             [&] { bstc_gemv_kernel<<<grid, 256, 0, stream>>>(p); });
+    }
+    check_cuda(cudaGetLastError(), "bstc_gemv launch");
+    return;
+  }
   const long long tiles = ((N + 63) / 64) * ((M + 63) / 64);
+  // split K when few output tiles face a long reduction
+  const long long K = sh.K1 * sh.K2 * sh.K3;
+  long long ksplit = 1;
+  if (tiles * nitems < 2 * 152 && K >= 2048) {
+    ksplit = std::min<long long>((4 * 152 + tiles * nitems - 1) / (tiles * nitems), K / 512);
+    ksplit = std::max<long long>(1, std::min<long long>(ksplit, 65535));
+  }
+  if (ksplit > 1) {
+    p.kchunk = ((K + ksplit - 1) / ksplit + 15) / 16 * 16;
+    ksplit = (K + p.kchunk - 1) / p.kchunk;
+    p.atomic = 1;
+  } else {
+    p.kchunk = 0;
+  }
   for (int z0 = 0; z0 < nitems; z0 += 65535) {
     p.items = it + z0;
     int nz = std::min(65535, nitems - z0);
-    dim3 grid((unsigned)tiles, (unsigned)nz);
-    launch("bstc_kernel", 2.0 * M * N * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
+    dim3 grid((unsigned)tiles, (unsigned)nz, (unsigned)ksplit);
+    const std::string name = tag.empty() ? std::string("bstc_kernel") : "bstc_kernel:" + tag;
+    launch(name.c_str(), 2.0 * M * N * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
            [&] { bstc_kernel<<<grid, 256, 0, stream>>>(p); });
   }
   check_cuda(cudaGetLastError(), "bstc launch");
@@ -220,7 +250,7 @@ void mlcc3_ctx::bstc1(const double *A, const double *B, double *C, const Shape &
                       const BstcItem &item, const std::string &key) {
   int n = 0;
   const BstcItem *d = dev_items(key, [&] { return std::vector<BstcItem>{item}; }, &n);
-  bstc(A, B, C, sh, alpha, d, n, false);
+  bstc(A, B, C, sh, alpha, d, n, false, key);
 }
 
 void mlcc3_ctx::dot(const double *A, const double *B, double *C, const Shape &sh, double alpha,
@@ -387,10 +417,16 @@ void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string
 }
 
 void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
-  long long n = nblocks * c->nv * c->nv * c->nv;
-  launch_1d(c, n, "contra3", [&](int g) {
-    c->launch("contra3_kernel", 0.0, [&] { contra3_kernel<<<g, 256, 0, c->stream>>>(X, Xt, nblocks, (int)c->nv); });
-  });
+  if (nblocks <= 0 || c->nv == 0) return;
+  const long long nv3 = c->nv * c->nv * c->nv;
+  for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
+    const long long nb = std::min<long long>(65535, nblocks - b0);
+    dim3 grid((unsigned)std::min<long long>((nv3 + 255) / 256, 1024), (unsigned)nb);
+    c->launch("contra3_kernel", 0.0, [&] {
+      contra3_kernel<<<grid, 256, 0, c->stream>>>(X + b0 * nv3, Xt + b0 * nv3, nb, (int)c->nv);
+    });
+  }
+  check_cuda(cudaGetLastError(), "contra3");
 }
 
 TripTerm term(int kind, int R, double coef, const double *A, std::array<long long, 4> sA,
@@ -430,13 +466,22 @@ struct BackSet {
   const double *GD = nullptr;
   std::string gd_key;      // split-mode name of GD's transposed copies
   bool gd_convert = false; // convert GD now (per-vector operand)
+  std::string gl_key;      // split-mode name of GL's transposed copy
+  bool gl_convert = false;
 };
+
+// Tensor-core form of the L slot, defined with the split helpers below.
+void tc_back_L(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
+               const BackSet &b, double *Zb);
 
 // Tensor-core form of the D slot, defined with the split helpers below.
 void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
                const BackSet &b, double *Zb);
 bool split_mode(const mlcc3_ctx *c);
 void split_gt(mlcc3_ctx *c, const std::string &key, const double *G);
+mlcc3_ctx::SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const double *G);
+mlcc3_ctx::SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk);
+void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
 
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
@@ -454,7 +499,7 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true);
+    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true, okey + ":bs");
   }
   if (bset.F) {
     it = c->dev_items(okey + ":bF", [&] {
@@ -466,9 +511,11 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-    c->bstc(X, bset.F, Zb, sh, bset.cF, it, n, true);
+    c->bstc(X, bset.F, Zb, sh, bset.cF, it, n, true, okey + ":bF");
   }
-  if (bset.GL) {
+  if (bset.GL && split_mode(c)) {
+    tc_back_L(c, X, ords, okey, bset, Zb);
+  } else if (bset.GL) {
     it = c->dev_items(okey + ":bL", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ords)
@@ -478,7 +525,7 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NO;
-    c->bstc(X, bset.GL, Zb, sh, bset.cL, it, n, true);
+    c->bstc(X, bset.GL, Zb, sh, bset.cL, it, n, true, okey + ":bL");
   }
   if (bset.GD && split_mode(c)) {
     tc_back_D(c, X, ords, okey, bset, Zb);
@@ -492,7 +539,7 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NV;
-    c->bstc(X, bset.GD, Zb, sh, bset.cD, it, n, true);
+    c->bstc(X, bset.GD, Zb, sh, bset.cD, it, n, true, okey + ":bD");
   }
 }
 
@@ -518,11 +565,97 @@ void transpose_tl(mlcc3_ctx *c, const double *X, double *T) {
 using SplitOp = mlcc3_ctx::SplitOp;
 enum class Box { Pair, Row };
 
+// Items (output tiles) and their K segments of one tensor-core launch.
+struct TcPlan {
+  std::vector<TcItem> items;
+  std::vector<TcSeg> segs;
+  void tile(int r1_0, int r2_0, int c0, long long off) {
+    TcItem it;
+    std::memset(&it, 0, sizeof(it));
+    it.seg_begin = (int)segs.size();
+    it.r1_0 = r1_0;
+    it.r2_0 = r2_0;
+    it.c0 = c0;
+    it.out_off = off;
+    items.push_back(it);
+  }
+  void seg(int amap, int bmap, int nk, int a1, int a2, int a3, int b1, int b2, int b3) {
+    TcSeg g;
+    std::memset(&g, 0, sizeof(g));
+    g.amap = amap;
+    g.bmap = bmap;
+    g.nk = nk;
+    g.ac[1] = a1; g.ac[2] = a2; g.ac[3] = a3;
+    g.bc[1] = b1; g.bc[2] = b2; g.bc[3] = b3;
+    segs.push_back(g);
+    items.back().seg_count += 1;
+  }
+  void drop_empty_last() {
+    if (!items.empty() && items.back().seg_count == 0) items.pop_back();
+  }
+};
+
+struct TcDev {
+  const TcItem *items;
+  const TcSeg *segs;
+  int nitems;
+};
+
+void *upload_cached(mlcc3_ctx *c, const std::string &key, const void *data, size_t bytes) {
+  auto it = c->items.find(key);
+  if (it != c->items.end()) return it->second.first;
+  void *p = nullptr;
+  check_cuda(cudaMalloc(&p, std::max<size_t>(bytes, 16)), "cudaMalloc tc plan");
+  if (bytes) check_cuda(cudaMemcpy(p, data, bytes, cudaMemcpyHostToDevice), "upload tc plan");
+  c->items[key] = {p, 0};
+  return p;
+}
+
+// The plan of `key`, built once by `build` and kept on the device.
+TcDev tc_plan(mlcc3_ctx *c, const std::string &key, const std::function<void(TcPlan &)> &build) {
+  auto it = c->items.find(key + ":items");
+  if (it != c->items.end())
+    return TcDev{static_cast<const TcItem *>(it->second.first),
+                 static_cast<const TcSeg *>(c->items.at(key + ":segs").first), it->second.second};
+  TcPlan pl;
+  build(pl);
+  void *si = upload_cached(c, key + ":items", pl.items.data(), pl.items.size() * sizeof(TcItem));
+  void *ss = upload_cached(c, key + ":segs", pl.segs.data(), pl.segs.size() * sizeof(TcSeg));
+  c->items[key + ":items"].second = (int)pl.items.size();
+  return TcDev{static_cast<const TcItem *>(si), static_cast<const TcSeg *>(ss),
+               (int)pl.items.size()};
+}
+
+void tc_launch(mlcc3_ctx *c, int BN, const TcMaps &maps, const TcDev &d, const TcEpi &epi,
+               double flops) {
+  if (d.nitems == 0) return;
+  c->launch("tc_gemm_kernel", flops, [&] {
+    check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, epi, c->status, c->stream),
+               "tc_gemm");
+  });
+}
+
+TcEpi make_epi(void *out, int mode, int R2, long long s1, long long s2, long long sn, long long lim1,
+               long long lim2, long long nlim, double alpha) {
+  TcEpi e;
+  e.out = out;
+  e.mode = mode;
+  e.R2 = R2;
+  e.s1 = s1;
+  e.s2 = s2;
+  e.sn = sn;
+  e.lim1 = (int)lim1;
+  e.lim2 = (int)lim2;
+  e.nlim = (int)nlim;
+  e.alpha = (float)alpha;
+  return e;
+}
+
 // hi/lo bfloat16 copy out[D0][D1][D2][Kp] of src (strides s0..s3, K innermost,
 // padded with zeros to a multiple of 64) and its two 4-D tensor maps.
 SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, long long D0,
                     long long D1, long long D2, long long K, long long s0, long long s1,
-                    long long s2, long long s3, double scale, Box box) {
+                    long long s2, long long s3, double scale, Box box, unsigned rowbox = 0) {
   const long long Kp = (K + 63) / 64 * 64;
   SplitOp &op = c->splits[key];
   const size_t n = (size_t)(D0 * D1 * D2 * Kp);
@@ -538,7 +671,7 @@ SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, lon
                                      (unsigned long long)(Kp * 2 * D2 * D1)};
   unsigned bx[4] = {64, 16, 8, 1};
   if (box == Box::Row) {
-    bx[1] = (unsigned)tc_tile_width(c->nv);
+    bx[1] = rowbox ? rowbox : (unsigned)tc_tile_width(c->nv);
     bx[2] = 1;
   }
   std::string err;
@@ -623,69 +756,30 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
   const int BN = tc_tile_width(s.nv);
   for (int o = 0; o < 3; ++o) {
     const int p1 = o == 0 ? 1 : 0, p2 = o == 2 ? 1 : 2;
-    int n = 0;
-    const BstcItem *raw_items = c->dev_items("tc:" + bkey + ":" + sig + ":" + std::to_string(o), [&] {
-      std::vector<TcItem> v;
+    TcDev dv = tc_plan(c, "tc:" + bkey + ":" + sig + ":" + std::to_string(o), [&](TcPlan &pl) {
       for (long long u = 0; u < nb; ++u) {
         const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
         for (long long t1 = 0; t1 < nt1; ++t1)
           for (long long t2 = 0; t2 < nt2; ++t2) {
-            TcItem it;
-            std::memset(&it, 0, sizeof(it));
-            it.r1_0 = (int)(8 * t1);
-            it.r2_0 = (int)(16 * t2);
-            it.c0 = 0;
-            it.out_off = bs[u].off;
-            int ns = 0;
+            pl.tile((int)(8 * t1), (int)(16 * t2), 0, bs[u].off);
             for (size_t t = 0; t < terms.size(); ++t) {
               for (int sg = 0; sg < 6; ++sg) {
                 const int s0 = kPermH[sg][0], s1 = kPermH[sg][1], s2 = kPermH[sg][2];
-                TcSeg &g = it.seg[ns];
-                if (terms[t].dtype && s0 == o) {
-                  g.amap = (int)(6 * t) + (s1 < s2 ? 0 : 2);
-                  g.bmap = (int)(6 * t) + 4;
-                  g.nk = (int)NVk;
-                  g.ac[1] = it.r2_0; g.ac[2] = it.r1_0; g.ac[3] = I[s2];
-                  g.bc[2] = I[s1]; g.bc[3] = I[s0];
-                  ++ns;
-                } else if (!terms[t].dtype && s2 == o) {
-                  g.amap = (int)(6 * t) + (s0 < s1 ? 0 : 2);
-                  g.bmap = (int)(6 * t) + 4;
-                  g.nk = (int)NOk;
-                  g.ac[1] = it.r2_0; g.ac[2] = it.r1_0; g.ac[3] = I[s0];
-                  g.bc[2] = I[s2]; g.bc[3] = I[s1];
-                  ++ns;
-                }
+                if (terms[t].dtype && s0 == o)
+                  pl.seg((int)(6 * t) + (s1 < s2 ? 0 : 2), (int)(6 * t) + 4, (int)NVk,
+                         (int)(16 * t2), (int)(8 * t1), I[s2], 0, I[s1], I[s0]);
+                else if (!terms[t].dtype && s2 == o)
+                  pl.seg((int)(6 * t) + (s0 < s1 ? 0 : 2), (int)(6 * t) + 4, (int)NOk,
+                         (int)(16 * t2), (int)(8 * t1), I[s0], 0, I[s2], I[s1]);
               }
             }
-            it.nseg = ns;
-            v.push_back(it);
           }
       }
-      // reuse the generic item cache: store TcItems as raw bytes
-      std::vector<BstcItem> raw((v.size() * sizeof(TcItem) + sizeof(BstcItem) - 1) / sizeof(BstcItem) + 1);
-      std::memcpy(raw.data(), v.data(), v.size() * sizeof(TcItem));
-      return raw;
-    }, &n);
-    const TcItem *items = reinterpret_cast<const TcItem *>(raw_items);
-    const int nitems = (int)(nb * nt1 * nt2);
-    TcEpi epi;
-    epi.out = W;
-    epi.mode = (o == 0) ? 0 : 1;
-    epi.R2 = 16;
-    epi.s1 = cs[p1];
-    epi.s2 = cs[p2];
-    epi.sn = cs[o];
-    epi.lim1 = (int)s.nv;
-    epi.lim2 = (int)s.nv;
-    epi.nlim = (int)s.nv;
-    epi.alpha = 1.0f;
+    });
+    TcEpi epi = make_epi(W, o == 0 ? 0 : 1, 16, cs[p1], cs[p2], cs[o], s.nv, s.nv, s.nv, 1.0);
     double K = 0.0;
     for (auto &t : terms) K += 2.0 * (t.dtype ? (double)s.NV : (double)s.NO);
-    const double fl = 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb;
-    c->launch("tc_gemm_kernel", fl, [&] {
-      check_cuda(launch_tc_gemm(BN, maps, items, nitems, epi, c->status, c->stream), "tc_gemm");
-    });
+    tc_launch(c, BN, maps, dv, epi, 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb);
   }
   TripTerms tt{};
   for (auto &t : rank1) tt.t[tt.n++] = t;
@@ -702,12 +796,15 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     db = static_cast<const TripItem *>(it->second.first);
   }
   (void)n;
-  launch_1d(c, nb * s.nv3, "triples_finish", [&](int g) {
+  for (long long b0 = 0; b0 < nb; b0 += 65535) {
+    const long long nbc = std::min<long long>(65535, nb - b0);
+    dim3 grid((unsigned)std::min<long long>((s.nv3 + 255) / 256, 1024), (unsigned)nbc);
     c->launch("triples_finish_kernel", 0.0, [&] {
-      triples_finish_kernel<<<g, 256, 0, c->stream>>>(W, db, (int)nb, tt, c->eps, (int)s.NO,
-                                                      (int)s.nv, omega, out, c->status);
+      triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps,
+                                                         (int)s.NO, (int)s.nv, omega, out, c->status);
     });
-  });
+  }
+  check_cuda(cudaGetLastError(), "triples_finish");
 }
 
 bool split_mode(const mlcc3_ctx *c) { return c->precision == MLCC3_SPLIT_BF16X3; }
@@ -726,6 +823,10 @@ void build_split_persistent(mlcc3_ctx *c) {
   make_split(c, "Gx:N", c->Gx, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
   split_gt(c, "Gb", c->Gb);
   split_gt(c, "Gv", c->Gv);
+  split_go_T(c, "Gx:T", c->Gx);
+  split_go_T(c, "Go:T", c->Go);
+  split_amp_T(c, "t:AT", c->t2c);
+  split_tl_T(c, "Tl", c->Tl);
 }
 
 // hi/lo split with a two-level K (k = k1 K2 + k2): out[o0][o1][Kp]; tensor maps
@@ -787,49 +888,201 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
   }
   const long long ntD = (s.NV + 127) / 128;
   const int nk = (int)((s.nv * s.nv + 63) / 64);
-  int n = 0;
-  const BstcItem *raw_items = c->dev_items("tcD:" + okey, [&] {
-    std::vector<TcItem> v;
+  TcDev dv = tc_plan(c, "tcD:" + okey, [&](TcPlan &pl) {
     for (auto &o : ords)
       for (long long t = 0; t < ntD; ++t) {
-        TcItem it;
-        std::memset(&it, 0, sizeof(it));
-        it.nseg = 1;
-        it.r1_0 = 0;
-        it.r2_0 = (int)(128 * t);
-        it.c0 = 0;
-        it.out_off = o.p * s.bi + o.q * s.bL;
-        TcSeg &g = it.seg[0];
-        g.amap = o.sp[1] < o.sp[2] ? 0 : 2;
-        g.bmap = 4 + 2 * o.sp[0];
-        g.nk = nk;
-        g.ac[1] = (int)(128 * t);
-        g.ac[3] = o.r;
-        g.bc[3] = (int)(o.off / s.nv3);
-        v.push_back(it);
+        pl.tile(0, (int)(128 * t), 0, o.p * s.bi + o.q * s.bL);
+        pl.seg(o.sp[1] < o.sp[2] ? 0 : 2, 4 + 2 * o.sp[0], nk, (int)(128 * t), 0, o.r, 0, 0,
+               (int)(o.off / s.nv3));
       }
-    std::vector<BstcItem> raw((v.size() * sizeof(TcItem) + sizeof(BstcItem) - 1) / sizeof(BstcItem) + 1);
-    std::memcpy(raw.data(), v.data(), v.size() * sizeof(TcItem));
-    return raw;
-  }, &n);
-  TcEpi epi;
-  epi.out = Zb;
-  epi.mode = 2;
-  epi.R2 = 128;
-  epi.s1 = 0;
-  epi.s2 = 1;
-  epi.sn = s.ba;
-  epi.lim1 = 1;
-  epi.lim2 = (int)s.NV;
-  epi.nlim = (int)s.nv;
-  epi.alpha = (float)b.cD;
-  const int nitems = (int)(ords.size() * ntD);
-  const double fl = 2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size();
-  c->launch("tc_gemm_kernel", fl, [&] {
-    check_cuda(launch_tc_gemm((int)BN, maps, reinterpret_cast<const TcItem *>(raw_items), nitems,
-                              epi, c->status, c->stream),
-               "tc_gemm back");
   });
+  TcEpi epi = make_epi(Zb, 2, 128, 0, 1, s.ba, 1, s.NV, s.nv, b.cD);
+  tc_launch(c, (int)BN, maps, dv, epi,
+            2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size());
+}
+
+// ---- layouts of the canonical triples blocks X[u][x0][x1][x2] ----
+// XL_k: row = canonical position k, K = the other two positions (ascending).
+SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k, unsigned rows) {
+  S s(c);
+  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
+  const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
+  return make_split_k2(c, key, X, (long long)c->batches.size(), s.nv, s.nv, s.nv, s.nv3, cs[k],
+                       cs[a], cs[b], rows);
+}
+
+// R_k: K = canonical position k, rows = the other two as (smaller, larger) pair tiles.
+SplitOp &layout_R(mlcc3_ctx *c, const std::string &key, const double *X, int k) {
+  S s(c);
+  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
+  const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
+  return make_split(c, key, X, (long long)c->batches.size(), s.nv, s.nv, s.nv, s.nv3, cs[a], cs[b],
+                    cs[k], 1.0, Box::Pair);
+}
+
+int occ_of(const Ord &o, int pos) { return pos == 0 ? o.p : pos == 1 ? o.q : o.r; }
+
+// out[occ_g][pair][n] += coef sum_{orderings, grouped by occupied position g}
+//                        sum_{x at view position vk} X_{pqr}[..] * B_{occ b1, occ b2}[n][x]
+// Rows: the two view positions other than vk, as pair tiles read from R_{s_vk}
+// (K = canonical position s_vk).  B: a split operand [occ b1][occ b2][n][K]
+// (map dims (K, n, occ b2, occ b1)) with box BN = tile_width(nN).
+// out address = out_off(occ_g) + view-pair strides (Sp1, Sp2) + n * Sn.
+void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp &B, long long nN,
+             const std::vector<Ord> &ords, const std::string &okey, int vk, int g, long long Sg,
+             long long Sp1, long long Sp2, long long Sn, double coef, double *out) {
+  S s(c);
+  if (ords.empty() || s.nv == 0 || nN == 0) return;
+  const int vp1 = vk == 0 ? 1 : 0, vp2 = vk == 2 ? 1 : 2;
+  const int b1 = g == 0 ? 1 : 0, b2 = g == 2 ? 1 : 2;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int k = 0; k < 3; ++k) {
+    SplitOp &r = layout_R(c, xkey + ":R" + std::to_string(k), X, k);
+    maps.m[2 * k] = r.mhi;
+    maps.m[2 * k + 1] = r.mlo;
+  }
+  maps.m[6] = B.mhi;
+  maps.m[7] = B.mlo;
+  const int BN = tc_tile_width(nN);
+  const long long nt1 = (s.nv + 7) / 8, nt2 = (s.nv + 15) / 16, ntN = (nN + BN - 1) / BN;
+  const int nk = (int)((s.nv + 63) / 64);
+  for (int cls = 0; cls < 2; ++cls) {
+    const std::string key = "tcP:" + okey + ":" + std::to_string(vk) + std::to_string(g) +
+                            std::to_string(cls) + ":" + std::to_string(nN);
+    TcDev dv = tc_plan(c, key, [&](TcPlan &pl) {
+      for (long long og = 0; og < s.no; ++og)
+        for (long long t1 = 0; t1 < nt1; ++t1)
+          for (long long t2 = 0; t2 < nt2; ++t2)
+            for (long long tn = 0; tn < ntN; ++tn) {
+              pl.tile((int)(8 * t1), (int)(16 * t2), (int)(BN * tn), og * Sg);
+              for (auto &o : ords) {
+                if (occ_of(o, g) != og) continue;
+                const bool ascending = o.sp[vp1] < o.sp[vp2];
+                if (ascending != (cls == 0)) continue;
+                pl.seg(2 * o.sp[vk], 6, nk, (int)(16 * t2), (int)(8 * t1), (int)(o.off / s.nv3),
+                       (int)(BN * tn), occ_of(o, b2), occ_of(o, b1));
+              }
+              pl.drop_empty_last();
+            }
+    });
+    // rows of R are (smaller, larger) canonical positions: the view pair in
+    // order (cls 0) or swapped (cls 1)
+    TcEpi epi = make_epi(out, 2, 16, cls == 0 ? Sp1 : Sp2, cls == 0 ? Sp2 : Sp1, Sn, s.nv, s.nv,
+                         nN, coef);
+    tc_launch(c, BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size() / 2.0);
+  }
+}
+
+// out[occ o1][occ o2][row][n] += coef sum_{orderings grouped by (o1, o2)}
+//      sum_{x,y at view positions (vk1 < vk2)} X_{pqr}[..] * T_{occ t}[n][(x,y)]
+// Rows: view position vr from XL_{s_vr} (128-row tiles); T: split [occ t][n][(x,y)]
+// in both K orders (T, Ts), map dims (K, n, 1, occ t), box BN = tile_width(nN).
+void tc_xt(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp &T,
+           const SplitOp &Ts, long long nN, const std::vector<Ord> &ords, const std::string &okey,
+           int vr, int tpos, long long S1, long long S2, long long Srow, double coef, double *out) {
+  S s(c);
+  if (ords.empty() || s.nv == 0 || nN == 0) return;
+  const int vk1 = vr == 0 ? 1 : 0, vk2 = vr == 2 ? 1 : 2;
+  const int o1 = tpos == 0 ? 1 : 0, o2 = tpos == 2 ? 1 : 2;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int k = 0; k < 3; ++k) {
+    SplitOp &r = layout_XL(c, xkey + ":XL" + std::to_string(k), X, k, 128);
+    maps.m[2 * k] = r.mhi;
+    maps.m[2 * k + 1] = r.mlo;
+  }
+  maps.m[6] = T.mhi;
+  maps.m[7] = T.mlo;
+  maps.m[8] = Ts.mhi;
+  maps.m[9] = Ts.mlo;
+  const int BN = tc_tile_width(nN);
+  const long long ntM = (s.nv + 127) / 128, ntN = (nN + BN - 1) / BN;
+  const int nk = (int)((s.nv * s.nv + 63) / 64);
+  const std::string key = "tcX:" + okey + ":" + std::to_string(vr) + std::to_string(tpos) + ":" +
+                          std::to_string(nN);
+  TcDev dv = tc_plan(c, key, [&](TcPlan &pl) {
+    for (long long x1 = 0; x1 < s.no; ++x1)
+      for (long long x2 = 0; x2 < s.no; ++x2)
+        for (long long tm = 0; tm < ntM; ++tm)
+          for (long long tn = 0; tn < ntN; ++tn) {
+            pl.tile(0, (int)(128 * tm), (int)(BN * tn), x1 * S1 + x2 * S2);
+            for (auto &o : ords) {
+              if (occ_of(o, o1) != x1 || occ_of(o, o2) != x2) continue;
+              pl.seg(2 * o.sp[vr], o.sp[vk1] < o.sp[vk2] ? 6 : 8, nk, (int)(128 * tm), 0,
+                     (int)(o.off / s.nv3), (int)(BN * tn), 0, occ_of(o, tpos));
+            }
+            pl.drop_empty_last();
+          }
+  });
+  TcEpi epi = make_epi(out, 2, 128, 0, Srow, 1, 1, s.nv, nN, coef);
+  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
+}
+
+// out[c][d] (row stride ld) += alpha sum_{orderings} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
+// Rows c and columns d both from XL_{s2} layouts (same K order for X and Y).
+void tc_vv(mlcc3_ctx *c, const double *X, const std::string &xkey, const double *Y,
+           const std::string &ykey, const std::vector<Ord> &ords, const std::string &okey, double *out,
+           long long ld, double alpha) {
+  S s(c);
+  if (ords.empty() || s.nv == 0) return;
+  const unsigned BN = (unsigned)tc_tile_width(s.nv);
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int k = 0; k < 3; ++k) {
+    SplitOp &x = layout_XL(c, xkey + ":XL" + std::to_string(k), X, k, 128);
+    SplitOp &y = layout_XL(c, ykey + ":YL" + std::to_string(k), Y, k, BN);
+    maps.m[2 * k] = x.mhi;
+    maps.m[2 * k + 1] = x.mlo;
+    maps.m[6 + 2 * k] = y.mhi;
+    maps.m[6 + 2 * k + 1] = y.mlo;
+  }
+  const long long ntM = (s.nv + 127) / 128;
+  const int nk = (int)((s.nv * s.nv + 63) / 64);
+  const size_t G = 16;  // orderings per tile (split K)
+  TcDev dv = tc_plan(c, "tcV:" + okey, [&](TcPlan &pl) {
+    for (long long tm = 0; tm < ntM; ++tm)
+      for (size_t o0 = 0; o0 < ords.size(); o0 += G) {
+        pl.tile(0, (int)(128 * tm), 0, 0);
+        for (size_t i = o0; i < std::min(ords.size(), o0 + G); ++i) {
+          const Ord &o = ords[i];
+          const int u = (int)(o.off / s.nv3);
+          pl.seg(2 * o.sp[2], 6 + 2 * o.sp[2], nk, (int)(128 * tm), 0, u, 0, 0, u);
+        }
+      }
+  });
+  TcEpi epi = make_epi(out, 2, 128, 0, ld, 1, 1, s.nv, s.nv, alpha);
+  tc_launch(c, (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)ords.size());
+}
+
+// Split copies of small operands (per call or at build):
+// amplitude block X[p][a][q][D] as [p][q][D][a] (Y1/P2 B operand)
+SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk) {
+  S s(c);
+  return make_split(c, key, Xblk, s.no, s.no, s.NV, s.nv, s.bi, s.bL, 1, s.ba, 1.0, Box::Row,
+                    (unsigned)tc_tile_width(s.NV));
+}
+// Go-like G[q][r][c][L] as [q][r][L][c] (Z_L B operand)
+SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const double *G) {
+  S s(c);
+  return make_split(c, key, G, s.no, s.no, s.NO, s.nv, s.oj, s.ok, 1, s.oc, 1.0, Box::Row,
+                    (unsigned)tc_tile_width(s.NO));
+}
+// Tl-like T[p][x][y][L] as [p][L][(x,y)] and [p][L][(y,x)] (tc_xt operands)
+void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T) {
+  S s(c);
+  const unsigned bn = (unsigned)tc_tile_width(s.NO);
+  make_split_k2(c, key + ":T", T, s.no, s.NO, s.nv, s.nv, s.ti, 1, s.ta, s.tb, bn);
+  make_split_k2(c, key + ":Ts", T, s.no, s.NO, s.nv, s.nv, s.ti, 1, s.tb, s.ta, bn);
+}
+
+// Z[p][a][L][b] += cL sum_{qr} sum_c X_{pqr}[a][b][c] G_{qr}[c][L] on the tensor cores.
+void tc_back_L(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
+               const BackSet &b, double *Zb) {
+  S s(c);
+  if (b.gl_convert) split_go_T(c, b.gl_key + ":T", b.GL);
+  tc_pair(c, X, "X", c->splits.at(b.gl_key + ":T"), s.NO, ords, okey, 2, 0, s.bi, s.ba, 1, s.bL,
+          b.cL, Zb);
 }
 
 // tau3 terms on the tensor cores: D (t, Gv), L (Tl, Go).
@@ -863,6 +1116,8 @@ void build_tau(mlcc3_ctx *c, double **tau, double **taut) {
   size_t nb = c->batches.size();
   *tau = c->buf("tau", nb * s.nv3);
   *taut = c->buf("taut", nb * s.nv3);
+  if (c->tau_valid) return;  // tau depends only on t2 and the integrals of the last build
+  c->tau_valid = true;
   if (split_mode(c))
     triples_split(c, tau_split_terms(c), {}, "batches", c->batches, 0.0, *tau);
   else
@@ -1006,6 +1261,7 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   fock_ov(c, c->t1, c->F, "F");
   transpose_tl(c, c->t2c, c->Tl);
   if (split_mode(c)) build_split_persistent(c);
+  c->tau_valid = false;
   c->built = true;
 }
 
@@ -1021,7 +1277,7 @@ static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_ou
   BackSet b;
   b.cs = 0.5; b.Gs = c->Govov;
   b.cF = 0.5; b.F = c->F;
-  b.cL = -1.0; b.GL = c->Gx;
+  b.cL = -1.0; b.GL = c->Gx; b.gl_key = "Gx";
   b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
   back_contract(c, taut, c->ords, "ords", b, o1, Zb);
   finalize(c, Zb, o2, 0);
@@ -1066,12 +1322,12 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     BackSet b;
     b.cs = 0.5; b.Gs = c->Govov;
     b.cF = 0.5; b.F = c->F;
-    b.cL = -1.0; b.GL = c->Gx;
+    b.cL = -1.0; b.GL = c->Gx; b.gl_key = "Gx";
     b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
     back_contract(c, R3t, os, okey, b, rho1, Zb);
     BackSet bt;  // tau terms: 1/2 taut Upsilon_kc, -taut H1, +taut H2 (H2 carries the minus)
     bt.cF = 0.5; bt.F = u.Ukc;
-    bt.cL = -1.0; bt.GL = u.H1;
+    bt.cL = -1.0; bt.GL = u.H1; bt.gl_key = "H1"; bt.gl_convert = true;
     bt.cD = 1.0; bt.GD = u.H2; bt.gd_key = "H2"; bt.gd_convert = true;
     back_contract(c, taut, os, okey, bt, nullptr, Zb);
     finalize(c, Zb, rho2, 0);
@@ -1126,7 +1382,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
     c->zero(Sb, s.blk());
     BackSet b;
-    b.cL = -1.0; b.GL = c->Go;
+    b.cL = -1.0; b.GL = c->Go; b.gl_key = "Go";
     b.cD = 1.0; b.GD = c->Gv; b.gd_key = "Gv";
     back_contract(c, L3t, os, okey, b, nullptr, Sb);
     finalize(c, Sb, sig2, 1);
@@ -1137,6 +1393,17 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     int n = 0;
     const BstcItem *it;
     Shape sh;
+    if (split_mode(c)) {
+      // tensor cores: Y1/P2 (K = a, rows (b,c)), Y2/P1 (K = (a,b), rows c)
+      tc_pair(c, L3t, "X", c->splits.at("t:AT"), s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1, 1.0, Y1);
+      tc_pair(c, taut, "X", split_amp_T(c, "Lc:AT", Lc), s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1,
+              1.0, P2);
+      tc_xt(c, L3t, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, os, okey, 2, 0, s.oj,
+            s.ok, s.oc, 1.0, Y2);
+      split_tl_T(c, "LcT", LcT);
+      tc_xt(c, taut, "X", c->splits.at("LcT:T"), c->splits.at("LcT:Ts"), s.NO, os, okey, 2, 0, s.oj,
+            s.ok, s.oc, 1.0, P1);
+    } else {
     // Y1[r][b][c][D] += sum_a Lt3_{pqr}[a][b][c] t2c[p][a][q][D]  (and P2 with taut, Lc)
     it = c->dev_items(okey + ":y1", [&] {
       std::vector<BstcItem> vv;
@@ -1146,8 +1413,8 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       return vv;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NV;
-    c->bstc(L3t, c->t2c, Y1, sh, 1.0, it, n, true);
-    c->bstc(taut, Lc, P2, sh, 1.0, it, n, true);
+    c->bstc(L3t, c->t2c, Y1, sh, 1.0, it, n, true, okey + ":y1");
+    c->bstc(taut, Lc, P2, sh, 1.0, it, n, true, okey + ":y1");
     // Y2[q][r][c][L] += sum_{ab} Lt3_{pqr}[a][b][c] Tl[p][a][b][L]  (and P1 with taut, LcT)
     it = c->dev_items(okey + ":y2", [&] {
       std::vector<BstcItem> vv;
@@ -1157,8 +1424,9 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       return vv;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
-    c->bstc(L3t, c->Tl, Y2, sh, 1.0, it, n, true);
-    c->bstc(taut, LcT, P1, sh, 1.0, it, n, true);
+    c->bstc(L3t, c->Tl, Y2, sh, 1.0, it, n, true, okey + ":y2");
+    c->bstc(taut, LcT, P1, sh, 1.0, it, n, true, okey + ":y2");
+    }
     // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
     it = c->dev_items(okey + ":y3", [&] {
       std::vector<BstcItem> vv;
@@ -1168,7 +1436,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       return vv;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true);
+    c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
     // --- singles through the Cholesky factors ---
     c->zero(sig1, s.NV * NO);
     for (double *p : {W, Z2, Z4, yv, Q, Q2}) (void)p;
@@ -1291,27 +1559,29 @@ struct ViewMap {
 void pair_dots(mlcc3_ctx *c, const ViewMap &vm, const double *X, const double *Y, double *out,
                long long ldo, bool kl, double alpha, const std::string &key) {
   S s(c);
-  int n = 0;
-  const BstcItem *it = c->dev_items(key, [&] {
-    std::vector<BstcItem> v;
-    for (long long i = 0; i < s.no; ++i)
-      for (long long j = 0; j < s.no; ++j)
-        for (long long k = 0; k < s.no; ++k) {
-          long long y = vm.idx(i, j, k);
-          if (!vm.have[y]) continue;
-          for (long long l = 0; l < s.no; ++l) {
-            long long x = vm.idx(i, j, l);
-            if (!vm.have[x]) continue;
-            long long o = kl ? k * ldo + l : l * ldo + k;
-            v.push_back(mk_item(vm.off[x], vm.off[y], o, {0, 0, vm.s0[x], vm.s1[x], vm.s2[x]},
-                                {vm.s0[y], vm.s1[y], vm.s2[y], 0, 0}, {0, 0, 0, 0}));
-          }
-        }
-    return v;
-  }, &n);
-  Shape sh;
-  sh.K1 = s.nv; sh.K2 = s.nv; sh.K3 = s.nv;
-  c->dot(X, Y, out, sh, alpha, it, n);
+  const long long n3 = s.no * s.no * s.no;
+  if (n3 == 0 || s.nv == 0) return;
+  // view tables on the device (built once)
+  void *voff = upload_cached(c, "pd:off", vm.off.data(), n3 * sizeof(long long));
+  std::vector<int> str(3 * n3);
+  for (long long x = 0; x < n3; ++x) {
+    str[3 * x] = (int)vm.s0[x];
+    str[3 * x + 1] = (int)vm.s1[x];
+    str[3 * x + 2] = (int)vm.s2[x];
+  }
+  void *vstr = upload_cached(c, "pd:str", str.data(), str.size() * sizeof(int));
+  void *vhave = upload_cached(c, "pd:have", vm.have.data(), n3);
+  const size_t smem = 2 * (size_t)s.no * 256 * sizeof(double);
+  check_cuda(cudaFuncSetAttribute(pair_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem), "pair_dots smem");
+  dim3 grid((unsigned)((s.nv3 + 255) / 256), (unsigned)(s.no * s.no));
+  c->launch("pair_dots_kernel", 2.0 * (double)(s.no * s.no) * (double)(s.no * s.no) * (double)s.nv3, [&] {
+    pair_dots_kernel<<<grid, 256, smem, c->stream>>>(X, Y, static_cast<const long long *>(voff),
+                                                     static_cast<const int *>(vstr),
+                                                     static_cast<const char *>(vhave), (int)s.no,
+                                                     (int)s.nv, out, ldo, kl ? 1 : 0, alpha);
+  });
+  (void)key;
 }
 
 // out[c][d] += alpha sum_{pqr} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
@@ -1328,7 +1598,7 @@ void vv_block(mlcc3_ctx *c, const double *X, const double *Y, double *out, long 
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.N1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(X, Y, out, sh, alpha, it, n, true);
+  c->bstc(X, Y, out, sh, alpha, it, n, true, "ords:vv:" + std::to_string(ldo));
 }
 
 // out[r][c] (row stride ldo, col stride 1) += alpha sum_{ab} X_{pqr}[a][b][c] B[p][a][q][b]
@@ -1346,7 +1616,7 @@ void y3_like(mlcc3_ctx *c, const double *X, const double *B, double *out, long l
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(X, B, out, sh, alpha, it, n, true);
+  c->bstc(X, B, out, sh, alpha, it, n, true, key);
 }
 
 // V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
@@ -1362,7 +1632,7 @@ void v_like(mlcc3_ctx *c, const double *X, const double *T, double *V) {
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
-  c->bstc(X, T, V, sh, 1.0, it, n, true);
+  c->bstc(X, T, V, sh, 1.0, it, n, true, "ords:vlike");
 }
 
 // D[L][NO+D] += alpha sum_{q,r,b} V[q][r][b][L] X[q][b][r][D]   (X in block layout)
@@ -1389,10 +1659,17 @@ void density_left_gpu(mlcc3_ctx *c, const ViewMap &vm, const double *Xt3, const 
   // D_LD -= sum Xt^{abc}_{ijk} t^{ac}_{iL} t^{bD}_{jk}
   double *V = c->buf("dV", s.gosz());
   c->zero(V, s.gosz());
-  v_like(c, Xt3, c->Tl, V);
+  if (split_mode(c))
+    tc_xt(c, Xt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, c->ords, "ords", 1, 0,
+          s.oj, s.ok, s.oc, 1.0, V);
+  else
+    v_like(c, Xt3, c->Tl, V);
   d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
   // D_cd += 1/2 sum Xt^{abc}_{ijk} tau^{abd}_{ijk}
-  vv_block(c, Xt3, tau, D + NO * nmo + NO, nmo, 0.5);
+  if (split_mode(c))
+    tc_vv(c, Xt3, "X", tau, "Y", c->ords, "ords", D + NO * nmo + NO, nmo, 0.5);
+  else
+    vv_block(c, Xt3, tau, D + NO * nmo + NO, nmo, 0.5);
   (void)tag;
 }
 
@@ -1482,7 +1759,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     return v;
   }, &n);
   sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-  c->bstc(lt3, R1, U, sh, 1.0, it, n, true);
+  c->bstc(lt3, R1, U, sh, 1.0, it, n, true, "ords:U");
   // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
   sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
   c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
@@ -1497,7 +1774,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     return v;
   }, &n);
   sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(tau, U, D + NO, sh, 1.0, it, n, true);
+  c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, "ords:ld1");
   it = c->dev_items("ords:ld2", [&] {
     std::vector<BstcItem> v;
     for (auto &o : c->ords)
@@ -1505,7 +1782,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
                           {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
     return v;
   }, &n);
-  c->bstc(tau, U, D + NO, sh, -1.0, it, n, true);
+  c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, "ords:ld2");
   //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
   y3_like(c, R3t, lc, D + NO, nmo, 0.5, "ords:y3d");
   // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}
@@ -1519,7 +1796,13 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}
   double *V = c->buf("dV", s.gosz());
   c->zero(V, s.gosz());
-  v_like(c, lt3, Rbl, V);
+  if (split_mode(c)) {
+    split_tl_T(c, "Rbl", Rbl);
+    tc_xt(c, lt3, "X", c->splits.at("Rbl:T"), c->splits.at("Rbl:Ts"), s.NO, c->ords, "ords", 1, 0,
+          s.oj, s.ok, s.oc, 1.0, V);
+  } else {
+    v_like(c, lt3, Rbl, V);
+  }
   d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
   //   D_LD -= sum lt^{abc}_{ijk} Rbar^{aD}_{ik} t^{bc}_{jL}
   double *V3 = c->buf("dV3", s.gosz());
@@ -1532,7 +1815,11 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     return v;
   }, &n);
   sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = NO;
-  c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true);
+  if (split_mode(c))
+    tc_xt(c, lt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, c->ords, "ords", 0, 1,
+          s.oj, s.ok, s.oc, 1.0, V3);
+  else
+    c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true, "ords:v3");
   sh = Shape{}; sh.M1 = NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
   c->bstc1(V3, Rbar, D + NO, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dLD3");
   // D_lD -= 1/2 sum_k E[l][k] R^D_k,  E[l][k] = sum lt_{ijk} tau_{ijl}
@@ -1543,7 +1830,10 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   c->bstc1(E, R1, D + NO, sh, -0.5, mk_item(0, 0, 0, {s.no, 0, 1, 0, 0}, {1, 0, 0, NO, 0}, {nmo, 0, 1, 0}), "dlD");
   // D_Ld -= 1/2 sum_c E2[c][d] R^c_L,  E2[c][d] = sum lt^{abc}_{ijk} tau^{abd}_{ijk}
   double *E2 = E + s.no * s.no;
-  vv_block(c, lt3, tau, E2, s.nv, 1.0);
+  if (split_mode(c))
+    tc_vv(c, lt3, "X", tau, "Y", c->ords, "ords", E2, s.nv, 1.0);
+  else
+    vv_block(c, lt3, tau, E2, s.nv, 1.0);
   sh = Shape{}; sh.M1 = NO; sh.N1 = s.nv; sh.K1 = s.nv;
   c->bstc1(R1, E2, D + NO, sh, -0.5, mk_item(0, 0, 0, {1, 0, NO, 0, 0}, {s.nv, 0, 0, 1, 0}, {nmo, 0, 1, 0}), "dLd");
   // D_ck += W3[k][c]
@@ -1559,7 +1849,10 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
   c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dcD");
   // D_cd += 1/2 sum lt^{abc}_{ijk} R^{abd}_{ijk}
-  vv_block(c, lt3, R3, D + NO * nmo + NO, nmo, 0.5);
+  if (split_mode(c))
+    tc_vv(c, lt3, "X", R3, "Y", c->ords, "ords", D + NO * nmo + NO, nmo, 0.5);
+  else
+    vv_block(c, lt3, R3, D + NO * nmo + NO, nmo, 0.5);
   // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings), lambda_SD.R_SD
   double *sc = c->dscal + 1;
   c->zero(sc, 2);

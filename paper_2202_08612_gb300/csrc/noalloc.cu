@@ -170,9 +170,11 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
   const long long nt = (nv + 7) / 8;
   triples_build_kernel<<<dim3((unsigned)(nt * nt * nt), (unsigned)nb), 256, 0, st>>>(
       tt, dbatch, c->eps, (int)NO, (int)nv, 0.0, tau, c->status);
-  long long tot = nb * nv3;
-  int g = (int)std::min<long long>((tot + 255) / 256, 152LL * 64);
-  contra3_kernel<<<g, 256, 0, st>>>(tau, taut, nb, (int)nv);
+  for (long long b0 = 0; b0 < nb; b0 += 65535) {
+    const long long nbc = std::min<long long>(65535, nb - b0);
+    dim3 cg((unsigned)std::min<long long>((nv3 + 255) / 256, 1024), (unsigned)nbc);
+    contra3_kernel<<<cg, 256, 0, st>>>(tau + b0 * nv3, taut + b0 * nv3, nbc, (int)nv);
+  }
   // scratch keeps the previous call's contents: clear the accumulators
   if (!chk(cudaMemsetAsync(Zb, 0, sizeof(double) * blk, st), "memset Zb") ||
       !chk(cudaMemsetAsync(omega1, 0, sizeof(double) * NV * NO, st), "memset omega1"))
@@ -209,7 +211,7 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
       bstc_kernel<<<dim3((unsigned)tiles, (unsigned)bp.nitems), 256, 0, st>>>(bp);
     }
   }
-  g = (int)std::min<long long>((blk + 255) / 256, 152LL * 64);
+  const int g = (int)std::min<long long>((blk + 255) / 256, 152LL * 64);
   finalize_doubles_kernel<<<std::max(g, 1), 256, 0, st>>>(Zb, omega2, (int)no, (int)nv, (int)NO,
                                                           (int)NV, 0);
   if (!chk(cudaGetLastError(), "launch")) return MLCC3_ERR_CUDA;

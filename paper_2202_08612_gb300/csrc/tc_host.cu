@@ -16,8 +16,8 @@
 namespace mlcc3 {
 
 void set_last_error(const std::string &msg);
-cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, int nitems,
-                           const TcEpi &epi, int *status, cudaStream_t stream);
+cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream);
 int tc_tile_width(long long n);
 __global__ void split_bf16_kernel(const double *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
                                   long long, long long, long long, long long, long long, long long,
@@ -122,26 +122,34 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
       return fail(MLCC3_ERR_CUDA, err);
   }
   std::vector<TcItem> items;
+  std::vector<TcSeg> segs;
   for (int m0 = 0; m0 < M; m0 += 128)
     for (int n0 = 0; n0 < N; n0 += BN) {
       TcItem it{};
-      it.nseg = 1;
+      it.seg_begin = (int)segs.size();
+      it.seg_count = 1;
       it.r1_0 = 0;
       it.r2_0 = m0;
       it.c0 = n0;
       it.out_off = 0;
-      it.seg[0].amap = 0;
-      it.seg[0].bmap = 2;
-      it.seg[0].nk = (int)(Kp / 64);
-      it.seg[0].ac[1] = m0;
-      it.seg[0].bc[1] = n0;
+      TcSeg sg{};
+      sg.amap = 0;
+      sg.bmap = 2;
+      sg.nk = (int)(Kp / 64);
+      sg.ac[1] = m0;
+      sg.bc[1] = n0;
+      segs.push_back(sg);
       items.push_back(it);
     }
-  void *ditems = nullptr;
+  void *ditems = nullptr, *dsegs = nullptr;
   if (cudaMalloc(&ditems, sizeof(TcItem) * items.size()) != cudaSuccess)
     return fail(MLCC3_ERR_OOM, "cudaMalloc");
   mem.push_back(ditems);
+  if (cudaMalloc(&dsegs, sizeof(TcSeg) * segs.size()) != cudaSuccess)
+    return fail(MLCC3_ERR_OOM, "cudaMalloc");
+  mem.push_back(dsegs);
   cudaMemcpy(ditems, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(dsegs, segs.data(), sizeof(TcSeg) * segs.size(), cudaMemcpyHostToDevice);
   TcEpi epi{};
   epi.out = C;
   epi.mode = 3;
@@ -153,8 +161,8 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
   epi.lim2 = M;
   epi.nlim = N;
   epi.alpha = 1.0f;
-  cudaError_t e = launch_tc_gemm(BN, maps, static_cast<TcItem *>(ditems), (int)items.size(), epi,
-                                 status, st);
+  cudaError_t e = launch_tc_gemm(BN, maps, static_cast<TcItem *>(ditems),
+                                 static_cast<TcSeg *>(dsegs), (int)items.size(), epi, status, st);
   if (e != cudaSuccess) return fail(MLCC3_ERR_CUDA, std::string("tc_gemm: ") + cudaGetErrorString(e));
   int hst = 0;
   e = cudaMemcpy(&hst, status, sizeof(int), cudaMemcpyDeviceToHost);
