@@ -233,7 +233,15 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     const int lg = warp & 3;
     const int row = lg * 32 + lane;
-    const int r1 = it.r1_0 + row / epi.R2, r2 = it.r2_0 + row % epi.R2;
+    int r1, r2;
+    if (epi.linear) {
+      const int m = it.r2_0 + row;
+      r1 = m / epi.R2;
+      r2 = m % epi.R2;
+    } else {
+      r1 = it.r1_0 + row / epi.R2;
+      r2 = it.r2_0 + row % epi.R2;
+    }
     const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
     const long long base = it.out_off + (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
 #pragma unroll 1

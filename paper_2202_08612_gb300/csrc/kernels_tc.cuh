@@ -43,6 +43,7 @@ struct TcEpi {
   void *out;
   int mode;
   int R2;
+  int linear;   // 1: tile rows are a flattened index m = r2_0 + r, split as (m / R2, m % R2)
   long long s1, s2, sn;
   int lim1, lim2, nlim;
   float alpha;

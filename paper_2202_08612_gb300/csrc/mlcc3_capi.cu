@@ -482,6 +482,9 @@ void split_gt(mlcc3_ctx *c, const std::string &key, const double *G);
 mlcc3_ctx::SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const double *G);
 mlcc3_ctx::SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk);
 void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
+void tc_integrals(mlcc3_ctx *c);
+bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
+                const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2);
 
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
@@ -563,7 +566,7 @@ void transpose_tl(mlcc3_ctx *c, const double *X, double *T) {
 
 // ---- split-precision tensor-core path (MLCC3_SPLIT_BF16X3) ----
 using SplitOp = mlcc3_ctx::SplitOp;
-enum class Box { Pair, Row };
+enum class Box { Pair, Row, Flat };
 
 // Items (output tiles) and their K segments of one tensor-core launch.
 struct TcPlan {
@@ -636,11 +639,12 @@ void tc_launch(mlcc3_ctx *c, int BN, const TcMaps &maps, const TcDev &d, const T
 }
 
 TcEpi make_epi(void *out, int mode, int R2, long long s1, long long s2, long long sn, long long lim1,
-               long long lim2, long long nlim, double alpha) {
+               long long lim2, long long nlim, double alpha, int linear = 0) {
   TcEpi e;
   e.out = out;
   e.mode = mode;
   e.R2 = R2;
+  e.linear = linear;
   e.s1 = s1;
   e.s2 = s2;
   e.sn = sn;
@@ -674,8 +678,17 @@ SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, lon
     bx[1] = rowbox ? rowbox : (unsigned)tc_tile_width(c->nv);
     bx[2] = 1;
   }
+  unsigned long long fdims[4] = {dims[0], (unsigned long long)(D0 * D1 * D2), 1ULL, 1ULL};
+  unsigned long long fstr[3] = {str[0], str[0] * fdims[1], str[0] * fdims[1]};
+  const unsigned long long *md = dims, *ms = str;
+  if (box == Box::Flat) {  // rows = the flattened (D0, D1, D2) index
+    bx[1] = rowbox ? rowbox : 128;
+    bx[2] = 1;
+    md = fdims;
+    ms = fstr;
+  }
   std::string err;
-  if (!encode_map(&op.mhi, op.hi, dims, str, bx, &err) || !encode_map(&op.mlo, op.lo, dims, str, bx, &err))
+  if (!encode_map(&op.mhi, op.hi, md, ms, bx, &err) || !encode_map(&op.mlo, op.lo, md, ms, bx, &err))
     throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
   return op;
 }
@@ -1085,6 +1098,98 @@ void tc_back_L(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
           b.cL, Zb);
 }
 
+// ---- Cholesky-index contractions on the tensor cores ----
+// out[w][k][c][n] (strides Sw, Sk, Sc, 1) += alpha sum_J sum_terms A_t[(k,c)][J] B_t[w][n][J]
+// rows (k,c) flattened (128-row tiles of a Flat split), columns n (tile BN of nN),
+// one item per (w, row tile, column tile); every term is one K segment (K = N_J).
+struct CholTerm {
+  const SplitOp *A;   // [(k,c)][J], Flat box of 128 rows
+  const SplitOp *B;   // [w][n][J], Row box of BN rows (map dims (J, n, w, 1))
+};
+void tc_chol(mlcc3_ctx *c, const std::vector<CholTerm> &terms, long long nW, long long nN,
+             long long Sw, long long Sk, long long Sc, double alpha, int mode, double *out,
+             const std::string &key) {
+  S s(c);
+  const long long M = s.no * s.nv;
+  if (M == 0 || nN == 0 || nW == 0) return;
+  if (terms.size() * 4 > (size_t)kTcMaps) throw Error{MLCC3_ERR_ARG, "too many Cholesky terms"};
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (size_t t = 0; t < terms.size(); ++t) {
+    maps.m[4 * t] = terms[t].A->mhi;
+    maps.m[4 * t + 1] = terms[t].A->mlo;
+    maps.m[4 * t + 2] = terms[t].B->mhi;
+    maps.m[4 * t + 3] = terms[t].B->mlo;
+  }
+  const int BN = tc_tile_width(nN);
+  const long long ntM = (M + 127) / 128, ntN = (nN + BN - 1) / BN;
+  const int nk = (int)((s.NJ + 63) / 64);
+  TcDev dv = tc_plan(c, "tcJ:" + key + ":" + std::to_string(terms.size()), [&](TcPlan &pl) {
+    for (long long w = 0; w < nW; ++w)
+      for (long long tm = 0; tm < ntM; ++tm)
+        for (long long tn = 0; tn < ntN; ++tn) {
+          pl.tile(0, (int)(128 * tm), (int)(BN * tn), w * Sw);
+          for (size_t t = 0; t < terms.size(); ++t)
+            pl.seg((int)(4 * t), (int)(4 * t + 2), nk, (int)(128 * tm), 0, 0, (int)(BN * tn),
+                   (int)w, 0);
+        }
+  });
+  TcEpi epi = make_epi(out, mode, (int)s.nv, Sk, Sc, 1, s.no, s.nv, nN, alpha, 1);
+  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)M * (double)nN * (double)nW * (double)s.NJ *
+                                      (double)terms.size());
+}
+
+// Split copies over the Cholesky index (K = J, stride lJ = n_mo^2 in Lt-like arrays).
+// rows (k,c) of X[J][r0 + c][k] (row offset r0, c stride cs, k stride ks), Flat 128-row box
+SplitOp &split_kc(mlcc3_ctx *c, const std::string &key, const double *X, long long ks, long long cs,
+                  long long Js) {
+  S s(c);
+  return make_split(c, key, X, 1, s.no, s.nv, s.NJ, 0, ks, cs, Js, 1.0, Box::Flat, 128);
+}
+// rows (w, n) of X with strides (ws, ns), K = J (stride Js), Row box of BN rows
+SplitOp &split_wn(mlcc3_ctx *c, const std::string &key, const double *X, long long nW, long long nN,
+                  long long ws, long long ns, long long Js) {
+  S s(c);
+  return make_split(c, key, X, 1, nW, nN, s.NJ, 0, ws, ns, Js, 1.0, Box::Row,
+                    (unsigned)tc_tile_width(nN));
+}
+
+// Gv[k][b][c][D] = sum_J Lt[J][NO+c][k] Lt[J][NO+b][NO+D] and
+// Gb[k][b][c][D] = sum_J Lt[J][k][NO+c] Lt[J][NO+D][NO+b] on the tensor cores.
+void tc_integrals(mlcc3_ctx *c) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const double *Lt = c->Lt;
+  split_kc(c, "LvoT", Lt + NO * nmo, 1, nmo, s.lJ);
+  split_kc(c, "LovT", Lt + NO, nmo, 1, s.lJ);
+  split_wn(c, "LvVT", Lt + NO * nmo + NO, s.nv, s.NV, nmo, 1, s.lJ);
+  split_wn(c, "LVvT", Lt + NO * nmo + NO, s.nv, s.NV, 1, nmo, s.lJ);
+  split_wn(c, "LOoT", Lt, s.no, s.NO, 1, nmo, s.lJ);
+  tc_chol(c, {{&c->splits.at("LvoT"), &c->splits.at("LvVT")}}, s.nv, s.NV, s.gb, s.gk, s.gc, 1.0, 3,
+          c->Gv, "Gv");
+  tc_chol(c, {{&c->splits.at("LovT"), &c->splits.at("LVvT")}}, s.nv, s.NV, s.gb, s.gk, s.gc, 1.0, 3,
+          c->Gb, "Gb");
+}
+
+// Upsilon_bDck, Upsilon_Ljck, H1, H2 on the tensor cores (split mode).
+bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
+                const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2) {
+  if (!split_mode(c)) return false;
+  S s(c);
+  const SplitOp &rvV = split_wn(c, "LRvVT", LRvV, s.nv, s.NV, s.NV, 1, s.nv * s.NV);
+  const SplitOp &rvo = split_kc(c, "LRvoT", LRvo, 1, s.no, s.nv * s.no);
+  const SplitOp &rOo = split_wn(c, "LROoT", LROo, s.no, s.NO, 1, s.no, s.NO * s.no);
+  const SplitOp &pa = split_wn(c, "PAT", PA, s.no, s.NO, s.NO, 1, s.no * s.NO);
+  const SplitOp &pb = split_wn(c, "PBT", PB, s.nv, s.NV, s.NV, 1, s.nv * s.NV);
+  const SplitOp &vo = c->splits.at("LvoT"), &ov = c->splits.at("LovT");
+  const SplitOp &vV = c->splits.at("LvVT"), &Oo = c->splits.at("LOoT");
+  tc_chol(c, {{&vo, &rvV}, {&rvo, &vV}}, s.nv, s.NV, s.gb, s.gk, s.gc, 1.0, 3, Uv, "Uv");
+  tc_chol(c, {{&vo, &rOo}, {&rvo, &Oo}}, s.no, s.NO, s.oj, s.ok, s.oc, 1.0, 3, Uo, "Uo");
+  tc_chol(c, {{&ov, &pa}}, s.no, s.NO, s.oj, s.ok, s.oc, 1.0, 3, H1, "H1");
+  tc_chol(c, {{&ov, &pb}}, s.nv, s.NV, s.gb, s.gk, s.gc, -1.0, 3, H2, "H2");
+  return true;
+}
+
 // tau3 terms on the tensor cores: D (t, Gv), L (Tl, Go).
 std::vector<SplitTerm> tau_split_terms(mlcc3_ctx *c) {
   return {SplitTerm{true, &c->splits.at("Gv:P"), &c->splits.at("Gv:S"), &c->splits.at("t:B")},
@@ -1165,6 +1270,13 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
   // LROo[J][L][j] = sum_E Lt[J][L][NO+E] R^E_j
   sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.NO; sh.N1 = s.no; sh.K1 = s.NV;
   c->bstc1(Lt + NO, R1, LROo, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.NO * s.no, s.no, 1, 0}), "ups4");
+  // PA[J][j][L] = sum_D Lt[J][j][NO+D] R^D_L, PB[J][b][D] = sum_L Lt[J][L][NO+b] R^D_L
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
+  c->bstc1(Lt + NO, R1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "ups9");
+  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.NV; sh.K1 = s.NO;
+  c->bstc1(Lt + NO, R1, PB, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 1, nmo, 0, 0}, {1, 0, 0, NO, 0}, {s.nv * s.NV, s.NV, 1, 0}), "ups11");
+  fock_ov(c, R1, u.Ukc, "ups");
+  if (tc_upsilon(c, LRvV, LRvo, LROo, PA, PB, u.Uv, u.Uo, u.H1, u.H2)) return u;
   // Uv[k][b][c][D] = sum_J (LRvV[J][b][D] Lt[J][NO+c][k] + Lt[J][NO+b][NO+D] LRvo[J][c][k])
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
   c->bstc1(Lt + NO * nmo, LRvV, u.Uv, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.nv * s.NV, 0, 0, s.NV, 1}, {s.gk, s.gc, s.gb, 1}), "ups5");
@@ -1173,16 +1285,10 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
   c->bstc1(Lt + NO * nmo, LROo, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.NO * s.no, 0, 0, 1, s.no}, {s.ok, s.oc, s.oj, 1}), "ups7");
   c->bstc1(LRvo, Lt, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, s.no, s.nv * s.no, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.ok, s.oc, s.oj, 1}), "ups8");
-  // Upsilon_kc
-  fock_ov(c, R1, u.Ukc, "ups");
-  // H1[j][k][c][L] = sum_J PA[J][j][L] Lt[J][k][NO+c], PA[J][j][L] = sum_D Lt[J][j][NO+D] R^D_L
-  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
-  c->bstc1(Lt + NO, R1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "ups9");
+  // H1[j][k][c][L] = sum_J PA[J][j][L] Lt[J][k][NO+c]
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
   c->bstc1(Lt + NO, PA, u.H1, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.no * s.NO, 0, 0, s.NO, 1}, {s.ok, s.oc, s.oj, 1}), "ups10");
-  // H2[k][b][c][D] = -sum_J PB[J][b][D] Lt[J][k][NO+c], PB[J][b][D] = sum_L Lt[J][L][NO+b] R^D_L
-  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.NV; sh.K1 = s.NO;
-  c->bstc1(Lt + NO, R1, PB, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 1, nmo, 0, 0}, {1, 0, 0, NO, 0}, {s.nv * s.NV, s.NV, 1, 0}), "ups11");
+  // H2[k][b][c][D] = -sum_J PB[J][b][D] Lt[J][k][NO+c]
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
   c->bstc1(Lt + NO, PB, u.H2, sh, -1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.nv * s.NV, 0, 0, s.NV, 1}, {s.gk, s.gc, s.gb, 1}), "ups12");
   return u;
@@ -1245,9 +1351,13 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   sh = Shape{};
   sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.nv; sh.N2 = s.NV; sh.K1 = s.NJ;
   // Gv[k][b][c][D] = g_bDck: A(k,c;J) = Lt[J][NO+c][k], B(J;b,D) = Lt[J][NO+b][NO+D]
+  if (split_mode(c)) {
+    tc_integrals(c);  // Gv, Gb on the tensor cores
+  } else {
   c->bstc1(Lt + NO * nmo, Lt + NO * nmo + NO, c->Gv, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.gk, s.gc, s.gb, 1}), "Gv");
   // Gb[k][b][c][D] = g_Dbkc: A(k,c;J) = Lt[J][k][NO+c], B(J;b,D) = Lt[J][NO+D][NO+b]
   c->bstc1(Lt + NO, Lt + NO * nmo + NO, c->Gb, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.gk, s.gc, s.gb, 1}), "Gb");
+  }
   sh = Shape{};
   sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = NO; sh.K1 = s.NJ;
   // Go[j][k][c][L] = g_Ljck: A(k,c;J) = Lt[J][NO+c][k], B(J;j,L) = Lt[J][L][j]
