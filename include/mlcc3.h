@@ -125,6 +125,17 @@ int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
 int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
                               const double *Dm0, const double *mu, double *f);
 
+/* Tuning parameters of a context (no counterpart in the paper; results stay
+ * within the precision mode's error bounds for every accepted value):
+ *   "tc_kcap"  longest FP32 accumulation chain of the split-precision tensor
+ *              core kernel, in 64-wide K blocks, for the contractions whose
+ *              partial results are summed in FP64 (back-contractions,
+ *              densities, Cholesky-index builds); 0 = unlimited.  The tensor
+ *              cores accumulate with truncation, so the error of a chain
+ *              grows with its length.  Default 16 (K = 1024).  Range 0..4096.
+ * Returns MLCC3_ERR_ARG for an unknown name or a value out of range. */
+int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
+
 /* Triples residual without allocating (no counterpart in the paper).
  * Some callers cannot allocate device memory at the moment they call: code
  * that runs while a stream is being captured into a CUDA graph, or a loop

@@ -26,7 +26,7 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
            "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
            "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
-           "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm")
+           "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param")
 
 
 class MLCC3Error(RuntimeError):
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_debug_nbatches.restype = ctypes.c_longlong
     lib.mlcc3_debug_profile.argtypes = [P, I]
     lib.mlcc3_debug_tc_gemm.argtypes = [P, P, P, I, I, I]
+    lib.mlcc3_set_param.argtypes = [P, ctypes.c_char_p, ctypes.c_longlong]
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -172,6 +173,10 @@ class Context:
         out = np.empty(n, dtype=np.float64)
         self._check(self.lib.mlcc3_debug_fetch(self.h, name.encode(), out.ctypes.data, n))
         return out
+
+    def set_param(self, name: str, value: int):
+        """mlcc3_set_param (tuning knobs such as "tc_kcap")."""
+        self._check(self.lib.mlcc3_set_param(self.h, name.encode(), int(value)))
 
     def profile(self, enable: bool):
         """Clear the launch counters; with enable, time every launch with CUDA events."""

@@ -61,6 +61,9 @@ struct mlcc3_ctx {
   std::vector<uint8_t> core;
   bool built = false;
   bool tau_valid = false;   // tau3 / its contravariant blocks match the current build
+  // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
+  // blocks, for contractions whose results are summed in FP64 (see tc_plan)
+  int tc_kcap = 16;
 
   // persistent device arrays (FP64)
   double *eps = nullptr, *t1 = nullptr, *Lt = nullptr, *t2c = nullptr, *t2x = nullptr;

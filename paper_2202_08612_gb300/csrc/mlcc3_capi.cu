@@ -614,14 +614,56 @@ void *upload_cached(mlcc3_ctx *c, const std::string &key, const void *data, size
   return p;
 }
 
-// The plan of `key`, built once by `build` and kept on the device.
-TcDev tc_plan(mlcc3_ctx *c, const std::string &key, const std::function<void(TcPlan &)> &build) {
+// Cut every item whose K segments add up to more than `cap` 64-wide blocks into
+// several items of at most `cap` blocks (a segment may be split at a block
+// boundary by offsetting its K coordinates).  The tensor cores accumulate in
+// FP32 with truncation, so the error of one accumulation chain grows with its
+// length; the pieces are summed in FP64 by the atomic epilogue.
+void cap_chains(TcPlan &pl, int cap) {
+  if (cap <= 0) return;
+  std::vector<TcItem> items;
+  std::vector<TcSeg> segs;
+  for (const TcItem &it : pl.items) {
+    int used = cap;
+    for (int q = 0; q < it.seg_count; ++q) {
+      const TcSeg g = pl.segs[it.seg_begin + q];
+      for (int k0 = 0; k0 < g.nk;) {
+        if (used == cap) {
+          TcItem n = it;
+          n.seg_begin = (int)segs.size();
+          n.seg_count = 0;
+          items.push_back(n);
+          used = 0;
+        }
+        const int take = std::min(cap - used, g.nk - k0);
+        TcSeg h = g;
+        h.ac[0] = g.ac[0] + 64 * k0;
+        h.bc[0] = g.bc[0] + 64 * k0;
+        h.nk = take;
+        segs.push_back(h);
+        items.back().seg_count += 1;
+        used += take;
+        k0 += take;
+      }
+    }
+  }
+  pl.items.swap(items);
+  pl.segs.swap(segs);
+}
+
+// The plan of `key`, built once by `build` and kept on the device.  `cap` > 0
+// limits the accumulation chain of every item (cap_chains); only plans whose
+// epilogue adds atomically in FP64 may pass it.
+TcDev tc_plan(mlcc3_ctx *c, const std::string &key0, const std::function<void(TcPlan &)> &build,
+              int cap = 0) {
+  const std::string key = key0 + (cap > 0 ? ":cap" + std::to_string(cap) : std::string());
   auto it = c->items.find(key + ":items");
   if (it != c->items.end())
     return TcDev{static_cast<const TcItem *>(it->second.first),
                  static_cast<const TcSeg *>(c->items.at(key + ":segs").first), it->second.second};
   TcPlan pl;
   build(pl);
+  cap_chains(pl, cap);
   void *si = upload_cached(c, key + ":items", pl.items.data(), pl.items.size() * sizeof(TcItem));
   void *ss = upload_cached(c, key + ":segs", pl.segs.data(), pl.segs.size() * sizeof(TcSeg));
   c->items[key + ":items"].second = (int)pl.items.size();
@@ -908,7 +950,7 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
         pl.seg(o.sp[1] < o.sp[2] ? 0 : 2, 4 + 2 * o.sp[0], nk, (int)(128 * t), 0, o.r, 0, 0,
                (int)(o.off / s.nv3));
       }
-  });
+  }, c->tc_kcap);
   TcEpi epi = make_epi(Zb, 2, 128, 0, 1, s.ba, 1, s.NV, s.nv, b.cD);
   tc_launch(c, (int)BN, maps, dv, epi,
             2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size());
@@ -978,7 +1020,7 @@ void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const Split
               }
               pl.drop_empty_last();
             }
-    });
+    }, c->tc_kcap);
     // rows of R are (smaller, larger) canonical positions: the view pair in
     // order (cls 0) or swapped (cls 1)
     TcEpi epi = make_epi(out, 2, 16, cls == 0 ? Sp1 : Sp2, cls == 0 ? Sp2 : Sp1, Sn, s.nv, s.nv,
@@ -1027,7 +1069,7 @@ void tc_xt(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp
             }
             pl.drop_empty_last();
           }
-  });
+  }, c->tc_kcap);
   TcEpi epi = make_epi(out, 2, 128, 0, Srow, 1, 1, s.nv, nN, coef);
   tc_launch(c, BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
 }
@@ -1063,7 +1105,7 @@ void tc_vv(mlcc3_ctx *c, const double *X, const std::string &xkey, const double 
           pl.seg(2 * o.sp[2], 6 + 2 * o.sp[2], nk, (int)(128 * tm), 0, u, 0, 0, u);
         }
       }
-  });
+  }, c->tc_kcap);
   TcEpi epi = make_epi(out, 2, 128, 0, ld, 1, 1, s.nv, s.nv, alpha);
   tc_launch(c, (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)ords.size());
 }
@@ -1124,6 +1166,13 @@ void tc_chol(mlcc3_ctx *c, const std::vector<CholTerm> &terms, long long nW, lon
   const int BN = tc_tile_width(nN);
   const long long ntM = (M + 127) / 128, ntN = (nN + BN - 1) / BN;
   const int nk = (int)((s.NJ + 63) / 64);
+  // one accumulation chain per tile when it is short enough, else pieces
+  // summed in FP64 into the zeroed output
+  const bool pieces = c->tc_kcap > 0 && nk * (int)terms.size() > c->tc_kcap;
+  if (pieces) {
+    if (mode == 3) c->zero(out, (size_t)((nW - 1) * Sw + (s.no - 1) * Sk + (s.nv - 1) * Sc + nN));
+    mode = 2;
+  }
   TcDev dv = tc_plan(c, "tcJ:" + key + ":" + std::to_string(terms.size()), [&](TcPlan &pl) {
     for (long long w = 0; w < nW; ++w)
       for (long long tm = 0; tm < ntM; ++tm)
@@ -1133,7 +1182,7 @@ void tc_chol(mlcc3_ctx *c, const std::vector<CholTerm> &terms, long long nW, lon
             pl.seg((int)(4 * t), (int)(4 * t + 2), nk, (int)(128 * tm), 0, 0, (int)(BN * tn),
                    (int)w, 0);
         }
-  });
+  }, pieces ? c->tc_kcap : 0);
   TcEpi epi = make_epi(out, mode, (int)s.nv, Sk, Sc, 1, s.no, s.nv, nN, alpha, 1);
   tc_launch(c, BN, maps, dv, epi, 2.0 * (double)M * (double)nN * (double)nW * (double)s.NJ *
                                       (double)terms.size());
@@ -2167,6 +2216,19 @@ extern "C" int mlcc3_debug_fetch(mlcc3_ctx *c, const char *name, double *host, s
     check_cuda(cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                "fetch");
     check_cuda(cudaStreamSynchronize(c->stream), "fetch sync");
+  });
+}
+
+extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) {
+  return guarded([&] {
+    if (!c || !name) throw Error{MLCC3_ERR_ARG, "null argument"};
+    const std::string n(name);
+    if (n == "tc_kcap") {
+      if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, "tc_kcap out of range 0..4096"};
+      c->tc_kcap = (int)value;
+    } else {
+      throw Error{MLCC3_ERR_ARG, "unknown parameter " + n};
+    }
   });
 }
 

@@ -11,7 +11,14 @@ the shapes below stand in for them:
 
 * orbital energies: occupied U[-1.5, -0.3], virtual U[0.1, 3.0] Hartree;
   optionally occupied orbital 0 is a core orbital at -10 Hartree;
-* Cholesky vectors  L^J_pq = L^J_qp ~ N(0, 0.05^2), (pq|rs) = sum_J L^J_pq L^J_rs;
+* Cholesky vectors  L^J_pq = L^J_qp ~ N(0, sigma^2), (pq|rs) = sum_J L^J_pq L^J_rs,
+  sigma = 0.05.  Optional molecule-scaled variant (``t2_norm``): sigma lowered
+  so that the active doubles block has Frobenius norm at most ``t2_norm``.
+  Independent Gaussian vectors have no locality, so at a fixed sigma the
+  correlation grows without bound with the orbital counts (at N_O=20, N_V=200,
+  N_J=600 the MP2-like amplitudes reach 1.7 and the triples corrections swamp
+  the singles part of the transition moments), while real closed-shell
+  molecules have doubles norms of a few tenths;
 * t1 ~ N(0, 0.01^2);
 * t2 MP2-like, t^{AB}_{IJ} = (AI|BJ) / (eps_I + eps_J - eps_A - eps_B);
 * trial vectors R ~ N(0, 1) on unique elements, scaled to a singles weight
@@ -105,7 +112,7 @@ def symmetrize_block(d: Dims, x: np.ndarray) -> np.ndarray:
     return x
 
 
-def make_system(NO, NV, no, nv, NJ, seed=DEFAULT_SEED, core=False) -> System:
+def make_system(NO, NV, no, nv, NJ, seed=DEFAULT_SEED, core=False, t2_norm=None) -> System:
     d = Dims(NO, NV, no, nv, NJ)
     nmo = d.n_mo
     r = _rng(seed, 1)
@@ -128,6 +135,13 @@ def make_system(NO, NV, no, nv, NJ, seed=DEFAULT_SEED, core=False) -> System:
     # t2x[i][a][L][D] = t^{aD}_{Li} = (a L | D i) / (e_L + e_i - e_a - e_D)
     num = np.einsum('JaL,JDi->iaLD', Lvo[:, :nv, :], Lvo[:, :, :no], optimize=True)
     t2x = num / den
+    # amplitudes are quadratic in the Cholesky scale: cap the doubles norm
+    nrm = float(np.sqrt(np.sum(t2c * t2c)))
+    if t2_norm is not None and nrm > t2_norm:
+        f = t2_norm / nrm
+        chol *= np.sqrt(f)
+        t2c *= f
+        t2x *= f
     core_mask = None
     if core:
         core_mask = np.zeros(NO, dtype=np.uint8)

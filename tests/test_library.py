@@ -49,6 +49,7 @@ def test_argument_errors_without_gpu(lib):
     assert L.mlcc3_create(None, ctypes.byref(ok), 0, None) == -1
     assert L.mlcc3_triples_omega(None, None, None) == -1
     assert L.mlcc3_debug_nbatches(None) == -1
+    assert L.mlcc3_set_param(None, b"tc_kcap", 8) == -1
 
 
 def test_ptr_marshalling():
