@@ -133,6 +133,11 @@ int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
  *              densities, Cholesky-index builds); 0 = unlimited.  The tensor
  *              cores accumulate with truncation, so the error of a chain
  *              grows with its length.  Default 16 (K = 1024).  Range 0..4096.
+ *   "chunk_blocks"  most unique batches whose triples blocks (n_v^3 each) the
+ *              context holds on the device at once; larger systems are swept
+ *              in chunks (the densities by ranges of occupied indices, which
+ *              rebuilds the blocks a range shares with others).  0 (default)
+ *              sizes the chunks from the free device memory at create.
  * Returns MLCC3_ERR_ARG for an unknown name or a value out of range. */
 int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
 

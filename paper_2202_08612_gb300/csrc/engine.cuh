@@ -50,6 +50,20 @@ struct Ord {
   int sp[3];          // canonical positions of x1, x2, x3
 };
 
+// The unique batches held on the device at one time.  Block offsets (TripItem
+// off, Ord off) are local to the chunk's arrays of nb * n_v^3 elements.
+struct Chunk {
+  std::string key;              // suffix of every cache key built for this chunk
+  long long nb = 0;             // blocks held
+  std::vector<TripItem> bs;     // batches built
+  std::vector<TripItem> bs_cvs; // those of them with a core index
+  std::vector<Ord> own;         // orderings of the batches this chunk owns (each batch
+  std::vector<Ord> own_cvs;     //   is owned by exactly one chunk); ... with a core index
+  std::vector<Ord> held;        // orderings of every held block
+  int p0 = 0, p1 = 0;           // terms that pair blocks of different batches take the
+                                // ordered views whose leading occupied index is in [p0, p1)
+};
+
 }  // namespace mlcc3
 
 struct mlcc3_ctx {
@@ -64,6 +78,14 @@ struct mlcc3_ctx {
   // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)
   int tc_kcap = 16;
+  // batch chunking: at most chunk_blocks blocks held per chunk (0 = sized from
+  // the device memory); parts / parts_cvs partition all / the core batches,
+  // groups cover all batches by occupied-index ranges (densities)
+  long long chunk_blocks = 0;
+  int chunk_gen = 0;
+  std::vector<mlcc3::Chunk> parts, parts_cvs, groups;
+  long long chunk_nb = 0;       // blocks of the chunk being processed
+  std::string tau_key;          // chunk whose tau / contravariant tau the buffers hold
 
   // persistent device arrays (FP64)
   double *eps = nullptr, *t1 = nullptr, *Lt = nullptr, *t2c = nullptr, *t2x = nullptr;

@@ -546,12 +546,12 @@ __global__ void __launch_bounds__(256) pair_dots_kernel(const double *__restrict
                                                         const long long *__restrict__ voff,
                                                         const int *__restrict__ vstr,
                                                         const char *__restrict__ vhave, int no, int nv,
-                                                        double *__restrict__ out, long long ldo, int kl,
-                                                        double alpha) {
+                                                        int p0, double *__restrict__ out, long long ldo,
+                                                        int kl, double alpha) {
   extern __shared__ double sm[];
   double *xs = sm;                  // [no][256]
   double *ys = sm + (size_t)no * 256;  // [no][256]
-  const int i = blockIdx.y / no, j = blockIdx.y % no;
+  const int i = p0 + (int)blockIdx.y / no, j = (int)blockIdx.y % no;
   const int nv3 = nv * nv * nv;
   const int r = blockIdx.x * 256 + threadIdx.x;
   const int a = r / (nv * nv), b = (r / nv) % nv, c = r % nv;

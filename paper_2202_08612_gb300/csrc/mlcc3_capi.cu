@@ -31,7 +31,7 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
 __global__ void pair_dots_kernel(const double *, const double *, const long long *, const int *,
-                                 const char *, int, int, double *, long long, int, double);
+                                 const char *, int, int, int, double *, long long, int, double);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, double *, int *);
@@ -302,6 +302,35 @@ struct S {
   size_t gosz() const { return (size_t)(no * no * nv * NO); }
 };
 
+// Distinct ordered views (p,q,r) of the batches in `bs`, with the strides of
+// the view's virtual indices inside the canonical block.
+std::vector<Ord> ords_of(const mlcc3_ctx *c, const std::vector<TripItem> &bs) {
+  std::vector<Ord> v;
+  const long long cs[3] = {c->nv * c->nv, c->nv, 1};
+  for (size_t u = 0; u < bs.size(); ++u) {
+    const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
+    std::set<std::tuple<int, int, int>> seen;
+    for (int sg = 0; sg < 6; ++sg) {
+      int p = I[kPermH[sg][0]], q = I[kPermH[sg][1]], r = I[kPermH[sg][2]];
+      if (!seen.insert({p, q, r}).second) continue;
+      Ord o;
+      o.u = (int)u;
+      o.p = p;
+      o.q = q;
+      o.r = r;
+      o.off = bs[u].off;
+      for (int t = 0; t < 3; ++t) o.vs[t] = cs[kPermH[sg][t]];
+      for (int t = 0; t < 3; ++t) o.sp[t] = kPermH[sg][t];
+      v.push_back(o);
+    }
+  }
+  return v;
+}
+
+bool has_core(const mlcc3_ctx *c, const TripItem &t) {
+  return !c->core.empty() && (c->core[t.i] || c->core[t.j] || c->core[t.k]);
+}
+
 void make_batches(mlcc3_ctx *c) {
   c->batches.clear();
   c->batches_cvs.clear();
@@ -314,34 +343,91 @@ void make_batches(mlcc3_ctx *c) {
         t.off = (long long)c->batches.size() * nv3;
         c->batches.push_back(t);
       }
-  for (auto t : c->batches) {
-    bool core = !c->core.empty() && (c->core[t.i] || c->core[t.j] || c->core[t.k]);
-    if (core) c->batches_cvs.push_back(t);  // keeps the full-list block offset
-  }
-  auto ords_of = [&](const std::vector<TripItem> &bs) {
-    std::vector<Ord> v;
-    const long long cs[3] = {c->nv * c->nv, c->nv, 1};
-    for (size_t u = 0; u < bs.size(); ++u) {
-      const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
-      std::set<std::tuple<int, int, int>> seen;
-      for (int sg = 0; sg < 6; ++sg) {
-        int p = I[kPermH[sg][0]], q = I[kPermH[sg][1]], r = I[kPermH[sg][2]];
-        if (!seen.insert({p, q, r}).second) continue;
-        Ord o;
-        o.u = (int)u;
-        o.p = p;
-        o.q = q;
-        o.r = r;
-        o.off = bs[u].off;
-        for (int t = 0; t < 3; ++t) o.vs[t] = cs[kPermH[sg][t]];
-        for (int t = 0; t < 3; ++t) o.sp[t] = kPermH[sg][t];
-        v.push_back(o);
-      }
+  for (auto t : c->batches)
+    if (has_core(c, t)) c->batches_cvs.push_back(t);  // keeps the full-list block offset
+  c->ords = ords_of(c, c->batches);
+  c->ords_cvs = ords_of(c, c->batches_cvs);
+}
+
+// A chunk holding `held` (given in the global order), owning those whose
+// largest index lies in [p0, p1) (all of them for a partition chunk).
+Chunk make_chunk(const mlcc3_ctx *c, const std::vector<TripItem> &held, int p0, int p1,
+                 const std::string &key) {
+  const long long nv3 = c->nv * c->nv * c->nv;
+  Chunk ch;
+  ch.key = key;
+  ch.p0 = p0;
+  ch.p1 = p1;
+  ch.nb = (long long)held.size();
+  std::vector<TripItem> own, own_cvs;
+  for (size_t u = 0; u < held.size(); ++u) {
+    TripItem t = held[u];
+    t.off = (long long)u * nv3;
+    ch.bs.push_back(t);
+    const bool core = has_core(c, t);
+    if (core) ch.bs_cvs.push_back(t);
+    if (t.i >= p0 && t.i < p1) {
+      own.push_back(t);
+      if (core) own_cvs.push_back(t);
     }
-    return v;
+  }
+  ch.own = ords_of(c, own);
+  ch.own_cvs = ords_of(c, own_cvs);
+  ch.held = ords_of(c, ch.bs);
+  return ch;
+}
+
+// Split the unique batches into chunks of at most chunk_blocks blocks (or, when
+// it is 0, as many as fit in 55% of the device memory left free once the
+// context's persistent arrays exist: about 64 bytes per element for the
+// Jacobian passes and 96 for the densities, which hold more triples arrays
+// and their split copies).
+void make_chunks(mlcc3_ctx *c) {
+  c->chunk_gen += 1;
+  c->tau_key.clear();
+  c->parts.clear();
+  c->parts_cvs.clear();
+  c->groups.clear();
+  const long long nv3 = std::max<long long>(1, c->nv * c->nv * c->nv);
+  long long part_max = c->chunk_blocks, group_max = c->chunk_blocks;
+  if (part_max <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)40 << 30;
+    const double budget = 0.55 * (double)fr;
+    part_max = std::max<long long>(1, (long long)(budget / (64.0 * (double)nv3)));
+    group_max = std::max<long long>(1, (long long)(budget / (96.0 * (double)nv3)));
+  }
+  const std::string g = "#" + std::to_string(c->chunk_gen);
+  auto partition = [&](const std::vector<TripItem> &list, const std::string &tag) {
+    std::vector<Chunk> out;
+    for (size_t a = 0; a < list.size() || (a == 0 && out.empty()); a += (size_t)part_max) {
+      const size_t b = std::min(list.size(), a + (size_t)part_max);
+      std::vector<TripItem> held(list.begin() + a, list.begin() + b);
+      out.push_back(make_chunk(c, held, 0, (int)c->no, g + tag + std::to_string(out.size())));
+      if (b >= list.size()) break;
+    }
+    return out;
   };
-  c->ords = ords_of(c->batches);
-  c->ords_cvs = ords_of(c->batches_cvs);
+  c->parts = partition(c->batches, "p");
+  c->parts_cvs = partition(c->batches_cvs, "c");
+  if ((long long)c->batches.size() <= group_max) {
+    c->groups = c->parts;  // one chunk: the same key shares the tau cache
+    return;
+  }
+  // occupied-index groups [p0, p1): hold every batch with an index in the range
+  auto held_of = [&](int p0, int p1) {
+    std::vector<TripItem> h;
+    for (auto &t : c->batches)
+      if ((t.i >= p0 && t.i < p1) || (t.j >= p0 && t.j < p1) || (t.k >= p0 && t.k < p1))
+        h.push_back(t);
+    return h;
+  };
+  for (int p0 = 0; p0 < (int)c->no;) {
+    int p1 = p0 + 1;
+    while (p1 < (int)c->no && (long long)held_of(p0, p1 + 1).size() <= group_max) ++p1;
+    c->groups.push_back(make_chunk(c, held_of(p0, p1), p0, p1, g + "g" + std::to_string(p0)));
+    p0 = p1;
+  }
 }
 
 void launch_1d(mlcc3_ctx *c, long long n, const char *what,
@@ -802,7 +888,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     maps.m[6 * t + 5] = st.amp->mlo;
   }
   const long long nb = (long long)bs.size();
-  float *W = static_cast<float *>(c->raw("tcW", sizeof(float) * (size_t)(c->batches.size() * s.nv3)));
+  float *W = static_cast<float *>(c->raw("tcW", sizeof(float) * (size_t)(c->chunk_nb * s.nv3)));
   const long long NVk = (s.NV + 63) / 64, NOk = (s.NO + 63) / 64;
   const long long nt1 = (s.nv + 7) / 8, nt2 = (s.nv + 15) / 16;
   const long long cs[3] = {s.nv * s.nv, s.nv, 1};
@@ -926,7 +1012,7 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
                const BackSet &b, double *Zb) {
   S s(c);
   if (ords.empty() || s.nv == 0) return;
-  const long long nb = (long long)c->batches.size();
+  const long long nb = c->chunk_nb;
   const unsigned BN = (unsigned)tc_tile_width(s.nv);
   // row = canonical position 0 / 1 / 2; K = the other two (ascending)
   make_split_k2(c, "XL0", X, nb, s.nv, s.nv, s.nv, s.nv3, s.nv * s.nv, s.nv, 1, BN);
@@ -962,7 +1048,7 @@ SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k,
   S s(c);
   const long long cs[3] = {s.nv * s.nv, s.nv, 1};
   const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
-  return make_split_k2(c, key, X, (long long)c->batches.size(), s.nv, s.nv, s.nv, s.nv3, cs[k],
+  return make_split_k2(c, key, X, c->chunk_nb, s.nv, s.nv, s.nv, s.nv3, cs[k],
                        cs[a], cs[b], rows);
 }
 
@@ -971,7 +1057,7 @@ SplitOp &layout_R(mlcc3_ctx *c, const std::string &key, const double *X, int k) 
   S s(c);
   const long long cs[3] = {s.nv * s.nv, s.nv, 1};
   const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
-  return make_split(c, key, X, (long long)c->batches.size(), s.nv, s.nv, s.nv, s.nv3, cs[a], cs[b],
+  return make_split(c, key, X, c->chunk_nb, s.nv, s.nv, s.nv, s.nv3, cs[a], cs[b],
                     cs[k], 1.0, Box::Pair);
 }
 
@@ -1264,19 +1350,21 @@ void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const 
   triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out);
 }
 
-// tau and its contravariant form for all unique batches.
-void build_tau(mlcc3_ctx *c, double **tau, double **taut) {
+// tau and its contravariant form for the batches of chunk `ch` (kept until the
+// next integral build or until another chunk needs the buffers).
+void build_tau(mlcc3_ctx *c, const Chunk &ch, double **tau, double **taut) {
   S s(c);
-  size_t nb = c->batches.size();
-  *tau = c->buf("tau", nb * s.nv3);
-  *taut = c->buf("taut", nb * s.nv3);
-  if (c->tau_valid) return;  // tau depends only on t2 and the integrals of the last build
+  c->chunk_nb = ch.nb;
+  *tau = c->buf("tau", (size_t)ch.nb * s.nv3);
+  *taut = c->buf("taut", (size_t)ch.nb * s.nv3);
+  if (c->tau_valid && c->tau_key == ch.key) return;
   c->tau_valid = true;
+  c->tau_key = ch.key;
   if (split_mode(c))
-    triples_split(c, tau_split_terms(c), {}, "batches", c->batches, 0.0, *tau);
+    triples_split(c, tau_split_terms(c), {}, "b" + ch.key, ch.bs, 0.0, *tau);
   else
-    triples(c, tau_terms(c), "batches", c->batches, 0.0, *tau);
-  contra3(c, *tau, *taut, (long long)nb);
+    triples(c, tau_terms(c), "b" + ch.key, ch.bs, 0.0, *tau);
+  contra3(c, *tau, *taut, ch.nb);
 }
 
 // Upsilon blocks for one trial vector (Eqs. ups_v, ups_o) and the rho tau-term
@@ -1428,8 +1516,6 @@ static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_ou
   S s(c);
   double *o1 = c->out(omega1_out, s.NV * s.NO, "omega1");
   double *o2 = c->out(omega2_out, s.blk(), "omega2");
-  double *tau, *taut;
-  build_tau(c, &tau, &taut);
   double *Zb = c->buf("Zb", s.blk());
   c->zero(Zb, s.blk());
   c->zero(o1, s.NV * s.NO);
@@ -1438,7 +1524,11 @@ static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_ou
   b.cF = 0.5; b.F = c->F;
   b.cL = -1.0; b.GL = c->Gx; b.gl_key = "Gx";
   b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
-  back_contract(c, taut, c->ords, "ords", b, o1, Zb);
+  for (const Chunk &ch : c->parts) {
+    double *tau, *taut;
+    build_tau(c, ch, &tau, &taut);
+    back_contract(c, taut, ch.own, "o" + ch.key, b, o1, Zb);
+  }
   finalize(c, Zb, o2, 0);
 }
 
@@ -1446,19 +1536,11 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
                               const double *R2_in, double *rho1_out, double *rho2_out) {
   S s(c);
   const bool cvs = !c->core.empty();
-  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
-  const std::vector<Ord> &os = cvs ? c->ords_cvs : c->ords;
-  const std::string bkey = cvs ? "batches_cvs" : "batches";
-  const std::string okey = cvs ? "ords_cvs" : "ords";
+  const std::vector<Chunk> &chunks = cvs ? c->parts_cvs : c->parts;
   const double *R1all = c->in(R1_in, (size_t)n_vec * s.NV * s.NO, "R1");
   const double *R2all = c->in(R2_in, (size_t)n_vec * s.blk(), "R2");
   double *rho1all = c->out(rho1_out, (size_t)n_vec * s.NV * s.NO, "rho1");
   double *rho2all = c->out(rho2_out, (size_t)n_vec * s.blk(), "rho2");
-  double *tau, *taut;
-  build_tau(c, &tau, &taut);
-  size_t nb = c->batches.size();
-  double *R3 = c->buf("R3", nb * s.nv3);
-  double *R3t = c->buf("R3t", nb * s.nv3);
   double *Rbar = c->buf("Rbar", s.blk());
   double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * s.NO);
   double *Zb = c->buf("Zb", s.blk());
@@ -1473,22 +1555,29 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     });
     transpose_tl(c, Rbar, Rbl);
     Ups u = build_upsilon(c, R1);
-    // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
-    right_triples(c, Rbar, Rbl, u, bkey, bs, omega[v], R3);
-    contra3(c, R3, R3t, (long long)nb);
     c->zero(Zb, s.blk());
     c->zero(rho1, s.NV * s.NO);
-    BackSet b;
-    b.cs = 0.5; b.Gs = c->Govov;
-    b.cF = 0.5; b.F = c->F;
-    b.cL = -1.0; b.GL = c->Gx; b.gl_key = "Gx";
-    b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
-    back_contract(c, R3t, os, okey, b, rho1, Zb);
-    BackSet bt;  // tau terms: 1/2 taut Upsilon_kc, -taut H1, +taut H2 (H2 carries the minus)
-    bt.cF = 0.5; bt.F = u.Ukc;
-    bt.cL = -1.0; bt.GL = u.H1; bt.gl_key = "H1"; bt.gl_convert = true;
-    bt.cD = 1.0; bt.GD = u.H2; bt.gd_key = "H2"; bt.gd_convert = true;
-    back_contract(c, taut, os, okey, bt, nullptr, Zb);
+    for (size_t q = 0; q < chunks.size(); ++q) {
+      const Chunk &ch = chunks[q];
+      double *tau, *taut;
+      build_tau(c, ch, &tau, &taut);
+      double *R3 = c->buf("R3", (size_t)ch.nb * s.nv3);
+      double *R3t = c->buf("R3t", (size_t)ch.nb * s.nv3);
+      // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
+      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, omega[v], R3);
+      contra3(c, R3, R3t, ch.nb);
+      BackSet b;
+      b.cs = 0.5; b.Gs = c->Govov;
+      b.cF = 0.5; b.F = c->F;
+      b.cL = -1.0; b.GL = c->Gx; b.gl_key = "Gx";
+      b.cD = 1.0; b.GD = c->Gb; b.gd_key = "Gb";
+      back_contract(c, R3t, ch.own, "o" + ch.key, b, rho1, Zb);
+      BackSet bt;  // tau terms: 1/2 taut Upsilon_kc, -taut H1, +taut H2 (H2 carries the minus)
+      bt.cF = 0.5; bt.F = u.Ukc;
+      bt.cL = -1.0; bt.GL = u.H1; bt.gl_key = "H1"; bt.gl_convert = q == 0;
+      bt.cD = 1.0; bt.GD = u.H2; bt.gd_key = "H2"; bt.gd_convert = q == 0;
+      back_contract(c, taut, ch.own, "o" + ch.key, bt, nullptr, Zb);
+    }
     finalize(c, Zb, rho2, 0);
   }
 }
@@ -1497,19 +1586,11 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
                              const double *L2_in, double *sig1_out, double *sig2_out) {
   S s(c);
   const bool cvs = !c->core.empty();
-  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
-  const std::vector<Ord> &os = cvs ? c->ords_cvs : c->ords;
-  const std::string bkey = cvs ? "batches_cvs" : "batches";
-  const std::string okey = cvs ? "ords_cvs" : "ords";
+  const std::vector<Chunk> &chunks = cvs ? c->parts_cvs : c->parts;
   const double *L1all = c->in(L1_in, (size_t)n_vec * s.NV * s.NO, "L1");
   const double *L2all = c->in(L2_in, (size_t)n_vec * s.blk(), "L2");
   double *sig1all = c->out(sig1_out, (size_t)n_vec * s.NV * s.NO, "sigma1");
   double *sig2all = c->out(sig2_out, (size_t)n_vec * s.blk(), "sigma2");
-  double *tau, *taut;
-  build_tau(c, &tau, &taut);
-  size_t nb = c->batches.size();
-  double *L3 = c->buf("L3", nb * s.nv3);
-  double *L3t = c->buf("L3t", nb * s.nv3);
   double *Lc = c->buf("Lc", s.blk());
   double *LcT = c->buf("LcT", s.no * s.nv * s.nv * s.NO);
   double *Sb = c->buf("Zb", s.blk());
@@ -1535,67 +1616,79 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV); });
     });
     transpose_tl(c, Lc, LcT);
-    // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
-    left_triples(c, "L", L1, Lc, LcT, bkey, bs, omega[v], L3);
-    contra3(c, L3, L3t, (long long)nb);
-    // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
     c->zero(Sb, s.blk());
-    BackSet b;
-    b.cL = -1.0; b.GL = c->Go; b.gl_key = "Go";
-    b.cD = 1.0; b.GD = c->Gv; b.gd_key = "Gv";
-    back_contract(c, L3t, os, okey, b, nullptr, Sb);
-    finalize(c, Sb, sig2, 1);
-    // singles intermediates
     for (double *p : {Y1, P2}) c->zero(p, s.gvsz());
     for (double *p : {Y2, P1}) c->zero(p, s.gosz());
     c->zero(Y3, s.no * s.nv);
-    int n = 0;
-    const BstcItem *it;
-    Shape sh;
+    const SplitOp *LcA = nullptr;
     if (split_mode(c)) {
-      // tensor cores: Y1/P2 (K = a, rows (b,c)), Y2/P1 (K = (a,b), rows c)
-      tc_pair(c, L3t, "X", c->splits.at("t:AT"), s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1, 1.0, Y1);
-      tc_pair(c, taut, "X", split_amp_T(c, "Lc:AT", Lc), s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1,
-              1.0, P2);
-      tc_xt(c, L3t, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, os, okey, 2, 0, s.oj,
-            s.ok, s.oc, 1.0, Y2);
+      LcA = &split_amp_T(c, "Lc:AT", Lc);
       split_tl_T(c, "LcT", LcT);
-      tc_xt(c, taut, "X", c->splits.at("LcT:T"), c->splits.at("LcT:Ts"), s.NO, os, okey, 2, 0, s.oj,
-            s.ok, s.oc, 1.0, P1);
-    } else {
-    // Y1[r][b][c][D] += sum_a Lt3_{pqr}[a][b][c] t2c[p][a][q][D]  (and P2 with taut, Lc)
-    it = c->dev_items(okey + ":y1", [&] {
-      std::vector<BstcItem> vv;
-      for (auto &o : os)
-        vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.gk,
-                             {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {s.ba, 0, 0, 1, 0}, {s.gb, s.gc, 1, 0}));
-      return vv;
-    }, &n);
-    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NV;
-    c->bstc(L3t, c->t2c, Y1, sh, 1.0, it, n, true, okey + ":y1");
-    c->bstc(taut, Lc, P2, sh, 1.0, it, n, true, okey + ":y1");
-    // Y2[q][r][c][L] += sum_{ab} Lt3_{pqr}[a][b][c] Tl[p][a][b][L]  (and P1 with taut, LcT)
-    it = c->dev_items(okey + ":y2", [&] {
-      std::vector<BstcItem> vv;
-      for (auto &o : os)
-        vv.push_back(mk_item(o.off, o.p * s.ti, o.q * s.oj + o.r * s.ok,
-                             {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
-      return vv;
-    }, &n);
-    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
-    c->bstc(L3t, c->Tl, Y2, sh, 1.0, it, n, true, okey + ":y2");
-    c->bstc(taut, LcT, P1, sh, 1.0, it, n, true, okey + ":y2");
     }
-    // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
-    it = c->dev_items(okey + ":y3", [&] {
-      std::vector<BstcItem> vv;
-      for (auto &o : os)
-        vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
-                             {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
-      return vv;
-    }, &n);
-    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
+    for (const Chunk &ch : chunks) {
+      double *tau, *taut;
+      build_tau(c, ch, &tau, &taut);
+      double *L3 = c->buf("L3", (size_t)ch.nb * s.nv3);
+      double *L3t = c->buf("L3t", (size_t)ch.nb * s.nv3);
+      const std::vector<Ord> &os = ch.own;
+      const std::string okey = "o" + ch.key;
+      // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
+      left_triples(c, "L", L1, Lc, LcT, "b" + ch.key, ch.bs, omega[v], L3);
+      contra3(c, L3, L3t, ch.nb);
+      // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
+      BackSet b;
+      b.cL = -1.0; b.GL = c->Go; b.gl_key = "Go";
+      b.cD = 1.0; b.GD = c->Gv; b.gd_key = "Gv";
+      back_contract(c, L3t, os, okey, b, nullptr, Sb);
+      // singles intermediates
+      int n = 0;
+      const BstcItem *it;
+      Shape sh;
+      if (split_mode(c)) {
+        // tensor cores: Y1/P2 (K = a, rows (b,c)), Y2/P1 (K = (a,b), rows c)
+        tc_pair(c, L3t, "X", c->splits.at("t:AT"), s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1, 1.0, Y1);
+        tc_pair(c, taut, "X", *LcA, s.NV, os, okey, 0, 2, s.gk, s.gb, s.gc, 1, 1.0, P2);
+        tc_xt(c, L3t, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, os, okey, 2, 0, s.oj,
+              s.ok, s.oc, 1.0, Y2);
+        tc_xt(c, taut, "X", c->splits.at("LcT:T"), c->splits.at("LcT:Ts"), s.NO, os, okey, 2, 0, s.oj,
+              s.ok, s.oc, 1.0, P1);
+      } else {
+        // Y1[r][b][c][D] += sum_a Lt3_{pqr}[a][b][c] t2c[p][a][q][D]  (and P2 with taut, Lc)
+        it = c->dev_items(okey + ":y1", [&] {
+          std::vector<BstcItem> vv;
+          for (auto &o : os)
+            vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.gk,
+                                 {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {s.ba, 0, 0, 1, 0}, {s.gb, s.gc, 1, 0}));
+          return vv;
+        }, &n);
+        sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv; sh.N1 = s.NV;
+        c->bstc(L3t, c->t2c, Y1, sh, 1.0, it, n, true, okey + ":y1");
+        c->bstc(taut, Lc, P2, sh, 1.0, it, n, true, okey + ":y1");
+        // Y2[q][r][c][L] += sum_{ab} Lt3_{pqr}[a][b][c] Tl[p][a][b][L]  (and P1 with taut, LcT)
+        it = c->dev_items(okey + ":y2", [&] {
+          std::vector<BstcItem> vv;
+          for (auto &o : os)
+            vv.push_back(mk_item(o.off, o.p * s.ti, o.q * s.oj + o.r * s.ok,
+                                 {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
+          return vv;
+        }, &n);
+        sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
+        c->bstc(L3t, c->Tl, Y2, sh, 1.0, it, n, true, okey + ":y2");
+        c->bstc(taut, LcT, P1, sh, 1.0, it, n, true, okey + ":y2");
+      }
+      // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
+      it = c->dev_items(okey + ":y3", [&] {
+        std::vector<BstcItem> vv;
+        for (auto &o : os)
+          vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
+                               {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
+        return vv;
+      }, &n);
+      sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+      c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
+    }
+    finalize(c, Sb, sig2, 1);
+    Shape sh;
     // --- singles through the Cholesky factors ---
     c->zero(sig1, s.NV * NO);
     for (double *p : {W, Z2, Z4, yv, Q, Q2}) (void)p;
@@ -1710,65 +1803,75 @@ struct ViewMap {
       have[x] = 1;
     }
   }
-  long long idx(long long p, long long q, long long r) const { return (p * n + q) * n + r; }
 };
 
 // out[k][l] (or [l][k]) += alpha sum_{ij} sum_{abc} X_{ijl}[abc] Y_{ijk}[abc]
-// over all ordered (i,j,k), (i,j,l) with stored blocks.
-void pair_dots(mlcc3_ctx *c, const ViewMap &vm, const double *X, const double *Y, double *out,
-               long long ldo, bool kl, double alpha, const std::string &key) {
+// over the ordered (i,j,k), (i,j,l) of the chunk's held blocks with i in
+// [p0, p1) (each i belongs to one chunk, so every pair is counted once).
+void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, double *out,
+               long long ldo, bool kl, double alpha) {
   S s(c);
   const long long n3 = s.no * s.no * s.no;
-  if (n3 == 0 || s.nv == 0) return;
-  // view tables on the device (built once)
-  void *voff = upload_cached(c, "pd:off", vm.off.data(), n3 * sizeof(long long));
-  std::vector<int> str(3 * n3);
-  for (long long x = 0; x < n3; ++x) {
-    str[3 * x] = (int)vm.s0[x];
-    str[3 * x + 1] = (int)vm.s1[x];
-    str[3 * x + 2] = (int)vm.s2[x];
+  if (n3 == 0 || s.nv == 0 || ch.p1 <= ch.p0) return;
+  const std::string key = "pd" + ch.key;
+  void *voff = nullptr, *vstr = nullptr, *vhave = nullptr;
+  if (c->items.find(key + ":off") == c->items.end()) {
+    ViewMap vm(ch.held, s.no);
+    std::vector<int> str(3 * n3);
+    for (long long x = 0; x < n3; ++x) {
+      str[3 * x] = (int)vm.s0[x];
+      str[3 * x + 1] = (int)vm.s1[x];
+      str[3 * x + 2] = (int)vm.s2[x];
+    }
+    upload_cached(c, key + ":off", vm.off.data(), n3 * sizeof(long long));
+    upload_cached(c, key + ":str", str.data(), str.size() * sizeof(int));
+    upload_cached(c, key + ":have", vm.have.data(), n3);
   }
-  void *vstr = upload_cached(c, "pd:str", str.data(), str.size() * sizeof(int));
-  void *vhave = upload_cached(c, "pd:have", vm.have.data(), n3);
+  voff = c->items.at(key + ":off").first;
+  vstr = c->items.at(key + ":str").first;
+  vhave = c->items.at(key + ":have").first;
   const size_t smem = 2 * (size_t)s.no * 256 * sizeof(double);
   check_cuda(cudaFuncSetAttribute(pair_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem), "pair_dots smem");
-  dim3 grid((unsigned)((s.nv3 + 255) / 256), (unsigned)(s.no * s.no));
-  c->launch("pair_dots_kernel", 2.0 * (double)(s.no * s.no) * (double)(s.no * s.no) * (double)s.nv3, [&] {
+  const long long np = ch.p1 - ch.p0;
+  dim3 grid((unsigned)((s.nv3 + 255) / 256), (unsigned)(np * s.no));
+  c->launch("pair_dots_kernel", 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3, [&] {
     pair_dots_kernel<<<grid, 256, smem, c->stream>>>(X, Y, static_cast<const long long *>(voff),
                                                      static_cast<const int *>(vstr),
                                                      static_cast<const char *>(vhave), (int)s.no,
-                                                     (int)s.nv, out, ldo, kl ? 1 : 0, alpha);
+                                                     (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
   });
-  (void)key;
 }
 
 // out[c][d] += alpha sum_{pqr} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
-void vv_block(mlcc3_ctx *c, const double *X, const double *Y, double *out, long long ldo,
-              double alpha) {
+void vv_block(mlcc3_ctx *c, const double *X, const double *Y, const std::vector<Ord> &os,
+              const std::string &okey, double *out, long long ldo, double alpha) {
   S s(c);
   int n = 0;
-  const BstcItem *it = c->dev_items("ords:vv:" + std::to_string(ldo), [&] {
+  const std::string key = okey + ":vv:" + std::to_string(ldo);
+  const BstcItem *it = c->dev_items(key, [&] {
     std::vector<BstcItem> v;
-    for (auto &o : c->ords)
+    for (auto &o : os)
       v.push_back(mk_item(o.off, o.off, 0, {o.vs[2], 0, o.vs[0], o.vs[1], 0},
                           {o.vs[0], o.vs[1], 0, o.vs[2], 0}, {ldo, 0, 1, 0}));
     return v;
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.N1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(X, Y, out, sh, alpha, it, n, true, "ords:vv:" + std::to_string(ldo));
+  c->bstc(X, Y, out, sh, alpha, it, n, true, key);
 }
 
 // out[r][c] (row stride ldo, col stride 1) += alpha sum_{ab} X_{pqr}[a][b][c] B[p][a][q][b]
 // with B in the active-pair block layout.
-void y3_like(mlcc3_ctx *c, const double *X, const double *B, double *out, long long ldo,
-             double alpha, const std::string &key) {
+void y3_like(mlcc3_ctx *c, const double *X, const double *B, const std::vector<Ord> &os,
+             const std::string &okey, double *out, long long ldo, double alpha,
+             const std::string &tag) {
   S s(c);
   int n = 0;
+  const std::string key = okey + ":" + tag;
   const BstcItem *it = c->dev_items(key, [&] {
     std::vector<BstcItem> v;
-    for (auto &o : c->ords)
+    for (auto &o : os)
       v.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * ldo,
                           {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
     return v;
@@ -1779,19 +1882,21 @@ void y3_like(mlcc3_ctx *c, const double *X, const double *B, double *out, long l
 }
 
 // V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
-void v_like(mlcc3_ctx *c, const double *X, const double *T, double *V) {
+void v_like(mlcc3_ctx *c, const double *X, const double *T, const std::vector<Ord> &os,
+            const std::string &okey, double *V) {
   S s(c);
   int n = 0;
-  const BstcItem *it = c->dev_items("ords:vlike", [&] {
+  const std::string key = okey + ":vlike";
+  const BstcItem *it = c->dev_items(key, [&] {
     std::vector<BstcItem> v;
-    for (auto &o : c->ords)
+    for (auto &o : os)
       v.push_back(mk_item(o.off, o.p * s.ti, o.q * s.oj + o.r * s.ok,
                           {o.vs[1], 0, o.vs[0], o.vs[2], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
     return v;
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = s.NO;
-  c->bstc(X, T, V, sh, 1.0, it, n, true, "ords:vlike");
+  c->bstc(X, T, V, sh, 1.0, it, n, true, key);
 }
 
 // D[L][NO+D] += alpha sum_{q,r,b} V[q][r][b][L] X[q][b][r][D]   (X in block layout)
@@ -1806,30 +1911,30 @@ void d_LD_from_v(mlcc3_ctx *c, const double *V, const double *X, double *D, doub
 }
 
 // Triples part of the left density from (contravariant left triples Xt3,
-// covariant-combined doubles Lc, tau, contravariant tau).
-void density_left_gpu(mlcc3_ctx *c, const ViewMap &vm, const double *Xt3, const double *Lc,
-                      const double *tau, const double *taut, double *D, const std::string &tag) {
+// covariant-combined doubles Lc, tau, contravariant tau), the chunk's share.
+void density_left_gpu(mlcc3_ctx *c, const Chunk &ch, const double *Xt3, const double *Lc,
+                      const double *tau, const double *taut, double *D) {
   S s(c);
   const long long nmo = s.nmo, NO = s.NO;
+  const std::string okey = "o" + ch.key;
   // D_kl -= 1/2 sum Xt_{ijl} tau_{ijk}
-  pair_dots(c, vm, Xt3, tau, D, nmo, true, -0.5, "pd:kl");
+  pair_dots(c, ch, Xt3, tau, D, nmo, true, -0.5);
   // D_ld += 1/2 sum Lc^{ab}_{ij} taut^{abd}_{ijl}
-  y3_like(c, taut, Lc, D + NO, nmo, 0.5, "ords:y3d");
+  y3_like(c, taut, Lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
   // D_LD -= sum Xt^{abc}_{ijk} t^{ac}_{iL} t^{bD}_{jk}
   double *V = c->buf("dV", s.gosz());
   c->zero(V, s.gosz());
   if (split_mode(c))
-    tc_xt(c, Xt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, c->ords, "ords", 1, 0,
+    tc_xt(c, Xt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, ch.own, okey, 1, 0,
           s.oj, s.ok, s.oc, 1.0, V);
   else
-    v_like(c, Xt3, c->Tl, V);
+    v_like(c, Xt3, c->Tl, ch.own, okey, V);
   d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
   // D_cd += 1/2 sum Xt^{abc}_{ijk} tau^{abd}_{ijk}
   if (split_mode(c))
-    tc_vv(c, Xt3, "X", tau, "Y", c->ords, "ords", D + NO * nmo + NO, nmo, 0.5);
+    tc_vv(c, Xt3, "X", tau, "Y", ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
   else
-    vv_block(c, Xt3, tau, D + NO * nmo + NO, nmo, 0.5);
-  (void)tag;
+    vv_block(c, Xt3, tau, ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
 }
 
 }  // namespace
@@ -1853,179 +1958,179 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   double *Dm0 = c->out(Dm0_out, nmo * nmo, "Dm0");
   double *D0m = c->out(D0m_out, nmo * nmo, "D0m");
   for (double *p : {D00, Dm0, D0m}) c->zero(p, nmo * nmo);
-  const size_t nb = c->batches.size();
-  const std::vector<TripItem> &bs = cvs ? c->batches_cvs : c->batches;
-  const std::string bkey = cvs ? "batches_cvs" : "batches";
-  ViewMap vm(c->ords, s.no);
 
-  double *tau, *taut;
-  build_tau(c, &tau, &taut);
-  // lambda3 (omega = 0) and its contravariant form
+  // doubles-level operands of the three triples amplitudes
   double *lc = c->buf("lamc", s.blk());
   double *lcT = c->buf("lamcT", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
     c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, lc, lcT);
-  double *lam3 = c->buf("lam3", nb * s.nv3);
-  double *lt3 = c->buf("lam3t", nb * s.nv3);
-  left_triples(c, "lam", lam1, lc, lcT, "batches", c->batches, 0.0, lam3);
-  contra3(c, lam3, lt3, (long long)nb);
-  // L3 (omega) and its contravariant form
   double *Lc = c->buf("Lc", s.blk());
   double *LcT = c->buf("LcT", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
     c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, Lc, LcT);
-  double *L3 = c->buf("L3", nb * s.nv3);
-  double *L3t = c->buf("L3t", nb * s.nv3);
-  if (cvs) c->zero(L3, nb * s.nv3);
-  left_triples(c, "L", L1, Lc, LcT, bkey, bs, omega, L3);
-  contra3(c, L3, L3t, (long long)nb);
-  // R3 (omega) and its contravariant form
   double *Rbar = c->buf("Rbar", s.blk());
   double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * NO);
   launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
     c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, Rbar, Rbl);
-  double *R3 = c->buf("R3", nb * s.nv3);
-  double *R3t = c->buf("R3t", nb * s.nv3);
-  if (cvs) c->zero(R3, nb * s.nv3);
-  {
-    Ups u = build_upsilon(c, R1);
-    right_triples(c, Rbar, Rbl, u, bkey, bs, omega, R3);
-    contra3(c, R3, R3t, (long long)nb);
-  }
-  // D^{0-0} and D^{m-0}
-  density_left_gpu(c, vm, lt3, lc, tau, taut, D00, "00");
-  density_left_gpu(c, vm, L3t, Lc, tau, taut, Dm0, "m0");
-
-  // D^{0-m}
-  double *D = D0m;
-  int n = 0;
-  const BstcItem *it;
-  Shape sh;
-  // U[q][r][b][c] = sum_{p,a} lt_{pqr}[a][b][c] R^a_p
-  double *U = c->buf("dU", s.no * s.no * s.nv * s.nv);
-  c->zero(U, s.no * s.no * s.nv * s.nv);
-  it = c->dev_items("ords:U", [&] {
-    std::vector<BstcItem> v;
-    for (auto &o : c->ords)
-      v.push_back(mk_item(o.off, o.p, (o.q * s.no + o.r) * s.nv * s.nv,
-                          {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {NO, 0, 0, 0, 0}, {s.nv, 1, 0, 0}));
-    return v;
-  }, &n);
-  sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-  c->bstc(lt3, R1, U, sh, 1.0, it, n, true, "ords:U");
-  // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
-  sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
-  c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
-  // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
-  pair_dots(c, vm, lt3, R3, D, nmo, true, -0.5, "pd:kl");
-  // D_ld += sum U[j][k][b][c] (tau^{bcd}_{jkl} - tau^{bcd}_{jlk})
-  it = c->dev_items("ords:ld1", [&] {
-    std::vector<BstcItem> v;
-    for (auto &o : c->ords)
-      v.push_back(mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
-                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
-    return v;
-  }, &n);
-  sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, "ords:ld1");
-  it = c->dev_items("ords:ld2", [&] {
-    std::vector<BstcItem> v;
-    for (auto &o : c->ords)
-      v.push_back(mk_item(o.off, (o.p * s.no + o.r) * s.nv * s.nv, o.q * nmo,
-                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
-    return v;
-  }, &n);
-  c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, "ords:ld2");
-  //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
-  y3_like(c, R3t, lc, D + NO, nmo, 0.5, "ords:y3d");
-  // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}
-  double *W3 = c->buf("dW3", s.no * s.nv);
-  c->zero(W3, s.no * s.nv);
-  y3_like(c, lt3, Rbar, W3, s.nv, 0.5, "ords:y3w");
-  //   D_LD += sum_{kc} W3[k][c] (2 t^{cD}_{kL} - t^{cD}_{Lk})
-  sh = Shape{}; sh.M1 = NO; sh.M2 = s.NV; sh.K1 = s.no; sh.K2 = s.nv;
-  c->bstc1(c->t2c, W3, D + NO, sh, 2.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
-  c->bstc1(c->t2x, W3, D + NO, sh, -1.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
-  //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}
-  double *V = c->buf("dV", s.gosz());
-  c->zero(V, s.gosz());
-  if (split_mode(c)) {
-    split_tl_T(c, "Rbl", Rbl);
-    tc_xt(c, lt3, "X", c->splits.at("Rbl:T"), c->splits.at("Rbl:Ts"), s.NO, c->ords, "ords", 1, 0,
-          s.oj, s.ok, s.oc, 1.0, V);
-  } else {
-    v_like(c, lt3, Rbl, V);
-  }
-  d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
-  //   D_LD -= sum lt^{abc}_{ijk} Rbar^{aD}_{ik} t^{bc}_{jL}
-  double *V3 = c->buf("dV3", s.gosz());
-  c->zero(V3, s.gosz());
-  it = c->dev_items("ords:v3", [&] {
-    std::vector<BstcItem> v;
-    for (auto &o : c->ords)
-      v.push_back(mk_item(o.off, o.q * s.ti, o.p * s.oj + o.r * s.ok,
-                          {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
-    return v;
-  }, &n);
-  sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = NO;
-  if (split_mode(c))
-    tc_xt(c, lt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, c->ords, "ords", 0, 1,
-          s.oj, s.ok, s.oc, 1.0, V3);
-  else
-    c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true, "ords:v3");
-  sh = Shape{}; sh.M1 = NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
-  c->bstc1(V3, Rbar, D + NO, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dLD3");
-  // D_lD -= 1/2 sum_k E[l][k] R^D_k,  E[l][k] = sum lt_{ijk} tau_{ijl}
-  double *E = c->buf("dE", s.no * s.no + s.nv * s.nv);
-  c->zero(E, s.no * s.no + s.nv * s.nv);
-  pair_dots(c, vm, tau, lt3, E, s.no, false, 1.0, "pd:E");
-  sh = Shape{}; sh.M1 = s.no; sh.N1 = s.NV; sh.K1 = s.no;
-  c->bstc1(E, R1, D + NO, sh, -0.5, mk_item(0, 0, 0, {s.no, 0, 1, 0, 0}, {1, 0, 0, NO, 0}, {nmo, 0, 1, 0}), "dlD");
-  // D_Ld -= 1/2 sum_c E2[c][d] R^c_L,  E2[c][d] = sum lt^{abc}_{ijk} tau^{abd}_{ijk}
-  double *E2 = E + s.no * s.no;
-  if (split_mode(c))
-    tc_vv(c, lt3, "X", tau, "Y", c->ords, "ords", E2, s.nv, 1.0);
-  else
-    vv_block(c, lt3, tau, E2, s.nv, 1.0);
-  sh = Shape{}; sh.M1 = NO; sh.N1 = s.nv; sh.K1 = s.nv;
-  c->bstc1(R1, E2, D + NO, sh, -0.5, mk_item(0, 0, 0, {1, 0, NO, 0, 0}, {s.nv, 0, 0, 1, 0}, {nmo, 0, 1, 0}), "dLd");
-  // D_ck += W3[k][c]
+  Ups u = build_upsilon(c, R1);
+  if (split_mode(c)) split_tl_T(c, "Rbl", Rbl);
   double *one = c->dscal;
+  double *sc = c->dscal + 1;
   {
     double h1 = 1.0;
     check_cuda(cudaMemcpyAsync(one, &h1, sizeof(double), cudaMemcpyHostToDevice, c->stream), "one");
     check_cuda(cudaStreamSynchronize(c->stream), "one sync");
   }
-  sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.no;
-  c->bstc1(W3, one, D + NO * nmo, sh, 1.0, mk_item(0, 0, 0, {1, s.nv, 0, 0, 0}, {0, 0, 0, 0, 0}, {nmo, 1, 0, 0}), "dck");
-  // D_cD += sum_{j,k,b} U[j][k][b][c] t^{bD}_{jk}
-  sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
-  c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dcD");
-  // D_cd += 1/2 sum lt^{abc}_{ijk} R^{abd}_{ijk}
-  if (split_mode(c))
-    tc_vv(c, lt3, "X", R3, "Y", c->ords, "ords", D + NO * nmo + NO, nmo, 0.5);
-  else
-    vv_block(c, lt3, R3, D + NO * nmo + NO, nmo, 0.5);
-  // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings), lambda_SD.R_SD
-  double *sc = c->dscal + 1;
   c->zero(sc, 2);
-  it = c->dev_items("bdots", [&] {
-    std::vector<BstcItem> v;
-    std::map<int, int> mult;
-    for (auto &o : c->ords) mult[o.u]++;
-    (void)mult;
-    for (auto &o : c->ords)
-      v.push_back(mk_item(o.off, o.off, 0, {0, 0, 0, 0, 1}, {0, 0, 1, 0, 0}, {0, 0, 0, 0}));
-    return v;
-  }, &n);
-  sh = Shape{}; sh.K3 = s.nv3;
-  c->dot(lt3, R3, sc, sh, 1.0 / 6.0, it, n);
+  double *D = D0m;
+  for (const Chunk &ch : c->groups) {
+    const std::string bkey = "b" + ch.key, okey = "o" + ch.key;
+    const long long bw = ch.nb * s.nv3;
+    double *tau, *taut;
+    build_tau(c, ch, &tau, &taut);
+    // lambda3 (omega = 0) and its contravariant form
+    double *lam3 = c->buf("lam3", bw);
+    double *lt3 = c->buf("lam3t", bw);
+    left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
+    contra3(c, lam3, lt3, ch.nb);
+    // L3 (omega) and R3 (omega), with their contravariant forms (CVS: core batches only)
+    double *L3 = c->buf("L3", bw);
+    double *L3t = c->buf("L3t", bw);
+    if (cvs) c->zero(L3, bw);
+    const std::string bkey3 = cvs ? bkey + "cvs" : bkey;  // the batch list is cached per key
+    left_triples(c, "L", L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3);
+    contra3(c, L3, L3t, ch.nb);
+    double *R3 = c->buf("R3", bw);
+    double *R3t = c->buf("R3t", bw);
+    if (cvs) c->zero(R3, bw);
+    right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3);
+    contra3(c, R3, R3t, ch.nb);
+    // D^{0-0} and D^{m-0}
+    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
+    density_left_gpu(c, ch, L3t, Lc, tau, taut, Dm0);
+
+    // D^{0-m}
+    int n = 0;
+    const BstcItem *it;
+    Shape sh;
+    // U[q][r][b][c] = sum_{p,a} lt_{pqr}[a][b][c] R^a_p  (rows q in [p0, p1))
+    double *U = c->buf("dU", s.no * s.no * s.nv * s.nv);
+    c->zero(U, s.no * s.no * s.nv * s.nv);
+    it = c->dev_items(okey + ":U", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ch.held)
+        if (o.q >= ch.p0 && o.q < ch.p1)
+          v.push_back(mk_item(o.off, o.p, (o.q * s.no + o.r) * s.nv * s.nv,
+                              {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {NO, 0, 0, 0, 0}, {s.nv, 1, 0, 0}));
+      return v;
+    }, &n);
+    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
+    c->bstc(lt3, R1, U, sh, 1.0, it, n, true, okey + ":U");
+    // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
+    sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
+    c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
+    // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
+    pair_dots(c, ch, lt3, R3, D, nmo, true, -0.5);
+    // D_ld += sum U[j][k][b][c] (tau^{bcd}_{jkl} - tau^{bcd}_{jlk})  (views with j in [p0, p1))
+    it = c->dev_items(okey + ":ld1", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ch.held)
+        if (o.p >= ch.p0 && o.p < ch.p1)
+          v.push_back(mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
+                              {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
+      return v;
+    }, &n);
+    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+    c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, okey + ":ld1");
+    it = c->dev_items(okey + ":ld2", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ch.held)
+        if (o.p >= ch.p0 && o.p < ch.p1)
+          v.push_back(mk_item(o.off, (o.p * s.no + o.r) * s.nv * s.nv, o.q * nmo,
+                              {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
+      return v;
+    }, &n);
+    c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, okey + ":ld2");
+    //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
+    y3_like(c, R3t, lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
+    // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}
+    double *W3 = c->buf("dW3", s.no * s.nv);
+    c->zero(W3, s.no * s.nv);
+    y3_like(c, lt3, Rbar, ch.own, okey, W3, s.nv, 0.5, "y3w");
+    //   D_LD += sum_{kc} W3[k][c] (2 t^{cD}_{kL} - t^{cD}_{Lk})
+    sh = Shape{}; sh.M1 = NO; sh.M2 = s.NV; sh.K1 = s.no; sh.K2 = s.nv;
+    c->bstc1(c->t2c, W3, D + NO, sh, 2.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
+    c->bstc1(c->t2x, W3, D + NO, sh, -1.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
+    //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}
+    double *V = c->buf("dV", s.gosz());
+    c->zero(V, s.gosz());
+    if (split_mode(c))
+      tc_xt(c, lt3, "X", c->splits.at("Rbl:T"), c->splits.at("Rbl:Ts"), s.NO, ch.own, okey, 1, 0,
+            s.oj, s.ok, s.oc, 1.0, V);
+    else
+      v_like(c, lt3, Rbl, ch.own, okey, V);
+    d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
+    //   D_LD -= sum lt^{abc}_{ijk} Rbar^{aD}_{ik} t^{bc}_{jL}
+    double *V3 = c->buf("dV3", s.gosz());
+    c->zero(V3, s.gosz());
+    if (split_mode(c)) {
+      tc_xt(c, lt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, ch.own, okey, 0, 1,
+            s.oj, s.ok, s.oc, 1.0, V3);
+    } else {
+      it = c->dev_items(okey + ":v3", [&] {
+        std::vector<BstcItem> v;
+        for (auto &o : ch.own)
+          v.push_back(mk_item(o.off, o.q * s.ti, o.p * s.oj + o.r * s.ok,
+                              {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.ta, s.tb, 0, 1, 0}, {s.oc, 0, 1, 0}));
+        return v;
+      }, &n);
+      sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = NO;
+      c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true, okey + ":v3");
+    }
+    sh = Shape{}; sh.M1 = NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
+    c->bstc1(V3, Rbar, D + NO, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dLD3");
+    // D_lD -= 1/2 sum_k E[l][k] R^D_k,  E[l][k] = sum lt_{ijk} tau_{ijl}
+    double *E = c->buf("dE", s.no * s.no + s.nv * s.nv);
+    c->zero(E, s.no * s.no + s.nv * s.nv);
+    pair_dots(c, ch, tau, lt3, E, s.no, false, 1.0);
+    sh = Shape{}; sh.M1 = s.no; sh.N1 = s.NV; sh.K1 = s.no;
+    c->bstc1(E, R1, D + NO, sh, -0.5, mk_item(0, 0, 0, {s.no, 0, 1, 0, 0}, {1, 0, 0, NO, 0}, {nmo, 0, 1, 0}), "dlD");
+    // D_Ld -= 1/2 sum_c E2[c][d] R^c_L,  E2[c][d] = sum lt^{abc}_{ijk} tau^{abd}_{ijk}
+    double *E2 = E + s.no * s.no;
+    if (split_mode(c))
+      tc_vv(c, lt3, "X", tau, "Y", ch.own, okey, E2, s.nv, 1.0);
+    else
+      vv_block(c, lt3, tau, ch.own, okey, E2, s.nv, 1.0);
+    sh = Shape{}; sh.M1 = NO; sh.N1 = s.nv; sh.K1 = s.nv;
+    c->bstc1(R1, E2, D + NO, sh, -0.5, mk_item(0, 0, 0, {1, 0, NO, 0, 0}, {s.nv, 0, 0, 1, 0}, {nmo, 0, 1, 0}), "dLd");
+    // D_ck += W3[k][c]
+    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.no;
+    c->bstc1(W3, one, D + NO * nmo, sh, 1.0, mk_item(0, 0, 0, {1, s.nv, 0, 0, 0}, {0, 0, 0, 0, 0}, {nmo, 1, 0, 0}), "dck");
+    // D_cD += sum_{j,k,b} U[j][k][b][c] t^{bD}_{jk}
+    sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
+    c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dcD");
+    // D_cd += 1/2 sum lt^{abc}_{ijk} R^{abd}_{ijk}
+    if (split_mode(c))
+      tc_vv(c, lt3, "X", R3, "Y", ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
+    else
+      vv_block(c, lt3, R3, ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
+    // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings)
+    it = c->dev_items(okey + ":dots", [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : ch.own)
+        v.push_back(mk_item(o.off, o.off, 0, {0, 0, 0, 0, 1}, {0, 0, 1, 0, 0}, {0, 0, 0, 0}));
+      return v;
+    }, &n);
+    sh = Shape{}; sh.K3 = s.nv3;
+    c->dot(lt3, R3, sc, sh, 1.0 / 6.0, it, n);
+  }
+  // lambda_SD.R_SD, then the normalisation term of D^{0-m}
   launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
     c->launch("sd_dot_kernel", 0.0, [&] { sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, R1, R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1); });
   });
@@ -2101,6 +2206,7 @@ extern "C" int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *d, int precision,
       check_cuda(cudaMalloc(&c->status, sizeof(int)), "cudaMalloc status");
       check_cuda(cudaMemset(c->status, 0, sizeof(int)), "memset status");
       make_batches(c);
+      make_chunks(c);
     } catch (...) {
       mlcc3_destroy(c);
       throw;
@@ -2226,6 +2332,10 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     if (n == "tc_kcap") {
       if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, "tc_kcap out of range 0..4096"};
       c->tc_kcap = (int)value;
+    } else if (n == "chunk_blocks") {
+      if (value < 0) throw Error{MLCC3_ERR_ARG, "chunk_blocks must be >= 0"};
+      c->chunk_blocks = value;
+      make_chunks(c);
     } else {
       throw Error{MLCC3_ERR_ARG, "unknown parameter " + n};
     }
