@@ -112,6 +112,23 @@ struct mlcc3_ctx {
     CUtensorMap mhi, mlo;
   };
   std::map<std::string, SplitOp> splits;
+  // split layouts of triples arrays, converted once per (array, write
+  // generation): slots hold the layouts converted so far of one array; every
+  // path that writes a triples array marks it (wrote), which retires them
+  struct TriSlot {
+    const double *src = nullptr;
+    unsigned long long gen = 0, tick = 0;
+    long long nb = 0;
+    unsigned mask = 0;
+  };
+  TriSlot tri[4];
+  unsigned long long tri_tick = 0, gen_next = 0;
+  std::map<const void *, unsigned long long> gens;
+  void wrote(const void *p) { gens[p] = ++gen_next; }
+  unsigned long long gen_of(const void *p) const {
+    auto it = gens.find(p);
+    return it == gens.end() ? 0ULL : it->second;
+  }
   // output copies back to host pointers at the end of a call
   std::vector<std::array<void *, 3>> pending_out;
 

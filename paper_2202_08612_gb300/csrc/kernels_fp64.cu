@@ -455,46 +455,61 @@ __global__ void density_norm_kernel(double *__restrict__ D, const double *__rest
 
 namespace mlcc3 {
 
+// 1/d to about 1e-14 relative: an FP32 reciprocal refined by one Newton step
+// in FP64 (the step squares the relative error of the starting value).
+__device__ __forceinline__ double recip_newton(double d) {
+  const double r0 = (double)(1.0f / (float)d);
+  return r0 * fma(-d, r0, 2.0);
+}
+
 // Finish of the tensor-core triples build: X = -(W + rank-1 terms) / (eps - omega)
 // per element of every block in `items`, W the FP32 sum of the six permuted
 // two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
 // Only kinds 2 and 3 of `terms` are evaluated here (summed over the six pair
-// permutations in FP64).
+// permutations; in FP32 when fp32_rank1 is set, the split-precision mode).
+// The denominator is formed in FP64.
 __global__ void triples_finish_kernel(const float *__restrict__ W, const TripItem *__restrict__ items,
                                       int nitems, const TripTerms terms,
                                       const double *__restrict__ eps, int NO, int nv, double omega,
-                                      double *__restrict__ out, int *__restrict__ status) {
+                                      int fp32_rank1, double *__restrict__ out,
+                                      int *__restrict__ status) {
   const int nv3 = nv * nv * nv;
   if ((int)blockIdx.y >= nitems) return;
   const TripItem it = items[blockIdx.y];
+  const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
     const int X[3] = {r / (nv * nv), (r / nv) % nv, r % nv};
     const int I[3] = {it.i, it.j, it.k};
     double acc = (double)W[it.off + r];
+    float acc32 = 0.0f;
     for (int t = 0; t < terms.n; ++t) {
       const TripTerm &tm = terms.t[t];
       if (tm.kind < 2) continue;
       for (int sg = 0; sg < 6; ++sg) {
         const long long x = I[kPerm[sg][0]], y = I[kPerm[sg][1]], z = I[kPerm[sg][2]];
         const long long u = X[kPerm[sg][0]], v = X[kPerm[sg][1]], w = X[kPerm[sg][2]];
-        double val;
-        if (tm.kind == 2)
-          val = tm.A[x * tm.sA[0] + u * tm.sA[1]] *
-                tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+        double a, b;
+        if (tm.kind == 2) {
+          a = tm.A[x * tm.sA[0] + u * tm.sA[1]];
+          b = tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+        } else {
+          a = tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
+          b = tm.B[z * tm.sB[0] + w * tm.sB[1]];
+        }
+        if (fp32_rank1)
+          acc32 = fmaf((float)tm.coef * (float)a, (float)b, acc32);
         else
-          val = tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]] *
-                tm.B[z * tm.sB[0] + w * tm.sB[1]];
-        acc = fma(tm.coef, val, acc);
+          acc = fma(tm.coef, a * b, acc);
       }
     }
-    const double den = eps[NO + X[0]] + eps[NO + X[1]] + eps[NO + X[2]] - eps[it.i] - eps[it.j] -
-                       eps[it.k] - omega;
+    acc += (double)acc32;
+    const double den = eps[NO + X[0]] + eps[NO + X[1]] + eps[NO + X[2]] + eo;
     double val;
     if (fabs(den) < 1e-3) {
       atomicOr(status, 1);
       val = 0.0;
     } else {
-      val = -acc / den;
+      val = -acc * recip_newton(den);
     }
     out[it.off + r] = val;
   }
@@ -535,46 +550,98 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
 
 namespace mlcc3 {
 
-// D[k][l] (or [l][k]) += alpha sum_{ij} sum_{abc} X_{ijl}[abc] Y_{ijk}[abc] for
-// one (i,j) pair per blockIdx.y and a chunk of 256 (a,b,c) per blockIdx.x: the
-// chunk of every block X_{ij.} and Y_{ij.} is read once and all n_o^2 partial
-// dot products are formed from shared memory.  Views: off/stride tables per
-// ordered triple (p,q,r) -> canonical block offset and strides of x1, x2, x3
-// (have == 0 marks a triple without a stored block).
-__global__ void __launch_bounds__(256) pair_dots_kernel(const double *__restrict__ X,
-                                                        const double *__restrict__ Y,
-                                                        const long long *__restrict__ voff,
-                                                        const int *__restrict__ vstr,
-                                                        const char *__restrict__ vhave, int no, int nv,
-                                                        int p0, double *__restrict__ out, long long ldo,
-                                                        int kl, double alpha) {
-  extern __shared__ double sm[];
-  double *xs = sm;                  // [no][256]
-  double *ys = sm + (size_t)no * 256;  // [no][256]
+// D_kl-type pair terms: out[k][l] (kl = 1, else out[l][k]) += alpha sum_{abc}
+// X_{ijl}[abc] Y_{ijk}[abc] for the ordered pair (i, j) = (p0 + y / no, y % no),
+// y = blockIdx.y, over all k, l with stored views.  View (p,q,r) is the block
+// at voff[v] with strides vstr[3v..3v+2] of its (a, b, c) (v = (p no + q) no + r,
+// vhave[v] = 0 for a missing block).  Each block sweeps 4x8x8 tiles of (a,b,c)
+// (tile = blockIdx.x, blockIdx.x + gridDim.x, ...), so whichever of a, b, c is a
+// view's contiguous axis, neighbouring threads read runs of at least four
+// elements; thread t keeps the 2x2 (k,l) tile (t % TT) of partial sums over the
+// (t / TT)-th share of every tile and adds it to `out` once.  T is the type of
+// the products and of the per-tile sums (FP32 in the split-precision mode,
+// else FP64); the sums over tiles are FP64.  Requires no <= 32.
+template <typename T>
+__device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
+                                               const double *__restrict__ Y,
+                                               const long long *__restrict__ voff,
+                                               const int *__restrict__ vstr,
+                                               const char *__restrict__ vhave, int no, int nv, int p0,
+                                               double *__restrict__ out, long long ldo, int kl,
+                                               double alpha) {
+  extern __shared__ unsigned char smraw[];
+  T *xs = reinterpret_cast<T *>(smraw);     // [no][257]
+  T *ys = xs + (size_t)no * 257;            // [no][257]
   const int i = p0 + (int)blockIdx.y / no, j = (int)blockIdx.y % no;
-  const int nv3 = nv * nv * nv;
-  const int r = blockIdx.x * 256 + threadIdx.x;
-  const int a = r / (nv * nv), b = (r / nv) % nv, c = r % nv;
-  for (int k = 0; k < no; ++k) {
-    const int v = (i * no + j) * no + k;
-    double xv = 0.0, yv = 0.0;
-    if (r < nv3 && vhave[v]) {
-      const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
-                          (long long)c * vstr[3 * v + 2];
-      xv = X[o];
-      yv = Y[o];
+  const int t = threadIdx.x;
+  const int nh = (no + 1) / 2;
+  const int TT = nh * nh;                   // 2x2 tiles of (k, l)
+  const int H = 256 / TT;                   // element shares per tile
+  const int tile = t % TT, h = t / TT;
+  const int k0 = 2 * (tile / nh), l0 = 2 * (tile % nh);
+  const int e0 = h * (256 / H), e1 = (h + 1 == H) ? 256 : (h + 1) * (256 / H);
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // FP64 running sums over tiles
+  const int ta = (nv + 3) / 4, tb = (nv + 7) / 8, tc = (nv + 7) / 8;
+  const int ntiles = ta * tb * tc;
+  const int a_in = t / 64, b_in = (t / 8) % 8, c_in = t % 8;
+  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const int qa = q / (tb * tc), qb = (q / tc) % tb, qc = q % tc;
+    const int a = 4 * qa + a_in, b = 8 * qb + b_in, c = 8 * qc + c_in;
+    const bool in = a < nv && b < nv && c < nv;
+    __syncthreads();  // the previous tile's reads are done
+    for (int r = 0; r < no; ++r) {
+      const int v = (i * no + j) * no + r;
+      T xv = T(0), yv = T(0);
+      if (in && vhave[v]) {
+        const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
+                            (long long)c * vstr[3 * v + 2];
+        xv = (T)X[o];
+        yv = (T)Y[o];
+      }
+      xs[r * 257 + t] = xv;
+      ys[r * 257 + t] = yv;
     }
-    xs[k * 256 + threadIdx.x] = xv;
-    ys[k * 256 + threadIdx.x] = yv;
+    __syncthreads();
+    if (h < H) {
+      const int ka = min(k0, no - 1), kb = min(k0 + 1, no - 1);
+      const int la = min(l0, no - 1), lb = min(l0 + 1, no - 1);
+      const T *x0 = xs + la * 257, *x1 = xs + lb * 257;
+      const T *y0 = ys + ka * 257, *y1 = ys + kb * 257;
+      T p00 = T(0), p01 = T(0), p10 = T(0), p11 = T(0);  // this tile's share
+      for (int e = e0; e < e1; ++e) {
+        const T u0 = x0[e], u1 = x1[e], w0 = y0[e], w1 = y1[e];
+        p00 += w0 * u0;
+        p01 += w0 * u1;
+        p10 += w1 * u0;
+        p11 += w1 * u1;
+      }
+      acc[0][0] += (double)p00;
+      acc[0][1] += (double)p01;
+      acc[1][0] += (double)p10;
+      acc[1][1] += (double)p11;
+    }
   }
-  __syncthreads();
-  // thread t handles the pairs (k, l) with k*no + l = t, t + 256, ...
-  for (int t = threadIdx.x; t < no * no; t += 256) {
-    const int k = t / no, l = t % no;
-    double s = 0.0;
-    for (int e = 0; e < 256; ++e) s += xs[l * 256 + e] * ys[k * 256 + e];
-    if (s != 0.0) atomicAdd(out + (kl ? k * ldo + l : l * ldo + k), alpha * s);
-  }
+  if (h >= H) return;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dl = 0; dl < 2; ++dl) {
+      const int kk = k0 + dk, ll = l0 + dl;
+      if (kk >= no || ll >= no || acc[dk][dl] == 0.0) continue;
+      atomicAdd(out + (kl ? kk * ldo + ll : ll * ldo + kk), alpha * acc[dk][dl]);
+    }
+}
+
+__global__ void __launch_bounds__(256) pair_dots_f32_kernel(
+    const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
+    const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
+    double *__restrict__ out, long long ldo, int kl, double alpha) {
+  pair_dots_body<float>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+}
+
+__global__ void __launch_bounds__(256) pair_dots_f64_kernel(
+    const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
+    const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
+    double *__restrict__ out, long long ldo, int kl, double alpha) {
+  pair_dots_body<double>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 }  // namespace mlcc3

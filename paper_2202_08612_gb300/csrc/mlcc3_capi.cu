@@ -30,8 +30,10 @@ namespace mlcc3 {
 __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
-__global__ void pair_dots_kernel(const double *, const double *, const long long *, const int *,
-                                 const char *, int, int, int, double *, long long, int, double);
+__global__ void pair_dots_f32_kernel(const double *, const double *, const long long *, const int *,
+                                     const char *, int, int, int, double *, long long, int, double);
+__global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
+                                     const char *, int, int, int, double *, long long, int, double);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, double *, int *);
@@ -45,7 +47,7 @@ __global__ void sd_dot_kernel(const double *, const double *, const double *, co
 __global__ void density_norm_kernel(double *, const double *, const double *, const double *,
                                     int, int);
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
-                                      const double *, int, int, double, double *, int *);
+                                      const double *, int, int, double, int, double *, int *);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
@@ -123,6 +125,7 @@ void mlcc3_ctx::collect_events() {
 }
 
 void mlcc3_ctx::zero(double *p, size_t n) {
+  wrote(p);
   check_cuda(cudaMemsetAsync(p, 0, n * sizeof(double), stream), "memset");
 }
 
@@ -378,10 +381,12 @@ Chunk make_chunk(const mlcc3_ctx *c, const std::vector<TripItem> &held, int p0, 
 }
 
 // Split the unique batches into chunks of at most chunk_blocks blocks (or, when
-// it is 0, as many as fit in 55% of the device memory left free once the
-// context's persistent arrays exist: about 64 bytes per element for the
-// Jacobian passes and 96 for the densities, which hold more triples arrays
-// and their split copies).
+// it is 0, as many as fit in half of the device memory left free once the
+// context's persistent arrays exist, at 140 bytes per block element: the
+// eight FP64 triples arrays the passes keep (tau, R3, L3, lambda3 and their
+// contravariant forms) plus up to 18 cached split-precision layouts of
+// triples arrays (tri_layout); scratch buffers persist across calls, so one
+// size serves all).
 void make_chunks(mlcc3_ctx *c) {
   c->chunk_gen += 1;
   c->tau_key.clear();
@@ -393,9 +398,8 @@ void make_chunks(mlcc3_ctx *c) {
   if (part_max <= 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)40 << 30;
-    const double budget = 0.55 * (double)fr;
-    part_max = std::max<long long>(1, (long long)(budget / (64.0 * (double)nv3)));
-    group_max = std::max<long long>(1, (long long)(budget / (96.0 * (double)nv3)));
+    const double budget = 0.5 * (double)fr;
+    part_max = group_max = std::max<long long>(1, (long long)(budget / (140.0 * (double)nv3)));
   }
   const std::string g = "#" + std::to_string(c->chunk_gen);
   auto partition = [&](const std::vector<TripItem> &list, const std::string &tag) {
@@ -470,6 +474,7 @@ void fock_ov(mlcc3_ctx *c, const double *x1, double *out, const std::string &tag
 // Triples blocks X_u for every batch of `bs`, written at bs[u].off of `out`.
 void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string &bkey,
              const std::vector<TripItem> &bs, double omega, double *out) {
+  c->wrote(out);
   if (bs.empty() || c->nv == 0) return;
   if (terms.size() > (size_t)kMaxTerms) throw Error{MLCC3_ERR_ARG, "too many triples terms"};
   TripTerms tt{};
@@ -503,6 +508,7 @@ void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string
 }
 
 void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
+  c->wrote(Xt);
   if (nblocks <= 0 || c->nv == 0) return;
   const long long nv3 = c->nv * c->nv * c->nv;
   for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
@@ -569,6 +575,9 @@ mlcc3_ctx::SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const doubl
 mlcc3_ctx::SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk);
 void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
 void tc_integrals(mlcc3_ctx *c);
+void split_chol_kpairs(mlcc3_ctx *c);
+mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k,
+                              unsigned rows);
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
                 const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2);
 
@@ -793,10 +802,11 @@ SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, lon
   const size_t n = (size_t)(D0 * D1 * D2 * Kp);
   op.hi = c->raw("split:" + key + ":hi", n * 2);
   op.lo = c->raw("split:" + key + ":lo", n * 2);
-  check_cuda(split_bf16(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
-                        D0, D1, D2, K, Kp, s0, s1, s2, s3, scale, c->stream),
-             "split_bf16");
-  c->kstats["split_bf16_kernel"].launches += 1;
+  c->launch("split_bf16_kernel", 0.0, [&] {
+    check_cuda(split_bf16(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
+                          D0, D1, D2, K, Kp, s0, s1, s2, s3, scale, c->stream),
+               "split_bf16");
+  });
   const unsigned long long dims[4] = {(unsigned long long)Kp, (unsigned long long)D2,
                                       (unsigned long long)D1, (unsigned long long)D0};
   const unsigned long long str[3] = {(unsigned long long)(Kp * 2), (unsigned long long)(Kp * 2 * D2),
@@ -874,6 +884,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
                    const std::vector<TripTerm> &rank1, const std::string &bkey,
                    const std::vector<TripItem> &bs, double omega, double *out) {
   S s(c);
+  c->wrote(out);
   if (bs.empty() || s.nv == 0) return;
   if (terms.size() * 6 > (size_t)kTcMaps) throw Error{MLCC3_ERR_ARG, "too many tensor-core terms"};
   TcMaps maps;
@@ -942,7 +953,8 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     dim3 grid((unsigned)std::min<long long>((s.nv3 + 255) / 256, 1024), (unsigned)nbc);
     c->launch("triples_finish_kernel", 0.0, [&] {
       triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps,
-                                                         (int)s.NO, (int)s.nv, omega, out, c->status);
+                                                         (int)s.NO, (int)s.nv, omega, 1, out,
+                                                         c->status);
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
@@ -968,31 +980,73 @@ void build_split_persistent(mlcc3_ctx *c) {
   split_go_T(c, "Go:T", c->Go);
   split_amp_T(c, "t:AT", c->t2c);
   split_tl_T(c, "Tl", c->Tl);
+  split_chol_kpairs(c);
 }
 
 // hi/lo split with a two-level K (k = k1 K2 + k2): out[o0][o1][Kp]; tensor maps
 // over (Kp, o1, -, o0) with a box of `rows` rows.
 SplitOp &make_split_k2(mlcc3_ctx *c, const std::string &key, const double *src, long long D0,
                        long long D1, long long K1, long long K2, long long s0, long long s1,
-                       long long sk1, long long sk2, unsigned rows) {
+                       long long sk1, long long sk2, unsigned rows, bool flat = false) {
   const long long Kp = (K1 * K2 + 63) / 64 * 64;
   SplitOp &op = c->splits[key];
   const size_t n = (size_t)(D0 * D1 * Kp);
   op.hi = c->raw("split:" + key + ":hi", n * 2);
   op.lo = c->raw("split:" + key + ":lo", n * 2);
-  check_cuda(split_bf16_k2(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
-                           D0, D1, K1, K2, Kp, s0, s1, sk1, sk2, 1.0, c->stream),
-             "split_bf16_k2");
-  c->kstats["split_bf16_kernel"].launches += 1;
-  const unsigned long long dims[4] = {(unsigned long long)Kp, (unsigned long long)D1, 1ULL,
-                                      (unsigned long long)D0};
-  const unsigned long long str[3] = {(unsigned long long)(Kp * 2), (unsigned long long)(Kp * 2 * D1),
-                                     (unsigned long long)(Kp * 2 * D1)};
+  c->launch("split_bf16_k2_kernel", 0.0, [&] {
+    check_cuda(split_bf16_k2(src, static_cast<__nv_bfloat16 *>(op.hi), static_cast<__nv_bfloat16 *>(op.lo),
+                             D0, D1, K1, K2, Kp, s0, s1, sk1, sk2, 1.0, c->stream),
+               "split_bf16_k2");
+  });
+  // rows over o1 within one o0, or (flat) over the flattened (o0, o1)
+  const unsigned long long R = flat ? (unsigned long long)(D0 * D1) : (unsigned long long)D1;
+  const unsigned long long dims[4] = {(unsigned long long)Kp, R, 1ULL,
+                                      flat ? 1ULL : (unsigned long long)D0};
+  const unsigned long long str[3] = {(unsigned long long)(Kp * 2), (unsigned long long)(Kp * 2) * R,
+                                     (unsigned long long)(Kp * 2) * R};
   const unsigned bx[4] = {64, rows, 1, 1};
   std::string err;
   if (!encode_map(&op.mhi, op.hi, dims, str, bx, &err) || !encode_map(&op.mlo, op.lo, dims, str, bx, &err))
     throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
   return op;
+}
+
+// out[m][n] (m = r1 R2 + r2 at r1 s1 + r2 s2, n at n sn) += alpha sum_k A[m][k] B[n][k]
+// for flat split operands A (128-row box) and B (box tile_width(N)); the
+// accumulation chains are capped and summed in FP64.
+void tc_flat_gemm(mlcc3_ctx *c, const SplitOp &A, const SplitOp &B, long long M, long long N,
+                  long long K, double *out, int R2, long long s1, long long s2, long long sn,
+                  double alpha, const std::string &key) {
+  if (M == 0 || N == 0 || K == 0) return;
+  TcMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  maps.m[0] = A.mhi;
+  maps.m[1] = A.mlo;
+  maps.m[2] = B.mhi;
+  maps.m[3] = B.mlo;
+  const int BN = tc_tile_width(N);
+  const long long ntM = (M + 127) / 128, ntN = (N + BN - 1) / BN;
+  const int nk = (int)((K + 63) / 64);
+  TcDev dv = tc_plan(c, "tcF:" + key, [&](TcPlan &pl) {
+    for (long long tm = 0; tm < ntM; ++tm)
+      for (long long tn = 0; tn < ntN; ++tn) {
+        pl.tile(0, (int)(128 * tm), (int)(BN * tn), 0);
+        pl.seg(0, 2, nk, (int)(128 * tm), 0, 0, (int)(BN * tn), 0, 0);
+      }
+  }, c->tc_kcap);
+  TcEpi epi = make_epi(out, 2, R2, s1, s2, sn, M / R2, R2, N, alpha, 1);
+  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)M * (double)N * (double)K);
+}
+
+// Cholesky factors as [J][(x, y)] split operands of the sigma singles tail.
+void split_chol_kpairs(mlcc3_ctx *c) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const unsigned bj = (unsigned)tc_tile_width(s.NJ);
+  // Lt[J][NO+b][NO+D] as K = (b, D); Lt[J][NO+c][k] and Lt[J][k][NO+c] as K = (c, k)
+  make_split_k2(c, "LvV:J", c->Lt + NO * nmo + NO, 1, s.NJ, s.nv, s.NV, 0, s.lJ, nmo, 1, bj, true);
+  make_split_k2(c, "Lvo:J", c->Lt + NO * nmo, 1, s.NJ, s.nv, s.no, 0, s.lJ, nmo, 1, bj, true);
+  make_split_k2(c, "Lov:J", c->Lt + NO, 1, s.NJ, s.nv, s.no, 0, s.lJ, 1, nmo, bj, true);
 }
 
 // G[k][b][c][D] (Gv-like) transposed to [k][D][(b,c)] and [k][D][(c,b)].
@@ -1012,17 +1066,16 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
                const BackSet &b, double *Zb) {
   S s(c);
   if (ords.empty() || s.nv == 0) return;
-  const long long nb = c->chunk_nb;
   const unsigned BN = (unsigned)tc_tile_width(s.nv);
   // row = canonical position 0 / 1 / 2; K = the other two (ascending)
-  make_split_k2(c, "XL0", X, nb, s.nv, s.nv, s.nv, s.nv3, s.nv * s.nv, s.nv, 1, BN);
-  make_split_k2(c, "XL1", X, nb, s.nv, s.nv, s.nv, s.nv3, s.nv, s.nv * s.nv, 1, BN);
-  make_split_k2(c, "XL2", X, nb, s.nv, s.nv, s.nv, s.nv3, 1, s.nv * s.nv, s.nv, BN);
+  const SplitOp &x0 = layout_XL(c, "bD:XL0", X, 0, BN);
+  const SplitOp &x1 = layout_XL(c, "bD:XL1", X, 1, BN);
+  const SplitOp &x2 = layout_XL(c, "bD:XL2", X, 2, BN);
   if (b.gd_convert) split_gt(c, b.gd_key, b.GD);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  const SplitOp *ops[5] = {&c->splits.at(b.gd_key + ":T"), &c->splits.at(b.gd_key + ":Ts"),
-                           &c->splits.at("XL0"), &c->splits.at("XL1"), &c->splits.at("XL2")};
+  const SplitOp *ops[5] = {&c->splits.at(b.gd_key + ":T"), &c->splits.at(b.gd_key + ":Ts"), &x0, &x1,
+                           &x2};
   for (int i = 0; i < 5; ++i) {
     maps.m[2 * i] = ops[i]->mhi;
     maps.m[2 * i + 1] = ops[i]->mlo;
@@ -1042,23 +1095,87 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
             2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size());
 }
 
+// hi/lo buffers of layout L of the triples array X (chunk_nb blocks), converted
+// at most once per write of X: L = 0..2 is XL_L, L = 3..5 is R_{L-3}.
+std::pair<void *, void *> tri_layout(mlcc3_ctx *c, const double *X, int L) {
+  S s(c);
+  const unsigned long long g = c->gen_of(X);
+  int q = -1;
+  for (int t = 0; t < 4; ++t)
+    if (c->tri[t].src == X && c->tri[t].gen == g && c->tri[t].nb == c->chunk_nb) q = t;
+  if (q < 0) {
+    q = 0;
+    for (int t = 1; t < 4; ++t)
+      if (c->tri[t].tick < c->tri[q].tick) q = t;
+    c->tri[q] = mlcc3_ctx::TriSlot{};
+    c->tri[q].src = X;
+    c->tri[q].gen = g;
+    c->tri[q].nb = c->chunk_nb;
+  }
+  mlcc3_ctx::TriSlot &ts = c->tri[q];
+  ts.tick = ++c->tri_tick;
+  const std::string base = "tri" + std::to_string(q) + ":" + std::to_string(L);
+  const long long nb = c->chunk_nb;
+  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
+  const int k = L % 3, a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
+  const bool xl = L < 3;
+  const long long Kp = xl ? (s.nv * s.nv + 63) / 64 * 64 : (s.nv + 63) / 64 * 64;
+  const size_t n = (size_t)nb * (size_t)(xl ? s.nv : s.nv * s.nv) * (size_t)Kp;
+  void *hi = c->raw(base + ":hi", n * 2), *lo = c->raw(base + ":lo", n * 2);
+  if (!(ts.mask & (1u << L))) {
+    ts.mask |= 1u << L;
+    __nv_bfloat16 *h = static_cast<__nv_bfloat16 *>(hi), *l = static_cast<__nv_bfloat16 *>(lo);
+    if (xl)
+      c->launch("split_bf16_k2_kernel", 0.0, [&] {
+        check_cuda(split_bf16_k2(X, h, l, nb, s.nv, s.nv, s.nv, Kp, s.nv3, cs[k], cs[a], cs[b], 1.0,
+                                 c->stream), "split_bf16_k2");
+      });
+    else
+      c->launch("split_bf16_kernel", 0.0, [&] {
+        check_cuda(split_bf16(X, h, l, nb, s.nv, s.nv, s.nv, Kp, s.nv3, cs[a], cs[b], cs[k], 1.0,
+                              c->stream), "split_bf16");
+      });
+  }
+  return {hi, lo};
+}
+
+void encode_split(mlcc3_ctx::SplitOp &op, const std::string &key, const unsigned long long dims[4],
+                  const unsigned long long str[3], const unsigned bx[4]) {
+  std::string err;
+  if (!encode_map(&op.mhi, op.hi, dims, str, bx, &err) || !encode_map(&op.mlo, op.lo, dims, str, bx, &err))
+    throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
+}
+
 // ---- layouts of the canonical triples blocks X[u][x0][x1][x2] ----
-// XL_k: row = canonical position k, K = the other two positions (ascending).
+// XL_k: row = canonical position k, K = the other two positions (ascending);
+// tensor maps over (K, row, -, block) with a box of `rows` rows.
 SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k, unsigned rows) {
   S s(c);
-  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
-  const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
-  return make_split_k2(c, key, X, c->chunk_nb, s.nv, s.nv, s.nv, s.nv3, cs[k],
-                       cs[a], cs[b], rows);
+  auto hl = tri_layout(c, X, k);
+  SplitOp &op = c->splits[key];
+  op.hi = hl.first;
+  op.lo = hl.second;
+  const unsigned long long Kp = (unsigned long long)((s.nv * s.nv + 63) / 64 * 64), nv = s.nv;
+  const unsigned long long dims[4] = {Kp, nv, 1ULL, (unsigned long long)c->chunk_nb};
+  const unsigned long long str[3] = {Kp * 2, Kp * 2 * nv, Kp * 2 * nv};
+  const unsigned bx[4] = {64, rows, 1, 1};
+  encode_split(op, key, dims, str, bx);
+  return op;
 }
 
 // R_k: K = canonical position k, rows = the other two as (smaller, larger) pair tiles.
 SplitOp &layout_R(mlcc3_ctx *c, const std::string &key, const double *X, int k) {
   S s(c);
-  const long long cs[3] = {s.nv * s.nv, s.nv, 1};
-  const int a = k == 0 ? 1 : 0, b = k == 2 ? 1 : 2;
-  return make_split(c, key, X, c->chunk_nb, s.nv, s.nv, s.nv, s.nv3, cs[a], cs[b],
-                    cs[k], 1.0, Box::Pair);
+  auto hl = tri_layout(c, X, 3 + k);
+  SplitOp &op = c->splits[key];
+  op.hi = hl.first;
+  op.lo = hl.second;
+  const unsigned long long Kp = (unsigned long long)((s.nv + 63) / 64 * 64), nv = s.nv;
+  const unsigned long long dims[4] = {Kp, nv, nv, (unsigned long long)c->chunk_nb};
+  const unsigned long long str[3] = {Kp * 2, Kp * 2 * nv, Kp * 2 * nv * nv};
+  const unsigned bx[4] = {64, 16, 8, 1};
+  encode_split(op, key, dims, str, bx);
+  return op;
 }
 
 int occ_of(const Ord &o, int pos) { return pos == 0 ? o.p : pos == 1 ? o.q : o.r; }
@@ -1697,8 +1814,15 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     c->zero(Z4, s.NJ * s.no * NO);
     c->zero(yv, s.NJ);
     // W[J][k][c] = sum_{b,D} Y1[k][b][c][D] Lt[J][NO+b][NO+D] - sum_{L,j} Y2[j][k][c][L] Lt[J][L][j]
-    sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.NV;
-    c->bstc1(Y1, Lt + NO * nmo + NO, W, sh, 1.0, mk_item(0, 0, 0, {s.gk, s.gc, s.gb, 1, 0}, {nmo, 1, 0, s.lJ, 0}, {s.nv, 1, s.no * s.nv, 0}), "sg1");
+    const bool tc = split_mode(c);
+    if (tc) {
+      const SplitOp &a = make_split_k2(c, "Y1:kc", Y1, s.no, s.nv, s.nv, s.NV, s.gk, s.gc, s.gb, 1, 128, true);
+      tc_flat_gemm(c, a, c->splits.at("LvV:J"), s.no * s.nv, s.NJ, s.nv * s.NV, W, (int)s.nv, s.nv, 1,
+                   s.no * s.nv, 1.0, "sg1");
+    } else {
+      sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.NV;
+      c->bstc1(Y1, Lt + NO * nmo + NO, W, sh, 1.0, mk_item(0, 0, 0, {s.gk, s.gc, s.gb, 1, 0}, {nmo, 1, 0, s.lJ, 0}, {s.nv, 1, s.no * s.nv, 0}), "sg1");
+    }
     sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.NJ; sh.K1 = NO; sh.K2 = s.no;
     c->bstc1(Y2, Lt, W, sh, -1.0, mk_item(0, 0, 0, {s.ok, s.oc, 1, s.oj, 0}, {nmo, 1, 0, s.lJ, 0}, {s.nv, 1, s.no * s.nv, 0}), "sg2");
     // sigma[E][k] += sum_{J,c} W[J][k][c] Lt[J][NO+c][NO+E]
@@ -1708,8 +1832,14 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     sh = Shape{}; sh.M1 = s.nv; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.no;
     c->bstc1(W, Lt, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv, s.nv, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg4");
     // Z2[J][b][D] = sum_{c,k} Y1[k][b][c][D] Lt[J][NO+c][k];  sigma[b][M] -= sum_{J,D} Z2 Lt[J][M][NO+D]
-    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
-    c->bstc1(Y1, Lt + NO * nmo, Z2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {nmo, 1, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg5");
+    if (tc) {
+      const SplitOp &a = make_split_k2(c, "Y1:bD", Y1, s.nv, s.NV, s.nv, s.no, s.gb, 1, s.gc, s.gk, 128, true);
+      tc_flat_gemm(c, a, c->splits.at("Lvo:J"), s.nv * s.NV, s.NJ, s.nv * s.no, Z2, (int)s.NV, s.NV, 1,
+                   s.nv * s.NV, 1.0, "sg5");
+    } else {
+      sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
+      c->bstc1(Y1, Lt + NO * nmo, Z2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {nmo, 1, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg5");
+    }
     sh = Shape{}; sh.M1 = s.nv; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.NV;
     c->bstc1(Z2, Lt + NO, sig1, sh, -1.0, mk_item(0, 0, 0, {s.NV, 0, s.nv * s.NV, 1, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg6");
     // Z4[J][j][L] = sum_{c,k} Y2[j][k][c][L] Lt[J][NO+c][k];  sigma[E][j] -= sum_{J,L} Lt[J][L][NO+E] Z4
@@ -1736,8 +1866,14 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     c->bstc1(Lt + NO, Q, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.lJ, nmo, 0}, {s.no * NO, NO, 0, 1, 0}, {NO, 0, 1, 0}), "sg14");
     // P2 term: Q2[J][b][D] = sum_{c,k} P2[k][b][c][D] Lt[J][k][NO+c]; sigma[D][L] -= sum_{J,b} Q2 Lt[J][L][NO+b]
     c->zero(Q2, s.NJ * s.nv * s.NV);
-    sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
-    c->bstc1(P2, Lt + NO, Q2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {1, nmo, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg15");
+    if (tc) {
+      const SplitOp &a = make_split_k2(c, "P2:bD", P2, s.nv, s.NV, s.nv, s.no, s.gb, 1, s.gc, s.gk, 128, true);
+      tc_flat_gemm(c, a, c->splits.at("Lov:J"), s.nv * s.NV, s.NJ, s.nv * s.no, Q2, (int)s.NV, s.NV, 1,
+                   s.nv * s.NV, 1.0, "sg15");
+    } else {
+      sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.NV; sh.N1 = s.NJ; sh.K1 = s.nv; sh.K2 = s.no;
+      c->bstc1(P2, Lt + NO, Q2, sh, 1.0, mk_item(0, 0, 0, {s.gb, 1, s.gc, s.gk, 0}, {1, nmo, 0, s.lJ, 0}, {s.NV, 1, s.nv * s.NV, 0}), "sg15");
+    }
     sh = Shape{}; sh.M1 = s.NV; sh.N1 = NO; sh.K1 = s.NJ; sh.K2 = s.nv;
     c->bstc1(Q2, Lt + NO, sig1, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.nv * s.NV, s.NV, 0}, {s.lJ, 1, 0, nmo, 0}, {NO, 0, 1, 0}), "sg16");
   }
@@ -1830,17 +1966,31 @@ void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, 
   voff = c->items.at(key + ":off").first;
   vstr = c->items.at(key + ":str").first;
   vhave = c->items.at(key + ":have").first;
-  const size_t smem = 2 * (size_t)s.no * 256 * sizeof(double);
-  check_cuda(cudaFuncSetAttribute(pair_dots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem), "pair_dots smem");
+  const bool f32 = split_mode(c);
+  const size_t smem = 2 * (size_t)s.no * 257 * (f32 ? sizeof(float) : sizeof(double));
   const long long np = ch.p1 - ch.p0;
-  dim3 grid((unsigned)((s.nv3 + 255) / 256), (unsigned)(np * s.no));
-  c->launch("pair_dots_kernel", 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3, [&] {
-    pair_dots_kernel<<<grid, 256, smem, c->stream>>>(X, Y, static_cast<const long long *>(voff),
-                                                     static_cast<const int *>(vstr),
-                                                     static_cast<const char *>(vhave), (int)s.no,
-                                                     (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
-  });
+  const long long ntiles = ((s.nv + 3) / 4) * ((s.nv + 7) / 8) * ((s.nv + 7) / 8);
+  // about eight resident blocks' worth per SM over the whole launch
+  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, (8 * 152 + np * s.no - 1) / (np * s.no)));
+  dim3 grid((unsigned)gx, (unsigned)(np * s.no));
+  const double fl = 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3;
+  if (f32) {
+    check_cuda(cudaFuncSetAttribute(pair_dots_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem), "pair_dots smem");
+    c->launch("pair_dots_kernel", fl, [&] {
+      pair_dots_f32_kernel<<<grid, 256, smem, c->stream>>>(
+          X, Y, static_cast<const long long *>(voff), static_cast<const int *>(vstr),
+          static_cast<const char *>(vhave), (int)s.no, (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
+    });
+  } else {
+    check_cuda(cudaFuncSetAttribute(pair_dots_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem), "pair_dots smem");
+    c->launch("pair_dots_kernel", fl, [&] {
+      pair_dots_f64_kernel<<<grid, 256, smem, c->stream>>>(
+          X, Y, static_cast<const long long *>(voff), static_cast<const int *>(vstr),
+          static_cast<const char *>(vhave), (int)s.no, (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
+    });
+  }
 }
 
 // out[c][d] += alpha sum_{pqr} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
@@ -2170,6 +2320,7 @@ extern "C" int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *d, int precision,
         d->n_act_occ > d->n_occ || d->n_act_vir > d->n_vir || d->n_chol < 1)
       throw Error{MLCC3_ERR_ARG, "invalid dimensions"};
     if (d->n_occ + d->n_vir > 46340) throw Error{MLCC3_ERR_ARG, "n_mo too large"};
+    if (d->n_act_occ > 32) throw Error{MLCC3_ERR_ARG, "n_o above 32 is not supported"};
     if (precision != MLCC3_FP64 && precision != MLCC3_SPLIT_BF16X3)
       throw Error{MLCC3_ERR_ARG, "unknown precision mode"};
     int dev = 0;

@@ -121,7 +121,9 @@ def make_system(NO, NV, no, nv, NJ, seed=DEFAULT_SEED, core=False, t2_norm=None)
         eps[0] = -10.0
     r = _rng(seed, 2)
     chol = r.normal(0.0, 0.05, (NJ, nmo, nmo))
-    chol = np.triu(chol) + np.transpose(np.triu(chol, 1), (0, 2, 1))
+    for J in range(NJ):  # mirror the upper triangle, one vector at a time
+        cj = chol[J]
+        cj[...] = np.triu(cj) + np.triu(cj, 1).T
     r = _rng(seed, 3)
     t1 = r.normal(0.0, 0.01, (NV, NO))
     # MP2-like doubles from the bare integrals (AI|BJ).
