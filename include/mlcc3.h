@@ -125,6 +125,42 @@ int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
 int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
                               const double *Dm0, const double *mu, double *f);
 
+/* Batched sweep (Sec. 3: the triples right transformation is the part of a
+ * Davidson iteration that scales as N_V n_v^3 n_o^3; the paper applies it per
+ * trial vector): the right Jacobian transformations of several systems, each
+ * with its own context and possibly different (n_o, n_v, N_V), and of all
+ * their trial vectors, run as one CUDA graph launch.  Each system runs on its
+ * own stream, forked from and joined back into `cuda_stream` inside the graph,
+ * so that small systems fill the GPU together.
+ *   mlcc3_sweep_create   contexts (built, same device, each once); with tune,
+ *                        the first run times, per system, the candidates 0, 2,
+ *                        4, 8 of "bstc_fill" on one trial vector and keeps the
+ *                        fastest, then keeps the faster of the concurrent and
+ *                        the serial graph.  Contexts whose "chunk_blocks" is 0
+ *                        get a share of half the free device memory.
+ *   mlcc3_sweep_set_system  n_vec trial vectors of system `sys`: R1, R2, rho1,
+ *                        rho2 are DEVICE arrays with the shapes of
+ *                        mlcc3_jacobian_right; the graph reads and writes these
+ *                        addresses, so they must stay valid.
+ *   mlcc3_sweep_run      omega[sum of n_vec] (host, system-major).  The first
+ *                        run (and the first after mlcc3_sweep_set_system,
+ *                        mlcc3_build_integrals or a change of "chunk_blocks" on
+ *                        any of the contexts) runs eagerly once, tunes, and
+ *                        captures the graph; later runs copy omega to the
+ *                        device and replay it.  Results as mlcc3_jacobian_right.
+ *                        Blocks the host until the graph has finished.
+ *   mlcc3_sweep_info     a JSON summary (graph nodes, tuning choices and times).
+ * Calls on the contexts themselves may be mixed with sweeps; a sweep does not
+ * rely on their state (it rebuilds tau in every replay).  Not thread safe. */
+typedef struct mlcc3_sweep mlcc3_sweep;
+int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int n_sys, int tune,
+                       void *cuda_stream);
+int mlcc3_sweep_set_system(mlcc3_sweep *sweep, int sys, int n_vec, const double *R1,
+                           const double *R2, double *rho1, double *rho2);
+int mlcc3_sweep_run(mlcc3_sweep *sweep, const double *omega);
+int mlcc3_sweep_info(mlcc3_sweep *sweep, char *buf, size_t len);
+void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
+
 /* Tuning parameters of a context (no counterpart in the paper; results stay
  * within the precision mode's error bounds for every accepted value):
  *   "tc_kcap"  longest FP32 accumulation chain of the split-precision tensor
@@ -133,6 +169,9 @@ int mlcc3_oscillator_strength(mlcc3_ctx *ctx, double omega, const double *D0m,
  *              densities, Cholesky-index builds); 0 = unlimited.  The tensor
  *              cores accumulate with truncation, so the error of a chain
  *              grows with its length.  Default 16 (K = 1024).  Range 0..4096.
+ *   "bstc_fill"  split-K target of the FP64 strided contractions: a launch
+ *              with few output tiles and a long reduction splits K until about
+ *              bstc_fill x 152 CTAs run; 0 never splits.  Default 4.  Range 0..64.
  *   "chunk_blocks"  most unique batches whose triples blocks (n_v^3 each) the
  *              context holds on the device at once; larger systems are swept
  *              in chunks (the densities by ranges of occupied indices, which

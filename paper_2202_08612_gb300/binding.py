@@ -26,7 +26,9 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_triples_omega", "mlcc3_jacobian_right", "mlcc3_jacobian_left",
            "mlcc3_transition_density", "mlcc3_oscillator_strength", "mlcc3_debug_fetch",
            "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
-           "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param")
+           "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param",
+           "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
+           "mlcc3_sweep_destroy")
 
 
 class MLCC3Error(RuntimeError):
@@ -71,6 +73,12 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_debug_profile.argtypes = [P, I]
     lib.mlcc3_debug_tc_gemm.argtypes = [P, P, P, I, I, I]
     lib.mlcc3_set_param.argtypes = [P, ctypes.c_char_p, ctypes.c_longlong]
+    lib.mlcc3_sweep_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), I, I, P]
+    lib.mlcc3_sweep_set_system.argtypes = [P, I, I, P, P, P, P]
+    lib.mlcc3_sweep_run.argtypes = [P, P]
+    lib.mlcc3_sweep_info.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.mlcc3_sweep_destroy.argtypes = [P]
+    lib.mlcc3_sweep_destroy.restype = None
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -195,3 +203,51 @@ class Context:
 
     def nbatches(self) -> int:
         return int(self.lib.mlcc3_debug_nbatches(self.h))
+
+
+class Sweep:
+    """mlcc3_sweep_*: right Jacobian transformations of several systems in one
+    captured CUDA graph (see the header).  Vectors must be device tensors; the
+    sweep keeps references to them because the graph reads their addresses."""
+
+    def __init__(self, contexts, tune=True, stream=None):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.h for c in self.contexts])
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(stream)
+        self._check(self.lib.mlcc3_sweep_create(ctypes.byref(h), arr, len(self.contexts),
+                                                1 if tune else 0, s))
+        self.h = h
+        self._keep = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MLCC3Error(rc, self.lib.mlcc3_last_error().decode())
+
+    def set_system(self, q, R1, R2, rho1, rho2):
+        n_vec = int(R1.shape[0])
+        self._keep[q] = (R1, R2, rho1, rho2)
+        self._check(self.lib.mlcc3_sweep_set_system(self.h, q, n_vec, _ptr(R1), _ptr(R2),
+                                                    _ptr(rho1), _ptr(rho2)))
+
+    def run(self, omega):
+        w = np.ascontiguousarray(omega, dtype=np.float64)
+        self._check(self.lib.mlcc3_sweep_run(self.h, w.ctypes.data))
+
+    def info(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.lib.mlcc3_sweep_info(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mlcc3_sweep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

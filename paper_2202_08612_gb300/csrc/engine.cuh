@@ -74,6 +74,10 @@ struct mlcc3_ctx {
   int device;
   std::vector<uint8_t> core;
   bool built = false;
+  unsigned long long build_gen = 0;  // counts mlcc3_build_integrals calls
+  // split-K target of the FP64 strided contraction: when few output tiles
+  // face a long reduction, split K until about bstc_fill * 152 CTAs run (0 = never)
+  int bstc_fill = 4;
   bool tau_valid = false;   // tau3 / its contravariant blocks match the current build
   // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)
@@ -86,6 +90,9 @@ struct mlcc3_ctx {
   std::vector<mlcc3::Chunk> parts, parts_cvs, groups;
   long long chunk_nb = 0;       // blocks of the chunk being processed
   std::string tau_key;          // chunk whose tau / contravariant tau the buffers hold
+  // when set, the R3 / L3 finishers read omega from this device address instead
+  // of their by-value argument (a sweep's captured graph replays with new omega)
+  const double *omega_dev = nullptr;
 
   // persistent device arrays (FP64)
   double *eps = nullptr, *t1 = nullptr, *Lt = nullptr, *t2c = nullptr, *t2x = nullptr;

@@ -177,9 +177,11 @@ constexpr int TR = 32;
 __global__ void __launch_bounds__(256) triples_build_kernel(const TripTerms terms,
                                                             const TripItem *__restrict__ items,
                                                             const double *__restrict__ eps, int NO,
-                                                            int nv, double omega,
+                                                            int nv, double omega_v,
+                                                            const double *__restrict__ omega_p,
                                                             double *__restrict__ out,
                                                             int *__restrict__ status) {
+  const double omega = omega_p ? *omega_p : omega_v;  // device-resident omega (graph replay)
   __shared__ double Ps[TT][TR + 1];
   __shared__ double Qs[TT * TT][TR + 1];
   const TripTerm *sterm = terms.t;
@@ -467,12 +469,13 @@ __device__ __forceinline__ double recip_newton(double d) {
 // two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
 // Only kinds 2 and 3 of `terms` are evaluated here (summed over the six pair
 // permutations; in FP32 when fp32_rank1 is set, the split-precision mode).
-// The denominator is formed in FP64.
+// The denominator is formed in FP64; omega is read from omega_p when it is set.
 __global__ void triples_finish_kernel(const float *__restrict__ W, const TripItem *__restrict__ items,
                                       int nitems, const TripTerms terms,
-                                      const double *__restrict__ eps, int NO, int nv, double omega,
-                                      int fp32_rank1, double *__restrict__ out,
-                                      int *__restrict__ status) {
+                                      const double *__restrict__ eps, int NO, int nv, double omega_v,
+                                      const double *__restrict__ omega_p, int fp32_rank1,
+                                      double *__restrict__ out, int *__restrict__ status) {
+  const double omega = omega_p ? *omega_p : omega_v;  // device-resident omega (graph replay)
   const int nv3 = nv * nv * nv;
   if ((int)blockIdx.y >= nitems) return;
   const TripItem it = items[blockIdx.y];

@@ -36,7 +36,7 @@ __global__ void pair_dots_f64_kernel(const double *, const double *, const long 
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
-                                     double, double *, int *);
+                                     double, const double *, double *, int *);
 __global__ void contra3_kernel(const double *, double *, long long, int);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 __global__ void c2_block_kernel(const double *, double *, int, int, int, int);
@@ -47,7 +47,8 @@ __global__ void sd_dot_kernel(const double *, const double *, const double *, co
 __global__ void density_norm_kernel(double *, const double *, const double *, const double *,
                                     int, int);
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
-                                      const double *, int, int, double, int, double *, int *);
+                                      const double *, int, int, double, const double *, int,
+                                      double *, int *);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
@@ -227,8 +228,8 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
   // split K when few output tiles face a long reduction
   const long long K = sh.K1 * sh.K2 * sh.K3;
   long long ksplit = 1;
-  if (tiles * nitems < 2 * 152 && K >= 2048) {
-    ksplit = std::min<long long>((4 * 152 + tiles * nitems - 1) / (tiles * nitems), K / 512);
+  if (bstc_fill > 0 && tiles * nitems < 2 * 152 && K >= 2048) {
+    ksplit = std::min<long long>((bstc_fill * 152LL + tiles * nitems - 1) / (tiles * nitems), K / 512);
     ksplit = std::max<long long>(1, std::min<long long>(ksplit, 65535));
   }
   if (ksplit > 1) {
@@ -502,7 +503,7 @@ void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string
   for (auto &t : terms) fl += 12.0 * nv3 * (t.kind <= 1 ? (double)t.R : 1.0);
   c->launch("triples_build_kernel", fl * n, [&] {
     triples_build_kernel<<<grid, 256, 0, c->stream>>>(tt, db, c->eps, (int)c->NO, (int)c->nv,
-                                                      omega, out, c->status);
+                                                      omega, c->omega_dev, out, c->status);
   });
   check_cuda(cudaGetLastError(), "triples_build launch");
 }
@@ -953,8 +954,8 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     dim3 grid((unsigned)std::min<long long>((s.nv3 + 255) / 256, 1024), (unsigned)nbc);
     c->launch("triples_finish_kernel", 0.0, [&] {
       triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps,
-                                                         (int)s.NO, (int)s.nv, omega, 1, out,
-                                                         c->status);
+                                                         (int)s.NO, (int)s.nv, omega, c->omega_dev,
+                                                         1, out, c->status);
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
@@ -1627,6 +1628,7 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   if (split_mode(c)) build_split_persistent(c);
   c->tau_valid = false;
   c->built = true;
+  c->build_gen += 1;
 }
 
 static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_out) {
@@ -1649,8 +1651,12 @@ static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_ou
   finalize(c, Zb, o2, 0);
 }
 
+// omega: host array of n_vec frequencies, or (omega_dev set) a device array
+// that the R3 finishers read, so that a captured graph can be replayed with new
+// frequencies.
 static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, const double *R1_in,
-                              const double *R2_in, double *rho1_out, double *rho2_out) {
+                              const double *R2_in, double *rho1_out, double *rho2_out,
+                              const double *omega_dev = nullptr) {
   S s(c);
   const bool cvs = !c->core.empty();
   const std::vector<Chunk> &chunks = cvs ? c->parts_cvs : c->parts;
@@ -1666,7 +1672,8 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
     const double *R2 = R2all + (size_t)v * s.blk();
     double *rho1 = rho1all + (size_t)v * s.NV * s.NO;
     double *rho2 = rho2all + (size_t)v * s.blk();
-    if (!(std::fabs(omega[v]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
+    if (!omega_dev && !(std::fabs(omega[v]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
+    const double wv = omega_dev ? 0.0 : omega[v];
     launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
       c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)s.NO, (int)s.NV); });
     });
@@ -1681,7 +1688,9 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
       double *R3 = c->buf("R3", (size_t)ch.nb * s.nv3);
       double *R3t = c->buf("R3t", (size_t)ch.nb * s.nv3);
       // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
-      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, omega[v], R3);
+      c->omega_dev = omega_dev ? omega_dev + v : nullptr;
+      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3);
+      c->omega_dev = nullptr;
       contra3(c, R3, R3t, ch.nb);
       BackSet b;
       b.cs = 0.5; b.Gs = c->Govov;
@@ -2483,6 +2492,9 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     if (n == "tc_kcap") {
       if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, "tc_kcap out of range 0..4096"};
       c->tc_kcap = (int)value;
+    } else if (n == "bstc_fill") {
+      if (value < 0 || value > 64) throw Error{MLCC3_ERR_ARG, "bstc_fill out of range 0..64"};
+      c->bstc_fill = (int)value;
     } else if (n == "chunk_blocks") {
       if (value < 0) throw Error{MLCC3_ERR_ARG, "chunk_blocks must be >= 0"};
       c->chunk_blocks = value;
@@ -2520,4 +2532,362 @@ extern "C" int mlcc3_debug_kernel_stats(mlcc3_ctx *c, int index, char *name, siz
 
 extern "C" long long mlcc3_debug_nbatches(mlcc3_ctx *c) {
   return c ? (long long)c->batches.size() : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweep: the right Jacobian transformations of several systems (each
+// its own context) and all of their trial vectors, captured once into a CUDA
+// graph and replayed.  Systems run on their own streams, forked from and joined
+// back into the sweep's stream, so small systems fill the GPU together; omega
+// lives in device memory, so a replay takes new frequencies without a new
+// capture.  Before the first capture an autotuner times, per system, the
+// split-K target of the FP64 contractions, and then the concurrent against the
+// serial graph.
+// ---------------------------------------------------------------------------
+struct mlcc3_sweep {
+  struct Sys {
+    mlcc3_ctx *c = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t join = nullptr;
+    int n_vec = 0;
+    const double *R1 = nullptr, *R2 = nullptr;
+    double *rho1 = nullptr, *rho2 = nullptr;
+    long long w0 = 0;  // first frequency of this system in the omega array
+    unsigned long long build_gen = 0;
+    int chunk_gen = 0;
+    int fill = 4;
+    std::vector<double> fill_ms;  // tuning times per candidate
+  };
+  std::vector<Sys> sys;
+  int device = 0;
+  cudaStream_t s0 = nullptr;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  double *omega_dev = nullptr, *omega_pin = nullptr;
+  long long n_omega = 0;
+  int *status_pin = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t nodes = 0;
+  int tune = 1, tuned = 0, multi = 1;
+  bool own_s0 = false;
+  double ms_multi = 0.0, ms_serial = 0.0;
+};
+
+namespace {
+
+const int kSweepFill[4] = {0, 2, 4, 8};
+
+// The systems' transformations on their streams (multi) or one after another
+// on the sweep's stream.  Every pass rebuilds tau and converts the layouts it
+// reads, so that a captured graph depends on no state left by other calls.
+void sweep_pass(mlcc3_sweep *sw, bool multi, int only = -1, int nvec_cap = 0) {
+  check_cuda(cudaEventRecord(sw->fork, sw->s0), "sweep fork");
+  for (size_t q = 0; q < sw->sys.size(); ++q) {
+    if (only >= 0 && (int)q != only) continue;
+    mlcc3_sweep::Sys &y = sw->sys[q];
+    if (y.n_vec == 0) continue;
+    mlcc3_ctx *c = y.c;
+    const cudaStream_t saved = c->stream;
+    const bool prof = c->prof;
+    c->stream = multi ? y.st : sw->s0;
+    c->prof = false;  // no per-launch events inside graphs
+    try {
+      if (multi) check_cuda(cudaStreamWaitEvent(y.st, sw->fork, 0), "sweep wait");
+      c->tau_valid = false;
+      for (auto &t : c->tri) t = mlcc3_ctx::TriSlot{};
+      const int nv = nvec_cap > 0 ? std::min(nvec_cap, y.n_vec) : y.n_vec;
+      do_jacobian_right(c, nv, nullptr, y.R1, y.R2, y.rho1, y.rho2, sw->omega_dev + y.w0);
+      if (multi) {
+        check_cuda(cudaEventRecord(y.join, y.st), "sweep join");
+        check_cuda(cudaStreamWaitEvent(sw->s0, y.join, 0), "sweep join wait");
+      }
+    } catch (...) {
+      c->stream = saved;
+      c->prof = prof;
+      throw;
+    }
+    c->stream = saved;
+    c->prof = prof;
+  }
+}
+
+double sweep_time(mlcc3_sweep *sw, const std::function<void()> &f) {
+  check_cuda(cudaEventRecord(sw->t0, sw->s0), "sweep t0");
+  f();
+  check_cuda(cudaEventRecord(sw->t1, sw->s0), "sweep t1");
+  check_cuda(cudaEventSynchronize(sw->t1), "sweep sync");
+  float ms = 0.f;
+  check_cuda(cudaEventElapsedTime(&ms, sw->t0, sw->t1), "sweep elapsed");
+  return ms;
+}
+
+cudaGraphExec_t sweep_capture(mlcc3_sweep *sw, bool multi, size_t *nodes) {
+  check_cuda(cudaStreamBeginCapture(sw->s0, cudaStreamCaptureModeRelaxed), "begin capture");
+  try {
+    sweep_pass(sw, multi);
+  } catch (...) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(sw->s0, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraph_t g = nullptr;
+  check_cuda(cudaStreamEndCapture(sw->s0, &g), "end capture");
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  cudaGraphDestroy(g);
+  check_cuda(e, "graph instantiate");
+  *nodes = n;
+  return ex;
+}
+
+void sweep_check_status(mlcc3_sweep *sw) {
+  for (size_t q = 0; q < sw->sys.size(); ++q)
+    check_cuda(cudaMemcpyAsync(sw->status_pin + q, sw->sys[q].c->status, sizeof(int),
+                               cudaMemcpyDeviceToHost, sw->s0), "sweep status");
+  check_cuda(cudaStreamSynchronize(sw->s0), "sweep sync");
+  int bits = 0;
+  for (size_t q = 0; q < sw->sys.size(); ++q) bits |= sw->status_pin[q];
+  if (bits) {
+    for (auto &y : sw->sys) check_cuda(cudaMemsetAsync(y.c->status, 0, sizeof(int), sw->s0), "reset");
+    check_cuda(cudaStreamSynchronize(sw->s0), "sweep sync");
+    if (bits & 2) throw Error{MLCC3_ERR_TIMEOUT, "tensor-core pipeline wait timed out"};
+    throw Error{MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk} - omega| < 1e-3 in a triples block"};
+  }
+}
+
+bool sweep_stale(const mlcc3_sweep *sw) {
+  if (!sw->exec) return true;
+  for (auto &y : sw->sys)
+    if (y.build_gen != y.c->build_gen || y.chunk_gen != y.c->chunk_gen) return true;
+  return false;
+}
+
+void sweep_prepare(mlcc3_sweep *sw) {
+  if (sw->exec) {
+    cudaGraphExecDestroy(sw->exec);
+    sw->exec = nullptr;
+  }
+  // eager pass: allocates every buffer and builds every plan the capture reads
+  sweep_pass(sw, true);
+  check_cuda(cudaStreamSynchronize(sw->s0), "sweep warm-up");
+  if (sw->tune && !sw->tuned) {
+    for (size_t q = 0; q < sw->sys.size(); ++q) {
+      mlcc3_sweep::Sys &y = sw->sys[q];
+      if (y.n_vec == 0) continue;
+      y.fill_ms.assign(4, 0.0);
+      int best = y.c->bstc_fill;
+      double best_ms = 1e300;
+      for (int f = 0; f < 4; ++f) {
+        y.c->bstc_fill = kSweepFill[f];
+        sweep_pass(sw, false, (int)q, 1);  // warm (split-K plans differ per candidate)
+        double ms = 1e300;
+        for (int r = 0; r < 2; ++r)
+          ms = std::min(ms, sweep_time(sw, [&] { sweep_pass(sw, false, (int)q, 1); }));
+        y.fill_ms[f] = ms;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = kSweepFill[f];
+        }
+      }
+      y.c->bstc_fill = y.fill = best;
+    }
+    size_t n_multi = 0, n_serial = 0;
+    cudaGraphExec_t gm = sweep_capture(sw, true, &n_multi);
+    cudaGraphExec_t gs = nullptr;
+    try {
+      gs = sweep_capture(sw, false, &n_serial);
+    } catch (...) {
+      cudaGraphExecDestroy(gm);
+      throw;
+    }
+    auto best_of = [&](cudaGraphExec_t g) {
+      double ms = 1e300;
+      for (int r = 0; r < 3; ++r)
+        ms = std::min(ms, sweep_time(sw, [&] { check_cuda(cudaGraphLaunch(g, sw->s0), "graph launch"); }));
+      return ms;
+    };
+    sw->ms_multi = best_of(gm);
+    sw->ms_serial = best_of(gs);
+    sw->multi = sw->ms_multi <= sw->ms_serial ? 1 : 0;
+    if (sw->multi) {
+      cudaGraphExecDestroy(gs);
+      sw->exec = gm;
+      sw->nodes = n_multi;
+    } else {
+      cudaGraphExecDestroy(gm);
+      sw->exec = gs;
+      sw->nodes = n_serial;
+    }
+    sw->tuned = 1;
+  } else {
+    sw->exec = sweep_capture(sw, sw->multi != 0, &sw->nodes);
+  }
+  for (auto &y : sw->sys) {
+    y.build_gen = y.c->build_gen;
+    y.chunk_gen = y.c->chunk_gen;
+  }
+}
+
+}  // namespace
+
+extern "C" int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int n_sys, int tune,
+                                  void *cuda_stream) {
+  return guarded([&] {
+    if (!out || !ctxs || n_sys < 1) throw Error{MLCC3_ERR_ARG, "null argument or n_sys < 1"};
+    *out = nullptr;
+    for (int q = 0; q < n_sys; ++q) require_built(ctxs[q]);
+    for (int q = 1; q < n_sys; ++q)
+      if (ctxs[q]->device != ctxs[0]->device) throw Error{MLCC3_ERR_ARG, "contexts on different devices"};
+    for (int q = 0; q < n_sys; ++q)
+      for (int r = 0; r < q; ++r)
+        if (ctxs[q] == ctxs[r]) throw Error{MLCC3_ERR_ARG, "a context appears twice"};
+    check_cuda(cudaSetDevice(ctxs[0]->device), "cudaSetDevice");
+    auto *sw = new mlcc3_sweep();
+    sw->device = ctxs[0]->device;
+    sw->tune = tune != 0;
+    try {
+      sw->s0 = static_cast<cudaStream_t>(cuda_stream);
+      if (!sw->s0) {  // graphs are not captured on the legacy default stream
+        check_cuda(cudaStreamCreateWithFlags(&sw->s0, cudaStreamNonBlocking), "stream");
+        sw->own_s0 = true;
+      }
+      check_cuda(cudaEventCreateWithFlags(&sw->fork, cudaEventDisableTiming), "event");
+      check_cuda(cudaEventCreate(&sw->t0), "event");
+      check_cuda(cudaEventCreate(&sw->t1), "event");
+      check_cuda(cudaMallocHost(&sw->status_pin, sizeof(int) * (size_t)n_sys), "cudaMallocHost");
+      // share the device memory: the systems' triples blocks are held together
+      size_t fr = 0, tot = 0;
+      check_cuda(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+      double demand = 0.0;
+      for (int q = 0; q < n_sys; ++q)
+        demand += 140.0 * (double)ctxs[q]->batches.size() * (double)(ctxs[q]->nv * ctxs[q]->nv * ctxs[q]->nv);
+      const double budget = 0.5 * (double)fr;
+      for (int q = 0; q < n_sys; ++q) {
+        mlcc3_ctx *c = ctxs[q];
+        mlcc3_sweep::Sys y;
+        y.c = c;
+        check_cuda(cudaStreamCreateWithFlags(&y.st, cudaStreamNonBlocking), "stream");
+        check_cuda(cudaEventCreateWithFlags(&y.join, cudaEventDisableTiming), "event");
+        sw->sys.push_back(y);
+        if (c->chunk_blocks == 0) {
+          const long long nb = (long long)c->batches.size();
+          c->chunk_blocks = demand <= budget ? std::max<long long>(1, nb)
+                                             : std::max<long long>(1, (long long)((double)nb * budget / demand));
+          make_chunks(c);
+        }
+      }
+    } catch (...) {
+      mlcc3_sweep_destroy(sw);
+      throw;
+    }
+    *out = sw;
+  });
+}
+
+extern "C" int mlcc3_sweep_set_system(mlcc3_sweep *sw, int q, int n_vec, const double *R1,
+                                      const double *R2, double *rho1, double *rho2) {
+  return guarded([&] {
+    if (!sw || q < 0 || q >= (int)sw->sys.size() || n_vec < 0)
+      throw Error{MLCC3_ERR_ARG, "bad sweep, system index or n_vec"};
+    if (n_vec > 0 && (!R1 || !R2 || !rho1 || !rho2)) throw Error{MLCC3_ERR_ARG, "null vector pointer"};
+    for (const void *p : {(const void *)R1, (const void *)R2, (const void *)rho1, (const void *)rho2}) {
+      if (!p) continue;
+      cudaPointerAttributes a{};
+      if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+          (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        throw Error{MLCC3_ERR_ARG, "sweep vectors must be device arrays"};
+      }
+    }
+    mlcc3_sweep::Sys &y = sw->sys[q];
+    y.n_vec = n_vec;
+    y.R1 = R1;
+    y.R2 = R2;
+    y.rho1 = rho1;
+    y.rho2 = rho2;
+    long long n = 0;
+    for (auto &z : sw->sys) {
+      z.w0 = n;
+      n += z.n_vec;
+    }
+    if (n > sw->n_omega) {
+      if (sw->omega_dev) cudaFree(sw->omega_dev);
+      if (sw->omega_pin) cudaFreeHost(sw->omega_pin);
+      sw->omega_dev = nullptr;
+      sw->omega_pin = nullptr;
+      check_cuda(cudaMalloc(&sw->omega_dev, sizeof(double) * (size_t)n), "cudaMalloc omega");
+      check_cuda(cudaMallocHost(&sw->omega_pin, sizeof(double) * (size_t)n), "cudaMallocHost omega");
+      sw->n_omega = n;
+    }
+    if (sw->exec) {
+      cudaGraphExecDestroy(sw->exec);
+      sw->exec = nullptr;
+    }
+  });
+}
+
+extern "C" int mlcc3_sweep_run(mlcc3_sweep *sw, const double *omega) {
+  return guarded([&] {
+    if (!sw) throw Error{MLCC3_ERR_ARG, "null sweep"};
+    long long n = 0;
+    for (auto &y : sw->sys) n += y.n_vec;
+    if (n == 0) return;
+    if (!omega) throw Error{MLCC3_ERR_ARG, "null omega"};
+    for (long long v = 0; v < n; ++v)
+      if (!(std::fabs(omega[v]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
+    check_cuda(cudaSetDevice(sw->device), "cudaSetDevice");
+    std::memcpy(sw->omega_pin, omega, sizeof(double) * (size_t)n);
+    check_cuda(cudaMemcpyAsync(sw->omega_dev, sw->omega_pin, sizeof(double) * (size_t)n,
+                               cudaMemcpyHostToDevice, sw->s0), "omega upload");
+    for (auto &y : sw->sys) {  // pending work of the contexts' own streams comes first
+      check_cuda(cudaStreamSynchronize(y.c->stream), "context sync");
+      y.c->collect_events();
+    }
+    if (sweep_stale(sw)) sweep_prepare(sw);
+    check_cuda(cudaGraphLaunch(sw->exec, sw->s0), "graph launch");
+    sweep_check_status(sw);
+  });
+}
+
+extern "C" int mlcc3_sweep_info(mlcc3_sweep *sw, char *buf, size_t len) {
+  return guarded([&] {
+    if (!sw || !buf || len == 0) throw Error{MLCC3_ERR_ARG, "null argument"};
+    std::string s = "{\"graph_nodes\": " + std::to_string(sw->nodes) +
+                    ", \"concurrent\": " + std::to_string(sw->multi) +
+                    ", \"ms_concurrent\": " + std::to_string(sw->ms_multi) +
+                    ", \"ms_serial\": " + std::to_string(sw->ms_serial) + ", \"systems\": [";
+    for (size_t q = 0; q < sw->sys.size(); ++q) {
+      const auto &y = sw->sys[q];
+      s += std::string(q ? ", " : "") + "{\"n_vec\": " + std::to_string(y.n_vec) +
+           ", \"chunk_blocks\": " + std::to_string(y.c->chunk_blocks) +
+           ", \"bstc_fill\": " + std::to_string(y.c->bstc_fill) + ", \"fill_ms\": [";
+      for (size_t f = 0; f < y.fill_ms.size(); ++f)
+        s += std::string(f ? ", " : "") + std::to_string(y.fill_ms[f]);
+      s += "]}";
+    }
+    s += "]}";
+    std::snprintf(buf, len, "%s", s.c_str());
+  });
+}
+
+extern "C" void mlcc3_sweep_destroy(mlcc3_sweep *sw) {
+  if (!sw) return;
+  cudaStreamSynchronize(sw->s0);
+  if (sw->exec) cudaGraphExecDestroy(sw->exec);
+  for (auto &y : sw->sys) {
+    if (y.st) {
+      cudaStreamSynchronize(y.st);
+      cudaStreamDestroy(y.st);
+    }
+    if (y.join) cudaEventDestroy(y.join);
+  }
+  for (cudaEvent_t e : {sw->fork, sw->t0, sw->t1})
+    if (e) cudaEventDestroy(e);
+  if (sw->omega_dev) cudaFree(sw->omega_dev);
+  if (sw->omega_pin) cudaFreeHost(sw->omega_pin);
+  if (sw->status_pin) cudaFreeHost(sw->status_pin);
+  if (sw->own_s0 && sw->s0) cudaStreamDestroy(sw->s0);
+  delete sw;
 }

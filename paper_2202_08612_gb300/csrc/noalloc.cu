@@ -19,7 +19,7 @@ namespace mlcc3 {
 void set_last_error(const std::string &msg);
 __global__ void bstc_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
-                                     double, double *, int *);
+                                     double, const double *, double *, int *);
 __global__ void contra3_kernel(const double *, double *, long long, int);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 }  // namespace mlcc3
@@ -169,7 +169,7 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
   tt.t[1] = TripTerm{1, (int)NO, -1.0, c->Tl, c->Go, {ti, ta, tb, 1}, {oj, ok, oc, 1}};
   const long long nt = (nv + 7) / 8;
   triples_build_kernel<<<dim3((unsigned)(nt * nt * nt), (unsigned)nb), 256, 0, st>>>(
-      tt, dbatch, c->eps, (int)NO, (int)nv, 0.0, tau, c->status);
+      tt, dbatch, c->eps, (int)NO, (int)nv, 0.0, nullptr, tau, c->status);
   for (long long b0 = 0; b0 < nb; b0 += 65535) {
     const long long nbc = std::min<long long>(65535, nb - b0);
     dim3 cg((unsigned)std::min<long long>((nv3 + 255) / 256, 1024), (unsigned)nbc);
