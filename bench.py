@@ -32,6 +32,9 @@ WORKLOADS = {
     "guanine_like_small": (20, 200, 12, 60, 600, 1),
     "tiny": (6, 24, 4, 8, 72, 1),
 }
+# uneven systems of the batched sweep, (n_o, n_v, N_V), N_O = n_o + 8, N_J = 3 N_V
+SWEEP_SYSTEMS = [(8, 40, 120), (11, 60, 216), (14, 80, 312), (18, 100, 408), (21, 120, 504),
+                 (24, 140, 600)]
 UNITS_PER_STEP = 4 + 8 + 8 + 10 + 10 + 16      # per state
 FP64_PEAK_TFLOPS = 1.25                        # nominal GB300 FP64 (ALU bound)
 
@@ -348,13 +351,85 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+def run_sweep(args):
+    """Batched sweep: right transformations of --vectors trial vectors on each of
+    the six uneven systems, one captured graph per sweep (mlcc3_sweep_*), timed
+    against the same transformations issued eagerly, system after system."""
+    import torch
+    from paper_2202_08612_gb300 import binding, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = binding.MLCC3_SPLIT_BF16X3 if args.precision == "split" else binding.MLCC3_FP64
+    ctxs, vecs, omegas, flops = [], [], [], 0.0
+    for q, (no, nv, NV) in enumerate(SWEEP_SYSTEMS):
+        NO, NJ = no + 8, 3 * NV
+        sysq = synth.make_system(NO, NV, no, nv, NJ, seed=2022 + q)
+        st = synth.make_states(sysq, args.vectors, seed=3022 + q)
+        d = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev)
+        c = binding.Context(NO, NV, no, nv, NJ, precision=prec)
+        c.build_integrals(d(sysq.chol), d(sysq.t1), d(sysq.eps), d(sysq.t2c), d(sysq.t2x))
+        R1, R2 = d(st.R1), d(st.R2)
+        rho1, rho2 = torch.zeros_like(R1), torch.zeros_like(R2)
+        ctxs.append(c)
+        vecs.append((R1, R2, rho1, rho2))
+        omegas.append(st.omega)
+        flops += 8.0 * NV * nv ** 3 * no ** 3 * args.vectors
+        del sysq, st
+    sw = binding.Sweep(ctxs, tune=True)
+    for q, v in enumerate(vecs):
+        sw.set_system(q, *v)
+    w = np.concatenate(omegas)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(f, n):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / n
+
+    for _ in range(args.warmup):
+        sw.run(w)
+    with ClockSampler(0) as clk:
+        t_graph = timed(lambda: sw.run(w), args.steps)
+
+    def eager():
+        for c, (R1, R2, rho1, rho2), om in zip(ctxs, vecs, omegas):
+            c.jacobian_right(om, R1, R2, rho1, rho2)
+    eager()
+    t_eager = timed(eager, max(1, args.steps // 2))
+    info = sw.info()
+    del stream
+    line = {"metric": METRIC, "value": flops / t_graph / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_graph * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if args.precision == "split" else "f64", "data": "synthetic",
+            "config": {"workload": "uneven_sweep: 6 systems (n_o,n_v,N_V) " +
+                       " ".join(f"({a},{b},{c})" for a, b, c in SWEEP_SYSTEMS) +
+                       f", N_O = n_o + 8, N_J = 3 N_V, {args.vectors} trial vectors each",
+                       "precision": args.precision},
+            "s_per_davidson_iter": t_graph, "eager": {"ms": t_eager * 1e3,
+                                                      "tflops": flops / t_eager / 1e12,
+                                                      "graph_speedup": t_eager / t_graph},
+            "graph": info, "clocks": clk.summary(), "algorithmic_flop_per_sweep": flops}
+    print(json.dumps(line), flush=True)
+    sw.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="guanine_like_small", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="guanine_like_small",
+                    choices=sorted(WORKLOADS) + ["uneven_sweep"])
+    ap.add_argument("--vectors", type=int, default=4,
+                    help="trial vectors per system of the uneven_sweep workload")
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the untimed FP64-path comparison step")
@@ -365,7 +440,9 @@ def main():
     if world > 1 and args.impl == "ours":
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.impl == "reference":
+    if args.impl == "ours" and args.workload == "uneven_sweep":
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args, rank)
     else:
         run_ours(args, rank, world, local_rank)

@@ -2681,9 +2681,9 @@ void sweep_prepare(mlcc3_sweep *sw) {
       double best_ms = 1e300;
       for (int f = 0; f < 4; ++f) {
         y.c->bstc_fill = kSweepFill[f];
-        sweep_pass(sw, false, (int)q, 1);  // warm (split-K plans differ per candidate)
+        // best of up to three runs on one trial vector (one when a run is long)
         double ms = 1e300;
-        for (int r = 0; r < 2; ++r)
+        for (int r = 0; r < 3 && (r == 0 || ms < 50.0); ++r)
           ms = std::min(ms, sweep_time(sw, [&] { sweep_pass(sw, false, (int)q, 1); }));
         y.fill_ms[f] = ms;
         if (ms < best_ms) {
@@ -2704,7 +2704,7 @@ void sweep_prepare(mlcc3_sweep *sw) {
     }
     auto best_of = [&](cudaGraphExec_t g) {
       double ms = 1e300;
-      for (int r = 0; r < 3; ++r)
+      for (int r = 0; r < 3 && (r == 0 || ms < 50.0); ++r)
         ms = std::min(ms, sweep_time(sw, [&] { check_cuda(cudaGraphLaunch(g, sw->s0), "graph launch"); }));
       return ms;
     };
@@ -2757,13 +2757,25 @@ extern "C" int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int
       check_cuda(cudaEventCreate(&sw->t0), "event");
       check_cuda(cudaEventCreate(&sw->t1), "event");
       check_cuda(cudaMallocHost(&sw->status_pin, sizeof(int) * (size_t)n_sys), "cudaMallocHost");
-      // share the device memory: the systems' triples blocks are held together
+      // share the device memory (the systems' triples blocks are held together):
+      // water-filling, smallest demand first, each takes all it needs or an
+      // equal share of what is left
       size_t fr = 0, tot = 0;
       check_cuda(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-      double demand = 0.0;
-      for (int q = 0; q < n_sys; ++q)
-        demand += 140.0 * (double)ctxs[q]->batches.size() * (double)(ctxs[q]->nv * ctxs[q]->nv * ctxs[q]->nv);
-      const double budget = 0.5 * (double)fr;
+      std::vector<double> demand(n_sys), share(n_sys);
+      std::vector<int> order(n_sys);
+      for (int q = 0; q < n_sys; ++q) {
+        const double nv = (double)ctxs[q]->nv;
+        demand[q] = 140.0 * (double)ctxs[q]->batches.size() * nv * nv * nv;
+        order[q] = q;
+      }
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return demand[a] < demand[b]; });
+      double left = 0.5 * (double)fr;
+      for (int r = 0; r < n_sys; ++r) {
+        const int q = order[r];
+        share[q] = std::min(demand[q], left / (double)(n_sys - r));
+        left -= share[q];
+      }
       for (int q = 0; q < n_sys; ++q) {
         mlcc3_ctx *c = ctxs[q];
         mlcc3_sweep::Sys y;
@@ -2773,8 +2785,8 @@ extern "C" int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int
         sw->sys.push_back(y);
         if (c->chunk_blocks == 0) {
           const long long nb = (long long)c->batches.size();
-          c->chunk_blocks = demand <= budget ? std::max<long long>(1, nb)
-                                             : std::max<long long>(1, (long long)((double)nb * budget / demand));
+          c->chunk_blocks = demand[q] <= 0.0 ? std::max<long long>(1, nb)
+                            : std::max<long long>(1, (long long)((double)nb * share[q] / demand[q]));
           make_chunks(c);
         }
       }
