@@ -169,6 +169,10 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              densities, Cholesky-index builds); 0 = unlimited.  The tensor
  *              cores accumulate with truncation, so the error of a chain
  *              grows with its length.  Default 16 (K = 1024).  Range 0..4096.
+ *   "tc_persist_from"  tensor-core launches with more output tiles than this
+ *              run the persistent kernel (one CTA per SM looping over tiles,
+ *              accumulator double-buffered in TMEM); smaller ones run one CTA
+ *              per tile.  Default 304; 0 always persistent.
  *   "bstc_fill"  split-K target of the FP64 strided contractions: a launch
  *              with few output tiles and a long reduction splits K until about
  *              bstc_fill x 152 CTAs run; 0 never splits.  Default 4.  Range 0..64.
@@ -224,10 +228,10 @@ long long mlcc3_debug_nbatches(mlcc3_ctx *ctx);
 int mlcc3_debug_profile(mlcc3_ctx *ctx, int enable);
 
 /* C = A B^T on the split-precision tensor-core path (the contraction kernel
- * of MLCC3_SPLIT_BF16X3): A [M][K], B [N][K], C [M][N], row-major FP64 device
- * arrays.  A and B are split into hi/lo bfloat16 pairs; the three products
- * A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32.  Diagnostic: it
- * allocates temporaries and synchronises the default stream. */
+ * of MLCC3_SPLIT_BF16X3, persistent form): A [M][K], B [N][K], C [M][N],
+ * row-major FP64 device arrays.  A and B are split into hi/lo bfloat16 pairs;
+ * the three products A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in FP32.
+ * Diagnostic: it allocates temporaries and synchronises the default stream. */
 int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, int M, int N, int K);
 int mlcc3_debug_kernel_stats(mlcc3_ctx *ctx, int index, char *name, size_t name_len,
                              long long *launches, double *ms, double *flops);

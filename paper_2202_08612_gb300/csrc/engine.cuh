@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "kernels_fp64.cuh"
+#include "kernels_tc.cuh"
 #include "mlcc3.h"
 
 namespace mlcc3 {
@@ -82,6 +83,8 @@ struct mlcc3_ctx {
   // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)
   int tc_kcap = 16;
+  // tensor-core launches with more tiles than this use the persistent kernel
+  int tc_persist_from = mlcc3::kTcPersistFrom;
   // batch chunking: at most chunk_blocks blocks held per chunk (0 = sized from
   // the device memory); parts / parts_cvs partition all / the core batches,
   // groups cover all batches by occupied-index ranges (densities)

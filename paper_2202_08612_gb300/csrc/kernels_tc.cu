@@ -113,6 +113,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// One epilogue element.  The adding modes use fire-and-forget reductions
+// (red.global.add): one writer per element per launch and stream-ordered
+// launches keep the sums deterministic, and no thread waits for a load.
+__device__ __forceinline__ void epi_put(const TcEpi &epi, long long a, float x) {
+  switch (epi.mode) {
+    case 0: static_cast<float *>(epi.out)[a] = x; break;
+    case 1: atomicAdd(static_cast<float *>(epi.out) + a, x); break;
+    case 2:
+    case 4: atomicAdd(static_cast<double *>(epi.out) + a, (double)x); break;
+    default: static_cast<double *>(epi.out)[a] = (double)x; break;
+  }
+}
+
 }  // namespace
 
 template <int BN, int STAGES>
@@ -254,18 +267,7 @@ __global__ void __launch_bounds__(192, 1)
         const int n = it.c0 + n0 + j;
         if (n >= epi.nlim) break;
         const long long a = base + (long long)n * epi.sn;
-        const float x = epi.alpha * v[j];
-        if (epi.mode == 0) {
-          static_cast<float *>(epi.out)[a] = x;
-        } else if (epi.mode == 1) {
-          static_cast<float *>(epi.out)[a] += x;
-        } else if (epi.mode == 2) {
-          atomicAdd(static_cast<double *>(epi.out) + a, (double)x);
-        } else if (epi.mode == 3) {
-          static_cast<double *>(epi.out)[a] = (double)x;
-        } else {
-          static_cast<double *>(epi.out)[a] += (double)x;
-        }
+        epi_put(epi, a, epi.alpha * v[j]);
       }
     }
   }
@@ -278,15 +280,229 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent form of tc_gemm_kernel: CTA b takes the items b, b + gridDim.x, ...
+// The producer and the MMA issuer run ahead across item boundaries through the
+// same ring of stages; the accumulator alternates between two TMEM buffers, so
+// the epilogue of one item overlaps the loads and MMAs of the next.
+//   tfull[u]  : the MMAs of the item held in buffer u have completed (commit)
+//   tempty[u] : the four epilogue warps have read buffer u (one arrive each)
+// A bounded wait that expires sets kStatusTimeout and the shared abort flag;
+// every role then leaves its loop, the producer waits (bounded) for its TMA
+// copies in flight and the MMA issuer for its last MMAs before TMEM is freed.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_persist_kernel(const __grid_constant__ TcMaps maps, const TcItem *__restrict__ items,
+                           const TcSeg *__restrict__ segs, int nitems, const TcEpi epi,
+                           int *__restrict__ status) {
+  constexpr int A_BYTES = 128 * 128;
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int NCOLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = smem_u32(bars + STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * STAGES);
+  const uint32_t tempty0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(tfull0 + 8 * u, 1);
+      mbar_init(tempty0 + 8 * u, 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t last[STAGES];
+    bool pending[STAGES];
+    for (int s = 0; s < STAGES; ++s) pending[s] = false;
+    for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x) {
+      const TcItem it = items[i];
+      for (int q = 0; q < it.seg_count && !*abort_flag; ++q) {
+        const TcSeg sg = segs[it.seg_begin + q];
+        for (int kc = 0; kc < sg.nk; ++kc) {
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
+            *abort_flag = 1;
+            break;
+          }
+          unsigned char *st = smem + stage * STAGE;
+          const uint32_t fb = full0 + 8 * stage;
+          mbar_expect_tx(fb, STAGE);
+          const int k = sg.ac[0] + 64 * kc, kb = sg.bc[0] + 64 * kc;
+          tma_load_4d(smem_u32(st), &maps.m[sg.amap], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
+          tma_load_4d(smem_u32(st + A_BYTES), &maps.m[sg.amap + 1], k, sg.ac[1], sg.ac[2],
+                      sg.ac[3], fb);
+          tma_load_4d(smem_u32(st + 2 * A_BYTES), &maps.m[sg.bmap], kb, sg.bc[1], sg.bc[2],
+                      sg.bc[3], fb);
+          tma_load_4d(smem_u32(st + 2 * A_BYTES + B_BYTES), &maps.m[sg.bmap + 1], kb, sg.bc[1],
+                      sg.bc[2], sg.bc[3], fb);
+          last[stage] = phase;
+          pending[stage] = true;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+    // the shared memory must outlive every copy issued into it
+    for (int s = 0; s < STAGES; ++s)
+      if (pending[s]) mbar_wait(full0 + 8 * s, last[s], status);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int stage = 0;
+    uint32_t phase = 0;
+    int t = 0;
+    for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x, ++t) {
+      const int u = t & 1;
+      if (!mbar_wait(tempty0 + 8 * u, ((uint32_t)(t >> 1) & 1u) ^ 1u, status)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const TcItem it = items[i];
+      int total = 0;
+      for (int q = 0; q < it.seg_count; ++q) total += segs[it.seg_begin + q].nk;
+      const uint32_t acc = tmem + (uint32_t)(u * NCOLS);
+      bool ok = true;
+      for (int c = 0; c < total; ++c) {
+        if (!mbar_wait(full0 + 8 * stage, phase, status)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        unsigned char *st = smem + stage * STAGE;
+        const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
+        const uint32_t bhi = smem_u32(st + 2 * A_BYTES), blo = smem_u32(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t off = kk * 32;
+          mma_bf16(acc, smem_desc(ahi + off), smem_desc(bhi + off), IDESC, (c > 0 || kk > 0));
+          mma_bf16(acc, smem_desc(ahi + off), smem_desc(blo + off), IDESC, 1u);
+          mma_bf16(acc, smem_desc(alo + off), smem_desc(bhi + off), IDESC, 1u);
+        }
+        mma_commit(empty0 + 8 * stage);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (!ok) break;
+      mma_commit(tfull0 + 8 * u);  // arrives when this item's MMAs have completed
+    }
+    mma_commit(done);
+    mbar_wait(done, 0, status);  // every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const int lg = warp & 3;
+    const int row = lg * 32 + lane;
+    int t = 0;
+    for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x, ++t) {
+      const int u = t & 1;
+      const bool ok = mbar_wait(tfull0 + 8 * u, (uint32_t)(t >> 1) & 1u, status);
+      if (!ok) *abort_flag = 1;
+      tc_fence_after();
+      const TcItem it = items[i];
+      int total = 0;
+      for (int q = 0; q < it.seg_count; ++q) total += segs[it.seg_begin + q].nk;
+      int r1, r2;
+      if (epi.linear) {
+        const int m = it.r2_0 + row;
+        r1 = m / epi.R2;
+        r2 = m % epi.R2;
+      } else {
+        r1 = it.r1_0 + row / epi.R2;
+        r2 = it.r2_0 + row % epi.R2;
+      }
+      const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
+      const long long base = it.out_off + (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+#pragma unroll 1
+      for (int n0 = 0; n0 < BN; n0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(u * NCOLS) + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
+        if (!rv) continue;
+        if (total == 0)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = it.c0 + n0 + j;
+          if (n >= epi.nlim) break;
+          const long long a = base + (long long)n * epi.sn;
+          epi_put(epi, a, epi.alpha * v[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * u);  // this warp is done with buffer u
+      if (!ok) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NCOLS)
+                 : "memory");
+  }
+}
+
 template <int BN, int STAGES>
 constexpr int tc_smem_bytes() {
-  return STAGES * (2 * 128 * 128 + 2 * BN * 128) + 1024 + (2 * STAGES + 1) * 8 + 16;
+  return STAGES * (2 * 128 * 128 + 2 * BN * 128) + 1024 + (2 * STAGES + 5) * 8 + 16;
 }
 
 template <int BN, int STAGES>
 static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, const TcSeg *segs,
-                             int nitems, const TcEpi &epi, int *status, cudaStream_t stream) {
+                             int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                             int persist_from) {
   constexpr int smem = tc_smem_bytes<BN, STAGES>();
+  if (nitems > persist_from) {  // persistent CTAs, one per SM
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_persist_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nitems < sms ? nitems : sms;
+    tc_gemm_persist_kernel<BN, STAGES><<<grid, 192, smem, stream>>>(maps, items, segs, nitems, epi,
+                                                                    status);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -296,13 +512,15 @@ static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, const TcSe
 
 // Host launcher: BN is the tile width (columns), one of 64, 128, 160, 256.
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
-                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream) {
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                           int persist_from) {
   if (nitems <= 0) return cudaSuccess;
+  const int pf = persist_from;
   switch (BN) {
-    case 64: return launch_bn<64, 4>(maps, items, segs, nitems, epi, status, stream);
-    case 128: return launch_bn<128, 3>(maps, items, segs, nitems, epi, status, stream);
-    case 160: return launch_bn<160, 3>(maps, items, segs, nitems, epi, status, stream);
-    case 256: return launch_bn<256, 2>(maps, items, segs, nitems, epi, status, stream);
+    case 64: return launch_bn<64, 4>(maps, items, segs, nitems, epi, status, stream, pf);
+    case 128: return launch_bn<128, 3>(maps, items, segs, nitems, epi, status, stream, pf);
+    case 160: return launch_bn<160, 3>(maps, items, segs, nitems, epi, status, stream, pf);
+    case 256: return launch_bn<256, 2>(maps, items, segs, nitems, epi, status, stream, pf);
     default: return cudaErrorInvalidValue;
   }
 }

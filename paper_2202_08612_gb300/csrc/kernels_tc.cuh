@@ -36,9 +36,10 @@ struct TcItem {
 };
 
 // Epilogue: out[out_off + r1 s1 + r2 s2 + n sn] (op) alpha * acc for
-// r1 < lim1, r2 < lim2, n < nlim, with n = c0 + the tile column.  mode 0: FP32 store, 1: FP32 add
-// (read-modify-write; one writer per element per launch), 2: FP64 atomicAdd,
-// 3: FP64 store, 4: FP64 add (read-modify-write; one writer per element per launch).
+// r1 < lim1, r2 < lim2, n < nlim, with n = c0 + the tile column.  mode 0: FP32 store,
+// 1: FP32 add (one writer per element per launch), 2: FP64 add (any number of writers),
+// 3: FP64 store, 4: FP64 add (one writer per element per launch).  The adds are
+// global reductions.
 struct TcEpi {
   void *out;
   int mode;
@@ -51,5 +52,9 @@ struct TcEpi {
 
 // Status bits written by the tensor-core kernels.
 constexpr int kStatusTimeout = 2;
+
+// Launches with more items than this run the persistent kernel (one CTA per
+// SM looping over items, TMEM double-buffered); smaller ones one CTA per item.
+constexpr int kTcPersistFrom = 304;
 
 }  // namespace mlcc3

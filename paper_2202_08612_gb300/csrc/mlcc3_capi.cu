@@ -55,7 +55,8 @@ cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, l
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
                        long long s1, long long s2, long long s3, double scale, cudaStream_t st);
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
-                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream);
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                           int persist_from);
 int tc_tile_width(long long n);
 cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                           long long D1, long long K1, long long K2, long long Kp, long long s0,
@@ -771,7 +772,8 @@ void tc_launch(mlcc3_ctx *c, int BN, const TcMaps &maps, const TcDev &d, const T
                double flops) {
   if (d.nitems == 0) return;
   c->launch("tc_gemm_kernel", flops, [&] {
-    check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, epi, c->status, c->stream),
+    check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, epi, c->status, c->stream,
+                              c->tc_persist_from),
                "tc_gemm");
   });
 }
@@ -2492,6 +2494,9 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     if (n == "tc_kcap") {
       if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, "tc_kcap out of range 0..4096"};
       c->tc_kcap = (int)value;
+    } else if (n == "tc_persist_from") {
+      if (value < 0) throw Error{MLCC3_ERR_ARG, "tc_persist_from must be >= 0"};
+      c->tc_persist_from = (int)std::min<long long>(value, 1LL << 30);
     } else if (n == "bstc_fill") {
       if (value < 0 || value > 64) throw Error{MLCC3_ERR_ARG, "bstc_fill out of range 0..64"};
       c->bstc_fill = (int)value;

@@ -17,7 +17,8 @@ namespace mlcc3 {
 
 void set_last_error(const std::string &msg);
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
-                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream);
+                           int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                           int persist_from);
 int tc_tile_width(long long n);
 __global__ void split_bf16_kernel(const double *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
                                   long long, long long, long long, long long, long long, long long,
@@ -161,8 +162,9 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
   epi.lim2 = M;
   epi.nlim = N;
   epi.alpha = 1.0f;
+  // the persistent kernel (the per-tile kernel is exercised by every small launch of a context)
   cudaError_t e = launch_tc_gemm(BN, maps, static_cast<TcItem *>(ditems),
-                                 static_cast<TcSeg *>(dsegs), (int)items.size(), epi, status, st);
+                                 static_cast<TcSeg *>(dsegs), (int)items.size(), epi, status, st, 0);
   if (e != cudaSuccess) return fail(MLCC3_ERR_CUDA, std::string("tc_gemm: ") + cudaGetErrorString(e));
   int hst = 0;
   e = cudaMemcpy(&hst, status, sizeof(int), cudaMemcpyDeviceToHost);

@@ -57,3 +57,43 @@ class Case:
     @staticmethod
     def host(x):
         return x.cpu().numpy() if hasattr(x, "cpu") else x
+
+
+def oracle_all(c):
+    """Oracle Omega, rho, sigma (state 0) and the three densities of a Case."""
+    o, st = c.oracle_ctx(), c.st
+    w = float(st.omega[0])
+    ref = {}
+    ref["o1"], r2 = O.triples_omega(o)
+    ref["o2"] = O.from_full(o, r2)
+    r1, r2 = O.jacobian_right(o, w, st.R1[0], O.to_full(o, st.R2[0]))
+    ref["rho1"], ref["rho2"] = r1, O.from_full(o, r2)
+    s1, s2 = O.jacobian_left(o, w, st.L1[0], O.to_full(o, st.L2[0]))
+    ref["sig1"], ref["sig2"] = s1, O.from_full(o, s2)
+    ref["D00"], ref["Dm0"], ref["D0m"] = O.transition_densities(
+        o, w, c.lam1, O.to_full(o, c.lam2), st.R1[0], O.to_full(o, st.R2[0]), st.L1[0],
+        O.to_full(o, st.L2[0]), c.D00_in)
+    return ref
+
+
+def run_all(c, g):
+    """The same quantities from library context g (state 0 of the Case)."""
+    st = c.st
+    NO, NV = c.sys.dims.n_occ, c.sys.dims.n_vir
+    nmo = NO + NV
+    out = {}
+    o1, o2 = c.empty_dev((NV, NO)), c.empty_dev(c.sys.t2c.shape)
+    g.triples_omega(o1, o2)
+    rho1, rho2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    sig1, sig2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    g.jacobian_right(st.omega, c.to_dev(st.R1), c.to_dev(st.R2), rho1, rho2)
+    g.jacobian_left(st.omega, c.to_dev(st.L1), c.to_dev(st.L2), sig1, sig2)
+    D = [c.empty_dev((nmo, nmo)) for _ in range(3)]
+    g.transition_density(float(st.omega[0]), c.to_dev(c.lam1), c.to_dev(c.lam2),
+                         c.to_dev(st.R1[0]), c.to_dev(st.R2[0]), c.to_dev(st.L1[0]),
+                         c.to_dev(st.L2[0]), c.to_dev(c.D00_in), *D)
+    out["o1"], out["o2"] = c.host(o1), c.host(o2)
+    out["rho1"], out["rho2"] = c.host(rho1)[0], c.host(rho2)[0]
+    out["sig1"], out["sig2"] = c.host(sig1)[0], c.host(sig2)[0]
+    out["D00"], out["Dm0"], out["D0m"] = map(c.host, D)
+    return out

@@ -112,3 +112,18 @@ def test_split_cvs():
     r1, r2 = O.jacobian_right(o, w, st.R1[0], O.to_full(o, st.R2[0]))
     assert rel_err(c.host(rho1)[0], r1) < TOL
     assert rel_err(c.host(rho2)[0], O.from_full(o, r2)) < TOL
+
+
+def test_split_persistent_kernel_everywhere():
+    """Every tensor-core launch through the persistent, TMEM double-buffered
+    kernel (tc_persist_from = 0); the whole split path still meets its bar."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)
+    g = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+    g.set_param("tc_persist_from", 0)
+    got, ref = run_all(c, g), oracle_all(c)
+    for k in ref:
+        assert rel_err(got[k], ref[k]) < TOL, (k, rel_err(got[k], ref[k]))
