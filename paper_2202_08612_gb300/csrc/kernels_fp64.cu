@@ -565,6 +565,17 @@ namespace mlcc3 {
 // the products and of the per-tile sums (FP32 in the split-precision mode,
 // else FP64); the sums over tiles are FP64.  Requires no <= 32.
 template <typename T>
+__device__ __forceinline__ T to_t(double x);
+template <>
+__device__ __forceinline__ float to_t<float>(double x) {
+  return (float)x;
+}
+template <>
+__device__ __forceinline__ double to_t<double>(double x) {
+  return x;
+}
+
+template <typename T>
 __device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
                                                const double *__restrict__ Y,
                                                const long long *__restrict__ voff,
@@ -598,8 +609,8 @@ __device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
       if (in && vhave[v]) {
         const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
                             (long long)c * vstr[3 * v + 2];
-        xv = (T)X[o];
-        yv = (T)Y[o];
+        xv = to_t<T>(X[o]);
+        yv = to_t<T>(Y[o]);
       }
       xs[r * 257 + t] = xv;
       ys[r * 257 + t] = yv;

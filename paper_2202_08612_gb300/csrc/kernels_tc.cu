@@ -12,6 +12,7 @@
 
 #include <cstdint>
 
+#include "fastconv.cuh"
 #include "kernels_tc.cuh"
 
 namespace mlcc3 {
@@ -529,24 +530,24 @@ int tc_tile_width(long long n) { return n <= 64 ? 64 : n <= 128 ? 128 : n <= 160
 
 // Split FP64 -> (hi, lo) bfloat16 with a 4-D permuted gather and K padding:
 // out[o0][o1][o2][o3] (o3 < K3p, zero for o3 >= K3) = scale * in[o0 s0 + o1 s1 + o2 s2 + o3 s3].
+// Groups of 64 threads take one output row (o0, o1, o2) at a time.
 __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
                                   __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
                                   long long D2, long long K3, long long K3p, long long s0,
                                   long long s1, long long s2, long long s3, double scale) {
-  const long long total = D0 * D1 * D2 * K3p;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long o3 = e % K3p;
-    long long r = e / K3p;
-    const long long o2 = r % D2;
-    r /= D2;
-    const long long o1 = r % D1;
-    const long long o0 = r / D1;
-    double x = 0.0;
-    if (o3 < K3) x = scale * in[o0 * s0 + o1 * s1 + o2 * s2 + o3 * s3];
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+  const int mode = scale == 1.0 ? 0 : scale == -1.0 ? 1 : 2;
+  const long long rows = D0 * D1 * D2;
+  const int g = threadIdx.x / 64, t = threadIdx.x % 64;
+  const int k3 = (int)K3, k3p = (int)K3p;
+  for (long long r = (long long)blockIdx.x * 4 + g; r < rows; r += (long long)gridDim.x * 4) {
+    const long long o2 = r % D2, r1 = r / D2;
+    const long long o1 = r1 % D1, o0 = r1 / D1;
+    const double *src = in + o0 * s0 + o1 * s1 + o2 * s2;
+    __nv_bfloat16 *h = hi + r * K3p, *l = lo + r * K3p;
+    for (int k = t; k < k3p; k += 64) {
+      const double x = k < k3 ? scaled(src[(long long)k * s3], mode, scale) : 0.0;
+      split_hi_lo(x, h[k], l[k]);
+    }
   }
 }
 
@@ -560,19 +561,69 @@ __global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat1
                                      __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
                                      long long K1, long long K2, long long Kp, long long s0,
                                      long long s1, long long sk1, long long sk2, double scale) {
-  const long long total = D0 * D1 * Kp;
-  const long long K = K1 * K2;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e % Kp;
-    const long long r = e / Kp;
+  const int mode = scale == 1.0 ? 0 : scale == -1.0 ? 1 : 2;
+  const long long rows = D0 * D1;
+  const int g = threadIdx.x / 64, t = threadIdx.x % 64;
+  const int kk2 = (int)K2, K = (int)(K1 * K2), kp = (int)Kp;
+  for (long long r = (long long)blockIdx.x * 4 + g; r < rows; r += (long long)gridDim.x * 4) {
     const long long o1 = r % D1, o0 = r / D1;
-    double x = 0.0;
-    if (k < K) x = scale * in[o0 * s0 + o1 * s1 + (k / K2) * sk1 + (k % K2) * sk2];
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+    const double *src = in + o0 * s0 + o1 * s1;
+    __nv_bfloat16 *h = hi + r * Kp, *l = lo + r * Kp;
+    for (int k = t; k < kp; k += 64) {
+      double x = 0.0;
+      if (k < K) {
+        const int q1 = k / kk2, q2 = k - q1 * kk2;
+        x = scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale);
+      }
+      split_hi_lo(x, h[k], l[k]);
+    }
   }
+}
+
+}  // namespace mlcc3
+
+namespace mlcc3 {
+
+// Batched transpose with the hi/lo bfloat16 split: for b < B, r < Rp, c < C
+//   hi/lo[b db + c dr + r] = split(src[b sb + r sr + c])   (r < R; zero for R <= r < Rp)
+// through 32 x 32 shared-memory tiles, so that both the FP64 reads (along c) and
+// the bf16 writes (along r) are coalesced.  Blocks of 32 x 8 threads loop over
+// (batch, tile) pairs.
+__global__ void __launch_bounds__(256) split_transpose_kernel(
+    const double *__restrict__ src, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+    long long B, int R, int Rp, int C, long long sb, long long sr, long long db, long long dr) {
+  __shared__ double tile[32][33];
+  const int tr = (Rp + 31) / 32, tc = (C + 31) / 32;
+  const long long ntiles = B * (long long)tr * tc;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const long long b = q / ((long long)tr * tc);
+    const int rt = (int)((q / tc) % tr), ct = (int)(q % tc);
+    const int r0 = rt * 32, c0 = ct * 32;
+    __syncthreads();  // the previous tile's reads of `tile` are done
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i, c = c0 + tx;
+      tile[i][tx] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : 0.0;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + tx;
+      if (c < C && r < Rp) {
+        const long long o = b * db + (long long)c * dr + r;
+        split_hi_lo(tile[tx][i], hi[o], lo[o]);
+      }
+    }
+  }
+}
+
+cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
+                            int R, int Rp, int C, long long sb, long long sr, long long db,
+                            long long dr, cudaStream_t st) {
+  const long long ntiles = B * (long long)((Rp + 31) / 32) * ((C + 31) / 32);
+  if (ntiles <= 0) return cudaSuccess;
+  const long long g = ntiles < 152LL * 16 ? ntiles : 152LL * 16;
+  split_transpose_kernel<<<(int)g, 256, 0, st>>>(src, hi, lo, B, R, Rp, C, sb, sr, db, dr);
+  return cudaGetLastError();
 }
 
 }  // namespace mlcc3

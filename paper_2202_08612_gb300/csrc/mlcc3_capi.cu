@@ -54,6 +54,9 @@ bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
                        long long s1, long long s2, long long s3, double scale, cudaStream_t st);
+cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
+                            int R, int Rp, int C, long long sb, long long sr, long long db,
+                            long long dr, cudaStream_t st);
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
                            int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
                            int persist_from);
@@ -1128,7 +1131,20 @@ std::pair<void *, void *> tri_layout(mlcc3_ctx *c, const double *X, int L) {
   if (!(ts.mask & (1u << L))) {
     ts.mask |= 1u << L;
     __nv_bfloat16 *h = static_cast<__nv_bfloat16 *>(hi), *l = static_cast<__nv_bfloat16 *>(lo);
-    if (xl)
+    const int nv = (int)s.nv;
+    if (L == 2 || L == 3 || L == 4) {
+      // the layouts whose K index is not the source's contiguous one: tiled transposes
+      // XL2: [u][x2][(x0 x1)] ; R0: [u][(x1 x2)][x0] ; R1: [u x0][x2][x1]
+      const long long B = L == 4 ? nb * s.nv : nb;
+      const int R = L == 2 ? nv * nv : nv, C = L == 3 ? nv * nv : nv;
+      const long long sb = L == 4 ? s.nv * s.nv : s.nv3;
+      const long long sr = L == 2 ? s.nv : L == 3 ? s.nv * s.nv : s.nv;
+      const long long db = (long long)C * Kp;
+      c->launch("split_transpose_kernel", 0.0, [&] {
+        check_cuda(split_transpose(X, h, l, B, R, (int)Kp, C, sb, sr, db, Kp, c->stream),
+                   "split_transpose");
+      });
+    } else if (xl)
       c->launch("split_bf16_k2_kernel", 0.0, [&] {
         check_cuda(split_bf16_k2(X, h, l, nb, s.nv, s.nv, s.nv, Kp, s.nv3, cs[k], cs[a], cs[b], 1.0,
                                  c->stream), "split_bf16_k2");

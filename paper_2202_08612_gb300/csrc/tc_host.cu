@@ -62,9 +62,9 @@ bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
                        long long s1, long long s2, long long s3, double scale, cudaStream_t st) {
-  long long total = D0 * D1 * D2 * K3p;
-  if (total <= 0) return cudaSuccess;
-  long long g = (total + 255) / 256;
+  const long long rows = D0 * D1 * D2;  // four rows per block at a time
+  if (rows <= 0 || K3p <= 0) return cudaSuccess;
+  long long g = (rows + 3) / 4;
   if (g > 152LL * 64) g = 152LL * 64;
   split_bf16_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, D2, K3, K3p, s0, s1, s2, s3,
                                              scale);
@@ -186,12 +186,13 @@ cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo
                           long long D1, long long K1, long long K2, long long Kp, long long s0,
                           long long s1, long long sk1, long long sk2, double scale,
                           cudaStream_t st) {
-  long long total = D0 * D1 * Kp;
-  if (total <= 0) return cudaSuccess;
-  long long g = (total + 255) / 256;
+  const long long rows = D0 * D1;  // four rows per block at a time
+  if (rows <= 0 || Kp <= 0) return cudaSuccess;
+  long long g = (rows + 3) / 4;
   if (g > 152LL * 64) g = 152LL * 64;
   split_bf16_k2_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2,
                                                 scale);
   return cudaGetLastError();
 }
 }  // namespace mlcc3
+

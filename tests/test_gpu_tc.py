@@ -1,6 +1,7 @@
 """The split-precision (hi/lo bfloat16, three products, FP32 accumulation)
 tcgen05 contraction kernel against an FP64 product, over every tile width and
 ragged M, N, K (K is padded to a multiple of 64 with zeros)."""
+import numpy as np
 import pytest
 
 from paper_2202_08612_gb300 import binding
@@ -26,3 +27,4 @@ def test_tc_gemm_matches_fp64(M, N, K):
     # a plain bf16 product would be ~3 orders of magnitude worse
     bf = (A.bfloat16().double() @ B.bfloat16().double().T)
     assert err < 0.1 * ((bf - ref).abs().max() / ref.abs().max()).item()
+
