@@ -64,7 +64,7 @@ typedef struct {
   int64_t n_occ;     /* N_O */
   int64_t n_vir;     /* N_V */
   int64_t n_act_occ; /* n_o, 0 <= n_o <= min(N_O, 32) */
-  int64_t n_act_vir; /* n_v, 0 <= n_v <= N_V */
+  int64_t n_act_vir; /* n_v, 0 <= n_v <= min(N_V, 1024) */
   int64_t n_chol;    /* N_J, number of Cholesky vectors */
   /* [N_O] host array, 1 = core orbital; NULL = no core-valence separation.
    * With a mask, the Jacobian transformations and the densities skip every

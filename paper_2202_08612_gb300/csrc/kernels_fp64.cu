@@ -457,6 +457,18 @@ __global__ void density_norm_kernel(double *__restrict__ D, const double *__rest
 
 namespace mlcc3 {
 
+// (hi, lo) += (bh, bl) for double-float numbers (pairs of FP32 whose sum is the
+// value): Knuth's error-free TwoSum of the high parts, then the low parts and a
+// renormalisation.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bh - bb);
+  const float t = err + lo + bl;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+
 // 1/d to about 1e-14 relative: an FP32 reciprocal refined by one Newton step
 // in FP64 (the step squares the relative error of the starting value).
 __device__ __forceinline__ double recip_newton(double d) {
@@ -480,39 +492,86 @@ __global__ void triples_finish_kernel(const float *__restrict__ W, const TripIte
   if ((int)blockIdx.y >= nitems) return;
   const TripItem it = items[blockIdx.y];
   const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
+  __shared__ double ev[1024];           // virtual orbital energies (n_v <= 1024)
+  __shared__ float eh[1024], el[1024];  // the same as FP32 (hi, lo) pairs
+  __shared__ float coef32[kMaxTerms];
+  const double *evp = ev;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+    const double e = eps[NO + q];
+    ev[q] = e;
+    eh[q] = (float)e;
+    el[q] = (float)(e - (double)eh[q]);
+  }
+  if (threadIdx.x < terms.n) coef32[threadIdx.x] = (float)terms.t[threadIdx.x].coef;
+  __syncthreads();
+  const float eoh = (float)eo, eol = (float)(eo - (double)eoh);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
     const int X[3] = {r / (nv * nv), (r / nv) % nv, r % nv};
     const int I[3] = {it.i, it.j, it.k};
-    double acc = (double)W[it.off + r];
-    float acc32 = 0.0f;
+    float acc32 = W[it.off + r];
+    double acc = 0.0;
     for (int t = 0; t < terms.n; ++t) {
       const TripTerm &tm = terms.t[t];
       if (tm.kind < 2) continue;
       for (int sg = 0; sg < 6; ++sg) {
-        const long long x = I[kPerm[sg][0]], y = I[kPerm[sg][1]], z = I[kPerm[sg][2]];
-        const long long u = X[kPerm[sg][0]], v = X[kPerm[sg][1]], w = X[kPerm[sg][2]];
+        const int p0 = kPerm[sg][0], p1 = kPerm[sg][1], p2 = kPerm[sg][2];
+        const long long x = I[p0], y = I[p1], z = I[p2];
+        const long long u = X[p0], v = X[p1], w = X[p2];
+        // read the form of each operand whose last index is the element's
+        // fastest one (X[2]) where the operand's symmetry allows it
+        if (fp32_rank1) {
+          float a, b;
+          if (tm.kind == 2) {
+            a = (p0 == 2 && tm.At32) ? tm.At32[u * tm.sAt[0] + x * tm.sAt[1]]
+                                     : tm.A32[x * tm.sA[0] + u * tm.sA[1]];
+            b = (p1 == 2 && tm.sym) ? tm.B32[z * tm.sB[0] + y * tm.sB[1] + w * tm.sB[2] + v * tm.sB[3]]
+                                    : tm.B32[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+          } else {
+            a = (p0 == 2 && tm.sym) ? tm.A32[y * tm.sA[0] + x * tm.sA[1] + v * tm.sA[2] + u * tm.sA[3]]
+                                    : tm.A32[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
+            b = tm.B32[z * tm.sB[0] + w * tm.sB[1]];
+          }
+          acc32 = fmaf(coef32[t] * a, b, acc32);
+          continue;
+        }
         double a, b;
         if (tm.kind == 2) {
-          a = tm.A[x * tm.sA[0] + u * tm.sA[1]];
-          b = tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+          a = (p0 == 2 && tm.At) ? tm.At[u * tm.sAt[0] + x * tm.sAt[1]]
+                                 : tm.A[x * tm.sA[0] + u * tm.sA[1]];
+          b = (p1 == 2 && tm.sym) ? tm.B[z * tm.sB[0] + y * tm.sB[1] + w * tm.sB[2] + v * tm.sB[3]]
+                                  : tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
         } else {
-          a = tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
+          a = (p0 == 2 && tm.sym) ? tm.A[y * tm.sA[0] + x * tm.sA[1] + v * tm.sA[2] + u * tm.sA[3]]
+                                  : tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
           b = tm.B[z * tm.sB[0] + w * tm.sB[1]];
         }
-        if (fp32_rank1)
-          acc32 = fmaf((float)tm.coef * (float)a, (float)b, acc32);
-        else
-          acc = fma(tm.coef, a * b, acc);
+        acc = fma(tm.coef, a * b, acc);
       }
     }
-    acc += (double)acc32;
-    const double den = eps[NO + X[0]] + eps[NO + X[1]] + eps[NO + X[2]] + eo;
     double val;
-    if (fabs(den) < 1e-3) {
-      atomicOr(status, 1);
-      val = 0.0;
+    if (fp32_rank1) {
+      // eps^{abc}_{ijk} - omega as an exact double-float sum of FP32 (hi, lo)
+      // pairs (error-free TwoSum steps): FP64 accuracy without the FP64 pipe;
+      // the numerator is an FP32 accumulation, so the quotient is taken in FP32
+      float dh = eh[X[0]], dl = el[X[0]];
+      df_add(dh, dl, eh[X[1]], el[X[1]]);
+      df_add(dh, dl, eh[X[2]], el[X[2]]);
+      df_add(dh, dl, eoh, eol);
+      const float den = dh + dl;
+      if (fabsf(den) < 1e-3f) {
+        atomicOr(status, 1);
+        val = 0.0;
+      } else {
+        val = (double)(-acc32 * __frcp_rn(den));
+      }
     } else {
-      val = -acc * recip_newton(den);
+      const double den = evp[X[0]] + (evp[X[1]] + evp[X[2]]) + eo;
+      if (fabs(den) < 1e-3) {
+        atomicOr(status, 1);
+        val = 0.0;
+      } else {
+        val = -((double)acc32 + acc) * recip_newton(den);
+      }
     }
     out[it.off + r] = val;
   }
@@ -656,6 +715,31 @@ __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
   pair_dots_body<double>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+}
+
+}  // namespace mlcc3
+
+namespace mlcc3 {
+
+// out[c][r] = in[r][c] for an R x C row-major matrix (small operands).
+__global__ void transpose2d_kernel(const double *__restrict__ in, double *__restrict__ out, int R,
+                                   int C) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)R * C;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / C, c = e % C;
+    out[c * R + r] = in[e];
+  }
+}
+
+}  // namespace mlcc3
+
+namespace mlcc3 {
+
+// out[e] = (float)in[e].
+__global__ void to_f32_kernel(const double *__restrict__ in, float *__restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
 }
 
 }  // namespace mlcc3

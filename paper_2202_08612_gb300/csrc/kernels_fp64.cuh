@@ -42,6 +42,16 @@ struct TripTerm {
   const double *A, *B;
   long long sA[4];
   long long sB[4];
+  // optional, read by triples_finish_kernel to keep the loads of the rank-1
+  // terms contiguous along the element's fastest index: sym = 1 when the
+  // two-pair operand (B of kind 2, A of kind 3) is symmetric under exchange of
+  // its (occupied, virtual) pairs; At (strides sAt) = the kind-2 vector A with
+  // its indices exchanged, At[u][x] = A[x][u]
+  int sym;
+  const double *At;
+  long long sAt[2];
+  // FP32 copies of A, B, At (same layouts) for the split-precision finish
+  const float *A32, *B32, *At32;
 };
 
 // A unique batch i >= j >= k with its output block offset (in elements).

@@ -35,6 +35,8 @@ __global__ void pair_dots_f32_kernel(const double *, const double *, const long 
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void bstc_copy_kernel(BstcParams p);
+__global__ void transpose2d_kernel(const double *, double *, int, int);
+__global__ void to_f32_kernel(const double *, float *, long long);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
 __global__ void contra3_kernel(const double *, double *, long long, int);
@@ -528,7 +530,7 @@ void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
 
 TripTerm term(int kind, int R, double coef, const double *A, std::array<long long, 4> sA,
               const double *B, std::array<long long, 4> sB) {
-  TripTerm t;
+  TripTerm t{};
   t.kind = kind;
   t.R = R;
   t.coef = coef;
@@ -581,6 +583,7 @@ mlcc3_ctx::SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const doub
 void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
 void tc_integrals(mlcc3_ctx *c);
 void split_chol_kpairs(mlcc3_ctx *c);
+float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long n);
 mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k,
                               unsigned rows);
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
@@ -1481,9 +1484,37 @@ void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const 
     triples(c, full, bkey, bs, omega, out);
     return;
   }
+  // the rank-1 terms' operands are pair-symmetric (g_jbkc, Lc), and L1 is also
+  // given transposed, so that the finish reads them along the fastest index
+  double *L1T = c->buf("L1T:" + tag, s.NV * s.NO);
+  launch_1d(c, s.NV * s.NO, "transpose2d", [&](int g) {
+    c->launch("transpose2d_kernel", 0.0, [&] {
+      transpose2d_kernel<<<g, 256, 0, c->stream>>>(L1, L1T, (int)s.NV, (int)s.NO);
+    });
+  });
+  full[2].sym = 1;
+  full[2].At = L1T;
+  full[2].sAt[0] = 1;
+  full[2].sAt[1] = s.NV;
+  full[3].sym = 1;
+  // FP32 copies for the finish (g_jbkc and F are converted once per integral build)
+  full[2].A32 = f32_copy(c, "L1:" + tag, L1, s.NV * s.NO);
+  full[2].At32 = f32_copy(c, "L1T:" + tag, L1T, s.NV * s.NO);
+  full[2].B32 = static_cast<const float *>(c->raw("f32:Govov", 4));
+  full[3].A32 = f32_copy(c, "Lc:" + tag, Lc, (long long)s.blk());
+  full[3].B32 = static_cast<const float *>(c->raw("f32:F", 4));
   SplitTerm d = split_d(c, tag + "c", Lc, true, "Gb", c->Gb, false);
   SplitTerm l = split_l(c, tag + "cT", LcT, true, "Gx", c->Gx, false);
   triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out);
+}
+
+// FP32 copy of n doubles in the named scratch buffer.
+float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long n) {
+  float *y = static_cast<float *>(c->raw("f32:" + key, sizeof(float) * (size_t)std::max(1LL, n)));
+  launch_1d(c, n, "to_f32", [&](int g) {
+    c->launch("to_f32_kernel", 0.0, [&] { to_f32_kernel<<<g, 256, 0, c->stream>>>(x, y, n); });
+  });
+  return y;
 }
 
 // tau and its contravariant form for the batches of chunk `ch` (kept until the
@@ -1643,7 +1674,11 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   c->bstc1(Lt + NO, Lt + NO, c->Govov, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.lJ, 0, 0, nmo, 1}, {s.vk, 1, s.vj, s.vb}), "Govov");
   fock_ov(c, c->t1, c->F, "F");
   transpose_tl(c, c->t2c, c->Tl);
-  if (split_mode(c)) build_split_persistent(c);
+  if (split_mode(c)) {
+    build_split_persistent(c);
+    f32_copy(c, "Govov", c->Govov, s.no * s.nv * s.no * s.nv);
+    f32_copy(c, "F", c->F, s.no * s.nv);
+  }
   c->tau_valid = false;
   c->built = true;
   c->build_gen += 1;
@@ -2348,6 +2383,7 @@ extern "C" int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *d, int precision,
       throw Error{MLCC3_ERR_ARG, "invalid dimensions"};
     if (d->n_occ + d->n_vir > 46340) throw Error{MLCC3_ERR_ARG, "n_mo too large"};
     if (d->n_act_occ > 32) throw Error{MLCC3_ERR_ARG, "n_o above 32 is not supported"};
+    if (d->n_act_vir > 1024) throw Error{MLCC3_ERR_ARG, "n_v above 1024 is not supported"};
     if (precision != MLCC3_FP64 && precision != MLCC3_SPLIT_BF16X3)
       throw Error{MLCC3_ERR_ARG, "unknown precision mode"};
     int dev = 0;
