@@ -469,113 +469,145 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl)
   lo = t - (hi - s);
 }
 
-// 1/d to about 1e-14 relative: an FP32 reciprocal refined by one Newton step
-// in FP64 (the step squares the relative error of the starting value).
-__device__ __forceinline__ double recip_newton(double d) {
-  const double r0 = (double)(1.0f / (float)d);
-  return r0 * fma(-d, r0, 2.0);
+
+// binary32 -> binary64 (exact) on the integer pipe; binary32 subnormals
+// (never produced here) become signed zeros.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned int e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ex = e == 255 ? 0x7FFull : (unsigned long long)(e + 896);
+  return __longlong_as_double((long long)(sign | (ex << 52) | ((unsigned long long)m << 29)));
 }
 
-// Finish of the tensor-core triples build: X = -(W + rank-1 terms) / (eps - omega)
+// q = x / d for x < 2^30 and d <= 1024 with the invariant-divisor multiplier
+// m = ceil(2^40 / d): the product overshoots x / d by less than x / 2^40 < 1 / d,
+// so its floor is exact (Granlund and Montgomery's multiply-shift division).
+__device__ __forceinline__ unsigned int div_inv(unsigned int x, unsigned long long m) {
+  return (unsigned int)(((unsigned long long)x * m) >> 40);
+}
+
+// Finish of the split-precision triples build: X = -(W + rank-1 terms) / (eps - omega)
 // per element of every block in `items`, W the FP32 sum of the six permuted
 // two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
-// Only kinds 2 and 3 of `terms` are evaluated here (summed over the six pair
-// permutations; in FP32 when fp32_rank1 is set, the split-precision mode).
-// The denominator is formed in FP64; omega is read from omega_p when it is set.
-__global__ void triples_finish_kernel(const float *__restrict__ W, const TripItem *__restrict__ items,
-                                      int nitems, const TripTerms terms,
-                                      const double *__restrict__ eps, int NO, int nv, double omega_v,
-                                      const double *__restrict__ omega_p, int fp32_rank1,
-                                      double *__restrict__ out, int *__restrict__ status) {
-  const double omega = omega_p ? *omega_p : omega_v;  // device-resident omega (graph replay)
-  const int nv3 = nv * nv * nv;
+// Terms of kind 2 and 3 (rank 1 in the pair indices) are summed here over the
+// six permutations in FP32, from FP32 copies of their operands; for each
+// (term, permutation) the block first tabulates base pointers and 32-bit
+// strides, choosing the symmetric or transposed form of an operand whose last
+// index is the element's fastest one.  eps^{abc}_{ijk} - omega is an exact
+// double-float sum of FP32 (hi, lo) pairs (ehl: the virtual energies' pairs),
+// which keeps FP64 accuracy off the FP64 pipe; the quotient of the FP32
+// numerator is taken in FP32 and widened on the integer pipe.  omega is read
+// from omega_p when it is set.
+__global__ void __launch_bounds__(256) triples_finish_kernel(
+    const float *__restrict__ W, const TripItem *__restrict__ items, int nitems,
+    const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
+    unsigned long long nvinv, double omega_v, const double *__restrict__ omega_p,
+    double *__restrict__ out, int *__restrict__ status) {
+  struct Ent {
+    const float *pa, *pb;
+    int au, av, bv, bw;
+    int p0, p1, p2;
+    float coef;
+  };
+  __shared__ Ent tab[2 * kMaxTerms * 6];
+  __shared__ float2 ev[1024];
+  __shared__ float eoh, eol;
+  __shared__ int nent;
   if ((int)blockIdx.y >= nitems) return;
   const TripItem it = items[blockIdx.y];
-  const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
-  __shared__ double ev[1024];           // virtual orbital energies (n_v <= 1024)
-  __shared__ float eh[1024], el[1024];  // the same as FP32 (hi, lo) pairs
-  __shared__ float coef32[kMaxTerms];
-  const double *evp = ev;
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-    const double e = eps[NO + q];
-    ev[q] = e;
-    eh[q] = (float)e;
-    el[q] = (float)(e - (double)eh[q]);
-  }
-  if (threadIdx.x < terms.n) coef32[threadIdx.x] = (float)terms.t[threadIdx.x].coef;
-  __syncthreads();
-  const float eoh = (float)eo, eol = (float)(eo - (double)eoh);
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
-    const int X[3] = {r / (nv * nv), (r / nv) % nv, r % nv};
-    const int I[3] = {it.i, it.j, it.k};
-    float acc32 = W[it.off + r];
-    double acc = 0.0;
+  const int I[3] = {it.i, it.j, it.k};
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) ev[q] = ehl[q];
+  if (threadIdx.x == 0) {
+    const double omega = omega_p ? *omega_p : omega_v;
+    const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
+    eoh = (float)eo;
+    eol = (float)(eo - (double)eoh);
+    int n = 0;
     for (int t = 0; t < terms.n; ++t) {
       const TripTerm &tm = terms.t[t];
       if (tm.kind < 2) continue;
       for (int sg = 0; sg < 6; ++sg) {
-        const int p0 = kPerm[sg][0], p1 = kPerm[sg][1], p2 = kPerm[sg][2];
-        const long long x = I[p0], y = I[p1], z = I[p2];
-        const long long u = X[p0], v = X[p1], w = X[p2];
-        // read the form of each operand whose last index is the element's
-        // fastest one (X[2]) where the operand's symmetry allows it
-        if (fp32_rank1) {
-          float a, b;
-          if (tm.kind == 2) {
-            a = (p0 == 2 && tm.At32) ? tm.At32[u * tm.sAt[0] + x * tm.sAt[1]]
-                                     : tm.A32[x * tm.sA[0] + u * tm.sA[1]];
-            b = (p1 == 2 && tm.sym) ? tm.B32[z * tm.sB[0] + y * tm.sB[1] + w * tm.sB[2] + v * tm.sB[3]]
-                                    : tm.B32[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
+        Ent e;
+        e.p0 = kPerm[sg][0];
+        e.p1 = kPerm[sg][1];
+        e.p2 = kPerm[sg][2];
+        const long long x = I[e.p0], y = I[e.p1], z = I[e.p2];
+        e.coef = (float)tm.coef;
+        e.av = 0;
+        if (tm.kind == 2) {  // A[x][u] B[y][z][v][w]
+          if (e.p0 == 2 && tm.At32) {
+            e.pa = tm.At32 + x * tm.sAt[1];
+            e.au = (int)tm.sAt[0];
           } else {
-            a = (p0 == 2 && tm.sym) ? tm.A32[y * tm.sA[0] + x * tm.sA[1] + v * tm.sA[2] + u * tm.sA[3]]
-                                    : tm.A32[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
-            b = tm.B32[z * tm.sB[0] + w * tm.sB[1]];
+            e.pa = tm.A32 + x * tm.sA[0];
+            e.au = (int)tm.sA[1];
           }
-          acc32 = fmaf(coef32[t] * a, b, acc32);
-          continue;
+          if (e.p1 == 2 && tm.sym) {
+            e.pb = tm.B32 + z * tm.sB[0] + y * tm.sB[1];
+            e.bv = (int)tm.sB[3];
+            e.bw = (int)tm.sB[2];
+          } else {
+            e.pb = tm.B32 + y * tm.sB[0] + z * tm.sB[1];
+            e.bv = (int)tm.sB[2];
+            e.bw = (int)tm.sB[3];
+          }
+        } else {  // A[x][y][u][v] B[z][w]
+          if (e.p0 == 2 && tm.sym) {
+            e.pa = tm.A32 + y * tm.sA[0] + x * tm.sA[1];
+            e.au = (int)tm.sA[3];
+            e.av = (int)tm.sA[2];
+          } else {
+            e.pa = tm.A32 + x * tm.sA[0] + y * tm.sA[1];
+            e.au = (int)tm.sA[2];
+            e.av = (int)tm.sA[3];
+          }
+          e.pb = tm.B32 + z * tm.sB[0];
+          e.bv = 0;
+          e.bw = (int)tm.sB[1];
         }
-        double a, b;
-        if (tm.kind == 2) {
-          a = (p0 == 2 && tm.At) ? tm.At[u * tm.sAt[0] + x * tm.sAt[1]]
-                                 : tm.A[x * tm.sA[0] + u * tm.sA[1]];
-          b = (p1 == 2 && tm.sym) ? tm.B[z * tm.sB[0] + y * tm.sB[1] + w * tm.sB[2] + v * tm.sB[3]]
-                                  : tm.B[y * tm.sB[0] + z * tm.sB[1] + v * tm.sB[2] + w * tm.sB[3]];
-        } else {
-          a = (p0 == 2 && tm.sym) ? tm.A[y * tm.sA[0] + x * tm.sA[1] + v * tm.sA[2] + u * tm.sA[3]]
-                                  : tm.A[x * tm.sA[0] + y * tm.sA[1] + u * tm.sA[2] + v * tm.sA[3]];
-          b = tm.B[z * tm.sB[0] + w * tm.sB[1]];
-        }
-        acc = fma(tm.coef, a * b, acc);
+        tab[n++] = e;
       }
     }
+    nent = n;
+  }
+  __syncthreads();
+  const unsigned int nv3 = (unsigned int)nv * nv * nv;
+  for (unsigned int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
+    const unsigned int q1 = div_inv(r, nvinv);
+    const unsigned int q0 = div_inv(q1, nvinv);
+    const int X[3] = {(int)q0, (int)(q1 - q0 * nv), (int)(r - q1 * nv)};
+    float acc = W[it.off + r];
+    for (int n = 0; n < nent; ++n) {
+      const Ent &e = tab[n];
+      const int u = X[e.p0], v = X[e.p1], w = X[e.p2];
+      acc = fmaf(e.coef * e.pa[u * e.au + v * e.av], e.pb[v * e.bv + w * e.bw], acc);
+    }
+    float dh = ev[X[0]].x, dl = ev[X[0]].y;
+    df_add(dh, dl, ev[X[1]].x, ev[X[1]].y);
+    df_add(dh, dl, ev[X[2]].x, ev[X[2]].y);
+    df_add(dh, dl, eoh, eol);
+    const float den = dh + dl;
     double val;
-    if (fp32_rank1) {
-      // eps^{abc}_{ijk} - omega as an exact double-float sum of FP32 (hi, lo)
-      // pairs (error-free TwoSum steps): FP64 accuracy without the FP64 pipe;
-      // the numerator is an FP32 accumulation, so the quotient is taken in FP32
-      float dh = eh[X[0]], dl = el[X[0]];
-      df_add(dh, dl, eh[X[1]], el[X[1]]);
-      df_add(dh, dl, eh[X[2]], el[X[2]]);
-      df_add(dh, dl, eoh, eol);
-      const float den = dh + dl;
-      if (fabsf(den) < 1e-3f) {
-        atomicOr(status, 1);
-        val = 0.0;
-      } else {
-        val = (double)(-acc32 * __frcp_rn(den));
-      }
+    if (fabsf(den) < 1e-3f) {
+      atomicOr(status, 1);
+      val = 0.0;
     } else {
-      const double den = evp[X[0]] + (evp[X[1]] + evp[X[2]]) + eo;
-      if (fabs(den) < 1e-3) {
-        atomicOr(status, 1);
-        val = 0.0;
-      } else {
-        val = -((double)acc32 + acc) * recip_newton(den);
-      }
+      val = widen_f32(-acc * __frcp_rn(den));
     }
     out[it.off + r] = val;
   }
 }
+
+// (hi, lo) FP32 pairs of n doubles: hi = binary32(x), lo = binary32(x - hi).
+__global__ void hilo_kernel(const double *__restrict__ x, float2 *__restrict__ y, int n) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const float h = (float)x[q];
+    y[q] = make_float2(h, (float)(x[q] - (double)h));
+  }
+}
+
 
 }  // namespace mlcc3
 

@@ -49,8 +49,9 @@ __global__ void sd_dot_kernel(const double *, const double *, const double *, co
 __global__ void density_norm_kernel(double *, const double *, const double *, const double *,
                                     int, int);
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
-                                      const double *, int, int, double, const double *, int,
-                                      double *, int *);
+                                      const double *, const float2 *, int, unsigned long long,
+                                      double, const double *, double *, int *);
+__global__ void hilo_kernel(const double *, float2 *, int);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
@@ -960,10 +961,12 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
   for (long long b0 = 0; b0 < nb; b0 += 65535) {
     const long long nbc = std::min<long long>(65535, nb - b0);
     dim3 grid((unsigned)std::min<long long>((s.nv3 + 255) / 256, 1024), (unsigned)nbc);
+    const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
+    const unsigned long long nvinv = ((1ULL << 40) + (unsigned long long)s.nv - 1) / (unsigned long long)s.nv;
     c->launch("triples_finish_kernel", 0.0, [&] {
-      triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps,
-                                                         (int)s.NO, (int)s.nv, omega, c->omega_dev,
-                                                         1, out, c->status);
+      triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps, ehl,
+                                                         (int)s.nv, nvinv, omega, c->omega_dev,
+                                                         out, c->status);
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
@@ -1678,6 +1681,12 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
     build_split_persistent(c);
     f32_copy(c, "Govov", c->Govov, s.no * s.nv * s.no * s.nv);
     f32_copy(c, "F", c->F, s.no * s.nv);
+    if (s.nv > 0) {  // FP32 (hi, lo) pairs of the virtual orbital energies
+      float2 *ehl = static_cast<float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
+      c->launch("hilo_kernel", 0.0, [&] {
+        hilo_kernel<<<1, 256, 0, c->stream>>>(c->eps + s.NO, ehl, (int)s.nv);
+      });
+    }
   }
   c->tau_valid = false;
   c->built = true;
