@@ -211,6 +211,20 @@ class Problem:
             fs.append(ctx.oscillator_strength(w, o["D0m"], o["Dm0"], x["mu"]))
         return fs
 
+    def sd_model_part(self, n):
+        """<L, D R> of state n with D the orbital-energy differences (the model of the
+        singles-doubles Jacobian block that the Rayleigh quotient is given)."""
+        from paper_2202_08612_gb300 import synth
+        NO, NV, no, nv, NJ = self.dims
+        e = self.host["eps"]
+        eo, ev = e[:NO], e[NO:]
+        d1 = ev[:, None] - eo[None, :]
+        d2 = (ev[None, :nv, None, None] + ev[None, None, None, :] - eo[:no, None, None, None]
+              - eo[None, None, :, None])
+        dims = synth.Dims(NO, NV, no, nv, NJ)
+        h = self.host
+        return synth.sd_dot(dims, h["L1"][n], h["L2"][n], d1 * h["R1"][n], d2 * h["R2"][n])
+
     def bytes_io(self):
         i = sum(v.nbytes for v in self.host.values()) + 8 * self.ns
         o = sum(v.nbytes for v in self.out_host.values()) + 8 * self.ns
@@ -319,10 +333,17 @@ def run_ours(args, rank, world, local_rank):
         e3.record(stream)
         barrier()
         ms64 = e2.elapsed_time(e3)
+        # excitation-energy Rayleigh quotient of state 0 in both precisions, with
+        # the orbital-energy-difference model of the singles-doubles block
+        sd = prob.sd_model_part(0)
+        x = prob.dev
+        rq = [cx.rayleigh_quotient(float(prob.omega[0]), x["R1"][0], x["R2"][0], x["L1"][0],
+                                   x["L2"][0], sd) for cx in (ctx, ctx64)]
         fp64 = {"value": fl / (ms64 * 1e-3) / 1e12, "ms_per_step": ms64,
                 "speedup_of_split": ms64 / ms,
                 "f_abs_diff": max(abs(a - b) for a, b in zip(f_ours, f64)),
-                "f_fp64": f64}
+                "f_fp64": f64,
+                "omega_rq": {"split": rq[0], "fp64": rq[1], "abs_diff_hartree": abs(rq[0] - rq[1])}}
         ctx64.close()
 
     if rank == 0:

@@ -118,6 +118,19 @@ int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
                              const double *L1, const double *L2, const double *D00_in,
                              double *D00_T, double *Dm0_T, double *D0m_T);
 
+/* Excitation-energy Rayleigh quotient of one state (Sec. 2: the CC3
+ * excitation energies are eigenvalues of the omega-dependent Jacobian A(omega);
+ * the Davidson iterations estimate them from trial vectors):
+ *   omega_rq = (sd_part + <L, rho_T(omega)>) / <L, R>
+ * rho_T = the triples part of A(omega) R (as mlcc3_jacobian_right), sd_part =
+ * the caller's <L, A_SD R> (its singles-doubles Jacobian, which the library
+ * does not hold), <,> the unique-element inner product (weight 1/2 on the
+ * doubles elements the active-pair block stores twice).  R1, R2, L1, L2 as one
+ * vector of mlcc3_jacobian_right / _left; the dot products are FP64 on the
+ * device; *omega_rq is a host scalar.  MLCC3_ERR_ARG when <L, R> = 0. */
+int mlcc3_rayleigh_quotient(mlcc3_ctx *ctx, double omega, const double *R1, const double *R2,
+                            const double *L1, const double *L2, double sd_part, double *omega_rq);
+
 /* Length-gauge oscillator strength of one state from its full (CCSD-level +
  * triples) transition densities (Sec. 2 transition moments):
  *   f = 2/3 omega sum_x (sum_pq D0m_pq mu~^x_pq)(sum_pq Dm0_pq mu~^x_pq),

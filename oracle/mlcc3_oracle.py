@@ -35,7 +35,7 @@ __all__ = [
     "contra2", "contra3", "sym3", "eps3", "tau3", "triples_omega",
     "upsilon", "right_R3", "jacobian_right", "left_L3", "jacobian_left",
     "lambda3", "density_left", "transition_densities", "oscillator_strength",
-    "sd_inner",
+    "sd_inner", "rayleigh_quotient",
 ]
 
 _PAIR_PERMS = ("ijkabc", "ikjacb", "jikbac", "jkibca", "kijcab", "kjicba")
@@ -452,6 +452,16 @@ def sd_inner(ctx, x1, x2, y1, y2):
     """Euclidean inner product over unique singles and doubles elements,
     with doubles in full storage: sum x1 y1 + 1/2 sum Delta x2 y2."""
     return float(np.sum(x1 * y1) + 0.5 * np.sum(delta(x2) * y2))
+
+
+def rayleigh_quotient(ctx, omega, R1, R2, L1, L2, sd_part):
+    """Excitation-energy Rayleigh quotient of the omega-dependent Jacobian
+    (Sec. 2: CC3 excitation energies are eigenvalues of A(omega)):
+      omega_RQ = (sd_part + <L, rho_T(omega)>) / <L, R>
+    rho_T the triples part of A(omega) R (jacobian_right), sd_part the caller's
+    <L, A_SD R>, <,> the unique-element inner product; doubles in full storage."""
+    r1, r2 = jacobian_right(ctx, omega, R1, R2)
+    return (sd_part + sd_inner(ctx, L1, L2, r1, r2)) / sd_inner(ctx, L1, L2, R1, R2)
 
 
 def oscillator_strength(ctx, omega, D0m, Dm0, mu):

@@ -28,7 +28,7 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
            "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param",
            "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
-           "mlcc3_sweep_destroy")
+           "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient")
 
 
 class MLCC3Error(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_sweep_info.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     lib.mlcc3_sweep_destroy.argtypes = [P]
     lib.mlcc3_sweep_destroy.restype = None
+    lib.mlcc3_rayleigh_quotient.argtypes = [P, D, P, P, P, P, D, P]
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -181,6 +182,14 @@ class Context:
         out = np.empty(n, dtype=np.float64)
         self._check(self.lib.mlcc3_debug_fetch(self.h, name.encode(), out.ctypes.data, n))
         return out
+
+    def rayleigh_quotient(self, omega, R1, R2, L1, L2, sd_part=0.0) -> float:
+        """(sd_part + <L, rho_T(omega)>) / <L, R> (mlcc3_rayleigh_quotient)."""
+        out = ctypes.c_double()
+        self._check(self.lib.mlcc3_rayleigh_quotient(self.h, float(omega), _ptr(R1), _ptr(R2),
+                                                     _ptr(L1), _ptr(L2), float(sd_part),
+                                                     ctypes.byref(out)))
+        return out.value
 
     def set_param(self, name: str, value: int):
         """mlcc3_set_param (tuning knobs such as "tc_kcap")."""

@@ -1950,6 +1950,33 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
   }
 }
 
+static void do_rayleigh(mlcc3_ctx *c, double omega, const double *R1_in, const double *R2_in,
+                        const double *L1_in, const double *L2_in, double sd_part, double *out) {
+  S s(c);
+  const double *R1 = c->in(R1_in, s.NV * s.NO, "R1");
+  const double *R2 = c->in(R2_in, s.blk(), "R2");
+  const double *L1 = c->in(L1_in, s.NV * s.NO, "L1");
+  const double *L2 = c->in(L2_in, s.blk(), "L2");
+  double *rho1 = c->buf("rq:rho1", s.NV * s.NO);
+  double *rho2 = c->buf("rq:rho2", s.blk());
+  do_jacobian_right(c, 1, &omega, R1, R2, rho1, rho2);
+  double *d = c->dscal + 4;  // <L, rho_T>, <L, R>
+  c->zero(d, 2);
+  const long long n = (long long)(s.NV * s.NO + s.blk());
+  for (int q = 0; q < 2; ++q)
+    launch_1d(c, n, "sd_dot", [&](int g) {
+      c->launch("sd_dot_kernel", 0.0, [&] {
+        sd_dot_kernel<<<g, 256, 0, c->stream>>>(L1, L2, q ? R1 : rho1, q ? R2 : rho2, (int)s.no,
+                                                (int)s.nv, (int)s.NO, (int)s.NV, d + q);
+      });
+    });
+  double h[2] = {0.0, 0.0};
+  check_cuda(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "rq read");
+  check_cuda(cudaStreamSynchronize(c->stream), "rq sync");
+  if (h[1] == 0.0) throw Error{MLCC3_ERR_ARG, "<L, R> = 0"};
+  *out = (sd_part + h[0]) / h[1];
+}
+
 static void do_oscillator(mlcc3_ctx *c, double omega, const double *D0m_in, const double *Dm0_in,
                           const double *mu_in, double *f) {
   S s(c);
@@ -2508,6 +2535,19 @@ extern "C" int mlcc3_transition_density(mlcc3_ctx *c, double omega, const double
   return guarded([&] {
     require_built(c);
     do_transition_density(c, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_rayleigh_quotient(mlcc3_ctx *c, double omega, const double *R1,
+                                       const double *R2, const double *L1, const double *L2,
+                                       double sd_part, double *omega_rq) {
+  return guarded([&] {
+    require_built(c);
+    if (!R1 || !R2 || !L1 || !L2 || !omega_rq) throw Error{MLCC3_ERR_ARG, "null argument"};
+    if (!(std::fabs(omega) < 1e300) || !(std::fabs(sd_part) < 1e300))
+      throw Error{MLCC3_ERR_ARG, "omega or sd_part is not finite"};
+    do_rayleigh(c, omega, R1, R2, L1, L2, sd_part, omega_rq);
     c->finish();
   });
 }

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import sdbasis
 from oracle import mlcc3_oracle as OM
 from detspace import DetSpace, Model, full_mp2_t2
 from paper_2202_08612_gb300 import synth
@@ -299,3 +300,19 @@ def test_biorthonormal_states():
     S = np.array([[O.sd_inner(ctx, st.L1[m], O.to_full(ctx, st.L2[m]), st.R1[n],
                                O.to_full(ctx, st.R2[n])) for n in range(3)] for m in range(3)])
     assert np.allclose(S, np.eye(3), atol=1e-13)
+
+
+def test_rayleigh_quotient_is_the_eigenvalue_at_the_fixed_point():
+    """omega-nonlinear eigenproblem of J(omega) = Delta-eps + A_T(omega) on the
+    unique singles/doubles space of a tiny system (A_T from the oracle applied to
+    every basis vector, eigenpairs from numpy.linalg.eig, omega iterated to
+    self-consistency): at the fixed point the Rayleigh quotient with the left
+    and right eigenvectors returns omega itself."""
+    s = synth.make_system(3, 4, 2, 2, 10, seed=5)
+    o = O.make_ctx(s)
+    w, R1, R2, L1, L2, sd_part = sdbasis.fixed_point_eigenpair(s, o)
+    rq = O.rayleigh_quotient(o, w, R1, O.to_full(o, R2), L1, O.to_full(o, L2), sd_part)
+    assert abs(rq - w) < 1e-11 * max(1.0, abs(w))
+    # a vector that is not an eigenvector gives something else
+    rq2 = O.rayleigh_quotient(o, w, R1 + 0.1, O.to_full(o, R2), L1, O.to_full(o, L2), sd_part)
+    assert abs(rq2 - w) > 1e-6
