@@ -32,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Ctx", "make_ctx", "to_full", "from_full", "delta", "delta_inv", "covariant2",
-    "contra2", "contra3", "sym3", "eps3", "tau3", "triples_omega",
+    "contra2", "contra3", "sym3", "eps3", "tau3", "tau3_block", "triples_omega",
     "upsilon", "right_R3", "jacobian_right", "left_L3", "jacobian_left",
     "lambda3", "density_left", "transition_densities", "oscillator_strength",
     "sd_inner", "rayleigh_quotient",
