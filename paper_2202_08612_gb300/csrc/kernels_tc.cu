@@ -627,3 +627,58 @@ cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 
 }
 
 }  // namespace mlcc3
+
+namespace mlcc3 {
+
+// Transposed split copy of a Gv-like block G[k][b][c][D] (strides gk, gb, gc, 1):
+//   out[k][D][r] = split(G[k][b][c][D] + fcoef delta_{D b} F[k][c]),  r = x nv + y,
+// (x, y) = (b, c) (swap = 0) or (c, b) (swap = 1), zero for nv^2 <= r < Kp.
+// The optional diagonal term folds a Fock-like F[k][c] (row stride nv) into the
+// integral operand (F = nullptr: none).  32 x 32 tiles over (r, D) in shared
+// memory keep the FP64 reads (along D) and the bf16 writes (along r) coalesced.
+__global__ void __launch_bounds__(256) split_gt_kernel(
+    const double *__restrict__ G, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+    int no, int NV, int nv, int Kp, long long gk, long long gb, long long gc, int swap,
+    const double *__restrict__ F, double fcoef) {
+  __shared__ double tile[32][33];
+  const int R = nv * nv;
+  const int tr = (Kp + 31) / 32, tc = (NV + 31) / 32;
+  const long long ntiles = (long long)no * tr * tc;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const int k = (int)(q / ((long long)tr * tc));
+    const int r0 = (int)((q / tc) % tr) * 32, d0 = (int)(q % tc) * 32;
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int r = r0 + i, D = d0 + tx;
+      double v = 0.0;
+      if (r < R && D < NV) {
+        const int x = r / nv, y = r - x * nv;
+        const int b = swap ? y : x, c = swap ? x : y;
+        v = G[(long long)k * gk + (long long)b * gb + (long long)c * gc + D];
+        if (F && D == b) v += fcoef * F[(long long)k * nv + c];
+      }
+      tile[i][tx] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int D = d0 + i, r = r0 + tx;
+      if (D < NV && r < Kp) {
+        const long long o = ((long long)k * NV + D) * Kp + r;
+        split_hi_lo(tile[tx][i], hi[o], lo[o]);
+      }
+    }
+  }
+}
+
+cudaError_t split_gt_launch(const double *G, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int no, int NV,
+                            int nv, int Kp, long long gk, long long gb, long long gc, int swap,
+                            const double *F, double fcoef, cudaStream_t st) {
+  const long long ntiles = (long long)no * ((Kp + 31) / 32) * ((NV + 31) / 32);
+  if (ntiles <= 0) return cudaSuccess;
+  const long long g = ntiles < 152LL * 16 ? ntiles : 152LL * 16;
+  split_gt_kernel<<<(int)g, 256, 0, st>>>(G, hi, lo, no, NV, nv, Kp, gk, gb, gc, swap, F, fcoef);
+  return cudaGetLastError();
+}
+
+}  // namespace mlcc3

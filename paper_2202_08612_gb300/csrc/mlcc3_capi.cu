@@ -57,6 +57,9 @@ bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
                        long long s1, long long s2, long long s3, double scale, cudaStream_t st);
+cudaError_t split_gt_launch(const double *G, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int no, int NV,
+                            int nv, int Kp, long long gk, long long gb, long long gc, int swap,
+                            const double *F, double fcoef, cudaStream_t st);
 cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
                             int R, int Rp, int C, long long sb, long long sr, long long db,
                             long long dr, cudaStream_t st);
@@ -578,7 +581,10 @@ void tc_back_L(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
 void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, const std::string &okey,
                const BackSet &b, double *Zb);
 bool split_mode(const mlcc3_ctx *c);
-void split_gt(mlcc3_ctx *c, const std::string &key, const double *G);
+void split_gt(mlcc3_ctx *c, const std::string &key, const double *G, const double *F = nullptr,
+              double fcoef = 0.0);
+void encode_split(mlcc3_ctx::SplitOp &op, const std::string &key, const unsigned long long dims[4],
+                  const unsigned long long str[3], const unsigned bx[4]);
 mlcc3_ctx::SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const double *G);
 mlcc3_ctx::SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk);
 void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
@@ -608,7 +614,8 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
     c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true, okey + ":bs");
   }
-  if (bset.F) {
+  // split mode: the F term rides on the D-slot GEMM (split_gt folds cF/cD F_kc into it)
+  if (bset.F && !(split_mode(c) && bset.GD)) {
     it = c->dev_items(okey + ":bF", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ords)
@@ -986,7 +993,7 @@ void build_split_persistent(mlcc3_ctx *c) {
   make_split(c, "Tl:S", c->Tl, s.no, s.nv, s.nv, s.NO, s.ti, s.tb, s.ta, 1, 1.0, Box::Pair);
   make_split(c, "Go:N", c->Go, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
   make_split(c, "Gx:N", c->Gx, s.no, s.no, s.nv, s.NO, s.oj, s.ok, s.oc, 1, -1.0, Box::Row);
-  split_gt(c, "Gb", c->Gb);
+  split_gt(c, "Gb", c->Gb, c->F, 0.5);  // Omega / rho: D slot g_Dbkc with 1/2 F_kc folded in
   split_gt(c, "Gv", c->Gv);
   split_go_T(c, "Gx:T", c->Gx);
   split_go_T(c, "Go:T", c->Go);
@@ -1062,10 +1069,32 @@ void split_chol_kpairs(mlcc3_ctx *c) {
 }
 
 // G[k][b][c][D] (Gv-like) transposed to [k][D][(b,c)] and [k][D][(c,b)].
-void split_gt(mlcc3_ctx *c, const std::string &key, const double *G) {
+// The optional F[k][c] (with coefficient fcoef) is folded in as fcoef delta_{Db} F_kc:
+// the D-slot back-contraction then also carries the F_kc term of the doubles.
+void split_gt(mlcc3_ctx *c, const std::string &key, const double *G, const double *F,
+              double fcoef) {
   S s(c);
-  make_split_k2(c, key + ":T", G, s.no, s.NV, s.nv, s.nv, s.gk, 1, s.gb, s.gc, 128);
-  make_split_k2(c, key + ":Ts", G, s.no, s.NV, s.nv, s.nv, s.gk, 1, s.gc, s.gb, 128);
+  const long long Kp = (s.nv * s.nv + 63) / 64 * 64;
+  for (int swap = 0; swap < 2; ++swap) {
+    const std::string k2 = key + (swap ? ":Ts" : ":T");
+    SplitOp &op = c->splits[k2];
+    const size_t n = (size_t)(s.no * s.NV * Kp);
+    op.hi = c->raw("split:" + k2 + ":hi", n * 2);
+    op.lo = c->raw("split:" + k2 + ":lo", n * 2);
+    c->launch("split_transpose_kernel", 0.0, [&] {
+      check_cuda(split_gt_launch(G, static_cast<__nv_bfloat16 *>(op.hi),
+                                 static_cast<__nv_bfloat16 *>(op.lo), (int)s.no, (int)s.NV,
+                                 (int)s.nv, (int)Kp, s.gk, s.gb, s.gc, swap, F, fcoef, c->stream),
+                 "split_gt");
+    });
+    const unsigned long long dims[4] = {(unsigned long long)Kp, (unsigned long long)s.NV, 1ULL,
+                                        (unsigned long long)s.no};
+    const unsigned long long str[3] = {(unsigned long long)(Kp * 2),
+                                       (unsigned long long)(Kp * 2 * s.NV),
+                                       (unsigned long long)(Kp * 2 * s.NV)};
+    const unsigned bx[4] = {64, 128, 1, 1};
+    encode_split(op, k2, dims, str, bx);
+  }
 }
 
 // Z[p][a][q][D] += cD sum_{bc} X_{pqr}[a][b][c] G_r[b][c][D] on the tensor cores:
@@ -1083,7 +1112,7 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
   const SplitOp &x0 = layout_XL(c, "bD:XL0", X, 0, BN);
   const SplitOp &x1 = layout_XL(c, "bD:XL1", X, 1, BN);
   const SplitOp &x2 = layout_XL(c, "bD:XL2", X, 2, BN);
-  if (b.gd_convert) split_gt(c, b.gd_key, b.GD);
+  if (b.gd_convert) split_gt(c, b.gd_key, b.GD, b.F, b.F ? b.cF / b.cD : 0.0);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   const SplitOp *ops[5] = {&c->splits.at(b.gd_key + ":T"), &c->splits.at(b.gd_key + ":Ts"), &x0, &x1,
