@@ -79,6 +79,7 @@ struct mlcc3_ctx {
   // split-K target of the FP64 strided contraction: when few output tiles
   // face a long reduction, split K until about bstc_fill * 152 CTAs run (0 = never)
   int bstc_fill = 4;
+  bool force_fp64 = false;  // strided contractions in FP64 even in the split mode
   bool tau_valid = false;   // tau3 / its contravariant blocks match the current build
   // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)

@@ -24,9 +24,12 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 }
 
-__global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+// T: product type; the FP32 form (split-precision mode) folds each thread's
+// FP32 partial sums into FP64 every four K tiles (64 products).
+template <typename T>
+__device__ __forceinline__ void bstc_body(const BstcParams &p) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   __shared__ long long rowA[BM], rowC[BM], colB[BN], colC[BN];
   __shared__ long long kA[BK], kB[BK];
 
@@ -67,11 +70,16 @@ __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
   const double *B = p.B + it.offB;
 
   const int ty = tid / 16, tx = tid % 16;
-  double acc[4][4];
+  T acc[4][4];
+  double accd[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = T(0);
+      accd[i][j] = 0.0;
+    }
+  int tiles = 0;
 
   const long long kbeg = p.kchunk ? (long long)blockIdx.z * p.kchunk : 0;
   const long long kend = p.kchunk ? min(K, kbeg + p.kchunk) : K;
@@ -92,21 +100,21 @@ __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
     for (int e = tid; e < BK * BM; e += 256) {
       int kk, mm;
       if (kfastA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
-      double v = 0.0;
-      if (rowA[mm] >= 0 && kA[kk] >= 0) v = A[rowA[mm] + kA[kk]];
+      T v = T(0);
+      if (rowA[mm] >= 0 && kA[kk] >= 0) v = (T)A[rowA[mm] + kA[kk]];
       As[kk][mm] = v;
     }
     for (int e = tid; e < BK * BN; e += 256) {
       int kk, nn;
       if (kfastB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
-      double v = 0.0;
-      if (colB[nn] >= 0 && kB[kk] >= 0) v = B[kB[kk] + colB[nn]];
+      T v = T(0);
+      if (colB[nn] >= 0 && kB[kk] >= 0) v = (T)B[kB[kk] + colB[nn]];
       Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
@@ -117,6 +125,16 @@ __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+    if (++tiles == 4) {
+      tiles = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accd[i][j] += (double)acc[i][j];
+          acc[i][j] = T(0);
+        }
+    }
   }
   double *C = p.C + it.offC;
 #pragma unroll
@@ -127,12 +145,15 @@ __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) {
     for (int j = 0; j < 4; ++j) {
       long long cc = colC[tx * 4 + j];
       if (cc < 0) continue;
-      double v = p.alpha * acc[i][j];
+      double v = p.alpha * (accd[i][j] + (double)acc[i][j]);
       if (p.atomic) atomicAdd(C + rc + cc, v);
       else C[rc + cc] += v;
     }
   }
 }
+
+__global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) { bstc_body<double>(p); }
+__global__ void __launch_bounds__(256) bstc_f32_kernel(BstcParams p) { bstc_body<float>(p); }
 
 // Dot-product form (M = N = 1, large K): one CTA per item reduces over K.
 __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
@@ -615,21 +636,44 @@ namespace mlcc3 {
 
 // Matrix-vector form of the batched strided contraction (N = 1): one warp per
 // output row m, the lanes stride over K, warp reduction, one (atomic) update.
+// Matrix-vector form of the batched strided contraction (N = 1): one warp per
+// output row m, the lanes stride over K, warp reduction, one (atomic) update.
+// Each lane splits its first K index into (k1, k2, k3) once and then advances
+// them by 32 with 32-bit carries (no division per element).  FP64 products:
+// every element is used once, so converting it would cost more than its FMA.
 __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
   const BstcItem &it = p.items[blockIdx.y];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long M = (long long)p.M1 * p.M2;
   const long long m = (long long)blockIdx.x * 8 + warp;
   if (m >= M) return;
-  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
+  const long long K = (long long)K1 * K2 * K3;
   const long long m1 = m / p.M2, m2 = m % p.M2;
   const double *A = p.A + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
   const double *B = p.B + it.offB;
+  const long long a1 = it.sA[2], a2 = it.sA[3], a3 = it.sA[4];
+  const long long b1 = it.sB[0], b2 = it.sB[1], b3 = it.sB[2];
+  int k3 = lane % K3, k12 = lane / K3;
+  int k2 = k12 % K2, k1 = k12 / K2;
+  const int d3 = 32 % K3, d12 = 32 / K3;  // advance of (k3, k12) per step
+  const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
   for (long long k = lane; k < K; k += 32) {
-    const long long k3 = k % p.K3, k12 = k / p.K3;
-    const long long k2 = k12 % p.K2, k1 = k12 / p.K2;
-    s += A[k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] * B[k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+    s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+    k3 += d3;
+    int c = 0;
+    if (k3 >= K3) {
+      k3 -= K3;
+      c = 1;
+    }
+    k2 += d2 + c;
+    c = 0;
+    if (k2 >= K2) {
+      k2 -= K2;
+      c = 1;
+    }
+    k1 += d1 + c;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

@@ -28,6 +28,7 @@
 
 namespace mlcc3 {
 __global__ void bstc_kernel(BstcParams p);
+__global__ void bstc_f32_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
 __global__ void pair_dots_f32_kernel(const double *, const double *, const long long *, const int *,
@@ -222,6 +223,9 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
   p.atomic = atomic ? 1 : 0;
   long long M = sh.M1 * sh.M2, N = sh.N1 * sh.N2;
   if (M == 0 || N == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
+  // split-precision mode: FP32 products with FP64 sums, except where a caller
+  // asks for FP64 (the oscillator strength and the Rayleigh quotient)
+  const bool f32 = precision == MLCC3_SPLIT_BF16X3 && !force_fp64;
   if (N == 1) {  // matrix-vector form: a warp per output row
     for (int z0 = 0; z0 < nitems; z0 += 65535) {
       p.items = it + z0;
@@ -238,8 +242,8 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
   // split K when few output tiles face a long reduction
   const long long K = sh.K1 * sh.K2 * sh.K3;
   long long ksplit = 1;
-  if (bstc_fill > 0 && tiles * nitems < 2 * 152 && K >= 2048) {
-    ksplit = std::min<long long>((bstc_fill * 152LL + tiles * nitems - 1) / (tiles * nitems), K / 512);
+  if (bstc_fill > 0 && tiles * nitems < 2 * 152 && K >= 1024) {
+    ksplit = std::min<long long>((bstc_fill * 152LL + tiles * nitems - 1) / (tiles * nitems), K / 256);
     ksplit = std::max<long long>(1, std::min<long long>(ksplit, 65535));
   }
   if (ksplit > 1) {
@@ -254,8 +258,10 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
     int nz = std::min(65535, nitems - z0);
     dim3 grid((unsigned)tiles, (unsigned)nz, (unsigned)ksplit);
     const std::string name = tag.empty() ? std::string("bstc_kernel") : "bstc_kernel:" + tag;
-    launch(name.c_str(), 2.0 * M * N * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
-           [&] { bstc_kernel<<<grid, 256, 0, stream>>>(p); });
+    launch(name.c_str(), 2.0 * M * N * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
+      if (f32) bstc_f32_kernel<<<grid, 256, 0, stream>>>(p);
+      else bstc_kernel<<<grid, 256, 0, stream>>>(p);
+    });
   }
   check_cuda(cudaGetLastError(), "bstc launch");
 }
@@ -1979,6 +1985,14 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
   }
 }
 
+// Scope in which every strided contraction of the context runs in FP64.
+struct Fp64Scope {
+  mlcc3_ctx *c;
+  bool old;
+  explicit Fp64Scope(mlcc3_ctx *cc) : c(cc), old(cc->force_fp64) { c->force_fp64 = true; }
+  ~Fp64Scope() { c->force_fp64 = old; }
+};
+
 static void do_rayleigh(mlcc3_ctx *c, double omega, const double *R1_in, const double *R2_in,
                         const double *L1_in, const double *L2_in, double sd_part, double *out) {
   S s(c);
@@ -2009,6 +2023,7 @@ static void do_rayleigh(mlcc3_ctx *c, double omega, const double *R1_in, const d
 static void do_oscillator(mlcc3_ctx *c, double omega, const double *D0m_in, const double *Dm0_in,
                           const double *mu_in, double *f) {
   S s(c);
+  Fp64Scope fp64(c);  // the final reduction to f stays FP64
   const long long nmo = s.nmo, NO = s.NO;
   const double *D0m = c->in(D0m_in, nmo * nmo, "D0m");
   const double *Dm0 = c->in(Dm0_in, nmo * nmo, "Dm0");
