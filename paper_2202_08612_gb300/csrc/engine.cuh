@@ -133,6 +133,7 @@ struct mlcc3_ctx {
     unsigned mask = 0;
   };
   TriSlot tri[4];
+  TriSlot f32s[4];  // FP32 copies of triples arrays (same keying)
   unsigned long long tri_tick = 0, gen_next = 0;
   std::map<const void *, unsigned long long> gens;
   void wrote(const void *p) { gens[p] = ++gen_next; }

@@ -159,13 +159,31 @@ __global__ void __launch_bounds__(256) bstc_f32_kernel(BstcParams p) { bstc_body
 __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   __shared__ double red[256];
   const BstcItem &it = p.items[blockIdx.x];
-  const long long K = (long long)p.K1 * p.K2 * p.K3;
+  const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
+  const long long K = (long long)K1 * K2 * K3;
+  const double *A = p.A + it.offA, *B = p.B + it.offB;
+  // split the first K index once, then advance by 256 with 32-bit carries
+  const int t0 = threadIdx.x;
+  int k3 = t0 % K3, k12 = t0 / K3;
+  int k2 = k12 % K2, k1 = k12 / K2;
+  const int d3 = 256 % K3, d12 = 256 / K3;
+  const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
-  for (long long k = threadIdx.x; k < K; k += 256) {
-    long long k3 = k % p.K3, k12 = k / p.K3;
-    long long k2 = k12 % p.K2, k1 = k12 / p.K2;
-    s += p.A[it.offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] *
-         p.B[it.offB + k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+  for (long long k = t0; k < K; k += 256) {
+    s += A[k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] * B[k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+    k3 += d3;
+    int c = 0;
+    if (k3 >= K3) {
+      k3 -= K3;
+      c = 1;
+    }
+    k2 += d2 + c;
+    c = 0;
+    if (k2 >= K2) {
+      k2 -= K2;
+      c = 1;
+    }
+    k1 += d1 + c;
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -699,20 +717,9 @@ namespace mlcc3 {
 // (t / TT)-th share of every tile and adds it to `out` once.  T is the type of
 // the products and of the per-tile sums (FP32 in the split-precision mode,
 // else FP64); the sums over tiles are FP64.  Requires no <= 32.
-template <typename T>
-__device__ __forceinline__ T to_t(double x);
-template <>
-__device__ __forceinline__ float to_t<float>(double x) {
-  return (float)x;
-}
-template <>
-__device__ __forceinline__ double to_t<double>(double x) {
-  return x;
-}
-
-template <typename T>
-__device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
-                                               const double *__restrict__ Y,
+template <typename T, typename S>
+__device__ __forceinline__ void pair_dots_body(const S *__restrict__ X,
+                                               const S *__restrict__ Y,
                                                const long long *__restrict__ voff,
                                                const int *__restrict__ vstr,
                                                const char *__restrict__ vhave, int no, int nv, int p0,
@@ -744,8 +751,8 @@ __device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
       if (in && vhave[v]) {
         const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
                             (long long)c * vstr[3 * v + 2];
-        xv = to_t<T>(X[o]);
-        yv = to_t<T>(Y[o]);
+        xv = (T)X[o];
+        yv = (T)Y[o];
       }
       xs[r * 257 + t] = xv;
       ys[r * 257 + t] = yv;
@@ -779,18 +786,19 @@ __device__ __forceinline__ void pair_dots_body(const double *__restrict__ X,
     }
 }
 
+// FP32 operands (FP32 copies of the triples arrays, split-precision mode).
 __global__ void __launch_bounds__(256) pair_dots_f32_kernel(
-    const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
+    const float *__restrict__ X, const float *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<float>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<float, float>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
     const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<double>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<double, double>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 }  // namespace mlcc3

@@ -31,7 +31,7 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_f32_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
-__global__ void pair_dots_f32_kernel(const double *, const double *, const long long *, const int *,
+__global__ void pair_dots_f32_kernel(const float *, const float *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
@@ -399,11 +399,11 @@ Chunk make_chunk(const mlcc3_ctx *c, const std::vector<TripItem> &held, int p0, 
 
 // Split the unique batches into chunks of at most chunk_blocks blocks (or, when
 // it is 0, as many as fit in half of the device memory left free once the
-// context's persistent arrays exist, at 140 bytes per block element: the
+// context's persistent arrays exist, at 156 bytes per block element: the
 // eight FP64 triples arrays the passes keep (tau, R3, L3, lambda3 and their
 // contravariant forms) plus up to 18 cached split-precision layouts of
-// triples arrays (tri_layout); scratch buffers persist across calls, so one
-// size serves all).
+// triples arrays (tri_layout) and four FP32 copies (tri_f32); scratch buffers
+// persist across calls, so one size serves all).
 void make_chunks(mlcc3_ctx *c) {
   c->chunk_gen += 1;
   c->tau_key.clear();
@@ -416,7 +416,7 @@ void make_chunks(mlcc3_ctx *c) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)40 << 30;
     const double budget = 0.5 * (double)fr;
-    part_max = group_max = std::max<long long>(1, (long long)(budget / (140.0 * (double)nv3)));
+    part_max = group_max = std::max<long long>(1, (long long)(budget / (156.0 * (double)nv3)));
   }
   const std::string g = "#" + std::to_string(c->chunk_gen);
   auto partition = [&](const std::vector<TripItem> &list, const std::string &tag) {
@@ -2064,6 +2064,29 @@ static void do_oscillator(mlcc3_ctx *c, double omega, const double *D0m_in, cons
 namespace {
 
 // View of the block of an ordered triple (p,q,r) (not all equal).
+// FP32 copy of the triples array X (chunk_nb blocks), made at most once per
+// write of X and kept in one of four slots (least recently used reused).
+const float *tri_f32(mlcc3_ctx *c, const double *X) {
+  S s(c);
+  const unsigned long long g = c->gen_of(X);
+  int q = -1;
+  for (int t = 0; t < 4; ++t)
+    if (c->f32s[t].src == X && c->f32s[t].gen == g && c->f32s[t].nb == c->chunk_nb) q = t;
+  const long long n = c->chunk_nb * s.nv3;
+  if (q < 0) {
+    q = 0;
+    for (int t = 1; t < 4; ++t)
+      if (c->f32s[t].tick < c->f32s[q].tick) q = t;
+    c->f32s[q] = mlcc3_ctx::TriSlot{};
+    c->f32s[q].src = X;
+    c->f32s[q].gen = g;
+    c->f32s[q].nb = c->chunk_nb;
+    f32_copy(c, "tri" + std::to_string(q), X, n);
+  }
+  c->f32s[q].tick = ++c->tri_tick;
+  return static_cast<const float *>(c->raw("f32:tri" + std::to_string(q), 4));
+}
+
 struct ViewMap {
   long long n;
   std::vector<long long> off, s0, s1, s2;
@@ -2119,9 +2142,10 @@ void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, 
   if (f32) {
     check_cuda(cudaFuncSetAttribute(pair_dots_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem), "pair_dots smem");
+    const float *X32 = tri_f32(c, X), *Y32 = tri_f32(c, Y);
     c->launch("pair_dots_kernel", fl, [&] {
       pair_dots_f32_kernel<<<grid, 256, smem, c->stream>>>(
-          X, Y, static_cast<const long long *>(voff), static_cast<const int *>(vstr),
+          X32, Y32, static_cast<const long long *>(voff), static_cast<const int *>(vstr),
           static_cast<const char *>(vhave), (int)s.no, (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
     });
   } else {
@@ -2744,6 +2768,7 @@ void sweep_pass(mlcc3_sweep *sw, bool multi, int only = -1, int nvec_cap = 0) {
       if (multi) check_cuda(cudaStreamWaitEvent(y.st, sw->fork, 0), "sweep wait");
       c->tau_valid = false;
       for (auto &t : c->tri) t = mlcc3_ctx::TriSlot{};
+      for (auto &t : c->f32s) t = mlcc3_ctx::TriSlot{};
       const int nv = nvec_cap > 0 ? std::min(nvec_cap, y.n_vec) : y.n_vec;
       do_jacobian_right(c, nv, nullptr, y.R1, y.R2, y.rho1, y.rho2, sw->omega_dev + y.w0);
       if (multi) {
@@ -2916,7 +2941,7 @@ extern "C" int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int
       std::vector<int> order(n_sys);
       for (int q = 0; q < n_sys; ++q) {
         const double nv = (double)ctxs[q]->nv;
-        demand[q] = 140.0 * (double)ctxs[q]->batches.size() * nv * nv * nv;
+        demand[q] = 156.0 * (double)ctxs[q]->batches.size() * nv * nv * nv;
         order[q] = q;
       }
       std::sort(order.begin(), order.end(), [&](int a, int b) { return demand[a] < demand[b]; });
