@@ -346,19 +346,108 @@ __global__ void __launch_bounds__(256) triples_build_kernel(const TripTerms term
 
 // Contravariant triples, virtual permutations with ijk fixed (Eq. contra_3):
 // Xt^{abc} = 4X^{abc} - 2X^{bac} - 2X^{cba} - 2X^{acb} + X^{cab} + X^{bca}.
-__global__ void contra3_kernel(const double *__restrict__ X, double *__restrict__ Xt,
-                               long long nblocks, int nv) {
-  const int nv3 = nv * nv * nv;
+// Contravariant triples by orbits of 8-wide tiles.  Block (o, u) takes the
+// tile orbit o, tile origins (A, B, C) with A <= B <= C, of block u: it loads
+// the distinct permuted tiles (A,B,C), (B,A,C), ... into shared memory once,
+// and each thread takes one orbit of elements {abc, bac, ...} through its
+// representative in tile (A,B,C) (a <= b where A = B, b <= c where B = C, so
+// that every element orbit has exactly one owner).  With E and O the sums of
+// the even (abc, cab, bca) and odd (bac, cba, acb) permutations,
+//   Xt^{abc} = 4X^{abc} - 2X^{bac} - 2X^{cba} - 2X^{acb} + X^{cab} + X^{bca}
+//            = 3X^{abc} + E - 2O,
+// and for an odd permutation of abc the roles of E and O exchange: six outputs
+// for 12 FP64 operations.  Rows of eight doubles keep the global loads and
+// stores sector-wide.
+namespace {
+constexpr int kC3SJ = 9, kC3SI = 8 * kC3SJ + 1, kC3T = 8 * kC3SI;  // padded tile strides
+__constant__ int kC3P[6][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}};
+}  // namespace
+
+__global__ void __launch_bounds__(512) contra3_kernel(const double *__restrict__ X,
+                                                      double *__restrict__ Xt, long long nblocks,
+                                                      int nv) {
+  __shared__ double tile[6 * kC3T];
+  __shared__ int org[6][3];
+  __shared__ int slot[6];
   const long long blk = blockIdx.y;
   if (blk >= nblocks) return;
-  const double *B = X + blk * (long long)nv3;
-  double *O = Xt + blk * (long long)nv3;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
-    const int a = r / (nv * nv), b = (r / nv) % nv, c = r % nv;
-    auto at = [&](int x, int y, int z) { return B[(x * nv + y) * nv + z]; };
-    O[r] = 4.0 * at(a, b, c) - 2.0 * at(b, a, c) - 2.0 * at(c, b, a) - 2.0 * at(a, c, b) +
-           at(c, a, b) + at(b, c, a);
+  const long long nv3 = (long long)nv * nv * nv;
+  const double *B = X + blk * nv3;
+  double *O = Xt + blk * nv3;
+  const int nt = (nv + 7) / 8;
+  if (threadIdx.x == 0) {
+    // decode orbit index -> (A, B, C), A <= B <= C < nt
+    int o = blockIdx.x, A = 0;
+    for (;; ++A) {
+      const int m = nt - A, cnt = m * (m + 1) / 2;
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    int Bt = A;
+    for (;; ++Bt) {
+      const int cnt = nt - Bt;
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    const int T[3] = {A, Bt, Bt + o};
+    for (int p = 0; p < 6; ++p) {
+      for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
+      int sl = p;
+      for (int r = 0; r < p; ++r)
+        if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
+          sl = slot[r];
+          break;
+        }
+      slot[p] = sl;
+    }
   }
+  __syncthreads();
+  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
+  const int sidx = li * kC3SI + lj * kC3SJ + lk;
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    tile[p * kC3T + sidx] = (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : 0.0;
+  }
+  __syncthreads();
+  const int A = org[0][0], Bt = org[0][1], C = org[0][2];
+  const int l[3] = {li, lj, lk};
+  const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
+                   8 * Bt + lj < nv && 8 * C + lk < nv;
+  double v[6];
+  int pos[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    pos[p] = slot[p] * kC3T + l[kC3P[p][0]] * kC3SI + l[kC3P[p][1]] * kC3SJ + l[kC3P[p][2]];
+    v[p] = tile[pos[p]];
+  }
+  __syncthreads();  // every thread holds its inputs; the tiles now take the outputs
+  if (own) {
+    const double E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
+    const double be = fma(-2.0, Od, E), bo = fma(-2.0, E, Od);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(3.0, v[p], p < 3 ? be : bo);
+  }
+  __syncthreads();
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
+  }
+}
+
+// Launch of contra3_kernel over nblocks blocks (grid: tile orbits x blocks).
+cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int nv,
+                           cudaStream_t st) {
+  if (nblocks <= 0 || nv <= 0) return cudaSuccess;
+  const long long nv3 = (long long)nv * nv * nv;
+  const long long nt = (nv + 7) / 8, norb = nt * (nt + 1) * (nt + 2) / 6;
+  for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
+    const long long nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
+    contra3_kernel<<<dim3((unsigned)norb, (unsigned)nb), 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3,
+                                                                       nb, nv);
+  }
+  return cudaGetLastError();
 }
 
 // Doubles element X(A,I,B,J) of a pair-symmetric quantity stored as the
@@ -652,33 +741,77 @@ __global__ void hilo_kernel(const double *__restrict__ x, float2 *__restrict__ y
 
 namespace mlcc3 {
 
-// Matrix-vector form of the batched strided contraction (N = 1): one warp per
-// output row m, the lanes stride over K, warp reduction, one (atomic) update.
-// Matrix-vector form of the batched strided contraction (N = 1): one warp per
-// output row m, the lanes stride over K, warp reduction, one (atomic) update.
-// Each lane splits its first K index into (k1, k2, k3) once and then advances
+// Matrix-vector form of the batched strided contraction (N = 1), eight output
+// rows per block.  Per item (block-uniform) the K index with the smallest A
+// stride becomes the fastest walking index, and the lanes are laid along the
+// finer of the two: along K (one warp per row, warp reduction) when a K stride
+// is the finest, else along the rows (lanes l, l+8, l+16, l+24 take row l at 32
+// K offsets per block, shared-memory reduction), so that a view of a triples
+// block is read in runs along its stride-1 axis whichever index that is.  Each
+// thread splits its first K index into (k1, k2, k3) once and then advances
 // them by 32 with 32-bit carries (no division per element).  FP64 products:
 // every element is used once, so converting it would cost more than its FMA.
-__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
+// T: element type of A and B.  FP32 products (split-precision mode, FP32
+// copies of the operands) are summed in FP32 over 64 K steps at a time and the
+// partial sums folded into the FP64 total.
+template <typename T>
+__device__ __forceinline__ void bstc_gemv_body(const BstcParams &p, const T *__restrict__ Ap,
+                                               const T *__restrict__ Bp) {
+  __shared__ double red[8][8];
   const BstcItem &it = p.items[blockIdx.y];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long M = (long long)p.M1 * p.M2;
-  const long long m = (long long)blockIdx.x * 8 + warp;
-  if (m >= M) return;
-  const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
+  // K axes with their strides; the one with the smallest A stride (among
+  // axes longer than one) becomes the fastest (third) walking index
+  int Kx[3] = {p.K1, p.K2, p.K3};
+  long long ax[3] = {it.sA[2], it.sA[3], it.sA[4]}, bx[3] = {it.sB[0], it.sB[1], it.sB[2]};
+  int f = -1;
+  for (int q = 0; q < 3; ++q)
+    if (Kx[q] > 1 && (f < 0 || llabs(ax[q]) < llabs(ax[f]))) f = q;
+  if (f >= 0 && f != 2) {
+    const int tk = Kx[f];
+    Kx[f] = Kx[2];
+    Kx[2] = tk;
+    const long long ta = ax[f];
+    ax[f] = ax[2];
+    ax[2] = ta;
+    const long long tb = bx[f];
+    bx[f] = bx[2];
+    bx[2] = tb;
+  }
+  // rows along the output's stride-1 index when it is finer than every K stride
+  const long long sm = p.M2 > 1 ? llabs(it.sA[1]) : llabs(it.sA[0]);
+  const bool rows = M > 1 && f >= 0 && sm < llabs(ax[2]);
+  const long long m = (long long)blockIdx.x * 8 + (rows ? (lane & 7) : warp);
+  const int kstart = rows ? warp * 4 + (lane >> 3) : lane;
+  if (!rows && m >= M) return;
+  const int K1 = Kx[0], K2 = Kx[1], K3 = Kx[2];
   const long long K = (long long)K1 * K2 * K3;
-  const long long m1 = m / p.M2, m2 = m % p.M2;
-  const double *A = p.A + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
-  const double *B = p.B + it.offB;
-  const long long a1 = it.sA[2], a2 = it.sA[3], a3 = it.sA[4];
-  const long long b1 = it.sB[0], b2 = it.sB[1], b3 = it.sB[2];
-  int k3 = lane % K3, k12 = lane / K3;
+  const long long mm = m < M ? m : M - 1;
+  const long long m1 = mm / p.M2, m2 = mm % p.M2;
+  const T *A = Ap + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
+  const T *B = Bp + it.offB;
+  const long long a1 = ax[0], a2 = ax[1], a3 = ax[2];
+  const long long b1 = bx[0], b2 = bx[1], b3 = bx[2];
+  int k3 = kstart % K3, k12 = kstart / K3;
   int k2 = k12 % K2, k1 = k12 / K2;
   const int d3 = 32 % K3, d12 = 32 / K3;  // advance of (k3, k12) per step
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
-  for (long long k = lane; k < K; k += 32) {
-    s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+  T part = T(0);
+  int np = 0;
+#pragma unroll 4
+  for (long long k = kstart; k < K; k += 32) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+      s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+    } else {
+      part += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+      if (++np == 64) {
+        s += (double)part;
+        part = T(0);
+        np = 0;
+      }
+    }
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {
@@ -693,13 +826,44 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
     }
     k1 += d1 + c;
   }
+  s += (double)part;
+  if (!rows) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
-    if (p.atomic) atomicAdd(C, p.alpha * s);
-    else *C += p.alpha * s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+      if (p.atomic) atomicAdd(C, p.alpha * s);
+      else *C += p.alpha * s;
+    }
+    return;
   }
+  // rows mode: lanes l, l + 8, l + 16, l + 24 of every warp share row l
+  s += __shfl_xor_sync(0xffffffffu, s, 8);
+  s += __shfl_xor_sync(0xffffffffu, s, 16);
+  if (lane < 8) red[warp][lane] = s;
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const long long mr = (long long)blockIdx.x * 8 + threadIdx.x;
+    if (mr < M) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+      const long long r1 = mr / p.M2, r2 = mr % p.M2;
+      double *C = p.C + it.offC + r1 * it.sC[0] + r2 * it.sC[1];
+      if (p.atomic) atomicAdd(C, p.alpha * t);
+      else *C += p.alpha * t;
+    }
+  }
+}
+
+
+__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
+  bstc_gemv_body<double>(p, p.A, p.B);
+}
+
+// Split-precision form: A and B are FP32 copies with the layouts of p.A, p.B.
+__global__ void __launch_bounds__(256) bstc_gemv_f32_kernel(BstcParams p, const float *A,
+                                                            const float *B) {
+  bstc_gemv_body<float>(p, A, B);
 }
 
 }  // namespace mlcc3
@@ -710,95 +874,173 @@ namespace mlcc3 {
 // X_{ijl}[abc] Y_{ijk}[abc] for the ordered pair (i, j) = (p0 + y / no, y % no),
 // y = blockIdx.y, over all k, l with stored views.  View (p,q,r) is the block
 // at voff[v] with strides vstr[3v..3v+2] of its (a, b, c) (v = (p no + q) no + r,
-// vhave[v] = 0 for a missing block).  Each block sweeps 4x8x8 tiles of (a,b,c)
-// (tile = blockIdx.x, blockIdx.x + gridDim.x, ...), so whichever of a, b, c is a
-// view's contiguous axis, neighbouring threads read runs of at least four
-// elements; thread t keeps the 2x2 (k,l) tile (t % TT) of partial sums over the
-// (t / TT)-th share of every tile and adds it to `out` once.  T is the type of
-// the products and of the per-tile sums (FP32 in the split-precision mode,
-// else FP64); the sums over tiles are FP64.  Requires no <= 32.
-template <typename T, typename S>
-__device__ __forceinline__ void pair_dots_body(const S *__restrict__ X,
-                                               const S *__restrict__ Y,
+// vhave[v] = 0 for a missing block); the strides are a permutation of
+// (nv^2, nv, 1).  The block copies its no views' offsets and axis orders to
+// shared memory once, then sweeps TA x 8 x 8 tiles of (a,b,c) (tile =
+// blockIdx.x, blockIdx.x + gridDim.x, ...): for every view, consecutive
+// threads take consecutive elements along that view's stride-1 axis, so each
+// load is a run of whole sectors whatever the permutation, and the element is
+// stored at its logical (a,b,c) position of the view's tile in shared memory
+// (padded strides, no bank conflicts along any axis; pads stay zero).  Thread
+// t keeps a 4x4 (k,l) tile (t % TT) of partial sums over the (t / TT)-th share
+// of every tile and adds it to `out` once.  T is the type of the products and
+// of the per-tile sums (FP32 in the split-precision mode, else FP64); the sums
+// over tiles are FP64.  Requires no <= 32.
+template <typename T, int TA>
+__device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
+                                               const T *__restrict__ Y,
                                                const long long *__restrict__ voff,
                                                const int *__restrict__ vstr,
                                                const char *__restrict__ vhave, int no, int nv, int p0,
                                                double *__restrict__ out, long long ldo, int kl,
                                                double alpha) {
+  constexpr int PB = 9, PA = 8 * PB + 1;        // padded logical strides of b and a
+  constexpr int TE = TA * PA;                   // positions of one view's tile
+  constexpr int TS = (TE + 31) / 32 * 32 + 1;   // row stride of a view, 1 mod 32
+  constexpr int NE = TA * 64;                   // elements of a tile
   extern __shared__ unsigned char smraw[];
-  T *xs = reinterpret_cast<T *>(smraw);     // [no][257]
-  T *ys = xs + (size_t)no * 257;            // [no][257]
+  T *xs = reinterpret_cast<T *>(smraw);         // [no][TS]
+  T *ys = xs + (size_t)no * TS;                 // [no][TS]
+  __shared__ long long s_off[32];
+  __shared__ int s_st[32][3];
+  __shared__ int s_ax[32][3];                   // logical axis of physical axis 0 (fastest), 1, 2
+  __shared__ int s_have[32];
   const int i = p0 + (int)blockIdx.y / no, j = (int)blockIdx.y % no;
   const int t = threadIdx.x;
-  const int nh = (no + 1) / 2;
-  const int TT = nh * nh;                   // 2x2 tiles of (k, l)
+  for (int q = t; q < 2 * no * TS; q += blockDim.x) xs[q] = T(0);
+  if (t < no) {
+    const int v = (i * no + j) * no + t;
+    s_have[t] = vhave[v];
+    s_off[t] = voff[v];
+    int st[3] = {vstr[3 * v], vstr[3 * v + 1], vstr[3 * v + 2]};
+    int ax[3] = {0, 1, 2};
+    // order the logical axes by stride (ascending): physical fastest first
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y + 1 < 3 - x; ++y)
+        if (st[ax[y]] > st[ax[y + 1]]) {
+          const int tmp = ax[y];
+          ax[y] = ax[y + 1];
+          ax[y + 1] = tmp;
+        }
+    for (int x = 0; x < 3; ++x) {
+      s_st[t][x] = st[x];
+      s_ax[t][x] = ax[x];
+    }
+  }
+  __syncthreads();
+  const int nh = (no + 3) / 4;
+  const int TT = nh * nh;                   // 4x4 tiles of (k, l)
   const int H = 256 / TT;                   // element shares per tile
   const int tile = t % TT, h = t / TT;
-  const int k0 = 2 * (tile / nh), l0 = 2 * (tile % nh);
-  const int e0 = h * (256 / H), e1 = (h + 1 == H) ? 256 : (h + 1) * (256 / H);
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // FP64 running sums over tiles
-  const int ta = (nv + 3) / 4, tb = (nv + 7) / 8, tc = (nv + 7) / 8;
+  const int k0 = 4 * (tile / nh), l0 = 4 * (tile % nh);
+  const int e0 = h * (TE / H), e1 = (h + 1 == H) ? TE : (h + 1) * (TE / H);
+  double acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
+  const int ta = (nv + TA - 1) / TA, tb = (nv + 7) / 8, tc = (nv + 7) / 8;
   const int ntiles = ta * tb * tc;
-  const int a_in = t / 64, b_in = (t / 8) % 8, c_in = t % 8;
   for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
-    const int qa = q / (tb * tc), qb = (q / tc) % tb, qc = q % tc;
-    const int a = 4 * qa + a_in, b = 8 * qb + b_in, c = 8 * qc + c_in;
-    const bool in = a < nv && b < nv && c < nv;
+    const int a0 = TA * (q / (tb * tc)), b0 = 8 * ((q / tc) % tb), c0 = 8 * (q % tc);
     __syncthreads();  // the previous tile's reads are done
     for (int r = 0; r < no; ++r) {
-      const int v = (i * no + j) * no + r;
-      T xv = T(0), yv = T(0);
-      if (in && vhave[v]) {
-        const long long o = voff[v] + (long long)a * vstr[3 * v] + (long long)b * vstr[3 * v + 1] +
-                            (long long)c * vstr[3 * v + 2];
-        xv = (T)X[o];
-        yv = (T)Y[o];
+      const int f = s_ax[r][0], m = s_ax[r][1];
+      const int df = f == 0 ? TA : 8, dm = m == 0 ? TA : 8;
+      const bool hv = s_have[r] != 0;
+      const long long base = s_off[r];
+      const int sa = s_st[r][0], sb = s_st[r][1], sc = s_st[r][2];
+#pragma unroll
+      for (int e = t; e < NE; e += 256) {
+        const int ef = e % df, em = (e / df) % dm, es = e / (df * dm);
+        const int la = f == 0 ? ef : m == 0 ? em : es;
+        const int lb = f == 1 ? ef : m == 1 ? em : es;
+        const int lc = f == 2 ? ef : m == 2 ? em : es;
+        const int a = a0 + la, b = b0 + lb, c = c0 + lc;
+        const bool ok = hv && a < nv && b < nv && c < nv;
+        const long long o = ok ? base + (long long)a * sa + (long long)b * sb + (long long)c * sc : 0;
+        const int sp = r * TS + la * PA + lb * PB + lc;
+        // asynchronous global -> shared copies; a missing element is zero-filled
+        const unsigned nbytes = ok ? (unsigned)sizeof(T) : 0u;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(xs + sp)),
+                     "l"(X + o), "n"(sizeof(T)), "r"(nbytes)
+                     : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(ys + sp)),
+                     "l"(Y + o), "n"(sizeof(T)), "r"(nbytes)
+                     : "memory");
       }
-      xs[r * 257 + t] = xv;
-      ys[r * 257 + t] = yv;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (h < H) {
-      const int ka = min(k0, no - 1), kb = min(k0 + 1, no - 1);
-      const int la = min(l0, no - 1), lb = min(l0 + 1, no - 1);
-      const T *x0 = xs + la * 257, *x1 = xs + lb * 257;
-      const T *y0 = ys + ka * 257, *y1 = ys + kb * 257;
-      T p00 = T(0), p01 = T(0), p10 = T(0), p11 = T(0);  // this tile's share
-      for (int e = e0; e < e1; ++e) {
-        const T u0 = x0[e], u1 = x1[e], w0 = y0[e], w1 = y1[e];
-        p00 += w0 * u0;
-        p01 += w0 * u1;
-        p10 += w1 * u0;
-        p11 += w1 * u1;
+      const T *xr[4], *yr[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        xr[d] = xs + min(l0 + d, no - 1) * TS;
+        yr[d] = ys + min(k0 + d, no - 1) * TS;
       }
-      acc[0][0] += (double)p00;
-      acc[0][1] += (double)p01;
-      acc[1][0] += (double)p10;
-      acc[1][1] += (double)p11;
+      T p[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) p[x][y] = T(0);
+      for (int e = e0; e < e1; ++e) {
+        T u[4], w[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          u[d] = xr[d][e];
+          w[d] = yr[d][e];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) p[x][y] += w[x] * u[y];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += (double)p[x][y];
     }
   }
   if (h >= H) return;
-  for (int dk = 0; dk < 2; ++dk)
-    for (int dl = 0; dl < 2; ++dl) {
+#pragma unroll
+  for (int dk = 0; dk < 4; ++dk)
+#pragma unroll
+    for (int dl = 0; dl < 4; ++dl) {
       const int kk = k0 + dk, ll = l0 + dl;
       if (kk >= no || ll >= no || acc[dk][dl] == 0.0) continue;
       atomicAdd(out + (kl ? kk * ldo + ll : ll * ldo + kk), alpha * acc[dk][dl]);
     }
 }
 
+// Shared-memory bytes of pair_dots_*_kernel for no views.
+size_t pair_dots_smem(int no, bool f32) {
+  const int TA = f32 ? 8 : 4;
+  const int TE = TA * 73, TS = (TE + 31) / 32 * 32 + 1;
+  return 2 * (size_t)no * TS * (f32 ? sizeof(float) : sizeof(double));
+}
+
+// Tiles of the (a,b,c) cube swept by pair_dots_*_kernel.
+long long pair_dots_tiles(int nv, bool f32) {
+  const int TA = f32 ? 8 : 4;
+  return (long long)((nv + TA - 1) / TA) * ((nv + 7) / 8) * ((nv + 7) / 8);
+}
+
 // FP32 operands (FP32 copies of the triples arrays, split-precision mode).
-__global__ void __launch_bounds__(256) pair_dots_f32_kernel(
+__global__ void __launch_bounds__(256, 3) pair_dots_f32_kernel(
     const float *__restrict__ X, const float *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<float, float>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<float, 8>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
     const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<double, double>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<double, 4>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 }  // namespace mlcc3

@@ -31,16 +31,20 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_f32_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
+__global__ void bstc_gemv_f32_kernel(BstcParams p, const float *, const float *);
 __global__ void pair_dots_f32_kernel(const float *, const float *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
+size_t pair_dots_smem(int no, bool f32);
+long long pair_dots_tiles(int nv, bool f32);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void transpose2d_kernel(const double *, double *, int, int);
 __global__ void to_f32_kernel(const double *, float *, long long);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
 __global__ void contra3_kernel(const double *, double *, long long, int);
+cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 __global__ void c2_block_kernel(const double *, double *, int, int, int, int);
 __global__ void delta_block_kernel(const double *, double *, int, int, int, int);
@@ -527,15 +531,9 @@ void triples(mlcc3_ctx *c, const std::vector<TripTerm> &terms, const std::string
 void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
   c->wrote(Xt);
   if (nblocks <= 0 || c->nv == 0) return;
-  const long long nv3 = c->nv * c->nv * c->nv;
-  for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
-    const long long nb = std::min<long long>(65535, nblocks - b0);
-    dim3 grid((unsigned)std::min<long long>((nv3 + 255) / 256, 1024), (unsigned)nb);
-    c->launch("contra3_kernel", 0.0, [&] {
-      contra3_kernel<<<grid, 256, 0, c->stream>>>(X + b0 * nv3, Xt + b0 * nv3, nb, (int)c->nv);
-    });
-  }
-  check_cuda(cudaGetLastError(), "contra3");
+  c->launch("contra3_kernel", 0.0, [&] {
+    check_cuda(launch_contra3(X, Xt, nblocks, (int)c->nv, c->stream), "contra3");
+  });
 }
 
 TripTerm term(int kind, int R, double coef, const double *A, std::array<long long, 4> sA,
@@ -602,6 +600,50 @@ mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
                 const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2);
 
+const float *tri_f32(mlcc3_ctx *c, const double *X);
+
+// Matrix-vector contraction (N = 1) whose A operand is a triples array X (the
+// chunk's blocks) and B a small operand of nB elements.  In the split mode the
+// products are FP32, from the cached FP32 copy of X and a fresh FP32 copy of B,
+// with FP64 sums (bstc_gemv_f32_kernel): GB300's FP64 pipe, not memory, bounds
+// the FP64 form of these one-use products.  Otherwise mlcc3_ctx::bstc.
+void bstc_tri(mlcc3_ctx *c, const double *X, const double *B, long long nB, double *C,
+              const Shape &sh, double alpha, const BstcItem *it, int nitems,
+              const std::string &tag) {
+  if (!split_mode(c) || c->force_fp64 || sh.N1 * sh.N2 != 1) {
+    c->bstc(X, B, C, sh, alpha, it, nitems, true, tag);
+    return;
+  }
+  const long long M = sh.M1 * sh.M2;
+  if (nitems == 0 || M == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
+  const float *X32 = tri_f32(c, X);
+  const float *B32 = f32_copy(c, "gvB", B, nB);
+  BstcParams p{};
+  p.A = X;
+  p.B = B;
+  p.C = C;
+  p.M1 = (int)sh.M1;
+  p.M2 = (int)sh.M2;
+  p.N1 = 1;
+  p.N2 = 1;
+  p.K1 = (int)sh.K1;
+  p.K2 = (int)sh.K2;
+  p.K3 = (int)sh.K3;
+  p.alpha = alpha;
+  p.nitems = nitems;
+  p.atomic = 1;
+  for (int z0 = 0; z0 < nitems; z0 += 65535) {
+    p.items = it + z0;
+    const int nz = std::min(65535, nitems - z0);
+    dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
+    const std::string name = "bstc_gemv_kernel:" + tag;
+    c->launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
+      bstc_gemv_f32_kernel<<<grid, 256, 0, c->stream>>>(p, X32, B32);
+    });
+  }
+  check_cuda(cudaGetLastError(), "bstc_gemv_f32 launch");
+}
+
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
   S s(c);
@@ -618,7 +660,7 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true, okey + ":bs");
+    bstc_tri(c, X, bset.Gs, s.vj * s.no, s1, sh, bset.cs, it, n, okey + ":bs");
   }
   // split mode: the F term rides on the D-slot GEMM (split_gt folds cF/cD F_kc into it)
   if (bset.F && !(split_mode(c) && bset.GD)) {
@@ -973,7 +1015,10 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
   (void)n;
   for (long long b0 = 0; b0 < nb; b0 += 65535) {
     const long long nbc = std::min<long long>(65535, nb - b0);
-    dim3 grid((unsigned)std::min<long long>((s.nv3 + 255) / 256, 1024), (unsigned)nbc);
+    // about sixteen 256-thread blocks per SM over the launch, each a large
+    // slice of one batch (the per-block operand tables are built serially)
+    const long long gx = std::max<long long>(1, std::min<long long>((s.nv3 + 255) / 256, (16 * 152 + nbc - 1) / nbc));
+    dim3 grid((unsigned)gx, (unsigned)nbc);
     const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
     const unsigned long long nvinv = ((1ULL << 40) + (unsigned long long)s.nv - 1) / (unsigned long long)s.nv;
     c->launch("triples_finish_kernel", 0.0, [&] {
@@ -1908,7 +1953,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
         return vv;
       }, &n);
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-      c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
+      bstc_tri(c, taut, Lc, (long long)s.blk(), Y3, sh, 0.5, it, n, okey + ":y3");
     }
     finalize(c, Sb, sig2, 1);
     Shape sh;
@@ -2132,11 +2177,13 @@ void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, 
   vstr = c->items.at(key + ":str").first;
   vhave = c->items.at(key + ":have").first;
   const bool f32 = split_mode(c);
-  const size_t smem = 2 * (size_t)s.no * 257 * (f32 ? sizeof(float) : sizeof(double));
+  const size_t smem = pair_dots_smem((int)s.no, f32);
   const long long np = ch.p1 - ch.p0;
-  const long long ntiles = ((s.nv + 3) / 4) * ((s.nv + 7) / 8) * ((s.nv + 7) / 8);
-  // about eight resident blocks' worth per SM over the whole launch
-  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, (8 * 152 + np * s.no - 1) / (np * s.no)));
+  const long long ntiles = pair_dots_tiles((int)s.nv, f32);
+  // 64 blocks per ordered pair sweep its tiles side by side, so that few pairs
+  // are in flight at once and the lines of their views stay in L2 between the
+  // neighbouring tiles that share them
+  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, 64));
   dim3 grid((unsigned)gx, (unsigned)(np * s.no));
   const double fl = 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3;
   if (f32) {
@@ -2194,7 +2241,7 @@ void y3_like(mlcc3_ctx *c, const double *X, const double *B, const std::vector<O
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(X, B, out, sh, alpha, it, n, true, key);
+  bstc_tri(c, X, B, (long long)s.blk(), out, sh, alpha, it, n, key);
 }
 
 // V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
@@ -2347,7 +2394,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-    c->bstc(lt3, R1, U, sh, 1.0, it, n, true, okey + ":U");
+    bstc_tri(c, lt3, R1, s.NV * NO, U, sh, 1.0, it, n, okey + ":U");
     // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
     sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
     c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
@@ -2363,7 +2410,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, okey + ":ld1");
+    bstc_tri(c, tau, U, s.no * s.no * s.nv * s.nv, D + NO, sh, 1.0, it, n, okey + ":ld1");
     it = c->dev_items(okey + ":ld2", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ch.held)
@@ -2372,7 +2419,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
                               {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
       return v;
     }, &n);
-    c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, okey + ":ld2");
+    bstc_tri(c, tau, U, s.no * s.no * s.nv * s.nv, D + NO, sh, -1.0, it, n, okey + ":ld2");
     //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
     y3_like(c, R3t, lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
     // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}

@@ -20,7 +20,7 @@ void set_last_error(const std::string &msg);
 __global__ void bstc_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
-__global__ void contra3_kernel(const double *, double *, long long, int);
+cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 }  // namespace mlcc3
 
@@ -170,11 +170,7 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
   const long long nt = (nv + 7) / 8;
   triples_build_kernel<<<dim3((unsigned)(nt * nt * nt), (unsigned)nb), 256, 0, st>>>(
       tt, dbatch, c->eps, (int)NO, (int)nv, 0.0, nullptr, tau, c->status);
-  for (long long b0 = 0; b0 < nb; b0 += 65535) {
-    const long long nbc = std::min<long long>(65535, nb - b0);
-    dim3 cg((unsigned)std::min<long long>((nv3 + 255) / 256, 1024), (unsigned)nbc);
-    contra3_kernel<<<cg, 256, 0, st>>>(tau + b0 * nv3, taut + b0 * nv3, nbc, (int)nv);
-  }
+  if (!chk(launch_contra3(tau, taut, nb, (int)nv, st), "contra3")) return MLCC3_ERR_CUDA;
   // scratch keeps the previous call's contents: clear the accumulators
   if (!chk(cudaMemsetAsync(Zb, 0, sizeof(double) * blk, st), "memset Zb") ||
       !chk(cudaMemsetAsync(omega1, 0, sizeof(double) * NV * NO, st), "memset omega1"))
