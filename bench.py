@@ -441,6 +441,163 @@ def run_sweep(args):
         c.close()
 
 
+# large systems: measured component by component (integral build, Omega, one
+# Davidson iteration = rho and sigma of every trial vector, densities of one state)
+# name: (N_O, N_V, n_o, n_v, N_J, valence trial vectors)
+LARGE = {
+    "guanine_like": (40, 500, 20, 120, 1500, 4),
+    "betaine_like": (100, 1000, 20, 150, 4000, 2),
+}
+
+
+def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core):
+    """Seeded synthetic inputs of the large workloads, drawn on the device
+    (torch Philox): the distributions of paper_2202_08612_gb300.synth, without
+    the host-side generation of a 10-40 GB Cholesky tensor."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    f64 = torch.float64
+    U = lambda lo, hi, n: lo + (hi - lo) * torch.rand(n, dtype=f64, device=dev, generator=g)
+    N = lambda *shape: torch.randn(*shape, dtype=f64, device=dev, generator=g)
+    nmo = NO + NV
+    eps = torch.cat([U(-1.5, -0.3, NO), U(0.1, 3.0, NV)])
+    if core:
+        eps[0] = -10.0
+    chol = torch.empty((NJ, nmo, nmo), dtype=f64, device=dev)
+    for j0 in range(0, NJ, 128):
+        b = N(min(128, NJ - j0), nmo, nmo) * 0.05
+        chol[j0:j0 + b.shape[0]] = (b + b.transpose(1, 2)) * (0.5 ** 0.5)
+        del b
+    t1 = N(NV, NO) * 0.01
+    Lvo = chol[:, NO:, :NO]                                   # [J][A][I]
+    den = (eps[:no, None, None, None] + eps[None, None, :NO, None]
+           - eps[NO:NO + nv][None, :, None, None] - eps[NO:][None, None, None, :])
+    A = Lvo[:, :nv, :no].permute(2, 1, 0).reshape(no * nv, NJ)
+    B = Lvo.permute(0, 2, 1).reshape(NJ, NO * NV)
+    t2c = (A @ B).reshape(no, nv, NO, NV) / den               # t^{aD}_{iL} = (ai|DL)/D
+    del A, B
+    A = Lvo[:, :nv, :].permute(1, 2, 0).reshape(nv * NO, NJ)  # [a][L][J]
+    B = Lvo[:, :, :no].reshape(NJ, NV * no)                   # [J][D][i]
+    t2x = (A @ B).reshape(nv, NO, NV, no).permute(3, 0, 1, 2).contiguous() / den  # t^{aD}_{Li}
+    del A, B, Lvo
+    R1 = N(nvec, NV, NO)
+    R2 = N(nvec, no, nv, NO, NV)
+    aa = R2[:, :, :, :no, :nv]
+    R2[:, :, :, :no, :nv] = 0.5 * (aa + aa.permute(0, 3, 4, 1, 2))
+    for n in range(nvec):
+        R1[n] *= (0.95 / R1[n].pow(2).sum()).sqrt()
+        R2[n] *= (0.05 / R2[n].pow(2).sum()).sqrt()
+    L1 = R1 + 0.3 * N(*R1.shape) * R1.abs().mean()
+    L2 = R2 + 0.3 * N(*R2.shape) * R2.abs().mean()
+    aa = L2[:, :, :, :no, :nv]
+    L2[:, :, :, :no, :nv] = 0.5 * (aa + aa.permute(0, 3, 4, 1, 2))
+    omega = (0.3 + 0.3 * torch.rand(nvec, dtype=f64, generator=torch.Generator().manual_seed(seed))).numpy()
+    mu = N(3, nmo, nmo) * 0.1
+    mu = 0.5 * (mu + mu.transpose(1, 2))
+    D00 = torch.zeros((nmo, nmo), dtype=f64, device=dev)
+    D00[range(NO), range(NO)] = 2.0
+    return dict(chol=chol, t1=t1, eps=eps, t2c=t2c, t2x=t2x, R1=R1, R2=R2, L1=L1, L2=L2,
+                lam1=N(NV, NO) * 0.01, lam2=t2c, mu=mu, D00_in=D00), omega
+
+
+def run_large(args):
+    """Large guanine- or betaine-shaped system in the split precision: integral
+    build, Omega, then --steps timed Davidson iterations (rho and sigma of all
+    valence trial vectors in one call each, after --warmup untimed ones), and
+    with --densities the three transition densities and f of one state.  The
+    roofline line is the tensor-core kernel's share of the Davidson iterations."""
+    import torch
+    from paper_2202_08612_gb300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    NO, NV, no, nv, NJ, nvec = LARGE[args.workload]
+    core = args.workload == "betaine_like"
+    x, omega = device_system(NO, NV, no, nv, NJ, nvec, 2022, dev, core)
+    stream = torch.cuda.current_stream(dev)
+    prec = binding.MLCC3_SPLIT_BF16X3 if args.precision == "split" else binding.MLCC3_FP64
+    z = lambda t: torch.zeros_like(t)
+    # every output exists before the context sizes its chunks from the free memory
+    o1, o2 = z(x["R1"][0]), z(x["t2c"])
+    rho1, rho2, sig1, sig2 = z(x["R1"]), z(x["R2"]), z(x["R1"]), z(x["R2"])
+    nmo = NO + NV
+    D = [torch.zeros((nmo, nmo), dtype=torch.float64, device=dev) for _ in range(3)]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    ctx = binding.Context(NO, NV, no, nv, NJ, precision=prec, stream=stream.cuda_stream)
+    # unique batches held per chunk: leaves room for the integral blocks, their
+    # split copies and the per-call scratch next to the caller's tensors
+    ctx.set_param("chunk_blocks", args.chunk_blocks)
+    unit = NV * nv ** 3 * no ** 3
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms_build = timed(lambda: ctx.build_integrals(x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"]))
+    ms_omega_first = timed(lambda: ctx.triples_omega(o1, o2))
+    ms_omega = timed(lambda: ctx.triples_omega(o1, o2))
+
+    def davidson():
+        ctx.jacobian_right(omega, x["R1"], x["R2"], rho1, rho2)
+        ctx.jacobian_left(omega, x["L1"], x["L2"], sig1, sig2)
+
+    for _ in range(args.warmup):
+        davidson()
+    ctx.profile(True)
+    with ClockSampler(0) as clk:
+        ms_it = timed(lambda: [davidson() for _ in range(args.steps)]) / args.steps
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    tc = [v for k, v in stats.items() if k.startswith("tc_gemm")]
+    tc_ms = sum(v[1] for v in tc) / args.steps
+    tc_fl = sum(v[2] for v in tc) / args.steps
+    pk = peaks().get("bf16_tflops_sustained") or 1700.0
+    alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    fl_it = 16.0 * unit * nvec
+    dens = None
+    if args.densities:
+        w = float(omega[0])
+        f = []
+        ms_d = timed(lambda: (ctx.transition_density(w, x["lam1"], x["lam2"], x["R1"][0], x["R2"][0],
+                                                     x["L1"][0], x["L2"][0], x["D00_in"], *D),
+                              f.append(ctx.oscillator_strength(w, D[2], D[1], x["mu"]))))
+        dens = {"ms": ms_d, "tflops": 36.0 * unit / (ms_d * 1e-3) / 1e12,
+                "flop_units": "(10 + 10 + 16) N_V n_v^3 n_o^3", "f": f[0]}
+    line = {"metric": METRIC, "value": fl_it / (ms_it * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_it,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if prec == binding.MLCC3_SPLIT_BF16X3 else "f64",
+            "data": "synthetic (device-generated, torch Philox)",
+            "config": {"workload": f"{args.workload}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}, "
+                                   f"{nvec} valence trial vectors" + (", core orbital at -10 Ha" if core else ""),
+                       "step": "one Davidson iteration: rho and sigma of all trial vectors",
+                       "chunk_blocks": args.chunk_blocks,
+                       "precision": args.precision},
+            "s_per_davidson_iter": ms_it * 1e-3,
+            "build_integrals_ms": ms_build,
+            "omega": {"ms": ms_omega, "ms_first_call": ms_omega_first,
+                      "tflops": 4.0 * unit / (ms_omega * 1e-3) / 1e12},
+            "densities_one_state": dens,
+            "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor",
+                         "achieved": 3.0 * alg if alg else None, "peak": pk, "unit": "TFLOP/s",
+                         "frac": 3.0 * alg / pk if alg else None, "achieved_algorithmic": alg,
+                         "share_of_step": tc_ms / ms_it,
+                         "peak_note": "measured sustained dense BF16 (MEASURED_PEAKS.json); achieved "
+                                      "counts the 3 BF16 products per product"},
+            "clocks": clk.summary(),
+            "hbm_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev)),
+            "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
+                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,10 +605,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="guanine_like_small",
-                    choices=sorted(WORKLOADS) + ["uneven_sweep"])
+                    choices=sorted(WORKLOADS) + ["uneven_sweep"] + sorted(LARGE))
     ap.add_argument("--vectors", type=int, default=4,
                     help="trial vectors per system of the uneven_sweep workload")
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
+    ap.add_argument("--chunk-blocks", type=int, default=128,
+                    help="large workloads: unique batches held per chunk")
+    ap.add_argument("--densities", action="store_true",
+                    help="large workloads: also time the densities and f of one state")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the untimed FP64-path comparison step")
     args = ap.parse_args()
@@ -463,6 +624,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "ours" and args.workload == "uneven_sweep":
         run_sweep(args)
+    elif args.impl == "ours" and args.workload in LARGE:
+        run_large(args)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:

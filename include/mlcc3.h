@@ -198,10 +198,11 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
 int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
 
 /* Triples residual without allocating (no counterpart in the paper).
- * Some callers cannot allocate device memory at the moment they call: code
- * that runs while a stream is being captured into a CUDA graph, or a loop
- * whose host application owns all device memory and forbids (or cannot afford
- * the stall of) a cudaMalloc.  This entry point returns the same omega1 and
+ * Some callers cannot allocate device memory at the moment they call: a
+ * solver loop whose host application gives all device memory to its own pool
+ * at start-up and forbids a cudaMalloc afterwards, or one that cannot afford
+ * the implicit device synchronisation that cudaMalloc/cudaFree can bring.
+ * This entry point returns the same omega1 and
  * omega2 as mlcc3_triples_omega but takes all of its scratch (the unique-batch
  * tau blocks, their contravariant copies, the doubles accumulator and the
  * index tables) from one fixed 32 MiB device array compiled into the

@@ -741,77 +741,33 @@ __global__ void hilo_kernel(const double *__restrict__ x, float2 *__restrict__ y
 
 namespace mlcc3 {
 
-// Matrix-vector form of the batched strided contraction (N = 1), eight output
-// rows per block.  Per item (block-uniform) the K index with the smallest A
-// stride becomes the fastest walking index, and the lanes are laid along the
-// finer of the two: along K (one warp per row, warp reduction) when a K stride
-// is the finest, else along the rows (lanes l, l+8, l+16, l+24 take row l at 32
-// K offsets per block, shared-memory reduction), so that a view of a triples
-// block is read in runs along its stride-1 axis whichever index that is.  Each
-// thread splits its first K index into (k1, k2, k3) once and then advances
+// Matrix-vector form of the batched strided contraction (N = 1): one warp per
+// output row m, the lanes stride over K, warp reduction, one (atomic) update.
+// Matrix-vector form of the batched strided contraction (N = 1): one warp per
+// output row m, the lanes stride over K, warp reduction, one (atomic) update.
+// Each lane splits its first K index into (k1, k2, k3) once and then advances
 // them by 32 with 32-bit carries (no division per element).  FP64 products:
 // every element is used once, so converting it would cost more than its FMA.
-// T: element type of A and B.  FP32 products (split-precision mode, FP32
-// copies of the operands) are summed in FP32 over 64 K steps at a time and the
-// partial sums folded into the FP64 total.
-template <typename T>
-__device__ __forceinline__ void bstc_gemv_body(const BstcParams &p, const T *__restrict__ Ap,
-                                               const T *__restrict__ Bp) {
-  __shared__ double red[8][8];
+__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
   const BstcItem &it = p.items[blockIdx.y];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long M = (long long)p.M1 * p.M2;
-  // K axes with their strides; the one with the smallest A stride (among
-  // axes longer than one) becomes the fastest (third) walking index
-  int Kx[3] = {p.K1, p.K2, p.K3};
-  long long ax[3] = {it.sA[2], it.sA[3], it.sA[4]}, bx[3] = {it.sB[0], it.sB[1], it.sB[2]};
-  int f = -1;
-  for (int q = 0; q < 3; ++q)
-    if (Kx[q] > 1 && (f < 0 || llabs(ax[q]) < llabs(ax[f]))) f = q;
-  if (f >= 0 && f != 2) {
-    const int tk = Kx[f];
-    Kx[f] = Kx[2];
-    Kx[2] = tk;
-    const long long ta = ax[f];
-    ax[f] = ax[2];
-    ax[2] = ta;
-    const long long tb = bx[f];
-    bx[f] = bx[2];
-    bx[2] = tb;
-  }
-  // rows along the output's stride-1 index when it is finer than every K stride
-  const long long sm = p.M2 > 1 ? llabs(it.sA[1]) : llabs(it.sA[0]);
-  const bool rows = M > 1 && f >= 0 && sm < llabs(ax[2]);
-  const long long m = (long long)blockIdx.x * 8 + (rows ? (lane & 7) : warp);
-  const int kstart = rows ? warp * 4 + (lane >> 3) : lane;
-  if (!rows && m >= M) return;
-  const int K1 = Kx[0], K2 = Kx[1], K3 = Kx[2];
+  const long long m = (long long)blockIdx.x * 8 + warp;
+  if (m >= M) return;
+  const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
   const long long K = (long long)K1 * K2 * K3;
-  const long long mm = m < M ? m : M - 1;
-  const long long m1 = mm / p.M2, m2 = mm % p.M2;
-  const T *A = Ap + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
-  const T *B = Bp + it.offB;
-  const long long a1 = ax[0], a2 = ax[1], a3 = ax[2];
-  const long long b1 = bx[0], b2 = bx[1], b3 = bx[2];
-  int k3 = kstart % K3, k12 = kstart / K3;
+  const long long m1 = m / p.M2, m2 = m % p.M2;
+  const double *A = p.A + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
+  const double *B = p.B + it.offB;
+  const long long a1 = it.sA[2], a2 = it.sA[3], a3 = it.sA[4];
+  const long long b1 = it.sB[0], b2 = it.sB[1], b3 = it.sB[2];
+  int k3 = lane % K3, k12 = lane / K3;
   int k2 = k12 % K2, k1 = k12 / K2;
   const int d3 = 32 % K3, d12 = 32 / K3;  // advance of (k3, k12) per step
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
-  T part = T(0);
-  int np = 0;
-#pragma unroll 4
-  for (long long k = kstart; k < K; k += 32) {
-    if constexpr (sizeof(T) == sizeof(double)) {
-      s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
-    } else {
-      part += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
-      if (++np == 64) {
-        s += (double)part;
-        part = T(0);
-        np = 0;
-      }
-    }
+  for (long long k = lane; k < K; k += 32) {
+    s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {
@@ -826,44 +782,13 @@ __device__ __forceinline__ void bstc_gemv_body(const BstcParams &p, const T *__r
     }
     k1 += d1 + c;
   }
-  s += (double)part;
-  if (!rows) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
-      if (p.atomic) atomicAdd(C, p.alpha * s);
-      else *C += p.alpha * s;
-    }
-    return;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+    if (p.atomic) atomicAdd(C, p.alpha * s);
+    else *C += p.alpha * s;
   }
-  // rows mode: lanes l, l + 8, l + 16, l + 24 of every warp share row l
-  s += __shfl_xor_sync(0xffffffffu, s, 8);
-  s += __shfl_xor_sync(0xffffffffu, s, 16);
-  if (lane < 8) red[warp][lane] = s;
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    const long long mr = (long long)blockIdx.x * 8 + threadIdx.x;
-    if (mr < M) {
-      double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
-      const long long r1 = mr / p.M2, r2 = mr % p.M2;
-      double *C = p.C + it.offC + r1 * it.sC[0] + r2 * it.sC[1];
-      if (p.atomic) atomicAdd(C, p.alpha * t);
-      else *C += p.alpha * t;
-    }
-  }
-}
-
-
-__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
-  bstc_gemv_body<double>(p, p.A, p.B);
-}
-
-// Split-precision form: A and B are FP32 copies with the layouts of p.A, p.B.
-__global__ void __launch_bounds__(256) bstc_gemv_f32_kernel(BstcParams p, const float *A,
-                                                            const float *B) {
-  bstc_gemv_body<float>(p, A, B);
 }
 
 }  // namespace mlcc3

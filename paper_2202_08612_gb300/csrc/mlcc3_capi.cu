@@ -31,7 +31,6 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_f32_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
-__global__ void bstc_gemv_f32_kernel(BstcParams p, const float *, const float *);
 __global__ void pair_dots_f32_kernel(const float *, const float *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
@@ -600,50 +599,6 @@ mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
                 const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2);
 
-const float *tri_f32(mlcc3_ctx *c, const double *X);
-
-// Matrix-vector contraction (N = 1) whose A operand is a triples array X (the
-// chunk's blocks) and B a small operand of nB elements.  In the split mode the
-// products are FP32, from the cached FP32 copy of X and a fresh FP32 copy of B,
-// with FP64 sums (bstc_gemv_f32_kernel): GB300's FP64 pipe, not memory, bounds
-// the FP64 form of these one-use products.  Otherwise mlcc3_ctx::bstc.
-void bstc_tri(mlcc3_ctx *c, const double *X, const double *B, long long nB, double *C,
-              const Shape &sh, double alpha, const BstcItem *it, int nitems,
-              const std::string &tag) {
-  if (!split_mode(c) || c->force_fp64 || sh.N1 * sh.N2 != 1) {
-    c->bstc(X, B, C, sh, alpha, it, nitems, true, tag);
-    return;
-  }
-  const long long M = sh.M1 * sh.M2;
-  if (nitems == 0 || M == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
-  const float *X32 = tri_f32(c, X);
-  const float *B32 = f32_copy(c, "gvB", B, nB);
-  BstcParams p{};
-  p.A = X;
-  p.B = B;
-  p.C = C;
-  p.M1 = (int)sh.M1;
-  p.M2 = (int)sh.M2;
-  p.N1 = 1;
-  p.N2 = 1;
-  p.K1 = (int)sh.K1;
-  p.K2 = (int)sh.K2;
-  p.K3 = (int)sh.K3;
-  p.alpha = alpha;
-  p.nitems = nitems;
-  p.atomic = 1;
-  for (int z0 = 0; z0 < nitems; z0 += 65535) {
-    p.items = it + z0;
-    const int nz = std::min(65535, nitems - z0);
-    dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
-    const std::string name = "bstc_gemv_kernel:" + tag;
-    c->launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
-      bstc_gemv_f32_kernel<<<grid, 256, 0, c->stream>>>(p, X32, B32);
-    });
-  }
-  check_cuda(cudaGetLastError(), "bstc_gemv_f32 launch");
-}
-
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
   S s(c);
@@ -660,7 +615,7 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     }, &n);
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    bstc_tri(c, X, bset.Gs, s.vj * s.no, s1, sh, bset.cs, it, n, okey + ":bs");
+    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true, okey + ":bs");
   }
   // split mode: the F term rides on the D-slot GEMM (split_gt folds cF/cD F_kc into it)
   if (bset.F && !(split_mode(c) && bset.GD)) {
@@ -1953,7 +1908,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
         return vv;
       }, &n);
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-      bstc_tri(c, taut, Lc, (long long)s.blk(), Y3, sh, 0.5, it, n, okey + ":y3");
+      c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
     }
     finalize(c, Sb, sig2, 1);
     Shape sh;
@@ -2180,10 +2135,8 @@ void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, 
   const size_t smem = pair_dots_smem((int)s.no, f32);
   const long long np = ch.p1 - ch.p0;
   const long long ntiles = pair_dots_tiles((int)s.nv, f32);
-  // 64 blocks per ordered pair sweep its tiles side by side, so that few pairs
-  // are in flight at once and the lines of their views stay in L2 between the
-  // neighbouring tiles that share them
-  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, 64));
+  // about eight resident blocks' worth per SM over the whole launch
+  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, (8 * 152 + np * s.no - 1) / (np * s.no)));
   dim3 grid((unsigned)gx, (unsigned)(np * s.no));
   const double fl = 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3;
   if (f32) {
@@ -2241,7 +2194,7 @@ void y3_like(mlcc3_ctx *c, const double *X, const double *B, const std::vector<O
   }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  bstc_tri(c, X, B, (long long)s.blk(), out, sh, alpha, it, n, key);
+  c->bstc(X, B, out, sh, alpha, it, n, true, key);
 }
 
 // V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
@@ -2394,7 +2347,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-    bstc_tri(c, lt3, R1, s.NV * NO, U, sh, 1.0, it, n, okey + ":U");
+    c->bstc(lt3, R1, U, sh, 1.0, it, n, true, okey + ":U");
     // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
     sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
     c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
@@ -2410,7 +2363,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    bstc_tri(c, tau, U, s.no * s.no * s.nv * s.nv, D + NO, sh, 1.0, it, n, okey + ":ld1");
+    c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, okey + ":ld1");
     it = c->dev_items(okey + ":ld2", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ch.held)
@@ -2419,7 +2372,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
                               {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
       return v;
     }, &n);
-    bstc_tri(c, tau, U, s.no * s.no * s.nv * s.nv, D + NO, sh, -1.0, it, n, okey + ":ld2");
+    c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, okey + ":ld2");
     //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
     y3_like(c, R3t, lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
     // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}

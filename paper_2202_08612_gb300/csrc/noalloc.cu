@@ -1,8 +1,9 @@
 // mlcc3_triples_omega_static: the triples residual with every piece of scratch
 // memory in one fixed device array compiled into the library, for callers that
-// must not allocate device memory when they call (for example while a stream is
-// being captured into a CUDA graph, or inside a loop whose host application
-// forbids or cannot afford a cudaMalloc).  Nothing here calls cudaMalloc,
+// must not allocate device memory when they call (for example a solver loop in
+// a host application that hands all device memory to its own pool at start-up
+// and forbids, or cannot afford the implicit synchronisation of, a cudaMalloc
+// in the loop).  Nothing here calls cudaMalloc,
 // cudaFree or any allocating routine; the context's persistent arrays (built by
 // mlcc3_build_integrals, which does allocate) are read as inputs.
 #include <cuda_runtime.h>

@@ -1,5 +1,7 @@
 """mlcc3_triples_omega_static: the triples residual for callers that cannot
-allocate device memory when they call (stream capture, allocation-free loops).
+allocate device memory when they call (solver loops whose application owns all
+device memory through its own pool, or that cannot afford an allocation's
+synchronisation).
 
 It must give the allocating entry point's results, call after call, while the
 device's free memory stays unchanged.  This file is collected last so that a
