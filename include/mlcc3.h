@@ -182,6 +182,12 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              densities, Cholesky-index builds); 0 = unlimited.  The tensor
  *              cores accumulate with truncation, so the error of a chain
  *              grows with its length.  Default 16 (K = 1024).  Range 0..4096.
+ *   "tc_group"  most unique batches stacked along N in one tile of the
+ *              split-precision triples build: batches that share the two
+ *              occupied indices outside the tile's single virtual position
+ *              share every integral-side operand, so up to tc_group of their
+ *              amplitude operands (one n_v-wide box each) fill one wider MMA.
+ *              Default 4.  Range 1..4 (capped at 256 columns).
  *   "tc_persist_from"  tensor-core launches with more output tiles than this
  *              run the persistent kernel (one CTA per SM looping over tiles,
  *              accumulator double-buffered in TMEM); smaller ones run one CTA

@@ -84,6 +84,7 @@ struct mlcc3_ctx {
   // longest FP32 accumulation chain of the tensor-core kernel, in 64-wide K
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)
   int tc_kcap = 16;
+  int tc_group = 4;  // batches stacked along N in a triples-build tile
   // tensor-core launches with more tiles than this use the persistent kernel
   int tc_persist_from = mlcc3::kTcPersistFrom;
   // batch chunking: at most chunk_blocks blocks held per chunk (0 = sized from

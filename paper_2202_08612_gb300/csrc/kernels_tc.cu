@@ -155,6 +155,38 @@ __device__ __forceinline__ void epi_put16(const TcEpi &epi, long long a0, int n0
   }
 }
 
+// Loads of one pipeline stage for chunk kc of segment sg: A hi/lo (128 rows),
+// then the segment's B boxes (hi into the first BN rows' region, lo into the
+// second), box q at row q * qrows.  The barrier expects exactly these bytes.
+template <int BN>
+__device__ __forceinline__ void issue_stage(const TcMaps &maps, const TcSeg &sg, int kc,
+                                            unsigned char *st, uint32_t fb, int qrows) {
+  constexpr int A_BYTES = 128 * 128;
+  constexpr int B_BYTES = BN * 128;
+  const int nb = sg.nb > 1 ? sg.nb : 1;
+  const int qb = qrows * 128;
+  mbar_expect_tx(fb, 2 * A_BYTES + 2 * nb * qb);
+  const int k = sg.ac[0] + 64 * kc, kb = sg.bc[0] + 64 * kc;
+  tma_load_4d(smem_u32(st), &maps.m[sg.amap], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
+  tma_load_4d(smem_u32(st + A_BYTES), &maps.m[sg.amap + 1], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
+  for (int q = 0; q < nb; ++q) {
+    const int c2 = q ? sg.bq[q - 1][0] : sg.bc[2], c3 = q ? sg.bq[q - 1][1] : sg.bc[3];
+    tma_load_4d(smem_u32(st + 2 * A_BYTES + q * qb), &maps.m[sg.bmap], kb, sg.bc[1], c2, c3, fb);
+    tma_load_4d(smem_u32(st + 2 * A_BYTES + B_BYTES + q * qb), &maps.m[sg.bmap + 1], kb, sg.bc[1],
+                c2, c3, fb);
+  }
+}
+
+// Instruction descriptor with the tile's N (a multiple of 16, at most 256).
+__device__ __forceinline__ uint32_t idesc_n(uint32_t idesc, int n) {
+  return (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n >> 3) << 17);
+}
+
+// Output offset of column group q of a tile.
+__device__ __forceinline__ long long group_off(const TcItem &it, int q) {
+  return q == 0 ? it.out_off : it.qoff[q - 1];
+}
+
 }  // namespace
 
 template <int BN, int STAGES>
@@ -179,6 +211,8 @@ __global__ void __launch_bounds__(192, 1)
   const TcItem &it = items[blockIdx.x];
   const TcSeg *seg = segs + it.seg_begin;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int qrows = epi.qw > 0 ? epi.qw : BN;
+  const int ntile = (it.nq > 1 ? it.nq : 1) * qrows;
   int total = 0;
   for (int s = 0; s < it.seg_count; ++s) total += seg[s].nk;
 
@@ -209,7 +243,7 @@ __global__ void __launch_bounds__(192, 1)
     int issued = 0;
     bool ok = true;
     for (int s = 0; s < it.seg_count && ok; ++s) {
-      const TcSeg sg = seg[s];
+      const TcSeg &sg = seg[s];
       for (int kc = 0; kc < sg.nk; ++kc) {
         if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
           ok = false;
@@ -217,15 +251,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         unsigned char *st = smem + stage * STAGE;
         const uint32_t fb = full0 + 8 * stage;
-        mbar_expect_tx(fb, STAGE);
-        const int k = sg.ac[0] + 64 * kc, kb = sg.bc[0] + 64 * kc;
-        tma_load_4d(smem_u32(st), &maps.m[sg.amap], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
-        tma_load_4d(smem_u32(st + A_BYTES), &maps.m[sg.amap + 1], k, sg.ac[1], sg.ac[2], sg.ac[3],
-                    fb);
-        tma_load_4d(smem_u32(st + 2 * A_BYTES), &maps.m[sg.bmap], kb, sg.bc[1], sg.bc[2],
-                    sg.bc[3], fb);
-        tma_load_4d(smem_u32(st + 2 * A_BYTES + B_BYTES), &maps.m[sg.bmap + 1], kb, sg.bc[1],
-                    sg.bc[2], sg.bc[3], fb);
+        issue_stage<BN>(maps, sg, kc, st, fb, qrows);
         ++issued;
         if (++stage == STAGES) {
           stage = 0;
@@ -255,12 +281,13 @@ __global__ void __launch_bounds__(192, 1)
       unsigned char *st = smem + stage * STAGE;
       const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
       const uint32_t bhi = smem_u32(st + 2 * A_BYTES), blo = smem_u32(st + 2 * A_BYTES + B_BYTES);
+      const uint32_t idesc = idesc_n(IDESC, ntile);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint32_t off = kk * 32;
-        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(bhi + off), IDESC, (c > 0 || kk > 0));
-        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(blo + off), IDESC, 1u);
-        mma_bf16(tmem, smem_desc(alo + off), smem_desc(bhi + off), IDESC, 1u);
+        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(bhi + off), idesc, (c > 0 || kk > 0));
+        mma_bf16(tmem, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1u);
+        mma_bf16(tmem, smem_desc(alo + off), smem_desc(bhi + off), idesc, 1u);
       }
       mma_commit(empty0 + 8 * stage);
       if (++stage == STAGES) {
@@ -285,13 +312,14 @@ __global__ void __launch_bounds__(192, 1)
       r2 = it.r2_0 + row % epi.R2;
     }
     const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
-    const long long base = it.out_off + (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+    const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
 #pragma unroll 1
-    for (int n0 = 0; n0 < BN; n0 += 16) {
+    for (int n0 = 0; n0 < ntile; n0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
       if (!rv) continue;
-      epi_put16(epi, base + (long long)(it.c0 + n0) * epi.sn, it.c0 + n0, v);
+      const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+      epi_put16(epi, group_off(it, q) + rowoff + (long long)nc * epi.sn, nc, v);
     }
   }
   tc_fence_before();
@@ -339,6 +367,7 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int qrows = epi.qw > 0 ? epi.qw : BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -375,7 +404,7 @@ __global__ void __launch_bounds__(192, 1)
     for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x) {
       const TcItem it = items[i];
       for (int q = 0; q < it.seg_count && !*abort_flag; ++q) {
-        const TcSeg sg = segs[it.seg_begin + q];
+        const TcSeg &sg = segs[it.seg_begin + q];
         for (int kc = 0; kc < sg.nk; ++kc) {
           if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
             *abort_flag = 1;
@@ -383,15 +412,7 @@ __global__ void __launch_bounds__(192, 1)
           }
           unsigned char *st = smem + stage * STAGE;
           const uint32_t fb = full0 + 8 * stage;
-          mbar_expect_tx(fb, STAGE);
-          const int k = sg.ac[0] + 64 * kc, kb = sg.bc[0] + 64 * kc;
-          tma_load_4d(smem_u32(st), &maps.m[sg.amap], k, sg.ac[1], sg.ac[2], sg.ac[3], fb);
-          tma_load_4d(smem_u32(st + A_BYTES), &maps.m[sg.amap + 1], k, sg.ac[1], sg.ac[2],
-                      sg.ac[3], fb);
-          tma_load_4d(smem_u32(st + 2 * A_BYTES), &maps.m[sg.bmap], kb, sg.bc[1], sg.bc[2],
-                      sg.bc[3], fb);
-          tma_load_4d(smem_u32(st + 2 * A_BYTES + B_BYTES), &maps.m[sg.bmap + 1], kb, sg.bc[1],
-                      sg.bc[2], sg.bc[3], fb);
+          issue_stage<BN>(maps, sg, kc, st, fb, qrows);
           last[stage] = phase;
           pending[stage] = true;
           if (++stage == STAGES) {
@@ -420,6 +441,7 @@ __global__ void __launch_bounds__(192, 1)
       int total = 0;
       for (int q = 0; q < it.seg_count; ++q) total += segs[it.seg_begin + q].nk;
       const uint32_t acc = tmem + (uint32_t)(u * NCOLS);
+      const uint32_t idesc = idesc_n(IDESC, (it.nq > 1 ? it.nq : 1) * qrows);
       bool ok = true;
       for (int c = 0; c < total; ++c) {
         if (!mbar_wait(full0 + 8 * stage, phase, status)) {
@@ -434,9 +456,9 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t off = kk * 32;
-          mma_bf16(acc, smem_desc(ahi + off), smem_desc(bhi + off), IDESC, (c > 0 || kk > 0));
-          mma_bf16(acc, smem_desc(ahi + off), smem_desc(blo + off), IDESC, 1u);
-          mma_bf16(acc, smem_desc(alo + off), smem_desc(bhi + off), IDESC, 1u);
+          mma_bf16(acc, smem_desc(ahi + off), smem_desc(bhi + off), idesc, (c > 0 || kk > 0));
+          mma_bf16(acc, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1u);
+          mma_bf16(acc, smem_desc(alo + off), smem_desc(bhi + off), idesc, 1u);
         }
         mma_commit(empty0 + 8 * stage);
         if (++stage == STAGES) {
@@ -472,16 +494,18 @@ __global__ void __launch_bounds__(192, 1)
         r2 = it.r2_0 + row % epi.R2;
       }
       const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
-      const long long base = it.out_off + (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+      const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+      const int ntile = (it.nq > 1 ? it.nq : 1) * qrows;
 #pragma unroll 1
-      for (int n0 = 0; n0 < BN; n0 += 16) {
+      for (int n0 = 0; n0 < ntile; n0 += 16) {
         float v[16];
         tmem_ld16(tmem + (uint32_t)(u * NCOLS) + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
         if (!rv) continue;
         if (total == 0)
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        epi_put16(epi, base + (long long)(it.c0 + n0) * epi.sn, it.c0 + n0, v);
+        const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+        epi_put16(epi, group_off(items[i], q) + rowoff + (long long)nc * epi.sn, nc, v);
       }
       tc_fence_before();
       __syncwarp();

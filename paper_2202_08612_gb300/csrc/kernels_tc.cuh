@@ -17,22 +17,28 @@ struct TcMaps {
 
 // One K segment: A rows from map `amap` (hi) / `amap + 1` (lo) at 4-D
 // coordinates ac (ac[0], the K coordinate, advances by 64 per chunk), and the
-// same for B with `bmap` and bc.
+// same for B with `bmap` and bc.  A grouped tile (TcItem::nq = nb > 1) stacks
+// nb B boxes of TcEpi::qw rows along N: box 0 at bc, box q at bc with
+// coordinates 2 and 3 replaced by bq[q - 1].
 struct TcSeg {
-  int amap, bmap, nk, pad;
+  int amap, bmap, nk, nb;
   int ac[4];
   int bc[4];
+  int bq[3][2];
 };
 
-// One 128 x BN output tile: the K segments seg[seg_begin, seg_begin + seg_count)
+// One 128 x N output tile: the K segments seg[seg_begin, seg_begin + seg_count)
 // of the launch's segment array.  Rows r of the tile map to global row
-// coordinates (r1_0 + r / R2, r2_0 + r % R2) in the epilogue.
+// coordinates (r1_0 + r / R2, r2_0 + r % R2) in the epilogue.  A grouped tile
+// has nq > 1 column groups of TcEpi::qw columns (N = nq qw); group q writes at
+// out_off (q = 0) or qoff[q - 1].
 struct TcItem {
   int seg_begin, seg_count;
   int r1_0, r2_0;
   int c0;             // global column of the tile's first column
-  int pad;
+  int nq;             // column groups (0 or 1: one group of BN columns)
   long long out_off;
+  long long qoff[3];
 };
 
 // Epilogue: out[out_off + r1 s1 + r2 s2 + n sn] (op) alpha * acc for
@@ -48,6 +54,7 @@ struct TcEpi {
   long long s1, s2, sn;
   int lim1, lim2, nlim;
   float alpha;
+  int qw;       // columns per group of a grouped tile (0: one group of the launch's BN)
 };
 
 // Status bits written by the tensor-core kernels.

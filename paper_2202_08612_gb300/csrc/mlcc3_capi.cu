@@ -809,6 +809,7 @@ TcEpi make_epi(void *out, int mode, int R2, long long s1, long long s2, long lon
   e.lim2 = (int)lim2;
   e.nlim = (int)nlim;
   e.alpha = (float)alpha;
+  e.qw = 0;
   return e;
 }
 
@@ -925,30 +926,71 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
   const long long cs[3] = {s.nv * s.nv, s.nv, 1};
   std::string sig;
   for (auto &t : terms) sig += t.dtype ? 'd' : 'l';
-  const int BN = tc_tile_width(s.nv);
+  // In orientation o every operand A (integral or Tl pairs) of a batch's tile
+  // depends only on the occupied indices at the other two positions, so the
+  // batches that share them are stacked along N, up to G per tile, each with
+  // its own amplitude box of BW rows and its own output block.
+  const int BW = tc_tile_width(s.nv);
+  const int G = std::max(1, std::min(c->tc_group, 256 / BW));
+  const int BN = tc_tile_width((long long)BW * G);
   for (int o = 0; o < 3; ++o) {
     const int p1 = o == 0 ? 1 : 0, p2 = o == 2 ? 1 : 2;
-    TcDev dv = tc_plan(c, "tc:" + bkey + ":" + sig + ":" + std::to_string(o), [&](TcPlan &pl) {
+    const std::string key = "tc:" + bkey + ":" + sig + ":" + std::to_string(o) + ":g" + std::to_string(G);
+    TcDev dv = tc_plan(c, key, [&](TcPlan &pl) {
+      std::map<std::pair<int, int>, std::vector<long long>> groups;
+      std::vector<std::pair<int, int>> order;
       for (long long u = 0; u < nb; ++u) {
         const int I[3] = {bs[u].i, bs[u].j, bs[u].k};
-        for (long long t1 = 0; t1 < nt1; ++t1)
-          for (long long t2 = 0; t2 < nt2; ++t2) {
-            pl.tile((int)(8 * t1), (int)(16 * t2), 0, bs[u].off);
-            for (size_t t = 0; t < terms.size(); ++t) {
-              for (int sg = 0; sg < 6; ++sg) {
-                const int s0 = kPermH[sg][0], s1 = kPermH[sg][1], s2 = kPermH[sg][2];
-                if (terms[t].dtype && s0 == o)
-                  pl.seg((int)(6 * t) + (s1 < s2 ? 0 : 2), (int)(6 * t) + 4, (int)NVk,
-                         (int)(16 * t2), (int)(8 * t1), I[s2], 0, I[s1], I[s0]);
-                else if (!terms[t].dtype && s2 == o)
-                  pl.seg((int)(6 * t) + (s0 < s1 ? 0 : 2), (int)(6 * t) + 4, (int)NOk,
-                         (int)(16 * t2), (int)(8 * t1), I[s0], 0, I[s2], I[s1]);
+        const auto g = std::make_pair(I[p1], I[p2]);
+        if (!groups.count(g)) order.push_back(g);
+        groups[g].push_back(u);
+      }
+      for (const auto &g : order) {
+        const std::vector<long long> &us = groups[g];
+        for (size_t q0 = 0; q0 < us.size(); q0 += (size_t)G) {
+          const int nq = (int)std::min<size_t>((size_t)G, us.size() - q0);
+          int I[4][3];
+          for (int q = 0; q < nq; ++q) {
+            const TripItem &b = bs[us[q0 + q]];
+            I[q][0] = b.i;
+            I[q][1] = b.j;
+            I[q][2] = b.k;
+          }
+          for (long long t1 = 0; t1 < nt1; ++t1)
+            for (long long t2 = 0; t2 < nt2; ++t2) {
+              pl.tile((int)(8 * t1), (int)(16 * t2), 0, bs[us[q0]].off);
+              pl.items.back().nq = nq;
+              for (int q = 1; q < nq; ++q) pl.items.back().qoff[q - 1] = bs[us[q0 + q]].off;
+              for (size_t t = 0; t < terms.size(); ++t) {
+                for (int sg = 0; sg < 6; ++sg) {
+                  const int s0 = kPermH[sg][0], s1 = kPermH[sg][1], s2 = kPermH[sg][2];
+                  int x = -1, y = -1;  // positions of the B box coordinates 2 and 3
+                  if (terms[t].dtype && s0 == o) {
+                    pl.seg((int)(6 * t) + (s1 < s2 ? 0 : 2), (int)(6 * t) + 4, (int)NVk,
+                           (int)(16 * t2), (int)(8 * t1), I[0][s2], 0, I[0][s1], I[0][s0]);
+                    x = s1;
+                    y = s0;
+                  } else if (!terms[t].dtype && s2 == o) {
+                    pl.seg((int)(6 * t) + (s0 < s1 ? 0 : 2), (int)(6 * t) + 4, (int)NOk,
+                           (int)(16 * t2), (int)(8 * t1), I[0][s0], 0, I[0][s2], I[0][s1]);
+                    x = s2;
+                    y = s1;
+                  }
+                  if (x < 0) continue;
+                  TcSeg &last = pl.segs.back();
+                  last.nb = nq;
+                  for (int q = 1; q < nq; ++q) {
+                    last.bq[q - 1][0] = I[q][x];
+                    last.bq[q - 1][1] = I[q][y];
+                  }
+                }
               }
             }
-          }
+        }
       }
     });
     TcEpi epi = make_epi(W, o == 0 ? 0 : 1, 16, cs[p1], cs[p2], cs[o], s.nv, s.nv, s.nv, 1.0);
+    epi.qw = BW;
     double K = 0.0;
     for (auto &t : terms) K += 2.0 * (t.dtype ? (double)s.NV : (double)s.NO);
     tc_launch(c, BN, maps, dv, epi, 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb);
@@ -2436,15 +2478,25 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       tc_vv(c, lt3, "X", R3, "Y", ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
     else
       vv_block(c, lt3, R3, ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
-    // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings)
-    it = c->dev_items(okey + ":dots", [&] {
-      std::vector<BstcItem> v;
-      for (auto &o : ch.own)
-        v.push_back(mk_item(o.off, o.off, 0, {0, 0, 0, 0, 1}, {0, 0, 1, 0, 0}, {0, 0, 0, 0}));
-      return v;
-    }, &n);
-    sh = Shape{}; sh.K3 = s.nv3;
-    c->dot(lt3, R3, sc, sh, 1.0 / 6.0, it, n);
+    // normalisation: lambda3.R3 = 1/6 sum lt R3 (all orderings).  Every
+    // ordering of a batch permutes both blocks alike, so each owned block is
+    // dotted once, weighted by its number of distinct orderings (6 or 3).
+    std::map<long long, int> mult;
+    for (auto &o : ch.own) mult[o.off] += 1;
+    for (int m = 1; m <= 6; ++m) {
+      bool any = false;
+      for (auto &kv : mult) any = any || kv.second == m;
+      if (!any) continue;
+      it = c->dev_items(okey + ":dots" + std::to_string(m), [&] {
+        std::vector<BstcItem> v;
+        for (auto &kv : mult)
+          if (kv.second == m)
+            v.push_back(mk_item(kv.first, kv.first, 0, {0, 0, 0, 0, 1}, {0, 0, 1, 0, 0}, {0, 0, 0, 0}));
+        return v;
+      }, &n);
+      sh = Shape{}; sh.K3 = s.nv3;
+      c->dot(lt3, R3, sc, sh, (double)m / 6.0, it, n);
+    }
   }
   // lambda_SD.R_SD, then the normalisation term of D^{0-m}
   launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
@@ -2663,6 +2715,9 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     if (n == "tc_kcap") {
       if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, "tc_kcap out of range 0..4096"};
       c->tc_kcap = (int)value;
+    } else if (n == "tc_group") {
+      if (value < 1 || value > 4) throw Error{MLCC3_ERR_ARG, "tc_group out of range 1..4"};
+      c->tc_group = (int)value;
     } else if (n == "tc_persist_from") {
       if (value < 0) throw Error{MLCC3_ERR_ARG, "tc_persist_from must be >= 0"};
       c->tc_persist_from = (int)std::min<long long>(value, 1LL << 30);
