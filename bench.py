@@ -503,11 +503,12 @@ def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core):
 
 
 def run_large(args):
-    """Large guanine- or betaine-shaped system in the split precision: integral
-    build, Omega, then --steps timed Davidson iterations (rho and sigma of all
-    valence trial vectors in one call each, after --warmup untimed ones), and
-    with --densities the three transition densities and f of one state.  The
-    roofline line is the tensor-core kernel's share of the Davidson iterations."""
+    """Large guanine- or betaine-shaped system in the split precision.  Stage
+    "davidson": integral build, Omega, then --steps timed Davidson iterations
+    (rho and sigma of all valence trial vectors in one call each, after --warmup
+    untimed ones); the roofline line is the tensor-core kernel's share of them.
+    Stage "densities": integral build, then the three transition densities and f
+    of one state (run_large_densities)."""
     import torch
     from paper_2202_08612_gb300 import binding, build
     build.build()
@@ -515,6 +516,8 @@ def run_large(args):
     torch.cuda.set_device(dev)
     NO, NV, no, nv, NJ, nvec = LARGE[args.workload]
     core = args.workload == "betaine_like"
+    if args.stage == "densities":
+        nvec = 1
     x, omega = device_system(NO, NV, no, nv, NJ, nvec, 2022, dev, core)
     stream = torch.cuda.current_stream(dev)
     prec = binding.MLCC3_SPLIT_BF16X3 if args.precision == "split" else binding.MLCC3_FP64
@@ -529,7 +532,8 @@ def run_large(args):
     ctx = binding.Context(NO, NV, no, nv, NJ, precision=prec, stream=stream.cuda_stream)
     # unique batches held per chunk: leaves room for the integral blocks, their
     # split copies and the per-call scratch next to the caller's tensors
-    ctx.set_param("chunk_blocks", args.chunk_blocks)
+    if args.stage != "densities":
+        ctx.set_param("chunk_blocks", args.chunk_blocks)
     if args.tc_group:
         ctx.set_param("tc_group", args.tc_group)
     unit = NV * nv ** 3 * no ** 3
@@ -546,6 +550,9 @@ def run_large(args):
     ms_build = timed(lambda: ctx.build_integrals(x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"]))
     del x["chol"]  # the context keeps its own T1-transformed copy
     torch.cuda.empty_cache()
+    if args.stage == "densities":
+        return run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ,
+                                   core, prec == binding.MLCC3_SPLIT_BF16X3)
     ms_omega_first = timed(lambda: ctx.triples_omega(o1, o2))
     ms_omega = timed(lambda: ctx.triples_omega(o1, o2))
 
@@ -566,24 +573,6 @@ def run_large(args):
     pk = peaks().get("bf16_tflops_sustained") or 1700.0
     alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
     fl_it = 16.0 * unit * nvec
-    dens = None
-    if args.densities:
-        # the densities hold six triples arrays at once: half-size chunks
-        del rho1, rho2, sig1, sig2
-        torch.cuda.empty_cache()
-        ctx.set_param("chunk_blocks", max(1, args.chunk_blocks // 2))
-        w = float(omega[0])
-        f = []
-        try:
-            ms_d = timed(lambda: (ctx.transition_density(w, x["lam1"], x["lam2"], x["R1"][0],
-                                                         x["R2"][0], x["L1"][0], x["L2"][0],
-                                                         x["D00_in"], *D),
-                                  f.append(ctx.oscillator_strength(w, D[2], D[1], x["mu"]))))
-            dens = {"ms": ms_d, "tflops": 36.0 * unit / (ms_d * 1e-3) / 1e12,
-                    "flop_units": "(10 + 10 + 16) N_V n_v^3 n_o^3", "f": f[0],
-                    "chunk_blocks": max(1, args.chunk_blocks // 2)}
-        except binding.MLCC3Error as e:
-            dens = {"error": str(e)}
     line = {"metric": METRIC, "value": fl_it / (ms_it * 1e-3) / 1e12, "unit": "TFLOP/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_it,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -598,7 +587,6 @@ def run_large(args):
             "build_integrals_ms": ms_build,
             "omega": {"ms": ms_omega, "ms_first_call": ms_omega_first,
                       "tflops": 4.0 * unit / (ms_omega * 1e-3) / 1e12},
-            "densities_one_state": dens,
             "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor",
                          "achieved": 3.0 * alg if alg else None, "peak": pk, "unit": "TFLOP/s",
                          "frac": 3.0 * alg / pk if alg else None, "achieved_algorithmic": alg,
@@ -608,6 +596,57 @@ def run_large(args):
             "clocks": clk.summary(),
             "hbm_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev)),
             "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
+                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ, core, split):
+    """The three transition densities and f of one state of a large system, in a
+    process of their own: the densities hold every batch that touches a range of
+    occupied indices (at 100/1000/20/150 about 300 blocks of n_v^3 per array)."""
+    import torch
+    w = float(omega[0])
+    f = []
+    dev = x["R1"].device
+    stream = torch.cuda.current_stream(dev)
+
+    def run():
+        ctx.transition_density(w, x["lam1"], x["lam2"], x["R1"][0], x["R2"][0], x["L1"][0],
+                               x["L2"][0], x["D00_in"], *D)
+        f.append(ctx.oscillator_strength(w, D[2], D[1], x["mu"]))
+
+    ctx.profile(True)
+    with ClockSampler(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    tc = [v for k, v in stats.items() if k.startswith("tc_gemm")]
+    tc_ms, tc_fl = sum(v[1] for v in tc), sum(v[2] for v in tc)
+    pk = peaks().get("bf16_tflops_sustained") or 1700.0
+    alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    line = {"metric": METRIC, "value": 36.0 * unit / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3" if split else "f64", "data": "synthetic (device-generated, torch Philox)",
+            "config": {"workload": f"{args.workload}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}, one state"
+                                   + (", core orbital at -10 Ha" if core else ""),
+                       "step": "D^{0-0}, D^{m-0}, D^{0-m} and f of one state (first call)",
+                       "flop_units": "(10 + 10 + 16) N_V n_v^3 n_o^3"},
+            "f": f[0], "build_integrals_ms": ms_build,
+            "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor",
+                         "achieved": 3.0 * alg if alg else None, "peak": pk, "unit": "TFLOP/s",
+                         "frac": 3.0 * alg / pk if alg else None, "achieved_algorithmic": alg,
+                         "share_of_step": tc_ms / ms},
+            "clocks": clk.summary(),
+            "hbm_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev)),
+            "call_sites": {k: round(v[1], 3) for k, v in
                            sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]}}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -628,8 +667,9 @@ def main():
                     help="batches per triples-build tensor-core tile (0: library default)")
     ap.add_argument("--chunk-blocks", type=int, default=128,
                     help="large workloads: unique batches held per chunk")
-    ap.add_argument("--densities", action="store_true",
-                    help="large workloads: also time the densities and f of one state")
+    ap.add_argument("--stage", default="davidson", choices=("davidson", "densities"),
+                    help="large workloads: Davidson iterations (rho, sigma) or the densities "
+                         "and f of one state")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the untimed FP64-path comparison step")
     args = ap.parse_args()

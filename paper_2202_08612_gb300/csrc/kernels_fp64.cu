@@ -633,10 +633,11 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
     unsigned long long nvinv, double omega_v, const double *__restrict__ omega_p,
     double *__restrict__ out, int *__restrict__ status) {
+  // one (term, permutation) pair: the operand indices are linear in the
+  // element's canonical coordinates (x0, x1, x2) with coefficients ca / cb
   struct Ent {
     const float *pa, *pb;
-    int au, av, bv, bw;
-    int p0, p1, p2;
+    int ca[3], cb[3];
     float coef;
   };
   __shared__ Ent tab[2 * kMaxTerms * 6];
@@ -658,42 +659,45 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
       if (tm.kind < 2) continue;
       for (int sg = 0; sg < 6; ++sg) {
         Ent e;
-        e.p0 = kPerm[sg][0];
-        e.p1 = kPerm[sg][1];
-        e.p2 = kPerm[sg][2];
-        const long long x = I[e.p0], y = I[e.p1], z = I[e.p2];
+        const int p0 = kPerm[sg][0], p1 = kPerm[sg][1], p2 = kPerm[sg][2];
+        const long long x = I[p0], y = I[p1], z = I[p2];
         e.coef = (float)tm.coef;
-        e.av = 0;
+        int au, av = 0, bv, bw;
         if (tm.kind == 2) {  // A[x][u] B[y][z][v][w]
-          if (e.p0 == 2 && tm.At32) {
+          if (p0 == 2 && tm.At32) {
             e.pa = tm.At32 + x * tm.sAt[1];
-            e.au = (int)tm.sAt[0];
+            au = (int)tm.sAt[0];
           } else {
             e.pa = tm.A32 + x * tm.sA[0];
-            e.au = (int)tm.sA[1];
+            au = (int)tm.sA[1];
           }
-          if (e.p1 == 2 && tm.sym) {
+          if (p1 == 2 && tm.sym) {
             e.pb = tm.B32 + z * tm.sB[0] + y * tm.sB[1];
-            e.bv = (int)tm.sB[3];
-            e.bw = (int)tm.sB[2];
+            bv = (int)tm.sB[3];
+            bw = (int)tm.sB[2];
           } else {
             e.pb = tm.B32 + y * tm.sB[0] + z * tm.sB[1];
-            e.bv = (int)tm.sB[2];
-            e.bw = (int)tm.sB[3];
+            bv = (int)tm.sB[2];
+            bw = (int)tm.sB[3];
           }
         } else {  // A[x][y][u][v] B[z][w]
-          if (e.p0 == 2 && tm.sym) {
+          if (p0 == 2 && tm.sym) {
             e.pa = tm.A32 + y * tm.sA[0] + x * tm.sA[1];
-            e.au = (int)tm.sA[3];
-            e.av = (int)tm.sA[2];
+            au = (int)tm.sA[3];
+            av = (int)tm.sA[2];
           } else {
             e.pa = tm.A32 + x * tm.sA[0] + y * tm.sA[1];
-            e.au = (int)tm.sA[2];
-            e.av = (int)tm.sA[3];
+            au = (int)tm.sA[2];
+            av = (int)tm.sA[3];
           }
           e.pb = tm.B32 + z * tm.sB[0];
-          e.bv = 0;
-          e.bw = (int)tm.sB[1];
+          bv = 0;
+          bw = (int)tm.sB[1];
+        }
+        // u = x_{p0}, v = x_{p1}, w = x_{p2}
+        for (int k = 0; k < 3; ++k) {
+          e.ca[k] = (p0 == k ? au : 0) + (p1 == k ? av : 0);
+          e.cb[k] = (p1 == k ? bv : 0) + (p2 == k ? bw : 0);
         }
         tab[n++] = e;
       }
@@ -701,30 +705,53 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     nent = n;
   }
   __syncthreads();
+  // eight elements per thread and pass (r0 + k * stride), so that each table
+  // entry is read once per eight elements
   const unsigned int nv3 = (unsigned int)nv * nv * nv;
-  for (unsigned int r = blockIdx.x * blockDim.x + threadIdx.x; r < nv3; r += gridDim.x * blockDim.x) {
-    const unsigned int q1 = div_inv(r, nvinv);
-    const unsigned int q0 = div_inv(q1, nvinv);
-    const int X[3] = {(int)q0, (int)(q1 - q0 * nv), (int)(r - q1 * nv)};
-    float acc = W[it.off + r];
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < nv3; r0 += 8 * stride) {
+    float acc[8];
+    int x0[8], x1[8], x2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned int r = r0 + k * stride;
+      const unsigned int rr = r < nv3 ? r : 0;
+      const unsigned int q1 = div_inv(rr, nvinv);
+      const unsigned int q0 = div_inv(q1, nvinv);
+      x0[k] = (int)q0;
+      x1[k] = (int)(q1 - q0 * nv);
+      x2[k] = (int)(rr - q1 * nv);
+      acc[k] = r < nv3 ? W[it.off + r] : 0.f;
+    }
     for (int n = 0; n < nent; ++n) {
       const Ent &e = tab[n];
-      const int u = X[e.p0], v = X[e.p1], w = X[e.p2];
-      acc = fmaf(e.coef * e.pa[u * e.au + v * e.av], e.pb[v * e.bv + w * e.bw], acc);
+      const float *pa = e.pa, *pb = e.pb;
+      const int a0 = e.ca[0], a1 = e.ca[1], a2 = e.ca[2];
+      const int b0 = e.cb[0], b1 = e.cb[1], b2 = e.cb[2];
+      const float cf = e.coef;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        acc[k] = fmaf(cf * pa[x0[k] * a0 + x1[k] * a1 + x2[k] * a2],
+                      pb[x0[k] * b0 + x1[k] * b1 + x2[k] * b2], acc[k]);
     }
-    float dh = ev[X[0]].x, dl = ev[X[0]].y;
-    df_add(dh, dl, ev[X[1]].x, ev[X[1]].y);
-    df_add(dh, dl, ev[X[2]].x, ev[X[2]].y);
-    df_add(dh, dl, eoh, eol);
-    const float den = dh + dl;
-    double val;
-    if (fabsf(den) < 1e-3f) {
-      atomicOr(status, 1);
-      val = 0.0;
-    } else {
-      val = widen_f32(-acc * __frcp_rn(den));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned int r = r0 + k * stride;
+      if (r >= nv3) break;
+      float dh = ev[x0[k]].x, dl = ev[x0[k]].y;
+      df_add(dh, dl, ev[x1[k]].x, ev[x1[k]].y);
+      df_add(dh, dl, ev[x2[k]].x, ev[x2[k]].y);
+      df_add(dh, dl, eoh, eol);
+      const float den = dh + dl;
+      double val;
+      if (fabsf(den) < 1e-3f) {
+        atomicOr(status, 1);
+        val = 0.0;
+      } else {
+        val = widen_f32(-acc[k] * __frcp_rn(den));
+      }
+      out[it.off + r] = val;
     }
-    out[it.off + r] = val;
   }
 }
 

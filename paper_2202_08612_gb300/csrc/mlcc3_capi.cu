@@ -1171,16 +1171,41 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
   }
   const long long ntD = (s.NV + 127) / 128;
   const int nk = (int)((s.nv * s.nv + 63) / 64);
-  TcDev dv = tc_plan(c, "tcD:" + okey, [&](TcPlan &pl) {
-    for (auto &o : ords)
-      for (long long t = 0; t < ntD; ++t) {
-        pl.tile(0, (int)(128 * t), 0, o.p * s.bi + o.q * s.bL);
-        pl.seg(o.sp[1] < o.sp[2] ? 0 : 2, 4 + 2 * o.sp[0], nk, (int)(128 * t), 0, o.r, 0, 0,
-               (int)(o.off / s.nv3));
+  // orderings with the same r and the same canonical positions share the
+  // integral operand and the layout map: up to G of them are stacked along N
+  const int G = std::max(1, std::min(c->tc_group, 256 / (int)BN));
+  TcDev dv = tc_plan(c, "tcD:" + okey + ":g" + std::to_string(G), [&](TcPlan &pl) {
+    std::map<std::array<int, 3>, std::vector<const Ord *>> groups;
+    std::vector<std::array<int, 3>> order;
+    for (auto &o : ords) {
+      const std::array<int, 3> g{o.r, o.sp[1] < o.sp[2] ? 0 : 2, o.sp[0]};
+      if (!groups.count(g)) order.push_back(g);
+      groups[g].push_back(&o);
+    }
+    for (const auto &g : order) {
+      const std::vector<const Ord *> &os = groups[g];
+      for (size_t q0 = 0; q0 < os.size(); q0 += (size_t)G) {
+        const int nq = (int)std::min<size_t>((size_t)G, os.size() - q0);
+        for (long long t = 0; t < ntD; ++t) {
+          const Ord &o = *os[q0];
+          pl.tile(0, (int)(128 * t), 0, o.p * s.bi + o.q * s.bL);
+          pl.items.back().nq = nq;
+          for (int q = 1; q < nq; ++q)
+            pl.items.back().qoff[q - 1] = os[q0 + q]->p * s.bi + os[q0 + q]->q * s.bL;
+          pl.seg(g[1], 4 + 2 * g[2], nk, (int)(128 * t), 0, o.r, 0, 0, (int)(o.off / s.nv3));
+          TcSeg &last = pl.segs.back();
+          last.nb = nq;
+          for (int q = 1; q < nq; ++q) {
+            last.bq[q - 1][0] = 0;
+            last.bq[q - 1][1] = (int)(os[q0 + q]->off / s.nv3);
+          }
+        }
       }
+    }
   }, c->tc_kcap);
   TcEpi epi = make_epi(Zb, 2, 128, 0, 1, s.ba, 1, s.NV, s.nv, b.cD);
-  tc_launch(c, (int)BN, maps, dv, epi,
+  epi.qw = (int)BN;
+  tc_launch(c, tc_tile_width((long long)BN * G), maps, dv, epi,
             2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size());
 }
 
