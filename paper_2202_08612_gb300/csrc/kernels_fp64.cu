@@ -160,12 +160,17 @@ __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   __shared__ double red[256];
   const BstcItem &it = p.items[blockIdx.x];
   const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
-  const long long K = (long long)K1 * K2 * K3;
+  const long long Kall = (long long)K1 * K2 * K3;
   const double *A = p.A + it.offA, *B = p.B + it.offB;
-  // split the first K index once, then advance by 256 with 32-bit carries
-  const int t0 = threadIdx.x;
-  int k3 = t0 % K3, k12 = t0 / K3;
-  int k2 = k12 % K2, k1 = k12 / K2;
+  // block y of gridDim.y takes the K range [y kchunk, (y + 1) kchunk) (kchunk a
+  // multiple of 256; 0 = all of K); split the thread's first K index once,
+  // then advance by 256 with 32-bit carries
+  const long long kb = p.kchunk > 0 ? (long long)blockIdx.y * p.kchunk : 0;
+  const long long K = p.kchunk > 0 ? min(Kall, kb + p.kchunk) : Kall;
+  const long long t0 = kb + threadIdx.x;
+  const long long k12l = t0 / K3;
+  int k3 = (int)(t0 % K3);
+  int k2 = (int)(k12l % K2), k1 = (int)(k12l / K2);
   const int d3 = 256 % K3, d12 = 256 / K3;
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
@@ -824,7 +829,8 @@ namespace mlcc3 {
 
 // D_kl-type pair terms: out[k][l] (kl = 1, else out[l][k]) += alpha sum_{abc}
 // X_{ijl}[abc] Y_{ijk}[abc] for the ordered pair (i, j) = (p0 + y / no, y % no),
-// y = blockIdx.y, over all k, l with stored views.  View (p,q,r) is the block
+// y = blockIdx.y, over all k, l with stored views; blocks with j > i return (their
+// sums are those of (j, i), counted twice by the block of (i, j)).  View (p,q,r) is the block
 // at voff[v] with strides vstr[3v..3v+2] of its (a, b, c) (v = (p no + q) no + r,
 // vhave[v] = 0 for a missing block); the strides are a permutation of
 // (nv^2, nv, 1).  The block copies its no views' offsets and axis orders to
@@ -858,6 +864,11 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
   __shared__ int s_ax[32][3];                   // logical axis of physical axis 0 (fastest), 1, 2
   __shared__ int s_have[32];
   const int i = p0 + (int)blockIdx.y / no, j = (int)blockIdx.y % no;
+  // the ordered pair (j, i) gives the same sums as (i, j): X_{jil}[abc] =
+  // X_{ijl}[bac] and Y likewise, and a <-> b only relabels the summation, so
+  // only j <= i runs, with weight 2 for j < i
+  if (j > i) return;
+  const double wij = j < i ? 2.0 : 1.0;
   const int t = threadIdx.x;
   for (int q = t; q < 2 * no * TS; q += blockDim.x) xs[q] = T(0);
   if (t < no) {
@@ -963,7 +974,7 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
     for (int dl = 0; dl < 4; ++dl) {
       const int kk = k0 + dk, ll = l0 + dl;
       if (kk >= no || ll >= no || acc[dk][dl] == 0.0) continue;
-      atomicAdd(out + (kl ? kk * ldo + ll : ll * ldo + kk), alpha * acc[dk][dl]);
+      atomicAdd(out + (kl ? kk * ldo + ll : ll * ldo + kk), wij * alpha * acc[dk][dl]);
     }
 }
 
@@ -987,6 +998,149 @@ __global__ void __launch_bounds__(256, 3) pair_dots_f32_kernel(
     double *__restrict__ out, long long ldo, int kl, double alpha) {
   pair_dots_body<float, 8>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
+
+// Physical-order form of pair_dots_f32_kernel for n_v a multiple of 4 (every
+// row of a block then starts on a 16-byte boundary): each view's 8x8x8 tile is
+// copied in its own storage order, sixteen bytes (four elements along the
+// stride-1 axis) per cp.async, and the products read each view through its
+// logical strides in shared memory (64, 8 or 1 per logical axis).  Thread t
+// keeps a 4x4 (k,l) tile of partial sums over a share of the tile's 64 (a,b)
+// rows.  Same sums as pair_dots_f32_kernel.
+constexpr int kPdTS = 512 + 4;  // floats per view tile in shared memory (16-byte multiple)
+
+__global__ void __launch_bounds__(256, 2) pair_dots_phys_kernel(
+    const float *__restrict__ X, const float *__restrict__ Y, const long long *__restrict__ voff,
+    const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
+    double *__restrict__ out, long long ldo, int kl, double alpha) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float *xs = reinterpret_cast<float *>(smraw);  // [no][kPdTS]
+  float *ys = xs + (size_t)no * kPdTS;           // [no][kPdTS]
+  __shared__ long long s_off[32];
+  __shared__ int s_ax[32][3];  // logical axis stored along physical axis x (slowest), y, z
+  __shared__ int s_sm[32][3];  // shared-memory stride of logical axis a, b, c
+  __shared__ int s_have[32];
+  const int i = p0 + (int)blockIdx.y / no, j = (int)blockIdx.y % no;
+  // the ordered pair (j, i) gives the same sums as (i, j): X_{jil}[abc] =
+  // X_{ijl}[bac] and Y likewise, and a <-> b only relabels the summation, so
+  // only j <= i runs, with weight 2 for j < i
+  if (j > i) return;
+  const double wij = j < i ? 2.0 : 1.0;
+  const int t = threadIdx.x;
+  for (int q = t; q < 2 * no * kPdTS; q += blockDim.x) xs[q] = 0.f;
+  if (t < no) {
+    const int v = (i * no + j) * no + t;
+    s_have[t] = vhave[v];
+    s_off[t] = voff[v];
+    // logical axes ordered by stride, ascending (a stable sort, so that a
+    // missing view, whose strides are all zero, still gets a permutation):
+    // the smallest stride is stored along z, the largest along x
+    int st[3] = {vstr[3 * v], vstr[3 * v + 1], vstr[3 * v + 2]};
+    int ax[3] = {0, 1, 2};
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y + 1 < 3 - x; ++y)
+        if (st[ax[y]] > st[ax[y + 1]]) {
+          const int tmp = ax[y];
+          ax[y] = ax[y + 1];
+          ax[y + 1] = tmp;
+        }
+    s_ax[t][2] = ax[0];
+    s_ax[t][1] = ax[1];
+    s_ax[t][0] = ax[2];
+    s_sm[t][ax[0]] = 1;
+    s_sm[t][ax[1]] = 8;
+    s_sm[t][ax[2]] = 64;
+  }
+  __syncthreads();
+  const int nh = (no + 3) / 4;
+  const int TT = nh * nh;
+  const int H = 256 / TT;
+  const int tile = t % TT, h = t / TT;
+  const int k0 = 4 * (tile / nh), l0 = 4 * (tile % nh);
+  const int row0 = h * 64 / H, row1 = (h + 1) * 64 / H;  // (a,b) rows of this share
+  int xr[4], yr[4];
+  for (int d = 0; d < 4; ++d) {
+    xr[d] = min(l0 + d, no - 1);
+    yr[d] = min(k0 + d, no - 1);
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
+  const int tb = (nv + 7) / 8;
+  const int ntiles = tb * tb * tb;
+  const long long nv2 = (long long)nv * nv;
+  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const int org[3] = {8 * (q / (tb * tb)), 8 * ((q / tb) % tb), 8 * (q % tb)};
+    __syncthreads();  // the previous tile's reads are done
+    // 128 sixteen-byte chunks per view tile: row (x, y) = c >> 1, z = 4 (c & 1)
+    for (int u = t; u < no * 128; u += 256) {
+      const int r = u >> 7, c = u & 127, row = c >> 1, hz = c & 1;
+      const int px = org[s_ax[r][0]] + (row >> 3), py = org[s_ax[r][1]] + (row & 7);
+      const int pz = org[s_ax[r][2]] + 4 * hz;
+      const bool ok = s_have[r] != 0 && px < nv && py < nv && pz < nv;
+      const long long o = ok ? s_off[r] + px * nv2 + (long long)py * nv + pz : 0;
+      const int sp = r * kPdTS + 4 * c;
+      const unsigned nbytes = ok ? 16u : 0u;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(xs + sp)),
+                   "l"(X + o), "r"(nbytes)
+                   : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(ys + sp)),
+                   "l"(Y + o), "r"(nbytes)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (h < H) {
+      float p[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) p[x][y] = 0.f;
+      for (int row = row0; row < row1; ++row) {
+        const int a = row >> 3, b = row & 7;
+        int ux[4], uy[4], cx[4], cy[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          ux[d] = xr[d] * kPdTS + a * s_sm[xr[d]][0] + b * s_sm[xr[d]][1];
+          uy[d] = yr[d] * kPdTS + a * s_sm[yr[d]][0] + b * s_sm[yr[d]][1];
+          cx[d] = s_sm[xr[d]][2];
+          cy[d] = s_sm[yr[d]][2];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float u[4], w[4];
+#pragma unroll
+          for (int d = 0; d < 4; ++d) {
+            u[d] = xs[ux[d] + c * cx[d]];
+            w[d] = ys[uy[d] + c * cy[d]];
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) p[x][y] += w[x] * u[y];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += (double)p[x][y];
+    }
+  }
+  if (h >= H) return;
+#pragma unroll
+  for (int dk = 0; dk < 4; ++dk)
+#pragma unroll
+    for (int dl = 0; dl < 4; ++dl) {
+      const int kk = k0 + dk, ll = l0 + dl;
+      if (kk >= no || ll >= no || acc[dk][dl] == 0.0) continue;
+      atomicAdd(out + (kl ? kk * ldo + ll : ll * ldo + kk), wij * alpha * acc[dk][dl]);
+    }
+}
+
+size_t pair_dots_phys_smem(int no) { return 2 * (size_t)no * kPdTS * sizeof(float); }
 
 __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
     const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,

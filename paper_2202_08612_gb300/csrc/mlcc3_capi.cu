@@ -36,6 +36,9 @@ __global__ void pair_dots_f32_kernel(const float *, const float *, const long lo
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 size_t pair_dots_smem(int no, bool f32);
+size_t pair_dots_phys_smem(int no);
+__global__ void pair_dots_phys_kernel(const float *, const float *, const long long *, const int *,
+                                      const char *, int, int, int, double *, long long, int, double);
 long long pair_dots_tiles(int nv, bool f32);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void transpose2d_kernel(const double *, double *, int, int);
@@ -289,8 +292,14 @@ void mlcc3_ctx::dot(const double *A, const double *B, double *C, const Shape &sh
   p.alpha = alpha;
   p.items = it;
   p.nitems = nitems;
-  launch("bstc_dot_kernel", 2.0 * (double)(sh.K1 * sh.K2 * sh.K3) * nitems,
-         [&] { bstc_dot_kernel<<<nitems, 256, 0, stream>>>(p); });
+  // long dots over few items: split K across blocks (partial sums added atomically)
+  const long long K = sh.K1 * sh.K2 * sh.K3;
+  long long ys = std::min<long long>(K / (256 * 64), (4 * 152 + nitems - 1) / nitems);
+  ys = std::max<long long>(1, std::min<long long>(ys, 65535));
+  p.kchunk = ys > 1 ? ((K + ys - 1) / ys + 255) / 256 * 256 : 0;
+  if (p.kchunk > 0) ys = (K + p.kchunk - 1) / p.kchunk;
+  launch("bstc_dot_kernel", 2.0 * (double)K * nitems,
+         [&] { bstc_dot_kernel<<<dim3((unsigned)nitems, (unsigned)ys), 256, 0, stream>>>(p); });
   check_cuda(cudaGetLastError(), "dot launch");
 }
 
@@ -599,6 +608,32 @@ mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
                 const double *PA, const double *PB, double *Uv, double *Uo, double *H1, double *H2);
 
+int occ_pos(const Ord &o, int pos) { return pos == 0 ? o.p : pos == 1 ? o.q : o.r; }
+
+// A strided contraction over the orderings `os` of pair-symmetric triples
+// blocks whose other operand is symmetric under the exchange of two of the
+// ordering's (occupied, virtual) pairs: the mirror ordering (positions x and y
+// exchanged) contributes exactly what the ordering does (the exchange only
+// relabels the summed virtual indices), so the orderings with o[x] < o[y] are
+// skipped and those with o[x] > o[y] counted twice.  `os` holds every distinct
+// ordering of each batch, so every mirror pair is present.
+void bstc_mirror(mlcc3_ctx *c, const double *X, const double *B, double *C, const Shape &sh,
+                 double alpha, const std::vector<Ord> &os, int x, int y, const std::string &key,
+                 const std::function<BstcItem(const Ord &)> &item) {
+  for (int w = 2; w >= 1; --w) {
+    int n = 0;
+    const BstcItem *it = c->dev_items(key + (w == 2 ? ":mx2" : ":mx1"), [&] {
+      std::vector<BstcItem> v;
+      for (auto &o : os) {
+        const int ox = occ_pos(o, x), oy = occ_pos(o, y);
+        if ((w == 2 && ox > oy) || (w == 1 && ox == oy)) v.push_back(item(o));
+      }
+      return v;
+    }, &n);
+    c->bstc(X, B, C, sh, alpha * w, it, n, true, key);
+  }
+}
+
 void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
                    const std::string &okey, const BackSet &bset, double *s1, double *Zb) {
   S s(c);
@@ -606,16 +641,13 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
   const BstcItem *it;
   Shape sh;
   if (bset.Gs) {
-    it = c->dev_items(okey + ":bs", [&] {
-      std::vector<BstcItem> v;
-      for (auto &o : ords)
-        v.push_back(mk_item(o.off, o.q * s.vj + o.r * s.vk, o.p,
-                            {o.vs[0], 0, o.vs[1], o.vs[2], 0}, {s.vb, 1, 0, 0, 0}, {s.NO, 0, 0, 0}));
-      return v;
-    }, &n);
+    // Gs[q][b][r][c] = g_qbrc is symmetric under (q,b) <-> (r,c)
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(X, bset.Gs, s1, sh, bset.cs, it, n, true, okey + ":bs");
+    bstc_mirror(c, X, bset.Gs, s1, sh, bset.cs, ords, 1, 2, okey + ":bs", [&](const Ord &o) {
+      return mk_item(o.off, o.q * s.vj + o.r * s.vk, o.p, {o.vs[0], 0, o.vs[1], o.vs[2], 0},
+                     {s.vb, 1, 0, 0, 0}, {s.NO, 0, 0, 0});
+    });
   }
   // split mode: the F term rides on the D-slot GEMM (split_gt folds cF/cD F_kc into it)
   if (bset.F && !(split_mode(c) && bset.GD)) {
@@ -1967,15 +1999,11 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
         c->bstc(taut, LcT, P1, sh, 1.0, it, n, true, okey + ":y2");
       }
       // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
-      it = c->dev_items(okey + ":y3", [&] {
-        std::vector<BstcItem> vv;
-        for (auto &o : os)
-          vv.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
-                               {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
-        return vv;
-      }, &n);
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-      c->bstc(taut, Lc, Y3, sh, 0.5, it, n, true, okey + ":y3");
+      bstc_mirror(c, taut, Lc, Y3, sh, 0.5, os, 0, 1, okey + ":y3", [&](const Ord &o) {
+        return mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
+                       {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0});
+      });
     }
     finalize(c, Sb, sig2, 1);
     Shape sh;
@@ -2175,7 +2203,9 @@ struct ViewMap {
 
 // out[k][l] (or [l][k]) += alpha sum_{ij} sum_{abc} X_{ijl}[abc] Y_{ijk}[abc]
 // over the ordered (i,j,k), (i,j,l) of the chunk's held blocks with i in
-// [p0, p1) (each i belongs to one chunk, so every pair is counted once).
+// [p0, p1) (each i belongs to one chunk, so every pair is counted once).  By
+// the pair symmetry the sums of (j, i) equal those of (i, j): the kernels run
+// j <= i and weight j < i twice (the pair's larger index decides the chunk).
 void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, double *out,
                long long ldo, bool kl, double alpha) {
   S s(c);
@@ -2202,11 +2232,30 @@ void pair_dots(mlcc3_ctx *c, const Chunk &ch, const double *X, const double *Y, 
   const size_t smem = pair_dots_smem((int)s.no, f32);
   const long long np = ch.p1 - ch.p0;
   const long long ntiles = pair_dots_tiles((int)s.nv, f32);
+  // ordered pairs (i, j) with j <= i run (the kernels skip j > i)
+  long long npairs = 0;
+  for (long long i = ch.p0; i < ch.p1; ++i) npairs += i + 1;
+  npairs = std::max<long long>(1, npairs);
   // about eight resident blocks' worth per SM over the whole launch
-  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, (8 * 152 + np * s.no - 1) / (np * s.no)));
+  const long long gx = std::max<long long>(1, std::min<long long>(ntiles, (8 * 152 + npairs - 1) / npairs));
   dim3 grid((unsigned)gx, (unsigned)(np * s.no));
   const double fl = 2.0 * (double)(np * s.no) * (double)(s.no * s.no) * (double)s.nv3;
-  if (f32) {
+  if (f32 && s.nv % 4 == 0) {
+    // every block row starts on a 16-byte boundary: tiles copied in storage order
+    const size_t sm2 = pair_dots_phys_smem((int)s.no);
+    check_cuda(cudaFuncSetAttribute(pair_dots_phys_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2),
+               "pair_dots smem");
+    const float *X32 = tri_f32(c, X), *Y32 = tri_f32(c, Y);
+    const long long nt8 = (s.nv + 7) / 8;
+    const long long gx2 = std::max<long long>(1, std::min<long long>(nt8 * nt8 * nt8, (8 * 152 + npairs - 1) / npairs));
+    dim3 grid2((unsigned)gx2, (unsigned)(np * s.no));
+    c->launch("pair_dots_kernel", fl, [&] {
+      pair_dots_phys_kernel<<<grid2, 256, sm2, c->stream>>>(
+          X32, Y32, static_cast<const long long *>(voff), static_cast<const int *>(vstr),
+          static_cast<const char *>(vhave), (int)s.no, (int)s.nv, ch.p0, out, ldo, kl ? 1 : 0, alpha);
+    });
+  } else if (f32) {
     check_cuda(cudaFuncSetAttribute(pair_dots_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem), "pair_dots smem");
     const float *X32 = tri_f32(c, X), *Y32 = tri_f32(c, Y);
@@ -2250,18 +2299,14 @@ void y3_like(mlcc3_ctx *c, const double *X, const double *B, const std::vector<O
              const std::string &okey, double *out, long long ldo, double alpha,
              const std::string &tag) {
   S s(c);
-  int n = 0;
   const std::string key = okey + ":" + tag;
-  const BstcItem *it = c->dev_items(key, [&] {
-    std::vector<BstcItem> v;
-    for (auto &o : os)
-      v.push_back(mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * ldo,
-                          {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0}));
-    return v;
-  }, &n);
   Shape sh;
   sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-  c->bstc(X, B, out, sh, alpha, it, n, true, key);
+  // B[p][a][q][b] (a pair-symmetric doubles block) is symmetric under (p,a) <-> (q,b)
+  bstc_mirror(c, X, B, out, sh, alpha, os, 0, 1, key, [&](const Ord &o) {
+    return mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * ldo, {o.vs[2], 0, o.vs[0], o.vs[1], 0},
+                   {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0});
+  });
 }
 
 // V[q][r][b][L] += sum_{a,c} X_{pqr}[a][b][c] T[p][a][c][L]   (T in [i][a][b][L] layout)
