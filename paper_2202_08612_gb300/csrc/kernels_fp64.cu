@@ -1153,6 +1153,20 @@ __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
 
 namespace mlcc3 {
 
+// U[r][q][c][b] = U[q][r][b][c] for q > r (U[no][no][nv][nv]): completes a
+// pair-symmetric occupied-pair block of which only the blocks q >= r were built.
+__global__ void mirror_pairs_kernel(double *__restrict__ U, int no, int nv) {
+  const long long nv2 = (long long)nv * nv, total = (long long)no * no * nv2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long qr = e / nv2, bc = e % nv2;
+    const int q = (int)(qr / no), r = (int)(qr % no);
+    if (q <= r) continue;
+    const int b = (int)(bc / nv), cc = (int)(bc % nv);
+    U[((long long)r * no + q) * nv2 + (long long)cc * nv + b] = U[e];
+  }
+}
+
 // out[c][r] = in[r][c] for an R x C row-major matrix (small operands).
 __global__ void transpose2d_kernel(const double *__restrict__ in, double *__restrict__ out, int R,
                                    int C) {

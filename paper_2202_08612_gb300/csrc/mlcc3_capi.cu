@@ -42,6 +42,7 @@ __global__ void pair_dots_phys_kernel(const float *, const float *, const long l
 long long pair_dots_tiles(int nv, bool f32);
 __global__ void bstc_copy_kernel(BstcParams p);
 __global__ void transpose2d_kernel(const double *, double *, int, int);
+__global__ void mirror_pairs_kernel(double *, int, int);
 __global__ void to_f32_kernel(const double *, float *, long long);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
@@ -1457,19 +1458,28 @@ void tc_vv(mlcc3_ctx *c, const double *X, const std::string &xkey, const double 
   const long long ntM = (s.nv + 127) / 128;
   const int nk = (int)((s.nv * s.nv + 63) / 64);
   const size_t G = 16;  // orderings per tile (split K)
-  TcDev dv = tc_plan(c, "tcV:" + okey, [&](TcPlan &pl) {
-    for (long long tm = 0; tm < ntM; ++tm)
-      for (size_t o0 = 0; o0 < ords.size(); o0 += G) {
-        pl.tile(0, (int)(128 * tm), 0, 0);
-        for (size_t i = o0; i < std::min(ords.size(), o0 + G); ++i) {
-          const Ord &o = ords[i];
-          const int u = (int)(o.off / s.nv3);
-          pl.seg(2 * o.sp[2], 6 + 2 * o.sp[2], nk, (int)(128 * tm), 0, u, 0, 0, u);
+  // the mirror orderings (p,q,r) and (q,p,r) give the same segment (same block,
+  // same layout: the K pair is in canonical order), so p > q runs once with
+  // weight 2 and p = q with weight 1
+  for (int w = 2; w >= 1; --w) {
+    std::vector<Ord> os;
+    for (auto &o : ords)
+      if ((w == 2 && o.p > o.q) || (w == 1 && o.p == o.q)) os.push_back(o);
+    if (os.empty()) continue;
+    TcDev dv = tc_plan(c, "tcV:" + okey + ":w" + std::to_string(w), [&](TcPlan &pl) {
+      for (long long tm = 0; tm < ntM; ++tm)
+        for (size_t o0 = 0; o0 < os.size(); o0 += G) {
+          pl.tile(0, (int)(128 * tm), 0, 0);
+          for (size_t i = o0; i < std::min(os.size(), o0 + G); ++i) {
+            const Ord &o = os[i];
+            const int u = (int)(o.off / s.nv3);
+            pl.seg(2 * o.sp[2], 6 + 2 * o.sp[2], nk, (int)(128 * tm), 0, u, 0, 0, u);
+          }
         }
-      }
-  }, c->tc_kcap);
-  TcEpi epi = make_epi(out, 2, 128, 0, ld, 1, 1, s.nv, s.nv, alpha);
-  tc_launch(c, (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)ords.size());
+    }, c->tc_kcap);
+    TcEpi epi = make_epi(out, 2, 128, 0, ld, 1, 1, s.nv, s.nv, alpha * w);
+    tc_launch(c, (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)os.size());
+  }
 }
 
 // Split copies of small operands (per call or at build):
@@ -2450,32 +2460,43 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     // U[q][r][b][c] = sum_{p,a} lt_{pqr}[a][b][c] R^a_p  (rows q in [p0, p1))
     double *U = c->buf("dU", s.no * s.no * s.nv * s.nv);
     c->zero(U, s.no * s.no * s.nv * s.nv);
+    // U[r][q][c][b] = U[q][r][b][c] (pair symmetry of lt): with one chunk, the
+    // blocks q >= r are contracted and the others copied from their mirrors
+    const bool umirror = c->groups.size() == 1;
     it = c->dev_items(okey + ":U", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ch.held)
-        if (o.q >= ch.p0 && o.q < ch.p1)
+        if (o.q >= ch.p0 && o.q < ch.p1 && (!umirror || o.q >= o.r))
           v.push_back(mk_item(o.off, o.p, (o.q * s.no + o.r) * s.nv * s.nv,
                               {o.vs[1], o.vs[2], o.vs[0], 0, 0}, {NO, 0, 0, 0, 0}, {s.nv, 1, 0, 0}));
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
     c->bstc(lt3, R1, U, sh, 1.0, it, n, true, okey + ":U");
+    if (umirror)
+      launch_1d(c, s.no * s.no * s.nv * s.nv, "mirror_u", [&](int g) {
+        c->launch("mirror_pairs_kernel", 0.0, [&] {
+          mirror_pairs_kernel<<<g, 256, 0, c->stream>>>(U, (int)s.no, (int)s.nv);
+        });
+      });
     // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
     sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
     c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
     // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
     pair_dots(c, ch, lt3, R3, D, nmo, true, -0.5);
     // D_ld += sum U[j][k][b][c] (tau^{bcd}_{jkl} - tau^{bcd}_{jlk})  (views with j in [p0, p1))
-    it = c->dev_items(okey + ":ld1", [&] {
-      std::vector<BstcItem> v;
+    // U[p][q][a][b] is symmetric under (p,a) <-> (q,b): mirror orderings (p,q,r),
+    // (q,p,r) contribute alike (each ordering lies in the chunk of its p)
+    {
+      std::vector<Ord> os1;
       for (auto &o : ch.held)
-        if (o.p >= ch.p0 && o.p < ch.p1)
-          v.push_back(mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
-                              {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
-      return v;
-    }, &n);
-    sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    c->bstc(tau, U, D + NO, sh, 1.0, it, n, true, okey + ":ld1");
+        if (o.p >= ch.p0 && o.p < ch.p1) os1.push_back(o);
+      sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
+      bstc_mirror(c, tau, U, D + NO, sh, 1.0, os1, 0, 1, okey + ":ld1", [&](const Ord &o) {
+        return mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
+                       {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0});
+      });
+    }
     it = c->dev_items(okey + ":ld2", [&] {
       std::vector<BstcItem> v;
       for (auto &o : ch.held)
