@@ -127,3 +127,25 @@ def test_split_persistent_kernel_everywhere():
     got, ref = run_all(c, g), oracle_all(c)
     for k in ref:
         assert rel_err(got[k], ref[k]) < TOL, (k, rel_err(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("group,persist", [(1, 304), (2, 304), (4, 304), (3, 0)])
+def test_split_grouped_tiles(group, persist):
+    """Batches stacked along N in the triples build and orderings stacked in the
+    D-slot back-contraction (tc_group batches per tile), in both kernel forms
+    (persist 0: every launch persistent): the whole split path meets its bar
+    for every group size, with ragged groups (n_o = 6 gives groups of 1 to 6)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    c = Case(NO=9, NV=40, no=6, nv=12, NJ=50, nstates=1)
+    g = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+    with pytest.raises(binding.MLCC3Error) as e:
+        g.set_param("tc_group", 5)
+    assert e.value.code == -1
+    g.set_param("tc_group", group)
+    g.set_param("tc_persist_from", persist)
+    got, ref = run_all(c, g), oracle_all(c)
+    for k in ref:
+        assert rel_err(got[k], ref[k]) < TOL, (group, k, rel_err(got[k], ref[k]))
