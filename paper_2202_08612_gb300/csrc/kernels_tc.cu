@@ -568,9 +568,26 @@ cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, cons
 
 int tc_tile_width(long long n) { return n <= 64 ? 64 : n <= 128 ? 128 : n <= 160 ? 160 : 256; }
 
+// Four consecutive outputs of a split: hi[0..3] and lo[0..3] as one 8-byte store
+// each (the destination index is a multiple of 4 in a 256-byte aligned array).
+__device__ __forceinline__ void split4_store(const double *x, __nv_bfloat16 *hi,
+                                             __nv_bfloat16 *lo) {
+  unsigned int hb[4], lb[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __nv_bfloat16 h, l;
+    split_hi_lo(x[j], h, l);
+    hb[j] = __bfloat16_as_ushort(h);
+    lb[j] = __bfloat16_as_ushort(l);
+  }
+  *reinterpret_cast<uint2 *>(hi) = make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+  *reinterpret_cast<uint2 *>(lo) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+}
+
 // Split FP64 -> (hi, lo) bfloat16 with a 4-D permuted gather and K padding:
 // out[o0][o1][o2][o3] (o3 < K3p, zero for o3 >= K3) = scale * in[o0 s0 + o1 s1 + o2 s2 + o3 s3].
-// Groups of 64 threads take one output row (o0, o1, o2) at a time.
+// K3p is a multiple of 4.  Groups of 64 threads take one output row (o0, o1,
+// o2) at a time, each thread four consecutive o3 per step.
 __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
                                   __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
                                   long long D2, long long K3, long long K3p, long long s0,
@@ -584,9 +601,12 @@ __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *
     const long long o1 = r1 % D1, o0 = r1 / D1;
     const double *src = in + o0 * s0 + o1 * s1 + o2 * s2;
     __nv_bfloat16 *h = hi + r * K3p, *l = lo + r * K3p;
-    for (int k = t; k < k3p; k += 64) {
-      const double x = k < k3 ? scaled(src[(long long)k * s3], mode, scale) : 0.0;
-      split_hi_lo(x, h[k], l[k]);
+    for (int k = 4 * t; k < k3p; k += 256) {
+      double x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : 0.0;
+      split4_store(x, h + k, l + k);
     }
   }
 }
@@ -596,7 +616,8 @@ __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *
 namespace mlcc3 {
 
 // Split with a two-level K: out[o0][o1][k] for k = k1 K2 + k2 < K1 K2 (zero up
-// to Kp) = scale * in[o0 s0 + o1 s1 + k1 sk1 + k2 sk2].
+// to Kp, a multiple of 4) = scale * in[o0 s0 + o1 s1 + k1 sk1 + k2 sk2].  Each
+// thread takes four consecutive k per step, dividing k by K2 once.
 __global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
                                      __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
                                      long long K1, long long K2, long long Kp, long long s0,
@@ -609,13 +630,18 @@ __global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat1
     const long long o1 = r % D1, o0 = r / D1;
     const double *src = in + o0 * s0 + o1 * s1;
     __nv_bfloat16 *h = hi + r * Kp, *l = lo + r * Kp;
-    for (int k = t; k < kp; k += 64) {
-      double x = 0.0;
-      if (k < K) {
-        const int q1 = k / kk2, q2 = k - q1 * kk2;
-        x = scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale);
+    for (int k = 4 * t; k < kp; k += 256) {
+      int q1 = k / kk2, q2 = k - q1 * kk2;
+      double x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = k + j < K ? scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale) : 0.0;
+        if (++q2 == kk2) {
+          q2 = 0;
+          ++q1;
+        }
       }
-      split_hi_lo(x, h[k], l[k]);
+      split4_store(x, h + k, l + k);
     }
   }
 }
@@ -646,11 +672,14 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
       tile[i][tx] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : 0.0;
     }
     __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      const int c = c0 + i, r = r0 + tx;
+    {
+      // thread t writes four consecutive r (8-byte stores) of column c0 + t / 8
+      const int ci = threadIdx.x >> 3, rq = 4 * (threadIdx.x & 7);
+      const int c = c0 + ci, r = r0 + rq;
       if (c < C && r < Rp) {
+        const double x[4] = {tile[rq][ci], tile[rq + 1][ci], tile[rq + 2][ci], tile[rq + 3][ci]};
         const long long o = b * db + (long long)c * dr + r;
-        split_hi_lo(tile[tx][i], hi[o], lo[o]);
+        split4_store(x, hi + o, lo + o);
       }
     }
   }
