@@ -153,6 +153,10 @@ def oracle_sample(workload, seed):
 def run_reference(args, rank):
     if rank != 0:
         return
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle sample is defined for {sorted(WORKLOADS)} only"}), flush=True)
+        return
     vals = []
     for i in range(args.warmup + args.steps):
         v, dt, sample = oracle_sample(args.workload, 1000 + i)
