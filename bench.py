@@ -240,6 +240,22 @@ class Problem:
         return i, o
 
 
+def job_throughput(ms_local, steps, flops_per_rank_step, world, device=None):
+    """Whole-job timing of a weak-scaling run: every rank processed its own
+    system for `steps` steps in ms_local milliseconds; the job's time is the
+    slowest rank's (an all-reduce MAX when a process group is up, on `device`)
+    and its throughput counts the work of all ranks.  Returns (ms per step,
+    TFLOP/s)."""
+    import torch
+    ms_total = ms_local
+    if device is not None:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / steps
+    return ms, flops_per_rank_step * world / (ms * 1e-3) / 1e12
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2202_08612_gb300 import binding, build
@@ -276,13 +292,8 @@ def run_ours(args, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     stats = ctx.kernel_stats()
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms_total], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms = ms_total / args.steps
     fl = algorithmic_flops(NO, NV, no, nv, ns)
-    value = fl * world / (ms * 1e-3) / 1e12
+    ms, value = job_throughput(ms_total, args.steps, fl, world, device if dist else None)
 
     # per-stage time of the Davidson-iteration part (rho + sigma of the state vectors)
     barrier()
