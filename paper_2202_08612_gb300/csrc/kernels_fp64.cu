@@ -626,9 +626,11 @@ __device__ __forceinline__ unsigned int div_inv(unsigned int x, unsigned long lo
 // two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
 // Terms of kind 2 and 3 (rank 1 in the pair indices) are summed here over the
 // six permutations in FP32, from FP32 copies of their operands; for each
-// (term, permutation) the block first tabulates base pointers and 32-bit
-// strides, choosing the symmetric or transposed form of an operand whose last
-// index is the element's fastest one.  eps^{abc}_{ijk} - omega is an exact
+// (term, permutation) the block first tabulates base pointers and the 32-bit
+// coefficients that make each operand index linear in the element's canonical
+// coordinates, choosing the symmetric or transposed form of an operand whose
+// last index is the element's fastest one; each thread then takes eight
+// elements per pass over the table.  eps^{abc}_{ijk} - omega is an exact
 // double-float sum of FP32 (hi, lo) pairs (ehl: the virtual energies' pairs),
 // which keeps FP64 accuracy off the FP64 pipe; the quotient of the FP32
 // numerator is taken in FP32 and widened on the integer pipe.  omega is read
