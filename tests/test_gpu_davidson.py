@@ -1,0 +1,57 @@
+"""The Davidson solver of the omega-nonlinear eigenproblem J(omega) R = omega R
+(orbital-energy model of the singles-doubles block plus the library's triples
+right transformation): on a tiny system it must reach the eigenpair that the
+explicit-matrix fixed-point iteration finds (J built column by column from the
+oracle), and on a larger one the split-precision path must give the FP64 path's
+excitation energy within 1e-5 Hartree."""
+import numpy as np
+import pytest
+
+import oracle as O
+import sdbasis
+from gpu_common import Case
+from paper_2202_08612_gb300 import binding, synth
+from paper_2202_08612_gb300.davidson import Davidson
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.mark.parametrize("precision,tol", [(binding.MLCC3_FP64, 1e-9), (binding.MLCC3_SPLIT_BF16X3, 1e-5)])
+def test_davidson_reaches_the_explicit_eigenpair(precision, tol):
+    torch = _torch()
+    s = synth.make_system(3, 4, 2, 2, 10, seed=5)
+    o = O.make_ctx(s)
+    w, R1, R2, L1, L2, sd = sdbasis.fixed_point_eigenpair(s, o)
+    c = Case(3, 4, 2, 2, 10, seed=5, nstates=1)
+    g = c.context(precision=precision)
+    dv = Davidson(g, s.eps, (3, 4, 2, 2), torch.device("cuda"))
+    res = dv.solve(tol=1e-10 if precision == binding.MLCC3_FP64 else 1e-7)
+    assert abs(res.omega - w) < tol, (res.omega, w)
+    # the eigenvector, up to normalisation and sign
+    x1, x2 = res.R1.cpu().numpy(), res.R2.cpu().numpy()
+    ref = np.concatenate([R1.ravel(), R2.ravel()])
+    got = np.concatenate([x1.ravel(), x2.ravel()])
+    ref, got = ref / np.linalg.norm(ref), got / np.linalg.norm(got)
+    assert min(np.abs(got - ref).max(), np.abs(got + ref).max()) < 1e3 * tol
+    g.close()
+
+
+def test_davidson_split_excitation_energy_within_1e5_hartree():
+    torch = _torch()
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)
+    om = []
+    for precision in (binding.MLCC3_FP64, binding.MLCC3_SPLIT_BF16X3):
+        g = c.context(precision=precision)
+        dv = Davidson(g, c.sys.eps, c.dims[:4], torch.device("cuda"))
+        res = dv.solve(tol=1e-8)
+        assert res.residual < 1e-6, res.residual
+        om.append(res.omega)
+        g.close()
+    assert abs(om[0] - om[1]) < 1e-5, om
