@@ -38,12 +38,17 @@ class DavidsonResult:
 class Davidson:
     """One excitation at a time from the lowest diagonal element of D (or from a
     given guess).  ctx: a binding.Context whose integrals are built; eps: host
-    orbital energies (occupied first); dims: (N_O, N_V, n_o, n_v)."""
+    orbital energies (occupied first); dims: (N_O, N_V, n_o, n_v).  diag: the
+    singles-doubles diagonal (host arrays in the vector layouts; default the
+    orbital-energy differences), the preconditioner; sd_apply: the caller's
+    singles-doubles block, (v1, v2) -> (y1, y2) on device tensors (default: the
+    diagonal model D v)."""
 
-    def __init__(self, ctx, eps, dims, device, diag=None):
+    def __init__(self, ctx, eps, dims, device, diag=None, sd_apply=None):
         import torch
         self.torch = torch
         self.ctx = ctx
+        self.sd_apply = sd_apply
         NO, NV, no, nv = dims
         self.dims = dims
         self.dev = device
@@ -76,7 +81,11 @@ class Davidson:
         rho1, rho2 = torch.empty_like(R1), torch.empty_like(R2)
         self.ctx.jacobian_right(np.full(len(vecs), omega), R1, R2, rho1, rho2)
         self.calls += 1
-        return [(self.D1 * v[0] + rho1[k], self.D2 * v[1] + rho2[k]) for k, v in enumerate(vecs)]
+        out = []
+        for k, v in enumerate(vecs):
+            y = self.sd_apply(v) if self.sd_apply else (self.D1 * v[0], self.D2 * v[1])
+            out.append((y[0] + rho1[k], y[1] + rho2[k]))
+        return out
 
     def _orthonormalize(self, v, basis):
         for _ in range(2):

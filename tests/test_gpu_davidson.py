@@ -55,3 +55,18 @@ def test_davidson_split_excitation_energy_within_1e5_hartree():
         om.append(res.omega)
         g.close()
     assert abs(om[0] - om[1]) < 1e-5, om
+
+
+def test_davidson_with_a_caller_block_equal_to_the_model():
+    """A caller-supplied singles-doubles product (here the same diagonal model,
+    passed as a function) gives the same root as the built-in model."""
+    torch = _torch()
+    c = Case(NO=6, NV=24, no=4, nv=8, NJ=72, nstates=1)
+    g = c.context()
+    dv0 = Davidson(g, c.sys.eps, c.dims[:4], torch.device("cuda"))
+    r0 = dv0.solve(tol=1e-9)
+    dv1 = Davidson(g, c.sys.eps, c.dims[:4], torch.device("cuda"),
+                   sd_apply=lambda v: (dv0.D1 * v[0], dv0.D2 * v[1]))
+    r1 = dv1.solve(tol=1e-9)
+    assert abs(r0.omega - r1.omega) < 1e-10, (r0.omega, r1.omega)
+    g.close()
