@@ -389,7 +389,9 @@ def run_ours(args, rank, world, local_rank):
                 "e2e": e2e, "clocks": clk.summary(), "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},
                 "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
-                               sorted(stats.items(), key=lambda kv: -kv[1][1])[:24]}}
+                               sorted(stats.items(), key=lambda kv: -kv[1][1])[:24]},
+                "tc_sites": tc_site_fracs(stats, args.steps,
+                                          peaks().get("bf16_tflops_sustained") or 1700.0)}
         print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -639,9 +641,18 @@ def run_large(args):
             "clocks": clk.summary(),
             "hbm_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev)),
             "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
-                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]}}
+                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
+            "tc_sites": tc_site_fracs(stats, args.steps, pk)}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def tc_site_fracs(stats, steps, pk):
+    """ms per step and fraction of the BF16 peak (3 products per product) of each
+    tensor-core call site."""
+    return {k.split(":", 1)[1]: {"ms": round(v[1] / steps, 3),
+                                 "frac": round(3.0 * v[2] / (v[1] * 1e-3) / 1e12 / pk, 4) if v[1] > 0 else None}
+            for k, v in stats.items() if k.startswith("tc_gemm_kernel:")}
 
 
 def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ, core, split):
@@ -690,7 +701,8 @@ def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, 
             "clocks": clk.summary(),
             "hbm_used_gb": (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev)),
             "call_sites": {k: round(v[1], 3) for k, v in
-                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]}}
+                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
+            "tc_sites": tc_site_fracs(stats, 1, pk)}
     print(json.dumps(line), flush=True)
     ctx.close()
 

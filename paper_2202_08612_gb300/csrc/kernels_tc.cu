@@ -155,6 +155,38 @@ __device__ __forceinline__ void epi_put16(const TcEpi &epi, long long a0, int n0
   }
 }
 
+// Sixteen columns of the warp's 32 rows in an FP64 mode with a unit column
+// stride.  Each thread holds 16 consecutive columns of its own row, and rows lie
+// far apart in memory, so a direct write touches 32 lines per instruction.  The
+// values pass through shared memory instead (tb: this warp's 32 x 17 floats) and
+// every reduction instruction then covers 16 consecutive columns of two rows.
+// rowoff: this thread's row offset; rvmask: bit r set when row r of the warp is
+// valid; base: the group offset plus the first column nc.
+__device__ __forceinline__ void epi_put16_rows(const TcEpi &epi, float *tb, int lane, const float *v,
+                                               long long rowoff, unsigned rvmask, long long base,
+                                               int nc) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = v[j];
+  __syncwarp();
+  const int cc = lane & 15, half = lane >> 4;
+  const bool cv = nc + cc < epi.nlim;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int rr = 2 * j + half;
+    const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+    const float x = tb[rr * 17 + cc];
+    if (cv && ((rvmask >> rr) & 1u)) epi_put(epi, base + ro + cc, epi.alpha * x);
+  }
+  __syncwarp();
+}
+
+// Shared-memory bytes of the epilogue's transpose buffers (four warps), and the
+// launches that use them: FP64 modes with a unit column stride.
+constexpr int kEpiTbBytes = 4 * 32 * 17 * 4;
+__host__ __device__ __forceinline__ bool epi_rows_t(const TcEpi &epi) {
+  return epi.sn == 1 && epi.mode >= 2;
+}
+
 // Loads of one pipeline stage for chunk kc of segment sg: A hi/lo (128 rows),
 // then the segment's B boxes (hi into the first BN rows' region, lo into the
 // second), box q at row q * qrows.  The barrier expects exactly these bytes.
@@ -189,7 +221,7 @@ __device__ __forceinline__ long long group_off(const TcItem &it, int q) {
 
 }  // namespace
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool ROWS_T>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcItem *__restrict__ items,
                    const TcSeg *__restrict__ segs, const TcEpi epi, int *__restrict__ status) {
@@ -313,13 +345,21 @@ __global__ void __launch_bounds__(192, 1)
     }
     const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
     const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
+    unsigned rvmask = 0;
+    if constexpr (ROWS_T) rvmask = __ballot_sync(0xffffffffu, rv);
 #pragma unroll 1
     for (int n0 = 0; n0 < ntile; n0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
-      if (!rv) continue;
-      const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
-      epi_put16(epi, group_off(it, q) + rowoff + (long long)nc * epi.sn, nc, v);
+      if constexpr (ROWS_T) {
+        const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+        float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
+        epi_put16_rows(epi, tb, lane, v, rowoff, rvmask, group_off(it, q) + nc, nc);
+      } else {
+        if (!rv) continue;
+        const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+        epi_put16(epi, group_off(it, q) + rowoff + (long long)nc * epi.sn, nc, v);
+      }
     }
   }
   tc_fence_before();
@@ -344,7 +384,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // A bounded wait that expires sets kStatusTimeout and the shared abort flag;
 // every role then leaves its loop, the producer waits (bounded) for its TMA
 // copies in flight and the MMA issuer for its last MMAs before TMEM is freed.
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool ROWS_T>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_persist_kernel(const __grid_constant__ TcMaps maps, const TcItem *__restrict__ items,
                            const TcSeg *__restrict__ segs, int nitems, const TcEpi epi,
@@ -496,16 +536,27 @@ __global__ void __launch_bounds__(192, 1)
       const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
       const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
       const int ntile = (it.nq > 1 ? it.nq : 1) * qrows;
+      unsigned rvmask = 0;
+      if constexpr (ROWS_T) rvmask = __ballot_sync(0xffffffffu, rv);
 #pragma unroll 1
       for (int n0 = 0; n0 < ntile; n0 += 16) {
         float v[16];
         tmem_ld16(tmem + (uint32_t)(u * NCOLS) + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
-        if (!rv) continue;
-        if (total == 0)
+        if constexpr (ROWS_T) {
+          if (total == 0)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
-        epi_put16(epi, group_off(items[i], q) + rowoff + (long long)nc * epi.sn, nc, v);
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+          const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+          float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
+          epi_put16_rows(epi, tb, lane, v, rowoff, rvmask, group_off(items[i], q) + nc, nc);
+        } else {
+          if (!rv) continue;
+          if (total == 0)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+          const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
+          epi_put16(epi, group_off(items[i], q) + rowoff + (long long)nc * epi.sn, nc, v);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -522,33 +573,48 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// Stages, 1024-byte alignment slack, barriers and TMEM slot (256), and the
+// epilogue's transpose buffers when the launch uses them (a launch without them
+// keeps the smaller shared-memory carve-out and the larger L1).
 template <int BN, int STAGES>
-constexpr int tc_smem_bytes() {
-  return STAGES * (2 * 128 * 128 + 2 * BN * 128) + 1024 + (2 * STAGES + 5) * 8 + 16;
+constexpr int tc_smem_bytes(bool rows_t) {
+  return STAGES * (2 * 128 * 128 + 2 * BN * 128) + 1024 + 256 + (rows_t ? kEpiTbBytes : 0);
 }
 
-template <int BN, int STAGES>
-static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, const TcSeg *segs,
-                             int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
-                             int persist_from) {
-  constexpr int smem = tc_smem_bytes<BN, STAGES>();
+template <int BN, int STAGES, bool ROWS_T>
+static cudaError_t launch_bn_t(const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                               int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                               int persist_from) {
+  constexpr int smem = tc_smem_bytes<BN, STAGES>(ROWS_T);
+  static_assert(smem <= 232448, "shared memory of one CTA exceeds 227 KB");
   if (nitems > persist_from) {  // persistent CTAs, one per SM
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_persist_kernel<BN, STAGES>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_persist_kernel<BN, STAGES, ROWS_T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nitems < sms ? nitems : sms;
-    tc_gemm_persist_kernel<BN, STAGES><<<grid, 192, smem, stream>>>(maps, items, segs, nitems, epi,
-                                                                    status);
+    tc_gemm_persist_kernel<BN, STAGES, ROWS_T><<<grid, 192, smem, stream>>>(maps, items, segs,
+                                                                            nitems, epi, status);
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>,
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES, ROWS_T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  tc_gemm_kernel<BN, STAGES><<<nitems, 192, smem, stream>>>(maps, items, segs, epi, status);
+  tc_gemm_kernel<BN, STAGES, ROWS_T><<<nitems, 192, smem, stream>>>(maps, items, segs, epi, status);
   return cudaGetLastError();
+}
+
+// The epilogue form is a template parameter: the launches that do not transpose
+// run the kernel without the transpose code or its shared memory.
+template <int BN, int STAGES>
+static cudaError_t launch_bn(const TcMaps &maps, const TcItem *items, const TcSeg *segs,
+                             int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
+                             int persist_from) {
+  if (epi_rows_t(epi))
+    return launch_bn_t<BN, STAGES, true>(maps, items, segs, nitems, epi, status, stream, persist_from);
+  return launch_bn_t<BN, STAGES, false>(maps, items, segs, nitems, epi, status, stream, persist_from);
 }
 
 // Host launcher: BN is the tile width (columns), one of 64, 128, 160, 256.

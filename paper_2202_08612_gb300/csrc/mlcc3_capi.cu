@@ -818,10 +818,12 @@ TcDev tc_plan(mlcc3_ctx *c, const std::string &key0, const std::function<void(Tc
                (int)pl.items.size()};
 }
 
-void tc_launch(mlcc3_ctx *c, int BN, const TcMaps &maps, const TcDev &d, const TcEpi &epi,
-               double flops) {
+// site: the contraction's tag in the per-call-site statistics ("tc_gemm_kernel:<site>").
+void tc_launch(mlcc3_ctx *c, const char *site, int BN, const TcMaps &maps, const TcDev &d,
+               const TcEpi &epi, double flops) {
   if (d.nitems == 0) return;
-  c->launch("tc_gemm_kernel", flops, [&] {
+  const std::string name = std::string("tc_gemm_kernel:") + site;
+  c->launch(name.c_str(), flops, [&] {
     check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, epi, c->status, c->stream,
                               c->tc_persist_from),
                "tc_gemm");
@@ -1026,7 +1028,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     epi.qw = BW;
     double K = 0.0;
     for (auto &t : terms) K += 2.0 * (t.dtype ? (double)s.NV : (double)s.NO);
-    tc_launch(c, BN, maps, dv, epi, 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb);
+    tc_launch(c, "build", BN, maps, dv, epi, 2.0 * (double)(s.nv * s.nv) * (double)s.nv * K * (double)nb);
   }
   TripTerms tt{};
   for (auto &t : rank1) tt.t[tt.n++] = t;
@@ -1135,7 +1137,7 @@ void tc_flat_gemm(mlcc3_ctx *c, const SplitOp &A, const SplitOp &B, long long M,
       }
   }, c->tc_kcap);
   TcEpi epi = make_epi(out, 2, R2, s1, s2, sn, M / R2, R2, N, alpha, 1);
-  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)M * (double)N * (double)K);
+  tc_launch(c, "flat", BN, maps, dv, epi, 2.0 * (double)M * (double)N * (double)K);
 }
 
 // Cholesky factors as [J][(x, y)] split operands of the sigma singles tail.
@@ -1238,7 +1240,7 @@ void tc_back_D(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords, cons
   }, c->tc_kcap);
   TcEpi epi = make_epi(Zb, 2, 128, 0, 1, s.ba, 1, s.NV, s.nv, b.cD);
   epi.qw = (int)BN;
-  tc_launch(c, tc_tile_width((long long)BN * G), maps, dv, epi,
+  tc_launch(c, "backD", tc_tile_width((long long)BN * G), maps, dv, epi,
             2.0 * (double)s.NV * (double)s.nv * (double)(s.nv * s.nv) * (double)ords.size());
 }
 
@@ -1388,7 +1390,7 @@ void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const Split
     // order (cls 0) or swapped (cls 1)
     TcEpi epi = make_epi(out, 2, 16, cls == 0 ? Sp1 : Sp2, cls == 0 ? Sp2 : Sp1, Sn, s.nv, s.nv,
                          nN, coef);
-    tc_launch(c, BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size() / 2.0);
+    tc_launch(c, "pair", BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size() / 2.0);
   }
 }
 
@@ -1434,7 +1436,7 @@ void tc_xt(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp
           }
   }, c->tc_kcap);
   TcEpi epi = make_epi(out, 2, 128, 0, Srow, 1, 1, s.nv, nN, coef);
-  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
+  tc_launch(c, "xt", BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
 }
 
 // out[c][d] (row stride ld) += alpha sum_{orderings} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
@@ -1478,7 +1480,7 @@ void tc_vv(mlcc3_ctx *c, const double *X, const std::string &xkey, const double 
         }
     }, c->tc_kcap);
     TcEpi epi = make_epi(out, 2, 128, 0, ld, 1, 1, s.nv, s.nv, alpha * w);
-    tc_launch(c, (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)os.size());
+    tc_launch(c, "vv", (int)BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)s.nv * (double)os.size());
   }
 }
 
@@ -1556,7 +1558,7 @@ void tc_chol(mlcc3_ctx *c, const std::vector<CholTerm> &terms, long long nW, lon
         }
   }, pieces ? c->tc_kcap : 0);
   TcEpi epi = make_epi(out, mode, (int)s.nv, Sk, Sc, 1, s.no, s.nv, nN, alpha, 1);
-  tc_launch(c, BN, maps, dv, epi, 2.0 * (double)M * (double)nN * (double)nW * (double)s.NJ *
+  tc_launch(c, "chol", BN, maps, dv, epi, 2.0 * (double)M * (double)nN * (double)nW * (double)s.NJ *
                                       (double)terms.size());
 }
 
