@@ -270,6 +270,8 @@ def run_ours(args, rank, world, local_rank):
     ctx = binding.Context(*prob.dims, precision=prec, stream=stream.cuda_stream)
     if args.tc_group:
         ctx.set_param("tc_group", args.tc_group)
+    if args.tc_wide_bn:
+        ctx.set_param("tc_wide_bn", args.tc_wide_bn)
     dist = world > 1
 
     def barrier():
@@ -576,6 +578,8 @@ def run_large(args):
         ctx.set_param("chunk_blocks", args.chunk_blocks)
     if args.tc_group:
         ctx.set_param("tc_group", args.tc_group)
+    if args.tc_wide_bn:
+        ctx.set_param("tc_wide_bn", args.tc_wide_bn)
     unit = NV * nv ** 3 * no ** 3
 
     def timed(f):
@@ -720,6 +724,9 @@ def main():
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
     ap.add_argument("--tc-group", type=int, default=0,
                     help="batches per triples-build tensor-core tile (0: library default)")
+    ap.add_argument("--tc-wide-bn", type=int, default=0,
+                    help="tile width of the pair contractions wider than 256 columns "
+                         "(128, 160 or 256; 0: the library default)")
     ap.add_argument("--chunk-blocks", type=int, default=128,
                     help="large workloads: unique batches held per chunk")
     ap.add_argument("--stage", default="davidson", choices=("davidson", "densities", "cvs"),

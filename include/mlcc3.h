@@ -188,6 +188,13 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              share every integral-side operand, so up to tc_group of their
  *              amplitude operands (one n_v-wide box each) fill one wider MMA.
  *              Default 4.  Range 1..4 (capped at 256 columns).
+ *   "tc_wide_bn"  tile width (columns) of the split-precision pair
+ *              contractions whose output has more than 256 columns (the sigma
+ *              singles intermediates, N = N_V): 256 (two pipeline stages fit in
+ *              shared memory), 160 or 128 (three stages).  Default 256.  Set it
+ *              before mlcc3_build_integrals: the operands converted there carry
+ *              the width, and a later change makes the transformations fail with
+ *              MLCC3_ERR_ARG.
  *   "tc_persist_from"  tensor-core launches with more output tiles than this
  *              run the persistent kernel (one CTA per SM looping over tiles,
  *              accumulator double-buffered in TMEM); smaller ones run one CTA

@@ -85,6 +85,7 @@ struct mlcc3_ctx {
   // blocks, for contractions whose results are summed in FP64 (see tc_plan)
   int tc_kcap = 16;
   int tc_group = 4;  // batches stacked along N in a triples-build tile
+  int tc_wide_bn = 256;  // tile width of the pair contractions with more than 256 columns
   // tensor-core launches with more tiles than this use the persistent kernel
   int tc_persist_from = mlcc3::kTcPersistFrom;
   // batch chunking: at most chunk_blocks blocks held per chunk (0 = sized from
@@ -122,6 +123,7 @@ struct mlcc3_ctx {
   struct SplitOp {
     void *hi = nullptr, *lo = nullptr;
     CUtensorMap mhi, mlo;
+    unsigned rows = 0;  // rows of the maps' box (make_split)
   };
   std::map<std::string, SplitOp> splits;
   // split layouts of triples arrays, converted once per (array, write

@@ -159,25 +159,40 @@ __device__ __forceinline__ void epi_put16(const TcEpi &epi, long long a0, int n0
 // stride.  Each thread holds 16 consecutive columns of its own row, and rows lie
 // far apart in memory, so a direct write touches 32 lines per instruction.  The
 // values pass through shared memory instead (tb: this warp's 32 x 17 floats) and
-// every reduction instruction then covers 16 consecutive columns of two rows.
-// rowoff: this thread's row offset; rvmask: bit r set when row r of the warp is
-// valid; base: the group offset plus the first column nc.
+// every reduction instruction then covers 16 consecutive columns of two rows:
+// lane l writes column l % 16 of rows 2j + l / 16, j = 0..15, whose offsets
+// ro[j] and validity bits vb (bit j) epi_rows_of gathers once per tile.
+// base: the group offset plus the first column nc.
+struct EpiRows {
+  long long ro[16];
+  unsigned vb;
+};
+
+__device__ __forceinline__ void epi_rows_of(EpiRows &r, int lane, long long rowoff, bool rv) {
+  const unsigned rvmask = __ballot_sync(0xffffffffu, rv);
+  const int half = lane >> 4;
+  r.vb = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    r.ro[j] = __shfl_sync(0xffffffffu, rowoff, 2 * j + half);
+    r.vb |= ((rvmask >> (2 * j + half)) & 1u) << j;
+  }
+}
+
 __device__ __forceinline__ void epi_put16_rows(const TcEpi &epi, float *tb, int lane, const float *v,
-                                               long long rowoff, unsigned rvmask, long long base,
-                                               int nc) {
+                                               const EpiRows &r, long long base, int nc) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = v[j];
   __syncwarp();
   const int cc = lane & 15, half = lane >> 4;
-  const bool cv = nc + cc < epi.nlim;
+  const unsigned vb = nc + cc < epi.nlim ? r.vb : 0u;
+  float x[16];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int rr = 2 * j + half;
-    const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
-    const float x = tb[rr * 17 + cc];
-    if (cv && ((rvmask >> rr) & 1u)) epi_put(epi, base + ro + cc, epi.alpha * x);
-  }
+  for (int j = 0; j < 16; ++j) x[j] = tb[(2 * j + half) * 17 + cc];
   __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if ((vb >> j) & 1u) epi_put(epi, base + r.ro[j] + cc, epi.alpha * x[j]);
 }
 
 // Shared-memory bytes of the epilogue's transpose buffers (four warps), and the
@@ -345,16 +360,16 @@ __global__ void __launch_bounds__(192, 1)
     }
     const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
     const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
-    unsigned rvmask = 0;
-    if constexpr (ROWS_T) rvmask = __ballot_sync(0xffffffffu, rv);
+    EpiRows er;
+    if constexpr (ROWS_T) epi_rows_of(er, lane, rowoff, rv);
+    float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
 #pragma unroll 1
     for (int n0 = 0; n0 < ntile; n0 += 16) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)n0, v);
       if constexpr (ROWS_T) {
         const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
-        float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
-        epi_put16_rows(epi, tb, lane, v, rowoff, rvmask, group_off(it, q) + nc, nc);
+        epi_put16_rows(epi, tb, lane, v, er, group_off(it, q) + nc, nc);
       } else {
         if (!rv) continue;
         const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
@@ -536,8 +551,9 @@ __global__ void __launch_bounds__(192, 1)
       const bool rv = ok && r1 < epi.lim1 && r2 < epi.lim2;
       const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
       const int ntile = (it.nq > 1 ? it.nq : 1) * qrows;
-      unsigned rvmask = 0;
-      if constexpr (ROWS_T) rvmask = __ballot_sync(0xffffffffu, rv);
+      EpiRows er;
+      if constexpr (ROWS_T) epi_rows_of(er, lane, rowoff, rv);
+      float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
 #pragma unroll 1
       for (int n0 = 0; n0 < ntile; n0 += 16) {
         float v[16];
@@ -547,8 +563,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = 0.f;
           const int q = n0 / qrows, nc = it.c0 + n0 - q * qrows;
-          float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
-          epi_put16_rows(epi, tb, lane, v, rowoff, rvmask, group_off(items[i], q) + nc, nc);
+          epi_put16_rows(epi, tb, lane, v, er, group_off(items[i], q) + nc, nc);
         } else {
           if (!rv) continue;
           if (total == 0)

@@ -884,7 +884,14 @@ SplitOp &make_split(mlcc3_ctx *c, const std::string &key, const double *src, lon
   std::string err;
   if (!encode_map(&op.mhi, op.hi, md, ms, bx, &err) || !encode_map(&op.mlo, op.lo, md, ms, bx, &err))
     throw Error{MLCC3_ERR_CUDA, "tensor map " + key + ": " + err};
+  op.rows = box == Box::Pair ? 128u : bx[1];
   return op;
+}
+
+// Tile width of a pair contraction with nN output columns, and the box rows of
+// its column operand (split_amp_T, split_go_T).
+int pair_bn(const mlcc3_ctx *c, long long nN) {
+  return nN > 256 ? c->tc_wide_bn : tc_tile_width(nN);
 }
 
 // Operands of one two-index term of the triples expression, as split copies:
@@ -1364,7 +1371,11 @@ void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const Split
   }
   maps.m[6] = B.mhi;
   maps.m[7] = B.mlo;
-  const int BN = tc_tile_width(nN);
+  const int BN = pair_bn(c, nN);
+  if (B.rows != (unsigned)BN)
+    throw Error{MLCC3_ERR_ARG, "pair contraction: operand box of " + std::to_string(B.rows) +
+                                   " rows for tile width " + std::to_string(BN) +
+                                   " (tc_wide_bn changed after build_integrals?)"};
   const long long nt1 = (s.nv + 7) / 8, nt2 = (s.nv + 15) / 16, ntN = (nN + BN - 1) / BN;
   const int nk = (int)((s.nv + 63) / 64);
   for (int cls = 0; cls < 2; ++cls) {
@@ -1489,13 +1500,13 @@ void tc_vv(mlcc3_ctx *c, const double *X, const std::string &xkey, const double 
 SplitOp &split_amp_T(mlcc3_ctx *c, const std::string &key, const double *Xblk) {
   S s(c);
   return make_split(c, key, Xblk, s.no, s.no, s.NV, s.nv, s.bi, s.bL, 1, s.ba, 1.0, Box::Row,
-                    (unsigned)tc_tile_width(s.NV));
+                    (unsigned)pair_bn(c, s.NV));
 }
 // Go-like G[q][r][c][L] as [q][r][L][c] (Z_L B operand)
 SplitOp &split_go_T(mlcc3_ctx *c, const std::string &key, const double *G) {
   S s(c);
   return make_split(c, key, G, s.no, s.no, s.NO, s.nv, s.oj, s.ok, 1, s.oc, 1.0, Box::Row,
-                    (unsigned)tc_tile_width(s.NO));
+                    (unsigned)pair_bn(c, s.NO));
 }
 // Tl-like T[p][x][y][L] as [p][L][(x,y)] and [p][L][(y,x)] (tc_xt operands)
 void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T) {
@@ -2811,6 +2822,10 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     } else if (n == "tc_group") {
       if (value < 1 || value > 4) throw Error{MLCC3_ERR_ARG, "tc_group out of range 1..4"};
       c->tc_group = (int)value;
+    } else if (n == "tc_wide_bn") {
+      if (value != 128 && value != 160 && value != 256)
+        throw Error{MLCC3_ERR_ARG, "tc_wide_bn must be 128, 160 or 256"};
+      c->tc_wide_bn = (int)value;
     } else if (n == "tc_persist_from") {
       if (value < 0) throw Error{MLCC3_ERR_ARG, "tc_persist_from must be >= 0"};
       c->tc_persist_from = (int)std::min<long long>(value, 1LL << 30);

@@ -34,10 +34,12 @@ class Case:
         return O.make_ctx(self.sys)
 
     # -- library --------------------------------------------------------------
-    def context(self, precision=binding.MLCC3_FP64, device=True):
+    def context(self, precision=binding.MLCC3_FP64, device=True, params=None):
         import torch
         ctx = binding.Context(*self.dims, precision=precision,
                               core_mask=self.sys.core_mask if self.core else None)
+        for k, v in (params or {}).items():
+            ctx.set_param(k, v)
         conv = self.to_dev if device else np.ascontiguousarray
         s = self.sys
         ctx.build_integrals(conv(s.chol), conv(s.t1), conv(s.eps), conv(s.t2c), conv(s.t2x))

@@ -149,3 +149,39 @@ def test_split_grouped_tiles(group, persist):
     got, ref = run_all(c, g), oracle_all(c)
     for k in ref:
         assert rel_err(got[k], ref[k]) < TOL, (group, k, rel_err(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("bn", [128, 160])
+def test_split_wide_pair_tiles(bn):
+    """The sigma pair contractions over N_V > 256 columns at the narrower tile
+    widths (three pipeline stages): the same sigma as the default 256-wide
+    tiles (only the order of the FP64 reductions differs) and the oracle's
+    within the split bar; a width change after the integral build is refused on
+    the host before any launch reads a mismatched operand."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(NO=6, NV=300, no=4, nv=10, NJ=40, nstates=1)
+    st = c.st
+    w = float(st.omega[0])
+    o = c.oracle_ctx()
+    r1, r2 = O.jacobian_left(o, w, st.L1[0], O.to_full(o, st.L2[0]))
+    ref = {"sig1": r1, "sig2": O.from_full(o, r2)}
+    out = {}
+    for name, params in (("wide", {"tc_wide_bn": bn}), ("default", None)):
+        g = c.context(precision=binding.MLCC3_SPLIT_BF16X3, params=params)
+        sig1, sig2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+        g.jacobian_left(st.omega, c.to_dev(st.L1), c.to_dev(st.L2), sig1, sig2)
+        out[name] = {"sig1": c.host(sig1)[0], "sig2": c.host(sig2)[0]}
+        if name == "wide":
+            with pytest.raises(binding.MLCC3Error) as e:
+                g.set_param("tc_wide_bn", 100)
+            assert e.value.code == -1
+            g.set_param("tc_wide_bn", 256)
+            with pytest.raises(binding.MLCC3Error) as e:
+                g.jacobian_left(st.omega, c.to_dev(st.L1), c.to_dev(st.L2), sig1, sig2)
+            assert e.value.code == -1
+            torch.cuda.synchronize()
+    for k in ref:
+        assert rel_err(out["wide"][k], out["default"][k]) < 1e-10, (bn, k)
+        assert rel_err(out["wide"][k], ref[k]) < TOL, (bn, k, rel_err(out["wide"][k], ref[k]))
