@@ -158,11 +158,14 @@ __device__ __forceinline__ void epi_put16(const TcEpi &epi, long long a0, int n0
 // Sixteen columns of the warp's 32 rows in an FP64 mode with a unit column
 // stride.  Each thread holds 16 consecutive columns of its own row, and rows lie
 // far apart in memory, so a direct write touches 32 lines per instruction.  The
-// values pass through shared memory instead (tb: this warp's 32 x 17 floats) and
-// every reduction instruction then covers 16 consecutive columns of two rows:
-// lane l writes column l % 16 of rows 2j + l / 16, j = 0..15, whose offsets
-// ro[j] and validity bits vb (bit j) epi_rows_of gathers once per tile.
-// base: the group offset plus the first column nc.
+// values pass through shared memory instead (tb: this warp's 32 x 16 floats, the
+// 16-byte chunks of row r XOR-permuted by (r / 2) % 4, so that both the
+// four-float stores of eight rows and the reads of two half rows hit distinct
+// banks) and every reduction instruction then covers 16 consecutive columns of
+// two rows: lane l writes column c = l % 16 of rows 2j + l / 16, j = 0..15, at
+// base + ro[j], where ro[j] (that row's offset plus c) and the validity bits vb
+// (bit j) are gathered once per tile by epi_rows_of.  base: the group offset
+// plus the first column nc.
 struct EpiRows {
   long long ro[16];
   unsigned vb;
@@ -170,34 +173,38 @@ struct EpiRows {
 
 __device__ __forceinline__ void epi_rows_of(EpiRows &r, int lane, long long rowoff, bool rv) {
   const unsigned rvmask = __ballot_sync(0xffffffffu, rv);
-  const int half = lane >> 4;
+  const int half = lane >> 4, cc = lane & 15;
   r.vb = 0;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    r.ro[j] = __shfl_sync(0xffffffffu, rowoff, 2 * j + half);
+    r.ro[j] = __shfl_sync(0xffffffffu, rowoff, 2 * j + half) + cc;
     r.vb |= ((rvmask >> (2 * j + half)) & 1u) << j;
   }
 }
 
 __device__ __forceinline__ void epi_put16_rows(const TcEpi &epi, float *tb, int lane, const float *v,
                                                const EpiRows &r, long long base, int nc) {
+  const int sw = (lane >> 1) & 3;
+  float4 *t4 = reinterpret_cast<float4 *>(tb + lane * 16);
 #pragma unroll
-  for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = v[j];
+  for (int q = 0; q < 4; ++q)
+    t4[q ^ sw] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   __syncwarp();
   const int cc = lane & 15, half = lane >> 4;
   const unsigned vb = nc + cc < epi.nlim ? r.vb : 0u;
   float x[16];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) x[j] = tb[(2 * j + half) * 17 + cc];
+  for (int j = 0; j < 16; ++j)
+    x[j] = tb[(2 * j + half) * 16 + ((((cc >> 2) ^ (j & 3))) << 2) + (cc & 3)];
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 16; ++j)
-    if ((vb >> j) & 1u) epi_put(epi, base + r.ro[j] + cc, epi.alpha * x[j]);
+    if ((vb >> j) & 1u) epi_put(epi, base + r.ro[j], epi.alpha * x[j]);
 }
 
 // Shared-memory bytes of the epilogue's transpose buffers (four warps), and the
 // launches that use them: FP64 modes with a unit column stride.
-constexpr int kEpiTbBytes = 4 * 32 * 17 * 4;
+constexpr int kEpiTbBytes = 4 * 32 * 16 * 4;
 __host__ __device__ __forceinline__ bool epi_rows_t(const TcEpi &epi) {
   return epi.sn == 1 && epi.mode >= 2;
 }
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(192, 1)
     const long long rowoff = (long long)r1 * epi.s1 + (long long)r2 * epi.s2;
     EpiRows er;
     if constexpr (ROWS_T) epi_rows_of(er, lane, rowoff, rv);
-    float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
+    float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 16;
 #pragma unroll 1
     for (int n0 = 0; n0 < ntile; n0 += 16) {
       float v[16];
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(192, 1)
       const int ntile = (it.nq > 1 ? it.nq : 1) * qrows;
       EpiRows er;
       if constexpr (ROWS_T) epi_rows_of(er, lane, rowoff, rv);
-      float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 17;
+      float *tb = reinterpret_cast<float *>(smem + STAGES * STAGE + 256) + lg * 32 * 16;
 #pragma unroll 1
       for (int n0 = 0; n0 < ntile; n0 += 16) {
         float v[16];
