@@ -5,7 +5,8 @@
 * the adjoint identity <L, A R> = <A^T L, R> for sigma (and L3);
 * finite differences: Upsilon = dg/dt1, R3(omega=0) = dtau3, rho(omega=0) = dOmega;
 * invariants: pair symmetry, i=j=k blocks, CCSD limit, traces;
-* the oscillator strength on a hand-computed case.
+* the oscillator strength on a hand-computed case and against exact transition
+  moments of the T1-dressed dipole in the determinant space.
 """
 import numpy as np
 import pytest
@@ -151,6 +152,74 @@ def test_densities_are_expectation_values(bf):
         assert abs(ref) > 1e-8
         assert abs(got - ref) <= 1e-11 * abs(ref)
     assert Rbar is not None
+
+
+def test_oscillator_strength_from_exact_moments(bf):
+    """f of the triples densities against exact transition moments: with the
+    bare dipole mu_x dressed by T1 as an operator, e^{-T1} mu_x e^{T1} (the
+    E_AI series on determinants, not a matrix formula), the moments are the
+    expectation values of the density pin; f = 2/3 omega sum_x T0m_x Tm0_x.
+    A transposed or sign-flipped T1 dressing of mu fails."""
+    s, ctx, ds, m, st = bf
+    w = float(st.omega[0])
+    R1, R2 = st.R1[0], O.to_full(ctx, st.R2[0])
+    L1, L2 = st.L1[0], O.to_full(ctx, st.L2[0])
+    lam1, lam2b = synth.make_multipliers(s, seed=4)
+    lam2 = O.to_full(ctx, lam2b)
+    tau = O.tau3(ctx)
+    R3 = O.right_R3(ctx, w, R1, R2)
+    nmo, hfi = ds.nmo, m.hf_index
+    D00_in = np.zeros((nmo, nmo))
+    for p in range(nmo):
+        for q in range(nmo):
+            E = np.zeros((nmo, nmo))
+            E[p, q] = 1.0
+            v = m.Abar(E, ds.hf)
+            D00_in[p, q] = v[hfi] + m.bra_sd(lam1, lam2, v)
+    _, Dm0T, D0mT = O.transition_densities(ctx, w, lam1, lam2, R1, R2, L1, L2, D00_in)
+    mu = np.random.default_rng(5).normal(size=(3, nmo, nmo))
+    mu = 0.5 * (mu + mu.transpose(0, 2, 1))
+
+    def exp_t1(V, sign):
+        out, term = V.copy(), V.copy()
+        for n in range(1, 12):
+            term = sign * ds.t1_op(ctx.t1, term) / n
+            if not np.any(term):
+                break
+            out = out + term
+        return out
+
+    def dressed(mx, V, t3):
+        """e^{-T} e^{-T1} mu_x e^{T1} e^{T} V, T = T2 (+ T3)."""
+        u = exp_t1(m.expT(V, 1.0, t3), 1.0)
+        return m.expT(exp_t1(ds.one_body(mx, u), -1.0), -1.0, t3)
+
+    Rsd = ds.t1_op(R1, ds.hf) + ds.t2_op(O.delta(R2), ds.hf)
+    R3k = ds.t3_op(R3, ds.hf)
+    lr_sd = O.sd_inner(ctx, lam1, lam2, R1, R2)
+    lr3 = m.bra_3(lam1, lam2, 0.0, R3k)
+    Tm0, T0m = np.zeros(3), np.zeros(3)
+    for x in range(3):
+        vw, vo = dressed(mu[x], ds.hf, tau), dressed(mu[x], ds.hf, None)
+        Tm0[x] = m.bra_sd(L1, L2, vw) + m.bra_3(L1, L2, w, vw) - m.bra_sd(L1, L2, vo)
+
+        def expect(with3):
+            t3 = tau if with3 else None
+            v = dressed(mu[x], Rsd + (R3k if with3 else 0.0), t3)
+            u = dressed(mu[x], ds.hf, t3)
+            b3 = (lambda y: m.bra_3(lam1, lam2, 0.0, y)) if with3 else (lambda y: 0.0)
+            xv = v[hfi] + m.bra_sd(lam1, lam2, v) + b3(v)
+            d00 = u[hfi] + m.bra_sd(lam1, lam2, u) + b3(u)
+            return xv - (lr_sd + (lr3 if with3 else 0.0)) * d00
+        T0m[x] = expect(True) - expect(False)
+    f_ref = 2.0 / 3.0 * w * float(np.dot(T0m, Tm0))
+    assert abs(f_ref) > 1e-10
+    got = O.oscillator_strength(ctx, w, D0mT, Dm0T, mu)
+    assert abs(got - f_ref) <= 1e-10 * abs(f_ref)
+    # the dressing matters at these amplitudes: the bare dipole gives another f
+    bare = 2.0 / 3.0 * w * float(np.dot(np.einsum('pq,xpq->x', D0mT, mu),
+                                        np.einsum('pq,xpq->x', Dm0T, mu)))
+    assert abs(bare - f_ref) > 1e-6 * abs(f_ref)
 
 
 def _small(seed=11, core=False):
