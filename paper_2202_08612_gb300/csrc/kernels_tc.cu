@@ -750,16 +750,28 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
   const int tr = (Rp + 31) / 32, tc = (C + 31) / 32;
   const long long ntiles = B * (long long)tr * tc;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  // rows ty, ty + 8, ty + 16, ty + 24 of tile q, column tx, into registers: the
+  // next tile's loads are issued before this tile's stores
+  double pf[4];
+  auto load = [&](long long q) {
+    const long long b = q / ((long long)tr * tc);
+    const int r0 = (int)((q / tc) % tr) * 32, c = (int)(q % tc) * 32 + tx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = r0 + ty + 8 * k;
+      pf[k] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : 0.0;
+    }
+  };
+  if (blockIdx.x < ntiles) load(blockIdx.x);
   for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
     const long long b = q / ((long long)tr * tc);
     const int rt = (int)((q / tc) % tr), ct = (int)(q % tc);
     const int r0 = rt * 32, c0 = ct * 32;
     __syncthreads();  // the previous tile's reads of `tile` are done
-    for (int i = ty; i < 32; i += 8) {
-      const int r = r0 + i, c = c0 + tx;
-      tile[i][tx] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : 0.0;
-    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = pf[k];
     __syncthreads();
+    if (q + gridDim.x < ntiles) load(q + gridDim.x);
     {
       // thread t writes four consecutive r (8-byte stores) of column c0 + t / 8
       const int ci = threadIdx.x >> 3, rq = 4 * (threadIdx.x & 7);
