@@ -7,7 +7,7 @@ equations), with every sum taken over *all* ordered occupied triples and full
 n_v^3 blocks, so that each line can be read against an equation.  No blocking,
 batching over i>=j>=k, fusion or reordering beyond the equations.
 
-Conventions (the readings are listed in the design doc as well):
+Conventions:
 
 * orbitals: occupied first, then virtual; active occupied = occupied [0, n_o),
   active virtual = virtual [0, n_v).
