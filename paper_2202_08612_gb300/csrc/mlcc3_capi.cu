@@ -811,6 +811,21 @@ TcDev tc_plan(mlcc3_ctx *c, const std::string &key0, const std::function<void(Tc
   TcPlan pl;
   build(pl);
   cap_chains(pl, cap);
+  if ((long long)pl.items.size() > (long long)c->tc_persist_from) {
+    // persistent launches hand out items round-robin: the longest chains first
+    // (stable, so equal items keep their order and their operand reuse) even
+    // out the work of the CTAs; every item owns its outputs, so the order of
+    // the items does not change the result
+    std::vector<int> len(pl.items.size());
+    for (size_t i = 0; i < pl.items.size(); ++i)
+      for (int q = 0; q < pl.items[i].seg_count; ++q) len[i] += pl.segs[pl.items[i].seg_begin + q].nk;
+    std::vector<size_t> ord(pl.items.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return len[a] > len[b]; });
+    std::vector<TcItem> sorted(pl.items.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = pl.items[ord[i]];
+    pl.items.swap(sorted);
+  }
   void *si = upload_cached(c, key + ":items", pl.items.data(), pl.items.size() * sizeof(TcItem));
   void *ss = upload_cached(c, key + ":segs", pl.segs.data(), pl.segs.size() * sizeof(TcSeg));
   c->items[key + ":items"].second = (int)pl.items.size();
