@@ -61,6 +61,7 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.first = 0
 
     def __enter__(self):
         try:
@@ -70,6 +71,12 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # sampling is running before the timed region starts; the rows that
+            # arrive from here on fall inside it
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.rows)
         except Exception:
             self.proc = None
         return self
@@ -89,13 +96,19 @@ class ClockSampler:
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace('.', '', 1).isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace('.', '', 1).isdigit()]
+        rows = self.rows[self.first:]
+        out = {}
+        if not rows:  # a timed region shorter than one sampling interval
+            rows = self.rows[-1:]
+            out["note"] = "no sample inside the timed region; the last one before it"
+        sm = [float(r[0]) for r in rows if r[0].replace('.', '', 1).isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace('.', '', 1).isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for r in self.rows for n, v in zip(names, r[4:8]) if v == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        out.update({"sm_mhz": statistics.median(sm) if sm else None,
+                    "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                    "samples": len(self.rows) - self.first})
+        return out
 
 
 # the sources that fix the tensor-core kernel and its launch plans (the DRAM
@@ -714,7 +727,7 @@ def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="guanine_like_small",

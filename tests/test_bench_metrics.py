@@ -24,3 +24,19 @@ def test_tc_site_fracs():
 def test_tc_site_fracs_zero_time():
     got = bench.tc_site_fracs({"tc_gemm_kernel:xt": (1, 0.0, 1.0e9)}, 1, 1700.0)
     assert got["xt"]["frac"] is None
+
+
+def test_clock_summary_counts_samples_inside_the_timed_region():
+    c = bench.ClockSampler(0)
+    row = lambda mhz, cap: [str(mhz), "2070", "900.0", "0x0", "Not Active", "Not Active",
+                            "Not Active", "Active" if cap else "Not Active"]
+    # one row before the region (sampler start), three inside
+    c.rows = [row(1200, False), row(2070, True), row(2055, False), row(2070, False)]
+    c.first = 1
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and "note" not in s
+    # a region shorter than the sampling interval: the last earlier row, flagged
+    c.first = 4
+    s = c.summary()
+    assert s["samples"] == 0 and s["sm_mhz"] == 2070.0 and "note" in s
