@@ -672,6 +672,56 @@ def tc_site_fracs(stats, steps, pk):
             for k, v in stats.items() if k.startswith("tc_gemm_kernel:")}
 
 
+def run_nv_scaling(args):
+    """The ρ and σ of one trial vector at fixed active space (N_O=20, n_o=12,
+    n_v=60, N_J=600) for N_V = 200, 400, 800: the time is affine in N_V (the
+    d-terms scale with N_V, the l-terms, conversions and denominators do not)."""
+    import torch
+    from paper_2202_08612_gb300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    NO, no, nv, NJ = 20, 12, 60, 600
+    pts = []
+    for NV in (200, 400, 800):
+        x, omega = device_system(NO, NV, no, nv, NJ, 1, 2022, dev, False)
+        out = [torch.zeros_like(x[k]) for k in ("R1", "R2", "R1", "R2")]
+        ctx = binding.Context(NO, NV, no, nv, NJ, precision=binding.MLCC3_SPLIT_BF16X3,
+                              stream=stream.cuda_stream)
+        ctx.build_integrals(x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"])
+
+        def it():
+            ctx.jacobian_right(omega, x["R1"], x["R2"], out[0], out[1])
+            ctx.jacobian_left(omega, x["L1"], x["L2"], out[2], out[3])
+        for _ in range(args.warmup):
+            it()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            it()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        pts.append({"N_V": NV, "ms": ms, "tflops": 16.0 * NV * nv ** 3 * no ** 3 / (ms * 1e-3) / 1e12})
+        ctx.close()
+        del x, out
+        torch.cuda.empty_cache()
+    nvs = np.array([p["N_V"] for p in pts], dtype=float)
+    ms = np.array([p["ms"] for p in pts])
+    slope, icpt = np.polyfit(nvs, ms, 1)
+    resid = float(np.max(np.abs(ms - (slope * nvs + icpt)) / ms))
+    print(json.dumps({"metric": METRIC, "value": pts[-1]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": pts[-1]["ms"],
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "bf16x3", "data": "synthetic (device-generated, torch Philox)",
+                      "config": {"workload": "nv_scaling: N_O=20 n_o=12 n_v=60 N_J=600, N_V = 200, 400, "
+                                             "800, one trial vector (value: the N_V = 800 point)"},
+                      "points": pts, "fit_ms": {"per_N_V": slope, "intercept": icpt,
+                                                "max_rel_residual": resid}}), flush=True)
+
+
 def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ, core, split):
     """The three transition densities and f of one state of a large system, in a
     process of their own: the densities hold every batch that touches a range of
@@ -731,7 +781,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="guanine_like_small",
-                    choices=sorted(WORKLOADS) + ["uneven_sweep"] + sorted(LARGE))
+                    choices=sorted(WORKLOADS) + ["uneven_sweep", "nv_scaling"] + sorted(LARGE))
     ap.add_argument("--vectors", type=int, default=4,
                     help="trial vectors per system of the uneven_sweep workload")
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
@@ -757,6 +807,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "ours" and args.workload == "uneven_sweep":
         run_sweep(args)
+    elif args.impl == "ours" and args.workload == "nv_scaling":
+        run_nv_scaling(args)
     elif args.impl == "ours" and args.workload in LARGE:
         run_large(args)
     elif args.impl == "reference":
