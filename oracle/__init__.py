@@ -5,3 +5,4 @@ leg may import this package.  The library itself never calls it, and it
 shares no code with the CUDA path.
 """
 from .mlcc3_oracle import *  # noqa: F401,F403
+from .cnto import *  # noqa: F401,F403
