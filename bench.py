@@ -296,8 +296,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         f_ours = prob.step(ctx, prob.dev, prob.out_dev)
     ctx.profile(True)
-    barrier()
     with ClockSampler(local_rank) as clk:
+        barrier()  # every rank's clock sampling is running before any rank starts
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
