@@ -35,7 +35,7 @@ __all__ = [
     "contra2", "contra3", "sym3", "eps3", "tau3", "tau3_block", "triples_omega",
     "upsilon", "right_R3", "jacobian_right", "left_L3", "jacobian_left",
     "lambda3", "density_left", "transition_densities", "oscillator_strength",
-    "sd_inner", "rayleigh_quotient",
+    "sd_inner", "rayleigh_quotient", "cvs_mask", "cvs_project", "cvs_exact_projection",
 ]
 
 _PAIR_PERMS = ("ijkabc", "ikjacb", "jikbac", "jkibca", "kijcab", "kjicba")
@@ -446,6 +446,32 @@ def transition_densities(ctx, omega, lam1, lam2, R1, R2, L1, L2, D00_in):
     lr_sd = sd_inner(ctx, lam1, lam2, R1, R2)
     D -= lr_sd * D00
     return D00, Dm0, D
+
+
+def cvs_project(ctx, x1, x2):
+    """The CVS space (Sec. 3): singles whose occupied index is a core orbital,
+    doubles (full storage) with at least one core occupied index."""
+    c = ctx.core
+    return x1 * c[None, :], x2 * (c[None, :, None, None] | c[None, None, None, :])
+
+
+def cvs_exact_projection(ctx, omega, R1, R2, L1, L2):
+    """Diagnostic of the CVS skip rule (Sec. 3; the paper drops the triples
+    batches without a core index): rho and sigma of CVS vectors (a) with the
+    rule, as jacobian_right / jacobian_left compute them, and (b) exactly:
+    every batch kept and the results projected onto the CVS space.  Both are
+    returned projected, as ((rho1, rho2, sigma1, sigma2) of (a), the same of
+    (b)); the difference is what the rule leaves out, including the valence
+    batches whose denominators lie near a core excitation energy."""
+    import copy
+    full = copy.copy(ctx)
+    full.core = np.zeros_like(ctx.core)
+    out = []
+    for c in (ctx, full):
+        r1, r2 = jacobian_right(c, omega, R1, R2)
+        s1, s2 = jacobian_left(c, omega, L1, L2)
+        out.append(cvs_project(ctx, r1, r2) + cvs_project(ctx, s1, s2))
+    return tuple(out)
 
 
 def sd_inner(ctx, x1, x2, y1, y2):

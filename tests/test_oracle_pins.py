@@ -346,6 +346,27 @@ def test_density_traces():
         assert np.abs(D).max() > 1e-9
 
 
+def test_cvs_skip_rule_against_the_exact_projection():
+    """Reading of the CVS skip rule (Sec. 3): its singles rho is exact (every
+    term of rho^a_I with a core I comes from a batch that holds I), while the
+    doubles and sigma differ from the exact projection by the valence batches'
+    terms; both forms satisfy the adjoint identity on CVS vectors."""
+    s = synth.make_system(5, 9, 3, 4, 12, seed=11, core=True)
+    ctx = O.make_ctx(s)
+    st = synth.make_states(s, 1, seed=12, cvs_states=(0,))
+    w = float(st.omega[0])
+    R1, R2 = st.R1[0], O.to_full(ctx, st.R2[0])
+    L1, L2 = st.L1[0], O.to_full(ctx, st.L2[0])
+    rule, exact = O.cvs_exact_projection(ctx, w, R1, R2, L1, L2)
+    assert np.abs(rule[0] - exact[0]).max() <= 1e-15 * np.abs(exact[0]).max()
+    gap = [np.linalg.norm(x - y) / np.linalg.norm(y) for x, y in zip(rule[1:], exact[1:])]
+    assert all(g > 1e-3 for g in gap)   # the rule is an approximation there
+    for r1, r2, s1, s2 in (rule, exact):
+        lhs = O.sd_inner(ctx, L1, L2, r1, r2)
+        rhs = O.sd_inner(ctx, s1, s2, R1, R2)
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
 def test_oscillator_strength_hand_case():
     """f = 2/3 w sum_x T0m_x Tm0_x on a case computed by hand: densities with
     one element each, identity t1 transform (t1 = 0)."""
