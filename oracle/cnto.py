@@ -10,6 +10,8 @@ from __future__ import annotations
 
 import numpy as np
 
+__all__ = ["cnto_M", "cnto_N", "cnto_state_average", "cnto_count"]
+
 
 def cnto_M(R1, R2):
     """Eq. M: M_ij = sum_a R^a_i R^a_j
