@@ -35,7 +35,10 @@ WORKLOADS = {
 # uneven systems of the batched sweep, (n_o, n_v, N_V), N_O = n_o + 8, N_J = 3 N_V
 SWEEP_SYSTEMS = [(8, 40, 120), (11, 60, 216), (14, 80, 312), (18, 100, 408), (21, 120, 504),
                  (24, 140, 600)]
-UNITS_PER_STEP = 4 + 8 + 8 + 10 + 10 + 16      # per state
+# Leading FLOP counts per state in units of N_V n_v^3 n_o^3 (Sec. 3); D^{0-0} is
+# D^{m-0} with the multipliers in place of L (same count)
+FLOP_UNITS = {"omega": 4, "rho": 8, "sigma": 8, "D_m0": 10, "D_00": 10, "D_0m": 16}
+UNITS_PER_STEP = sum(FLOP_UNITS.values())      # per state
 FP64_PEAK_TFLOPS = 1.25                        # nominal GB300 FP64 (ALU bound)
 
 
@@ -631,7 +634,8 @@ def run_large(args):
     alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
     # CVS: only the triples that carry the core index (n_o^3 - (n_o - 1)^3 of the n_o^3
     # ordered ones) contribute
-    fl_it = 16.0 * NV * nv ** 3 * (no ** 3 - (no - 1) ** 3) * nvec if cvs else 16.0 * unit * nvec
+    rs = float(FLOP_UNITS["rho"] + FLOP_UNITS["sigma"])
+    fl_it = rs * NV * nv ** 3 * (no ** 3 - (no - 1) ** 3) * nvec if cvs else rs * unit * nvec
     line = {"metric": METRIC, "value": fl_it / (ms_it * 1e-3) / 1e12, "unit": "TFLOP/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_it,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -648,7 +652,7 @@ def run_large(args):
             "s_per_davidson_iter": ms_it * 1e-3,
             "build_integrals_ms": ms_build,
             "omega": {"ms": ms_omega, "ms_first_call": ms_omega_first,
-                      "tflops": 4.0 * unit / (ms_omega * 1e-3) / 1e12},
+                      "tflops": FLOP_UNITS["omega"] * unit / (ms_omega * 1e-3) / 1e12},
             "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor",
                          "achieved": 3.0 * alg if alg else None, "peak": pk, "unit": "TFLOP/s",
                          "frac": 3.0 * alg / pk if alg else None, "achieved_algorithmic": alg,
@@ -704,7 +708,8 @@ def run_nv_scaling(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        pts.append({"N_V": NV, "ms": ms, "tflops": 16.0 * NV * nv ** 3 * no ** 3 / (ms * 1e-3) / 1e12})
+        rs = FLOP_UNITS["rho"] + FLOP_UNITS["sigma"]
+        pts.append({"N_V": NV, "ms": ms, "tflops": rs * NV * nv ** 3 * no ** 3 / (ms * 1e-3) / 1e12})
         ctx.close()
         del x, out
         torch.cuda.empty_cache()
@@ -752,7 +757,8 @@ def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, 
     tc_ms, tc_fl = sum(v[1] for v in tc), sum(v[2] for v in tc)
     pk = peaks().get("bf16_tflops_sustained") or 1700.0
     alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
-    line = {"metric": METRIC, "value": 36.0 * unit / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+    dens = float(FLOP_UNITS["D_m0"] + FLOP_UNITS["D_00"] + FLOP_UNITS["D_0m"])
+    line = {"metric": METRIC, "value": dens * unit / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
             "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3" if split else "f64", "data": "synthetic (device-generated, torch Philox)",

@@ -1,0 +1,36 @@
+"""Values the paper prints, as text fixtures under tests/golden/ (each line
+with the passage it comes from), against what the code uses."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _table(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            key, val = line.split()[:2]
+            out[key] = float(val)
+    return out
+
+
+def test_flop_prefactors_are_the_papers():
+    """The bench's algorithmic FLOP accounting uses the leading counts the
+    paper states (Sec. 3); D^{0-0} is D^{m-0} with the multipliers in place of
+    L, so it takes D^{m-0}'s count."""
+    t = _table("flop_prefactors.txt")
+    for k in ("omega", "rho", "sigma", "D_m0", "D_0m"):
+        assert bench.FLOP_UNITS[k] == t[k], k
+    assert bench.FLOP_UNITS["D_00"] == t["D_m0"]
+    assert bench.UNITS_PER_STEP == sum(bench.FLOP_UNITS.values()) == 56
+    NO, NV, no, nv = 20, 200, 12, 60
+    assert bench.algorithmic_flops(NO, NV, no, nv, 1) == 56 * NV * nv ** 3 * no ** 3
+    # the paper's CVS count (per transformation, N_V n_v^3 n_o^2 units) against the
+    # exact count of ordered triples holding the core index, which the bench reports
+    assert t["cvs"] == 8
+    assert no ** 3 - (no - 1) ** 3 == 3 * no ** 2 - 3 * no + 1
