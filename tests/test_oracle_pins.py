@@ -406,3 +406,37 @@ def test_rayleigh_quotient_is_the_eigenvalue_at_the_fixed_point():
     # a vector that is not an eigenvector gives something else
     rq2 = O.rayleigh_quotient(o, w, R1 + 0.1, O.to_full(o, R2), L1, O.to_full(o, L2), sd_part)
     assert abs(rq2 - w) > 1e-6
+
+
+@pytest.mark.parametrize("case", [(5, 9, 4, 5, 14, 21), (4, 7, 3, 4, 10, 22)])
+def test_tau3_block_equals_full_tensor(case):
+    """Eq. tau3 per ordered occupied triple: the one-block form used at large
+    sizes (six explicit pair permutations of W) equals the full tensor, whose
+    values the determinant-space brute force fixes, for every ordered (i,j,k)
+    including i = j, j = k and i = j = k."""
+    NO, NV, no, nv, NJ, seed = case
+    s = synth.make_system(NO, NV, no, nv, NJ, seed=seed)
+    ctx = O.make_ctx(s)
+    full = O.tau3(ctx)
+    scale = np.abs(full).max()
+    assert scale > 1e-6
+    seen = set()
+    for i in range(no):
+        for j in range(no):
+            for k in range(no):
+                blk = O.tau3_block(ctx, i, j, k)
+                assert np.abs(blk - full[i, j, k]).max() <= 1e-13 * scale, (i, j, k)
+                seen.add((i == j, j == k, i == k))
+    assert {(True, True, True), (True, False, False), (False, True, False),
+            (False, False, True), (False, False, False)} <= seen
+    # sharp: pairing one permuted W with the wrong virtual order fails
+    tA, tB = ctx.views(ctx.t2)
+    gv, go = ctx.gn("vVvo"), ctx.gn("Oovo")
+    i, j, k = 2, 1, 0
+    W = (np.einsum('aD,bDc->abc', tA[j, i], gv[:, :, :, k])
+         - np.einsum('abL,Lc->abc', tB[j], go[:, i, :, k]))
+    eo, ev = ctx.eo, ctx.ev[:nv]
+    den = ev[:, None, None] + ev[None, :, None] + ev[None, None, :] - eo[i] - eo[j] - eo[k]
+    good = O.tau3_block(ctx, i, j, k)
+    bad = good + (np.einsum('bac->abc', W) - np.einsum('acb->abc', W)) / den
+    assert np.abs(bad - full[i, j, k]).max() > 1e-6 * scale
