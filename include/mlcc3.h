@@ -6,7 +6,10 @@
  * the ground-state residual, the right and transpose Jacobian
  * transformations, the transition densities and the oscillator strength.
  * The triples amplitudes are built on the fly per batch of active occupied
- * indices i >= j >= k and never stored as a whole.
+ * indices i >= j >= k.  One n_v^3 block per unique batch of the current chunk
+ * is held on the device: when every block fits (mlcc3_set_param
+ * "chunk_blocks", sized from the free memory by default) that is all of the
+ * unique blocks; larger systems are swept in chunks.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -54,7 +57,13 @@ extern "C" {
 /* Arithmetic of the contractions.  MLCC3_FP64: every product and sum in
  * IEEE double.  MLCC3_SPLIT_BF16X3: integral-amplitude products on the
  * tensor cores from hi/lo bfloat16 splits with FP32 accumulation;
- * denominators and final reductions stay in FP64. */
+ * denominators and final reductions stay in FP64.
+ * An FP16 hi/lo split is not offered: FP16's five exponent bits put the low
+ * half of an operand of magnitude below about 2^-3 (most amplitudes and
+ * integrals here) into the subnormal range, where it loses the bits the
+ * split exists to keep, unless every operand is rescaled per block; the
+ * bfloat16 split has FP32's exponent range and needs no scaling.  The value 2
+ * is rejected with MLCC3_ERR_ARG. */
 #define MLCC3_FP64 0
 #define MLCC3_SPLIT_BF16X3 1
 
@@ -199,6 +208,20 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              run the persistent kernel (one CTA per SM looping over tiles,
  *              accumulator double-buffered in TMEM); smaller ones run one CTA
  *              per tile.  Default 304; 0 always persistent.
+ *   "cvs"      1 (default): a context created with a core mask applies the CVS
+ *              skip rule (mlcc3_dims.core_mask) in the Jacobian transformations
+ *              and the densities; 0: the same context treats its vectors as
+ *              valence states (every batch kept), so that the valence and the
+ *              core states of one system share one integral build.  1 needs a
+ *              core mask.
+ *   "tc_wait_clocks"  clock limit of the split-precision tensor-core kernel's
+ *              pipeline waits (a stage to fill or free, an accumulator to finish
+ *              or to be read); 0 (default) is about one second.  On expiry the
+ *              kernel stops issuing work, waits for the copies and MMAs it has
+ *              issued, frees its tensor memory and returns; the call then
+ *              returns MLCC3_ERR_TIMEOUT and drops the context's cached tau, and
+ *              the context stays usable.  A small value (a few clocks) makes the
+ *              waits run out: failure-path testing only.  Range 0..2^40.
  *   "bstc_fill"  split-K target of the FP64 strided contractions: a launch
  *              with few output tiles and a long reduction splits K until about
  *              bstc_fill x 152 CTAs run; 0 never splits.  Default 4.  Range 0..64.
@@ -221,6 +244,8 @@ int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
  * index tables) from one fixed 32 MiB device array compiled into the
  * library, which every device that loads the library holds until exit.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.
+ * It computes in FP64 (the FP64 kernels of the MLCC3_FP64 mode) and takes
+ * MLCC3_FP64 contexts only: a split-precision context gets MLCC3_ERR_STATE.
  * Requirements: mlcc3_build_integrals has run on `ctx` (that call allocates,
  * so make it during set-up); omega1/omega2 are device pointers (host arrays
  * would need staging buffers); the current device is the context's; and
@@ -229,6 +254,8 @@ int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
  * get MLCC3_ERR_ARG with the required size in mlcc3_last_error().
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept until exit: cudaDeviceReset while the library is
+ * loaded is not supported.
  * Every call shares the array and finds the previous call's contents in it
  * (the accumulators are cleared on entry); calls that overlap on the GPU
  * (other streams, other contexts on the same device) race on it and must be

@@ -74,6 +74,7 @@ struct mlcc3_ctx {
   cudaStream_t stream;
   int device;
   std::vector<uint8_t> core;
+  bool cvs = true;  // apply the CVS skip rule of the core mask (mlcc3_set_param "cvs")
   bool built = false;
   unsigned long long build_gen = 0;  // counts mlcc3_build_integrals calls
   // split-K target of the FP64 strided contraction: when few output tiles
@@ -86,6 +87,8 @@ struct mlcc3_ctx {
   int tc_kcap = 16;
   int tc_group = 4;  // batches stacked along N in a triples-build tile
   int tc_wide_bn = 256;  // tile width of the pair contractions with more than 256 columns
+  // clock limit of the tensor-core kernel's progress waits (0: about one second)
+  long long tc_wait = 0;
   // tensor-core launches with more tiles than this use the persistent kernel
   int tc_persist_from = mlcc3::kTcPersistFrom;
   // batch chunking: at most chunk_blocks blocks held per chunk (0 = sized from

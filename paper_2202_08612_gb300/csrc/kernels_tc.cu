@@ -4,9 +4,12 @@
 //   warp 0 lane 0  : TMA producer (A_hi, A_lo, B_hi, B_lo per 64-wide K chunk)
 //   warp 1         : TMEM allocation; lane 0 issues tcgen05.mma
 //   warps 2..5     : epilogue, tcgen05.ld of the FP32 accumulator
-// Every wait on an mbarrier is bounded (about one second of clock); on
-// expiry the kernel records kStatusTimeout in the status word, stops issuing
-// work, drains what it issued, frees its TMEM and returns.
+// Every wait on an mbarrier is bounded.  The progress waits (a stage to fill
+// or to free, an accumulator to finish or to be read) take TcEpi::wait clocks
+// (default about one second); on expiry the kernel records kStatusTimeout in
+// the status word and stops issuing work.  The drain waits, for the TMA copies
+// and MMAs already issued, always take the default bound, so that no copy is
+// still writing the shared memory and no MMA the TMEM when the CTA frees them.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -44,11 +47,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: about 2^31 clocks (~1 s at 2 GHz).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status) {
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait of `limit` clocks (0: kTcWaitDefault, about 1 s at 2 GHz); on
+// expiry it records kStatusTimeout and returns false.  Limits below 2^20 clocks
+// poll with the non-suspending test_wait, so that the limit is what ends the
+// wait (try_wait may suspend the thread until the phase completes).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status,
+                                          long long limit) {
+  if (limit <= 0) limit = kTcWaitDefault;
   const long long t0 = clock64();
+  if (limit < (1LL << 20)) {
+    while (!mbar_test_wait(bar, parity)) {
+      if (clock64() - t0 > limit) {
+        atomicOr(status, kStatusTimeout);
+        return false;
+      }
+    }
+    return true;
+  }
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 31)) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, kStatusTimeout);
       return false;
     }
@@ -299,7 +328,7 @@ __global__ void __launch_bounds__(192, 1)
     for (int s = 0; s < it.seg_count && ok; ++s) {
       const TcSeg &sg = seg[s];
       for (int kc = 0; kc < sg.nk; ++kc) {
-        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
+        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status, epi.wait)) {
           ok = false;
           break;
         }
@@ -313,12 +342,17 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
     }
-    if (!ok) {
-      // drain: wait (bounded) until every chunk this thread issued has landed
+    // drain: wait (bounded) until every chunk this thread issued has landed.  Also
+    // after a clean run: the MMA issuer may have given up before the last chunks
+    // arrived, and the shared memory must outlive every copy issued into it.  The
+    // chunks before the last STAGES were consumed by MMAs (their stages were
+    // reused), so only the last STAGES need a wait.
+    (void)ok;
+    {
       int st2 = 0;
       uint32_t ph2 = 0;
       for (int c = 0; c < issued; ++c) {
-        if (c >= issued - STAGES) mbar_wait(full0 + 8 * st2, ph2, status);
+        if (c >= issued - STAGES) mbar_wait(full0 + 8 * st2, ph2, status, kTcWaitDefault);
         if (++st2 == STAGES) {
           st2 = 0;
           ph2 ^= 1u;
@@ -330,7 +364,7 @@ __global__ void __launch_bounds__(192, 1)
     int stage = 0;
     uint32_t phase = 0;
     for (int c = 0; c < total; ++c) {
-      if (!mbar_wait(full0 + 8 * stage, phase, status)) break;
+      if (!mbar_wait(full0 + 8 * stage, phase, status, epi.wait)) break;
       tc_fence_after();
       unsigned char *st = smem + stage * STAGE;
       const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
@@ -352,7 +386,8 @@ __global__ void __launch_bounds__(192, 1)
     mma_commit(done);  // arrives once every MMA issued above has completed
   } else if (warp >= 2) {
     // ---- epilogue ----
-    const bool ok = mbar_wait(done, 0, status);
+    // a drain wait: every MMA issued has completed before TMEM is read and freed
+    const bool ok = mbar_wait(done, 0, status, kTcWaitDefault);
     tc_fence_after();
     const int lg = warp & 3;
     const int row = lg * 32 + lane;
@@ -468,7 +503,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int q = 0; q < it.seg_count && !*abort_flag; ++q) {
         const TcSeg &sg = segs[it.seg_begin + q];
         for (int kc = 0; kc < sg.nk; ++kc) {
-          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status)) {
+          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, status, epi.wait)) {
             *abort_flag = 1;
             break;
           }
@@ -486,7 +521,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     // the shared memory must outlive every copy issued into it
     for (int s = 0; s < STAGES; ++s)
-      if (pending[s]) mbar_wait(full0 + 8 * s, last[s], status);
+      if (pending[s]) mbar_wait(full0 + 8 * s, last[s], status, kTcWaitDefault);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     int stage = 0;
@@ -494,7 +529,7 @@ __global__ void __launch_bounds__(192, 1)
     int t = 0;
     for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x, ++t) {
       const int u = t & 1;
-      if (!mbar_wait(tempty0 + 8 * u, ((uint32_t)(t >> 1) & 1u) ^ 1u, status)) {
+      if (!mbar_wait(tempty0 + 8 * u, ((uint32_t)(t >> 1) & 1u) ^ 1u, status, epi.wait)) {
         *abort_flag = 1;
         break;
       }
@@ -506,7 +541,7 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t idesc = idesc_n(IDESC, (it.nq > 1 ? it.nq : 1) * qrows);
       bool ok = true;
       for (int c = 0; c < total; ++c) {
-        if (!mbar_wait(full0 + 8 * stage, phase, status)) {
+        if (!mbar_wait(full0 + 8 * stage, phase, status, epi.wait)) {
           *abort_flag = 1;
           ok = false;
           break;
@@ -532,7 +567,7 @@ __global__ void __launch_bounds__(192, 1)
       mma_commit(tfull0 + 8 * u);  // arrives when this item's MMAs have completed
     }
     mma_commit(done);
-    mbar_wait(done, 0, status);  // every MMA issued above has completed
+    mbar_wait(done, 0, status, kTcWaitDefault);  // every MMA issued above has completed
   } else if (warp >= 2) {
     // ---- epilogue ----
     const int lg = warp & 3;
@@ -540,7 +575,7 @@ __global__ void __launch_bounds__(192, 1)
     int t = 0;
     for (int i = blockIdx.x; i < nitems && !*abort_flag; i += gridDim.x, ++t) {
       const int u = t & 1;
-      const bool ok = mbar_wait(tfull0 + 8 * u, (uint32_t)(t >> 1) & 1u, status);
+      const bool ok = mbar_wait(tfull0 + 8 * u, (uint32_t)(t >> 1) & 1u, status, epi.wait);
       if (!ok) *abort_flag = 1;
       tc_fence_after();
       const TcItem it = items[i];

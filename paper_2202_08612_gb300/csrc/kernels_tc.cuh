@@ -55,7 +55,13 @@ struct TcEpi {
   int lim1, lim2, nlim;
   float alpha;
   int qw;       // columns per group of a grouped tile (0: one group of the launch's BN)
+  // clock limit of the pipeline's progress waits (0: kTcWaitDefault).  The
+  // drain waits (copies and MMAs already issued) always use kTcWaitDefault.
+  long long wait;
 };
+
+// About one second of clock at 2 GHz.
+constexpr long long kTcWaitDefault = 1LL << 31;
 
 // Status bits written by the tensor-core kernels.
 constexpr int kStatusTimeout = 2;

@@ -204,6 +204,13 @@ void mlcc3_ctx::finish() {
   check_cuda(cudaStreamSynchronize(stream), "synchronize");
   check_cuda(cudaGetLastError(), "kernel launch");
   collect_events();
+  if (st & kStatusTimeout) {
+    // the call's results are incomplete: nothing it cached may be reused
+    check_cuda(cudaMemsetAsync(status, 0, sizeof(int), stream), "reset status");
+    tau_valid = false;
+    tau_key.clear();
+    throw Error{MLCC3_ERR_TIMEOUT, "a tensor-core pipeline wait timed out"};
+  }
   if (st & 1) {
     check_cuda(cudaMemsetAsync(status, 0, sizeof(int), stream), "reset status");
     throw Error{MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk} - omega| < 1e-3 in a triples block"};
@@ -359,6 +366,9 @@ std::vector<Ord> ords_of(const mlcc3_ctx *c, const std::vector<TripItem> &bs) {
   }
   return v;
 }
+
+// The skip rule applies when the context has a core mask and "cvs" is on.
+bool cvs_on(const mlcc3_ctx *c) { return !c->core.empty() && c->cvs; }
 
 bool has_core(const mlcc3_ctx *c, const TripItem &t) {
   return !c->core.empty() && (c->core[t.i] || c->core[t.j] || c->core[t.k]);
@@ -838,8 +848,10 @@ void tc_launch(mlcc3_ctx *c, const char *site, int BN, const TcMaps &maps, const
                const TcEpi &epi, double flops) {
   if (d.nitems == 0) return;
   const std::string name = std::string("tc_gemm_kernel:") + site;
+  TcEpi e = epi;
+  e.wait = c->tc_wait;
   c->launch(name.c_str(), flops, [&] {
-    check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, epi, c->status, c->stream,
+    check_cuda(launch_tc_gemm(BN, maps, d.items, d.segs, d.nitems, e, c->status, c->stream,
                               c->tc_persist_from),
                "tc_gemm");
   });
@@ -860,6 +872,7 @@ TcEpi make_epi(void *out, int mode, int R2, long long s1, long long s2, long lon
   e.nlim = (int)nlim;
   e.alpha = (float)alpha;
   e.qw = 0;
+  e.wait = 0;
   return e;
 }
 
@@ -1892,7 +1905,7 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
                               const double *R2_in, double *rho1_out, double *rho2_out,
                               const double *omega_dev = nullptr) {
   S s(c);
-  const bool cvs = !c->core.empty();
+  const bool cvs = cvs_on(c);
   const std::vector<Chunk> &chunks = cvs ? c->parts_cvs : c->parts;
   const double *R1all = c->in(R1_in, (size_t)n_vec * s.NV * s.NO, "R1");
   const double *R2all = c->in(R2_in, (size_t)n_vec * s.blk(), "R2");
@@ -1945,7 +1958,7 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
 static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const double *L1_in,
                              const double *L2_in, double *sig1_out, double *sig2_out) {
   S s(c);
-  const bool cvs = !c->core.empty();
+  const bool cvs = cvs_on(c);
   const std::vector<Chunk> &chunks = cvs ? c->parts_cvs : c->parts;
   const double *L1all = c->in(L1_in, (size_t)n_vec * s.NV * s.NO, "L1");
   const double *L2all = c->in(L2_in, (size_t)n_vec * s.blk(), "L2");
@@ -2412,7 +2425,7 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
                                   double *D0m_out) {
   S s(c);
   const long long nmo = s.nmo, NO = s.NO;
-  const bool cvs = !c->core.empty();
+  const bool cvs = cvs_on(c);
   const double *lam1 = c->in(lam1_in, s.NV * NO, "lam1");
   const double *lam2 = c->in(lam2_in, s.blk(), "lam2");
   const double *R1 = c->in(R1_in, s.NV * NO, "R1");
@@ -2730,8 +2743,13 @@ extern "C" int mlcc3_build_integrals(mlcc3_ctx *c, const double *chol, const dou
                                      const double *eps, const double *t2c, const double *t2x) {
   return guarded([&] {
     if (!c) throw Error{MLCC3_ERR_ARG, "null context"};
-    do_build_integrals(c, chol, t1, eps, t2c, t2x);
-    c->finish();
+    try {
+      do_build_integrals(c, chol, t1, eps, t2c, t2x);
+      c->finish();
+    } catch (...) {
+      c->built = false;  // the integral blocks may be incomplete
+      throw;
+    }
   });
 }
 
@@ -2844,6 +2862,15 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     } else if (n == "tc_persist_from") {
       if (value < 0) throw Error{MLCC3_ERR_ARG, "tc_persist_from must be >= 0"};
       c->tc_persist_from = (int)std::min<long long>(value, 1LL << 30);
+    } else if (n == "cvs") {
+      if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "cvs must be 0 or 1"};
+      if (value == 1 && c->core.empty())
+        throw Error{MLCC3_ERR_ARG, "cvs = 1 needs a context created with a core mask"};
+      c->cvs = value == 1;
+    } else if (n == "tc_wait_clocks") {
+      if (value < 0 || value > (1LL << 40))
+        throw Error{MLCC3_ERR_ARG, "tc_wait_clocks out of range 0..2^40"};
+      c->tc_wait = value;
     } else if (n == "bstc_fill") {
       if (value < 0 || value > 64) throw Error{MLCC3_ERR_ARG, "bstc_fill out of range 0..64"};
       c->bstc_fill = (int)value;

@@ -19,6 +19,7 @@
 namespace mlcc3 {
 void set_last_error(const std::string &msg);
 __global__ void bstc_kernel(BstcParams p);
+__global__ void bstc_gemv_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
 cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t);
@@ -44,6 +45,9 @@ int fail(int code, const std::string &msg) {
 
 // Device address of the scratch array on the current device (looked up once
 // per device; a host-side reference to g_static_scratch is only a stand-in).
+// The address is kept for the life of the process: a cudaDeviceReset while the
+// library is loaded reloads the module and leaves it stale, so that is not
+// supported.
 int scratch_address(int dev, void **out) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (dev < 0 || dev >= kMaxDevices) return fail(MLCC3_ERR_ARG, "device ordinal out of range");
@@ -105,6 +109,10 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
                     " bytes (2 n_batch n_v^3 + n_o n_v N_O N_V doubles plus index tables), "
                     "limit " + std::to_string(kStaticScratchBytes) + " bytes");
   if (!c->built) return fail(MLCC3_ERR_STATE, "mlcc3_build_integrals has not been called");
+  if (c->precision != MLCC3_FP64)
+    return fail(MLCC3_ERR_STATE,
+                "the allocation-free residual computes in FP64 only; the context is split precision "
+                "(its integral blocks and mlcc3_triples_omega are split precision too)");
   if (!on_device(omega1) || !on_device(omega2))
     return fail(MLCC3_ERR_ARG, "outputs must be device pointers (host staging would allocate)");
   int dev = -1;
@@ -171,11 +179,20 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
   const long long nt = (nv + 7) / 8;
   triples_build_kernel<<<dim3((unsigned)(nt * nt * nt), (unsigned)nb), 256, 0, st>>>(
       tt, dbatch, c->eps, (int)NO, (int)nv, 0.0, nullptr, tau, c->status);
-  if (!chk(launch_contra3(tau, taut, nb, (int)nv, st), "contra3")) return MLCC3_ERR_CUDA;
+  // an error after the first launch drains the stream before returning, so that
+  // no queued work of this call still writes the shared array afterwards
+  auto drained = [&]() {
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return MLCC3_ERR_CUDA;
+  };
+  if (!chk(cudaGetLastError(), "triples_build launch") ||
+      !chk(launch_contra3(tau, taut, nb, (int)nv, st), "contra3"))
+    return drained();
   // scratch keeps the previous call's contents: clear the accumulators
   if (!chk(cudaMemsetAsync(Zb, 0, sizeof(double) * blk, st), "memset Zb") ||
       !chk(cudaMemsetAsync(omega1, 0, sizeof(double) * NV * NO, st), "memset omega1"))
-    return MLCC3_ERR_CUDA;
+    return drained();
   // contravariant back-contraction (SI Omega terms) over every distinct ordering
   struct Launch {
     const double *B;
@@ -205,18 +222,21 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
     for (long long z0 = 0; z0 < nord; z0 += 65535) {
       bp.items = ditems + k * nord + z0;
       bp.nitems = (int)std::min<long long>(65535, nord - z0);
-      bstc_kernel<<<dim3((unsigned)tiles, (unsigned)bp.nitems), 256, 0, st>>>(bp);
+      if (N == 1)  // matrix-vector form (singles and F terms): a warp per output row
+        bstc_gemv_kernel<<<dim3((unsigned)((M + 7) / 8), (unsigned)bp.nitems), 256, 0, st>>>(bp);
+      else
+        bstc_kernel<<<dim3((unsigned)tiles, (unsigned)bp.nitems), 256, 0, st>>>(bp);
     }
   }
   const int g = (int)std::min<long long>((blk + 255) / 256, 152LL * 64);
   finalize_doubles_kernel<<<std::max(g, 1), 256, 0, st>>>(Zb, omega2, (int)no, (int)nv, (int)NO,
                                                           (int)NV, 0);
-  if (!chk(cudaGetLastError(), "launch")) return MLCC3_ERR_CUDA;
+  if (!chk(cudaGetLastError(), "launch")) return drained();
   int status = 0;
   if (!chk(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, st),
            "status") ||
       !chk(cudaStreamSynchronize(st), "synchronize"))
-    return MLCC3_ERR_CUDA;
+    return drained();
   if (status & 1) {
     cudaMemsetAsync(c->status, 0, sizeof(int), st);
     return fail(MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk}| < 1e-3 in a triples block");

@@ -22,7 +22,9 @@ the shapes below stand in for them:
 * t1 ~ N(0, 0.01^2);
 * t2 MP2-like, t^{AB}_{IJ} = (AI|BJ) / (eps_I + eps_J - eps_A - eps_B);
 * trial vectors R ~ N(0, 1) on unique elements, scaled to a singles weight
-  |R1|^2 = 0.95 and doubles weight |R2|^2 = 0.05 (singly excited states);
+  |R1|^2 = 0.95 and doubles weight |R2|^2 = 0.05 (singly excited states), or
+  (``singles_weight=None``) plain random vectors of unit norm, whose weight
+  then sits almost entirely in the doubles;
   L = R + 0.3 noise, then biorthonormalised against R;
 * lambda1 ~ N(0, 0.01^2), lambda2 = t2;  dipole integrals symmetric N(0, 0.1^2).
 
@@ -160,7 +162,8 @@ def cvs_project(d: Dims, core_mask, x1, x2):
     return x1, x2 * keep
 
 
-def make_states(sys: System, nstates=1, seed=DEFAULT_SEED, cvs_states=()) -> States:
+def make_states(sys: System, nstates=1, seed=DEFAULT_SEED, cvs_states=(),
+                singles_weight=0.95) -> States:
     d = sys.dims
     NO, NV, no, nv = d.n_occ, d.n_vir, d.n_act_occ, d.n_act_vir
     r = _rng(seed, 10)
@@ -178,11 +181,17 @@ def make_states(sys: System, nstates=1, seed=DEFAULT_SEED, cvs_states=()) -> Sta
             x1, x2 = cvs_project(d, sys.core_mask, x1, x2)
             omega[n] = 10.2
             cvs[n] = True
-        # singles-dominated, like the paper's valence and core states:
-        # |R1|^2 = 0.95, |R2|^2 = 0.05 under the unique-element norm
         n1 = np.sqrt(np.sum(x1 * x1))
         n2 = np.sqrt(sd_dot(d, 0 * x1, x2, 0 * x1, x2))
-        R1[n], R2[n] = np.sqrt(0.95) * x1 / n1, np.sqrt(0.05) * x2 / n2
+        if singles_weight is None:
+            # plain random: unit norm under the unique-element inner product
+            nn = np.sqrt(n1 * n1 + n2 * n2)
+            R1[n], R2[n] = x1 / nn, x2 / nn
+        else:
+            # singles-dominated, like the paper's valence and core states:
+            # |R1|^2 = w, |R2|^2 = 1 - w under the unique-element norm
+            w1 = float(singles_weight)
+            R1[n], R2[n] = np.sqrt(w1) * x1 / n1, np.sqrt(1.0 - w1) * x2 / n2
         y1 = R1[n] + 0.3 * r.normal(size=(NV, NO)) / np.sqrt(R1[n].size)
         y2 = R2[n] + symmetrize_block(d, 0.3 * r.normal(size=(no, nv, NO, NV))
                                       / np.sqrt(R2[n].size))

@@ -19,10 +19,12 @@ def rel_err(got, ref):
 class Case:
     """A seeded synthetic system with states, multipliers and dipoles."""
 
-    def __init__(self, NO, NV, no, nv, NJ, seed=synth.DEFAULT_SEED, nstates=2, core=False):
-        self.sys = synth.make_system(NO, NV, no, nv, NJ, seed=seed, core=core)
+    def __init__(self, NO, NV, no, nv, NJ, seed=synth.DEFAULT_SEED, nstates=2, core=False,
+                 t2_norm=None, singles_weight=0.95):
+        self.sys = synth.make_system(NO, NV, no, nv, NJ, seed=seed, core=core, t2_norm=t2_norm)
         self.st = synth.make_states(self.sys, nstates, seed=seed + 1,
-                                    cvs_states=tuple(range(nstates)) if core else ())
+                                    cvs_states=tuple(range(nstates)) if core else (),
+                                    singles_weight=singles_weight)
         self.lam1, self.lam2 = synth.make_multipliers(self.sys, seed=seed + 2)
         self.mu = synth.make_dipole(self.sys, seed=seed + 3)
         self.D00_in = synth.reference_density(self.sys)
@@ -99,3 +101,28 @@ def run_all(c, g):
     out["sig1"], out["sig2"] = c.host(sig1)[0], c.host(sig2)[0]
     out["D00"], out["Dm0"], out["D0m"] = map(c.host, D)
     return out
+
+
+def full_densities(c, D0m_T, Dm0_T, v=0):
+    """CCSD-level leading-order transition densities plus the triples parts
+    (D^{0-m}_{AI} += R^A_I, D^{m-0}_{IA} += L^A_I), as the oscillator strength
+    takes them."""
+    NO = c.sys.dims.n_occ
+    D0m, Dm0 = np.array(D0m_T, copy=True), np.array(Dm0_T, copy=True)
+    D0m[NO:, :NO] += c.st.R1[v]
+    Dm0[:NO, NO:] += c.st.L1[v].T
+    return D0m, Dm0
+
+
+def oracle_f(c, ref):
+    """The oracle's oscillator strength of state 0 from oracle_all's densities."""
+    o = c.oracle_ctx()
+    D0m, Dm0 = full_densities(c, ref["D0m"], ref["Dm0"])
+    return O.oscillator_strength(o, float(c.st.omega[0]), D0m, Dm0, c.mu)
+
+
+def library_f(c, g, got):
+    """The library's oscillator strength of state 0 from run_all's densities."""
+    D0m, Dm0 = full_densities(c, got["D0m"], got["Dm0"])
+    return g.oscillator_strength(float(c.st.omega[0]), c.to_dev(D0m), c.to_dev(Dm0),
+                                 c.to_dev(c.mu))

@@ -32,10 +32,10 @@ def _torch():
 class Full:
     """A full-size seeded system on the device (the bench's seeds)."""
 
-    def __init__(self, dims, seed=2022):
+    def __init__(self, dims, seed=2022, t2_norm=None):
         torch = _torch()
         self.dims = dims
-        self.s = synth.make_system(*dims, seed=seed)
+        self.s = synth.make_system(*dims, seed=seed, t2_norm=t2_norm)
         self.st = synth.make_states(self.s, 1, seed=seed + 1)
         self.lam1, self.lam2 = synth.make_multipliers(self.s, seed=seed + 2)
         self.mu = synth.make_dipole(self.s, seed=seed + 3)
@@ -129,6 +129,25 @@ def test_c2_split_against_fp64_path(c2):
         assert rel_err(c2.split[k], c2.fp64[k]) < 5e-5, k
     assert abs(c2.split["f"] - c2.fp64["f"]) < 5e-5 * abs(c2.fp64["f"])
     assert abs(c2.split["rq"] - c2.fp64["rq"]) < 1e-5  # Hartree
+
+
+def test_c2_molecule_scaled_f_and_excitation_energy():
+    """The accuracy target of the split path at the benchmark size, on the
+    molecule-scaled variant of the recipe (doubles norm 0.3, f of physical
+    size): |f_split - f_FP64| < 1e-6 and the excitation-energy Rayleigh
+    quotients within 1e-5 Hartree, both against the FP64 GPU path."""
+    f = Full(C2, t2_norm=0.3)
+    g = f.context(binding.MLCC3_SPLIT_BF16X3)
+    split = f.outputs(g)
+    g.close()
+    g = f.context(binding.MLCC3_FP64)
+    fp64 = f.outputs(g)
+    g.close()
+    assert 1e-4 < abs(fp64["f"]) < 10.0
+    assert abs(split["f"] - fp64["f"]) < 1e-6, (split["f"], fp64["f"])
+    assert abs(split["rq"] - fp64["rq"]) < 1e-5
+    for k in ("o1", "o2", "rho1", "rho2", "sig1", "sig2", "D00", "Dm0", "D0m"):
+        assert rel_err(split[k], fp64[k]) < 5e-5, k
 
 
 def test_c2_finite_differences_in_t2_fp64(c2):

@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from gpu_common import Case, rel_err
-from paper_2202_08612_gb300 import binding
+from paper_2202_08612_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -163,6 +163,45 @@ def test_cvs_core_state():
     s1, s2 = O.jacobian_left(o, w, st.L1[0], O.to_full(o, st.L2[0]))
     assert rel_err(c.host(sig1)[0], s1) < TOL
     assert rel_err(c.host(sig2)[0], O.from_full(o, s2)) < TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(binding.MLCC3_FP64, 1e-10),
+                                           (binding.MLCC3_SPLIT_BF16X3, 1e-4)])
+def test_cvs_toggle_valence_and_core_states_in_one_context(precision, tol):
+    """One context with a core mask serves both kinds of state: with "cvs" 0 a
+    valence state's rho, sigma and densities are those of a context without a
+    mask (every batch kept), with "cvs" 1 a core state's rho follows the skip
+    rule; both against the oracle."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    import copy
+    core = Case(NO=6, NV=22, no=4, nv=9, NJ=30, core=True, nstates=1)
+    val = copy.copy(core)
+    val.core = False
+    val.st = synth.make_states(core.sys, 1, seed=synth.DEFAULT_SEED + 5)
+    g = core.context(precision=precision)
+    g.set_param("cvs", 0)
+    ov = O.make_ctx(core.sys)
+    ov.core = np.zeros_like(ov.core)          # the oracle without the skip rule
+    val.oracle_ctx = lambda: ov
+    got, ref = run_all(val, g), oracle_all(val)
+    for k in ref:
+        assert rel_err(got[k], ref[k]) < tol, (k, rel_err(got[k], ref[k]))
+    g.set_param("cvs", 1)
+    st, o = core.st, core.oracle_ctx()
+    rho1, rho2 = core.empty_dev(st.R1.shape), core.empty_dev(st.R2.shape)
+    g.jacobian_right(st.omega, core.to_dev(st.R1), core.to_dev(st.R2), rho1, rho2)
+    r1, r2 = O.jacobian_right(o, float(st.omega[0]), st.R1[0], O.to_full(o, st.R2[0]))
+    assert rel_err(core.host(rho1)[0], r1) < tol
+    assert rel_err(core.host(rho2)[0], O.from_full(o, r2)) < tol
+    g.close()
+    plain = binding.Context(4, 10, 2, 3, 8)
+    with pytest.raises(binding.MLCC3Error) as e:
+        plain.set_param("cvs", 1)
+    assert e.value.code == -1
+    plain.close()
 
 
 def test_error_codes_on_gpu():

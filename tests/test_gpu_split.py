@@ -185,3 +185,40 @@ def test_split_wide_pair_tiles(bn):
     for k in ref:
         assert rel_err(out["wide"][k], out["default"][k]) < 1e-10, (bn, k)
         assert rel_err(out["wide"][k], ref[k]) < TOL, (bn, k, rel_err(out["wide"][k], ref[k]))
+
+
+@pytest.mark.parametrize("persist", [304, 0])
+def test_split_wait_timeout_is_reported_and_the_context_recovers(persist):
+    """Failure path of the tensor-core pipeline: with a progress-wait limit of
+    one clock the waits run out (nothing fills a stage that fast), the kernels
+    stop issuing, drain what they issued and return, and the call reports
+    MLCC3_ERR_TIMEOUT through the status word; with the default limit the same
+    context then gives the oracle's results again (its cached tau was
+    dropped).  persist 0: every launch in the persistent kernel form."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)
+    g, o, st = c.context(precision=binding.MLCC3_SPLIT_BF16X3), c.oracle_ctx(), c.st
+    g.set_param("tc_persist_from", persist)
+    NO, NV = o.NO, o.NV
+    o1, o2 = c.empty_dev((NV, NO)), c.empty_dev(c.sys.t2c.shape)
+    rho1, rho2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    g.set_param("tc_wait_clocks", 1)
+    with pytest.raises(binding.MLCC3Error) as e:
+        g.triples_omega(o1, o2)
+    assert e.value.code == -5
+    with pytest.raises(binding.MLCC3Error) as e:
+        g.jacobian_right(st.omega, c.to_dev(st.R1), c.to_dev(st.R2), rho1, rho2)
+    assert e.value.code == -5
+    torch.cuda.synchronize()
+    g.set_param("tc_wait_clocks", 0)
+    g.triples_omega(o1, o2)
+    g.jacobian_right(st.omega, c.to_dev(st.R1), c.to_dev(st.R2), rho1, rho2)
+    r1, r2 = O.triples_omega(o)
+    assert rel_err(c.host(o1), r1) < TOL
+    assert rel_err(c.host(o2), O.from_full(o, r2)) < TOL
+    w = float(st.omega[0])
+    p1, p2 = O.jacobian_right(o, w, st.R1[0], O.to_full(o, st.R2[0]))
+    assert rel_err(c.host(rho1)[0], p1) < TOL
+    assert rel_err(c.host(rho2)[0], O.from_full(o, p2)) < TOL

@@ -47,6 +47,24 @@ def test_static_matches_allocating_entry_point():
     g.close()
 
 
+def test_static_rejects_split_precision_contexts():
+    """The allocation-free residual computes in FP64; a split-precision context
+    (whose integral blocks are split precision too) is refused, and the context
+    stays usable for its own entry points."""
+    _cuda()
+    c = Case(NO=6, NV=24, no=4, nv=8, NJ=72)
+    g = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+    NO, NV = c.sys.dims.n_occ, c.sys.dims.n_vir
+    o1, o2 = c.empty_dev((NV, NO)), c.empty_dev(c.sys.t2c.shape)
+    with pytest.raises(binding.MLCC3Error) as e:
+        g.triples_omega_static(o1, o2)
+    assert e.value.code == -6
+    assert "FP64 only" in str(e.value)
+    g.triples_omega(o1, o2)
+    assert float(abs(o2).max()) > 0.0
+    g.close()
+
+
 def test_static_rejects_systems_beyond_the_limit():
     _cuda()
     ctx = binding.Context(12, 60, 12, 60, 1)    # 2 x 352 blocks of 60^3 doubles: > 32 MiB
