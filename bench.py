@@ -492,10 +492,13 @@ LARGE = {
 }
 
 
-def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core):
+def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core, t2_norm=None, cvs_last=0):
     """Seeded synthetic inputs of the large workloads, drawn on the device
     (torch Philox): the distributions of paper_2202_08612_gb300.synth, without
-    the host-side generation of a 10-40 GB Cholesky tensor."""
+    the host-side generation of a 10-40 GB Cholesky tensor.  t2_norm: the
+    molecule-scaled variant (Cholesky scale lowered so that the active doubles
+    block has norm at most t2_norm).  cvs_last: the last cvs_last vectors are
+    core states (elements without the core orbital 0 removed, omega 10.2 Ha)."""
     import torch
     g = torch.Generator(device=dev).manual_seed(seed)
     f64 = torch.float64
@@ -522,6 +525,13 @@ def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core):
     B = Lvo[:, :, :no].reshape(NJ, NV * no)                   # [J][D][i]
     t2x = (A @ B).reshape(nv, NO, NV, no).permute(3, 0, 1, 2).contiguous() / den  # t^{aD}_{Li}
     del A, B, Lvo
+    if t2_norm is not None:
+        nrm = float(t2c.pow(2).sum().sqrt())
+        if nrm > t2_norm:  # amplitudes are quadratic in the Cholesky scale
+            f = t2_norm / nrm
+            chol *= f ** 0.5
+            t2c *= f
+            t2x *= f
     R1 = N(nvec, NV, NO)
     R2 = N(nvec, no, nv, NO, NV)
     aa = R2[:, :, :, :no, :nv]
@@ -534,6 +544,15 @@ def device_system(NO, NV, no, nv, NJ, nvec, seed, dev, core):
     aa = L2[:, :, :, :no, :nv]
     L2[:, :, :, :no, :nv] = 0.5 * (aa + aa.permute(0, 3, 4, 1, 2))
     omega = (0.3 + 0.3 * torch.rand(nvec, dtype=f64, generator=torch.Generator().manual_seed(seed))).numpy()
+    for n in range(nvec - cvs_last, nvec):
+        # a core state: only elements that carry the core occupied orbital 0
+        for X1, X2 in ((R1, R2), (L1, L2)):
+            X1[n][:, 1:] = 0.0
+            keep = torch.zeros_like(X2[n], dtype=torch.bool)
+            keep[0] = True
+            keep[:, :, 0] = True
+            X2[n] *= keep
+        omega[n] = 10.2
     mu = N(3, nmo, nmo) * 0.1
     mu = 0.5 * (mu + mu.transpose(1, 2))
     D00 = torch.zeros((nmo, nmo), dtype=f64, device=dev)
@@ -556,7 +575,7 @@ def run_large(args):
     torch.cuda.set_device(dev)
     NO, NV, no, nv, NJ, nvec = LARGE[args.workload]
     core = args.workload == "betaine_like"
-    if args.stage in ("densities", "cvs"):
+    if args.stage in ("densities", "cvs", "ground"):
         nvec = 1
     x, omega = device_system(NO, NV, no, nv, NJ, nvec, 2022, dev, core)
     cvs = args.stage == "cvs"
@@ -590,7 +609,7 @@ def run_large(args):
                           core_mask=core_mask)
     # unique batches held per chunk: leaves room for the integral blocks, their
     # split copies and the per-call scratch next to the caller's tensors
-    if args.stage != "densities":
+    if args.stage not in ("densities", "ground"):
         ctx.set_param("chunk_blocks", args.chunk_blocks)
     if args.tc_group:
         ctx.set_param("tc_group", args.tc_group)
@@ -613,6 +632,9 @@ def run_large(args):
     if args.stage == "densities":
         return run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ,
                                    core, prec == binding.MLCC3_SPLIT_BF16X3)
+    if args.stage == "ground":
+        return run_large_ground(args, ctx, x, D, unit, ms_build, NO, NV, no, nv, NJ, core,
+                                prec == binding.MLCC3_SPLIT_BF16X3, rho1, rho2)
     ms_omega_first = timed(lambda: ctx.triples_omega(o1, o2))
     ms_omega = timed(lambda: ctx.triples_omega(o1, o2))
 
@@ -727,6 +749,64 @@ def run_nv_scaling(args):
                                                 "max_rel_residual": resid}}), flush=True)
 
 
+def run_large_ground(args, ctx, x, D, unit, ms_build, NO, NV, no, nv, NJ, core, split, eta1, eta2):
+    """The ground-state stages of a large system (the paper's lambda and D^{0-0}
+    rows): the multipliers' triples transformation (lambda^T A at omega = 0,
+    counted as sigma, 8 N_V n_v^3 n_o^3) and the ground-state density D^{0-0}
+    alone (10 N_V n_v^3 n_o^3), each timed after one untimed call."""
+    import torch
+    dev = x["R1"].device
+    stream = torch.cuda.current_stream(dev)
+    lam1, lam2 = x["lam1"], x["lam2"]
+    e1, e2 = eta1[0], eta2[0]
+
+    def timed(f):
+        e0, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        f()
+        e1_.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1_)
+    ctx.multiplier_transformation(lam1, lam2, e1, e2)
+    ctx.ground_density(lam1, lam2, D[0])
+    ctx.profile(True)
+    with ClockSampler(0) as clk:
+        ms_lam = statistics.median(timed(lambda: ctx.multiplier_transformation(lam1, lam2, e1, e2))
+                                   for _ in range(max(1, args.steps)))
+        ms_d00 = statistics.median(timed(lambda: ctx.ground_density(lam1, lam2, D[0]))
+                                   for _ in range(max(1, args.steps)))
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    pk = peaks().get("bf16_tflops_sustained") or 1700.0
+    tc = [v for k, v in stats.items() if k.startswith("tc_gemm")]
+    tc_ms, tc_fl = sum(v[1] for v in tc), sum(v[2] for v in tc)
+    alg = tc_fl / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    fl_lam, fl_d00 = FLOP_UNITS["sigma"] * unit, FLOP_UNITS["D_00"] * unit
+    line = {"metric": METRIC, "value": (fl_lam + fl_d00) / ((ms_lam + ms_d00) * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": ms_lam + ms_d00, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3" if split else "f64",
+            "data": "synthetic (device-generated, torch Philox)",
+            "config": {"workload": f"{args.workload}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}"
+                                   + (", core orbital at -10 Ha" if core else ""),
+                       "step": "multiplier transformation (lambda^T A at omega = 0) + D^{0-0}",
+                       "flop_units": "8 + 10 N_V n_v^3 n_o^3"},
+            "lambda": {"ms": ms_lam, "tflops": fl_lam / (ms_lam * 1e-3) / 1e12},
+            "D00": {"ms": ms_d00, "tflops": fl_d00 / (ms_d00 * 1e-3) / 1e12},
+            "build_integrals_ms": ms_build,
+            "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor",
+                         "achieved": 3.0 * alg if alg else None, "peak": pk, "unit": "TFLOP/s",
+                         "frac": 3.0 * alg / pk if alg else None, "achieved_algorithmic": alg,
+                         "share_of_step": tc_ms / (max(1, args.steps) * (ms_lam + ms_d00))},
+            "clocks": clk.summary(),
+            "call_sites": {k: round(v[1] / max(1, args.steps), 3) for k, v in
+                           sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
+            "tc_sites": tc_site_fracs(stats, max(1, args.steps), pk)}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, NJ, core, split):
     """The three transition densities and f of one state of a large system, in a
     process of their own: the densities hold every batch that touches a range of
@@ -780,14 +860,412 @@ def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, 
     ctx.close()
 
 
+# --------------------------------------------------------------------------------------
+# The largest configuration as the default step: one pass of the whole path over
+# a betaine-shaped system with a core orbital, two valence states and one core
+# (CVS) state.  name: (N_O, N_V, n_o, n_v, N_J, valence states, core states)
+WHOLE = {"betaine_like": (100, 1000, 20, 150, 4000, 2, 1)}
+
+
+def whole_step_flops(NO, NV, no, nv, nval, ncore):
+    """Algorithmic flops of one whole step (the paper's leading counts, Sec. 3):
+    Omega once, rho + sigma + D^{m-0} + D^{0-0} + D^{0-m} per valence state
+    (units N_V n_v^3 n_o^3); a core state's rho and sigma with the paper's CVS
+    count (8 N_V n_v^3 n_o^2 each), its D^{m-0} and D^{0-m}, which read the
+    CVS-restricted L3 and R3, reduced the same way (units N_V n_v^3 n_o^2),
+    and its D^{0-0}, which the skip rule does not touch, in full."""
+    F = FLOP_UNITS
+    u3, u2 = NV * nv ** 3 * no ** 3, NV * nv ** 3 * no ** 2
+    val = (F["rho"] + F["sigma"] + F["D_m0"] + F["D_00"] + F["D_0m"]) * u3
+    core = (F["rho"] + F["sigma"] + F["D_m0"] + F["D_0m"]) * u2 + F["D_00"] * u3
+    return F["omega"] * u3 + nval * val + ncore * core
+
+
+class WholeProblem:
+    """Inputs and outputs of the whole step; `x`/`o` hold device tensors or pinned
+    host tensors (the same call sequence either way)."""
+
+    def __init__(self, x, omega, nval, ncore):
+        self.x, self.omega, self.nval, self.ncore = x, omega, nval, ncore
+
+    @staticmethod
+    def outputs(x, nval, like):
+        z = lambda t: like(t)
+        NV, NO = x["R1"].shape[1], x["R1"].shape[2]
+        nmo = NO + NV
+        o = {"o1": z(x["R1"][0]), "o2": z(x["t2c"]),
+             "rho1": z(x["R1"][:nval]), "rho2": z(x["R2"][:nval]),
+             "sig1": z(x["R1"][:nval]), "sig2": z(x["R2"][:nval]),
+             "D": [z(x["mu"][0]) for _ in range(3)]}
+        assert o["D"][0].shape == (nmo, nmo)
+        return o
+
+    def step(self, ctx, x, o, tally=None):
+        """Integral build, Omega, then rho and sigma of the valence vectors (one
+        call each, skip rule off), the densities and f of each valence state,
+        and rho, sigma, densities and f of the core state (skip rule on)."""
+        nv_, w = self.nval, self.omega
+        t = tally if tally is not None else (lambda *a: None)
+        ctx.build_integrals(x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"])
+        t("in", x["chol"], x["t1"], x["eps"], x["t2c"], x["t2x"])
+        ctx.triples_omega(o["o1"], o["o2"])
+        t("out", o["o1"], o["o2"])
+        ctx.set_param("cvs", 0)
+        ctx.jacobian_right(w[:nv_], x["R1"][:nv_], x["R2"][:nv_], o["rho1"], o["rho2"])
+        ctx.jacobian_left(w[:nv_], x["L1"][:nv_], x["L2"][:nv_], o["sig1"], o["sig2"])
+        t("in", x["R1"][:nv_], x["R2"][:nv_], x["L1"][:nv_], x["L2"][:nv_])
+        t("out", o["rho1"], o["rho2"], o["sig1"], o["sig2"])
+        fs = []
+        for n in range(nv_ + self.ncore):
+            if n == nv_:
+                ctx.set_param("cvs", 1)
+                sl = slice(n, n + 1)
+                ctx.jacobian_right(w[sl], x["R1"][sl], x["R2"][sl], o["rho1"][:1], o["rho2"][:1])
+                ctx.jacobian_left(w[sl], x["L1"][sl], x["L2"][sl], o["sig1"][:1], o["sig2"][:1])
+                t("in", x["R1"][sl], x["R2"][sl], x["L1"][sl], x["L2"][sl])
+                t("out", o["rho1"][:1], o["rho2"][:1], o["sig1"][:1], o["sig2"][:1])
+            wn = float(w[n])
+            ctx.transition_density(wn, x["lam1"], x["lam2"], x["R1"][n], x["R2"][n], x["L1"][n],
+                                   x["L2"][n], x["D00_in"], *o["D"])
+            fs.append(ctx.oscillator_strength(wn, o["D"][2], o["D"][1], x["mu"]))
+            t("in", x["lam1"], x["lam2"], x["R1"][n], x["R2"][n], x["L1"][n], x["L2"][n],
+              x["D00_in"], x["mu"])
+            t("out", *o["D"])
+        ctx.set_param("cvs", 1)
+        return fs
+
+
+def whole_fp64_comparison(NO, NV, no_s, nv, NJ, nval, ncore, dev, stream):
+    """The plain FP64 GPU path against the split path where the FP64 step fits in
+    the bench: the workload's shape with the active occupied space cut to
+    no_s, molecule-scaled amplitudes (doubles norm 0.3, f of physical size), the
+    same state mix.  Reports f with the leading-order CCSD-level densities added,
+    the excitation-energy Rayleigh quotient (orbital-energy model of the
+    singles-doubles block), normwise errors of every output and both step times."""
+    import torch
+    from paper_2202_08612_gb300 import binding
+    x, omega = device_system(NO, NV, no_s, nv, NJ, nval + ncore, 4044, dev, True, t2_norm=0.3,
+                             cvs_last=ncore)
+    mask = np.zeros(NO, dtype=np.uint8)
+    mask[0] = 1
+    prob = WholeProblem(x, omega, nval, ncore)
+    res = {}
+    for name, prec in (("split", binding.MLCC3_SPLIT_BF16X3), ("fp64", binding.MLCC3_FP64)):
+        ctx = binding.Context(NO, NV, no_s, nv, NJ, precision=prec, stream=stream.cuda_stream,
+                              core_mask=mask)
+        o = WholeProblem.outputs(x, nval, torch.zeros_like)
+        prob.step(ctx, x, o)  # warm-up (plans, layouts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.step(ctx, x, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        # f of the last state computed (the core state) and of valence state 0 with the
+        # leading-order CCSD-level parts: D^{0-m}_{AI} += R^A_I, D^{m-0}_{IA} += L^A_I
+        fs = []
+        for n in (0, nval):
+            ctx.set_param("cvs", 1 if n >= nval else 0)
+            D = [torch.zeros_like(d) for d in o["D"]]
+            ctx.transition_density(float(omega[n]), x["lam1"], x["lam2"], x["R1"][n], x["R2"][n],
+                                   x["L1"][n], x["L2"][n], x["D00_in"], *D)
+            D[2][NO:, :NO] += x["R1"][n]
+            D[1][:NO, NO:] += x["L1"][n].T
+            fs.append(ctx.oscillator_strength(float(omega[n]), D[2], D[1], x["mu"]))
+        ctx.set_param("cvs", 0)
+        e = x["eps"]
+        d1 = e[NO:, None] - e[None, :NO]
+        d2 = (e[NO:NO + nv][None, :, None, None] + e[NO:][None, None, None, :]
+              - e[:no_s, None, None, None] - e[None, None, :NO, None])
+        from paper_2202_08612_gb300 import synth
+        w_ = torch.from_numpy(synth.block_weights(synth.Dims(NO, NV, no_s, nv, NJ))).to(dev)
+        sd = float((x["L1"][0] * d1 * x["R1"][0]).sum() + (w_ * x["L2"][0] * d2 * x["R2"][0]).sum())
+        rq = ctx.rayleigh_quotient(float(omega[0]), x["R1"][0], x["R2"][0], x["L1"][0], x["L2"][0], sd)
+        res[name] = {"ms": e0.elapsed_time(e1), "f": fs, "rq": rq,
+                     "out": {k: (v.cpu().numpy() if not isinstance(v, list) else [d.cpu().numpy() for d in v])
+                             for k, v in o.items()}}
+        ctx.close()
+        del o
+        torch.cuda.empty_cache()
+    a, b = res["split"], res["fp64"]
+
+    def nrm(u, v):
+        return float(np.abs(u - v).max() / max(np.abs(v).max(), 1e-300))
+    errs = {k: nrm(a["out"][k], b["out"][k]) for k in ("o1", "o2", "rho1", "rho2", "sig1", "sig2")}
+    for i, k in enumerate(("D00", "Dm0", "D0m")):
+        errs[k] = nrm(a["out"]["D"][i], b["out"]["D"][i])
+    del x
+    torch.cuda.empty_cache()
+    return {"subset": f"N_O={NO} N_V={NV} n_o={no_s} n_v={nv} N_J={NJ} (the workload with the active "
+                      f"occupied space cut to {no_s}), molecule-scaled amplitudes (doubles norm 0.3), "
+                      f"{nval} valence + {ncore} core state(s)",
+            "ms_per_step": {"split": a["ms"], "fp64": b["ms"]},
+            "speedup_of_split": b["ms"] / a["ms"],
+            "f": {"split": a["f"], "fp64": b["f"],
+                  "abs_diff": max(abs(u - v) for u, v in zip(a["f"], b["f"]))},
+            "omega_rq": {"split": a["rq"], "fp64": b["rq"], "abs_diff_hartree": abs(a["rq"] - b["rq"])},
+            "normwise_rel_err": errs}
+
+
+def host_chol_rows(NO, NV, no, nv, NJ, seed):
+    """The recipe's Cholesky vectors on the rows the oracle's residual sample
+    reads (occupied and active virtual orbitals, all columns), drawn on the host
+    (torch CPU generator): symmetric on the held square block, N(0, 0.05^2)."""
+    import torch
+    g = torch.Generator().manual_seed(seed)
+    nmo = NO + NV
+    rows = np.concatenate([np.arange(NO), NO + np.arange(nv)])
+    data = torch.randn((NJ, len(rows), nmo), dtype=torch.float64, generator=g) * 0.05
+    sq = data[:, :, rows]
+    data[:, :, rows] = (sq + sq.transpose(1, 2)) * (0.5 ** 0.5)
+    return rows, data.numpy()
+
+
+def oracle_residual_sample(NO, NV, no, nv, NJ, rows, data, eps, t1, t2c, t2x, reps, core=True):
+    """The oracle's batched form on a bounded sample of the whole step: the
+    ground-state residual stage (tau3 blocks of every ordering, contravariant
+    form, back-contraction) of one unique batch i > j > k, `reps` times.  The
+    integral blocks it reads are built first and are not timed.  Returns
+    (TFLOP/s of the paper's Omega count for the batch's six orderings, seconds
+    per repetition, sample text)."""
+    from oracle import batched as B
+    cr = B.CholRows(rows, data)
+    mask = np.zeros(NO, dtype=np.uint8)
+    if core:
+        mask[0] = 1
+    b = B.BCtx(NO, NV, no, nv, eps, cr, t1, t2c, t2x, mask)
+    for n in ("vVvo", "Oovo", "ovov", "oOov", "Vvov", "ovOV", "oVOv"):
+        b.gn(n)
+    S = [(no - 1, no // 2, 1)]
+    dts = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        B.triples_omega(b, S)
+        dts.append(time.perf_counter() - t)
+    dt = statistics.median(dts)
+    fl = FLOP_UNITS["omega"] * NV * nv ** 3 * B.n_ordered(S)
+    return fl / dt / 1e12, dt, (f"oracle (batched form) ground-state residual stage of one unique "
+                                f"batch {S[0]} (its 6 orderings) of the workload, counted with the "
+                                f"paper's Omega flops for those orderings; integral blocks built "
+                                f"beforehand, untimed")
+
+
+def run_whole(args, rank, world, local_rank):
+    import torch
+    from paper_2202_08612_gb300 import binding, build
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    NO, NV, no, nv, NJ, nval, ncore = WHOLE[args.workload]
+    stream = torch.cuda.current_stream(dev)
+    x, omega = device_system(NO, NV, no, nv, NJ, nval + ncore, 2022 + 17 * rank, dev, True,
+                             cvs_last=ncore)
+    mask = np.zeros(NO, dtype=np.uint8)
+    mask[0] = 1
+    fl = whole_step_flops(NO, NV, no, nv, nval, ncore)
+    # the oracle sample's Cholesky rows, before the device memory fills up
+    rows = np.concatenate([np.arange(NO), NO + np.arange(nv)])
+    oracle_in = None
+    if rank == 0 and not args.no_cpu_baseline:
+        oracle_in = {"rows": rows, "data": x["chol"][:, torch.from_numpy(rows).to(dev), :].cpu().numpy(),
+                     **{k: x[k].cpu().numpy() for k in ("eps", "t1", "t2c", "t2x")}}
+    prob = WholeProblem(x, omega, nval, ncore)
+    o = WholeProblem.outputs(x, nval, torch.zeros_like)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    ctx = binding.Context(NO, NV, no, nv, NJ, precision=binding.MLCC3_SPLIT_BF16X3,
+                          stream=stream.cuda_stream, core_mask=mask)
+    ctx.set_param("chunk_blocks", args.chunk_blocks)
+    dist = world > 1
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(device=dev)
+
+    for _ in range(args.warmup):
+        f_ours = prob.step(ctx, x, o)
+    ctx.profile(True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            f_ours = prob.step(ctx, x, o)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    hbm_used = (lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info(dev))
+    ms, value = job_throughput(ms_total, args.steps, fl, world, dev if dist else None)
+    # one Davidson iteration of the step on its own: rho and sigma of the valence vectors
+    ctx.set_param("cvs", 0)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e2.record(stream)
+    ctx.jacobian_right(omega[:nval], x["R1"][:nval], x["R2"][:nval], o["rho1"], o["rho2"])
+    ctx.jacobian_left(omega[:nval], x["L1"][:nval], x["L2"][:nval], o["sig1"], o["sig2"])
+    e3.record(stream)
+    barrier()
+    s_iter = e2.elapsed_time(e3) * 1e-3
+    ctx.set_param("cvs", 1)
+
+    # end to end through the C ABI with pinned host buffers: every step copies its
+    # inputs in and its outputs out inside the timed region
+    xh = {k: v.cpu().pin_memory() for k, v in x.items()}
+    del x, o
+    prob.x = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    oh = WholeProblem.outputs(xh, nval, lambda t: torch.zeros_like(t).pin_memory())
+    tally = {"in": 0, "out": 0}
+
+    def count(kind, *arrs):
+        tally[kind] += sum(a.numel() * a.element_size() for a in arrs)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    prob.step(ctx, xh, oh)            # host staging buffers exist from here on
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        prob.step(ctx, xh, oh, tally=count)
+    torch.cuda.synchronize(device=dev)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    e2e = {"value": fl * world / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": tally["in"] // e2e_steps,
+           "d2h_bytes_per_step": tally["out"] // e2e_steps + 8 * (nval + ncore),
+           "steps": e2e_steps, "host_buffers": "pinned"}
+    ctx.close()
+    del xh, oh
+    torch.cuda.empty_cache()
+
+    # dominant kernel of the timed region
+    agg = {}
+    for k, (nl, kms_, kfl_) in stats.items():
+        a = agg.setdefault(k.split(":")[0], [0, 0.0, 0.0])
+        a[0] += nl
+        a[1] += kms_
+        a[2] += kfl_
+    name, (launches, kms, kfl) = max(agg.items(), key=lambda kv: kv[1][1])
+    alg = kfl / (kms * 1e-3) / 1e12 if kms > 0 else None
+    pk = peaks().get("bf16_tflops_sustained") or 1700.0
+    roofline = {"kernel": name, "bound": "tensor", "achieved": 3.0 * alg if alg else None, "peak": pk,
+                "unit": "TFLOP/s", "frac": 3.0 * alg / pk if alg else None,
+                "traffic": traffic_for(name), "achieved_algorithmic": alg,
+                "launches_per_step": launches / args.steps, "share_of_step": kms / ms_total,
+                "peak_note": "measured sustained dense BF16 (MEASURED_PEAKS.json); achieved "
+                             "counts the 3 BF16 products (hi*hi, hi*lo, lo*hi) per product; "
+                             "flops are the kernel's own products (launch accounting)"}
+    gpu_launches = sum(v[0] for v in stats.values())
+
+    fp64 = None
+    if rank == 0 and not args.no_fp64_compare:
+        fp64 = whole_fp64_comparison(NO, NV, 4, nv, NJ, nval, ncore, dev, stream)
+
+    if rank == 0:
+        cpu = None
+        if oracle_in is not None:
+            v, dt, sample = oracle_residual_sample(NO, NV, no, nv, NJ, oracle_in["rows"],
+                                                   oracle_in["data"], oracle_in["eps"],
+                                                   oracle_in["t1"], oracle_in["t2c"],
+                                                   oracle_in["t2x"], reps=1)
+            cpu = {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": sample, "seconds": dt}
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x3", "data": "synthetic (device-generated, torch Philox)",
+                "config": {"workload": f"{args.workload}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}, "
+                                       f"core orbital at -10 Ha, {nval} valence + {ncore} core (CVS) "
+                                       "state(s)",
+                           "step": "integral build, Omega, rho and sigma of the valence vectors, "
+                                   "D^{0-0}, D^{m-0}, D^{0-m} and f of each valence state, rho, sigma, "
+                                   "densities and f of the core state",
+                           "flop_count": "Omega 4 + 52 per valence state (N_V n_v^3 n_o^3); per "
+                                         "core state 42 N_V n_v^3 n_o^2 + 10 N_V n_v^3 n_o^3 "
+                                         "(whole_step_flops)",
+                           "algorithmic_flop_per_step": fl,
+                           "precision": "split bf16x3 / fp32 accumulate / fp64 denominators and reductions",
+                           "parallelism": f"replicas x{world} (independent systems)",
+                           "chunk_blocks": args.chunk_blocks,
+                           "l2": "inputs larger than L2 (Cholesky vectors "
+                                 f"{NJ * (NO + NV) ** 2 * 8 / 2**30:.1f} GiB)"},
+                "s_per_davidson_iter": s_iter, "fp64_gpu_path": fp64, "f": f_ours,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": gpu_launches, "hbm_used_gb": hbm_used,
+                "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},
+                "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
+                               sorted(stats.items(), key=lambda kv: -kv[1][1])[:24]},
+                "tc_sites": tc_site_fracs(stats, args.steps, pk)}
+        print(json.dumps(line), flush=True)
+
+
+def run_reference_whole(args, rank):
+    """The oracle's arm for the whole-step workload: inputs of the workload's shape
+    drawn on the host (the rows of the Cholesky vectors the sample reads), the
+    integral blocks built once, then `--warmup` + `--steps` samples of the
+    ground-state residual stage of one unique batch; the timed samples give the
+    value."""
+    if rank != 0:
+        return
+    import torch
+    from oracle import batched as B
+    NO, NV, no, nv, NJ, nval, ncore = WHOLE[args.workload]
+    rows, data = host_chol_rows(NO, NV, no, nv, NJ, 5151)
+    g = torch.Generator().manual_seed(5152)
+    eps = torch.cat([-1.5 + 1.2 * torch.rand(NO, dtype=torch.float64, generator=g),
+                     0.1 + 2.9 * torch.rand(NV, dtype=torch.float64, generator=g)]).numpy()
+    eps[0] = -10.0
+    t1 = (0.01 * torch.randn(NV, NO, dtype=torch.float64, generator=g)).numpy()
+    # MP2-like doubles from the bare integrals: Lov[J][L][D] = L^J_{L, N_O + D}
+    Lov = data[:, :NO, NO:]
+    eo, ev = eps[:NO], eps[NO:]
+    den = (eo[:no, None, None, None] + eo[None, None, :, None]
+           - ev[None, :nv, None, None] - ev[None, None, None, :])
+    J = data.shape[0]
+    A = Lov[:, :no, :nv].transpose(1, 2, 0).reshape(no * nv, J)
+    t2c = (A @ Lov.reshape(J, NO * NV)).reshape(no, nv, NO, NV) / den       # (ai|DL) / D
+    t2x = np.einsum('JLa,JiD->iaLD', Lov[:, :, :nv], Lov[:, :no, :], optimize=True) / den  # (aL|Di) / D
+    mask = np.zeros(NO, dtype=np.uint8)
+    mask[0] = 1
+    b = B.BCtx(NO, NV, no, nv, eps, B.CholRows(rows, data), t1, t2c, t2x, mask)
+    for n in ("vVvo", "Oovo", "ovov", "oOov", "Vvov", "ovOV", "oVOv"):
+        b.gn(n)
+    S = [(no - 1, no // 2, 1)]
+    fl = FLOP_UNITS["omega"] * NV * nv ** 3 * B.n_ordered(S)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        B.triples_omega(b, S)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            vals.append(dt)
+    dt = statistics.mean(vals)
+    value = fl / dt / 1e12
+    sample = (f"oracle (batched form) ground-state residual stage of one unique batch {S[0]} "
+              f"(its 6 orderings) of the workload per step, counted with the paper's Omega flops "
+              f"for those orderings; inputs drawn on the host, integral blocks built once, untimed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N_O={NO} N_V={NV} n_o={no} n_v={nv} N_J={NJ}, "
+                                   f"core orbital at -10 Ha, {nval} valence + {ncore} core (CVS) state(s)"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="guanine_like_small",
-                    choices=sorted(WORKLOADS) + ["uneven_sweep", "nv_scaling"] + sorted(LARGE))
+    ap.add_argument("--workload", default="betaine_like",
+                    choices=sorted(set(WORKLOADS) | set(WHOLE) | set(LARGE)) + ["uneven_sweep", "nv_scaling"])
     ap.add_argument("--vectors", type=int, default=4,
                     help="trial vectors per system of the uneven_sweep workload")
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
@@ -798,10 +1276,15 @@ def main():
                          "(128, 160 or 256; 0: the library default)")
     ap.add_argument("--chunk-blocks", type=int, default=128,
                     help="large workloads: unique batches held per chunk")
-    ap.add_argument("--stage", default="davidson", choices=("davidson", "densities", "cvs"),
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="whole-step workload: steps of the end-to-end (pinned host buffers) run")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle sample of the whole-step workload")
+    ap.add_argument("--stage", default=None, choices=("davidson", "densities", "cvs", "ground"),
                     help="large workloads: Davidson iterations (rho, sigma) of the valence "
-                         "vectors, the densities and f of one state, or the Davidson iteration "
-                         "of one core (CVS) state")
+                         "vectors, the densities and f of one state, the Davidson iteration "
+                         "of one core (CVS) state, or the ground-state stages (multiplier "
+                         "transformation and D^{0-0})")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the untimed FP64-path comparison step")
     args = ap.parse_args()
@@ -815,8 +1298,14 @@ def main():
         run_sweep(args)
     elif args.impl == "ours" and args.workload == "nv_scaling":
         run_nv_scaling(args)
-    elif args.impl == "ours" and args.workload in LARGE:
+    elif args.impl == "ours" and args.workload in LARGE and (args.stage is not None
+                                                             or args.workload not in WHOLE):
+        args.stage = args.stage or "davidson"
         run_large(args)
+    elif args.impl == "ours" and args.workload in WHOLE:
+        run_whole(args, rank, world, local_rank)
+    elif args.impl == "reference" and args.workload in WHOLE and args.stage is None:
+        run_reference_whole(args, rank)
     elif args.impl == "reference":
         run_reference(args, rank)
     else:

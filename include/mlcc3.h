@@ -19,7 +19,10 @@
  * Arrays: C row-major, IEEE double, dense.  Every array argument may be a
  *   device pointer or a host pointer (detected per call with
  *   cudaPointerGetAttributes); host arrays are staged through buffers the
- *   context owns.  The caller keeps ownership of all arrays.
+ *   context owns, except the Cholesky vectors of mlcc3_build_integrals, which
+ *   are copied straight into the context's own transformed copy from device,
+ *   pinned or pageable memory (no staging buffer of the largest input).  The
+ *   caller keeps ownership of all arrays.
  * Singles: X[A][I] = X^A_I, shape [N_V][N_O].
  * Doubles: the active-pair block X[i][a][L][D] = X^{aD}_{iL}, shape
  *   [n_o][n_v][N_O][N_V] (the paper's N_V N_O n_v n_o sub-block, Sec. 3).
@@ -126,6 +129,21 @@ int mlcc3_transition_density(mlcc3_ctx *ctx, double omega, const double *lam1,
                              const double *lam2, const double *R1, const double *R2,
                              const double *L1, const double *L2, const double *D00_in,
                              double *D00_T, double *Dm0_T, double *D0m_T);
+
+/* Ground-state multipliers (Sec. 2: the lambda equations lambda^T A(0) = -eta,
+ * eta without a triples part): the triples part of lambda^T A at omega = 0,
+ * i.e. mlcc3_jacobian_left of the one vector (lam1, lam2) at omega = 0, the
+ * skip rule of a core mask off (the ground state is not core-valence
+ * separated).  lam1 [N_V][N_O], lam2 [n_o][n_v][N_O][N_V]; eta1, eta2 the same
+ * shapes, overwritten. */
+int mlcc3_multiplier_transformation(mlcc3_ctx *ctx, const double *lam1, const double *lam2,
+                                    double *eta1, double *eta2);
+
+/* Triples part of the ground-state density D^{0-0} alone (SI: the D^{m-0}
+ * blocks kl, ld, LD, cd with lambda3, the L3 formula at omega = 0 on the
+ * multipliers, in place of L3), without the transition densities of a state.
+ * lam1, lam2 as above; D00_T [n_mo][n_mo], overwritten. */
+int mlcc3_ground_density(mlcc3_ctx *ctx, const double *lam1, const double *lam2, double *D00_T);
 
 /* Excitation-energy Rayleigh quotient of one state (Sec. 2: the CC3
  * excitation energies are eigenvalues of the omega-dependent Jacobian A(omega);

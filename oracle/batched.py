@@ -31,7 +31,7 @@ import itertools
 
 import numpy as np
 
-__all__ = ["BCtx", "make_bctx", "unique_batches", "orbit", "n_ordered",
+__all__ = ["BCtx", "CholRows", "make_bctx", "unique_batches", "orbit", "n_ordered",
            "triples_omega", "jacobian_right", "jacobian_left", "transition_densities",
            "oscillator_strength", "finish_doubles"]
 
@@ -63,9 +63,29 @@ def n_ordered(batches):
     return len(orbit(batches))
 
 
+class CholRows:
+    """Bare Cholesky vectors held on a subset R of the rows (all columns),
+    data[J][r][q] = L^J_{R[r] q}.  By the symmetry L^J_pq = L^J_qp a block
+    (P, Q) is read from the rows P, or transposed from the rows Q."""
+
+    def __init__(self, rows, data):
+        self.rows = np.asarray(rows)
+        self.pos = {int(r): n for n, r in enumerate(self.rows)}
+        self.data = data
+        self.shape = (data.shape[0], data.shape[2], data.shape[2])
+
+    def block(self, P, Q):
+        if all(int(p) in self.pos for p in P):
+            return self.data[:, [self.pos[int(p)] for p in P]][:, :, Q]
+        if all(int(q) in self.pos for q in Q):
+            return self.data[:, [self.pos[int(q)] for q in Q]][:, :, P].transpose(0, 2, 1)
+        raise KeyError("Cholesky block outside the held rows")
+
+
 class BCtx:
     """Sizes, orbital energies, bare Cholesky vectors and amplitudes; integral
-    blocks of the T1-transformed Cholesky vectors built on demand."""
+    blocks of the T1-transformed Cholesky vectors built on demand.  `chol` is
+    the full array [N_J][n_mo][n_mo] or a CholRows holding the rows it needs."""
 
     def __init__(self, NO, NV, no, nv, eps, chol, t1, t2c, t2x, core_mask=None):
         self.NO, self.NV, self.no, self.nv = NO, NV, no, nv
@@ -96,17 +116,22 @@ class BCtx:
         (P, Q), (occ, Q), (P, vir) and (occ, vir) only."""
         key = (P.tobytes(), Q.tobytes())
         if key not in self._L:
-            L, t, o, v = self.chol, self.t, self.occ, self.vir
+            t, o, v = self.t, self.occ, self.vir
             tP, tQ = t[P][:, o], t[v][:, Q]     # zero when P has no virtual / Q no occupied
-            out = L[:, P][:, :, Q].copy()
+            out = np.array(self._bare(P, Q), copy=True)
             if tP.any():
-                out -= _es('pr,Jrq->Jpq', tP, L[:, o][:, :, Q])
+                out -= _es('pr,Jrq->Jpq', tP, self._bare(o, Q))
             if tQ.any():
-                out += _es('Jpr,rq->Jpq', L[:, P][:, :, v], tQ)
+                out += _es('Jpr,rq->Jpq', self._bare(P, v), tQ)
             if tP.any() and tQ.any():
-                out -= _es('pr,Jrs,sq->Jpq', tP, L[:, o][:, :, v], tQ)
+                out -= _es('pr,Jrs,sq->Jpq', tP, self._bare(o, v), tQ)
             self._L[key] = out
         return self._L[key]
+
+    def _bare(self, P, Q):
+        if isinstance(self.chol, CholRows):
+            return self.chol.block(P, Q)
+        return self.chol[:, P][:, :, Q]
 
     def gn(self, name):
         """(PQ|RS) = sum_J Lt^J_PQ Lt^J_RS (Mulliken order, SI "Cholesky") on the
@@ -114,7 +139,11 @@ class BCtx:
         if name not in self._g:
             sets = {"o": self.aocc, "O": self.occ, "v": self.avir, "V": self.vir}
             P, Q, R, S = (sets[c] for c in name)
-            self._g[name] = _es('Jpq,Jrs->pqrs', self.Lt(P, Q), self.Lt(R, S))
+            A, B = self.Lt(P, Q), self.Lt(R, S)
+            # sum over J as one matrix product (pq) x (rs)
+            J = A.shape[0]
+            self._g[name] = (A.reshape(J, -1).T @ B.reshape(J, -1)).reshape(
+                len(P), len(Q), len(R), len(S))
         return self._g[name]
 
     def fock_ov(self, x1):

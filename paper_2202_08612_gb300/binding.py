@@ -28,7 +28,8 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_debug_nbatches", "mlcc3_debug_profile", "mlcc3_debug_kernel_stats",
            "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param",
            "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
-           "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient")
+           "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient", "mlcc3_ground_density",
+           "mlcc3_multiplier_transformation")
 
 
 class MLCC3Error(RuntimeError):
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_sweep_destroy.argtypes = [P]
     lib.mlcc3_sweep_destroy.restype = None
     lib.mlcc3_rayleigh_quotient.argtypes = [P, D, P, P, P, P, D, P]
+    lib.mlcc3_ground_density.argtypes = [P, P, P, P]
+    lib.mlcc3_multiplier_transformation.argtypes = [P, P, P, P, P]
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -171,6 +174,15 @@ class Context:
         self._check(self.lib.mlcc3_transition_density(
             self.h, float(omega), _ptr(lam1), _ptr(lam2), _ptr(R1), _ptr(R2), _ptr(L1), _ptr(L2),
             _ptr(D00_in), _ptr(D00_T), _ptr(Dm0_T), _ptr(D0m_T)))
+
+    def ground_density(self, lam1, lam2, D00_T):
+        """Triples part of D^{0-0} alone (mlcc3_ground_density)."""
+        self._check(self.lib.mlcc3_ground_density(self.h, _ptr(lam1), _ptr(lam2), _ptr(D00_T)))
+
+    def multiplier_transformation(self, lam1, lam2, eta1, eta2):
+        """Triples part of lambda^T A at omega = 0 (mlcc3_multiplier_transformation)."""
+        self._check(self.lib.mlcc3_multiplier_transformation(self.h, _ptr(lam1), _ptr(lam2),
+                                                             _ptr(eta1), _ptr(eta2)))
 
     def oscillator_strength(self, omega, D0m, Dm0, mu) -> float:
         f = ctypes.c_double()

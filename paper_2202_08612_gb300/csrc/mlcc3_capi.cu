@@ -1816,7 +1816,7 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
                                const double *eps_in, const double *t2c_in, const double *t2x_in) {
   S s(c);
   const long long nmo = s.nmo, NO = s.NO;
-  const double *chol = c->in(chol_in, s.NJ * s.lJ, "chol");
+  if (chol_in == nullptr) throw Error{MLCC3_ERR_ARG, "null input array: chol"};
   check_cuda(cudaMemcpyAsync(c->eps, c->in(eps_in, nmo, "eps"), nmo * sizeof(double),
                              cudaMemcpyDeviceToDevice, c->stream), "eps");
   check_cuda(cudaMemcpyAsync(c->t1, c->in(t1_in, s.NV * NO, "t1"), s.NV * NO * sizeof(double),
@@ -1827,11 +1827,15 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
                              cudaMemcpyDeviceToDevice, c->stream), "t2x");
   // Lt = (1 - t1) L (1 + t1) (Sec. 2, T1-transformed Hamiltonian):
   // X = L + L t (occupied columns), then Lt[NO+A][q] = X[NO+A][q] - sum_I t[A][I] X[I][q].
-  check_cuda(cudaMemcpyAsync(c->Lt, chol, s.NJ * s.lJ * sizeof(double), cudaMemcpyDeviceToDevice,
+  // The Cholesky vectors are copied straight into Lt from wherever they live
+  // (device, pinned host memory over the C2C link, or pageable host memory):
+  // no staging buffer of the largest input.  The first pass reads the virtual
+  // columns of the copy and writes its occupied columns (disjoint).
+  check_cuda(cudaMemcpyAsync(c->Lt, chol_in, s.NJ * s.lJ * sizeof(double), cudaMemcpyDefault,
                              c->stream), "Lt copy");
   Shape sh;
   sh.M1 = s.NJ; sh.M2 = nmo; sh.N1 = NO; sh.K1 = s.NV;
-  c->bstc1(chol + NO, c->t1, c->Lt, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.lJ, nmo, 1, 0}), "t1a");
+  c->bstc1(c->Lt + NO, c->t1, c->Lt, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.lJ, nmo, 1, 0}), "t1a");
   sh = Shape{};
   sh.M1 = s.NV; sh.N1 = s.NJ; sh.N2 = nmo; sh.K1 = NO;
   c->bstc1(c->t1, c->Lt, c->Lt + NO * nmo, sh, -1.0, mk_item(0, 0, 0, {NO, 0, 1, 0, 0}, {nmo, 0, 0, s.lJ, 1}, {nmo, 0, s.lJ, 1}), "t1b");
@@ -2639,6 +2643,35 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
   });
 }
 
+// Ground-state density D^{0-0} alone (SI: D^{m-0} with the multipliers and
+// omega = 0): tau, lambda3 and the kl, ld, LD and cd blocks, by occupied-index
+// ranges like the transition densities.
+static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double *lam2_in,
+                              double *D00_out) {
+  S s(c);
+  const long long nmo = s.nmo, NO = s.NO;
+  const double *lam1 = c->in(lam1_in, s.NV * NO, "lam1");
+  const double *lam2 = c->in(lam2_in, s.blk(), "lam2");
+  double *D00 = c->out(D00_out, nmo * nmo, "D00");
+  c->zero(D00, nmo * nmo);
+  double *lc = c->buf("lamc", s.blk());
+  double *lcT = c->buf("lamcT", s.no * s.nv * s.nv * NO);
+  launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
+    c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
+  });
+  transpose_tl(c, lc, lcT);
+  for (const Chunk &ch : c->groups) {
+    const long long bw = ch.nb * s.nv3;
+    double *tau, *taut;
+    build_tau(c, ch, &tau, &taut);
+    double *lam3 = c->buf("lam3", bw);
+    double *lt3 = c->buf("lam3t", bw);
+    left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3);
+    contra3(c, lam3, lt3, ch.nb);
+    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -2793,6 +2826,35 @@ extern "C" int mlcc3_transition_density(mlcc3_ctx *c, double omega, const double
     require_built(c);
     do_transition_density(c, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T);
     c->finish();
+  });
+}
+
+extern "C" int mlcc3_ground_density(mlcc3_ctx *c, const double *lam1, const double *lam2,
+                                    double *D00) {
+  return guarded([&] {
+    require_built(c);
+    do_ground_density(c, lam1, lam2, D00);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_multiplier_transformation(mlcc3_ctx *c, const double *lam1,
+                                               const double *lam2, double *eta1, double *eta2) {
+  return guarded([&] {
+    require_built(c);
+    const double zero = 0.0;
+    // the multipliers' triples terms are the transpose Jacobian at omega = 0;
+    // the skip rule of a core mask does not apply to the ground state
+    const bool cvs = c->cvs;
+    c->cvs = false;
+    try {
+      do_jacobian_left(c, 1, &zero, lam1, lam2, eta1, eta2);
+      c->finish();
+    } catch (...) {
+      c->cvs = cvs;
+      throw;
+    }
+    c->cvs = cvs;
   });
 }
 

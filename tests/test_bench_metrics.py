@@ -40,3 +40,39 @@ def test_clock_summary_counts_samples_inside_the_timed_region():
     c.first = 4
     s = c.summary()
     assert s["samples"] == 0 and s["sm_mhz"] == 2070.0 and "note" in s
+
+
+def test_whole_step_call_sequence():
+    """The default step's calls on a recording context: one integral build and
+    one Omega, the valence vectors' rho and sigma with the skip rule off, then
+    the core state's with it on, densities and f for every state, and the byte
+    tally of what crosses the boundary."""
+    import numpy as np
+    torch = __import__("pytest").importorskip("torch")
+    calls = []
+
+    class Rec:
+        def __getattr__(self, name):
+            def f(*a):
+                calls.append((name, a))
+                return 0.5 if name == "oscillator_strength" else None
+            return f
+    NO, NV, no, nv, NJ = 4, 9, 3, 4, 6
+    x, omega = bench.device_system(NO, NV, no, nv, NJ, 3, 1, torch.device("cpu"), True, cvs_last=1)
+    assert omega[2] == 10.2 and float(x["R1"][2][:, 1:].abs().max()) == 0.0
+    prob = bench.WholeProblem(x, omega, 2, 1)
+    o = bench.WholeProblem.outputs(x, 2, torch.zeros_like)
+    tally = {"in": 0, "out": 0}
+
+    def count(kind, *arrs):
+        tally[kind] += sum(a.numel() * a.element_size() for a in arrs)
+    fs = prob.step(Rec(), x, o, tally=count)
+    names = [c[0] for c in calls]
+    assert names.count("build_integrals") == 1 and names.count("triples_omega") == 1
+    assert names.count("jacobian_right") == 2 and names.count("transition_density") == 3
+    assert fs == [0.5, 0.5, 0.5]
+    cvs = [c[1][1] for c in calls if c[0] == "set_param"]
+    assert cvs == [0, 1, 1]
+    jr = [c[1] for c in calls if c[0] == "jacobian_right"]
+    assert len(jr[0][0]) == 2 and list(jr[1][0]) == [10.2]
+    assert tally["in"] > x["chol"].numel() * 8 and tally["out"] > 0

@@ -86,3 +86,19 @@ def test_subset_is_the_masked_full_tensor_equations():
     assert _rel(got1, s1) < 1e-12
     assert _rel(got2, O.from_full(o, OM._finish_doubles(Z))) < 1e-12
     assert B.n_ordered(S) == 6 + 3
+
+
+def test_cholesky_rows_suffice_for_the_residual():
+    """Held on the occupied and active virtual rows only (the other blocks read
+    through L^J_pq = L^J_qp), the Cholesky vectors give the same Omega."""
+    s = synth.make_system(5, 9, 3, 4, 12, seed=23)
+    b = B.make_bctx(s)
+    NO, nv = 5, 4
+    rows = np.concatenate([np.arange(NO), NO + np.arange(nv)])
+    cr = B.CholRows(rows, s.chol[:, rows, :].copy())
+    bs = B.BCtx(5, 9, 3, 4, s.eps, cr, s.t1, s.t2c, s.t2x)
+    S = [(2, 1, 0)]
+    for x, y in zip(B.triples_omega(bs, S), B.triples_omega(b, S)):
+        assert _rel(x, y) < 1e-14
+    with pytest.raises(KeyError):
+        cr.block(np.arange(NO + nv, NO + 9), np.arange(NO + nv, NO + 9))
