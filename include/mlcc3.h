@@ -232,6 +232,17 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              valence states (every batch kept), so that the valence and the
  *              core states of one system share one integral build.  1 needs a
  *              core mask.
+ *   "shard_count", "shard_index"  batch sharding across GPUs (default 1, 0):
+ *              mlcc3_triples_omega, the Jacobian transformations, the multiplier
+ *              transformation and the sweep run over the unique batches of shard
+ *              shard_index only (mlcc3_shard_batches gives the list), so that
+ *              one context per GPU, each with its own shard_index, computes
+ *              partial outputs whose sum over the shards (one all-reduce) is the
+ *              unsharded result: every one of these outputs is linear in the
+ *              per-batch terms.  The densities are not sharded (their
+ *              normalisation multiplies two sums over batches); they always run
+ *              over every batch.  A compute call with shard_index >= shard_count
+ *              returns MLCC3_ERR_ARG.
  *   "tc_wait_clocks"  clock limit of the split-precision tensor-core kernel's
  *              pipeline waits (a stage to fill or free, an accumulator to finish
  *              or to be read); 0 (default) is about one second.  On expiry the
@@ -250,6 +261,18 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              sizes the chunks from the free device memory at create.
  * Returns MLCC3_ERR_ARG for an unknown name or a value out of range. */
 int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
+
+/* CNTO matrices of one excited state (Sec. 2, Eqs. M and N; the active space
+ * of MLCC3 is spanned by the leading eigenvectors of their state averages):
+ *   M_ij = sum_a R^a_i R^a_j + 1/2 sum_{abk} (1 + delta_{ai,bk} delta_ij) R^{ab}_{ik} R^{ab}_{jk}
+ *   N_ab = sum_i R^a_i R^b_i + 1/2 sum_{cij} (1 + delta_{ai,cj} delta_ab) R^{ac}_{ij} R^{bc}_{ij}
+ * R1 [N_V][N_O]; R2 [N_V][N_O][N_V][N_O] = R^{AB}_{IJ} in full storage (a CCSD
+ * excitation vector, symmetric under (A,I) <-> (B,J)); M [N_O][N_O] and
+ * N [N_V][N_V] are overwritten.  Device pointers only (MLCC3_ERR_ARG
+ * otherwise); FP64; runs on `cuda_stream` and returns when it has finished.
+ * No context is needed. */
+int mlcc3_cnto_matrices(int64_t n_occ, int64_t n_vir, const double *R1, const double *R2,
+                        double *M, double *N, void *cuda_stream);
 
 /* Triples residual without allocating (no counterpart in the paper).
  * Some callers cannot allocate device memory at the moment they call: a
@@ -279,6 +302,16 @@ int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
  * (other streams, other contexts on the same device) race on it and must be
  * serialised by the caller. */
 int mlcc3_triples_omega_static(mlcc3_ctx *ctx, double *omega1, double *omega2);
+
+/* The unique batches i >= j >= k (i = j = k excluded; with cvs != 0 and a
+ * core_mask [n_act_occ] only those with a core index) that shard shard_index
+ * of shard_count processes under the "shard_count"/"shard_index" parameters:
+ * longest-processing-time assignment by the number of distinct orderings of a
+ * batch (6, or 3 with two equal indices), in list order.  Writes up to
+ * max_batches (i, j, k) triples to ijk[3 * max_batches] and returns the
+ * shard's batch count, or MLCC3_ERR_ARG.  Host only: no GPU is needed. */
+int mlcc3_shard_batches(int n_act_occ, const uint8_t *core_mask, int cvs, int shard_count,
+                        int shard_index, int *ijk, int max_batches);
 
 /* Diagnostics (used by the test-suite).  mlcc3_debug_fetch copies the first
  * n doubles of a named device buffer of the context into `host` (integral

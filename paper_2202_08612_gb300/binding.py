@@ -29,7 +29,7 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param",
            "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
            "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient", "mlcc3_ground_density",
-           "mlcc3_multiplier_transformation")
+           "mlcc3_multiplier_transformation", "mlcc3_cnto_matrices", "mlcc3_shard_batches")
 
 
 class MLCC3Error(RuntimeError):
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_rayleigh_quotient.argtypes = [P, D, P, P, P, P, D, P]
     lib.mlcc3_ground_density.argtypes = [P, P, P, P]
     lib.mlcc3_multiplier_transformation.argtypes = [P, P, P, P, P]
+    lib.mlcc3_cnto_matrices.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+    lib.mlcc3_shard_batches.argtypes = [I, P, I, I, I, P, I]
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -104,6 +106,32 @@ def _ptr(x):
     if not x.is_contiguous() or str(x.dtype) != "torch.float64":
         raise ValueError("tensors must be contiguous float64")
     return x.data_ptr()
+
+
+def cnto_matrices(R1, R2, M, N, stream=None):
+    """mlcc3_cnto_matrices: M [N_O][N_O], N [N_V][N_V] of one state (device arrays)."""
+    lib = load()
+    NV, NO = R1.shape
+    rc = lib.mlcc3_cnto_matrices(NO, NV, _ptr(R1), _ptr(R2), _ptr(M), _ptr(N), stream)
+    if rc != 0:
+        raise MLCC3Error(rc, lib.mlcc3_last_error().decode())
+
+
+def shard_batches(n_act_occ, core_mask, cvs, shard_count, shard_index):
+    """mlcc3_shard_batches: the unique batches (i, j, k) that shard
+    `shard_index` of `shard_count` processes (host only, no GPU needed)."""
+    lib = load()
+    mask = None
+    if core_mask is not None:
+        mask = np.ascontiguousarray(core_mask, dtype=np.uint8)
+    cap = n_act_occ ** 3 + 1
+    buf = np.zeros(3 * cap, dtype=np.int32)
+    n = lib.mlcc3_shard_batches(int(n_act_occ), None if mask is None else mask.ctypes.data,
+                                int(bool(cvs)), int(shard_count), int(shard_index),
+                                buf.ctypes.data, cap)
+    if n < 0:
+        raise MLCC3Error(n, lib.mlcc3_last_error().decode())
+    return [tuple(int(v) for v in buf[3 * u:3 * u + 3]) for u in range(n)]
 
 
 def tc_gemm(A, B, C):

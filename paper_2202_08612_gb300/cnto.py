@@ -10,12 +10,12 @@ averaged over the states; their eigenvectors are the occupied and virtual
 CNTOs, and the active space holds the fewest CNTOs (by decreasing eigenvalue)
 whose eigenvalues add up to more than 1 - xi.
 
-Each M and N is one GEMM over the doubles (K = N_V^2 N_O and N_V N_O^2) plus
-the singles GEMM and the diagonal term of the delta factor; on CUDA tensors the
-GEMMs run in cuBLAS and the eigendecompositions in cuSOLVER (through torch),
-FP64 throughout.  For a normalised vector tr M = tr N = <R, R> (the
-unique-element inner product), so the thresholds compare fractions of the
-excitation's weight.
+M and N come from the library's mlcc3_cnto_matrices (FP64 Gram-matrix
+kernels over the doubles, K = N_V^2 N_O and N_V N_O^2, plus the singles and
+the diagonal term of the delta factor); the small symmetric eigenproblems run
+in cuSOLVER (through torch), FP64 throughout.  CUDA tensors only.  For a
+normalised vector tr M = tr N = <R, R> (the unique-element inner product), so
+the thresholds compare fractions of the excitation's weight.
 """
 from __future__ import annotations
 
@@ -35,17 +35,16 @@ class CntoSpace:
 def cnto_matrices(R1, R2):
     """M [N_O][N_O] and N [N_V][N_V] of one excited state (Eqs. M, N)."""
     import torch
+    from . import binding
     NV, NO = R1.shape
     if tuple(R2.shape) != (NV, NO, NV, NO):
         raise ValueError(f"R2 must be [N_V][N_O][N_V][N_O] = {(NV, NO, NV, NO)}, got {tuple(R2.shape)}")
-    X = R2.permute(1, 0, 2, 3).reshape(NO, NV * NV * NO)     # [i][(a, b, k)]
-    Y = R2.reshape(NV, NO * NV * NO)                          # [a][(i, c, j)]
-    M = R1.T @ R1 + 0.5 * (X @ X.T)
-    N = R1 @ R1.T + 0.5 * (Y @ Y.T)
-    # the delta terms: only the elements R^{aa}_{ii} enter, on the diagonals
-    d = torch.diagonal(R2.reshape(NV * NO, NV * NO)).reshape(NV, NO)
-    M = M + 0.5 * torch.diag((d * d).sum(0))
-    N = N + 0.5 * torch.diag((d * d).sum(1))
+    if not (R1.is_cuda and R2.is_cuda):
+        raise ValueError("the CNTO matrices are computed on the GPU: R1 and R2 must be CUDA tensors")
+    R1, R2 = R1.contiguous(), R2.contiguous()
+    M = torch.empty((NO, NO), dtype=torch.float64, device=R1.device)
+    N = torch.empty((NV, NV), dtype=torch.float64, device=R1.device)
+    binding.cnto_matrices(R1, R2, M, N, stream=torch.cuda.current_stream(R1.device).cuda_stream)
     return M, N
 
 

@@ -75,6 +75,8 @@ struct mlcc3_ctx {
   int device;
   std::vector<uint8_t> core;
   bool cvs = true;  // apply the CVS skip rule of the core mask (mlcc3_set_param "cvs")
+  // batch sharding: Omega, rho and sigma run over shard shard_index of shard_count
+  int shard_count = 1, shard_index = 0;
   bool built = false;
   unsigned long long build_gen = 0;  // counts mlcc3_build_integrals calls
   // split-K target of the FP64 strided contraction: when few output tiles

@@ -420,6 +420,26 @@ Chunk make_chunk(const mlcc3_ctx *c, const std::vector<TripItem> &held, int p0, 
   return ch;
 }
 
+// The unique batches of shard `index` of `count` (batch sharding across GPUs):
+// longest-processing-time assignment with a batch's cost its number of
+// distinct orderings (6 for i > j > k, 3 with two equal indices), batches
+// taken in their list order, ties to the lowest shard; the shards partition
+// the list and every shard keeps the list order.
+std::vector<TripItem> shard_of(const std::vector<TripItem> &list, int count, int index) {
+  if (count <= 1) return list;
+  std::vector<long long> load(count, 0);
+  std::vector<TripItem> out;
+  for (const TripItem &t : list) {
+    const int w = (t.i != t.j && t.j != t.k) ? 6 : 3;
+    int best = 0;
+    for (int q = 1; q < count; ++q)
+      if (load[q] < load[best]) best = q;
+    load[best] += w;
+    if (best == index) out.push_back(t);
+  }
+  return out;
+}
+
 // Split the unique batches into chunks of at most chunk_blocks blocks (or, when
 // it is 0, as many as fit in half of the device memory left free once the
 // context's persistent arrays exist, at 156 bytes per block element: the
@@ -452,8 +472,8 @@ void make_chunks(mlcc3_ctx *c) {
     }
     return out;
   };
-  c->parts = partition(c->batches, "p");
-  c->parts_cvs = partition(c->batches_cvs, "c");
+  c->parts = partition(shard_of(c->batches, c->shard_count, c->shard_index), "p");
+  c->parts_cvs = partition(shard_of(c->batches_cvs, c->shard_count, c->shard_index), "c");
   if ((long long)c->batches.size() <= group_max) {
     c->groups = c->parts;  // one chunk: the same key shares the tau cache
     return;
@@ -2770,6 +2790,8 @@ extern "C" void mlcc3_destroy(mlcc3_ctx *c) {
 static void require_built(mlcc3_ctx *c) {
   if (!c) throw Error{MLCC3_ERR_ARG, "null context"};
   if (!c->built) throw Error{MLCC3_ERR_STATE, "mlcc3_build_integrals has not been called"};
+  if (c->shard_index >= c->shard_count)
+    throw Error{MLCC3_ERR_ARG, "shard_index must be below shard_count"};
 }
 
 extern "C" int mlcc3_build_integrals(mlcc3_ctx *c, const double *chol, const double *t1,
@@ -2924,6 +2946,11 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
     } else if (n == "tc_persist_from") {
       if (value < 0) throw Error{MLCC3_ERR_ARG, "tc_persist_from must be >= 0"};
       c->tc_persist_from = (int)std::min<long long>(value, 1LL << 30);
+    } else if (n == "shard_count" || n == "shard_index") {
+      if (value < 0 || value > 4096) throw Error{MLCC3_ERR_ARG, n + " out of range 0..4096"};
+      (n == "shard_count" ? c->shard_count : c->shard_index) = (int)value;
+      if (c->shard_count < 1) c->shard_count = 1;
+      make_chunks(c);
     } else if (n == "cvs") {
       if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "cvs must be 0 or 1"};
       if (value == 1 && c->core.empty())
@@ -2969,6 +2996,30 @@ extern "C" int mlcc3_debug_kernel_stats(mlcc3_ctx *c, int index, char *name, siz
     *ms = it->second.ms;
     *flops = it->second.flops;
   });
+}
+
+extern "C" int mlcc3_shard_batches(int n_act_occ, const uint8_t *core_mask, int cvs,
+                                   int shard_count, int shard_index, int *ijk, int max_batches) {
+  if (n_act_occ < 0 || n_act_occ > 32 || shard_count < 1 || shard_index < 0 ||
+      shard_index >= shard_count || max_batches < 0 || (max_batches > 0 && !ijk)) {
+    g_last_error = "mlcc3_shard_batches: bad argument";
+    return MLCC3_ERR_ARG;
+  }
+  std::vector<TripItem> list;
+  for (int i = 0; i < n_act_occ; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k) {
+        if (i == j && j == k) continue;
+        if (cvs && core_mask && !(core_mask[i] || core_mask[j] || core_mask[k])) continue;
+        list.push_back(TripItem{i, j, k, 0, 0});
+      }
+  std::vector<TripItem> mine = shard_of(list, shard_count, shard_index);
+  for (size_t u = 0; u < mine.size() && (int)u < max_batches; ++u) {
+    ijk[3 * u] = mine[u].i;
+    ijk[3 * u + 1] = mine[u].j;
+    ijk[3 * u + 2] = mine[u].k;
+  }
+  return (int)mine.size();
 }
 
 extern "C" long long mlcc3_debug_nbatches(mlcc3_ctx *c) {
