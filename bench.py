@@ -58,7 +58,8 @@ class ClockSampler:
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "memory.used")
 
     def __init__(self, index):
         self.index = index
@@ -108,9 +109,12 @@ class ClockSampler:
         mx = [float(r[1]) for r in rows if r[1].replace('.', '', 1).isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        mem = [float(r[8]) for r in rows if len(r) > 8 and r[8].replace('.', '', 1).isdigit()]
         out.update({"sm_mhz": statistics.median(sm) if sm else None,
                     "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                     "samples": len(self.rows) - self.first})
+        if mem:
+            out["memory_used_mib_max"] = max(mem)
         return out
 
 
@@ -1076,6 +1080,9 @@ def run_whole(args, rank, world, local_rank):
     ctx = binding.Context(NO, NV, no, nv, NJ, precision=binding.MLCC3_SPLIT_BF16X3,
                           stream=stream.cuda_stream, core_mask=mask)
     ctx.set_param("chunk_blocks", args.chunk_blocks)
+    # the densities' scratch and the Jacobians' do not fit side by side next to
+    # the resident inputs: every call frees its own
+    ctx.set_param("release_scratch", 1)
     dist = world > 1
 
     def barrier():

@@ -226,6 +226,16 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              run the persistent kernel (one CTA per SM looping over tiles,
  *              accumulator double-buffered in TMEM); smaller ones run one CTA
  *              per tile.  Default 304; 0 always persistent.
+ *   "release_scratch"  0 (default): the scratch of a call (triples blocks of
+ *              a chunk, their split copies, intermediates; sized for the
+ *              largest call so far) stays allocated for the next call and
+ *              keeps tau and the layouts cached.  1: every call ends by freeing
+ *              all scratch that mlcc3_build_integrals did not create, so that
+ *              the device holds only the integral blocks between calls and the
+ *              peak is the largest single call's, not the sum over the kinds of
+ *              call (the transition densities need more than the Jacobian
+ *              transformations); each call then allocates its scratch again.
+ *              A sweep needs contexts with 0 (MLCC3_ERR_STATE otherwise).
  *   "cvs"      1 (default): a context created with a core mask applies the CVS
  *              skip rule (mlcc3_dims.core_mask) in the Jacobian transformations
  *              and the densities; 0: the same context treats its vectors as

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <functional>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -121,6 +122,11 @@ struct mlcc3_ctx {
 
   // named scratch buffers, reused across calls (stream ordered)
   std::map<std::string, std::pair<void *, size_t>> scratch;
+  // "release_scratch": every call ends by freeing the scratch that the integral
+  // build did not create (keep_scratch / keep_splits are the build's names)
+  bool release_scratch = false;
+  std::set<std::string> keep_scratch, keep_splits;
+  void release();
   // item lists on the device, built once per pattern
   std::map<std::string, std::pair<void *, int>> items;
   // hi/lo bfloat16 copies of operands of the tensor-core path, with their

@@ -118,6 +118,31 @@ void *mlcc3_ctx::raw(const std::string &name, size_t bytes) {
   return p;
 }
 
+// Free the scratch of the last call (everything the integral build did not
+// create) and forget what was cached in it: split copies, triples layouts and
+// FP32 copies, tau.  The stream has been synchronised.
+void mlcc3_ctx::release() {
+  for (auto it = scratch.begin(); it != scratch.end();) {
+    if (keep_scratch.count(it->first)) {
+      ++it;
+      continue;
+    }
+    cudaFree(it->second.first);
+    it = scratch.erase(it);
+  }
+  for (auto it = splits.begin(); it != splits.end();) {
+    if (keep_splits.count(it->first)) ++it;
+    else it = splits.erase(it);
+  }
+  for (int t = 0; t < 4; ++t) {
+    tri[t] = TriSlot{};
+    f32s[t] = TriSlot{};
+  }
+  gens.clear();
+  tau_valid = false;
+  tau_key.clear();
+}
+
 double *mlcc3_ctx::buf(const std::string &name, size_t n) {
   return static_cast<double *>(raw(name, n * sizeof(double)));
 }
@@ -215,6 +240,7 @@ void mlcc3_ctx::finish() {
     check_cuda(cudaMemsetAsync(status, 0, sizeof(int), stream), "reset status");
     throw Error{MLCC3_ERR_SINGULAR_DENOM, "|eps^{abc}_{ijk} - omega| < 1e-3 in a triples block"};
   }
+  if (release_scratch && built) release();
 }
 
 void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &sh, double alpha,
@@ -1900,6 +1926,13 @@ static void do_build_integrals(mlcc3_ctx *c, const double *chol_in, const double
   c->tau_valid = false;
   c->built = true;
   c->build_gen += 1;
+  // what exists now is the build's own state: a context that releases its
+  // scratch after every call keeps exactly these
+  check_cuda(cudaStreamSynchronize(c->stream), "build sync");
+  c->keep_scratch.clear();
+  c->keep_splits.clear();
+  for (auto &kv : c->scratch) c->keep_scratch.insert(kv.first);
+  for (auto &kv : c->splits) c->keep_splits.insert(kv.first);
 }
 
 static void do_triples_omega(mlcc3_ctx *c, double *omega1_out, double *omega2_out) {
@@ -2951,6 +2984,13 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
       (n == "shard_count" ? c->shard_count : c->shard_index) = (int)value;
       if (c->shard_count < 1) c->shard_count = 1;
       make_chunks(c);
+    } else if (n == "release_scratch") {
+      if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "release_scratch must be 0 or 1"};
+      c->release_scratch = value == 1;
+      if (c->release_scratch && c->built) {
+        check_cuda(cudaStreamSynchronize(c->stream), "sync");
+        c->release();
+      }
     } else if (n == "cvs") {
       if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "cvs must be 0 or 1"};
       if (value == 1 && c->core.empty())
@@ -3231,6 +3271,9 @@ extern "C" int mlcc3_sweep_create(mlcc3_sweep **out, mlcc3_ctx *const *ctxs, int
     if (!out || !ctxs || n_sys < 1) throw Error{MLCC3_ERR_ARG, "null argument or n_sys < 1"};
     *out = nullptr;
     for (int q = 0; q < n_sys; ++q) require_built(ctxs[q]);
+    for (int q = 0; q < n_sys; ++q)
+      if (ctxs[q]->release_scratch)  // the captured graph reads the contexts' scratch
+        throw Error{MLCC3_ERR_STATE, "a sweep needs contexts that keep their scratch (release_scratch 0)"};
     for (int q = 1; q < n_sys; ++q)
       if (ctxs[q]->device != ctxs[0]->device) throw Error{MLCC3_ERR_ARG, "contexts on different devices"};
     for (int q = 0; q < n_sys; ++q)
@@ -3336,6 +3379,9 @@ extern "C" int mlcc3_sweep_set_system(mlcc3_sweep *sw, int q, int n_vec, const d
 extern "C" int mlcc3_sweep_run(mlcc3_sweep *sw, const double *omega) {
   return guarded([&] {
     if (!sw) throw Error{MLCC3_ERR_ARG, "null sweep"};
+    for (auto &y : sw->sys)
+      if (y.c->release_scratch)
+        throw Error{MLCC3_ERR_STATE, "a sweep needs contexts that keep their scratch (release_scratch 0)"};
     long long n = 0;
     for (auto &y : sw->sys) n += y.n_vec;
     if (n == 0) return;

@@ -89,3 +89,49 @@ def fixed_point_eigenpair(s, o):
     R1, R2 = to_vec(d, basis, R)
     L1, L2 = to_vec(d, basis, L)
     return w, R1, R2, L1, L2, float(L @ (dvec * R))
+
+
+def fixed_point_roots(s, o, k):
+    """The k lowest self-consistent roots of J(omega) = diag(Delta-eps) + A_T(omega)
+    on the explicit unique basis: omega_r = the r-th eigenvalue (by real part)
+    of J(omega_r), iterated from the r-th lowest singles diagonal element."""
+    d = s.dims
+    basis = unique_basis(d)
+    eps, NO = s.eps, d.n_occ
+
+    def diag(kind, idx):
+        if kind == "s":
+            A, I = idx
+            return eps[NO + A] - eps[I]
+        i, a, L, D = idx
+        return eps[NO + a] + eps[NO + D] - eps[i] - eps[L]
+
+    dvec = np.array([diag(kk, idx) for kk, idx in basis])
+    cols_cache = {}
+
+    def jmat(w):
+        if w not in cols_cache:
+            cols = []
+            for nu in range(len(basis)):
+                e = np.zeros(len(basis))
+                e[nu] = 1.0
+                r1, r2 = to_vec(d, basis, e)
+                y1, y2 = O.jacobian_right(o, w, r1, O.to_full(o, r2))
+                cols.append(coef(d, basis, y1, O.from_full(o, y2)))
+            cols_cache[w] = np.diag(dvec) + np.array(cols).T
+        return cols_cache[w]
+
+    singles = np.sort(np.array([dvec[n] for n, (kk, _) in enumerate(basis) if kk == "s"]))
+    out = []
+    for r in range(k):
+        w = float(singles[r])
+        for _ in range(60):
+            ev = np.sort_complex(np.linalg.eigvals(jmat(w)))
+            ev = ev[np.argsort(ev.real, kind="stable")]
+            w_new = float(ev[r].real)
+            if abs(w_new - w) < 1e-13:
+                w = w_new
+                break
+            w = w_new
+        out.append(w)
+    return np.array(out)

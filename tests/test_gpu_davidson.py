@@ -70,3 +70,42 @@ def test_davidson_with_a_caller_block_equal_to_the_model():
     r1 = dv1.solve(tol=1e-9)
     assert abs(r0.omega - r1.omega) < 1e-10, (r0.omega, r1.omega)
     g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(binding.MLCC3_FP64, 1e-9), (binding.MLCC3_SPLIT_BF16X3, 1e-5)])
+def test_block_davidson_reaches_the_explicit_roots(precision, tol):
+    """Three roots at once, the expansions of every root transformed at every
+    root's frequency in one sweep replay: the self-consistent roots of the
+    explicit-matrix iteration."""
+    torch = _torch()
+    from paper_2202_08612_gb300.davidson import BlockDavidson
+    s = synth.make_system(3, 4, 2, 2, 10, seed=5)
+    o = O.make_ctx(s)
+    ref = sdbasis.fixed_point_roots(s, o, 3)
+    c = Case(3, 4, 2, 2, 10, seed=5, nstates=1)
+    g = c.context(precision=precision)
+    bd = BlockDavidson([(g, s.eps, (3, 4, 2, 2))], torch.device("cuda"), 3)
+    res = bd.solve(tol=1e-10 if precision == binding.MLCC3_FP64 else 1e-7)[0]
+    assert np.all(res.residual < 1e-6), res.residual
+    assert np.abs(np.sort(res.omega) - np.sort(ref)).max() < tol, (res.omega, ref)
+    assert res.sweeps > 1
+    bd.close()
+    g.close()
+
+
+def test_block_davidson_two_systems_in_one_sweep():
+    """Two uneven systems solved together (one graph replay per expansion for
+    both): each gets the roots that the single-root solver finds for it."""
+    torch = _torch()
+    from paper_2202_08612_gb300.davidson import BlockDavidson
+    cs = [Case(NO=6, NV=24, no=4, nv=8, NJ=72, nstates=1), Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)]
+    gs = [c.context() for c in cs]
+    bd = BlockDavidson([(g, c.sys.eps, c.dims[:4]) for g, c in zip(gs, cs)], torch.device("cuda"), 2)
+    res = bd.solve(tol=1e-9)
+    for r, g, c in zip(res, gs, cs):
+        assert np.all(r.residual < 1e-7), r.residual
+        single = Davidson(g, c.sys.eps, c.dims[:4], torch.device("cuda")).solve(tol=1e-9)
+        assert np.abs(r.omega - single.omega).min() < 1e-8, (r.omega, single.omega)
+    bd.close()
+    for g in gs:
+        g.close()

@@ -222,3 +222,31 @@ def test_split_wait_timeout_is_reported_and_the_context_recovers(persist):
     p1, p2 = O.jacobian_right(o, w, st.R1[0], O.to_full(o, st.R2[0]))
     assert rel_err(c.host(rho1)[0], p1) < TOL
     assert rel_err(c.host(rho2)[0], O.from_full(o, p2)) < TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(binding.MLCC3_SPLIT_BF16X3, TOL), (binding.MLCC3_FP64, 1e-10)])
+def test_release_scratch_between_calls(precision, tol):
+    """With "release_scratch" every call frees the scratch the integral build
+    did not create: the whole path still matches the oracle, twice in a row
+    (every cache rebuilt), the device memory in use returns to the build's
+    after each call, and a sweep refuses the context."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)
+    g = c.context(precision=precision)
+    g.set_param("release_scratch", 1)
+    ref = oracle_all(c)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        got = run_all(c, g)
+        for k in ref:
+            assert rel_err(got[k], ref[k]) < tol, (k, rel_err(got[k], ref[k]))
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+    with pytest.raises(binding.MLCC3Error) as e:
+        binding.Sweep([g], tune=False)
+    assert e.value.code == -6
+    g.close()
