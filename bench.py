@@ -1197,7 +1197,12 @@ def run_whole(args, rank, world, local_rank):
                            "chunk_blocks": args.chunk_blocks,
                            "l2": "inputs larger than L2 (Cholesky vectors "
                                  f"{NJ * (NO + NV) ** 2 * 8 / 2**30:.1f} GiB)"},
-                "s_per_davidson_iter": s_iter, "fp64_gpu_path": fp64, "f": f_ours,
+                "s_per_davidson_iter": s_iter, "fp64_gpu_path": fp64,
+                "f_step": {"values": f_ours,
+                           "note": "f of the timed step's states from the triples parts of the "
+                                   "densities on the configuration's distribution (amplitudes of "
+                                   "order 1 at this size, hence not of physical size); the accuracy "
+                                   "of f is reported under fp64_gpu_path"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": gpu_launches, "hbm_used_gb": hbm_used,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},

@@ -2530,8 +2530,9 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     const long long bw = ch.nb * s.nv3;
     double *tau, *taut;
     build_tau(c, ch, &tau, &taut);
-    // lambda3 (omega = 0) and its contravariant form
-    double *lam3 = c->buf("lam3", bw);
+    // lambda3 (omega = 0) and its contravariant form; lambda3 itself is dead once
+    // the contravariant form exists, so L3 reuses its buffer
+    double *lam3 = c->buf("L3", bw);
     double *lt3 = c->buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
@@ -3089,6 +3090,8 @@ struct mlcc3_sweep {
     int chunk_gen = 0;
     int fill = 4;
     std::vector<double> fill_ms;  // tuning times per candidate
+    // tensor-core choices of the split mode and their tuning times
+    std::vector<std::pair<std::string, std::vector<std::pair<long long, double>>>> tc_ms;
   };
   std::vector<Sys> sys;
   int device = 0;
@@ -3197,6 +3200,40 @@ bool sweep_stale(const mlcc3_sweep *sw) {
   return false;
 }
 
+// Tensor-core knobs of system q (split mode), one after the other, each kept
+// at the fastest candidate on one trial vector: batches stacked per
+// triples-build tile (only where a tile can hold more than one batch, n_v <= 128),
+// the launch form (persistent above 304 tiles, always, never) and the longest
+// FP32 accumulation chain (1024 or 512 products; both within the split mode's
+// error bound, the shorter one more accurate and with more FP64 reductions).
+void sweep_tune_tc(mlcc3_sweep *sw, int q) {
+  mlcc3_sweep::Sys &y = sw->sys[q];
+  mlcc3_ctx *c = y.c;
+  y.tc_ms.clear();
+  auto tune = [&](const char *name, int *knob, std::vector<int> cands) {
+    std::vector<std::pair<long long, double>> times;
+    int best = *knob;
+    double best_ms = 1e300;
+    for (int v : cands) {
+      *knob = v;
+      sweep_pass(sw, false, q, 1);  // plans of this candidate, untimed
+      double ms = 1e300;
+      for (int r = 0; r < 3 && (r == 0 || ms < 50.0); ++r)
+        ms = std::min(ms, sweep_time(sw, [&] { sweep_pass(sw, false, q, 1); }));
+      times.push_back({v, ms});
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    *knob = best;
+    y.tc_ms.push_back({name, times});
+  };
+  if (c->nv <= 128) tune("tc_group", &c->tc_group, {1, 2, 4});
+  tune("tc_persist_from", &c->tc_persist_from, {kTcPersistFrom, 0, 1 << 30});
+  tune("tc_kcap", &c->tc_kcap, {16, 8});
+}
+
 void sweep_prepare(mlcc3_sweep *sw) {
   if (sw->exec) {
     cudaGraphExecDestroy(sw->exec);
@@ -3225,6 +3262,7 @@ void sweep_prepare(mlcc3_sweep *sw) {
         }
       }
       y.c->bstc_fill = y.fill = best;
+      if (split_mode(y.c)) sweep_tune_tc(sw, (int)q);
     }
     size_t n_multi = 0, n_serial = 0;
     cudaGraphExec_t gm = sweep_capture(sw, true, &n_multi);
@@ -3413,10 +3451,21 @@ extern "C" int mlcc3_sweep_info(mlcc3_sweep *sw, char *buf, size_t len) {
       const auto &y = sw->sys[q];
       s += std::string(q ? ", " : "") + "{\"n_vec\": " + std::to_string(y.n_vec) +
            ", \"chunk_blocks\": " + std::to_string(y.c->chunk_blocks) +
-           ", \"bstc_fill\": " + std::to_string(y.c->bstc_fill) + ", \"fill_ms\": [";
+           ", \"bstc_fill\": " + std::to_string(y.c->bstc_fill) +
+           ", \"tc_group\": " + std::to_string(y.c->tc_group) +
+           ", \"tc_persist_from\": " + std::to_string(y.c->tc_persist_from) +
+           ", \"tc_kcap\": " + std::to_string(y.c->tc_kcap) + ", \"fill_ms\": [";
       for (size_t f = 0; f < y.fill_ms.size(); ++f)
         s += std::string(f ? ", " : "") + std::to_string(y.fill_ms[f]);
-      s += "]}";
+      s += "], \"tc_ms\": {";
+      for (size_t t = 0; t < y.tc_ms.size(); ++t) {
+        s += std::string(t ? ", " : "") + "\"" + y.tc_ms[t].first + "\": [";
+        for (size_t u = 0; u < y.tc_ms[t].second.size(); ++u)
+          s += std::string(u ? ", " : "") + "[" + std::to_string(y.tc_ms[t].second[u].first) + ", " +
+               std::to_string(y.tc_ms[t].second[u].second) + "]";
+        s += "]";
+      }
+      s += "}}";
     }
     s += "]}";
     std::snprintf(buf, len, "%s", s.c_str());

@@ -101,6 +101,27 @@ def test_sweep_split_matches_oracle(cases):
     sw.close()
 
 
+def test_sweep_split_tuned_matches_oracle(cases):
+    """The autotuner on: per system the split-K fill, the triples-build tile
+    grouping, the launch form and the accumulation-chain cap are timed and the
+    fastest kept; the tuned graph still meets the split bar, also after a
+    replay with new frequencies."""
+    ctxs, sw, outs = run_sweep(cases, binding.MLCC3_SPLIT_BF16X3, tune=True)
+    omegas = [c.st.omega for c in cases]
+    sw.run(np.concatenate(omegas))
+    check(cases, outs, omegas, 1e-4)
+    info = sw.info()
+    for sy in info["systems"]:
+        assert sy["tc_group"] in (1, 2, 4) and sy["tc_kcap"] in (8, 16)
+        assert sy["tc_persist_from"] in (304, 0, 1 << 30)
+        assert set(sy["tc_ms"]) >= {"tc_persist_from", "tc_kcap"}
+        assert all(ms > 0 for _, ms in sy["tc_ms"]["tc_kcap"])
+    omegas2 = [w + 0.05 for w in omegas]
+    sw.run(np.concatenate(omegas2))
+    check(cases, outs, omegas2, 1e-4)
+    sw.close()
+
+
 def test_sweep_errors(cases):
     torch = _cuda()
     g = cases[0].context()
