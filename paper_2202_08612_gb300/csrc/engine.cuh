@@ -127,6 +127,16 @@ struct mlcc3_ctx {
   bool release_scratch = false;
   std::set<std::string> keep_scratch, keep_splits;
   void release();
+  // Triples arrays (tau, R3, L3, lambda3 and their contravariant forms) are
+  // handled as `double *`; in the split-precision mode (tri32) their storage is
+  // binary32, the accuracy of the FP32-accumulated tensor-core sums they come
+  // from.  tri_buf allocates one and registers its range, so that the generic
+  // kernels can tell a binary32 operand (is_tri32) by its address.
+  bool tri32 = false;
+  std::map<std::string, std::pair<const char *, size_t>> tri_regs;
+  double *tri_buf(const std::string &name, size_t n);
+  bool is_tri32(const void *p) const;
+  void zero_tri(double *p, size_t n);
   // item lists on the device, built once per pattern
   std::map<std::string, std::pair<void *, int>> items;
   // hi/lo bfloat16 copies of operands of the tensor-core path, with their

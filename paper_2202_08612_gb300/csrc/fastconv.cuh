@@ -15,11 +15,23 @@ __device__ __forceinline__ void split_hi_lo(double x, __nv_bfloat16 &hi, __nv_bf
   lo = __float2bfloat16_rn(f - __bfloat162float(hi));
 }
 
+// The same split of a binary32 value (no conversion from binary64).
+__device__ __forceinline__ void split_hi_lo(float f, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(f);
+  lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+}
+
 // x scaled by +1 (mode 0), -1 (mode 1, a sign flip of the bit pattern) or s.
 __device__ __forceinline__ double scaled(double x, int mode, double s) {
   if (mode == 0) return x;
   if (mode == 1) return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
   return s * x;
+}
+
+__device__ __forceinline__ float scaled(float x, int mode, double s) {
+  if (mode == 0) return x;
+  if (mode == 1) return -x;
+  return (float)s * x;
 }
 
 }  // namespace mlcc3

@@ -24,6 +24,12 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 }
 
+// Element i of an operand that holds binary64 (f32 = 0) or binary32 values.
+template <typename T>
+__device__ __forceinline__ T ld_op(const double *p, int f32, long long i) {
+  return f32 ? (T)reinterpret_cast<const float *>(p)[i] : (T)p[i];
+}
+
 // T: product type; the FP32 form (split-precision mode) folds each thread's
 // FP32 partial sums into FP64 every four K tiles (64 products).
 template <typename T>
@@ -66,8 +72,7 @@ __device__ __forceinline__ void bstc_body(const BstcParams &p) {
                       (p.K3 == 1 && p.K2 == 1 && it.sA[2] == 1);
   const bool kfastB = (it.sB[2] == 1 && p.K3 > 1) || (p.K3 == 1 && it.sB[1] == 1 && p.K2 > 1) ||
                       (p.K3 == 1 && p.K2 == 1 && it.sB[0] == 1);
-  const double *A = p.A + it.offA;
-  const double *B = p.B + it.offB;
+  const long long offA = it.offA, offB = it.offB;
 
   const int ty = tid / 16, tx = tid % 16;
   T acc[4][4];
@@ -101,14 +106,14 @@ __device__ __forceinline__ void bstc_body(const BstcParams &p) {
       int kk, mm;
       if (kfastA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
       T v = T(0);
-      if (rowA[mm] >= 0 && kA[kk] >= 0) v = (T)A[rowA[mm] + kA[kk]];
+      if (rowA[mm] >= 0 && kA[kk] >= 0) v = ld_op<T>(p.A, p.a32, offA + rowA[mm] + kA[kk]);
       As[kk][mm] = v;
     }
     for (int e = tid; e < BK * BN; e += 256) {
       int kk, nn;
       if (kfastB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
       T v = T(0);
-      if (colB[nn] >= 0 && kB[kk] >= 0) v = (T)B[kB[kk] + colB[nn]];
+      if (colB[nn] >= 0 && kB[kk] >= 0) v = ld_op<T>(p.B, p.b32, offB + kB[kk] + colB[nn]);
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   const BstcItem &it = p.items[blockIdx.x];
   const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
   const long long Kall = (long long)K1 * K2 * K3;
-  const double *A = p.A + it.offA, *B = p.B + it.offB;
+  const long long offA = it.offA, offB = it.offB;
   // block y of gridDim.y takes the K range [y kchunk, (y + 1) kchunk) (kchunk a
   // multiple of 256; 0 = all of K); split the thread's first K index once,
   // then advance by 256 with 32-bit carries
@@ -175,7 +180,8 @@ __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
   for (long long k = t0; k < K; k += 256) {
-    s += A[k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]] * B[k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]];
+    s += ld_op<double>(p.A, p.a32, offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]) *
+         ld_op<double>(p.B, p.b32, offB + k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]);
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {
@@ -368,17 +374,18 @@ constexpr int kC3SJ = 9, kC3SI = 8 * kC3SJ + 1, kC3T = 8 * kC3SI;  // padded til
 __constant__ int kC3P[6][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}};
 }  // namespace
 
-__global__ void __launch_bounds__(512) contra3_kernel(const double *__restrict__ X,
-                                                      double *__restrict__ Xt, long long nblocks,
+template <typename T>
+__global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
+                                                      T *__restrict__ Xt, long long nblocks,
                                                       int nv) {
-  __shared__ double tile[6 * kC3T];
+  __shared__ T tile[6 * kC3T];
   __shared__ int org[6][3];
   __shared__ int slot[6];
   const long long blk = blockIdx.y;
   if (blk >= nblocks) return;
   const long long nv3 = (long long)nv * nv * nv;
-  const double *B = X + blk * nv3;
-  double *O = Xt + blk * nv3;
+  const T *B = X + blk * nv3;
+  T *O = Xt + blk * nv3;
   const int nt = (nv + 7) / 8;
   if (threadIdx.x == 0) {
     // decode orbit index -> (A, B, C), A <= B <= C < nt
@@ -412,14 +419,14 @@ __global__ void __launch_bounds__(512) contra3_kernel(const double *__restrict__
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
     const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    tile[p * kC3T + sidx] = (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : 0.0;
+    tile[p * kC3T + sidx] = (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : T(0);
   }
   __syncthreads();
   const int A = org[0][0], Bt = org[0][1], C = org[0][2];
   const int l[3] = {li, lj, lk};
   const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
                    8 * Bt + lj < nv && 8 * C + lk < nv;
-  double v[6];
+  T v[6];
   int pos[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
@@ -428,10 +435,10 @@ __global__ void __launch_bounds__(512) contra3_kernel(const double *__restrict__
   }
   __syncthreads();  // every thread holds its inputs; the tiles now take the outputs
   if (own) {
-    const double E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
-    const double be = fma(-2.0, Od, E), bo = fma(-2.0, E, Od);
+    const T E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
+    const T be = fma(T(-2), Od, E), bo = fma(T(-2), E, Od);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(3.0, v[p], p < 3 ? be : bo);
+    for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(T(3), v[p], p < 3 ? be : bo);
   }
   __syncthreads();
   for (int p = 0; p < 6; ++p) {
@@ -441,16 +448,21 @@ __global__ void __launch_bounds__(512) contra3_kernel(const double *__restrict__
   }
 }
 
-// Launch of contra3_kernel over nblocks blocks (grid: tile orbits x blocks).
+// Launch of contra3_kernel over nblocks blocks (grid: tile orbits x blocks);
+// f32: the arrays hold binary32 elements (the split-precision mode's storage).
 cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int nv,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool f32) {
   if (nblocks <= 0 || nv <= 0) return cudaSuccess;
   const long long nv3 = (long long)nv * nv * nv;
   const long long nt = (nv + 7) / 8, norb = nt * (nt + 1) * (nt + 2) / 6;
   for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
     const long long nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
-    contra3_kernel<<<dim3((unsigned)norb, (unsigned)nb), 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3,
-                                                                       nb, nv);
+    const dim3 grid((unsigned)norb, (unsigned)nb);
+    if (f32)
+      contra3_kernel<float><<<grid, 512, 0, st>>>(reinterpret_cast<const float *>(X) + b0 * nv3,
+                                                  reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
+    else
+      contra3_kernel<double><<<grid, 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3, nb, nv);
   }
   return cudaGetLastError();
 }
@@ -639,7 +651,7 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     const float *__restrict__ W, const TripItem *__restrict__ items, int nitems,
     const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
     unsigned long long nvinv, double omega_v, const double *__restrict__ omega_p,
-    double *__restrict__ out, int *__restrict__ status) {
+    double *__restrict__ out, int out32, int *__restrict__ status) {
   // one (term, permutation) pair: the operand indices are linear in the
   // element's canonical coordinates (x0, x1, x2) with coefficients ca / cb
   struct Ent {
@@ -750,14 +762,15 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
       df_add(dh, dl, ev[x2[k]].x, ev[x2[k]].y);
       df_add(dh, dl, eoh, eol);
       const float den = dh + dl;
-      double val;
-      if (fabsf(den) < 1e-3f) {
+      float q = 0.f;
+      if (fabsf(den) < 1e-3f)
         atomicOr(status, 1);
-        val = 0.0;
-      } else {
-        val = widen_f32(-acc[k] * __frcp_rn(den));
-      }
-      out[it.off + r] = val;
+      else
+        q = -acc[k] * __frcp_rn(den);
+      if (out32)  // binary32 storage of the split-precision mode
+        reinterpret_cast<float *>(out)[it.off + r] = q;
+      else
+        out[it.off + r] = widen_f32(q);
     }
   }
 }
@@ -791,7 +804,7 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
   const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
   const long long K = (long long)K1 * K2 * K3;
   const long long m1 = m / p.M2, m2 = m % p.M2;
-  const double *A = p.A + it.offA + m1 * it.sA[0] + m2 * it.sA[1];
+  const long long offA = it.offA + m1 * it.sA[0] + m2 * it.sA[1];
   const double *B = p.B + it.offB;
   const long long a1 = it.sA[2], a2 = it.sA[3], a3 = it.sA[4];
   const long long b1 = it.sB[0], b2 = it.sB[1], b3 = it.sB[2];
@@ -801,7 +814,7 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
   for (long long k = lane; k < K; k += 32) {
-    s += A[k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+    s += ld_op<double>(p.A, p.a32, offA + k1 * a1 + k2 * a2 + k3 * a3) * B[k1 * b1 + k2 * b2 + k3 * b3];
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {

@@ -25,6 +25,7 @@ struct BstcParams {
   int nitems;
   int atomic;        // 1: accumulate with atomicAdd (items may overlap in C)
   long long kchunk;  // split-K: grid.z slices of this many K elements (0 = whole K)
+  int a32, b32;      // 1: A (B) holds binary32 elements (element offsets and strides as given)
 };
 
 // One additive term of the pre-permutation triples expression V^{abc}_{ijk}

@@ -693,7 +693,8 @@ int tc_tile_width(long long n) { return n <= 64 ? 64 : n <= 128 ? 128 : n <= 160
 
 // Four consecutive outputs of a split: hi[0..3] and lo[0..3] as one 8-byte store
 // each (the destination index is a multiple of 4 in a 256-byte aligned array).
-__device__ __forceinline__ void split4_store(const double *x, __nv_bfloat16 *hi,
+template <typename Tin>
+__device__ __forceinline__ void split4_store(const Tin *x, __nv_bfloat16 *hi,
                                              __nv_bfloat16 *lo) {
   unsigned int hb[4], lb[4];
 #pragma unroll
@@ -711,10 +712,13 @@ __device__ __forceinline__ void split4_store(const double *x, __nv_bfloat16 *hi,
 // out[o0][o1][o2][o3] (o3 < K3p, zero for o3 >= K3) = scale * in[o0 s0 + o1 s1 + o2 s2 + o3 s3].
 // K3p is a multiple of 4.  Groups of 64 threads take one output row (o0, o1,
 // o2) at a time, each thread four consecutive o3 per step.
-__global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
-                                  __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
-                                  long long D2, long long K3, long long K3p, long long s0,
-                                  long long s1, long long s2, long long s3, double scale) {
+// Tin: binary64 or binary32 input (the split-precision mode stores its triples
+// arrays in binary32).
+template <typename Tin>
+__device__ __forceinline__ void split_bf16_body(const Tin *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                                __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                                long long D2, long long K3, long long K3p, long long s0,
+                                                long long s1, long long s2, long long s3, double scale) {
   const int mode = scale == 1.0 ? 0 : scale == -1.0 ? 1 : 2;
   const long long rows = D0 * D1 * D2;
   const int g = threadIdx.x / 64, t = threadIdx.x % 64;
@@ -722,16 +726,30 @@ __global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *
   for (long long r = (long long)blockIdx.x * 4 + g; r < rows; r += (long long)gridDim.x * 4) {
     const long long o2 = r % D2, r1 = r / D2;
     const long long o1 = r1 % D1, o0 = r1 / D1;
-    const double *src = in + o0 * s0 + o1 * s1 + o2 * s2;
+    const Tin *src = in + o0 * s0 + o1 * s1 + o2 * s2;
     __nv_bfloat16 *h = hi + r * K3p, *l = lo + r * K3p;
     for (int k = 4 * t; k < k3p; k += 256) {
-      double x[4];
+      Tin x[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : 0.0;
+        x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : Tin(0);
       split4_store(x, h + k, l + k);
     }
   }
+}
+
+__global__ void split_bf16_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                  __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                  long long D2, long long K3, long long K3p, long long s0,
+                                  long long s1, long long s2, long long s3, double scale) {
+  split_bf16_body(in, hi, lo, D0, D1, D2, K3, K3p, s0, s1, s2, s3, scale);
+}
+
+__global__ void split_bf16_f32_kernel(const float *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                      __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                      long long D2, long long K3, long long K3p, long long s0,
+                                      long long s1, long long s2, long long s3, double scale) {
+  split_bf16_body(in, hi, lo, D0, D1, D2, K3, K3p, s0, s1, s2, s3, scale);
 }
 
 }  // namespace mlcc3
@@ -741,24 +759,25 @@ namespace mlcc3 {
 // Split with a two-level K: out[o0][o1][k] for k = k1 K2 + k2 < K1 K2 (zero up
 // to Kp, a multiple of 4) = scale * in[o0 s0 + o1 s1 + k1 sk1 + k2 sk2].  Each
 // thread takes four consecutive k per step, dividing k by K2 once.
-__global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
-                                     __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
-                                     long long K1, long long K2, long long Kp, long long s0,
-                                     long long s1, long long sk1, long long sk2, double scale) {
+template <typename Tin>
+__device__ __forceinline__ void split_bf16_k2_body(const Tin *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                                   __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                                   long long K1, long long K2, long long Kp, long long s0,
+                                                   long long s1, long long sk1, long long sk2, double scale) {
   const int mode = scale == 1.0 ? 0 : scale == -1.0 ? 1 : 2;
   const long long rows = D0 * D1;
   const int g = threadIdx.x / 64, t = threadIdx.x % 64;
   const int kk2 = (int)K2, K = (int)(K1 * K2), kp = (int)Kp;
   for (long long r = (long long)blockIdx.x * 4 + g; r < rows; r += (long long)gridDim.x * 4) {
     const long long o1 = r % D1, o0 = r / D1;
-    const double *src = in + o0 * s0 + o1 * s1;
+    const Tin *src = in + o0 * s0 + o1 * s1;
     __nv_bfloat16 *h = hi + r * Kp, *l = lo + r * Kp;
     for (int k = 4 * t; k < kp; k += 256) {
       int q1 = k / kk2, q2 = k - q1 * kk2;
-      double x[4];
+      Tin x[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        x[j] = k + j < K ? scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale) : 0.0;
+        x[j] = k + j < K ? scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale) : Tin(0);
         if (++q2 == kk2) {
           q2 = 0;
           ++q1;
@@ -767,6 +786,20 @@ __global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat1
       split4_store(x, h + k, l + k);
     }
   }
+}
+
+__global__ void split_bf16_k2_kernel(const double *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                     __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                     long long K1, long long K2, long long Kp, long long s0,
+                                     long long s1, long long sk1, long long sk2, double scale) {
+  split_bf16_k2_body(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2, scale);
+}
+
+__global__ void split_bf16_k2_f32_kernel(const float *__restrict__ in, __nv_bfloat16 *__restrict__ hi,
+                                         __nv_bfloat16 *__restrict__ lo, long long D0, long long D1,
+                                         long long K1, long long K2, long long Kp, long long s0,
+                                         long long s1, long long sk1, long long sk2, double scale) {
+  split_bf16_k2_body(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2, scale);
 }
 
 }  // namespace mlcc3
@@ -778,23 +811,24 @@ namespace mlcc3 {
 // through 32 x 32 shared-memory tiles, so that both the FP64 reads (along c) and
 // the bf16 writes (along r) are coalesced.  Blocks of 32 x 8 threads loop over
 // (batch, tile) pairs.
+template <typename Tin>
 __global__ void __launch_bounds__(256) split_transpose_kernel(
-    const double *__restrict__ src, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+    const Tin *__restrict__ src, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
     long long B, int R, int Rp, int C, long long sb, long long sr, long long db, long long dr) {
-  __shared__ double tile[32][33];
+  __shared__ Tin tile[32][33];
   const int tr = (Rp + 31) / 32, tc = (C + 31) / 32;
   const long long ntiles = B * (long long)tr * tc;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   // rows ty, ty + 8, ty + 16, ty + 24 of tile q, column tx, into registers: the
   // next tile's loads are issued before this tile's stores
-  double pf[4];
+  Tin pf[4];
   auto load = [&](long long q) {
     const long long b = q / ((long long)tr * tc);
     const int r0 = (int)((q / tc) % tr) * 32, c = (int)(q % tc) * 32 + tx;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int r = r0 + ty + 8 * k;
-      pf[k] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : 0.0;
+      pf[k] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : Tin(0);
     }
   };
   if (blockIdx.x < ntiles) load(blockIdx.x);
@@ -812,7 +846,7 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
       const int ci = threadIdx.x >> 3, rq = 4 * (threadIdx.x & 7);
       const int c = c0 + ci, r = r0 + rq;
       if (c < C && r < Rp) {
-        const double x[4] = {tile[rq][ci], tile[rq + 1][ci], tile[rq + 2][ci], tile[rq + 3][ci]};
+        const Tin x[4] = {tile[rq][ci], tile[rq + 1][ci], tile[rq + 2][ci], tile[rq + 3][ci]};
         const long long o = b * db + (long long)c * dr + r;
         split4_store(x, hi + o, lo + o);
       }
@@ -822,11 +856,15 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
 
 cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
                             int R, int Rp, int C, long long sb, long long sr, long long db,
-                            long long dr, cudaStream_t st) {
+                            long long dr, cudaStream_t st, bool in32) {
   const long long ntiles = B * (long long)((Rp + 31) / 32) * ((C + 31) / 32);
   if (ntiles <= 0) return cudaSuccess;
   const long long g = ntiles < 152LL * 16 ? ntiles : 152LL * 16;
-  split_transpose_kernel<<<(int)g, 256, 0, st>>>(src, hi, lo, B, R, Rp, C, sb, sr, db, dr);
+  if (in32)
+    split_transpose_kernel<float><<<(int)g, 256, 0, st>>>(reinterpret_cast<const float *>(src), hi, lo,
+                                                          B, R, Rp, C, sb, sr, db, dr);
+  else
+    split_transpose_kernel<double><<<(int)g, 256, 0, st>>>(src, hi, lo, B, R, Rp, C, sb, sr, db, dr);
   return cudaGetLastError();
 }
 

@@ -46,8 +46,7 @@ __global__ void mirror_pairs_kernel(double *, int, int);
 __global__ void to_f32_kernel(const double *, float *, long long);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
-__global__ void contra3_kernel(const double *, double *, long long, int);
-cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t);
+cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t, bool);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 __global__ void c2_block_kernel(const double *, double *, int, int, int, int);
 __global__ void delta_block_kernel(const double *, double *, int, int, int, int);
@@ -58,19 +57,20 @@ __global__ void density_norm_kernel(double *, const double *, const double *, co
                                     int, int);
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
                                       const double *, const float2 *, int, unsigned long long,
-                                      double, const double *, double *, int *);
+                                      double, const double *, double *, int, int *);
 __global__ void hilo_kernel(const double *, float2 *, int);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
-                       long long s1, long long s2, long long s3, double scale, cudaStream_t st);
+                       long long s1, long long s2, long long s3, double scale, cudaStream_t st,
+                       bool in32 = false);
 cudaError_t split_gt_launch(const double *G, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int no, int NV,
                             int nv, int Kp, long long gk, long long gb, long long gc, int swap,
                             const double *F, double fcoef, cudaStream_t st);
 cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
                             int R, int Rp, int C, long long sb, long long sr, long long db,
-                            long long dr, cudaStream_t st);
+                            long long dr, cudaStream_t st, bool in32);
 cudaError_t launch_tc_gemm(int BN, const TcMaps &maps, const TcItem *items, const TcSeg *segs,
                            int nitems, const TcEpi &epi, int *status, cudaStream_t stream,
                            int persist_from);
@@ -78,7 +78,7 @@ int tc_tile_width(long long n);
 cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                           long long D1, long long K1, long long K2, long long Kp, long long s0,
                           long long s1, long long sk1, long long sk2, double scale,
-                          cudaStream_t st);
+                          cudaStream_t st, bool in32 = false);
 
 static thread_local std::string g_last_error;
 
@@ -111,6 +111,7 @@ void *mlcc3_ctx::raw(const std::string &name, size_t bytes) {
     check_cuda(cudaStreamSynchronize(stream), "sync before realloc");
     cudaFree(it->second.first);
     scratch.erase(it);
+    tri_regs.erase(name);
   }
   void *p = nullptr;
   check_cuda(cudaMalloc(&p, bytes < 256 ? 256 : bytes), ("cudaMalloc " + name).c_str());
@@ -139,12 +140,32 @@ void mlcc3_ctx::release() {
     f32s[t] = TriSlot{};
   }
   gens.clear();
+  tri_regs.clear();
   tau_valid = false;
   tau_key.clear();
 }
 
 double *mlcc3_ctx::buf(const std::string &name, size_t n) {
   return static_cast<double *>(raw(name, n * sizeof(double)));
+}
+
+double *mlcc3_ctx::tri_buf(const std::string &name, size_t n) {
+  const size_t bytes = n * (tri32 ? sizeof(float) : sizeof(double));
+  void *p = raw(name, bytes);
+  tri_regs[name] = {static_cast<const char *>(p), bytes};
+  return static_cast<double *>(p);
+}
+
+bool mlcc3_ctx::is_tri32(const void *p) const {
+  if (!tri32) return false;
+  const char *q = static_cast<const char *>(p);
+  for (auto &kv : tri_regs)
+    if (q >= kv.second.first && q < kv.second.first + kv.second.second) return true;
+  return false;
+}
+
+void mlcc3_ctx::zero_tri(double *p, size_t n) {
+  check_cuda(cudaMemsetAsync(p, 0, n * (tri32 ? sizeof(float) : sizeof(double)), stream), "zero");
 }
 
 cudaEvent_t mlcc3_ctx::get_event() {
@@ -261,6 +282,8 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
   p.items = it;
   p.nitems = nitems;
   p.atomic = atomic ? 1 : 0;
+  p.a32 = is_tri32(A) ? 1 : 0;
+  p.b32 = is_tri32(B) ? 1 : 0;
   long long M = sh.M1 * sh.M2, N = sh.N1 * sh.N2;
   if (M == 0 || N == 0 || sh.K1 * sh.K2 * sh.K3 == 0) return;
   // split-precision mode: FP32 products with FP64 sums, except where a caller
@@ -326,6 +349,8 @@ void mlcc3_ctx::dot(const double *A, const double *B, double *C, const Shape &sh
   p.alpha = alpha;
   p.items = it;
   p.nitems = nitems;
+  p.a32 = is_tri32(A) ? 1 : 0;
+  p.b32 = is_tri32(B) ? 1 : 0;
   // long dots over few items: split K across blocks (partial sums added atomically)
   const long long K = sh.K1 * sh.K2 * sh.K3;
   long long ys = std::min<long long>(K / (256 * 64), (4 * 152 + nitems - 1) / nitems);
@@ -471,8 +496,9 @@ std::vector<TripItem> shard_of(const std::vector<TripItem> &list, int count, int
 // context's persistent arrays exist, at 156 bytes per block element: the
 // eight FP64 triples arrays the passes keep (tau, R3, L3, lambda3 and their
 // contravariant forms) plus up to 18 cached split-precision layouts of
-// triples arrays (tri_layout) and four FP32 copies (tri_f32); scratch buffers
-// persist across calls, so one size serves all).
+// triples arrays (tri_layout) and four FP32 copies (tri_f32); 108 bytes in the
+// split mode, whose triples arrays are binary32 and need no copies; scratch
+// buffers persist across calls, so one size serves all).
 void make_chunks(mlcc3_ctx *c) {
   c->chunk_gen += 1;
   c->tau_key.clear();
@@ -485,7 +511,9 @@ void make_chunks(mlcc3_ctx *c) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)40 << 30;
     const double budget = 0.5 * (double)fr;
-    part_max = group_max = std::max<long long>(1, (long long)(budget / (156.0 * (double)nv3)));
+    // binary32 triples arrays in the split mode (and no separate FP32 copies)
+    const double per_elem = c->tri32 ? 108.0 : 156.0;
+    part_max = group_max = std::max<long long>(1, (long long)(budget / (per_elem * (double)nv3)));
   }
   const std::string g = "#" + std::to_string(c->chunk_gen);
   auto partition = [&](const std::vector<TripItem> &list, const std::string &tag) {
@@ -597,7 +625,7 @@ void contra3(mlcc3_ctx *c, const double *X, double *Xt, long long nblocks) {
   c->wrote(Xt);
   if (nblocks <= 0 || c->nv == 0) return;
   c->launch("contra3_kernel", 0.0, [&] {
-    check_cuda(launch_contra3(X, Xt, nblocks, (int)c->nv, c->stream), "contra3");
+    check_cuda(launch_contra3(X, Xt, nblocks, (int)c->nv, c->stream, c->tri32), "contra3");
   });
 }
 
@@ -1137,7 +1165,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     c->launch("triples_finish_kernel", 0.0, [&] {
       triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps, ehl,
                                                          (int)s.nv, nvinv, omega, c->omega_dev,
-                                                         out, c->status);
+                                                         out, c->tri32 ? 1 : 0, c->status);
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
@@ -1365,18 +1393,18 @@ std::pair<void *, void *> tri_layout(mlcc3_ctx *c, const double *X, int L) {
       const long long sr = L == 2 ? s.nv : L == 3 ? s.nv * s.nv : s.nv;
       const long long db = (long long)C * Kp;
       c->launch("split_transpose_kernel", 0.0, [&] {
-        check_cuda(split_transpose(X, h, l, B, R, (int)Kp, C, sb, sr, db, Kp, c->stream),
-                   "split_transpose");
+        check_cuda(split_transpose(X, h, l, B, R, (int)Kp, C, sb, sr, db, Kp, c->stream,
+                                   c->is_tri32(X)), "split_transpose");
       });
     } else if (xl)
       c->launch("split_bf16_k2_kernel", 0.0, [&] {
         check_cuda(split_bf16_k2(X, h, l, nb, s.nv, s.nv, s.nv, Kp, s.nv3, cs[k], cs[a], cs[b], 1.0,
-                                 c->stream), "split_bf16_k2");
+                                 c->stream, c->is_tri32(X)), "split_bf16_k2");
       });
     else
       c->launch("split_bf16_kernel", 0.0, [&] {
         check_cuda(split_bf16(X, h, l, nb, s.nv, s.nv, s.nv, Kp, s.nv3, cs[a], cs[b], cs[k], 1.0,
-                              c->stream), "split_bf16");
+                              c->stream, c->is_tri32(X)), "split_bf16");
       });
   }
   return {hi, lo};
@@ -1756,8 +1784,8 @@ float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long
 void build_tau(mlcc3_ctx *c, const Chunk &ch, double **tau, double **taut) {
   S s(c);
   c->chunk_nb = ch.nb;
-  *tau = c->buf("tau", (size_t)ch.nb * s.nv3);
-  *taut = c->buf("taut", (size_t)ch.nb * s.nv3);
+  *tau = c->tri_buf("tau", (size_t)ch.nb * s.nv3);
+  *taut = c->tri_buf("taut", (size_t)ch.nb * s.nv3);
   if (c->tau_valid && c->tau_key == ch.key) return;
   c->tau_valid = true;
   c->tau_key = ch.key;
@@ -1989,8 +2017,8 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
       const Chunk &ch = chunks[q];
       double *tau, *taut;
       build_tau(c, ch, &tau, &taut);
-      double *R3 = c->buf("R3", (size_t)ch.nb * s.nv3);
-      double *R3t = c->buf("R3t", (size_t)ch.nb * s.nv3);
+      double *R3 = c->tri_buf("R3", (size_t)ch.nb * s.nv3);
+      double *R3t = c->tri_buf("R3t", (size_t)ch.nb * s.nv3);
       // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
       c->omega_dev = omega_dev ? omega_dev + v : nullptr;
       right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3);
@@ -2058,8 +2086,8 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
     for (const Chunk &ch : chunks) {
       double *tau, *taut;
       build_tau(c, ch, &tau, &taut);
-      double *L3 = c->buf("L3", (size_t)ch.nb * s.nv3);
-      double *L3t = c->buf("L3t", (size_t)ch.nb * s.nv3);
+      double *L3 = c->tri_buf("L3", (size_t)ch.nb * s.nv3);
+      double *L3t = c->tri_buf("L3t", (size_t)ch.nb * s.nv3);
       const std::vector<Ord> &os = ch.own;
       const std::string okey = "o" + ch.key;
       // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
@@ -2270,6 +2298,7 @@ namespace {
 // FP32 copy of the triples array X (chunk_nb blocks), made at most once per
 // write of X and kept in one of four slots (least recently used reused).
 const float *tri_f32(mlcc3_ctx *c, const double *X) {
+  if (c->is_tri32(X)) return reinterpret_cast<const float *>(X);  // binary32 storage already
   S s(c);
   const unsigned long long g = c->gen_of(X);
   int q = -1;
@@ -2532,20 +2561,20 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     build_tau(c, ch, &tau, &taut);
     // lambda3 (omega = 0) and its contravariant form; lambda3 itself is dead once
     // the contravariant form exists, so L3 reuses its buffer
-    double *lam3 = c->buf("L3", bw);
-    double *lt3 = c->buf("lam3t", bw);
+    double *lam3 = c->tri_buf("L3", bw);
+    double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
     // L3 (omega) and R3 (omega), with their contravariant forms (CVS: core batches only)
-    double *L3 = c->buf("L3", bw);
-    double *L3t = c->buf("L3t", bw);
-    if (cvs) c->zero(L3, bw);
+    double *L3 = c->tri_buf("L3", bw);
+    double *L3t = c->tri_buf("L3t", bw);
+    if (cvs) c->zero_tri(L3, bw);
     const std::string bkey3 = cvs ? bkey + "cvs" : bkey;  // the batch list is cached per key
     left_triples(c, "L", L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3);
     contra3(c, L3, L3t, ch.nb);
-    double *R3 = c->buf("R3", bw);
-    double *R3t = c->buf("R3t", bw);
-    if (cvs) c->zero(R3, bw);
+    double *R3 = c->tri_buf("R3", bw);
+    double *R3t = c->tri_buf("R3t", bw);
+    if (cvs) c->zero_tri(R3, bw);
     right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3);
     contra3(c, R3, R3t, ch.nb);
     // D^{0-0} and D^{m-0}
@@ -2718,8 +2747,8 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     const long long bw = ch.nb * s.nv3;
     double *tau, *taut;
     build_tau(c, ch, &tau, &taut);
-    double *lam3 = c->buf("lam3", bw);
-    double *lt3 = c->buf("lam3t", bw);
+    double *lam3 = c->tri_buf("lam3", bw);
+    double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
     density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
@@ -2771,6 +2800,7 @@ extern "C" int mlcc3_create(mlcc3_ctx **out, const mlcc3_dims *d, int precision,
     c->NJ = d->n_chol;
     c->nmo = c->NO + c->NV;
     c->precision = precision;
+    c->tri32 = precision == MLCC3_SPLIT_BF16X3;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->device = dev;
     if (d->core_mask) c->core.assign(d->core_mask, d->core_mask + d->n_occ);
@@ -2955,6 +2985,15 @@ extern "C" int mlcc3_debug_fetch(mlcc3_ctx *c, const char *name, double *host, s
       if (it == c->scratch.end()) throw Error{MLCC3_ERR_ARG, "unknown buffer " + nm};
       src = static_cast<const double *>(it->second.first);
       have = it->second.second / sizeof(double);
+      if (c->is_tri32(src)) {  // binary32 storage: widened on the host
+        if (n > it->second.second / sizeof(float)) throw Error{MLCC3_ERR_ARG, "fetch larger than buffer"};
+        std::vector<float> tmp(n);
+        check_cuda(cudaMemcpyAsync(tmp.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost,
+                                   c->stream), "fetch");
+        check_cuda(cudaStreamSynchronize(c->stream), "fetch sync");
+        for (size_t q = 0; q < n; ++q) host[q] = (double)tmp[q];
+        return;
+      }
     }
     if (n > have) throw Error{MLCC3_ERR_ARG, "fetch larger than buffer"};
     check_cuda(cudaMemcpyAsync(host, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),

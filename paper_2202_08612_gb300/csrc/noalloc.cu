@@ -22,7 +22,7 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
 __global__ void triples_build_kernel(const TripTerms, const TripItem *, const double *, int, int,
                                      double, const double *, double *, int *);
-cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t);
+cudaError_t launch_contra3(const double *, double *, long long, int, cudaStream_t, bool);
 __global__ void finalize_doubles_kernel(const double *, double *, int, int, int, int, int);
 }  // namespace mlcc3
 
@@ -187,7 +187,7 @@ extern "C" int mlcc3_triples_omega_static(mlcc3_ctx *c, double *omega1, double *
     return MLCC3_ERR_CUDA;
   };
   if (!chk(cudaGetLastError(), "triples_build launch") ||
-      !chk(launch_contra3(tau, taut, nb, (int)nv, st), "contra3"))
+      !chk(launch_contra3(tau, taut, nb, (int)nv, st, false), "contra3"))
     return drained();
   // scratch keeps the previous call's contents: clear the accumulators
   if (!chk(cudaMemsetAsync(Zb, 0, sizeof(double) * blk, st), "memset Zb") ||

@@ -23,6 +23,9 @@ int tc_tile_width(long long n);
 __global__ void split_bf16_kernel(const double *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
                                   long long, long long, long long, long long, long long, long long,
                                   long long, long long, double);
+__global__ void split_bf16_f32_kernel(const float *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
+                                      long long, long long, long long, long long, long long,
+                                      long long, long long, long long, double);
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::mutex g_encode_mutex;
@@ -59,15 +62,21 @@ bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[
   return true;
 }
 
+// in32: `in` holds binary32 elements (element strides as given).
 cudaError_t split_bf16(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                        long long D1, long long D2, long long K3, long long K3p, long long s0,
-                       long long s1, long long s2, long long s3, double scale, cudaStream_t st) {
+                       long long s1, long long s2, long long s3, double scale, cudaStream_t st,
+                       bool in32) {
   const long long rows = D0 * D1 * D2;  // four rows per block at a time
   if (rows <= 0 || K3p <= 0) return cudaSuccess;
   long long g = (rows + 3) / 4;
   if (g > 152LL * 64) g = 152LL * 64;
-  split_bf16_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, D2, K3, K3p, s0, s1, s2, s3,
-                                             scale);
+  if (in32)
+    split_bf16_f32_kernel<<<(int)g, 256, 0, st>>>(reinterpret_cast<const float *>(in), hi, lo, D0, D1,
+                                                   D2, K3, K3p, s0, s1, s2, s3, scale);
+  else
+    split_bf16_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, D2, K3, K3p, s0, s1, s2, s3,
+                                               scale);
   return cudaGetLastError();
 }
 
@@ -107,8 +116,8 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
   mem.push_back(status);
   cudaMemset(status, 0, sizeof(int));
   cudaStream_t st = 0;
-  if (split_bf16(A, buf[0], buf[1], 1, 1, M, K, Kp, 0, 0, K, 1, 1.0, st) != cudaSuccess ||
-      split_bf16(B, buf[2], buf[3], 1, 1, N, K, Kp, 0, 0, K, 1, 1.0, st) != cudaSuccess)
+  if (split_bf16(A, buf[0], buf[1], 1, 1, M, K, Kp, 0, 0, K, 1, 1.0, st, false) != cudaSuccess ||
+      split_bf16(B, buf[2], buf[3], 1, 1, N, K, Kp, 0, 0, K, 1, 1.0, st, false) != cudaSuccess)
     return fail(MLCC3_ERR_CUDA, "split");
   const int BN = tc_tile_width(N);
   TcMaps maps{};
@@ -181,17 +190,24 @@ namespace mlcc3 {
 __global__ void split_bf16_k2_kernel(const double *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
                                      long long, long long, long long, long long, long long,
                                      long long, long long, long long, double);
+__global__ void split_bf16_k2_f32_kernel(const float *, __nv_bfloat16 *, __nv_bfloat16 *, long long,
+                                         long long, long long, long long, long long, long long,
+                                         long long, long long, long long, double);
 
 cudaError_t split_bf16_k2(const double *in, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long D0,
                           long long D1, long long K1, long long K2, long long Kp, long long s0,
                           long long s1, long long sk1, long long sk2, double scale,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool in32) {
   const long long rows = D0 * D1;  // four rows per block at a time
   if (rows <= 0 || Kp <= 0) return cudaSuccess;
   long long g = (rows + 3) / 4;
   if (g > 152LL * 64) g = 152LL * 64;
-  split_bf16_k2_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2,
-                                                scale);
+  if (in32)
+    split_bf16_k2_f32_kernel<<<(int)g, 256, 0, st>>>(reinterpret_cast<const float *>(in), hi, lo, D0,
+                                                      D1, K1, K2, Kp, s0, s1, sk1, sk2, scale);
+  else
+    split_bf16_k2_kernel<<<(int)g, 256, 0, st>>>(in, hi, lo, D0, D1, K1, K2, Kp, s0, s1, sk1, sk2,
+                                                  scale);
   return cudaGetLastError();
 }
 }  // namespace mlcc3
