@@ -873,16 +873,17 @@ WHOLE = {"betaine_like": (100, 1000, 20, 150, 4000, 2, 1)}
 
 def whole_step_flops(NO, NV, no, nv, nval, ncore):
     """Algorithmic flops of one whole step (the paper's leading counts, Sec. 3):
-    Omega once, rho + sigma + D^{m-0} + D^{0-0} + D^{0-m} per valence state
-    (units N_V n_v^3 n_o^3); a core state's rho and sigma with the paper's CVS
-    count (8 N_V n_v^3 n_o^2 each), its D^{m-0} and D^{0-m}, which read the
-    CVS-restricted L3 and R3, reduced the same way (units N_V n_v^3 n_o^2),
-    and its D^{0-0}, which the skip rule does not touch, in full."""
+    Omega once; rho + sigma + D^{m-0} + D^{0-m} per valence state and D^{0-0}
+    once for all of them (one densities call; D^{0-0} does not depend on the
+    state) (units N_V n_v^3 n_o^3); a core state's rho and sigma with the
+    paper's CVS count (8 N_V n_v^3 n_o^2 each), its D^{m-0} and D^{0-m}, which
+    read the CVS-restricted L3 and R3, reduced the same way (units
+    N_V n_v^3 n_o^2), and the D^{0-0} its own densities call builds, in full."""
     F = FLOP_UNITS
     u3, u2 = NV * nv ** 3 * no ** 3, NV * nv ** 3 * no ** 2
-    val = (F["rho"] + F["sigma"] + F["D_m0"] + F["D_00"] + F["D_0m"]) * u3
+    val = (F["rho"] + F["sigma"] + F["D_m0"] + F["D_0m"]) * u3
     core = (F["rho"] + F["sigma"] + F["D_m0"] + F["D_0m"]) * u2 + F["D_00"] * u3
-    return F["omega"] * u3 + nval * val + ncore * core
+    return (F["omega"] + (F["D_00"] if nval else 0)) * u3 + nval * val + ncore * core
 
 
 class WholeProblem:
@@ -900,8 +901,8 @@ class WholeProblem:
         o = {"o1": z(x["R1"][0]), "o2": z(x["t2c"]),
              "rho1": z(x["R1"][:nval]), "rho2": z(x["R2"][:nval]),
              "sig1": z(x["R1"][:nval]), "sig2": z(x["R2"][:nval]),
-             "D": [z(x["mu"][0]) for _ in range(3)]}
-        assert o["D"][0].shape == (nmo, nmo)
+             "D00": z(x["mu"][0]), "Dm0": z(x["mu"][:nval]), "D0m": z(x["mu"][:nval])}
+        assert o["D00"].shape == (nmo, nmo)
         return o
 
     def step(self, ctx, x, o, tally=None):
@@ -920,21 +921,27 @@ class WholeProblem:
         t("in", x["R1"][:nv_], x["R2"][:nv_], x["L1"][:nv_], x["L2"][:nv_])
         t("out", o["rho1"], o["rho2"], o["sig1"], o["sig2"])
         fs = []
-        for n in range(nv_ + self.ncore):
-            if n == nv_:
+        for sl in (slice(0, nv_), slice(nv_, nv_ + self.ncore)):   # valence, then core states
+            m = sl.stop - sl.start
+            if m == 0:
+                continue
+            if sl.start == nv_:
                 ctx.set_param("cvs", 1)
-                sl = slice(n, n + 1)
-                ctx.jacobian_right(w[sl], x["R1"][sl], x["R2"][sl], o["rho1"][:1], o["rho2"][:1])
-                ctx.jacobian_left(w[sl], x["L1"][sl], x["L2"][sl], o["sig1"][:1], o["sig2"][:1])
+                ctx.jacobian_right(w[sl], x["R1"][sl], x["R2"][sl], o["rho1"][:m], o["rho2"][:m])
+                ctx.jacobian_left(w[sl], x["L1"][sl], x["L2"][sl], o["sig1"][:m], o["sig2"][:m])
                 t("in", x["R1"][sl], x["R2"][sl], x["L1"][sl], x["L2"][sl])
-                t("out", o["rho1"][:1], o["rho2"][:1], o["sig1"][:1], o["sig2"][:1])
-            wn = float(w[n])
-            ctx.transition_density(wn, x["lam1"], x["lam2"], x["R1"][n], x["R2"][n], x["L1"][n],
-                                   x["L2"][n], x["D00_in"], *o["D"])
-            fs.append(ctx.oscillator_strength(wn, o["D"][2], o["D"][1], x["mu"]))
-            t("in", x["lam1"], x["lam2"], x["R1"][n], x["R2"][n], x["L1"][n], x["L2"][n],
-              x["D00_in"], x["mu"])
-            t("out", *o["D"])
+                t("out", o["rho1"][:m], o["rho2"][:m], o["sig1"][:m], o["sig2"][:m])
+            # the densities of the group's states in one call (tau, lambda3, D^{0-0} shared)
+            ctx.transition_densities(w[sl], x["lam1"], x["lam2"], x["R1"][sl], x["R2"][sl],
+                                     x["L1"][sl], x["L2"][sl], x["D00_in"], o["D00"],
+                                     o["Dm0"][:m], o["D0m"][:m])
+            t("in", x["lam1"], x["lam2"], x["R1"][sl], x["R2"][sl], x["L1"][sl], x["L2"][sl],
+              x["D00_in"])
+            t("out", o["D00"], o["Dm0"][:m], o["D0m"][:m])
+            for k in range(m):
+                fs.append(ctx.oscillator_strength(float(w[sl.start + k]), o["D0m"][k], o["Dm0"][k],
+                                                  x["mu"]))
+                t("in", x["mu"])
         ctx.set_param("cvs", 1)
         return fs
 
@@ -970,7 +977,7 @@ def whole_fp64_comparison(NO, NV, no_s, nv, NJ, nval, ncore, dev, stream):
         fs = []
         for n in (0, nval):
             ctx.set_param("cvs", 1 if n >= nval else 0)
-            D = [torch.zeros_like(d) for d in o["D"]]
+            D = [torch.zeros_like(o["D00"]) for _ in range(3)]
             ctx.transition_density(float(omega[n]), x["lam1"], x["lam2"], x["R1"][n], x["R2"][n],
                                    x["L1"][n], x["L2"][n], x["D00_in"], *D)
             D[2][NO:, :NO] += x["R1"][n]
@@ -986,8 +993,7 @@ def whole_fp64_comparison(NO, NV, no_s, nv, NJ, nval, ncore, dev, stream):
         sd = float((x["L1"][0] * d1 * x["R1"][0]).sum() + (w_ * x["L2"][0] * d2 * x["R2"][0]).sum())
         rq = ctx.rayleigh_quotient(float(omega[0]), x["R1"][0], x["R2"][0], x["L1"][0], x["L2"][0], sd)
         res[name] = {"ms": e0.elapsed_time(e1), "f": fs, "rq": rq,
-                     "out": {k: (v.cpu().numpy() if not isinstance(v, list) else [d.cpu().numpy() for d in v])
-                             for k, v in o.items()}}
+                     "out": {k: v.cpu().numpy() for k, v in o.items()}}
         ctx.close()
         del o
         torch.cuda.empty_cache()
@@ -995,9 +1001,8 @@ def whole_fp64_comparison(NO, NV, no_s, nv, NJ, nval, ncore, dev, stream):
 
     def nrm(u, v):
         return float(np.abs(u - v).max() / max(np.abs(v).max(), 1e-300))
-    errs = {k: nrm(a["out"][k], b["out"][k]) for k in ("o1", "o2", "rho1", "rho2", "sig1", "sig2")}
-    for i, k in enumerate(("D00", "Dm0", "D0m")):
-        errs[k] = nrm(a["out"]["D"][i], b["out"]["D"][i])
+    errs = {k: nrm(a["out"][k], b["out"][k])
+            for k in ("o1", "o2", "rho1", "rho2", "sig1", "sig2", "D00", "Dm0", "D0m")}
     del x
     torch.cuda.empty_cache()
     return {"subset": f"N_O={NO} N_V={NV} n_o={no_s} n_v={nv} N_J={NJ} (the workload with the active "
@@ -1186,11 +1191,12 @@ def run_whole(args, rank, world, local_rank):
                                        f"core orbital at -10 Ha, {nval} valence + {ncore} core (CVS) "
                                        "state(s)",
                            "step": "integral build, Omega, rho and sigma of the valence vectors, "
-                                   "D^{0-0}, D^{m-0}, D^{0-m} and f of each valence state, rho, sigma, "
-                                   "densities and f of the core state",
-                           "flop_count": "Omega 4 + 52 per valence state (N_V n_v^3 n_o^3); per "
-                                         "core state 42 N_V n_v^3 n_o^2 + 10 N_V n_v^3 n_o^3 "
-                                         "(whole_step_flops)",
+                                   "their densities in one call (D^{0-0} once, D^{m-0} and D^{0-m} "
+                                   "per state) and f, then rho, sigma, densities and f of the core "
+                                   "state",
+                           "flop_count": "Omega 4 + D^{0-0} 10 + 42 per valence state "
+                                         "(N_V n_v^3 n_o^3); per core state 42 N_V n_v^3 n_o^2 + "
+                                         "10 N_V n_v^3 n_o^3 (whole_step_flops)",
                            "algorithmic_flop_per_step": fl,
                            "precision": "split bf16x3 / fp32 accumulate / fp64 denominators and reductions",
                            "parallelism": f"replicas x{world} (independent systems)",

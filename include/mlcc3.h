@@ -145,6 +145,19 @@ int mlcc3_multiplier_transformation(mlcc3_ctx *ctx, const double *lam1, const do
  * lam1, lam2 as above; D00_T [n_mo][n_mo], overwritten. */
 int mlcc3_ground_density(mlcc3_ctx *ctx, const double *lam1, const double *lam2, double *D00_T);
 
+/* The densities of n_states states in one call (same definitions as
+ * mlcc3_transition_density): tau, lambda3 and D^{0-0}, which do not depend on
+ * the state, are built once per block of batches and shared; L3, R3, D^{m-0}
+ * and D^{0-m} are per state.  omega [n_states] (host); R1, L1
+ * [n_states][N_V][N_O]; R2, L2 [n_states][n_o][n_v][N_O][N_V]; D00_T
+ * [n_mo][n_mo]; Dm0_T, D0m_T [n_states][n_mo][n_mo].  Every state follows
+ * the context's skip rule ("cvs"): pass valence and core states in separate
+ * calls. */
+int mlcc3_transition_densities(mlcc3_ctx *ctx, int n_states, const double *omega,
+                               const double *lam1, const double *lam2, const double *R1,
+                               const double *R2, const double *L1, const double *L2,
+                               const double *D00_in, double *D00_T, double *Dm0_T, double *D0m_T);
+
 /* Excitation-energy Rayleigh quotient of one state (Sec. 2: the CC3
  * excitation energies are eigenvalues of the omega-dependent Jacobian A(omega);
  * the Davidson iterations estimate them from trial vectors):

@@ -29,7 +29,8 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_triples_omega_static", "mlcc3_debug_tc_gemm", "mlcc3_set_param",
            "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
            "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient", "mlcc3_ground_density",
-           "mlcc3_multiplier_transformation", "mlcc3_cnto_matrices", "mlcc3_shard_batches")
+           "mlcc3_multiplier_transformation", "mlcc3_cnto_matrices", "mlcc3_shard_batches",
+           "mlcc3_transition_densities")
 
 
 class MLCC3Error(RuntimeError):
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_multiplier_transformation.argtypes = [P, P, P, P, P]
     lib.mlcc3_cnto_matrices.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
     lib.mlcc3_shard_batches.argtypes = [I, P, I, I, I, P, I]
+    lib.mlcc3_transition_densities.argtypes = [P, I, P] + [P] * 10
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -202,6 +204,14 @@ class Context:
         self._check(self.lib.mlcc3_transition_density(
             self.h, float(omega), _ptr(lam1), _ptr(lam2), _ptr(R1), _ptr(R2), _ptr(L1), _ptr(L2),
             _ptr(D00_in), _ptr(D00_T), _ptr(Dm0_T), _ptr(D0m_T)))
+
+    def transition_densities(self, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T):
+        """mlcc3_transition_densities: several states in one call (shared tau,
+        lambda3 and D^{0-0}); R1, R2, L1, L2, Dm0_T, D0m_T hold len(omega) states."""
+        w = np.ascontiguousarray(omega, dtype=np.float64)
+        self._check(self.lib.mlcc3_transition_densities(
+            self.h, len(w), w.ctypes.data, _ptr(lam1), _ptr(lam2), _ptr(R1), _ptr(R2), _ptr(L1),
+            _ptr(L2), _ptr(D00_in), _ptr(D00_T), _ptr(Dm0_T), _ptr(D0m_T)))
 
     def ground_density(self, lam1, lam2, D00_T):
         """Triples part of D^{0-0} alone (mlcc3_ground_density)."""

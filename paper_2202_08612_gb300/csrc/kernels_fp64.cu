@@ -179,9 +179,24 @@ __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   const int d3 = 256 % K3, d12 = 256 / K3;
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
+  // both operands binary32: FP32 products, eight per thread summed in FP32 and
+  // then folded into the FP64 sum
+  const bool f32 = p.a32 && p.b32;
+  float sf = 0.f;
+  int nf = 0;
   for (long long k = t0; k < K; k += 256) {
-    s += ld_op<double>(p.A, p.a32, offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4]) *
-         ld_op<double>(p.B, p.b32, offB + k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2]);
+    const long long ia = offA + k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4];
+    const long long ib = offB + k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2];
+    if (f32) {
+      sf = fmaf(reinterpret_cast<const float *>(p.A)[ia], reinterpret_cast<const float *>(p.B)[ib], sf);
+      if (++nf == 8) {
+        s += (double)sf;
+        sf = 0.f;
+        nf = 0;
+      }
+    } else {
+      s += ld_op<double>(p.A, p.a32, ia) * ld_op<double>(p.B, p.b32, ib);
+    }
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {
@@ -196,7 +211,7 @@ __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
     }
     k1 += d1 + c;
   }
-  red[threadIdx.x] = s;
+  red[threadIdx.x] = s + (double)sf;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -573,7 +588,7 @@ __global__ void sd_dot_kernel(const double *__restrict__ x1, const double *__res
       s += w * x2[f] * y2[f];
     }
   }
-  red[threadIdx.x] = s;
+  red[threadIdx.x] = s + (double)sf;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -813,8 +828,23 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
   const int d3 = 32 % K3, d12 = 32 / K3;  // advance of (k3, k12) per step
   const int d2 = d12 % K2, d1 = d12 / K2;
   double s = 0.0;
+  // binary32 A (the split mode's triples arrays): FP32 products, eight per lane
+  // summed in FP32 and then folded into the FP64 sum (one conversion of B per
+  // element instead of a conversion of A and an FP64 product)
+  const float *Af = p.a32 ? reinterpret_cast<const float *>(p.A) + offA : nullptr;
+  float sf = 0.f;
+  int nf = 0;
   for (long long k = lane; k < K; k += 32) {
-    s += ld_op<double>(p.A, p.a32, offA + k1 * a1 + k2 * a2 + k3 * a3) * B[k1 * b1 + k2 * b2 + k3 * b3];
+    if (Af) {
+      sf = fmaf(Af[k1 * a1 + k2 * a2 + k3 * a3], (float)B[k1 * b1 + k2 * b2 + k3 * b3], sf);
+      if (++nf == 8) {
+        s += (double)sf;
+        sf = 0.f;
+        nf = 0;
+      }
+    } else {
+      s += p.A[offA + k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
+    }
     k3 += d3;
     int c = 0;
     if (k3 >= K3) {
@@ -829,6 +859,7 @@ __global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
     }
     k1 += d1 + c;
   }
+  s += (double)sf;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {

@@ -1715,12 +1715,13 @@ bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const doub
   const SplitOp &rvV = split_wn(c, "LRvVT", LRvV, s.nv, s.NV, s.NV, 1, s.nv * s.NV);
   const SplitOp &rvo = split_kc(c, "LRvoT", LRvo, 1, s.no, s.nv * s.no);
   const SplitOp &rOo = split_wn(c, "LROoT", LROo, s.no, s.NO, 1, s.no, s.NO * s.no);
-  const SplitOp &pa = split_wn(c, "PAT", PA, s.no, s.NO, s.NO, 1, s.no * s.NO);
-  const SplitOp &pb = split_wn(c, "PBT", PB, s.nv, s.NV, s.NV, 1, s.nv * s.NV);
   const SplitOp &vo = c->splits.at("LvoT"), &ov = c->splits.at("LovT");
   const SplitOp &vV = c->splits.at("LvVT"), &Oo = c->splits.at("LOoT");
   tc_chol(c, {{&vo, &rvV}, {&rvo, &vV}}, s.nv, s.NV, s.gb, s.gk, s.gc, 1.0, 3, Uv, "Uv");
   tc_chol(c, {{&vo, &rOo}, {&rvo, &Oo}}, s.no, s.NO, s.oj, s.ok, s.oc, 1.0, 3, Uo, "Uo");
+  if (!H1) return true;  // no rho tau-term intermediates wanted
+  const SplitOp &pa = split_wn(c, "PAT", PA, s.no, s.NO, s.NO, 1, s.no * s.NO);
+  const SplitOp &pb = split_wn(c, "PBT", PB, s.nv, s.NV, s.NV, 1, s.nv * s.NV);
   tc_chol(c, {{&ov, &pa}}, s.no, s.NO, s.oj, s.ok, s.oc, 1.0, 3, H1, "H1");
   tc_chol(c, {{&ov, &pb}}, s.nv, s.NV, s.gb, s.gk, s.gc, -1.0, 3, H2, "H2");
   return true;
@@ -1802,26 +1803,32 @@ struct Ups {
   double *Uv, *Uo, *Ukc, *H1, *H2;
 };
 
-Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
+// tag: suffix of the output buffers' names (one set per state of a
+// multi-state call); need_h: also the rho tau-term intermediates H1, H2.
+Ups build_upsilon(mlcc3_ctx *c, const double *R1, const std::string &tag = "", bool need_h = true) {
   S s(c);
   Ups u;
-  u.Uv = c->buf("Uv", s.gvsz());
-  u.Uo = c->buf("Uo", s.gosz());
-  u.Ukc = c->buf("Ukc", s.no * s.nv);
-  u.H1 = c->buf("H1", s.gosz());
-  u.H2 = c->buf("H2", s.gvsz());
+  u.Uv = c->buf("Uv" + tag, s.gvsz());
+  u.Uo = c->buf("Uo" + tag, s.gosz());
+  u.Ukc = c->buf("Ukc" + tag, s.no * s.nv);
+  u.H1 = need_h ? c->buf("H1", s.gosz()) : nullptr;
+  u.H2 = need_h ? c->buf("H2", s.gvsz()) : nullptr;
   double *LRvV = c->buf("LRvV", s.NJ * s.nv * s.NV);
   double *LRvo = c->buf("LRvo", s.NJ * s.nv * s.no);
   double *LROo = c->buf("LROo", s.NJ * s.NO * s.no);
-  double *PA = c->buf("PA", s.NJ * s.no * s.NO);
-  double *PB = c->buf("PB", s.NJ * s.nv * s.NV);
-  for (double *p : {u.Uv, u.H2}) c->zero(p, s.gvsz());
-  for (double *p : {u.Uo, u.H1}) c->zero(p, s.gosz());
+  double *PA = need_h ? c->buf("PA", s.NJ * s.no * s.NO) : nullptr;
+  double *PB = need_h ? c->buf("PB", s.NJ * s.nv * s.NV) : nullptr;
+  c->zero(u.Uv, s.gvsz());
+  c->zero(u.Uo, s.gosz());
+  if (need_h) {
+    c->zero(u.H2, s.gvsz());
+    c->zero(u.H1, s.gosz());
+    c->zero(PA, s.NJ * s.no * s.NO);
+    c->zero(PB, s.NJ * s.nv * s.NV);
+  }
   c->zero(LRvV, s.NJ * s.nv * s.NV);
   c->zero(LRvo, s.NJ * s.nv * s.no);
   c->zero(LROo, s.NJ * s.NO * s.no);
-  c->zero(PA, s.NJ * s.no * s.NO);
-  c->zero(PB, s.NJ * s.nv * s.NV);
   const double *Lt = c->Lt;
   const long long nmo = s.nmo, NO = s.NO;
   Shape sh;
@@ -1837,10 +1844,12 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
   sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.NO; sh.N1 = s.no; sh.K1 = s.NV;
   c->bstc1(Lt + NO, R1, LROo, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.NO * s.no, s.no, 1, 0}), "ups4");
   // PA[J][j][L] = sum_D Lt[J][j][NO+D] R^D_L, PB[J][b][D] = sum_L Lt[J][L][NO+b] R^D_L
-  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
-  c->bstc1(Lt + NO, R1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "ups9");
-  sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.NV; sh.K1 = s.NO;
-  c->bstc1(Lt + NO, R1, PB, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 1, nmo, 0, 0}, {1, 0, 0, NO, 0}, {s.nv * s.NV, s.NV, 1, 0}), "ups11");
+  if (need_h) {
+    sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.no; sh.N1 = s.NO; sh.K1 = s.NV;
+    c->bstc1(Lt + NO, R1, PA, sh, 1.0, mk_item(0, 0, 0, {s.lJ, nmo, 1, 0, 0}, {NO, 0, 0, 1, 0}, {s.no * s.NO, s.NO, 1, 0}), "ups9");
+    sh = Shape{}; sh.M1 = s.NJ; sh.M2 = s.nv; sh.N1 = s.NV; sh.K1 = s.NO;
+    c->bstc1(Lt + NO, R1, PB, sh, 1.0, mk_item(0, 0, 0, {s.lJ, 1, nmo, 0, 0}, {1, 0, 0, NO, 0}, {s.nv * s.NV, s.NV, 1, 0}), "ups11");
+  }
   fock_ov(c, R1, u.Ukc, "ups");
   if (tc_upsilon(c, LRvV, LRvo, LROo, PA, PB, u.Uv, u.Uo, u.H1, u.H2)) return u;
   // Uv[k][b][c][D] = sum_J (LRvV[J][b][D] Lt[J][NO+c][k] + Lt[J][NO+b][NO+D] LRvo[J][c][k])
@@ -1851,6 +1860,7 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1) {
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
   c->bstc1(Lt + NO * nmo, LROo, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, nmo, s.lJ, 0, 0}, {s.NO * s.no, 0, 0, 1, s.no}, {s.ok, s.oc, s.oj, 1}), "ups7");
   c->bstc1(LRvo, Lt, u.Uo, sh, 1.0, mk_item(0, 0, 0, {1, s.no, s.nv * s.no, 0, 0}, {s.lJ, 0, 0, 1, nmo}, {s.ok, s.oc, s.oj, 1}), "ups8");
+  if (!need_h) return u;
   // H1[j][k][c][L] = sum_J PA[J][j][L] Lt[J][k][NO+c]
   sh = Shape{}; sh.M1 = s.no; sh.M2 = s.nv; sh.N1 = s.no; sh.N2 = s.NO; sh.K1 = s.NJ;
   c->bstc1(Lt + NO, PA, u.H1, sh, 1.0, mk_item(0, 0, 0, {nmo, 1, s.lJ, 0, 0}, {s.no * s.NO, 0, 0, s.NO, 1}, {s.ok, s.oc, s.oj, 1}), "ups10");
@@ -2504,25 +2514,35 @@ void density_left_gpu(mlcc3_ctx *c, const Chunk &ch, const double *Xt3, const do
 
 }  // namespace
 
-static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1_in,
-                                  const double *lam2_in, const double *R1_in, const double *R2_in,
+// n_st states at once (frequencies omega[n_st], host): tau, lambda3 and
+// D^{0-0} are state independent and built once per occupied-index range; L3,
+// R3, D^{m-0} and D^{0-m} per state.  R1, R2, L1, L2 hold n_st consecutive
+// vectors, Dm0_out and D0m_out n_st consecutive [n_mo][n_mo] blocks.
+static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
+                                  const double *lam1_in, const double *lam2_in,
+                                  const double *R1_in, const double *R2_in,
                                   const double *L1_in, const double *L2_in,
                                   const double *D00_in_in, double *D00_out, double *Dm0_out,
                                   double *D0m_out) {
   S s(c);
   const long long nmo = s.nmo, NO = s.NO;
   const bool cvs = cvs_on(c);
-  const double *lam1 = c->in(lam1_in, s.NV * NO, "lam1");
-  const double *lam2 = c->in(lam2_in, s.blk(), "lam2");
-  const double *R1 = c->in(R1_in, s.NV * NO, "R1");
-  const double *R2 = c->in(R2_in, s.blk(), "R2");
-  const double *L1 = c->in(L1_in, s.NV * NO, "L1");
-  const double *L2 = c->in(L2_in, s.blk(), "L2");
-  const double *D00_in = c->in(D00_in_in, nmo * nmo, "D00_in");
-  double *D00 = c->out(D00_out, nmo * nmo, "D00");
-  double *Dm0 = c->out(Dm0_out, nmo * nmo, "Dm0");
-  double *D0m = c->out(D0m_out, nmo * nmo, "D0m");
-  for (double *p : {D00, Dm0, D0m}) c->zero(p, nmo * nmo);
+  const size_t n1 = (size_t)(s.NV * NO), n2 = s.blk(), nd = (size_t)(nmo * nmo);
+  for (int st = 0; st < n_st; ++st)
+    if (!(std::fabs(omega_h[st]) < 1e300)) throw Error{MLCC3_ERR_ARG, "omega is not finite"};
+  const double *lam1 = c->in(lam1_in, n1, "lam1");
+  const double *lam2 = c->in(lam2_in, n2, "lam2");
+  const double *R1all = c->in(R1_in, n_st * n1, "R1");
+  const double *R2all = c->in(R2_in, n_st * n2, "R2");
+  const double *L1all = c->in(L1_in, n_st * n1, "L1");
+  const double *L2all = c->in(L2_in, n_st * n2, "L2");
+  const double *D00_in = c->in(D00_in_in, nd, "D00_in");
+  double *D00 = c->out(D00_out, nd, "D00");
+  double *Dm0all = c->out(Dm0_out, n_st * nd, "Dm0");
+  double *D0mall = c->out(D0m_out, n_st * nd, "D0m");
+  c->zero(D00, nd);
+  c->zero(Dm0all, n_st * nd);
+  c->zero(D0mall, n_st * nd);
 
   // doubles-level operands of the three triples amplitudes
   double *lc = c->buf("lamc", s.blk());
@@ -2531,29 +2551,44 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, lc, lcT);
-  double *Lc = c->buf("Lc", s.blk());
-  double *LcT = c->buf("LcT", s.no * s.nv * s.nv * NO);
-  launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
-    c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
-  });
-  transpose_tl(c, Lc, LcT);
-  double *Rbar = c->buf("Rbar", s.blk());
-  double *Rbl = c->buf("Rbarl", s.no * s.nv * s.nv * NO);
-  launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
-    c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(R2, Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
-  });
-  transpose_tl(c, Rbar, Rbl);
-  Ups u = build_upsilon(c, R1);
-  if (split_mode(c)) split_tl_T(c, "Rbl", Rbl);
+  // per state: Lc, Rbar (and their [i][a][b][L] forms) and the Upsilon blocks
+  struct StateOps {
+    const double *R1, *R2, *L1;
+    double *Lc, *LcT, *Rbar, *Rbl, *Dm0, *D0m;
+    Ups u;
+  };
+  std::vector<StateOps> sts(n_st);
+  for (int st = 0; st < n_st; ++st) {
+    StateOps &o = sts[st];
+    const std::string tg = st ? ":s" + std::to_string(st) : std::string();
+    o.R1 = R1all + st * n1;
+    o.R2 = R2all + st * n2;
+    o.L1 = L1all + st * n1;
+    const double *L2 = L2all + st * n2;
+    o.Dm0 = Dm0all + st * nd;
+    o.D0m = D0mall + st * nd;
+    o.Lc = c->buf("Lc" + tg, s.blk());
+    o.LcT = c->buf("LcT" + tg, s.no * s.nv * s.nv * NO);
+    launch_1d(c, (long long)s.blk(), "c2", [&](int g) {
+      c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(L2, o.Lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
+    });
+    transpose_tl(c, o.Lc, o.LcT);
+    o.Rbar = c->buf("Rbar" + tg, s.blk());
+    o.Rbl = c->buf("Rbarl" + tg, s.no * s.nv * s.nv * NO);
+    launch_1d(c, (long long)s.blk(), "delta", [&](int g) {
+      c->launch("delta_block_kernel", 0.0, [&] { delta_block_kernel<<<g, 256, 0, c->stream>>>(o.R2, o.Rbar, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
+    });
+    transpose_tl(c, o.Rbar, o.Rbl);
+    o.u = build_upsilon(c, o.R1, tg, false);
+  }
   double *one = c->dscal;
-  double *sc = c->dscal + 1;
+  double *scall = c->buf("dsc", 2 * (size_t)n_st);  // per state: lambda3.R3, lambda_SD.R_SD
   {
     double h1 = 1.0;
     check_cuda(cudaMemcpyAsync(one, &h1, sizeof(double), cudaMemcpyHostToDevice, c->stream), "one");
     check_cuda(cudaStreamSynchronize(c->stream), "one sync");
   }
-  c->zero(sc, 2);
-  double *D = D0m;
+  c->zero(scall, 2 * (size_t)n_st);
   for (const Chunk &ch : c->groups) {
     const std::string bkey = "b" + ch.key, okey = "o" + ch.key;
     const long long bw = ch.nb * s.nv3;
@@ -2565,6 +2600,16 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
+    // D^{0-0} (state independent)
+    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
+    for (int st = 0; st < n_st; ++st) {
+    const StateOps &so = sts[st];
+    const double omega = omega_h[st];
+    const double *R1 = so.R1, *L1 = so.L1, *Lc = so.Lc, *LcT = so.LcT;
+    const double *Rbar = so.Rbar, *Rbl = so.Rbl;
+    const Ups &u = so.u;
+    double *D = so.D0m, *sc = scall + 2 * st;
+    if (split_mode(c)) split_tl_T(c, "Rbl", Rbl);
     // L3 (omega) and R3 (omega), with their contravariant forms (CVS: core batches only)
     double *L3 = c->tri_buf("L3", bw);
     double *L3t = c->tri_buf("L3t", bw);
@@ -2577,9 +2622,8 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
     if (cvs) c->zero_tri(R3, bw);
     right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3);
     contra3(c, R3, R3t, ch.nb);
-    // D^{0-0} and D^{m-0}
-    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
-    density_left_gpu(c, ch, L3t, Lc, tau, taut, Dm0);
+    // D^{m-0}
+    density_left_gpu(c, ch, L3t, Lc, tau, taut, so.Dm0);
 
     // D^{0-m}
     int n = 0;
@@ -2716,14 +2760,19 @@ static void do_transition_density(mlcc3_ctx *c, double omega, const double *lam1
       sh = Shape{}; sh.K3 = s.nv3;
       c->dot(lt3, R3, sc, sh, (double)m / 6.0, it, n);
     }
+    }  // states
   }
-  // lambda_SD.R_SD, then the normalisation term of D^{0-m}
-  launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
-    c->launch("sd_dot_kernel", 0.0, [&] { sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, R1, R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1); });
-  });
-  launch_1d(c, nmo * nmo, "density_norm", [&](int g) {
-    c->launch("density_norm_kernel", 0.0, [&] { density_norm_kernel<<<g, 256, 0, c->stream>>>(D, D00_in, D00, sc, (int)nmo, (int)NO); });
-  });
+  // lambda_SD.R_SD, then the normalisation term of D^{0-m}, per state
+  for (int st = 0; st < n_st; ++st) {
+    const StateOps &so = sts[st];
+    double *sc = scall + 2 * st;
+    launch_1d(c, (long long)(s.NV * NO + s.blk()), "sd_dot", [&](int g) {
+      c->launch("sd_dot_kernel", 0.0, [&] { sd_dot_kernel<<<g, 256, 0, c->stream>>>(lam1, lam2, so.R1, so.R2, (int)s.no, (int)s.nv, (int)NO, (int)s.NV, sc + 1); });
+    });
+    launch_1d(c, nmo * nmo, "density_norm", [&](int g) {
+      c->launch("density_norm_kernel", 0.0, [&] { density_norm_kernel<<<g, 256, 0, c->stream>>>(so.D0m, D00_in, D00, sc, (int)nmo, (int)NO); });
+    });
+  }
 }
 
 // Ground-state density D^{0-0} alone (SI: D^{m-0} with the multipliers and
@@ -2910,7 +2959,21 @@ extern "C" int mlcc3_transition_density(mlcc3_ctx *c, double omega, const double
                                         double *D00_T, double *Dm0_T, double *D0m_T) {
   return guarded([&] {
     require_built(c);
-    do_transition_density(c, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T);
+    do_transition_density(c, 1, &omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T, D0m_T);
+    c->finish();
+  });
+}
+
+extern "C" int mlcc3_transition_densities(mlcc3_ctx *c, int n_states, const double *omega,
+                                          const double *lam1, const double *lam2,
+                                          const double *R1, const double *R2, const double *L1,
+                                          const double *L2, const double *D00_in, double *D00_T,
+                                          double *Dm0_T, double *D0m_T) {
+  return guarded([&] {
+    require_built(c);
+    if (n_states < 1 || !omega) throw Error{MLCC3_ERR_ARG, "bad n_states/omega"};
+    do_transition_density(c, n_states, omega, lam1, lam2, R1, R2, L1, L2, D00_in, D00_T, Dm0_T,
+                          D0m_T);
     c->finish();
   });
 }

@@ -69,7 +69,9 @@ def test_whole_step_call_sequence():
     fs = prob.step(Rec(), x, o, tally=count)
     names = [c[0] for c in calls]
     assert names.count("build_integrals") == 1 and names.count("triples_omega") == 1
-    assert names.count("jacobian_right") == 2 and names.count("transition_density") == 3
+    assert names.count("jacobian_right") == 2 and names.count("transition_densities") == 2
+    td = [c[1] for c in calls if c[0] == "transition_densities"]
+    assert len(td[0][0]) == 2 and list(td[1][0]) == [10.2]
     assert fs == [0.5, 0.5, 0.5]
     cvs = [c[1][1] for c in calls if c[0] == "set_param"]
     assert cvs == [0, 1, 1]

@@ -38,10 +38,13 @@ def test_flop_prefactors_are_the_papers():
 
 def test_whole_step_count():
     """The default bench step (two valence states and one core state of the
-    100/1000/20/150 system): Omega once, 52 units per valence state, and the
-    core state's rho and sigma at the paper's CVS count."""
+    100/1000/20/150 system): Omega once, 42 units per valence state plus one
+    D^{0-0} for their shared densities call, and the core state's rho and sigma
+    at the paper's CVS count."""
     NO, NV, no, nv = 100, 1000, 20, 150
     u3, u2 = NV * nv ** 3 * no ** 3, NV * nv ** 3 * no ** 2
     t = _table("flop_prefactors.txt")
     cvs = 2 * t["cvs"] * u2 + (t["D_m0"] + t["D_0m"]) * u2 + t["D_m0"] * u3
-    assert bench.whole_step_flops(NO, NV, no, nv, 2, 1) == t["omega"] * u3 + 2 * 52 * u3 + cvs
+    val = (t["rho"] + t["sigma"] + t["D_m0"] + t["D_0m"]) * u3
+    # D^{0-0} (D^{m-0}'s count) once for the valence states' densities call
+    assert bench.whole_step_flops(NO, NV, no, nv, 2, 1) == (t["omega"] + t["D_m0"]) * u3 + 2 * val + cvs

@@ -221,3 +221,39 @@ def test_error_codes_on_gpu():
         g.jacobian_right([w], c.to_dev(c.st.R1), c.to_dev(c.st.R2),
                          c.empty_dev(c.st.R1.shape), c.empty_dev(c.st.R2.shape))
     assert e.value.code == -4
+
+
+@pytest.mark.parametrize("precision,tol", [(binding.MLCC3_FP64, 1e-10),
+                                           (binding.MLCC3_SPLIT_BF16X3, 1e-4)])
+@pytest.mark.parametrize("chunk", [0, 9])
+def test_densities_of_several_states_in_one_call(precision, tol, chunk):
+    """mlcc3_transition_densities: three states in one call (tau, lambda3 and
+    D^{0-0} built once) give every state's densities of the one-state call and
+    of the oracle, unchunked and by occupied-index ranges."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=3)
+    g = c.context(precision=precision, params={"chunk_blocks": chunk} if chunk else None)
+    o, st = c.oracle_ctx(), c.st
+    nmo = o.nmo
+    D00 = c.empty_dev((nmo, nmo))
+    Dm0, D0m = c.empty_dev((3, nmo, nmo)), c.empty_dev((3, nmo, nmo))
+    g.transition_densities(st.omega, c.to_dev(c.lam1), c.to_dev(c.lam2), c.to_dev(st.R1),
+                           c.to_dev(st.R2), c.to_dev(st.L1), c.to_dev(st.L2), c.to_dev(c.D00_in),
+                           D00, Dm0, D0m)
+    for v in range(3):
+        w = float(st.omega[v])
+        r00, rm0, r0m = O.transition_densities(o, w, c.lam1, O.to_full(o, c.lam2), st.R1[v],
+                                               O.to_full(o, st.R2[v]), st.L1[v],
+                                               O.to_full(o, st.L2[v]), c.D00_in)
+        assert rel_err(c.host(D00), r00) < tol
+        assert rel_err(c.host(Dm0)[v], rm0) < tol, v
+        assert rel_err(c.host(D0m)[v], r0m) < tol, v
+        one = [c.empty_dev((nmo, nmo)) for _ in range(3)]
+        g.transition_density(w, c.to_dev(c.lam1), c.to_dev(c.lam2), c.to_dev(st.R1[v]),
+                             c.to_dev(st.R2[v]), c.to_dev(st.L1[v]), c.to_dev(st.L2[v]),
+                             c.to_dev(c.D00_in), *one)
+        assert rel_err(c.host(Dm0)[v], c.host(one[1])) < 10 * tol
+        assert rel_err(c.host(D0m)[v], c.host(one[2])) < 10 * tol
+    g.close()
