@@ -588,7 +588,7 @@ __global__ void sd_dot_kernel(const double *__restrict__ x1, const double *__res
       s += w * x2[f] * y2[f];
     }
   }
-  red[threadIdx.x] = s + (double)sf;
+  red[threadIdx.x] = s;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
