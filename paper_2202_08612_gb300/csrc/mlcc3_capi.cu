@@ -688,6 +688,8 @@ void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
 void tc_integrals(mlcc3_ctx *c);
 void split_chol_kpairs(mlcc3_ctx *c);
 float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long n);
+const double *f32_operand(mlcc3_ctx *c, const std::string &key, const double *x, long long n,
+                          bool convert);
 mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k,
                               unsigned rows);
 bool tc_upsilon(mlcc3_ctx *c, const double *LRvV, const double *LRvo, const double *LROo,
@@ -729,7 +731,10 @@ void back_contract(mlcc3_ctx *c, const double *X, const std::vector<Ord> &ords,
     // Gs[q][b][r][c] = g_qbrc is symmetric under (q,b) <-> (r,c)
     sh = Shape{};
     sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-    bstc_mirror(c, X, bset.Gs, s1, sh, bset.cs, ords, 1, 2, okey + ":bs", [&](const Ord &o) {
+    const double *Gs = bset.Gs == c->Govov && c->is_tri32(X)
+                           ? f32_operand(c, "Govov", c->Govov, s.no * s.nv * s.no * s.nv, false)
+                           : bset.Gs;
+    bstc_mirror(c, X, Gs, s1, sh, bset.cs, ords, 1, 2, okey + ":bs", [&](const Ord &o) {
       return mk_item(o.off, o.q * s.vj + o.r * s.vk, o.p, {o.vs[0], 0, o.vs[1], o.vs[2], 0},
                      {s.vb, 1, 0, 0, 0}, {s.NO, 0, 0, 0});
     });
@@ -1780,6 +1785,20 @@ float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long
   return y;
 }
 
+// The FP32 copy of an operand that meets binary32 triples arrays in the
+// matrix-vector contractions of the split mode (convert = false: the copy
+// f32:key exists already), registered as a binary32 operand: those
+// contractions then run without any FP64 operation per product.  In the FP64
+// mode the operand itself.
+const double *f32_operand(mlcc3_ctx *c, const std::string &key, const double *x, long long n,
+                          bool convert = true) {
+  if (!c->tri32) return x;
+  float *y = convert ? f32_copy(c, key, x, n)
+                     : static_cast<float *>(c->raw("f32:" + key, sizeof(float) * (size_t)std::max(1LL, n)));
+  c->tri_regs["f32:" + key] = {reinterpret_cast<const char *>(y), sizeof(float) * (size_t)std::max(1LL, n)};
+  return reinterpret_cast<const double *>(y);
+}
+
 // tau and its contravariant form for the batches of chunk `ch` (kept until the
 // next integral build or until another chunk needs the buffers).
 void build_tau(mlcc3_ctx *c, const Chunk &ch, double **tau, double **taut) {
@@ -2093,6 +2112,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       LcA = &split_amp_T(c, "Lc:AT", Lc);
       split_tl_T(c, "LcT", LcT);
     }
+    const double *Lc32 = f32_operand(c, "Lc:y3", Lc, (long long)s.blk(), true);
     for (const Chunk &ch : chunks) {
       double *tau, *taut;
       build_tau(c, ch, &tau, &taut);
@@ -2146,7 +2166,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       }
       // Y3[r][c] += 1/2 sum_{ab} taut_{pqr}[a][b][c] Lc[p][a][q][b]
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-      bstc_mirror(c, taut, Lc, Y3, sh, 0.5, os, 0, 1, okey + ":y3", [&](const Ord &o) {
+      bstc_mirror(c, taut, Lc32, Y3, sh, 0.5, os, 0, 1, okey + ":y3", [&](const Ord &o) {
         return mk_item(o.off, o.p * s.bi + o.q * s.bL, o.r * s.nv,
                        {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.ba, 1, 0, 0, 0}, {1, 0, 0, 0});
       });
@@ -2551,10 +2571,12 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, lc, lcT);
+  const double *lc32 = f32_operand(c, "lamc", lc, (long long)s.blk(), true);
   // per state: Lc, Rbar (and their [i][a][b][L] forms) and the Upsilon blocks
   struct StateOps {
     const double *R1, *R2, *L1;
     double *Lc, *LcT, *Rbar, *Rbl, *Dm0, *D0m;
+    const double *Lc32, *Rbar32, *R1_32;  // FP32 copies for the matrix-vector contractions (split mode)
     Ups u;
   };
   std::vector<StateOps> sts(n_st);
@@ -2580,6 +2602,9 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     });
     transpose_tl(c, o.Rbar, o.Rbl);
     o.u = build_upsilon(c, o.R1, tg, false);
+    o.Lc32 = f32_operand(c, "Lc" + tg, o.Lc, (long long)s.blk(), true);
+    o.Rbar32 = f32_operand(c, "Rbar" + tg, o.Rbar, (long long)s.blk(), true);
+    o.R1_32 = f32_operand(c, "R1" + tg, o.R1, (long long)n1, true);
   }
   double *one = c->dscal;
   double *scall = c->buf("dsc", 2 * (size_t)n_st);  // per state: lambda3.R3, lambda_SD.R_SD
@@ -2601,7 +2626,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
     // D^{0-0} (state independent)
-    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
+    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
     for (int st = 0; st < n_st; ++st) {
     const StateOps &so = sts[st];
     const double omega = omega_h[st];
@@ -2623,7 +2648,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3);
     contra3(c, R3, R3t, ch.nb);
     // D^{m-0}
-    density_left_gpu(c, ch, L3t, Lc, tau, taut, so.Dm0);
+    density_left_gpu(c, ch, L3t, so.Lc32, tau, taut, so.Dm0);
 
     // D^{0-m}
     int n = 0;
@@ -2644,7 +2669,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
       return v;
     }, &n);
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.nv; sh.K1 = s.nv;
-    c->bstc(lt3, R1, U, sh, 1.0, it, n, true, okey + ":U");
+    c->bstc(lt3, so.R1_32, U, sh, 1.0, it, n, true, okey + ":U");
     if (umirror)
       launch_1d(c, s.no * s.no * s.nv * s.nv, "mirror_u", [&](int g) {
         c->launch("mirror_pairs_kernel", 0.0, [&] {
@@ -2656,6 +2681,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
     // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
     pair_dots(c, ch, lt3, R3, D, nmo, true, -0.5);
+    const double *U32 = f32_operand(c, "dU", U, s.no * s.no * s.nv * s.nv, true);
     // D_ld += sum U[j][k][b][c] (tau^{bcd}_{jkl} - tau^{bcd}_{jlk})  (views with j in [p0, p1))
     // U[p][q][a][b] is symmetric under (p,a) <-> (q,b): mirror orderings (p,q,r),
     // (q,p,r) contribute alike (each ordering lies in the chunk of its p)
@@ -2664,7 +2690,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
       for (auto &o : ch.held)
         if (o.p >= ch.p0 && o.p < ch.p1) os1.push_back(o);
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv;
-      bstc_mirror(c, tau, U, D + NO, sh, 1.0, os1, 0, 1, okey + ":ld1", [&](const Ord &o) {
+      bstc_mirror(c, tau, U32, D + NO, sh, 1.0, os1, 0, 1, okey + ":ld1", [&](const Ord &o) {
         return mk_item(o.off, (o.p * s.no + o.q) * s.nv * s.nv, o.r * nmo,
                        {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0});
       });
@@ -2677,13 +2703,13 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
                               {o.vs[2], 0, o.vs[0], o.vs[1], 0}, {s.nv, 1, 0, 0, 0}, {1, 0, 0, 0}));
       return v;
     }, &n);
-    c->bstc(tau, U, D + NO, sh, -1.0, it, n, true, okey + ":ld2");
+    c->bstc(tau, U32, D + NO, sh, -1.0, it, n, true, okey + ":ld2");
     //        + 1/2 sum lc^{ab}_{ij} Rt^{abd}_{ijl}
-    y3_like(c, R3t, lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
+    y3_like(c, R3t, lc32, ch.own, okey, D + NO, nmo, 0.5, "y3d");
     // D_LD: W3[k][c] = 1/2 sum lt^{abc}_{ijk} Rbar^{ab}_{ij}
     double *W3 = c->buf("dW3", s.no * s.nv);
     c->zero(W3, s.no * s.nv);
-    y3_like(c, lt3, Rbar, ch.own, okey, W3, s.nv, 0.5, "y3w");
+    y3_like(c, lt3, so.Rbar32, ch.own, okey, W3, s.nv, 0.5, "y3w");
     //   D_LD += sum_{kc} W3[k][c] (2 t^{cD}_{kL} - t^{cD}_{Lk})
     sh = Shape{}; sh.M1 = NO; sh.M2 = s.NV; sh.K1 = s.no; sh.K2 = s.nv;
     c->bstc1(c->t2c, W3, D + NO, sh, 2.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
@@ -2792,6 +2818,7 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     c->launch("c2_block_kernel", 0.0, [&] { c2_block_kernel<<<g, 256, 0, c->stream>>>(lam2, lc, (int)s.no, (int)s.nv, (int)NO, (int)s.NV); });
   });
   transpose_tl(c, lc, lcT);
+  const double *lc32 = f32_operand(c, "lamc", lc, (long long)s.blk(), true);
   for (const Chunk &ch : c->groups) {
     const long long bw = ch.nb * s.nv3;
     double *tau, *taut;
@@ -2800,7 +2827,7 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3);
     contra3(c, lam3, lt3, ch.nb);
-    density_left_gpu(c, ch, lt3, lc, tau, taut, D00);
+    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
   }
 }
 
