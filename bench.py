@@ -31,6 +31,9 @@ WORKLOADS = {
     # name: (N_O, N_V, n_o, n_v, N_J, states)
     "guanine_like_small": (20, 200, 12, 60, 600, 1),
     "tiny": (6, 24, 4, 8, 72, 1),
+    # a small system with the largest workload's active virtual space (n_v = 150:
+    # one batch per tensor-core tile), for kernel captures that must stay small
+    "betaine_shape_small": (10, 300, 6, 150, 600, 1),
 }
 # uneven systems of the batched sweep, (n_o, n_v, N_V), N_O = n_o + 8, N_J = 3 N_V
 SWEEP_SYSTEMS = [(8, 40, 120), (11, 60, 216), (14, 80, 312), (18, 100, 408), (21, 120, 504),
@@ -391,7 +394,11 @@ def run_ours(args, rank, world, local_rank):
         ctx64.close()
 
     if rank == 0:
-        cpu_v, cpu_dt, sample = oracle_sample(args.workload, 77)
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu_v, cpu_dt, sample = oracle_sample(args.workload, 77)
+            cpu = {"value": cpu_v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": sample, "seconds": cpu_dt}
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -406,8 +413,7 @@ def run_ours(args, rank, world, local_rank):
                 "s_per_davidson_iter": s_iter,
                 "fp64_gpu_path": fp64, "f": f_ours,
                 "roofline": roofline,
-                "cpu_baseline": {"value": cpu_v, "unit": "TFLOP/s", "cores": os.cpu_count(),
-                                 "kind": "oracle", "sample": sample, "seconds": cpu_dt},
+                "cpu_baseline": cpu,
                 "e2e": e2e, "clocks": clk.summary(), "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},
                 "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
@@ -1214,8 +1220,20 @@ def run_whole(args, rank, world, local_rank):
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in agg.items()},
                 "call_sites": {k: round(v[1] / args.steps, 3) for k, v in
                                sorted(stats.items(), key=lambda kv: -kv[1][1])[:24]},
+                "site_totals": site_totals(stats, args.steps),
                 "tc_sites": tc_site_fracs(stats, args.steps, pk)}
         print(json.dumps(line), flush=True)
+
+
+def site_totals(stats, steps):
+    """ms per step of each (kernel, call site) pair, the chunk part of the tag
+    dropped (a site runs once per chunk of batches): "kernel:site"."""
+    out = {}
+    for k, v in stats.items():
+        parts = k.split(":")
+        key = parts[0] + (":" + parts[-1] if len(parts) > 1 else "")
+        out[key] = out.get(key, 0.0) + v[1] / steps
+    return {k: round(v, 3) for k, v in sorted(out.items(), key=lambda kv: -kv[1]) if v >= 1.0}
 
 
 def run_reference_whole(args, rank):
@@ -1297,7 +1315,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="whole-step workload: steps of the end-to-end (pinned host buffers) run")
     ap.add_argument("--no-cpu-baseline", action="store_true",
-                    help="skip the oracle sample of the whole-step workload")
+                    help="skip the oracle sample (CPU baseline)")
     ap.add_argument("--stage", default=None, choices=("davidson", "densities", "cvs", "ground"),
                     help="large workloads: Davidson iterations (rho, sigma) of the valence "
                          "vectors, the densities and f of one state, the Davidson iteration "
