@@ -803,6 +803,137 @@ __global__ void hilo_kernel(const double *__restrict__ x, float2 *__restrict__ y
 
 namespace mlcc3 {
 
+// Matrix-vector form of the batched strided contraction for a binary32 A (the
+// split mode's triples arrays are permuted views of n_v^3 blocks, so the
+// index that is contiguous in memory may be an output index or a reduction
+// index, depending on the item).  Each block takes one item and picks the
+// mapping whose loads run along the contiguous index:
+//  * an output index contiguous: the 32 lanes take 32 consecutive outputs
+//    along it and the 8 warps split K (sums of the warps added in shared
+//    memory);
+//  * otherwise: one warp per output, the lanes along K with the contiguous K
+//    index (if any) the fastest.
+// FP32 products (B binary32 when b32, else converted), 16 per lane summed in
+// FP32 and folded into FP64; one atomic update per output.  Grid: x =
+// ceil(M / 8) (the first mapping uses ceil(M / 32) of them), y = items.
+__global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
+  __shared__ double red[8][33];
+  const BstcItem &it = p.items[blockIdx.y];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long M1 = p.M1, M2 = p.M2, M = M1 * M2;
+  const float *A = reinterpret_cast<const float *>(p.A) + it.offA;
+  const float *Bf = p.b32 ? reinterpret_cast<const float *>(p.B) + it.offB : nullptr;
+  const double *Bd = p.B + (p.b32 ? 0 : it.offB);
+  int Kn[3] = {p.K1, p.K2, p.K3};
+  long long ka[3] = {it.sA[2], it.sA[3], it.sA[4]}, kb[3] = {it.sB[0], it.sB[1], it.sB[2]};
+  const long long K = (long long)Kn[0] * Kn[1] * Kn[2];
+  auto ldb = [&](long long i) { return Bf ? Bf[i] : (float)Bd[i]; };
+  // output mapping along a contiguous output index
+  int mf = -1;  // 1: m2 is contiguous (m2 fastest), 0: m1 contiguous (m1 fastest)
+  if (M2 > 1 && it.sA[1] == 1) mf = 1;
+  else if (it.sA[0] == 1 && (M1 > 1 || M2 == 1)) mf = 0;
+  if (mf >= 0) {
+    if ((long long)blockIdx.x * 32 >= M) return;
+    const long long m = (long long)blockIdx.x * 32 + lane;
+    const bool valid = m < M;
+    const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
+    const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
+    double s = 0.0;
+    float sf = 0.f;
+    int nf = 0;
+    if (valid) {
+      // k = warp, warp + 8, ...: (k1, k2, k3) advanced with carries
+      int k3 = warp % Kn[2], k12 = warp / Kn[2];
+      int k2 = k12 % Kn[1], k1 = k12 / Kn[1];
+      const int d3 = 8 % Kn[2], d12 = 8 / Kn[2];
+      const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
+      for (long long k = warp; k < K; k += 8) {
+        sf = fmaf(Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]], ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]), sf);
+        if (++nf == 16) {
+          s += (double)sf;
+          sf = 0.f;
+          nf = 0;
+        }
+        k3 += d3;
+        int c = 0;
+        if (k3 >= Kn[2]) {
+          k3 -= Kn[2];
+          c = 1;
+        }
+        k2 += d2 + c;
+        c = 0;
+        if (k2 >= Kn[1]) {
+          k2 -= Kn[1];
+          c = 1;
+        }
+        k1 += d1 + c;
+      }
+    }
+    red[warp][lane] = s + (double)sf;
+    __syncthreads();
+    if (warp == 0 && valid) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += red[w][lane];
+      double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+      atomicAdd(C, p.alpha * t);
+    }
+    return;
+  }
+  // one warp per output; the contiguous K index (if any) becomes the fastest
+  for (int q = 0; q < 2; ++q)
+    if (ka[q] == 1 && Kn[q] > 1 && !(ka[2] == 1 && Kn[2] > 1)) {
+      const int tn = Kn[q];
+      const long long ta = ka[q], tb = kb[q];
+      Kn[q] = Kn[2];
+      ka[q] = ka[2];
+      kb[q] = kb[2];
+      Kn[2] = tn;
+      ka[2] = ta;
+      kb[2] = tb;
+    }
+  const long long m = (long long)blockIdx.x * 8 + warp;
+  if (m >= M) return;
+  const long long m1 = m / M2, m2 = m % M2;
+  const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
+  int k3 = lane % Kn[2], k12 = lane / Kn[2];
+  int k2 = k12 % Kn[1], k1 = k12 / Kn[1];
+  const int d3 = 32 % Kn[2], d12 = 32 / Kn[2];
+  const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
+  double s = 0.0;
+  float sf = 0.f;
+  int nf = 0;
+  for (long long k = lane; k < K; k += 32) {
+    sf = fmaf(Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]], ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]), sf);
+    if (++nf == 16) {
+      s += (double)sf;
+      sf = 0.f;
+      nf = 0;
+    }
+    k3 += d3;
+    int c = 0;
+    if (k3 >= Kn[2]) {
+      k3 -= Kn[2];
+      c = 1;
+    }
+    k2 += d2 + c;
+    c = 0;
+    if (k2 >= Kn[1]) {
+      k2 -= Kn[1];
+      c = 1;
+    }
+    k1 += d1 + c;
+  }
+  s += (double)sf;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+    if (p.atomic) atomicAdd(C, p.alpha * s);
+    else *C += p.alpha * s;
+  }
+}
+
 // Matrix-vector form of the batched strided contraction (N = 1): one warp per
 // output row m, the lanes stride over K, warp reduction, one (atomic) update.
 // Matrix-vector form of the batched strided contraction (N = 1): one warp per

@@ -31,6 +31,7 @@ __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_f32_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
+__global__ void bstc_gemv32_kernel(BstcParams p);
 __global__ void pair_dots_f32_kernel(const float *, const float *, const long long *, const int *,
                                      const char *, int, int, int, double *, long long, int, double);
 __global__ void pair_dots_f64_kernel(const double *, const double *, const long long *, const int *,
@@ -295,8 +296,12 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
       int nz = std::min(65535, nitems - z0);
       dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
       const std::string name = tag.empty() ? std::string("bstc_gemv_kernel") : "bstc_gemv_kernel:" + tag;
-      launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz,
-             [&] { bstc_gemv_kernel<<<grid, 256, 0, stream>>>(p); });
+      launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
+        if (p.a32)  // binary32 triples operand: the mapping follows its contiguous index
+          bstc_gemv32_kernel<<<grid, 256, 0, stream>>>(p);
+        else
+          bstc_gemv_kernel<<<grid, 256, 0, stream>>>(p);
+      });
     }
     check_cuda(cudaGetLastError(), "bstc_gemv launch");
     return;
@@ -1094,19 +1099,24 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
         if (!groups.count(g)) order.push_back(g);
         groups[g].push_back(u);
       }
+      // items of one pair tile (t1, t2) for every batch of the group follow each
+      // other: the concurrently running CTAs then share that tile's rows of the
+      // group's integral-side operand (read from DRAM once per group instead of
+      // once per batch), while the batches' amplitude boxes (a few MB per group)
+      // stay in L2 across the tiles
       for (const auto &g : order) {
         const std::vector<long long> &us = groups[g];
-        for (size_t q0 = 0; q0 < us.size(); q0 += (size_t)G) {
-          const int nq = (int)std::min<size_t>((size_t)G, us.size() - q0);
-          int I[4][3];
-          for (int q = 0; q < nq; ++q) {
-            const TripItem &b = bs[us[q0 + q]];
-            I[q][0] = b.i;
-            I[q][1] = b.j;
-            I[q][2] = b.k;
-          }
-          for (long long t1 = 0; t1 < nt1; ++t1)
-            for (long long t2 = 0; t2 < nt2; ++t2) {
+        for (long long t1 = 0; t1 < nt1; ++t1)
+          for (long long t2 = 0; t2 < nt2; ++t2)
+            for (size_t q0 = 0; q0 < us.size(); q0 += (size_t)G) {
+              const int nq = (int)std::min<size_t>((size_t)G, us.size() - q0);
+              int I[4][3];
+              for (int q = 0; q < nq; ++q) {
+                const TripItem &b = bs[us[q0 + q]];
+                I[q][0] = b.i;
+                I[q][1] = b.j;
+                I[q][2] = b.k;
+              }
               pl.tile((int)(8 * t1), (int)(16 * t2), 0, bs[us[q0]].off);
               pl.items.back().nq = nq;
               for (int q = 1; q < nq; ++q) pl.items.back().qoff[q - 1] = bs[us[q0 + q]].off;
@@ -1135,7 +1145,6 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
                 }
               }
             }
-        }
       }
     });
     TcEpi epi = make_epi(W, o == 0 ? 0 : 1, 16, cs[p1], cs[p2], cs[o], s.nv, s.nv, s.nv, 1.0);

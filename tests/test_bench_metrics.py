@@ -78,3 +78,10 @@ def test_whole_step_call_sequence():
     jr = [c[1] for c in calls if c[0] == "jacobian_right"]
     assert len(jr[0][0]) == 2 and list(jr[1][0]) == [10.2]
     assert tally["in"] > x["chol"].numel() * 8 and tally["out"] > 0
+
+
+def test_site_totals_merge_chunks():
+    stats = {"bstc_gemv_kernel:o#1g0:y3d": (4, 2.0, 0.0), "bstc_gemv_kernel:o#1g1:y3d": (4, 4.0, 0.0),
+             "tc_gemm_kernel:build": (6, 10.0, 1e12), "contra3_kernel": (2, 0.5, 0.0)}
+    got = bench.site_totals(stats, 2)
+    assert got == {"tc_gemm_kernel:build": 5.0, "bstc_gemv_kernel:y3d": 3.0}
