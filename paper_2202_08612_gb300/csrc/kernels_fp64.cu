@@ -463,6 +463,106 @@ __global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
   }
 }
 
+// The binary32 form with 16-wide tiles (rows of 64 bytes instead of 32 for the
+// global loads and stores; 105 KB of shared memory per block): the same orbit
+// scheme, each of the 512 threads taking eight elements of every tile.
+namespace {
+constexpr int kC3W = 16, kC3WJ = kC3W + 1, kC3WI = kC3W * kC3WJ + 1, kC3WT = kC3W * kC3WI;
+constexpr size_t kC3WSmem = 6 * kC3WT * sizeof(float);
+}  // namespace
+
+__global__ void __launch_bounds__(512) contra3_w16_kernel(const float *__restrict__ X,
+                                                          float *__restrict__ Xt,
+                                                          long long nblocks, int nv) {
+  extern __shared__ float tl[];
+  __shared__ int org[6][3];
+  __shared__ int slot[6];
+  const long long blk = blockIdx.y;
+  if (blk >= nblocks) return;
+  const long long nv3 = (long long)nv * nv * nv;
+  const float *B = X + blk * nv3;
+  float *O = Xt + blk * nv3;
+  const int nt = (nv + kC3W - 1) / kC3W;
+  if (threadIdx.x == 0) {
+    int o = blockIdx.x, A = 0;
+    for (;; ++A) {
+      const int m = nt - A, cnt = m * (m + 1) / 2;
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    int Bt = A;
+    for (;; ++Bt) {
+      const int cnt = nt - Bt;
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    const int T[3] = {A, Bt, Bt + o};
+    for (int p = 0; p < 6; ++p) {
+      for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
+      int sl = p;
+      for (int r = 0; r < p; ++r)
+        if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
+          sl = slot[r];
+          break;
+        }
+      slot[p] = sl;
+    }
+  }
+  __syncthreads();
+  // element e = threadIdx.x + 512 r of a tile: (li, lj, lk) with lk fastest
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = threadIdx.x + 512 * r;
+      const int li = e >> 8, lj = (e >> 4) & 15, lk = e & 15;
+      const int x = kC3W * org[p][0] + li, y = kC3W * org[p][1] + lj, z = kC3W * org[p][2] + lk;
+      tl[p * kC3WT + li * kC3WI + lj * kC3WJ + lk] =
+          (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : 0.f;
+    }
+  }
+  __syncthreads();
+  const int A = org[0][0], Bt = org[0][1], C = org[0][2];
+  auto pos_of = [&](int e, int p) {  // position of permutation p of element e's orbit
+    const int l[3] = {e >> 8, (e >> 4) & 15, e & 15};
+    return slot[p] * kC3WT + l[kC3P[p][0]] * kC3WI + l[kC3P[p][1]] * kC3WJ + l[kC3P[p][2]];
+  };
+  float v[8][6];
+  unsigned own = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int e = threadIdx.x + 512 * r;
+    const int l0 = e >> 8, l1 = (e >> 4) & 15, l2 = e & 15;
+    if ((A < Bt || l0 <= l1) && (Bt < C || l1 <= l2) && kC3W * A + l0 < nv &&
+        kC3W * Bt + l1 < nv && kC3W * C + l2 < nv)
+      own |= 1u << r;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) v[r][p] = tl[pos_of(e, p)];
+  }
+  __syncthreads();  // every thread holds its inputs; the tiles now take the outputs
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    if (!((own >> r) & 1u)) continue;
+    const int e = threadIdx.x + 512 * r;
+    const float E = (v[r][0] + v[r][1]) + v[r][2], Od = (v[r][3] + v[r][4]) + v[r][5];
+    const float be = fmaf(-2.f, Od, E), bo = fmaf(-2.f, E, Od);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) tl[pos_of(e, p)] = fmaf(3.f, v[r][p], p < 3 ? be : bo);
+  }
+  __syncthreads();
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = threadIdx.x + 512 * r;
+      const int li = e >> 8, lj = (e >> 4) & 15, lk = e & 15;
+      const int x = kC3W * org[p][0] + li, y = kC3W * org[p][1] + lj, z = kC3W * org[p][2] + lk;
+      if (x < nv && y < nv && z < nv)
+        O[((long long)x * nv + y) * nv + z] = tl[p * kC3WT + li * kC3WI + lj * kC3WJ + lk];
+    }
+  }
+}
+
 // Launch of contra3_kernel over nblocks blocks (grid: tile orbits x blocks);
 // f32: the arrays hold binary32 elements (the split-precision mode's storage).
 cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int nv,
@@ -473,10 +573,14 @@ cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int n
   for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
     const long long nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
     const dim3 grid((unsigned)norb, (unsigned)nb);
-    if (f32)
-      contra3_kernel<float><<<grid, 512, 0, st>>>(reinterpret_cast<const float *>(X) + b0 * nv3,
-                                                  reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
-    else
+    if (f32) {
+      const long long nt16 = (nv + kC3W - 1) / kC3W, norb16 = nt16 * (nt16 + 1) * (nt16 + 2) / 6;
+      cudaError_t e = cudaFuncSetAttribute(contra3_w16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kC3WSmem);
+      if (e != cudaSuccess) return e;
+      contra3_w16_kernel<<<dim3((unsigned)norb16, (unsigned)nb), 512, kC3WSmem, st>>>(
+          reinterpret_cast<const float *>(X) + b0 * nv3, reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
+    } else
       contra3_kernel<double><<<grid, 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3, nb, nv);
   }
   return cudaGetLastError();
