@@ -918,8 +918,60 @@ namespace mlcc3 {
 //  * otherwise: one warp per output, the lanes along K with the contiguous K
 //    index (if any) the fastest.
 // FP32 products (B binary32 when b32, else converted), 16 per lane summed in
-// FP32 and folded into FP64; one atomic update per output.  Grid: x =
-// ceil(M / 8) (the first mapping uses ceil(M / 32) of them), y = items.
+// FP32 and folded into FP64; one atomic update per output (and per K slice).
+// Grid: x = 4 ceil(M / 8) (the second mapping uses the first quarter; the
+// first splits the extra blocks over K), y = items.
+// Strided dot product of a binary32 row with B over the K elements k = k0,
+// k0 + step, ... < kend, (k1, k2, k3) the split of k (k3 fastest) advanced with
+// carries.  U elements are loaded before their FMAs, so that a warp keeps U
+// loads in flight (one at a time leaves the loop bound by the load latency).
+// FP32 products, 16 per FP32 partial sum, partial sums added in FP64.
+template <int U, typename LdB>
+__device__ __forceinline__ double strided_dot32(const float *__restrict__ Am, LdB ldb,
+                                                const int Kn[3], const long long ka[3],
+                                                const long long kb[3], long long k0,
+                                                long long kend, int step) {
+  int k3 = (int)(k0 % Kn[2]);
+  const long long k12 = k0 / Kn[2];
+  int k2 = (int)(k12 % Kn[1]), k1 = (int)(k12 / Kn[1]);
+  const int d3 = step % Kn[2], d12 = step / Kn[2];
+  const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
+  double s = 0.0;
+  float sf = 0.f;
+  int nf = 0;
+  for (long long k = k0; k < kend; k += (long long)U * step) {
+    float av[U], bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k + (long long)u * step < kend;
+      av[u] = ok ? Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]] : 0.f;
+      bv[u] = ok ? ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]) : 0.f;
+      k3 += d3;
+      int c = 0;
+      if (k3 >= Kn[2]) {
+        k3 -= Kn[2];
+        c = 1;
+      }
+      k2 += d2 + c;
+      c = 0;
+      if (k2 >= Kn[1]) {
+        k2 -= Kn[1];
+        c = 1;
+      }
+      k1 += d1 + c;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) sf = fmaf(av[u], bv[u], sf);
+    nf += U;
+    if (nf >= 16) {
+      s += (double)sf;
+      sf = 0.f;
+      nf = 0;
+    }
+  }
+  return s + (double)sf;
+}
+
 __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   __shared__ double red[8][33];
   const BstcItem &it = p.items[blockIdx.y];
@@ -937,43 +989,23 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   if (M2 > 1 && it.sA[1] == 1) mf = 1;
   else if (it.sA[0] == 1 && (M1 > 1 || M2 == 1)) mf = 0;
   if (mf >= 0) {
-    if ((long long)blockIdx.x * 32 >= M) return;
-    const long long m = (long long)blockIdx.x * 32 + lane;
+    // blocks: (column group cg of 32 outputs, K slice z); the slices keep at
+    // least 64 reduction elements each
+    const long long ncg = (M + 31) / 32;
+    long long nsplit = gridDim.x / ncg;
+    const long long kmin = (K + 63) / 64;
+    if (nsplit > kmin) nsplit = kmin;
+    if (nsplit < 1) nsplit = 1;
+    const long long cg = blockIdx.x % ncg, z = blockIdx.x / ncg;
+    if (z >= nsplit) return;
+    const long long kc = (K + nsplit - 1) / nsplit, kbeg = z * kc, kend = kbeg + kc < K ? kbeg + kc : K;
+    const long long m = cg * 32 + lane;
     const bool valid = m < M;
     const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
     const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
-    double s = 0.0;
-    float sf = 0.f;
-    int nf = 0;
-    if (valid) {
-      // k = warp, warp + 8, ...: (k1, k2, k3) advanced with carries
-      int k3 = warp % Kn[2], k12 = warp / Kn[2];
-      int k2 = k12 % Kn[1], k1 = k12 / Kn[1];
-      const int d3 = 8 % Kn[2], d12 = 8 / Kn[2];
-      const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
-      for (long long k = warp; k < K; k += 8) {
-        sf = fmaf(Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]], ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]), sf);
-        if (++nf == 16) {
-          s += (double)sf;
-          sf = 0.f;
-          nf = 0;
-        }
-        k3 += d3;
-        int c = 0;
-        if (k3 >= Kn[2]) {
-          k3 -= Kn[2];
-          c = 1;
-        }
-        k2 += d2 + c;
-        c = 0;
-        if (k2 >= Kn[1]) {
-          k2 -= Kn[1];
-          c = 1;
-        }
-        k1 += d1 + c;
-      }
-    }
-    red[warp][lane] = s + (double)sf;
+    // the warps take k = kbeg + warp, + 8, ...
+    const double s = valid ? strided_dot32<8>(Am, ldb, Kn, ka, kb, kbeg + warp, kend, 8) : 0.0;
+    red[warp][lane] = s;
     __syncthreads();
     if (warp == 0 && valid) {
       double t = 0.0;
@@ -1000,35 +1032,7 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   if (m >= M) return;
   const long long m1 = m / M2, m2 = m % M2;
   const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
-  int k3 = lane % Kn[2], k12 = lane / Kn[2];
-  int k2 = k12 % Kn[1], k1 = k12 / Kn[1];
-  const int d3 = 32 % Kn[2], d12 = 32 / Kn[2];
-  const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
-  double s = 0.0;
-  float sf = 0.f;
-  int nf = 0;
-  for (long long k = lane; k < K; k += 32) {
-    sf = fmaf(Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]], ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]), sf);
-    if (++nf == 16) {
-      s += (double)sf;
-      sf = 0.f;
-      nf = 0;
-    }
-    k3 += d3;
-    int c = 0;
-    if (k3 >= Kn[2]) {
-      k3 -= Kn[2];
-      c = 1;
-    }
-    k2 += d2 + c;
-    c = 0;
-    if (k2 >= Kn[1]) {
-      k2 -= Kn[1];
-      c = 1;
-    }
-    k1 += d1 + c;
-  }
-  s += (double)sf;
+  double s = strided_dot32<8>(Am, ldb, Kn, ka, kb, lane, K, 32);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
@@ -1038,8 +1042,6 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   }
 }
 
-// Matrix-vector form of the batched strided contraction (N = 1): one warp per
-// output row m, the lanes stride over K, warp reduction, one (atomic) update.
 // Matrix-vector form of the batched strided contraction (N = 1): one warp per
 // output row m, the lanes stride over K, warp reduction, one (atomic) update.
 // Each lane splits its first K index into (k1, k2, k3) once and then advances

@@ -298,7 +298,7 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
       const std::string name = tag.empty() ? std::string("bstc_gemv_kernel") : "bstc_gemv_kernel:" + tag;
       launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
         if (p.a32)  // binary32 triples operand: the mapping follows its contiguous index
-          bstc_gemv32_kernel<<<grid, 256, 0, stream>>>(p);
+          bstc_gemv32_kernel<<<dim3(4 * grid.x, grid.y), 256, 0, stream>>>(p);
         else
           bstc_gemv_kernel<<<grid, 256, 0, stream>>>(p);
       });
