@@ -139,6 +139,9 @@ struct mlcc3_ctx {
   void zero_tri(double *p, size_t n);
   // item lists on the device, built once per pattern
   std::map<std::string, std::pair<void *, int>> items;
+  // host copies of the uploaded item lists, by device address (launch shapes
+  // that depend on the items' strides are chosen from them)
+  std::map<const void *, std::vector<mlcc3::BstcItem>> host_items;
   // hi/lo bfloat16 copies of operands of the tensor-core path, with their
   // tensor maps (MLCC3_SPLIT_BF16X3)
   struct SplitOp {

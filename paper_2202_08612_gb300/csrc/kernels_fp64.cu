@@ -389,54 +389,41 @@ constexpr int kC3SJ = 9, kC3SI = 8 * kC3SJ + 1, kC3T = 8 * kC3SI;  // padded til
 __constant__ int kC3P[6][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}};
 }  // namespace
 
-template <typename T>
-__global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
-                                                      T *__restrict__ Xt, long long nblocks,
-                                                      int nv) {
-  __shared__ T tile[6 * kC3T];
-  __shared__ int org[6][3];
-  __shared__ int slot[6];
-  const long long blk = blockIdx.y;
-  if (blk >= nblocks) return;
-  const long long nv3 = (long long)nv * nv * nv;
-  const T *B = X + blk * nv3;
-  T *O = Xt + blk * nv3;
-  const int nt = (nv + 7) / 8;
-  if (threadIdx.x == 0) {
-    // decode orbit index -> (A, B, C), A <= B <= C < nt
-    int o = blockIdx.x, A = 0;
-    for (;; ++A) {
-      const int m = nt - A, cnt = m * (m + 1) / 2;
-      if (o < cnt) break;
-      o -= cnt;
-    }
-    int Bt = A;
-    for (;; ++Bt) {
-      const int cnt = nt - Bt;
-      if (o < cnt) break;
-      o -= cnt;
-    }
-    const int T[3] = {A, Bt, Bt + o};
-    for (int p = 0; p < 6; ++p) {
-      for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
-      int sl = p;
-      for (int r = 0; r < p; ++r)
-        if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
-          sl = slot[r];
-          break;
-        }
-      slot[p] = sl;
-    }
+// Thread 0 of a block: orbit index o -> tile origins (A, B, C), A <= B <= C < nt,
+// the origins org[p] of the six permuted tiles and, for each, the slot of the
+// first permutation with the same origin (its shared-memory tile).
+__device__ __forceinline__ void c3_orbit(int o, int nt, int org[6][3], int slot[6]) {
+  int A = 0;
+  for (;; ++A) {
+    const int m = nt - A, cnt = m * (m + 1) / 2;
+    if (o < cnt) break;
+    o -= cnt;
   }
-  __syncthreads();
-  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
-  const int sidx = li * kC3SI + lj * kC3SJ + lk;
+  int Bt = A;
+  for (;; ++Bt) {
+    const int cnt = nt - Bt;
+    if (o < cnt) break;
+    o -= cnt;
+  }
+  const int T[3] = {A, Bt, Bt + o};
   for (int p = 0; p < 6; ++p) {
-    if (slot[p] != p) continue;
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    tile[p * kC3T + sidx] = (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : T(0);
+    for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
+    int sl = p;
+    for (int r = 0; r < p; ++r)
+      if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
+        sl = slot[r];
+        break;
+      }
+    slot[p] = sl;
   }
-  __syncthreads();
+}
+
+// The in-place transform of the staged tiles (all threads of the block; the
+// tiles hold X on entry and Xt on return, both barriers inside).
+template <typename T>
+__device__ __forceinline__ void c3_transform(T *tile, const int org[6][3], const int slot[6],
+                                             int nv) {
+  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
   const int A = org[0][0], Bt = org[0][1], C = org[0][2];
   const int l[3] = {li, lj, lk};
   const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
@@ -456,110 +443,40 @@ __global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
     for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(T(3), v[p], p < 3 ? be : bo);
   }
   __syncthreads();
-  for (int p = 0; p < 6; ++p) {
-    if (slot[p] != p) continue;
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
-  }
 }
 
-// The binary32 form with 16-wide tiles (rows of 64 bytes instead of 32 for the
-// global loads and stores; 105 KB of shared memory per block): the same orbit
-// scheme, each of the 512 threads taking eight elements of every tile.
-namespace {
-constexpr int kC3W = 16, kC3WJ = kC3W + 1, kC3WI = kC3W * kC3WJ + 1, kC3WT = kC3W * kC3WI;
-constexpr size_t kC3WSmem = 6 * kC3WT * sizeof(float);
-}  // namespace
-
-__global__ void __launch_bounds__(512) contra3_w16_kernel(const float *__restrict__ X,
-                                                          float *__restrict__ Xt,
-                                                          long long nblocks, int nv) {
-  extern __shared__ float tl[];
+template <typename T>
+__global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
+                                                      T *__restrict__ Xt, long long nblocks,
+                                                      int nv) {
+  __shared__ T tile[6 * kC3T];
   __shared__ int org[6][3];
   __shared__ int slot[6];
   const long long blk = blockIdx.y;
   if (blk >= nblocks) return;
   const long long nv3 = (long long)nv * nv * nv;
-  const float *B = X + blk * nv3;
-  float *O = Xt + blk * nv3;
-  const int nt = (nv + kC3W - 1) / kC3W;
-  if (threadIdx.x == 0) {
-    int o = blockIdx.x, A = 0;
-    for (;; ++A) {
-      const int m = nt - A, cnt = m * (m + 1) / 2;
-      if (o < cnt) break;
-      o -= cnt;
-    }
-    int Bt = A;
-    for (;; ++Bt) {
-      const int cnt = nt - Bt;
-      if (o < cnt) break;
-      o -= cnt;
-    }
-    const int T[3] = {A, Bt, Bt + o};
-    for (int p = 0; p < 6; ++p) {
-      for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
-      int sl = p;
-      for (int r = 0; r < p; ++r)
-        if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
-          sl = slot[r];
-          break;
-        }
-      slot[p] = sl;
-    }
-  }
+  const T *B = X + blk * nv3;
+  T *O = Xt + blk * nv3;
+  if (threadIdx.x == 0) c3_orbit(blockIdx.x, (nv + 7) / 8, org, slot);
   __syncthreads();
-  // element e = threadIdx.x + 512 r of a tile: (li, lj, lk) with lk fastest
+  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
+  const int sidx = li * kC3SI + lj * kC3SJ + lk;
+  // the six loads are issued before any of them is stored to shared memory
+  T x6[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    x6[p] = (slot[p] == p && x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : T(0);
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p)
+    if (slot[p] == p) tile[p * kC3T + sidx] = x6[p];
+  __syncthreads();
+  c3_transform(tile, org, slot, nv);
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int e = threadIdx.x + 512 * r;
-      const int li = e >> 8, lj = (e >> 4) & 15, lk = e & 15;
-      const int x = kC3W * org[p][0] + li, y = kC3W * org[p][1] + lj, z = kC3W * org[p][2] + lk;
-      tl[p * kC3WT + li * kC3WI + lj * kC3WJ + lk] =
-          (x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : 0.f;
-    }
-  }
-  __syncthreads();
-  const int A = org[0][0], Bt = org[0][1], C = org[0][2];
-  auto pos_of = [&](int e, int p) {  // position of permutation p of element e's orbit
-    const int l[3] = {e >> 8, (e >> 4) & 15, e & 15};
-    return slot[p] * kC3WT + l[kC3P[p][0]] * kC3WI + l[kC3P[p][1]] * kC3WJ + l[kC3P[p][2]];
-  };
-  float v[8][6];
-  unsigned own = 0;
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int e = threadIdx.x + 512 * r;
-    const int l0 = e >> 8, l1 = (e >> 4) & 15, l2 = e & 15;
-    if ((A < Bt || l0 <= l1) && (Bt < C || l1 <= l2) && kC3W * A + l0 < nv &&
-        kC3W * Bt + l1 < nv && kC3W * C + l2 < nv)
-      own |= 1u << r;
-#pragma unroll
-    for (int p = 0; p < 6; ++p) v[r][p] = tl[pos_of(e, p)];
-  }
-  __syncthreads();  // every thread holds its inputs; the tiles now take the outputs
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    if (!((own >> r) & 1u)) continue;
-    const int e = threadIdx.x + 512 * r;
-    const float E = (v[r][0] + v[r][1]) + v[r][2], Od = (v[r][3] + v[r][4]) + v[r][5];
-    const float be = fmaf(-2.f, Od, E), bo = fmaf(-2.f, E, Od);
-#pragma unroll
-    for (int p = 0; p < 6; ++p) tl[pos_of(e, p)] = fmaf(3.f, v[r][p], p < 3 ? be : bo);
-  }
-  __syncthreads();
-  for (int p = 0; p < 6; ++p) {
-    if (slot[p] != p) continue;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int e = threadIdx.x + 512 * r;
-      const int li = e >> 8, lj = (e >> 4) & 15, lk = e & 15;
-      const int x = kC3W * org[p][0] + li, y = kC3W * org[p][1] + lj, z = kC3W * org[p][2] + lk;
-      if (x < nv && y < nv && z < nv)
-        O[((long long)x * nv + y) * nv + z] = tl[p * kC3WT + li * kC3WI + lj * kC3WJ + lk];
-    }
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
   }
 }
 
@@ -573,14 +490,10 @@ cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int n
   for (long long b0 = 0; b0 < nblocks; b0 += 65535) {
     const long long nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
     const dim3 grid((unsigned)norb, (unsigned)nb);
-    if (f32) {
-      const long long nt16 = (nv + kC3W - 1) / kC3W, norb16 = nt16 * (nt16 + 1) * (nt16 + 2) / 6;
-      cudaError_t e = cudaFuncSetAttribute(contra3_w16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kC3WSmem);
-      if (e != cudaSuccess) return e;
-      contra3_w16_kernel<<<dim3((unsigned)norb16, (unsigned)nb), 512, kC3WSmem, st>>>(
-          reinterpret_cast<const float *>(X) + b0 * nv3, reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
-    } else
+    if (f32)
+      contra3_kernel<float><<<grid, 512, 0, st>>>(reinterpret_cast<const float *>(X) + b0 * nv3,
+                                                  reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
+    else
       contra3_kernel<double><<<grid, 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3, nb, nv);
   }
   return cudaGetLastError();
@@ -752,6 +665,81 @@ __device__ __forceinline__ unsigned int div_inv(unsigned int x, unsigned long lo
   return (unsigned int)(((unsigned long long)x * m) >> 40);
 }
 
+// One (term, permutation) pair of the rank-1 terms in the finish: the operand
+// indices are linear in the element's canonical coordinates (x0, x1, x2) with
+// coefficients ca / cb.
+struct FinishEnt {
+  const float *pa, *pb;
+  int ca[3], cb[3];
+  float coef;
+};
+
+// The entry of permutation sg of a rank-1 term (kind 2 or 3) for the occupied
+// triple I, choosing the symmetric or transposed form of an operand whose last
+// index is the element's fastest one.
+__device__ __forceinline__ FinishEnt finish_entry(const TripTerm &tm, int sg, const int I[3]) {
+  FinishEnt e;
+  const int p0 = kPerm[sg][0], p1 = kPerm[sg][1], p2 = kPerm[sg][2];
+  const long long x = I[p0], y = I[p1], z = I[p2];
+  e.coef = (float)tm.coef;
+  int au, av = 0, bv, bw;
+  if (tm.kind == 2) {  // A[x][u] B[y][z][v][w]
+    if (p0 == 2 && tm.At32) {
+      e.pa = tm.At32 + x * tm.sAt[1];
+      au = (int)tm.sAt[0];
+    } else {
+      e.pa = tm.A32 + x * tm.sA[0];
+      au = (int)tm.sA[1];
+    }
+    if (p1 == 2 && tm.sym) {
+      e.pb = tm.B32 + z * tm.sB[0] + y * tm.sB[1];
+      bv = (int)tm.sB[3];
+      bw = (int)tm.sB[2];
+    } else {
+      e.pb = tm.B32 + y * tm.sB[0] + z * tm.sB[1];
+      bv = (int)tm.sB[2];
+      bw = (int)tm.sB[3];
+    }
+  } else {  // A[x][y][u][v] B[z][w]
+    if (p0 == 2 && tm.sym) {
+      e.pa = tm.A32 + y * tm.sA[0] + x * tm.sA[1];
+      au = (int)tm.sA[3];
+      av = (int)tm.sA[2];
+    } else {
+      e.pa = tm.A32 + x * tm.sA[0] + y * tm.sA[1];
+      au = (int)tm.sA[2];
+      av = (int)tm.sA[3];
+    }
+    e.pb = tm.B32 + z * tm.sB[0];
+    bv = 0;
+    bw = (int)tm.sB[1];
+  }
+  // u = x_{p0}, v = x_{p1}, w = x_{p2}
+  for (int k = 0; k < 3; ++k) {
+    e.ca[k] = (p0 == k ? au : 0) + (p1 == k ? av : 0);
+    e.cb[k] = (p1 == k ? bv : 0) + (p2 == k ? bw : 0);
+  }
+  return e;
+}
+
+// Appends e to tab[0..n) or, when an entry with the same operands and
+// coefficients is there, adds its coefficient to that one: the two
+// permutations that a symmetric operand relates (and any that coincide for
+// equal occupied indices) give the same entry, since the symmetric forms above
+// are chosen by position.  Returns the new count.
+__device__ __forceinline__ int finish_merge(FinishEnt *tab, int n, const FinishEnt &e) {
+  for (int m = 0; m < n; ++m) {
+    FinishEnt &f = tab[m];
+    if (f.pa == e.pa && f.pb == e.pb && f.ca[0] == e.ca[0] && f.ca[1] == e.ca[1] &&
+        f.ca[2] == e.ca[2] && f.cb[0] == e.cb[0] && f.cb[1] == e.cb[1] && f.cb[2] == e.cb[2]) {
+      f.coef += e.coef;
+      return n;
+    }
+  }
+  tab[n] = e;
+  return n + 1;
+}
+
 // Finish of the split-precision triples build: X = -(W + rank-1 terms) / (eps - omega)
 // per element of every block in `items`, W the FP32 sum of the six permuted
 // two-index terms (Eq. tau3 / Eq. R3 / SI L3) accumulated by the tensor cores.
@@ -759,8 +747,7 @@ __device__ __forceinline__ unsigned int div_inv(unsigned int x, unsigned long lo
 // six permutations in FP32, from FP32 copies of their operands; for each
 // (term, permutation) the block first tabulates base pointers and the 32-bit
 // coefficients that make each operand index linear in the element's canonical
-// coordinates, choosing the symmetric or transposed form of an operand whose
-// last index is the element's fastest one; each thread then takes eight
+// coordinates (finish_entry, finish_merge); each thread then takes eight
 // elements per pass over the table.  eps^{abc}_{ijk} - omega is an exact
 // double-float sum of FP32 (hi, lo) pairs (ehl: the virtual energies' pairs),
 // which keeps FP64 accuracy off the FP64 pipe; the quotient of the FP32
@@ -771,13 +758,7 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
     unsigned long long nvinv, double omega_v, const double *__restrict__ omega_p,
     double *__restrict__ out, int out32, int *__restrict__ status) {
-  // one (term, permutation) pair: the operand indices are linear in the
-  // element's canonical coordinates (x0, x1, x2) with coefficients ca / cb
-  struct Ent {
-    const float *pa, *pb;
-    int ca[3], cb[3];
-    float coef;
-  };
+  using Ent = FinishEnt;
   __shared__ Ent tab[2 * kMaxTerms * 6];
   __shared__ float2 ev[1024];
   __shared__ float eoh, eol;
@@ -793,60 +774,71 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     eol = (float)(eo - (double)eoh);
     int n = 0;
     for (int t = 0; t < terms.n; ++t) {
-      const TripTerm &tm = terms.t[t];
-      if (tm.kind < 2) continue;
-      for (int sg = 0; sg < 6; ++sg) {
-        Ent e;
-        const int p0 = kPerm[sg][0], p1 = kPerm[sg][1], p2 = kPerm[sg][2];
-        const long long x = I[p0], y = I[p1], z = I[p2];
-        e.coef = (float)tm.coef;
-        int au, av = 0, bv, bw;
-        if (tm.kind == 2) {  // A[x][u] B[y][z][v][w]
-          if (p0 == 2 && tm.At32) {
-            e.pa = tm.At32 + x * tm.sAt[1];
-            au = (int)tm.sAt[0];
-          } else {
-            e.pa = tm.A32 + x * tm.sA[0];
-            au = (int)tm.sA[1];
-          }
-          if (p1 == 2 && tm.sym) {
-            e.pb = tm.B32 + z * tm.sB[0] + y * tm.sB[1];
-            bv = (int)tm.sB[3];
-            bw = (int)tm.sB[2];
-          } else {
-            e.pb = tm.B32 + y * tm.sB[0] + z * tm.sB[1];
-            bv = (int)tm.sB[2];
-            bw = (int)tm.sB[3];
-          }
-        } else {  // A[x][y][u][v] B[z][w]
-          if (p0 == 2 && tm.sym) {
-            e.pa = tm.A32 + y * tm.sA[0] + x * tm.sA[1];
-            au = (int)tm.sA[3];
-            av = (int)tm.sA[2];
-          } else {
-            e.pa = tm.A32 + x * tm.sA[0] + y * tm.sA[1];
-            au = (int)tm.sA[2];
-            av = (int)tm.sA[3];
-          }
-          e.pb = tm.B32 + z * tm.sB[0];
-          bv = 0;
-          bw = (int)tm.sB[1];
-        }
-        // u = x_{p0}, v = x_{p1}, w = x_{p2}
-        for (int k = 0; k < 3; ++k) {
-          e.ca[k] = (p0 == k ? au : 0) + (p1 == k ? av : 0);
-          e.cb[k] = (p1 == k ? bv : 0) + (p2 == k ? bw : 0);
-        }
-        tab[n++] = e;
-      }
+      if (terms.t[t].kind < 2) continue;
+      for (int sg = 0; sg < 6; ++sg) n = finish_merge(tab, n, finish_entry(terms.t[t], sg, I));
     }
     nent = n;
   }
   __syncthreads();
-  // eight elements per thread and pass (r0 + k * stride), so that each table
-  // entry is read once per eight elements
   const unsigned int nv3 = (unsigned int)nv * nv * nv;
   const unsigned int stride = gridDim.x * blockDim.x;
+  // no rank-1 terms: a streaming pass, four 16-byte loads in flight per thread
+  // (quads of consecutive elements; a block whose offset or pointers are not
+  // 16-byte aligned takes the general loop below)
+  if (nent == 0 && nv >= 4 && (nv3 & 3u) == 0 && (it.off & 3) == 0 &&
+      ((reinterpret_cast<unsigned long long>(W) | reinterpret_cast<unsigned long long>(out)) & 15) == 0) {
+    const unsigned int nq = nv3 / 4;
+    const float4 *W4 = reinterpret_cast<const float4 *>(W + it.off);
+    for (unsigned int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < nq; q0 += 4 * stride) {
+      float4 w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned int q = q0 + k * stride;
+        w[k] = q < nq ? W4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned int q = q0 + k * stride;
+        if (q >= nq) break;
+        const unsigned int r = 4 * q;
+        const unsigned int q1 = div_inv(r, nvinv);
+        int x0 = (int)div_inv(q1, nvinv);
+        int x1 = (int)(q1 - (unsigned int)x0 * nv);
+        int x2 = (int)(r - q1 * nv);
+        const float wv[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+        float qv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float dh = ev[x0].x, dl = ev[x0].y;
+          df_add(dh, dl, ev[x1].x, ev[x1].y);
+          df_add(dh, dl, ev[x2].x, ev[x2].y);
+          df_add(dh, dl, eoh, eol);
+          const float den = dh + dl;
+          qv[e] = 0.f;
+          if (fabsf(den) < 1e-3f)
+            atomicOr(status, 1);
+          else
+            qv[e] = -wv[e] * __frcp_rn(den);
+          if (++x2 == nv) {  // next element: carry into x1, x0
+            x2 = 0;
+            if (++x1 == nv) {
+              x1 = 0;
+              ++x0;
+            }
+          }
+        }
+        if (out32)
+          reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + it.off)[q] =
+              make_float4(qv[0], qv[1], qv[2], qv[3]);
+        else
+#pragma unroll
+          for (int e = 0; e < 4; ++e) out[it.off + r + e] = widen_f32(qv[e]);
+      }
+    }
+    return;
+  }
+  // eight elements per thread and pass (r0 + k * stride), so that each table
+  // entry is read once per eight elements
   for (unsigned int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < nv3; r0 += 8 * stride) {
     float acc[8];
     int x0[8], x1[8], x2[8];
@@ -891,6 +883,98 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
       else
         out[it.off + r] = widen_f32(q);
     }
+  }
+}
+
+// Fused finish and contravariant transform of the split-precision triples
+// build (binary32 storage).  Block (o, u) takes the tile orbit o (8-wide tiles,
+// as in contra3_kernel) of batch u: it loads the orbit's distinct permuted
+// tiles of W, finishes every element in registers as triples_finish_kernel
+// does (rank-1 terms, -1 / (eps - omega)), stores X (unless out is null) and
+// keeps it in shared memory, then applies the in-place transform of
+// contra3_kernel and stores Xt (Eq. contra_3).  W is read once and X is not
+// read back: 12 bytes per element instead of 16 for the two separate passes.
+__global__ void __launch_bounds__(512, 4) triples_finish_contra_kernel(
+    const float *__restrict__ W, const TripItem *__restrict__ items, int nitems,
+    const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
+    double omega_v, const double *__restrict__ omega_p, float *__restrict__ out,
+    float *__restrict__ outt, int *__restrict__ status) {
+  __shared__ float tile[6 * kC3T];
+  __shared__ FinishEnt raw[kMaxTerms * 6], tab[kMaxTerms * 6];
+  __shared__ int org[6][3], slot[6];
+  __shared__ float eoh, eol;
+  __shared__ int nent;
+  if ((int)blockIdx.y >= nitems) return;
+  const TripItem it = items[blockIdx.y];
+  const int I[3] = {it.i, it.j, it.k};
+  const int t = threadIdx.x;
+  int nr = 0;  // rank-1 terms
+  for (int q = 0; q < terms.n; ++q) nr += terms.t[q].kind >= 2 ? 1 : 0;
+  if (t < 6 * nr) {  // thread 6 r + sg: entry sg of the r-th rank-1 term
+    int q = 0;
+    for (int r = t / 6;; ++q)
+      if (terms.t[q].kind >= 2 && r-- == 0) break;
+    raw[t] = finish_entry(terms.t[q], t % 6, I);
+  }
+  if (t == 0) {
+    c3_orbit(blockIdx.x, (nv + 7) / 8, org, slot);
+    const double omega = omega_p ? *omega_p : omega_v;
+    const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
+    eoh = (float)eo;
+    eol = (float)(eo - (double)eoh);
+  }
+  __syncthreads();
+  if (nr > 0) {
+    if (t == 0) {
+      int n = 0;
+      for (int q = 0; q < 6 * nr; ++q) n = finish_merge(tab, n, raw[q]);
+      nent = n;
+    }
+    __syncthreads();
+  }
+  const int ne = nr > 0 ? nent : 0;
+  const int li = t / 64, lj = (t / 8) % 8, lk = t % 8;
+  const int sidx = li * kC3SI + lj * kC3SJ + lk;
+  const float *Wb = W + it.off;
+  float w6[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    w6[p] = (slot[p] == p && x < nv && y < nv && z < nv) ? Wb[((long long)x * nv + y) * nv + z] : 0.f;
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    float q = 0.f;
+    if (x < nv && y < nv && z < nv) {
+      float acc = w6[p];
+      for (int n = 0; n < ne; ++n) {
+        const FinishEnt &e = tab[n];
+        acc = fmaf(e.coef * e.pa[x * e.ca[0] + y * e.ca[1] + z * e.ca[2]],
+                   e.pb[x * e.cb[0] + y * e.cb[1] + z * e.cb[2]], acc);
+      }
+      const float2 ex = __ldg(ehl + x), ey = __ldg(ehl + y), ez = __ldg(ehl + z);
+      float dh = ex.x, dl = ex.y;
+      df_add(dh, dl, ey.x, ey.y);
+      df_add(dh, dl, ez.x, ez.y);
+      df_add(dh, dl, eoh, eol);
+      const float den = dh + dl;
+      if (fabsf(den) < 1e-3f)
+        atomicOr(status, 1);
+      else
+        q = -acc * __frcp_rn(den);
+      if (out) out[it.off + ((long long)x * nv + y) * nv + z] = q;
+    }
+    tile[p * kC3T + sidx] = q;
+  }
+  __syncthreads();
+  c3_transform(tile, org, slot, nv);
+  float *O = outt + it.off;
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
+    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
   }
 }
 
@@ -985,16 +1069,26 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   const long long K = (long long)Kn[0] * Kn[1] * Kn[2];
   auto ldb = [&](long long i) { return Bf ? Bf[i] : (float)Bd[i]; };
   // output mapping along a contiguous output index
-  int mf = -1;  // 1: m2 is contiguous (m2 fastest), 0: m1 contiguous (m1 fastest)
-  if (M2 > 1 && it.sA[1] == 1) mf = 1;
-  else if (it.sA[0] == 1 && (M1 > 1 || M2 == 1)) mf = 0;
+  const GemvMap g = gemv32_map(it, M1, M2, K);
+  const int mf = g.mf;
+  if (mf >= 0 && g.small_k) {
+    // a warp per group of 32 consecutive outputs, the whole of K
+    const long long cg = (long long)blockIdx.x * 8 + warp;
+    if (cg >= g.ncg) return;
+    const long long m = cg * 32 + lane;
+    if (m >= M) return;
+    const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
+    const double s = strided_dot32<8>(A + m1 * it.sA[0] + m2 * it.sA[1], ldb, Kn, ka, kb, 0, K, 1);
+    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
+    if (p.atomic) atomicAdd(C, p.alpha * s);
+    else *C += p.alpha * s;
+    return;
+  }
   if (mf >= 0) {
-    // blocks: (column group cg of 32 outputs, K slice z); the slices keep at
-    // least 64 reduction elements each
-    const long long ncg = (M + 31) / 32;
-    long long nsplit = gridDim.x / ncg;
-    const long long kmin = (K + 63) / 64;
-    if (nsplit > kmin) nsplit = kmin;
+    // blocks: (column group cg of 32 outputs, K slice z), the warps of a block
+    // striding over its slice
+    const long long ncg = g.ncg;
+    long long nsplit = p.kchunk > 0 ? p.kchunk : gridDim.x / ncg;
     if (nsplit < 1) nsplit = 1;
     const long long cg = blockIdx.x % ncg, z = blockIdx.x / ncg;
     if (z >= nsplit) return;

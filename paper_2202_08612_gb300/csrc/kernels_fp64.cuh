@@ -16,6 +16,26 @@ struct BstcItem {
   long long sC[4];  // m1, m2, n1, n2
 };
 
+// Mapping of one item in the binary32 matrix-vector kernel (N = 1), shared by
+// the kernel and the host's choice of grid: mf = 1 (0) when the output index
+// m2 (m1) is contiguous in A, -1 when neither is; with a contiguous output
+// index a short reduction (small_k) gives each warp 32 outputs and the whole
+// of K, a long one gives each block 32 outputs and a slice of K.  ncg = groups
+// of 32 outputs.
+struct GemvMap {
+  int mf;
+  bool small_k;
+  long long ncg;
+};
+constexpr long long kGemvSmallK = 1024;
+__host__ __device__ inline GemvMap gemv32_map(const BstcItem &it, long long M1, long long M2,
+                                              long long K) {
+  GemvMap g{-1, K <= kGemvSmallK, (M1 * M2 + 31) / 32};
+  if (M2 > 1 && it.sA[1] == 1) g.mf = 1;
+  else if (it.sA[0] == 1 && (M1 > 1 || M2 == 1)) g.mf = 0;
+  return g;
+}
+
 struct BstcParams {
   const double *A, *B;
   double *C;
@@ -24,7 +44,8 @@ struct BstcParams {
   const BstcItem *items;
   int nitems;
   int atomic;        // 1: accumulate with atomicAdd (items may overlap in C)
-  long long kchunk;  // split-K: grid.z slices of this many K elements (0 = whole K)
+  long long kchunk;  // split-K: grid.z slices of this many K elements (0 = whole K); the
+                     // binary32 matrix-vector kernel: the number of K slices (0: from the grid)
   int a32, b32;      // 1: A (B) holds binary32 elements (element offsets and strides as given)
 };
 

@@ -59,6 +59,9 @@ __global__ void density_norm_kernel(double *, const double *, const double *, co
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
                                       const double *, const float2 *, int, unsigned long long,
                                       double, const double *, double *, int, int *);
+__global__ void triples_finish_contra_kernel(const float *, const TripItem *, int, const TripTerms,
+                                             const double *, const float2 *, int, double,
+                                             const double *, float *, float *, int *);
 __global__ void hilo_kernel(const double *, float2 *, int);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
@@ -211,6 +214,7 @@ const BstcItem *mlcc3_ctx::dev_items(const std::string &key,
                "upload items");
   items[key] = {p, (int)v.size()};
   *n = (int)v.size();
+  host_items[p] = std::move(v);
   return static_cast<const BstcItem *>(p);
 }
 
@@ -295,10 +299,39 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
       p.items = it + z0;
       int nz = std::min(65535, nitems - z0);
       dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
+      if (p.a32) {
+        // binary32 triples operand: each item's mapping follows its contiguous
+        // index; the grid covers the item that needs the most blocks
+        p.kchunk = 0;
+        auto hv = host_items.find(it);
+        if (hv != host_items.end() && (int)hv->second.size() >= z0 + nz) {
+          const long long K = sh.K1 * sh.K2 * sh.K3;
+          long long gx = 1, ncg_min = -1;
+          for (int q = z0; q < z0 + nz; ++q) {
+            const GemvMap g = gemv32_map(hv->second[q], sh.M1, sh.M2, K);
+            if (g.mf >= 0 && !g.small_k) ncg_min = ncg_min < 0 ? g.ncg : std::min(ncg_min, g.ncg);
+            gx = std::max(gx, g.mf < 0 ? (M + 7) / 8 : g.small_k ? (g.ncg + 7) / 8 : g.ncg);
+          }
+          if (ncg_min > 0) {
+            // K slices for the output-contiguous items with a long reduction:
+            // about two waves of blocks over the launch, slices of >= 512 elements
+            const long long want = (2LL * 152 * 8 + (long long)nz * ncg_min - 1) / ((long long)nz * ncg_min);
+            const long long ns = std::max(1LL, std::min({want, (K + 511) / 512, 16LL}));
+            p.kchunk = ns;
+            long long gmax = 1;
+            for (int q = z0; q < z0 + nz; ++q) {
+              const GemvMap g = gemv32_map(hv->second[q], sh.M1, sh.M2, K);
+              gmax = std::max(gmax, g.mf < 0 ? (M + 7) / 8 : g.small_k ? (g.ncg + 7) / 8 : g.ncg * ns);
+            }
+            gx = gmax;
+          }
+          grid.x = (unsigned)gx;
+        }
+      }
       const std::string name = tag.empty() ? std::string("bstc_gemv_kernel") : "bstc_gemv_kernel:" + tag;
       launch(name.c_str(), 2.0 * M * (double)(sh.K1 * sh.K2 * sh.K3) * nz, [&] {
-        if (p.a32)  // binary32 triples operand: the mapping follows its contiguous index
-          bstc_gemv32_kernel<<<dim3(4 * grid.x, grid.y), 256, 0, stream>>>(p);
+        if (p.a32)
+          bstc_gemv32_kernel<<<grid, 256, 0, stream>>>(p);
         else
           bstc_gemv_kernel<<<grid, 256, 0, stream>>>(p);
       });
@@ -1055,11 +1088,16 @@ SplitTerm split_l(mlcc3_ctx *c, const std::string &ak, const double *ampl, bool 
 //   index sits at position o and the L-part of each W^{sigma} whose third
 //   virtual index sits at position o (Eq. tau3, P^{abc}_{ijk}).
 // triples_finish_kernel then adds the rank-1 terms and divides by (eps - omega).
+// With outt set the contravariant blocks (Eq. contra_3) are formed as well:
+// with binary32 storage by triples_finish_contra_kernel in the same pass (out is
+// then written only if keep_out), else by contra3 over the nbt blocks.
 void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
                    const std::vector<TripTerm> &rank1, const std::string &bkey,
-                   const std::vector<TripItem> &bs, double omega, double *out) {
+                   const std::vector<TripItem> &bs, double omega, double *out,
+                   double *outt = nullptr, long long nbt = 0, bool keep_out = true) {
   S s(c);
   c->wrote(out);
+  if (outt) c->wrote(outt);
   if (bs.empty() || s.nv == 0) return;
   if (terms.size() * 6 > (size_t)kTcMaps) throw Error{MLCC3_ERR_ARG, "too many tensor-core terms"};
   TcMaps maps;
@@ -1175,6 +1213,16 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     const long long gx = std::max<long long>(1, std::min<long long>((s.nv3 + 255) / 256, (16 * 152 + nbc - 1) / nbc));
     dim3 grid((unsigned)gx, (unsigned)nbc);
     const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
+    if (outt && c->tri32) {
+      const long long nt = (s.nv + 7) / 8, norb = nt * (nt + 1) * (nt + 2) / 6;
+      c->launch("triples_finish_contra_kernel", 0.0, [&] {
+        triples_finish_contra_kernel<<<dim3((unsigned)norb, (unsigned)nbc), 512, 0, c->stream>>>(
+            W, db + b0, (int)nbc, tt, c->eps, ehl, (int)s.nv, omega, c->omega_dev,
+            keep_out ? reinterpret_cast<float *>(out) : nullptr, reinterpret_cast<float *>(outt),
+            c->status);
+      });
+      continue;
+    }
     const unsigned long long nvinv = ((1ULL << 40) + (unsigned long long)s.nv - 1) / (unsigned long long)s.nv;
     c->launch("triples_finish_kernel", 0.0, [&] {
       triples_finish_kernel<<<grid, 256, 0, c->stream>>>(W, db + b0, (int)nbc, tt, c->eps, ehl,
@@ -1183,6 +1231,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
+  if (outt && !c->tri32) contra3(c, out, outt, nbt);
 }
 
 bool split_mode(const mlcc3_ctx *c) { return c->precision == MLCC3_SPLIT_BF16X3; }
@@ -1748,9 +1797,10 @@ std::vector<SplitTerm> tau_split_terms(mlcc3_ctx *c) {
 }
 
 // L3 / lambda3 (SI): D (Lc, Gb), L (LcT, Gx), plus the rank-1 terms in FP64.
+// outt, nbt, keep_out: the contravariant blocks as in triples_split.
 void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const double *Lc,
                   const double *LcT, const std::string &bkey, const std::vector<TripItem> &bs,
-                  double omega, double *out) {
+                  double omega, double *out, double *outt, long long nbt, bool keep_out = true) {
   S s(c);
   std::vector<TripTerm> full = {
       term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
@@ -1759,6 +1809,7 @@ void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const 
       term(3, 0, 0.5, Lc, {s.bi, s.bL, s.ba, 1}, c->F, {s.nv, 1, 0, 0})};
   if (!split_mode(c)) {
     triples(c, full, bkey, bs, omega, out);
+    contra3(c, out, outt, nbt);
     return;
   }
   // the rank-1 terms' operands are pair-symmetric (g_jbkc, Lc), and L1 is also
@@ -1782,7 +1833,7 @@ void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const 
   full[3].B32 = static_cast<const float *>(c->raw("f32:F", 4));
   SplitTerm d = split_d(c, tag + "c", Lc, true, "Gb", c->Gb, false);
   SplitTerm l = split_l(c, tag + "cT", LcT, true, "Gx", c->Gx, false);
-  triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out);
+  triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out, outt, nbt, keep_out);
 }
 
 // FP32 copy of n doubles in the named scratch buffer.
@@ -1818,11 +1869,12 @@ void build_tau(mlcc3_ctx *c, const Chunk &ch, double **tau, double **taut) {
   if (c->tau_valid && c->tau_key == ch.key) return;
   c->tau_valid = true;
   c->tau_key = ch.key;
-  if (split_mode(c))
-    triples_split(c, tau_split_terms(c), {}, "b" + ch.key, ch.bs, 0.0, *tau);
-  else
+  if (split_mode(c)) {
+    triples_split(c, tau_split_terms(c), {}, "b" + ch.key, ch.bs, 0.0, *tau, *taut, ch.nb);
+  } else {
     triples(c, tau_terms(c), "b" + ch.key, ch.bs, 0.0, *tau);
-  contra3(c, *tau, *taut, ch.nb);
+    contra3(c, *tau, *taut, ch.nb);
+  }
 }
 
 // Upsilon blocks for one trial vector (Eqs. ups_v, ups_o) and the rho tau-term
@@ -1899,9 +1951,10 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1, const std::string &tag = "", b
 }
 
 // R3 (Eq. R3): D (Rbar, Gv), L (Rbar_l, Go), D (t, Upsilon_v), L (Tl, Upsilon_o).
+// outt, nbt: the contravariant blocks as in triples_split.
 void right_triples(mlcc3_ctx *c, const double *Rbar, const double *Rbl, const Ups &u,
                    const std::string &bkey, const std::vector<TripItem> &bs, double omega,
-                   double *out) {
+                   double *out, double *outt, long long nbt) {
   S s(c);
   if (!split_mode(c)) {
     std::vector<TripTerm> terms = {
@@ -1910,13 +1963,14 @@ void right_triples(mlcc3_ctx *c, const double *Rbar, const double *Rbl, const Up
         term(0, (int)s.NV, 1.0, c->t2c, {s.bi, s.bL, s.ba, 1}, u.Uv, {s.gk, s.gb, s.gc, 1}),
         term(1, (int)s.NO, -1.0, c->Tl, {s.ti, s.ta, s.tb, 1}, u.Uo, {s.oj, s.ok, s.oc, 1})};
     triples(c, terms, bkey, bs, omega, out);
+    contra3(c, out, outt, nbt);
     return;
   }
   SplitTerm d1 = split_d(c, "Rbar", Rbar, true, "Gv", c->Gv, false);
   SplitTerm l1 = split_l(c, "Rbarl", Rbl, true, "Go", c->Go, false);
   SplitTerm d2 = split_d(c, "t", c->t2c, false, "Uv", u.Uv, true);
   SplitTerm l2 = split_l(c, "Tl", c->Tl, false, "Uo", u.Uo, true);
-  triples_split(c, {d1, l1, d2, l2}, {}, bkey, bs, omega, out);
+  triples_split(c, {d1, l1, d2, l2}, {}, bkey, bs, omega, out, outt, nbt);
 }
 
 }  // namespace
@@ -2059,9 +2113,8 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
       double *R3t = c->tri_buf("R3t", (size_t)ch.nb * s.nv3);
       // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
       c->omega_dev = omega_dev ? omega_dev + v : nullptr;
-      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3);
+      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3, R3t, ch.nb);
       c->omega_dev = nullptr;
-      contra3(c, R3, R3t, ch.nb);
       BackSet b;
       b.cs = 0.5; b.Gs = c->Govov;
       b.cF = 0.5; b.F = c->F;
@@ -2130,8 +2183,7 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       const std::vector<Ord> &os = ch.own;
       const std::string okey = "o" + ch.key;
       // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
-      left_triples(c, "L", L1, Lc, LcT, "b" + ch.key, ch.bs, omega[v], L3);
-      contra3(c, L3, L3t, ch.nb);
+      left_triples(c, "L", L1, Lc, LcT, "b" + ch.key, ch.bs, omega[v], L3, L3t, ch.nb);
       // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
       BackSet b;
       b.cL = -1.0; b.GL = c->Go; b.gl_key = "Go";
@@ -2632,8 +2684,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     // the contravariant form exists, so L3 reuses its buffer
     double *lam3 = c->tri_buf("L3", bw);
     double *lt3 = c->tri_buf("lam3t", bw);
-    left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3);
-    contra3(c, lam3, lt3, ch.nb);
+    left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3, lt3, ch.nb, false);
     // D^{0-0} (state independent)
     density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
     for (int st = 0; st < n_st; ++st) {
@@ -2647,15 +2698,19 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     // L3 (omega) and R3 (omega), with their contravariant forms (CVS: core batches only)
     double *L3 = c->tri_buf("L3", bw);
     double *L3t = c->tri_buf("L3t", bw);
-    if (cvs) c->zero_tri(L3, bw);
+    if (cvs) {  // the blocks outside the core-valence space stay zero
+      c->zero_tri(L3, bw);
+      c->zero_tri(L3t, bw);
+    }
     const std::string bkey3 = cvs ? bkey + "cvs" : bkey;  // the batch list is cached per key
-    left_triples(c, "L", L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3);
-    contra3(c, L3, L3t, ch.nb);
+    left_triples(c, "L", L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3, L3t, ch.nb);
     double *R3 = c->tri_buf("R3", bw);
     double *R3t = c->tri_buf("R3t", bw);
-    if (cvs) c->zero_tri(R3, bw);
-    right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3);
-    contra3(c, R3, R3t, ch.nb);
+    if (cvs) {
+      c->zero_tri(R3, bw);
+      c->zero_tri(R3t, bw);
+    }
+    right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3, R3t, ch.nb);
     // D^{m-0}
     density_left_gpu(c, ch, L3t, so.Lc32, tau, taut, so.Dm0);
 
@@ -2834,8 +2889,7 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     build_tau(c, ch, &tau, &taut);
     double *lam3 = c->tri_buf("lam3", bw);
     double *lt3 = c->tri_buf("lam3t", bw);
-    left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3);
-    contra3(c, lam3, lt3, ch.nb);
+    left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3, lt3, ch.nb, false);
     density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
   }
 }
