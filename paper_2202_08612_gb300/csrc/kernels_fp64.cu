@@ -887,19 +887,32 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
 }
 
 // Fused finish and contravariant transform of the split-precision triples
-// build (binary32 storage).  Block (o, u) takes the tile orbit o (8-wide tiles,
-// as in contra3_kernel) of batch u: it loads the orbit's distinct permuted
-// tiles of W, finishes every element in registers as triples_finish_kernel
-// does (rank-1 terms, -1 / (eps - omega)), stores X (unless out is null) and
-// keeps it in shared memory, then applies the in-place transform of
-// contra3_kernel and stores Xt (Eq. contra_3).  W is read once and X is not
-// read back: 12 bytes per element instead of 16 for the two separate passes.
-__global__ void __launch_bounds__(512, 4) triples_finish_contra_kernel(
+// build (binary32 storage).  Block (o, u) takes the orbit o of 16-wide tiles
+// (origins A <= B <= C, the orbit scheme of contra3_kernel with rows of 64
+// bytes) of batch u:
+//  1. the orbit's distinct permuted tiles of W are copied to shared memory by
+//     asynchronous 4-byte copies (48 in flight per thread, no registers held;
+//     elements outside the block are zero-filled);
+//  2. every element is finished as in triples_finish_kernel (rank-1 terms,
+//     -1 / (eps - omega)) in place, and X is stored (unless out is null);
+//  3. each thread takes the element orbits it owns in tile (A, B, C), reads
+//     their six permuted values and writes the six outputs of Eq. contra_3 in
+//     place (the orbits are disjoint, so no barrier separates the reads from
+//     the writes), and Xt is stored.
+// W is read once and X is not read back: 12 bytes per element instead of 16
+// for separate finish and transform passes.  512 threads, each taking eight
+// elements of every tile; 105 KB of dynamic shared memory (two blocks per SM).
+namespace {
+constexpr int kFW = 16, kFSJ = kFW + 1, kFSI = kFW * kFSJ + 1, kFT = kFW * kFSI;
+}  // namespace
+constexpr size_t kFinishContraSmem = 6 * kFT * sizeof(float);
+
+__global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
     const float *__restrict__ W, const TripItem *__restrict__ items, int nitems,
     const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
     double omega_v, const double *__restrict__ omega_p, float *__restrict__ out,
     float *__restrict__ outt, int *__restrict__ status) {
-  __shared__ float tile[6 * kC3T];
+  extern __shared__ float ftile[];
   __shared__ FinishEnt raw[kMaxTerms * 6], tab[kMaxTerms * 6];
   __shared__ int org[6][3], slot[6];
   __shared__ float eoh, eol;
@@ -917,65 +930,129 @@ __global__ void __launch_bounds__(512, 4) triples_finish_contra_kernel(
     raw[t] = finish_entry(terms.t[q], t % 6, I);
   }
   if (t == 0) {
-    c3_orbit(blockIdx.x, (nv + 7) / 8, org, slot);
+    c3_orbit(blockIdx.x, (nv + kFW - 1) / kFW, org, slot);
     const double omega = omega_p ? *omega_p : omega_v;
     const double eo = -eps[it.i] - eps[it.j] - eps[it.k] - omega;
     eoh = (float)eo;
     eol = (float)(eo - (double)eoh);
   }
   __syncthreads();
-  if (nr > 0) {
-    if (t == 0) {
-      int n = 0;
-      for (int q = 0; q < 6 * nr; ++q) n = finish_merge(tab, n, raw[q]);
-      nent = n;
-    }
-    __syncthreads();
+  if (t == 0 && nr > 0) {
+    int n = 0;
+    for (int q = 0; q < 6 * nr; ++q) n = finish_merge(tab, n, raw[q]);
+    nent = n;
   }
-  const int ne = nr > 0 ? nent : 0;
-  const int li = t / 64, lj = (t / 8) % 8, lk = t % 8;
-  const int sidx = li * kC3SI + lj * kC3SJ + lk;
+  // element e = t + 512 r of a tile: (l0, l1, l2) = (e >> 8, (e >> 4) & 15, e & 15)
+  const int l0b = t >> 8, l1 = (t >> 4) & 15, l2 = t & 15;
   const float *Wb = W + it.off;
-  float w6[6];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) {
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    w6[p] = (slot[p] == p && x < nv && y < nv && z < nv) ? Wb[((long long)x * nv + y) * nv + z] : 0.f;
-  }
-#pragma unroll
+  // 1. asynchronous copies of the distinct tiles
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    float q = 0.f;
-    if (x < nv && y < nv && z < nv) {
-      float acc = w6[p];
+    const int y = kFW * org[p][1] + l1, z = kFW * org[p][2] + l2;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int l0 = l0b + 2 * r, x = kFW * org[p][0] + l0;
+      const bool ok = x < nv && y < nv && z < nv;
+      const float *src = ok ? Wb + ((long long)x * nv + y) * nv + z : Wb;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(ftile + p * kFT + l0 * kFSI + l1 * kFSJ + l2)),
+                   "l"(src), "r"(ok ? 4u : 0u)
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  // 2. finish in place, X stored
+  const int ne = nr > 0 ? nent : 0;
+  for (int p = 0; p < 6; ++p) {
+    if (slot[p] != p) continue;
+    const int y = kFW * org[p][1] + l1, z = kFW * org[p][2] + l2;
+    if (y >= nv || z >= nv) continue;
+    const float2 ey = __ldg(ehl + y), ez = __ldg(ehl + z);
+    float yh = ey.x, yl = ey.y;  // eps_y + eps_z + (-eps_ijk - omega), shared by the column
+    df_add(yh, yl, ez.x, ez.y);
+    df_add(yh, yl, eoh, eol);
+#pragma unroll 2
+    for (int r = 0; r < 8; ++r) {
+      const int l0 = l0b + 2 * r, x = kFW * org[p][0] + l0;
+      if (x >= nv) break;
+      float *cell = ftile + p * kFT + l0 * kFSI + l1 * kFSJ + l2;
+      float acc = *cell;
       for (int n = 0; n < ne; ++n) {
         const FinishEnt &e = tab[n];
         acc = fmaf(e.coef * e.pa[x * e.ca[0] + y * e.ca[1] + z * e.ca[2]],
                    e.pb[x * e.cb[0] + y * e.cb[1] + z * e.cb[2]], acc);
       }
-      const float2 ex = __ldg(ehl + x), ey = __ldg(ehl + y), ez = __ldg(ehl + z);
+      const float2 ex = __ldg(ehl + x);
       float dh = ex.x, dl = ex.y;
-      df_add(dh, dl, ey.x, ey.y);
-      df_add(dh, dl, ez.x, ez.y);
-      df_add(dh, dl, eoh, eol);
+      df_add(dh, dl, yh, yl);
       const float den = dh + dl;
+      float q = 0.f;
       if (fabsf(den) < 1e-3f)
         atomicOr(status, 1);
       else
         q = -acc * __frcp_rn(den);
+      *cell = q;
       if (out) out[it.off + ((long long)x * nv + y) * nv + z] = q;
     }
-    tile[p * kC3T + sidx] = q;
   }
   __syncthreads();
-  c3_transform(tile, org, slot, nv);
+  // 3. the transform of the element orbits owned in tile (A, B, C)
+  {
+    const int A = org[0][0], Bt = org[0][1], C = org[0][2];
+#pragma unroll 2
+    for (int r = 0; r < 8; ++r) {
+      const int l0 = l0b + 2 * r;
+      const bool own = (A < Bt || l0 <= l1) && (Bt < C || l1 <= l2) && kFW * A + l0 < nv &&
+                       kFW * Bt + l1 < nv && kFW * C + l2 < nv;
+      if (!own) continue;
+      const int l[3] = {l0, l1, l2};
+      float v[6];
+      int pos[6];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        pos[p] = slot[p] * kFT + l[kC3P[p][0]] * kFSI + l[kC3P[p][1]] * kFSJ + l[kC3P[p][2]];
+        v[p] = ftile[pos[p]];
+      }
+      const float E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
+      const float be = fmaf(-2.f, Od, E), bo = fmaf(-2.f, E, Od);
+#pragma unroll
+      for (int p = 0; p < 6; ++p) ftile[pos[p]] = fmaf(3.f, v[p], p < 3 ? be : bo);
+    }
+  }
+  __syncthreads();
   float *O = outt + it.off;
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
+    const int y = kFW * org[p][1] + l1, z = kFW * org[p][2] + l2;
+    if (y >= nv || z >= nv) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int l0 = l0b + 2 * r, x = kFW * org[p][0] + l0;
+      if (x < nv) O[((long long)x * nv + y) * nv + z] = ftile[p * kFT + l0 * kFSI + l1 * kFSJ + l2];
+    }
   }
+}
+
+// Launch of triples_finish_contra_kernel over nbatch batches (grid: orbits of
+// 16-wide tiles x batches), raising the kernel's dynamic shared-memory limit
+// on first use.
+cudaError_t launch_finish_contra(const float *W, const TripItem *items, int nbatch,
+                                 const TripTerms &terms, const double *eps, const float2 *ehl,
+                                 int nv, double omega, const double *omega_p, float *out,
+                                 float *outt, int *status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(triples_finish_contra_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFinishContraSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const long long nt = (nv + kFW - 1) / kFW, norb = nt * (nt + 1) * (nt + 2) / 6;
+  triples_finish_contra_kernel<<<dim3((unsigned)norb, (unsigned)nbatch), 512, kFinishContraSmem, st>>>(
+      W, items, nbatch, terms, eps, ehl, nv, omega, omega_p, out, outt, status);
+  return cudaGetLastError();
 }
 
 // (hi, lo) FP32 pairs of n doubles: hi = binary32(x), lo = binary32(x - hi).

@@ -59,9 +59,9 @@ __global__ void density_norm_kernel(double *, const double *, const double *, co
 __global__ void triples_finish_kernel(const float *, const TripItem *, int, const TripTerms,
                                       const double *, const float2 *, int, unsigned long long,
                                       double, const double *, double *, int, int *);
-__global__ void triples_finish_contra_kernel(const float *, const TripItem *, int, const TripTerms,
-                                             const double *, const float2 *, int, double,
-                                             const double *, float *, float *, int *);
+cudaError_t launch_finish_contra(const float *, const TripItem *, int, const TripTerms &,
+                                 const double *, const float2 *, int, double, const double *,
+                                 float *, float *, int *, cudaStream_t);
 __global__ void hilo_kernel(const double *, float2 *, int);
 bool encode_map(CUtensorMap *m, const void *base, const unsigned long long dims[4],
                 const unsigned long long strides[3], const unsigned box[4], std::string *err);
@@ -1214,12 +1214,12 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     dim3 grid((unsigned)gx, (unsigned)nbc);
     const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
     if (outt && c->tri32) {
-      const long long nt = (s.nv + 7) / 8, norb = nt * (nt + 1) * (nt + 2) / 6;
       c->launch("triples_finish_contra_kernel", 0.0, [&] {
-        triples_finish_contra_kernel<<<dim3((unsigned)norb, (unsigned)nbc), 512, 0, c->stream>>>(
-            W, db + b0, (int)nbc, tt, c->eps, ehl, (int)s.nv, omega, c->omega_dev,
-            keep_out ? reinterpret_cast<float *>(out) : nullptr, reinterpret_cast<float *>(outt),
-            c->status);
+        check_cuda(launch_finish_contra(W, db + b0, (int)nbc, tt, c->eps, ehl, (int)s.nv, omega,
+                                        c->omega_dev,
+                                        keep_out ? reinterpret_cast<float *>(out) : nullptr,
+                                        reinterpret_cast<float *>(outt), c->status, c->stream),
+                   "finish_contra");
       });
       continue;
     }
