@@ -142,6 +142,17 @@ struct mlcc3_ctx {
   // host copies of the uploaded item lists, by device address (launch shapes
   // that depend on the items' strides are chosen from them)
   std::map<const void *, std::vector<mlcc3::BstcItem>> host_items;
+  // D_LD-type contractions deferred to the end of a density call: each
+  // accumulator V (summed over the chunks) is contracted once with X into D
+  struct DeferredLD {
+    std::string name;
+    double *V;
+    const double *X;
+    double *D;
+    double alpha;
+    std::string tag;
+  };
+  std::vector<DeferredLD> dld_pending;
   // hi/lo bfloat16 copies of operands of the tensor-core path, with their
   // tensor maps (MLCC3_SPLIT_BF16X3)
   struct SplitOp {

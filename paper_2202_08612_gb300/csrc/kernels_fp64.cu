@@ -1082,31 +1082,31 @@ namespace mlcc3 {
 // FP32 and folded into FP64; one atomic update per output (and per K slice).
 // Grid: x = 4 ceil(M / 8) (the second mapping uses the first quarter; the
 // first splits the extra blocks over K), y = items.
-// Strided dot product of a binary32 row with B over the K elements k = k0,
-// k0 + step, ... < kend, (k1, k2, k3) the split of k (k3 fastest) advanced with
-// carries.  U elements are loaded before their FMAs, so that a warp keeps U
-// loads in flight (one at a time leaves the loop bound by the load latency).
-// FP32 products, 16 per FP32 partial sum, partial sums added in FP64.
-template <int U, typename LdB>
-__device__ __forceinline__ double strided_dot32(const float *__restrict__ Am, LdB ldb,
-                                                const int Kn[3], const long long ka[3],
-                                                const long long kb[3], long long k0,
-                                                long long kend, int step) {
+// Strided dot product of a row of A (binary32 or binary64) with B over the K
+// elements k = k0, k0 + step, ... < kend, (k1, k2, k3) the split of k (k3
+// fastest) advanced with carries.  U elements are loaded before their FMAs, so
+// that a warp keeps U loads in flight (one at a time leaves the loop bound by
+// the load latency).  Binary32 A: FP32 products, 16 per FP32 partial sum,
+// partial sums added in FP64; binary64 A: FP64 products and sums.
+template <int U, typename TA, typename LdB>
+__device__ __forceinline__ double strided_dot(const TA *__restrict__ Am, LdB ldb, const int Kn[3],
+                                              const long long ka[3], const long long kb[3],
+                                              long long k0, long long kend, int step) {
   int k3 = (int)(k0 % Kn[2]);
   const long long k12 = k0 / Kn[2];
   int k2 = (int)(k12 % Kn[1]), k1 = (int)(k12 / Kn[1]);
   const int d3 = step % Kn[2], d12 = step / Kn[2];
   const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
   double s = 0.0;
-  float sf = 0.f;
+  TA sf = TA(0);
   int nf = 0;
   for (long long k = k0; k < kend; k += (long long)U * step) {
-    float av[U], bv[U];
+    TA av[U], bv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool ok = k + (long long)u * step < kend;
-      av[u] = ok ? Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]] : 0.f;
-      bv[u] = ok ? ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]) : 0.f;
+      av[u] = ok ? Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]] : TA(0);
+      bv[u] = ok ? ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]) : TA(0);
       k3 += d3;
       int c = 0;
       if (k3 >= Kn[2]) {
@@ -1122,30 +1122,48 @@ __device__ __forceinline__ double strided_dot32(const float *__restrict__ Am, Ld
       k1 += d1 + c;
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) sf = fmaf(av[u], bv[u], sf);
+    for (int u = 0; u < U; ++u) sf = fma(av[u], bv[u], sf);
     nf += U;
     if (nf >= 16) {
       s += (double)sf;
-      sf = 0.f;
+      sf = TA(0);
       nf = 0;
     }
   }
   return s + (double)sf;
 }
 
-__global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
+// Matrix-vector form of the batched strided contraction (N = 1).  The triples
+// arrays are permuted views of n_v^3 blocks and the amplitude arrays are
+// strided, so the index that is contiguous in A may be an output index or a
+// reduction index, depending on the item; each block takes one item and picks
+// the mapping whose loads run along the contiguous index (gemv32_map):
+//  * an output index contiguous, short reduction: each warp takes 32
+//    consecutive outputs along it and the whole of K;
+//  * an output index contiguous, long reduction: each block takes 32
+//    consecutive outputs, its 8 warps split its slice of K (sums of the warps
+//    added in shared memory; p.kchunk slices per output group, or as many as
+//    the grid holds);
+//  * otherwise: one warp per output, the lanes along K with the contiguous K
+//    index (if any) the fastest.
+// TA = float: binary32 A (the split mode's triples arrays), FP32 products (B
+// binary32 when b32, else converted) folded into FP64 sums; TA = double: FP64
+// products and sums.  One (atomic) update per output and K slice.  Grid: x =
+// the most blocks any item's mapping needs (ceil(M / 8) covers them all),
+// y = items.
+template <typename TA>
+__device__ __forceinline__ void gemv_body(const BstcParams &p) {
   __shared__ double red[8][33];
   const BstcItem &it = p.items[blockIdx.y];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long M1 = p.M1, M2 = p.M2, M = M1 * M2;
-  const float *A = reinterpret_cast<const float *>(p.A) + it.offA;
+  const TA *A = reinterpret_cast<const TA *>(p.A) + it.offA;
   const float *Bf = p.b32 ? reinterpret_cast<const float *>(p.B) + it.offB : nullptr;
   const double *Bd = p.B + (p.b32 ? 0 : it.offB);
   int Kn[3] = {p.K1, p.K2, p.K3};
   long long ka[3] = {it.sA[2], it.sA[3], it.sA[4]}, kb[3] = {it.sB[0], it.sB[1], it.sB[2]};
   const long long K = (long long)Kn[0] * Kn[1] * Kn[2];
-  auto ldb = [&](long long i) { return Bf ? Bf[i] : (float)Bd[i]; };
-  // output mapping along a contiguous output index
+  auto ldb = [&](long long i) { return Bf ? (TA)Bf[i] : (TA)Bd[i]; };
   const GemvMap g = gemv32_map(it, M1, M2, K);
   const int mf = g.mf;
   if (mf >= 0 && g.small_k) {
@@ -1155,7 +1173,7 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
     const long long m = cg * 32 + lane;
     if (m >= M) return;
     const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
-    const double s = strided_dot32<8>(A + m1 * it.sA[0] + m2 * it.sA[1], ldb, Kn, ka, kb, 0, K, 1);
+    const double s = strided_dot<8>(A + m1 * it.sA[0] + m2 * it.sA[1], ldb, Kn, ka, kb, 0, K, 1);
     double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
     if (p.atomic) atomicAdd(C, p.alpha * s);
     else *C += p.alpha * s;
@@ -1173,9 +1191,9 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
     const long long m = cg * 32 + lane;
     const bool valid = m < M;
     const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
-    const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
+    const TA *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
     // the warps take k = kbeg + warp, + 8, ...
-    const double s = valid ? strided_dot32<8>(Am, ldb, Kn, ka, kb, kbeg + warp, kend, 8) : 0.0;
+    const double s = valid ? strided_dot<8>(Am, ldb, Kn, ka, kb, kbeg + warp, kend, 8) : 0.0;
     red[warp][lane] = s;
     __syncthreads();
     if (warp == 0 && valid) {
@@ -1202,8 +1220,8 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   const long long m = (long long)blockIdx.x * 8 + warp;
   if (m >= M) return;
   const long long m1 = m / M2, m2 = m % M2;
-  const float *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
-  double s = strided_dot32<8>(Am, ldb, Kn, ka, kb, lane, K, 32);
+  const TA *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
+  double s = strided_dot<8>(Am, ldb, Kn, ka, kb, lane, K, 32);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
@@ -1213,73 +1231,10 @@ __global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) {
   }
 }
 
-// Matrix-vector form of the batched strided contraction (N = 1): one warp per
-// output row m, the lanes stride over K, warp reduction, one (atomic) update.
-// Each lane splits its first K index into (k1, k2, k3) once and then advances
-// them by 32 with 32-bit carries (no division per element).  FP64 products:
-// every element is used once, so converting it would cost more than its FMA.
-__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) {
-  const BstcItem &it = p.items[blockIdx.y];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const long long M = (long long)p.M1 * p.M2;
-  const long long m = (long long)blockIdx.x * 8 + warp;
-  if (m >= M) return;
-  const int K1 = p.K1, K2 = p.K2, K3 = p.K3;
-  const long long K = (long long)K1 * K2 * K3;
-  const long long m1 = m / p.M2, m2 = m % p.M2;
-  const long long offA = it.offA + m1 * it.sA[0] + m2 * it.sA[1];
-  const double *B = p.B + it.offB;
-  const long long a1 = it.sA[2], a2 = it.sA[3], a3 = it.sA[4];
-  const long long b1 = it.sB[0], b2 = it.sB[1], b3 = it.sB[2];
-  int k3 = lane % K3, k12 = lane / K3;
-  int k2 = k12 % K2, k1 = k12 / K2;
-  const int d3 = 32 % K3, d12 = 32 / K3;  // advance of (k3, k12) per step
-  const int d2 = d12 % K2, d1 = d12 / K2;
-  double s = 0.0;
-  // binary32 A (the split mode's triples arrays): FP32 products, eight per lane
-  // summed in FP32 and then folded into the FP64 sum (one conversion of B per
-  // element instead of a conversion of A and an FP64 product)
-  // (with a binary32 B as well no conversion is left: the products stay off the
-  // FP64 pipe, which retires about two operations per clock and SM on GB300)
-  const float *Af = p.a32 ? reinterpret_cast<const float *>(p.A) + offA : nullptr;
-  const float *Bf = p.b32 ? reinterpret_cast<const float *>(p.B) + it.offB : nullptr;
-  float sf = 0.f;
-  int nf = 0;
-  for (long long k = lane; k < K; k += 32) {
-    if (Af) {
-      const long long ib = k1 * b1 + k2 * b2 + k3 * b3;
-      sf = fmaf(Af[k1 * a1 + k2 * a2 + k3 * a3], Bf ? Bf[ib] : (float)B[ib], sf);
-      if (++nf == 16) {
-        s += (double)sf;
-        sf = 0.f;
-        nf = 0;
-      }
-    } else {
-      s += p.A[offA + k1 * a1 + k2 * a2 + k3 * a3] * B[k1 * b1 + k2 * b2 + k3 * b3];
-    }
-    k3 += d3;
-    int c = 0;
-    if (k3 >= K3) {
-      k3 -= K3;
-      c = 1;
-    }
-    k2 += d2 + c;
-    c = 0;
-    if (k2 >= K2) {
-      k2 -= K2;
-      c = 1;
-    }
-    k1 += d1 + c;
-  }
-  s += (double)sf;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
-    if (p.atomic) atomicAdd(C, p.alpha * s);
-    else *C += p.alpha * s;
-  }
-}
+__global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) { gemv_body<float>(p); }
+
+__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) { gemv_body<double>(p); }
+
 
 }  // namespace mlcc3
 
@@ -1292,17 +1247,20 @@ namespace mlcc3 {
 // at voff[v] with strides vstr[3v..3v+2] of its (a, b, c) (v = (p no + q) no + r,
 // vhave[v] = 0 for a missing block); the strides are a permutation of
 // (nv^2, nv, 1).  The block copies its no views' offsets and axis orders to
-// shared memory once, then sweeps TA x 8 x 8 tiles of (a,b,c) (tile =
+// shared memory once, then sweeps TA x TB x TB tiles of (a,b,c) (tile =
 // blockIdx.x, blockIdx.x + gridDim.x, ...): for every view, consecutive
 // threads take consecutive elements along that view's stride-1 axis, so each
-// load is a run of whole sectors whatever the permutation, and the element is
+// load is a run of whole sectors whatever the permutation (with j <= i that
+// axis is b or c, the one of the smaller of j and the view's third index,
+// except for ties: the binary32 form takes TA = 2, TB = 16, rows of 64 bytes),
+// and the element is
 // stored at its logical (a,b,c) position of the view's tile in shared memory
 // (padded strides, no bank conflicts along any axis; pads stay zero).  Thread
 // t keeps a 4x4 (k,l) tile (t % TT) of partial sums over the (t / TT)-th share
 // of every tile and adds it to `out` once.  T is the type of the products and
 // of the per-tile sums (FP32 in the split-precision mode, else FP64); the sums
 // over tiles are FP64.  Requires no <= 32.
-template <typename T, int TA>
+template <typename T, int TA, int TB>
 __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
                                                const T *__restrict__ Y,
                                                const long long *__restrict__ voff,
@@ -1310,10 +1268,10 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
                                                const char *__restrict__ vhave, int no, int nv, int p0,
                                                double *__restrict__ out, long long ldo, int kl,
                                                double alpha) {
-  constexpr int PB = 9, PA = 8 * PB + 1;        // padded logical strides of b and a
+  constexpr int PB = TB + 1, PA = TB * PB + 1;  // padded logical strides of b and a
   constexpr int TE = TA * PA;                   // positions of one view's tile
   constexpr int TS = (TE + 31) / 32 * 32 + 1;   // row stride of a view, 1 mod 32
-  constexpr int NE = TA * 64;                   // elements of a tile
+  constexpr int NE = TA * TB * TB;              // elements of a tile
   extern __shared__ unsigned char smraw[];
   T *xs = reinterpret_cast<T *>(smraw);         // [no][TS]
   T *ys = xs + (size_t)no * TS;                 // [no][TS]
@@ -1360,14 +1318,14 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
-  const int ta = (nv + TA - 1) / TA, tb = (nv + 7) / 8, tc = (nv + 7) / 8;
+  const int ta = (nv + TA - 1) / TA, tb = (nv + TB - 1) / TB, tc = (nv + TB - 1) / TB;
   const int ntiles = ta * tb * tc;
   for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
-    const int a0 = TA * (q / (tb * tc)), b0 = 8 * ((q / tc) % tb), c0 = 8 * (q % tc);
+    const int a0 = TA * (q / (tb * tc)), b0 = TB * ((q / tc) % tb), c0 = TB * (q % tc);
     __syncthreads();  // the previous tile's reads are done
     for (int r = 0; r < no; ++r) {
       const int f = s_ax[r][0], m = s_ax[r][1];
-      const int df = f == 0 ? TA : 8, dm = m == 0 ? TA : 8;
+      const int df = f == 0 ? TA : TB, dm = m == 0 ? TA : TB;
       const bool hv = s_have[r] != 0;
       const long long base = s_off[r];
       const int sa = s_st[r][0], sb = s_st[r][1], sc = s_st[r][2];
@@ -1438,23 +1396,23 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
 
 // Shared-memory bytes of pair_dots_*_kernel for no views.
 size_t pair_dots_smem(int no, bool f32) {
-  const int TA = f32 ? 8 : 4;
-  const int TE = TA * 73, TS = (TE + 31) / 32 * 32 + 1;
+  const int TA = f32 ? 2 : 4, TB = f32 ? 16 : 8;
+  const int TE = TA * (TB * (TB + 1) + 1), TS = (TE + 31) / 32 * 32 + 1;
   return 2 * (size_t)no * TS * (f32 ? sizeof(float) : sizeof(double));
 }
 
 // Tiles of the (a,b,c) cube swept by pair_dots_*_kernel.
 long long pair_dots_tiles(int nv, bool f32) {
-  const int TA = f32 ? 8 : 4;
-  return (long long)((nv + TA - 1) / TA) * ((nv + 7) / 8) * ((nv + 7) / 8);
+  const int TA = f32 ? 2 : 4, TB = f32 ? 16 : 8;
+  return (long long)((nv + TA - 1) / TA) * ((nv + TB - 1) / TB) * ((nv + TB - 1) / TB);
 }
 
 // FP32 operands (FP32 copies of the triples arrays, split-precision mode).
-__global__ void __launch_bounds__(256, 3) pair_dots_f32_kernel(
+__global__ void __launch_bounds__(256, 2) pair_dots_f32_kernel(
     const float *__restrict__ X, const float *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<float, 8>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<float, 2, 16>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 // Physical-order form of pair_dots_f32_kernel for n_v a multiple of 4 (every
@@ -1604,7 +1562,7 @@ __global__ void __launch_bounds__(256) pair_dots_f64_kernel(
     const double *__restrict__ X, const double *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<double, 4>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<double, 4, 8>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 }  // namespace mlcc3

@@ -723,9 +723,16 @@ __device__ __forceinline__ void split_bf16_body(const Tin *__restrict__ in, __nv
   const long long rows = D0 * D1 * D2;
   const int g = threadIdx.x / 64, t = threadIdx.x % 64;
   const int k3 = (int)K3, k3p = (int)K3p;
-  for (long long r = (long long)blockIdx.x * 4 + g; r < rows; r += (long long)gridDim.x * 4) {
-    const long long o2 = r % D2, r1 = r / D2;
-    const long long o1 = r1 % D1, o0 = r1 / D1;
+  // each group of 64 threads takes a contiguous range of rows, so that the row
+  // indices (o0, o1, o2) are split by division once and then carried (a 64-bit
+  // division per row cost more than the row's copy)
+  const long long ngroups = (long long)gridDim.x * 4;
+  const long long per = (rows + ngroups - 1) / ngroups;
+  long long r = ((long long)blockIdx.x * 4 + g) * per;
+  const long long rend = r + per < rows ? r + per : rows;
+  if (r >= rend) return;
+  long long o2 = r % D2, o1 = (r / D2) % D1, o0 = (r / D2) / D1;
+  for (; r < rend; ++r) {
     const Tin *src = in + o0 * s0 + o1 * s1 + o2 * s2;
     __nv_bfloat16 *h = hi + r * K3p, *l = lo + r * K3p;
     for (int k = 4 * t; k < k3p; k += 256) {
@@ -734,6 +741,13 @@ __device__ __forceinline__ void split_bf16_body(const Tin *__restrict__ in, __nv
       for (int j = 0; j < 4; ++j)
         x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : Tin(0);
       split4_store(x, h + k, l + k);
+    }
+    if (++o2 == D2) {
+      o2 = 0;
+      if (++o1 == D1) {
+        o1 = 0;
+        ++o0;
+      }
     }
   }
 }
@@ -772,18 +786,27 @@ __device__ __forceinline__ void split_bf16_k2_body(const Tin *__restrict__ in, _
     const long long o1 = r % D1, o0 = r / D1;
     const Tin *src = in + o0 * s0 + o1 * s1;
     __nv_bfloat16 *h = hi + r * Kp, *l = lo + r * Kp;
+    // (q1, q2) = split of k, advanced by 256 per step with a carry
+    int q1 = (4 * t) / kk2, q2 = 4 * t - q1 * kk2;
+    const int dq1 = 256 / kk2, dq2 = 256 - dq1 * kk2;
     for (int k = 4 * t; k < kp; k += 256) {
-      int q1 = k / kk2, q2 = k - q1 * kk2;
+      int a1 = q1, a2 = q2;
       Tin x[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        x[j] = k + j < K ? scaled(src[(long long)q1 * sk1 + (long long)q2 * sk2], mode, scale) : Tin(0);
-        if (++q2 == kk2) {
-          q2 = 0;
-          ++q1;
+        x[j] = k + j < K ? scaled(src[(long long)a1 * sk1 + (long long)a2 * sk2], mode, scale) : Tin(0);
+        if (++a2 == kk2) {
+          a2 = 0;
+          ++a1;
         }
       }
       split4_store(x, h + k, l + k);
+      q1 += dq1;
+      q2 += dq2;
+      if (q2 >= kk2) {
+        q2 -= kk2;
+        ++q1;
+      }
     }
   }
 }
@@ -808,25 +831,42 @@ namespace mlcc3 {
 
 // Batched transpose with the hi/lo bfloat16 split: for b < B, r < Rp, c < C
 //   hi/lo[b db + c dr + r] = split(src[b sb + r sr + c])   (r < R; zero for R <= r < Rp)
-// through 32 x 32 shared-memory tiles, so that both the FP64 reads (along c) and
-// the bf16 writes (along r) are coalesced.  Blocks of 32 x 8 threads loop over
-// (batch, tile) pairs.
+// through 64 x 32 (r x c) shared-memory tiles, so that both the reads (along c,
+// 32 elements per row) and the bf16 writes (along r, 64 elements = 128 bytes
+// per column) are coalesced.  Blocks of 32 x 8 threads loop over (batch, tile)
+// pairs; each thread keeps the next tile's eight loads in flight while it
+// stores the current one.  Rp is a multiple of 8.
+template <typename Tin>
+__device__ __forceinline__ void split8_store(const Tin *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+  unsigned int hb[8], lb[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    __nv_bfloat16 h, l;
+    split_hi_lo(x[j], h, l);
+    hb[j] = __bfloat16_as_ushort(h);
+    lb[j] = __bfloat16_as_ushort(l);
+  }
+  *reinterpret_cast<uint4 *>(hi) = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16),
+                                              hb[4] | (hb[5] << 16), hb[6] | (hb[7] << 16));
+  *reinterpret_cast<uint4 *>(lo) = make_uint4(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16),
+                                              lb[4] | (lb[5] << 16), lb[6] | (lb[7] << 16));
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(256) split_transpose_kernel(
     const Tin *__restrict__ src, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
     long long B, int R, int Rp, int C, long long sb, long long sr, long long db, long long dr) {
-  __shared__ Tin tile[32][33];
-  const int tr = (Rp + 31) / 32, tc = (C + 31) / 32;
+  __shared__ Tin tile[64][33];
+  const int tr = (Rp + 63) / 64, tc = (C + 31) / 32;
   const long long ntiles = B * (long long)tr * tc;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  // rows ty, ty + 8, ty + 16, ty + 24 of tile q, column tx, into registers: the
-  // next tile's loads are issued before this tile's stores
-  Tin pf[4];
+  // rows ty, ty + 8, ..., ty + 56 of tile q, column tx, into registers
+  Tin pf[8];
   auto load = [&](long long q) {
     const long long b = q / ((long long)tr * tc);
-    const int r0 = (int)((q / tc) % tr) * 32, c = (int)(q % tc) * 32 + tx;
+    const int r0 = (int)((q / tc) % tr) * 64, c = (int)(q % tc) * 32 + tx;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
       const int r = r0 + ty + 8 * k;
       pf[k] = (r < R && c < C) ? src[b * sb + (long long)r * sr + c] : Tin(0);
     }
@@ -834,22 +874,21 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
   if (blockIdx.x < ntiles) load(blockIdx.x);
   for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
     const long long b = q / ((long long)tr * tc);
-    const int rt = (int)((q / tc) % tr), ct = (int)(q % tc);
-    const int r0 = rt * 32, c0 = ct * 32;
+    const int r0 = (int)((q / tc) % tr) * 64, c0 = (int)(q % tc) * 32;
     __syncthreads();  // the previous tile's reads of `tile` are done
 #pragma unroll
-    for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = pf[k];
+    for (int k = 0; k < 8; ++k) tile[ty + 8 * k][tx] = pf[k];
     __syncthreads();
     if (q + gridDim.x < ntiles) load(q + gridDim.x);
-    {
-      // thread t writes four consecutive r (8-byte stores) of column c0 + t / 8
-      const int ci = threadIdx.x >> 3, rq = 4 * (threadIdx.x & 7);
-      const int c = c0 + ci, r = r0 + rq;
-      if (c < C && r < Rp) {
-        const Tin x[4] = {tile[rq][ci], tile[rq + 1][ci], tile[rq + 2][ci], tile[rq + 3][ci]};
-        const long long o = b * db + (long long)c * dr + r;
-        split4_store(x, hi + o, lo + o);
-      }
+    // thread t writes eight consecutive r (16-byte stores) of column c0 + t / 8
+    const int ci = threadIdx.x >> 3, rq = 8 * (threadIdx.x & 7);
+    const int c = c0 + ci, r = r0 + rq;
+    if (c < C && r < Rp) {
+      Tin x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = tile[rq + j][ci];
+      const long long o = b * db + (long long)c * dr + r;
+      split8_store(x, hi + o, lo + o);
     }
   }
 }
@@ -857,7 +896,7 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
 cudaError_t split_transpose(const double *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, long long B,
                             int R, int Rp, int C, long long sb, long long sr, long long db,
                             long long dr, cudaStream_t st, bool in32) {
-  const long long ntiles = B * (long long)((Rp + 31) / 32) * ((C + 31) / 32);
+  const long long ntiles = B * (long long)((Rp + 63) / 64) * ((C + 31) / 32);
   if (ntiles <= 0) return cudaSuccess;
   const long long g = ntiles < 152LL * 16 ? ntiles : 152LL * 16;
   if (in32)

@@ -299,9 +299,9 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
       p.items = it + z0;
       int nz = std::min(65535, nitems - z0);
       dim3 grid((unsigned)((M + 7) / 8), (unsigned)nz);
-      if (p.a32) {
-        // binary32 triples operand: each item's mapping follows its contiguous
-        // index; the grid covers the item that needs the most blocks
+      {
+        // each item's mapping follows the contiguous index of its A operand;
+        // the grid covers the item that needs the most blocks
         p.kchunk = 0;
         auto hv = host_items.find(it);
         if (hv != host_items.end() && (int)hv->second.size() >= z0 + nz) {
@@ -1214,7 +1214,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     dim3 grid((unsigned)gx, (unsigned)nbc);
     const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
     if (outt && c->tri32) {
-      c->launch("triples_finish_contra_kernel", 0.0, [&] {
+      c->launch(rank1.empty() ? "triples_finish_contra_kernel" : "triples_finish_contra_kernel:rank1", 0.0, [&] {
         check_cuda(launch_finish_contra(W, db + b0, (int)nbc, tt, c->eps, ehl, (int)s.nv, omega,
                                         c->omega_dev,
                                         keep_out ? reinterpret_cast<float *>(out) : nullptr,
@@ -2566,10 +2566,31 @@ void d_LD_from_v(mlcc3_ctx *c, const double *V, const double *X, double *D, doub
            key);
 }
 
+// The accumulator `name` of a deferred D_LD contraction (D += alpha sum V X as
+// in d_LD_from_v): zeroed when first requested in a call; the chunks add their
+// shares to it and dld_flush contracts it once.  V is linear in the chunks'
+// orderings, so one contraction of the sum replaces one per chunk.
+double *dld_acc(mlcc3_ctx *c, const std::string &name, const double *X, double *D, double alpha,
+                const std::string &tag) {
+  S s(c);
+  for (auto &d : c->dld_pending)
+    if (d.name == name) return d.V;
+  double *V = c->buf("dVacc:" + name, s.gosz());
+  c->zero(V, s.gosz());
+  c->dld_pending.push_back({name, V, X, D, alpha, tag});
+  return V;
+}
+
+void dld_flush(mlcc3_ctx *c) {
+  for (auto &d : c->dld_pending) d_LD_from_v(c, d.V, d.X, d.D, d.alpha, d.tag);
+  c->dld_pending.clear();
+}
+
 // Triples part of the left density from (contravariant left triples Xt3,
 // covariant-combined doubles Lc, tau, contravariant tau), the chunk's share.
+// `acc`: the name of the D_LD accumulator of this density (dld_acc).
 void density_left_gpu(mlcc3_ctx *c, const Chunk &ch, const double *Xt3, const double *Lc,
-                      const double *tau, const double *taut, double *D) {
+                      const double *tau, const double *taut, double *D, const std::string &acc) {
   S s(c);
   const long long nmo = s.nmo, NO = s.NO;
   const std::string okey = "o" + ch.key;
@@ -2577,15 +2598,13 @@ void density_left_gpu(mlcc3_ctx *c, const Chunk &ch, const double *Xt3, const do
   pair_dots(c, ch, Xt3, tau, D, nmo, true, -0.5);
   // D_ld += 1/2 sum Lc^{ab}_{ij} taut^{abd}_{ijl}
   y3_like(c, taut, Lc, ch.own, okey, D + NO, nmo, 0.5, "y3d");
-  // D_LD -= sum Xt^{abc}_{ijk} t^{ac}_{iL} t^{bD}_{jk}
-  double *V = c->buf("dV", s.gosz());
-  c->zero(V, s.gosz());
+  // D_LD -= sum Xt^{abc}_{ijk} t^{ac}_{iL} t^{bD}_{jk}  (V summed over the chunks)
+  double *V = dld_acc(c, acc, c->t2c, D, -1.0, "dLD");
   if (split_mode(c))
     tc_xt(c, Xt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, ch.own, okey, 1, 0,
           s.oj, s.ok, s.oc, 1.0, V);
   else
     v_like(c, Xt3, c->Tl, ch.own, okey, V);
-  d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
   // D_cd += 1/2 sum Xt^{abc}_{ijk} tau^{abd}_{ijk}
   if (split_mode(c))
     tc_vv(c, Xt3, "X", tau, "Y", ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
@@ -2686,7 +2705,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3, lt3, ch.nb, false);
     // D^{0-0} (state independent)
-    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
+    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00, "D00");
     for (int st = 0; st < n_st; ++st) {
     const StateOps &so = sts[st];
     const double omega = omega_h[st];
@@ -2712,7 +2731,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     }
     right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3, R3t, ch.nb);
     // D^{m-0}
-    density_left_gpu(c, ch, L3t, so.Lc32, tau, taut, so.Dm0);
+    density_left_gpu(c, ch, L3t, so.Lc32, tau, taut, so.Dm0, "Dm0:" + std::to_string(st));
 
     // D^{0-m}
     int n = 0;
@@ -2740,9 +2759,11 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
           mirror_pairs_kernel<<<g, 256, 0, c->stream>>>(U, (int)s.no, (int)s.nv);
         });
       });
-    // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}
-    sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = s.no; sh.K2 = s.nv; sh.K3 = s.nv;
-    c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), "dKl");
+    // D_Kl -= sum_{j,b,c} U[j][l][b][c] t^{bc}_{jK}  (U vanishes outside the
+    // chunk's rows j in [p0, p1): the reduction runs over those only)
+    const long long nj = ch.p1 - ch.p0;
+    sh = Shape{}; sh.M1 = NO; sh.N1 = s.no; sh.K1 = nj; sh.K2 = s.nv; sh.K3 = s.nv;
+    c->bstc1(c->Tl, U, D, sh, -1.0, mk_item(ch.p0 * s.ti, ch.p0 * s.no * s.nv * s.nv, 0, {1, 0, s.ti, s.ta, s.tb}, {s.no * s.nv * s.nv, s.nv, 1, s.nv * s.nv, 0}, {nmo, 0, 1, 0}), okey + ":dKl");
     // D_kl -= 1/2 sum lt_{ijl} R3_{ijk}
     pair_dots(c, ch, lt3, R3, D, nmo, true, -0.5);
     const double *U32 = f32_operand(c, "dU", U, s.no * s.no * s.nv * s.nv, true);
@@ -2778,18 +2799,15 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     sh = Shape{}; sh.M1 = NO; sh.M2 = s.NV; sh.K1 = s.no; sh.K2 = s.nv;
     c->bstc1(c->t2c, W3, D + NO, sh, 2.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
     c->bstc1(c->t2x, W3, D + NO, sh, -1.0, mk_item(0, 0, 0, {s.bL, 1, s.bi, s.ba, 0}, {s.nv, 1, 0, 0, 0}, {nmo, 1, 0, 0}), "dLDw");
-    //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}
-    double *V = c->buf("dV", s.gosz());
-    c->zero(V, s.gosz());
+    //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}  (V, V3 summed over the chunks)
+    double *V = dld_acc(c, "D0m:" + std::to_string(st), c->t2c, D, -1.0, "dLD");
     if (split_mode(c))
       tc_xt(c, lt3, "X", c->splits.at("Rbl:T"), c->splits.at("Rbl:Ts"), s.NO, ch.own, okey, 1, 0,
             s.oj, s.ok, s.oc, 1.0, V);
     else
       v_like(c, lt3, Rbl, ch.own, okey, V);
-    d_LD_from_v(c, V, c->t2c, D, -1.0, "dLD");
     //   D_LD -= sum lt^{abc}_{ijk} Rbar^{aD}_{ik} t^{bc}_{jL}
-    double *V3 = c->buf("dV3", s.gosz());
-    c->zero(V3, s.gosz());
+    double *V3 = dld_acc(c, "D0m3:" + std::to_string(st), Rbar, D, -1.0, "dLD3");
     if (split_mode(c)) {
       tc_xt(c, lt3, "X", c->splits.at("Tl:T"), c->splits.at("Tl:Ts"), s.NO, ch.own, okey, 0, 1,
             s.oj, s.ok, s.oc, 1.0, V3);
@@ -2804,8 +2822,6 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
       sh = Shape{}; sh.M1 = s.nv; sh.K1 = s.nv; sh.K2 = s.nv; sh.N1 = NO;
       c->bstc(lt3, c->Tl, V3, sh, 1.0, it, n, true, okey + ":v3");
     }
-    sh = Shape{}; sh.M1 = NO; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
-    c->bstc1(V3, Rbar, D + NO, sh, -1.0, mk_item(0, 0, 0, {1, 0, s.oj, s.ok, s.oc}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dLD3");
     // D_lD -= 1/2 sum_k E[l][k] R^D_k,  E[l][k] = sum lt_{ijk} tau_{ijl}
     double *E = c->buf("dE", s.no * s.no + s.nv * s.nv);
     c->zero(E, s.no * s.no + s.nv * s.nv);
@@ -2823,9 +2839,9 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     // D_ck += W3[k][c]
     sh = Shape{}; sh.M1 = s.nv; sh.M2 = s.no;
     c->bstc1(W3, one, D + NO * nmo, sh, 1.0, mk_item(0, 0, 0, {1, s.nv, 0, 0, 0}, {0, 0, 0, 0, 0}, {nmo, 1, 0, 0}), "dck");
-    // D_cD += sum_{j,k,b} U[j][k][b][c] t^{bD}_{jk}
-    sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = s.no; sh.K2 = s.no; sh.K3 = s.nv;
-    c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(0, 0, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), "dcD");
+    // D_cD += sum_{j,k,b} U[j][k][b][c] t^{bD}_{jk}  (j in [p0, p1), as above)
+    sh = Shape{}; sh.M1 = s.nv; sh.N1 = s.NV; sh.K1 = nj; sh.K2 = s.no; sh.K3 = s.nv;
+    c->bstc1(U, c->t2c, D + NO * nmo + NO, sh, 1.0, mk_item(ch.p0 * s.no * s.nv * s.nv, ch.p0 * s.bi, 0, {1, 0, s.no * s.nv * s.nv, s.nv * s.nv, s.nv}, {s.bi, s.bL, s.ba, 1, 0}, {nmo, 0, 1, 0}), okey + ":dcD");
     // D_cd += 1/2 sum lt^{abc}_{ijk} R^{abd}_{ijk}
     if (split_mode(c))
       tc_vv(c, lt3, "X", R3, "Y", ch.own, okey, D + NO * nmo + NO, nmo, 0.5);
@@ -2852,6 +2868,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     }
     }  // states
   }
+  dld_flush(c);
   // lambda_SD.R_SD, then the normalisation term of D^{0-m}, per state
   for (int st = 0; st < n_st; ++st) {
     const StateOps &so = sts[st];
@@ -2890,8 +2907,9 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     double *lam3 = c->tri_buf("lam3", bw);
     double *lt3 = c->tri_buf("lam3t", bw);
     left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3, lt3, ch.nb, false);
-    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00);
+    density_left_gpu(c, ch, lt3, lc32, tau, taut, D00, "D00");
   }
+  dld_flush(c);
 }
 
 // ---------------------------------------------------------------------------
