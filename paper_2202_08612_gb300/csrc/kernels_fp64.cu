@@ -962,27 +962,39 @@ __global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // 2. finish in place, X stored
+  // 2. finish in place, X stored.  A thread's eight elements of a tile share
+  // (y, z): each table entry is read once per eight elements, the (y, z) parts
+  // of its operand indices and of the denominator once per column.
   const int ne = nr > 0 ? nent : 0;
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
     const int y = kFW * org[p][1] + l1, z = kFW * org[p][2] + l2;
     if (y >= nv || z >= nv) continue;
+    const int x0 = kFW * org[p][0] + l0b;
+    float acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      acc[r] = x0 + 2 * r < nv ? ftile[p * kFT + (l0b + 2 * r) * kFSI + l1 * kFSJ + l2] : 0.f;
+    for (int n = 0; n < ne; ++n) {
+      const FinishEnt &e = tab[n];
+      const float *pa = e.pa + (y * e.ca[1] + z * e.ca[2]);
+      const float *pb = e.pb + (y * e.cb[1] + z * e.cb[2]);
+      const int a0 = e.ca[0], b0 = e.cb[0];
+      const float cf = e.coef;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int x = x0 + 2 * r;
+        if (x < nv) acc[r] = fmaf(cf * pa[x * a0], pb[x * b0], acc[r]);
+      }
+    }
     const float2 ey = __ldg(ehl + y), ez = __ldg(ehl + z);
     float yh = ey.x, yl = ey.y;  // eps_y + eps_z + (-eps_ijk - omega), shared by the column
     df_add(yh, yl, ez.x, ez.y);
     df_add(yh, yl, eoh, eol);
-#pragma unroll 2
+#pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int l0 = l0b + 2 * r, x = kFW * org[p][0] + l0;
+      const int x = x0 + 2 * r;
       if (x >= nv) break;
-      float *cell = ftile + p * kFT + l0 * kFSI + l1 * kFSJ + l2;
-      float acc = *cell;
-      for (int n = 0; n < ne; ++n) {
-        const FinishEnt &e = tab[n];
-        acc = fmaf(e.coef * e.pa[x * e.ca[0] + y * e.ca[1] + z * e.ca[2]],
-                   e.pb[x * e.cb[0] + y * e.cb[1] + z * e.cb[2]], acc);
-      }
       const float2 ex = __ldg(ehl + x);
       float dh = ex.x, dl = ex.y;
       df_add(dh, dl, yh, yl);
@@ -991,8 +1003,8 @@ __global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
       if (fabsf(den) < 1e-3f)
         atomicOr(status, 1);
       else
-        q = -acc * __frcp_rn(den);
-      *cell = q;
+        q = -acc[r] * __frcp_rn(den);
+      ftile[p * kFT + (l0b + 2 * r) * kFSI + l1 * kFSJ + l2] = q;
       if (out) out[it.off + ((long long)x * nv + y) * nv + z] = q;
     }
   }
@@ -1076,8 +1088,9 @@ namespace mlcc3 {
 //  * an output index contiguous: the 32 lanes take 32 consecutive outputs
 //    along it and the 8 warps split K (sums of the warps added in shared
 //    memory);
-//  * otherwise: one warp per output, the lanes along K with the contiguous K
-//    index (if any) the fastest.
+//  * otherwise: lpo lanes per output (about K / 16, 4 to 32; a short
+//    reduction over a whole warp was mostly shuffles and atomics), the lanes
+//    of an output along K with the contiguous K index (if any) the fastest.
 // FP32 products (B binary32 when b32, else converted), 16 per lane summed in
 // FP32 and folded into FP64; one atomic update per output (and per K slice).
 // Grid: x = 4 ceil(M / 8) (the second mapping uses the first quarter; the
@@ -1144,8 +1157,9 @@ __device__ __forceinline__ double strided_dot(const TA *__restrict__ Am, LdB ldb
 //    consecutive outputs, its 8 warps split its slice of K (sums of the warps
 //    added in shared memory; p.kchunk slices per output group, or as many as
 //    the grid holds);
-//  * otherwise: one warp per output, the lanes along K with the contiguous K
-//    index (if any) the fastest.
+//  * otherwise: lpo lanes per output (about K / 16, 4 to 32; a short
+//    reduction over a whole warp was mostly shuffles and atomics), the lanes
+//    of an output along K with the contiguous K index (if any) the fastest.
 // TA = float: binary32 A (the split mode's triples arrays), FP32 products (B
 // binary32 when b32, else converted) folded into FP64 sums; TA = double: FP64
 // products and sums.  One (atomic) update per output and K slice.  Grid: x =
@@ -1217,14 +1231,16 @@ __device__ __forceinline__ void gemv_body(const BstcParams &p) {
       ka[2] = ta;
       kb[2] = tb;
     }
-  const long long m = (long long)blockIdx.x * 8 + warp;
-  if (m >= M) return;
-  const long long m1 = m / M2, m2 = m % M2;
+  // lpo lanes per output (aligned groups), 32 / lpo outputs per warp
+  const int lpo = g.lpo, sub = lane % lpo;
+  const long long m = ((long long)blockIdx.x * 8 + warp) * (32 / lpo) + lane / lpo;
+  if (((long long)blockIdx.x * 8 + warp) * (32 / lpo) >= M) return;  // the whole warp
+  const bool valid = m < M;
+  const long long m1 = valid ? m / M2 : 0, m2 = valid ? m % M2 : 0;
   const TA *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
-  double s = strided_dot<8>(Am, ldb, Kn, ka, kb, lane, K, 32);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) {
+  double s = valid ? strided_dot<8>(Am, ldb, Kn, ka, kb, sub, K, lpo) : 0.0;
+  for (int o = lpo / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (valid && sub == 0) {
     double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
     if (p.atomic) atomicAdd(C, p.alpha * s);
     else *C += p.alpha * s;

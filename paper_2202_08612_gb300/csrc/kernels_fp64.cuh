@@ -22,18 +22,31 @@ struct BstcItem {
 // index a short reduction (small_k) gives each warp 32 outputs and the whole
 // of K, a long one gives each block 32 outputs and a slice of K.  ncg = groups
 // of 32 outputs.
+// Without a contiguous output index each output takes lpo lanes (a power of
+// two, 4 to 32, about K / 16) and a warp 32 / lpo outputs.
 struct GemvMap {
   int mf;
   bool small_k;
   long long ncg;
+  int lpo;
 };
 constexpr long long kGemvSmallK = 1024;
 __host__ __device__ inline GemvMap gemv32_map(const BstcItem &it, long long M1, long long M2,
                                               long long K) {
-  GemvMap g{-1, K <= kGemvSmallK, (M1 * M2 + 31) / 32};
+  GemvMap g{-1, K <= kGemvSmallK, (M1 * M2 + 31) / 32, 32};
   if (M2 > 1 && it.sA[1] == 1) g.mf = 1;
   else if (it.sA[0] == 1 && (M1 > 1 || M2 == 1)) g.mf = 0;
+  while (g.lpo > 4 && 16 * g.lpo > K) g.lpo /= 2;
   return g;
+}
+// Blocks (of 8 warps) that an item's mapping needs; ns = K slices of the
+// output-contiguous form with a long reduction.
+__host__ __device__ inline long long gemv32_blocks(const GemvMap &g, long long M, long long ns) {
+  if (g.mf < 0) {
+    const long long per = 8LL * (32 / g.lpo);
+    return (M + per - 1) / per;
+  }
+  return g.small_k ? (g.ncg + 7) / 8 : g.ncg * ns;
 }
 
 struct BstcParams {

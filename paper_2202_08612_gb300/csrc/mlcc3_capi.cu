@@ -310,7 +310,7 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
           for (int q = z0; q < z0 + nz; ++q) {
             const GemvMap g = gemv32_map(hv->second[q], sh.M1, sh.M2, K);
             if (g.mf >= 0 && !g.small_k) ncg_min = ncg_min < 0 ? g.ncg : std::min(ncg_min, g.ncg);
-            gx = std::max(gx, g.mf < 0 ? (M + 7) / 8 : g.small_k ? (g.ncg + 7) / 8 : g.ncg);
+            gx = std::max(gx, gemv32_blocks(g, M, 1));
           }
           if (ncg_min > 0) {
             // K slices for the output-contiguous items with a long reduction:
@@ -319,10 +319,8 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
             const long long ns = std::max(1LL, std::min({want, (K + 511) / 512, 16LL}));
             p.kchunk = ns;
             long long gmax = 1;
-            for (int q = z0; q < z0 + nz; ++q) {
-              const GemvMap g = gemv32_map(hv->second[q], sh.M1, sh.M2, K);
-              gmax = std::max(gmax, g.mf < 0 ? (M + 7) / 8 : g.small_k ? (g.ncg + 7) / 8 : g.ncg * ns);
-            }
+            for (int q = z0; q < z0 + nz; ++q)
+              gmax = std::max(gmax, gemv32_blocks(gemv32_map(hv->second[q], sh.M1, sh.M2, K), M, ns));
             gx = gmax;
           }
           grid.x = (unsigned)gx;
