@@ -88,33 +88,71 @@ __device__ __forceinline__ void bstc_body(const BstcParams &p) {
 
   const long long kbeg = p.kchunk ? (long long)blockIdx.z * p.kchunk : 0;
   const long long kend = p.kchunk ? min(K, kbeg + p.kchunk) : K;
+  // threads tid < BK keep the split (k1, k2, k3) of k = k0 + tid, divided once
+  // and then advanced by BK with carries (a 64-bit division per K tile held
+  // the whole block at the barrier)
+  int q1 = 0, q2 = 0, q3 = 0;
+  const int K2i = p.K2, K3i = p.K3;
+  const int d3 = BK % K3i, d12 = BK / K3i, d2 = d12 % K2i, d1 = d12 / K2i;
+  if (tid < BK) {
+    const long long k = kbeg + tid;
+    q3 = (int)(k % K3i);
+    const long long k12 = k / K3i;
+    q2 = (int)(k12 % K2i);
+    q1 = (int)(k12 / K2i);
+  }
   for (long long k0 = kbeg; k0 < kend; k0 += BK) {
     if (tid < BK) {
-      long long k = k0 + tid;
-      if (k < kend) {
-        long long k3 = k % p.K3, k12 = k / p.K3;
-        long long k2 = k12 % p.K2, k1 = k12 / p.K2;
-        kA[tid] = k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4];
-        kB[tid] = k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2];
+      if (k0 + tid < kend) {
+        kA[tid] = q1 * it.sA[2] + q2 * it.sA[3] + q3 * it.sA[4];
+        kB[tid] = q1 * it.sB[0] + q2 * it.sB[1] + q3 * it.sB[2];
       } else {
         kA[tid] = -1;
         kB[tid] = -1;
       }
+      q3 += d3;
+      int c = 0;
+      if (q3 >= K3i) {
+        q3 -= K3i;
+        c = 1;
+      }
+      q2 += d2 + c;
+      c = 0;
+      if (q2 >= K2i) {
+        q2 -= K2i;
+        c = 1;
+      }
+      q1 += d1 + c;
     }
     __syncthreads();
-    for (int e = tid; e < BK * BM; e += 256) {
+    // the eight loads of a thread are issued before any of them is stored to
+    // shared memory (a load-then-store loop kept one load in flight)
+    T va[BK * BM / 256], vb[BK * BN / 256];
+#pragma unroll
+    for (int q = 0; q < BK * BM / 256; ++q) {
+      const int e = tid + 256 * q;
       int kk, mm;
       if (kfastA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
-      T v = T(0);
-      if (rowA[mm] >= 0 && kA[kk] >= 0) v = ld_op<T>(p.A, p.a32, offA + rowA[mm] + kA[kk]);
-      As[kk][mm] = v;
+      va[q] = (rowA[mm] >= 0 && kA[kk] >= 0) ? ld_op<T>(p.A, p.a32, offA + rowA[mm] + kA[kk]) : T(0);
     }
-    for (int e = tid; e < BK * BN; e += 256) {
+#pragma unroll
+    for (int q = 0; q < BK * BN / 256; ++q) {
+      const int e = tid + 256 * q;
       int kk, nn;
       if (kfastB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
-      T v = T(0);
-      if (colB[nn] >= 0 && kB[kk] >= 0) v = ld_op<T>(p.B, p.b32, offB + kB[kk] + colB[nn]);
-      Bs[kk][nn] = v;
+      vb[q] = (colB[nn] >= 0 && kB[kk] >= 0) ? ld_op<T>(p.B, p.b32, offB + kB[kk] + colB[nn]) : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < BK * BM / 256; ++q) {
+      const int e = tid + 256 * q;
+      if (kfastA) As[e % BK][e / BK] = va[q];
+      else As[e / BM][e % BM] = va[q];
+    }
+#pragma unroll
+    for (int q = 0; q < BK * BN / 256; ++q) {
+      const int e = tid + 256 * q;
+      if (kfastB) Bs[e % BK][e / BK] = vb[q];
+      else Bs[e / BN][e % BN] = vb[q];
     }
     __syncthreads();
 #pragma unroll
@@ -1284,6 +1322,10 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
                                                const char *__restrict__ vhave, int no, int nv, int p0,
                                                double *__restrict__ out, long long ldo, int kl,
                                                double alpha) {
+  static_assert((TA & (TA - 1)) == 0 && (TB & (TB - 1)) == 0, "tile extents are powers of two");
+  constexpr int LTA = TA == 1 ? 0 : TA == 2 ? 1 : TA == 4 ? 2 : TA == 8 ? 3 : 4;
+  constexpr int LTB = TB == 1 ? 0 : TB == 2 ? 1 : TB == 4 ? 2 : TB == 8 ? 3 : 4;
+  static_assert((1 << LTA) == TA && (1 << LTB) == TB, "tile extents up to 16");
   constexpr int PB = TB + 1, PA = TB * PB + 1;  // padded logical strides of b and a
   constexpr int TE = TA * PA;                   // positions of one view's tile
   constexpr int TS = (TE + 31) / 32 * 32 + 1;   // row stride of a view, 1 mod 32
@@ -1341,13 +1383,15 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
     __syncthreads();  // the previous tile's reads are done
     for (int r = 0; r < no; ++r) {
       const int f = s_ax[r][0], m = s_ax[r][1];
-      const int df = f == 0 ? TA : TB, dm = m == 0 ? TA : TB;
+      // TA and TB are powers of two: the split of e by shifts and masks
+      const int lf = f == 0 ? LTA : LTB, lm = m == 0 ? LTA : LTB;
+      const int mf = (1 << lf) - 1, mm = (1 << lm) - 1;
       const bool hv = s_have[r] != 0;
       const long long base = s_off[r];
       const int sa = s_st[r][0], sb = s_st[r][1], sc = s_st[r][2];
 #pragma unroll
       for (int e = t; e < NE; e += 256) {
-        const int ef = e % df, em = (e / df) % dm, es = e / (df * dm);
+        const int ef = e & mf, em = (e >> lf) & mm, es = e >> (lf + lm);
         const int la = f == 0 ? ef : m == 0 ? em : es;
         const int lb = f == 1 ? ef : m == 1 ? em : es;
         const int lc = f == 2 ? ef : m == 2 ? em : es;
