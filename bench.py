@@ -291,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
     split = args.precision == "split"
     prec = binding.MLCC3_SPLIT_BF16X3 if split else binding.MLCC3_FP64
     ctx = binding.Context(*prob.dims, precision=prec, stream=stream.cuda_stream)
+    apply_params(ctx, args)
     if args.tc_group:
         ctx.set_param("tc_group", args.tc_group)
     if args.tc_wide_bn:
@@ -619,6 +620,7 @@ def run_large(args):
                           core_mask=core_mask)
     # unique batches held per chunk: leaves room for the integral blocks, their
     # split copies and the per-call scratch next to the caller's tensors
+    apply_params(ctx, args)
     if args.stage not in ("densities", "ground"):
         ctx.set_param("chunk_blocks", args.chunk_blocks)
     if args.tc_group:
@@ -877,6 +879,13 @@ def run_large_densities(args, ctx, x, omega, D, unit, ms_build, NO, NV, no, nv, 
 WHOLE = {"betaine_like": (100, 1000, 20, 150, 4000, 2, 1)}
 
 
+def apply_params(ctx, args):
+    """The --param KEY=VALUE settings, applied to a timed context."""
+    for kv in args.param:
+        k, _, v = kv.partition("=")
+        ctx.set_param(k.strip(), int(v))
+
+
 def whole_step_flops(NO, NV, no, nv, nval, ncore):
     """Algorithmic flops of one whole step (the paper's leading counts, Sec. 3):
     Omega once; rho + sigma + D^{m-0} + D^{0-m} per valence state and D^{0-0}
@@ -1091,6 +1100,7 @@ def run_whole(args, rank, world, local_rank):
     ctx = binding.Context(NO, NV, no, nv, NJ, precision=binding.MLCC3_SPLIT_BF16X3,
                           stream=stream.cuda_stream, core_mask=mask)
     ctx.set_param("chunk_blocks", args.chunk_blocks)
+    apply_params(ctx, args)
     # the densities' scratch and the Jacobians' do not fit side by side next to
     # the resident inputs: every call frees its own
     ctx.set_param("release_scratch", 1)
@@ -1207,6 +1217,7 @@ def run_whole(args, rank, world, local_rank):
                            "precision": "split bf16x3 / fp32 accumulate / fp64 denominators and reductions",
                            "parallelism": f"replicas x{world} (independent systems)",
                            "chunk_blocks": args.chunk_blocks,
+                           **({"params": list(args.param)} if args.param else {}),
                            "l2": "inputs larger than L2 (Cholesky vectors "
                                  f"{NJ * (NO + NV) ** 2 * 8 / 2**30:.1f} GiB)"},
                 "s_per_davidson_iter": s_iter, "fp64_gpu_path": fp64,
@@ -1321,6 +1332,8 @@ def main():
                          "vectors, the densities and f of one state, the Davidson iteration "
                          "of one core (CVS) state, or the ground-state stages (multiplier "
                          "transformation and D^{0-0})")
+    ap.add_argument("--param", action="append", default=[], metavar="KEY=VALUE",
+                    help="a context parameter (mlcc3_set_param) for the timed contexts; repeatable")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the untimed FP64-path comparison step")
     args = ap.parse_args()

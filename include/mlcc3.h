@@ -249,6 +249,11 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              call (the transition densities need more than the Jacobian
  *              transformations); each call then allocates its scratch again.
  *              A sweep needs contexts with 0 (MLCC3_ERR_STATE otherwise).
+ *   "finish_fused"  1 (default): in the split-precision mode the finish of a
+ *              triples build (rank-1 terms, denominators) and the contravariant
+ *              transform of its blocks run as one pass over tile orbits; 0: as
+ *              a streaming finish followed by the transform.  Same results up
+ *              to rounding order.
  *   "cvs"      1 (default): a context created with a core mask applies the CVS
  *              skip rule (mlcc3_dims.core_mask) in the Jacobian transformations
  *              and the densities; 0: the same context treats its vectors as

@@ -125,6 +125,8 @@ struct mlcc3_ctx {
   // "release_scratch": every call ends by freeing the scratch that the integral
   // build did not create (keep_scratch / keep_splits are the build's names)
   bool release_scratch = false;
+  // split mode: finish and contravariant transform of a triples build fused
+  bool finish_fused = true;
   std::set<std::string> keep_scratch, keep_splits;
   void release();
   // Triples arrays (tau, R3, L3, lambda3 and their contravariant forms) are

@@ -88,71 +88,33 @@ __device__ __forceinline__ void bstc_body(const BstcParams &p) {
 
   const long long kbeg = p.kchunk ? (long long)blockIdx.z * p.kchunk : 0;
   const long long kend = p.kchunk ? min(K, kbeg + p.kchunk) : K;
-  // threads tid < BK keep the split (k1, k2, k3) of k = k0 + tid, divided once
-  // and then advanced by BK with carries (a 64-bit division per K tile held
-  // the whole block at the barrier)
-  int q1 = 0, q2 = 0, q3 = 0;
-  const int K2i = p.K2, K3i = p.K3;
-  const int d3 = BK % K3i, d12 = BK / K3i, d2 = d12 % K2i, d1 = d12 / K2i;
-  if (tid < BK) {
-    const long long k = kbeg + tid;
-    q3 = (int)(k % K3i);
-    const long long k12 = k / K3i;
-    q2 = (int)(k12 % K2i);
-    q1 = (int)(k12 / K2i);
-  }
   for (long long k0 = kbeg; k0 < kend; k0 += BK) {
     if (tid < BK) {
-      if (k0 + tid < kend) {
-        kA[tid] = q1 * it.sA[2] + q2 * it.sA[3] + q3 * it.sA[4];
-        kB[tid] = q1 * it.sB[0] + q2 * it.sB[1] + q3 * it.sB[2];
+      long long k = k0 + tid;
+      if (k < kend) {
+        long long k3 = k % p.K3, k12 = k / p.K3;
+        long long k2 = k12 % p.K2, k1 = k12 / p.K2;
+        kA[tid] = k1 * it.sA[2] + k2 * it.sA[3] + k3 * it.sA[4];
+        kB[tid] = k1 * it.sB[0] + k2 * it.sB[1] + k3 * it.sB[2];
       } else {
         kA[tid] = -1;
         kB[tid] = -1;
       }
-      q3 += d3;
-      int c = 0;
-      if (q3 >= K3i) {
-        q3 -= K3i;
-        c = 1;
-      }
-      q2 += d2 + c;
-      c = 0;
-      if (q2 >= K2i) {
-        q2 -= K2i;
-        c = 1;
-      }
-      q1 += d1 + c;
     }
     __syncthreads();
-    // the eight loads of a thread are issued before any of them is stored to
-    // shared memory (a load-then-store loop kept one load in flight)
-    T va[BK * BM / 256], vb[BK * BN / 256];
-#pragma unroll
-    for (int q = 0; q < BK * BM / 256; ++q) {
-      const int e = tid + 256 * q;
+    for (int e = tid; e < BK * BM; e += 256) {
       int kk, mm;
       if (kfastA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
-      va[q] = (rowA[mm] >= 0 && kA[kk] >= 0) ? ld_op<T>(p.A, p.a32, offA + rowA[mm] + kA[kk]) : T(0);
+      T v = T(0);
+      if (rowA[mm] >= 0 && kA[kk] >= 0) v = ld_op<T>(p.A, p.a32, offA + rowA[mm] + kA[kk]);
+      As[kk][mm] = v;
     }
-#pragma unroll
-    for (int q = 0; q < BK * BN / 256; ++q) {
-      const int e = tid + 256 * q;
+    for (int e = tid; e < BK * BN; e += 256) {
       int kk, nn;
       if (kfastB) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
-      vb[q] = (colB[nn] >= 0 && kB[kk] >= 0) ? ld_op<T>(p.B, p.b32, offB + kB[kk] + colB[nn]) : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < BK * BM / 256; ++q) {
-      const int e = tid + 256 * q;
-      if (kfastA) As[e % BK][e / BK] = va[q];
-      else As[e / BM][e % BM] = va[q];
-    }
-#pragma unroll
-    for (int q = 0; q < BK * BN / 256; ++q) {
-      const int e = tid + 256 * q;
-      if (kfastB) Bs[e % BK][e / BK] = vb[q];
-      else Bs[e / BN][e % BN] = vb[q];
+      T v = T(0);
+      if (colB[nn] >= 0 && kB[kk] >= 0) v = ld_op<T>(p.B, p.b32, offB + kB[kk] + colB[nn]);
+      Bs[kk][nn] = v;
     }
     __syncthreads();
 #pragma unroll

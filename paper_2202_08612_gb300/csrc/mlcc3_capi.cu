@@ -724,6 +724,8 @@ void split_tl_T(mlcc3_ctx *c, const std::string &key, const double *T);
 void tc_integrals(mlcc3_ctx *c);
 void split_chol_kpairs(mlcc3_ctx *c);
 float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long n);
+const float *f32_cached(mlcc3_ctx *c, const std::string &key, const double *x, long long n,
+                        bool convert);
 const double *f32_operand(mlcc3_ctx *c, const std::string &key, const double *x, long long n,
                           bool convert);
 mlcc3_ctx::SplitOp &layout_XL(mlcc3_ctx *c, const std::string &key, const double *X, int k,
@@ -1211,7 +1213,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     const long long gx = std::max<long long>(1, std::min<long long>((s.nv3 + 255) / 256, (16 * 152 + nbc - 1) / nbc));
     dim3 grid((unsigned)gx, (unsigned)nbc);
     const float2 *ehl = static_cast<const float2 *>(c->raw("ehl", sizeof(float2) * (size_t)s.nv));
-    if (outt && c->tri32) {
+    if (outt && c->tri32 && c->finish_fused) {
       c->launch(rank1.empty() ? "triples_finish_contra_kernel" : "triples_finish_contra_kernel:rank1", 0.0, [&] {
         check_cuda(launch_finish_contra(W, db + b0, (int)nbc, tt, c->eps, ehl, (int)s.nv, omega,
                                         c->omega_dev,
@@ -1229,7 +1231,7 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
     });
   }
   check_cuda(cudaGetLastError(), "triples_finish");
-  if (outt && !c->tri32) contra3(c, out, outt, nbt);
+  if (outt && !(c->tri32 && c->finish_fused)) contra3(c, out, outt, nbt);
 }
 
 bool split_mode(const mlcc3_ctx *c) { return c->precision == MLCC3_SPLIT_BF16X3; }
@@ -1796,9 +1798,13 @@ std::vector<SplitTerm> tau_split_terms(mlcc3_ctx *c) {
 
 // L3 / lambda3 (SI): D (Lc, Gb), L (LcT, Gx), plus the rank-1 terms in FP64.
 // outt, nbt, keep_out: the contravariant blocks as in triples_split.
+// convert = false: the split and FP32 copies of L1, Lc, LcT made under the same
+// tag by an earlier call (the first chunk of a loop over chunks, with the same
+// operands) are reused.
 void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const double *Lc,
                   const double *LcT, const std::string &bkey, const std::vector<TripItem> &bs,
-                  double omega, double *out, double *outt, long long nbt, bool keep_out = true) {
+                  double omega, double *out, double *outt, long long nbt, bool keep_out = true,
+                  bool convert = true) {
   S s(c);
   std::vector<TripTerm> full = {
       term(0, (int)s.NV, 1.0, Lc, {s.bi, s.bL, s.ba, 1}, c->Gb, {s.gk, s.gb, s.gc, 1}),
@@ -1813,24 +1819,25 @@ void left_triples(mlcc3_ctx *c, const std::string &tag, const double *L1, const 
   // the rank-1 terms' operands are pair-symmetric (g_jbkc, Lc), and L1 is also
   // given transposed, so that the finish reads them along the fastest index
   double *L1T = c->buf("L1T:" + tag, s.NV * s.NO);
-  launch_1d(c, s.NV * s.NO, "transpose2d", [&](int g) {
-    c->launch("transpose2d_kernel", 0.0, [&] {
-      transpose2d_kernel<<<g, 256, 0, c->stream>>>(L1, L1T, (int)s.NV, (int)s.NO);
+  if (convert)
+    launch_1d(c, s.NV * s.NO, "transpose2d", [&](int g) {
+      c->launch("transpose2d_kernel", 0.0, [&] {
+        transpose2d_kernel<<<g, 256, 0, c->stream>>>(L1, L1T, (int)s.NV, (int)s.NO);
+      });
     });
-  });
   full[2].sym = 1;
   full[2].At = L1T;
   full[2].sAt[0] = 1;
   full[2].sAt[1] = s.NV;
   full[3].sym = 1;
   // FP32 copies for the finish (g_jbkc and F are converted once per integral build)
-  full[2].A32 = f32_copy(c, "L1:" + tag, L1, s.NV * s.NO);
-  full[2].At32 = f32_copy(c, "L1T:" + tag, L1T, s.NV * s.NO);
+  full[2].A32 = f32_cached(c, "L1:" + tag, L1, s.NV * s.NO, convert);
+  full[2].At32 = f32_cached(c, "L1T:" + tag, L1T, s.NV * s.NO, convert);
   full[2].B32 = static_cast<const float *>(c->raw("f32:Govov", 4));
-  full[3].A32 = f32_copy(c, "Lc:" + tag, Lc, (long long)s.blk());
+  full[3].A32 = f32_cached(c, "Lc:" + tag, Lc, (long long)s.blk(), convert);
   full[3].B32 = static_cast<const float *>(c->raw("f32:F", 4));
-  SplitTerm d = split_d(c, tag + "c", Lc, true, "Gb", c->Gb, false);
-  SplitTerm l = split_l(c, tag + "cT", LcT, true, "Gx", c->Gx, false);
+  SplitTerm d = split_d(c, tag + "c", Lc, convert, "Gb", c->Gb, false);
+  SplitTerm l = split_l(c, tag + "cT", LcT, convert, "Gx", c->Gx, false);
   triples_split(c, {d, l}, {full[2], full[3]}, bkey, bs, omega, out, outt, nbt, keep_out);
 }
 
@@ -1841,6 +1848,13 @@ float *f32_copy(mlcc3_ctx *c, const std::string &key, const double *x, long long
     c->launch("to_f32_kernel", 0.0, [&] { to_f32_kernel<<<g, 256, 0, c->stream>>>(x, y, n); });
   });
   return y;
+}
+
+// f32_copy, or (convert = false) the copy made under the same key before.
+const float *f32_cached(mlcc3_ctx *c, const std::string &key, const double *x, long long n,
+                        bool convert) {
+  if (convert) return f32_copy(c, key, x, n);
+  return static_cast<const float *>(c->raw("f32:" + key, sizeof(float) * (size_t)std::max(1LL, n)));
 }
 
 // The FP32 copy of an operand that meets binary32 triples arrays in the
@@ -1949,10 +1963,14 @@ Ups build_upsilon(mlcc3_ctx *c, const double *R1, const std::string &tag = "", b
 }
 
 // R3 (Eq. R3): D (Rbar, Gv), L (Rbar_l, Go), D (t, Upsilon_v), L (Tl, Upsilon_o).
-// outt, nbt: the contravariant blocks as in triples_split.
+// outt, nbt: the contravariant blocks as in triples_split.  convert = false:
+// the split copies of Rbar and Rbl made under the same tag before are reused;
+// convert_u = false: those of Upsilon likewise (the first chunk of a loop over
+// chunks converts them, the others reuse them).
 void right_triples(mlcc3_ctx *c, const double *Rbar, const double *Rbl, const Ups &u,
                    const std::string &bkey, const std::vector<TripItem> &bs, double omega,
-                   double *out, double *outt, long long nbt) {
+                   double *out, double *outt, long long nbt, const std::string &tag = "",
+                   bool convert = true, bool convert_u = true) {
   S s(c);
   if (!split_mode(c)) {
     std::vector<TripTerm> terms = {
@@ -1964,10 +1982,10 @@ void right_triples(mlcc3_ctx *c, const double *Rbar, const double *Rbl, const Up
     contra3(c, out, outt, nbt);
     return;
   }
-  SplitTerm d1 = split_d(c, "Rbar", Rbar, true, "Gv", c->Gv, false);
-  SplitTerm l1 = split_l(c, "Rbarl", Rbl, true, "Go", c->Go, false);
-  SplitTerm d2 = split_d(c, "t", c->t2c, false, "Uv", u.Uv, true);
-  SplitTerm l2 = split_l(c, "Tl", c->Tl, false, "Uo", u.Uo, true);
+  SplitTerm d1 = split_d(c, "Rbar" + tag, Rbar, convert, "Gv", c->Gv, false);
+  SplitTerm l1 = split_l(c, "Rbarl" + tag, Rbl, convert, "Go", c->Go, false);
+  SplitTerm d2 = split_d(c, "t", c->t2c, false, "Uv", u.Uv, convert_u);
+  SplitTerm l2 = split_l(c, "Tl", c->Tl, false, "Uo", u.Uo, convert_u);
   triples_split(c, {d1, l1, d2, l2}, {}, bkey, bs, omega, out, outt, nbt);
 }
 
@@ -2111,7 +2129,7 @@ static void do_jacobian_right(mlcc3_ctx *c, int n_vec, const double *omega, cons
       double *R3t = c->tri_buf("R3t", (size_t)ch.nb * s.nv3);
       // R3 (Eq. R3): Rbar g - Rbar g + t Upsilon - t Upsilon, denominator (eps - omega)
       c->omega_dev = omega_dev ? omega_dev + v : nullptr;
-      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3, R3t, ch.nb);
+      right_triples(c, Rbar, Rbl, u, "b" + ch.key, ch.bs, wv, R3, R3t, ch.nb, "", q == 0, q == 0);
       c->omega_dev = nullptr;
       BackSet b;
       b.cs = 0.5; b.Gs = c->Govov;
@@ -2181,7 +2199,8 @@ static void do_jacobian_left(mlcc3_ctx *c, int n_vec, const double *omega, const
       const std::vector<Ord> &os = ch.own;
       const std::string okey = "o" + ch.key;
       // L3 (SI): 1/2 L^a_i g_jbkc + 1/2 Lc^{ab}_{ij} F_kc - sum_L Lc^{ab}_{iL} g_jLkc + sum_D Lc^{aD}_{ij} g_Dbkc
-      left_triples(c, "L", L1, Lc, LcT, "b" + ch.key, ch.bs, omega[v], L3, L3t, ch.nb);
+      left_triples(c, "L", L1, Lc, LcT, "b" + ch.key, ch.bs, omega[v], L3, L3t, ch.nb, true,
+                   &ch == &chunks.front());
       // doubles: sigma^{aD}_{ij} += P sum Lt3 g_bDck, sigma^{ab}_{iL} -= P sum Lt3 g_Ljck
       BackSet b;
       b.cL = -1.0; b.GL = c->Go; b.gl_key = "Go";
@@ -2701,7 +2720,8 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     // the contravariant form exists, so L3 reuses its buffer
     double *lam3 = c->tri_buf("L3", bw);
     double *lt3 = c->tri_buf("lam3t", bw);
-    left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3, lt3, ch.nb, false);
+    const bool first = &ch == &c->groups.front();
+    left_triples(c, "lam", lam1, lc, lcT, bkey, ch.bs, 0.0, lam3, lt3, ch.nb, false, first);
     // D^{0-0} (state independent)
     density_left_gpu(c, ch, lt3, lc32, tau, taut, D00, "D00");
     for (int st = 0; st < n_st; ++st) {
@@ -2711,7 +2731,9 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     const double *Rbar = so.Rbar, *Rbl = so.Rbl;
     const Ups &u = so.u;
     double *D = so.D0m, *sc = scall + 2 * st;
-    if (split_mode(c)) split_tl_T(c, "Rbl", Rbl);
+    const std::string stag = std::to_string(st);
+    // split copies of the state's operands: made at the first chunk, kept per state
+    if (split_mode(c) && first) split_tl_T(c, "Rbl" + stag, Rbl);
     // L3 (omega) and R3 (omega), with their contravariant forms (CVS: core batches only)
     double *L3 = c->tri_buf("L3", bw);
     double *L3t = c->tri_buf("L3t", bw);
@@ -2720,14 +2742,16 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
       c->zero_tri(L3t, bw);
     }
     const std::string bkey3 = cvs ? bkey + "cvs" : bkey;  // the batch list is cached per key
-    left_triples(c, "L", L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3, L3t, ch.nb);
+    left_triples(c, "L" + stag, L1, Lc, LcT, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, L3, L3t, ch.nb,
+                 true, first);
     double *R3 = c->tri_buf("R3", bw);
     double *R3t = c->tri_buf("R3t", bw);
     if (cvs) {
       c->zero_tri(R3, bw);
       c->zero_tri(R3t, bw);
     }
-    right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3, R3t, ch.nb);
+    right_triples(c, Rbar, Rbl, u, bkey3, cvs ? ch.bs_cvs : ch.bs, omega, R3, R3t, ch.nb, stag,
+                  first, true);
     // D^{m-0}
     density_left_gpu(c, ch, L3t, so.Lc32, tau, taut, so.Dm0, "Dm0:" + std::to_string(st));
 
@@ -2800,7 +2824,7 @@ static void do_transition_density(mlcc3_ctx *c, int n_st, const double *omega_h,
     //   D_LD -= sum lt^{abc}_{ijk} Rbar^{ac}_{iL} t^{bD}_{jk}  (V, V3 summed over the chunks)
     double *V = dld_acc(c, "D0m:" + std::to_string(st), c->t2c, D, -1.0, "dLD");
     if (split_mode(c))
-      tc_xt(c, lt3, "X", c->splits.at("Rbl:T"), c->splits.at("Rbl:Ts"), s.NO, ch.own, okey, 1, 0,
+      tc_xt(c, lt3, "X", c->splits.at("Rbl" + stag + ":T"), c->splits.at("Rbl" + stag + ":Ts"), s.NO, ch.own, okey, 1, 0,
             s.oj, s.ok, s.oc, 1.0, V);
     else
       v_like(c, lt3, Rbl, ch.own, okey, V);
@@ -2904,7 +2928,8 @@ static void do_ground_density(mlcc3_ctx *c, const double *lam1_in, const double 
     build_tau(c, ch, &tau, &taut);
     double *lam3 = c->tri_buf("lam3", bw);
     double *lt3 = c->tri_buf("lam3t", bw);
-    left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3, lt3, ch.nb, false);
+    left_triples(c, "lam", lam1, lc, lcT, "b" + ch.key, ch.bs, 0.0, lam3, lt3, ch.nb, false,
+                 &ch == &c->groups.front());
     density_left_gpu(c, ch, lt3, lc32, tau, taut, D00, "D00");
   }
   dld_flush(c);
@@ -3200,6 +3225,9 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
         check_cuda(cudaStreamSynchronize(c->stream), "sync");
         c->release();
       }
+    } else if (n == "finish_fused") {
+      if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "finish_fused must be 0 or 1"};
+      c->finish_fused = value == 1;
     } else if (n == "cvs") {
       if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "cvs must be 0 or 1"};
       if (value == 1 && c->core.empty())

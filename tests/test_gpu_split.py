@@ -129,6 +129,45 @@ def test_split_persistent_kernel_everywhere():
         assert rel_err(got[k], ref[k]) < TOL, (k, rel_err(got[k], ref[k]))
 
 
+@pytest.mark.parametrize("chunk_blocks", [0, 7])
+def test_split_unfused_finish(chunk_blocks):
+    """finish_fused = 0: the streaming finish followed by the separate
+    contravariant transform, on one chunk and on several (the split copies of
+    the per-vector operands are then made at the first chunk and reused); the
+    whole split path meets its bar and agrees with the fused pass."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=2)
+    ref = oracle_all(c)
+    got = {}
+    for fused in (0, 1):
+        g = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+        g.set_param("chunk_blocks", chunk_blocks)
+        g.set_param("finish_fused", fused)
+        got[fused] = run_all(c, g)
+        for k in ref:
+            assert rel_err(got[fused][k], ref[k]) < TOL, (fused, k, rel_err(got[fused][k], ref[k]))
+    for k in ref:
+        assert rel_err(got[0][k], got[1][k]) < 1e-5, (k, rel_err(got[0][k], got[1][k]))
+    # every vector of one call (each converts its own operands at the first chunk)
+    o, st = c.oracle_ctx(), c.st
+    rho1, rho2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    sig1, sig2 = c.empty_dev(st.R1.shape), c.empty_dev(st.R2.shape)
+    g.jacobian_right(st.omega, c.to_dev(st.R1), c.to_dev(st.R2), rho1, rho2)
+    g.jacobian_left(st.omega, c.to_dev(st.L1), c.to_dev(st.L2), sig1, sig2)
+    rho1, rho2, sig1, sig2 = map(c.host, (rho1, rho2, sig1, sig2))
+    for v in range(len(st.omega)):
+        w = float(st.omega[v])
+        r1, r2 = O.jacobian_right(o, w, st.R1[v], O.to_full(o, st.R2[v]))
+        s1, s2 = O.jacobian_left(o, w, st.L1[v], O.to_full(o, st.L2[v]))
+        assert rel_err(rho1[v], r1) < TOL and rel_err(rho2[v], O.from_full(o, r2)) < TOL, v
+        assert rel_err(sig1[v], s1) < TOL and rel_err(sig2[v], O.from_full(o, s2)) < TOL, v
+    with pytest.raises(binding.MLCC3Error):
+        g.set_param("finish_fused", 2)
+
+
 @pytest.mark.parametrize("group,persist", [(1, 304), (2, 304), (4, 304), (3, 0)])
 def test_split_grouped_tiles(group, persist):
     """Batches stacked along N in the triples build and orderings stacked in the
