@@ -375,8 +375,8 @@ __global__ void __launch_bounds__(256) triples_build_kernel(const TripTerms term
 // Contravariant triples by orbits of 8-wide tiles.  Block (o, u) takes the
 // tile orbit o, tile origins (A, B, C) with A <= B <= C, of block u: it loads
 // the distinct permuted tiles (A,B,C), (B,A,C), ... into shared memory once,
-// and each thread takes one orbit of elements {abc, bac, ...} through its
-// representative in tile (A,B,C) (a <= b where A = B, b <= c where B = C, so
+// and each thread takes the orbits of elements {abc, bac, ...} of its
+// representatives in tile (A,B,C) (a <= b where A = B, b <= c where B = C, so
 // that every element orbit has exactly one owner).  With E and O the sums of
 // the even (abc, cab, bca) and odd (bac, cba, acb) permutations,
 //   Xt^{abc} = 4X^{abc} - 2X^{bac} - 2X^{cba} - 2X^{acb} + X^{cab} + X^{bca}
@@ -389,64 +389,41 @@ constexpr int kC3SJ = 9, kC3SI = 8 * kC3SJ + 1, kC3T = 8 * kC3SI;  // padded til
 __constant__ int kC3P[6][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}};
 }  // namespace
 
-// Thread 0 of a block: orbit index o -> tile origins (A, B, C), A <= B <= C < nt,
+// Thread 0 of a block: orbit index o -> tile origins (A, B, C), A <= B <= C,
 // the origins org[p] of the six permuted tiles and, for each, the slot of the
-// first permutation with the same origin (its shared-memory tile).
+// first permutation with the same origin (its shared-memory tile).  The orbits
+// are numbered C-major, o = C(C+1)(C+2)/6 + B(B+1)/2 + A, so that the first
+// nt(nt+1)(nt+2)/6 of them are those with C < nt whatever nt is, and o splits
+// in closed form (a cube and a square root, each corrected by at most a step).
 __device__ __forceinline__ void c3_orbit(int o, int nt, int org[6][3], int slot[6]) {
-  int A = 0;
-  for (;; ++A) {
-    const int m = nt - A, cnt = m * (m + 1) / 2;
-    if (o < cnt) break;
-    o -= cnt;
-  }
-  int Bt = A;
-  for (;; ++Bt) {
-    const int cnt = nt - Bt;
-    if (o < cnt) break;
-    o -= cnt;
-  }
-  const int T[3] = {A, Bt, Bt + o};
+  (void)nt;
+  int C = (int)cbrtf(6.f * (float)o);
+  while (C > 0 && C * (C + 1) * (C + 2) / 6 > o) --C;
+  while ((C + 1) * (C + 2) * (C + 3) / 6 <= o) ++C;
+  const int r = o - C * (C + 1) * (C + 2) / 6;
+  int Bt = (int)sqrtf(2.f * (float)r);
+  while (Bt > 0 && Bt * (Bt + 1) / 2 > r) --Bt;
+  while ((Bt + 1) * (Bt + 2) / 2 <= r) ++Bt;
+  const int A = r - Bt * (Bt + 1) / 2;
+  const int T[3] = {A, Bt, C};
   for (int p = 0; p < 6; ++p) {
     for (int q = 0; q < 3; ++q) org[p][q] = T[kC3P[p][q]];
     int sl = p;
-    for (int r = 0; r < p; ++r)
-      if (org[r][0] == org[p][0] && org[r][1] == org[p][1] && org[r][2] == org[p][2]) {
-        sl = slot[r];
+    for (int r2 = 0; r2 < p; ++r2)
+      if (org[r2][0] == org[p][0] && org[r2][1] == org[p][1] && org[r2][2] == org[p][2]) {
+        sl = slot[r2];
         break;
       }
     slot[p] = sl;
   }
 }
 
-// The in-place transform of the staged tiles (all threads of the block; the
-// tiles hold X on entry and Xt on return, both barriers inside).
+// 128 threads, each taking four consecutive elements (along the fastest
+// index) of a row of every tile, so that the row's address arithmetic and the
+// orbit bookkeeping serve four elements (one element per thread had left the
+// kernel bound by instruction issue).
 template <typename T>
-__device__ __forceinline__ void c3_transform(T *tile, const int org[6][3], const int slot[6],
-                                             int nv) {
-  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
-  const int A = org[0][0], Bt = org[0][1], C = org[0][2];
-  const int l[3] = {li, lj, lk};
-  const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
-                   8 * Bt + lj < nv && 8 * C + lk < nv;
-  T v[6];
-  int pos[6];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) {
-    pos[p] = slot[p] * kC3T + l[kC3P[p][0]] * kC3SI + l[kC3P[p][1]] * kC3SJ + l[kC3P[p][2]];
-    v[p] = tile[pos[p]];
-  }
-  __syncthreads();  // every thread holds its inputs; the tiles now take the outputs
-  if (own) {
-    const T E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
-    const T be = fma(T(-2), Od, E), bo = fma(T(-2), E, Od);
-#pragma unroll
-    for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(T(3), v[p], p < 3 ? be : bo);
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
+__global__ void __launch_bounds__(128) contra3_kernel(const T *__restrict__ X,
                                                       T *__restrict__ Xt, long long nblocks,
                                                       int nv) {
   __shared__ T tile[6 * kC3T];
@@ -459,24 +436,57 @@ __global__ void __launch_bounds__(512) contra3_kernel(const T *__restrict__ X,
   T *O = Xt + blk * nv3;
   if (threadIdx.x == 0) c3_orbit(blockIdx.x, (nv + 7) / 8, org, slot);
   __syncthreads();
-  const int li = threadIdx.x / 64, lj = (threadIdx.x / 8) % 8, lk = threadIdx.x % 8;
-  const int sidx = li * kC3SI + lj * kC3SJ + lk;
-  // the six loads are issued before any of them is stored to shared memory
-  T x6[6];
+  const int t = threadIdx.x;
+  const int li = t >> 4, lj = (t >> 1) & 7, lk0 = (t & 1) * 4;
+  const int srow = li * kC3SI + lj * kC3SJ + lk0;
+  // the loads of all six tiles are issued before any of them is stored
+  T v[6][4];
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    x6[p] = (slot[p] == p && x < nv && y < nv && z < nv) ? B[((long long)x * nv + y) * nv + z] : T(0);
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z0 = 8 * org[p][2] + lk0;
+    const bool row = slot[p] == p && x < nv && y < nv;
+    const T *src = B + ((long long)x * nv + y) * nv + z0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[p][e] = (row && z0 + e < nv) ? src[e] : T(0);
   }
 #pragma unroll
   for (int p = 0; p < 6; ++p)
-    if (slot[p] == p) tile[p * kC3T + sidx] = x6[p];
+    if (slot[p] == p)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tile[p * kC3T + srow + e] = v[p][e];
   __syncthreads();
-  c3_transform(tile, org, slot, nv);
+  // the element orbits owned in tile (A, B, C): reads and writes of disjoint
+  // orbits, no barrier between them
+  const int A = org[0][0], Bt = org[0][1], C = org[0][2];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int lk = lk0 + e;
+    const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
+                     8 * Bt + lj < nv && 8 * C + lk < nv;
+    if (!own) continue;
+    const int l[3] = {li, lj, lk};
+    T w[6];
+    int pos[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      pos[p] = slot[p] * kC3T + l[kC3P[p][0]] * kC3SI + l[kC3P[p][1]] * kC3SJ + l[kC3P[p][2]];
+      w[p] = tile[pos[p]];
+    }
+    const T E = (w[0] + w[1]) + w[2], Od = (w[3] + w[4]) + w[5];
+    const T be = fma(T(-2), Od, E), bo = fma(T(-2), E, Od);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) tile[pos[p]] = fma(T(3), w[p], p < 3 ? be : bo);
+  }
+  __syncthreads();
+#pragma unroll
   for (int p = 0; p < 6; ++p) {
     if (slot[p] != p) continue;
-    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z = 8 * org[p][2] + lk;
-    if (x < nv && y < nv && z < nv) O[((long long)x * nv + y) * nv + z] = tile[p * kC3T + sidx];
+    const int x = 8 * org[p][0] + li, y = 8 * org[p][1] + lj, z0 = 8 * org[p][2] + lk0;
+    if (x >= nv || y >= nv) continue;
+    T *dst = O + ((long long)x * nv + y) * nv + z0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (z0 + e < nv) dst[e] = tile[p * kC3T + srow + e];
   }
 }
 
@@ -491,10 +501,10 @@ cudaError_t launch_contra3(const double *X, double *Xt, long long nblocks, int n
     const long long nb = nblocks - b0 < 65535 ? nblocks - b0 : 65535;
     const dim3 grid((unsigned)norb, (unsigned)nb);
     if (f32)
-      contra3_kernel<float><<<grid, 512, 0, st>>>(reinterpret_cast<const float *>(X) + b0 * nv3,
+      contra3_kernel<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float *>(X) + b0 * nv3,
                                                   reinterpret_cast<float *>(Xt) + b0 * nv3, nb, nv);
     else
-      contra3_kernel<double><<<grid, 512, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3, nb, nv);
+      contra3_kernel<double><<<grid, 128, 0, st>>>(X + b0 * nv3, Xt + b0 * nv3, nb, nv);
   }
   return cudaGetLastError();
 }
@@ -807,24 +817,30 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
         int x2 = (int)(r - q1 * nv);
         const float wv[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
         float qv[4];
+        // eps_x0 + eps_x1 - eps_ijk - omega, shared by the quad's elements of one row
+        float bh = ev[x0].x, bl = ev[x0].y;
+        df_add(bh, bl, ev[x1].x, ev[x1].y);
+        df_add(bh, bl, eoh, eol);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          float dh = ev[x0].x, dl = ev[x0].y;
-          df_add(dh, dl, ev[x1].x, ev[x1].y);
+          float dh = bh, dl = bl;
           df_add(dh, dl, ev[x2].x, ev[x2].y);
-          df_add(dh, dl, eoh, eol);
           const float den = dh + dl;
           qv[e] = 0.f;
           if (fabsf(den) < 1e-3f)
             atomicOr(status, 1);
           else
             qv[e] = -wv[e] * __frcp_rn(den);
-          if (++x2 == nv) {  // next element: carry into x1, x0
+          if (++x2 == nv) {  // next element starts a row: carry into x1, x0
             x2 = 0;
             if (++x1 == nv) {
               x1 = 0;
               ++x0;
             }
+            bh = ev[x0].x;
+            bl = ev[x0].y;
+            df_add(bh, bl, ev[x1].x, ev[x1].y);
+            df_add(bh, bl, eoh, eol);
           }
         }
         if (out32)
@@ -1105,11 +1121,18 @@ template <int U, typename TA, typename LdB>
 __device__ __forceinline__ double strided_dot(const TA *__restrict__ Am, LdB ldb, const int Kn[3],
                                               const long long ka[3], const long long kb[3],
                                               long long k0, long long kend, int step) {
+  // running offsets of A and B: per element one add of the step's offset and,
+  // where k3 or k2 wraps, of the carry's correction (no multiplication)
   int k3 = (int)(k0 % Kn[2]);
   const long long k12 = k0 / Kn[2];
-  int k2 = (int)(k12 % Kn[1]), k1 = (int)(k12 / Kn[1]);
+  int k2 = (int)(k12 % Kn[1]);
+  const long long k1 = k12 / Kn[1];
+  long long oa = k1 * ka[0] + k2 * ka[1] + k3 * ka[2], ob = k1 * kb[0] + k2 * kb[1] + k3 * kb[2];
   const int d3 = step % Kn[2], d12 = step / Kn[2];
   const int d2 = d12 % Kn[1], d1 = d12 / Kn[1];
+  const long long sa = d1 * ka[0] + d2 * ka[1] + d3 * ka[2], sb = d1 * kb[0] + d2 * kb[1] + d3 * kb[2];
+  const long long c3a = ka[1] - Kn[2] * ka[2], c3b = kb[1] - Kn[2] * kb[2];  // k3 wraps into k2
+  const long long c2a = ka[0] - Kn[1] * ka[1], c2b = kb[0] - Kn[1] * kb[1];  // k2 wraps into k1
   double s = 0.0;
   TA sf = TA(0);
   int nf = 0;
@@ -1118,21 +1141,24 @@ __device__ __forceinline__ double strided_dot(const TA *__restrict__ Am, LdB ldb
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool ok = k + (long long)u * step < kend;
-      av[u] = ok ? Am[k1 * ka[0] + k2 * ka[1] + k3 * ka[2]] : TA(0);
-      bv[u] = ok ? ldb(k1 * kb[0] + k2 * kb[1] + k3 * kb[2]) : TA(0);
+      av[u] = ok ? Am[oa] : TA(0);
+      bv[u] = ok ? ldb(ob) : TA(0);
+      oa += sa;
+      ob += sb;
       k3 += d3;
       int c = 0;
       if (k3 >= Kn[2]) {
         k3 -= Kn[2];
         c = 1;
+        oa += c3a;
+        ob += c3b;
       }
       k2 += d2 + c;
-      c = 0;
       if (k2 >= Kn[1]) {
         k2 -= Kn[1];
-        c = 1;
+        oa += c2a;
+        ob += c2b;
       }
-      k1 += d1 + c;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) sf = fma(av[u], bv[u], sf);
@@ -1165,6 +1191,10 @@ __device__ __forceinline__ double strided_dot(const TA *__restrict__ Am, LdB ldb
 // products and sums.  One (atomic) update per output and K slice.  Grid: x =
 // the most blocks any item's mapping needs (ceil(M / 8) covers them all),
 // y = items.
+// loads in flight per lane: eight binary32 or four binary64 elements
+template <typename TA>
+constexpr int kGemvU = sizeof(TA) == 4 ? 8 : 4;
+
 template <typename TA>
 __device__ __forceinline__ void gemv_body(const BstcParams &p) {
   __shared__ double red[8][33];
@@ -1187,7 +1217,7 @@ __device__ __forceinline__ void gemv_body(const BstcParams &p) {
     const long long m = cg * 32 + lane;
     if (m >= M) return;
     const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
-    const double s = strided_dot<8>(A + m1 * it.sA[0] + m2 * it.sA[1], ldb, Kn, ka, kb, 0, K, 1);
+    const double s = strided_dot<kGemvU<TA>>(A + m1 * it.sA[0] + m2 * it.sA[1], ldb, Kn, ka, kb, 0, K, 1);
     double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
     if (p.atomic) atomicAdd(C, p.alpha * s);
     else *C += p.alpha * s;
@@ -1207,7 +1237,7 @@ __device__ __forceinline__ void gemv_body(const BstcParams &p) {
     const long long m1 = mf == 1 ? m / M2 : m % M1, m2 = mf == 1 ? m % M2 : m / M1;
     const TA *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
     // the warps take k = kbeg + warp, + 8, ...
-    const double s = valid ? strided_dot<8>(Am, ldb, Kn, ka, kb, kbeg + warp, kend, 8) : 0.0;
+    const double s = valid ? strided_dot<kGemvU<TA>>(Am, ldb, Kn, ka, kb, kbeg + warp, kend, 8) : 0.0;
     red[warp][lane] = s;
     __syncthreads();
     if (warp == 0 && valid) {
@@ -1238,7 +1268,7 @@ __device__ __forceinline__ void gemv_body(const BstcParams &p) {
   const bool valid = m < M;
   const long long m1 = valid ? m / M2 : 0, m2 = valid ? m % M2 : 0;
   const TA *Am = A + m1 * it.sA[0] + m2 * it.sA[1];
-  double s = valid ? strided_dot<8>(Am, ldb, Kn, ka, kb, sub, K, lpo) : 0.0;
+  double s = valid ? strided_dot<kGemvU<TA>>(Am, ldb, Kn, ka, kb, sub, K, lpo) : 0.0;
   for (int o = lpo / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (valid && sub == 0) {
     double *C = p.C + it.offC + m1 * it.sC[0] + m2 * it.sC[1];
@@ -1247,9 +1277,9 @@ __device__ __forceinline__ void gemv_body(const BstcParams &p) {
   }
 }
 
-__global__ void __launch_bounds__(256) bstc_gemv32_kernel(BstcParams p) { gemv_body<float>(p); }
+__global__ void __launch_bounds__(256, 3) bstc_gemv32_kernel(BstcParams p) { gemv_body<float>(p); }
 
-__global__ void __launch_bounds__(256) bstc_gemv_kernel(BstcParams p) { gemv_body<double>(p); }
+__global__ void __launch_bounds__(256, 3) bstc_gemv_kernel(BstcParams p) { gemv_body<double>(p); }
 
 
 }  // namespace mlcc3
