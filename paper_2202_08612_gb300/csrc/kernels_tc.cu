@@ -860,11 +860,29 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
   const int tr = (Rp + 63) / 64, tc = (C + 31) / 32;
   const long long ntiles = B * (long long)tr * tc;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  // tile index -> (batch, row tile, column tile) in 32-bit arithmetic when the
+  // tile count allows it (a 64-bit division costs several times more)
+  const bool small = ntiles < (1LL << 31);
+  const unsigned int utc = (unsigned int)tc, utrc = (unsigned int)(tr * tc);
+  auto split = [&](long long q, long long &b, int &rt, int &ct) {
+    if (small) {
+      const unsigned int uq = (unsigned int)q, qb = uq / utrc, rem = uq - qb * utrc;
+      b = qb;
+      rt = (int)(rem / utc);
+      ct = (int)(rem - (unsigned int)rt * utc);
+    } else {
+      b = q / ((long long)tr * tc);
+      rt = (int)((q / tc) % tr);
+      ct = (int)(q % tc);
+    }
+  };
   // rows ty, ty + 8, ..., ty + 56 of tile q, column tx, into registers
   Tin pf[8];
   auto load = [&](long long q) {
-    const long long b = q / ((long long)tr * tc);
-    const int r0 = (int)((q / tc) % tr) * 64, c = (int)(q % tc) * 32 + tx;
+    long long b;
+    int rt, ct;
+    split(q, b, rt, ct);
+    const int r0 = rt * 64, c = ct * 32 + tx;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int r = r0 + ty + 8 * k;
@@ -873,8 +891,10 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(
   };
   if (blockIdx.x < ntiles) load(blockIdx.x);
   for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
-    const long long b = q / ((long long)tr * tc);
-    const int r0 = (int)((q / tc) % tr) * 64, c0 = (int)(q % tc) * 32;
+    long long b;
+    int rt, ct;
+    split(q, b, rt, ct);
+    const int r0 = rt * 64, c0 = ct * 32;
     __syncthreads();  // the previous tile's reads of `tile` are done
 #pragma unroll
     for (int k = 0; k < 8; ++k) tile[ty + 8 * k][tx] = pf[k];
