@@ -708,6 +708,33 @@ __device__ __forceinline__ void split4_store(const Tin *x, __nv_bfloat16 *hi,
   *reinterpret_cast<uint2 *>(lo) = make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
 }
 
+// Four consecutive elements p[0..3] of a contiguous row (n of them valid,
+// zeros beyond): one 16-byte load where p is 16-byte aligned, else 8-byte
+// loads where it is 8-byte aligned, else single elements.
+__device__ __forceinline__ void load4_row(const float *p, int n, float x[4]) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  if (n >= 4 && (a & 15) == 0) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else if (n >= 4 && (a & 7) == 0) {
+    const float2 u = reinterpret_cast<const float2 *>(p)[0], v = reinterpret_cast<const float2 *>(p)[1];
+    x[0] = u.x; x[1] = u.y; x[2] = v.x; x[3] = v.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = j < n ? p[j] : 0.f;
+  }
+}
+__device__ __forceinline__ void load4_row(const double *p, int n, double x[4]) {
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  if (n >= 4 && (a & 15) == 0) {
+    const double2 u = reinterpret_cast<const double2 *>(p)[0], v = reinterpret_cast<const double2 *>(p)[1];
+    x[0] = u.x; x[1] = u.y; x[2] = v.x; x[3] = v.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = j < n ? p[j] : 0.0;
+  }
+}
+
 // Split FP64 -> (hi, lo) bfloat16 with a 4-D permuted gather and K padding:
 // out[o0][o1][o2][o3] (o3 < K3p, zero for o3 >= K3) = scale * in[o0 s0 + o1 s1 + o2 s2 + o3 s3].
 // K3p is a multiple of 4.  Groups of 64 threads take one output row (o0, o1,
@@ -735,12 +762,30 @@ __device__ __forceinline__ void split_bf16_body(const Tin *__restrict__ in, __nv
   for (; r < rend; ++r) {
     const Tin *src = in + o0 * s0 + o1 * s1 + o2 * s2;
     __nv_bfloat16 *h = hi + r * K3p, *l = lo + r * K3p;
-    for (int k = 4 * t; k < k3p; k += 256) {
-      Tin x[4];
+    if (s3 == 1) {
+      // contiguous row: vector loads, two steps' loads issued before their stores
+      for (int k = 4 * t; k < k3p; k += 512) {
+        Tin x[4], y[4];
+        load4_row(src + k, k3 - k, x);
+        const bool two = k + 256 < k3p;
+        if (two) load4_row(src + k + 256, k3 - k - 256, y);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : Tin(0);
-      split4_store(x, h + k, l + k);
+        for (int j = 0; j < 4; ++j) x[j] = scaled(x[j], mode, scale);
+        split4_store(x, h + k, l + k);
+        if (two) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) y[j] = scaled(y[j], mode, scale);
+          split4_store(y, h + k + 256, l + k + 256);
+        }
+      }
+    } else {
+      for (int k = 4 * t; k < k3p; k += 256) {
+        Tin x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          x[j] = k + j < k3 ? scaled(src[(long long)(k + j) * s3], mode, scale) : Tin(0);
+        split4_store(x, h + k, l + k);
+      }
     }
     if (++o2 == D2) {
       o2 = 0;
@@ -786,6 +831,25 @@ __device__ __forceinline__ void split_bf16_k2_body(const Tin *__restrict__ in, _
     const long long o1 = r % D1, o0 = r / D1;
     const Tin *src = in + o0 * s0 + o1 * s1;
     __nv_bfloat16 *h = hi + r * Kp, *l = lo + r * Kp;
+    if (sk2 == 1 && sk1 == K2) {
+      // the K pair is one contiguous row: vector loads, two steps' loads
+      // issued before their stores
+      for (int k = 4 * t; k < kp; k += 512) {
+        Tin x[4], y[4];
+        load4_row(src + k, K - k, x);
+        const bool two = k + 256 < kp;
+        if (two) load4_row(src + k + 256, K - k - 256, y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = scaled(x[j], mode, scale);
+        split4_store(x, h + k, l + k);
+        if (two) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) y[j] = scaled(y[j], mode, scale);
+          split4_store(y, h + k + 256, l + k + 256);
+        }
+      }
+      continue;
+    }
     // (q1, q2) = split of k, advanced by 256 per step with a carry
     int q1 = (4 * t) / kk2, q2 = 4 * t - q1 * kk2;
     const int dq1 = 256 / kk2, dq2 = 256 - dq1 * kk2;
