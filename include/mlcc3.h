@@ -249,6 +249,11 @@ void mlcc3_sweep_destroy(mlcc3_sweep *sweep);
  *              call (the transition densities need more than the Jacobian
  *              transformations); each call then allocates its scratch again.
  *              A sweep needs contexts with 0 (MLCC3_ERR_STATE otherwise).
+ *   "bstc_big_from"  split-precision contractions with one reduction index
+ *              and at least this many multiply-adds per launch (M N K summed
+ *              over the launch's items) run on 128 x 128 CUDA-core tiles with
+ *              FP32 accumulation over K ranges of at most 1024 (summed in
+ *              FP64); the others on 64 x 64 tiles.  Default 10^9; 0: never.
  *   "finish_fused"  1 (default): in the split-precision mode the finish of a
  *              triples build (rank-1 terms, denominators) and the contravariant
  *              transform of its blocks run as one pass over tile orbits; 0: as

@@ -127,6 +127,9 @@ struct mlcc3_ctx {
   bool release_scratch = false;
   // split mode: finish and contravariant transform of a triples build fused
   bool finish_fused = true;
+  // split mode: flat contractions (one K index) with at least this many
+  // multiply-adds (M N K per launch) run on the 128 x 128 kernel (0: never)
+  long long bstc_big_from = 1000000000LL;
   std::set<std::string> keep_scratch, keep_splits;
   void release();
   // Triples arrays (tau, R3, L3, lambda3 and their contravariant forms) are

@@ -160,6 +160,160 @@ __device__ __forceinline__ void bstc_body(const BstcParams &p) {
 __global__ void __launch_bounds__(256) bstc_kernel(BstcParams p) { bstc_body<double>(p); }
 __global__ void __launch_bounds__(256) bstc_f32_kernel(BstcParams p) { bstc_body<float>(p); }
 
+// Large contractions with a single K index (K2 = K3 = 1) in the split mode:
+// 128 x 128 tiles of C, 256 threads with 8 x 8 outputs each, K tiles of 8
+// double-buffered in shared memory (the next tile's loads in registers while
+// the current one is multiplied), FP32 products accumulated in FP32 over the
+// block's K range (at most 1024, the host splits longer reductions over
+// grid.z) and added to C in FP64.  The loads of A run along K when A is
+// K-contiguous, else along M; those of B along N when B is N-contiguous, else
+// along K.  For the T1 transformation of the Cholesky vectors and the other
+// long flat contractions, which the 64 x 64 kernel ran at 8% of the FP32 rate.
+namespace {
+constexpr int GBM = 128, GBN = 128, GBK = 8, GPAD = 4;
+}
+
+__device__ __forceinline__ float ld_f(const double *p, int f32, long long i) {
+  return f32 ? reinterpret_cast<const float *>(p)[i] : (float)p[i];
+}
+
+__global__ void __launch_bounds__(256, 1) bstc_big_kernel(BstcParams p) {
+  __shared__ __align__(16) float As[2][GBK][GBM + GPAD];
+  __shared__ __align__(16) float Bs[2][GBK][GBN + GPAD];
+  const BstcItem &it = p.items[blockIdx.y];
+  const int t = threadIdx.x;
+  const long long M = (long long)p.M1 * p.M2, N = (long long)p.N1 * p.N2, K = p.K1;
+  const long long ntn = (N + GBN - 1) / GBN;
+  const long long m0 = ((long long)blockIdx.x / ntn) * GBM, n0 = ((long long)blockIdx.x % ntn) * GBN;
+  const long long kbeg = p.kchunk ? (long long)blockIdx.z * p.kchunk : 0;
+  const long long kend = p.kchunk ? min(K, kbeg + p.kchunk) : K;
+  const long long sAk = it.sA[2], sBk = it.sB[0];
+  auto aoff = [&](long long m) -> long long {
+    if (m >= M) return -1;
+    return it.offA + (m / p.M2) * it.sA[0] + (m % p.M2) * it.sA[1];
+  };
+  auto boff = [&](long long n) -> long long {
+    if (n >= N) return -1;
+    return it.offB + (n / p.N2) * it.sB[3] + (n % p.N2) * it.sB[4];
+  };
+  // loader mappings
+  const bool akc = sAk == 1;                                        // A along K
+  const bool bnc = p.N2 > 1 ? it.sB[4] == 1 : it.sB[3] == 1;        // B along N
+  int ar, ak, bc, bk;
+  long long ao[4], bo[4];
+  if (akc) {
+    ar = t >> 1;
+    ak = (t & 1) * 4;
+    ao[0] = aoff(m0 + ar);
+  } else {
+    ak = t >> 5;
+    ar = (t & 31) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ao[j] = aoff(m0 + ar + j);
+  }
+  if (bnc) {
+    bk = t >> 5;
+    bc = (t & 31) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bo[j] = boff(n0 + bc + j);
+  } else {
+    bc = t >> 1;
+    bk = (t & 1) * 4;
+    bo[0] = boff(n0 + bc);
+  }
+  float ra[4], rb[4];
+  auto gload = [&](long long k0) {
+    if (akc) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long k = k0 + ak + j;
+        ra[j] = (ao[0] >= 0 && k < kend) ? ld_f(p.A, p.a32, ao[0] + k) : 0.f;
+      }
+    } else {
+      const long long k = k0 + ak;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ra[j] = (ao[j] >= 0 && k < kend) ? ld_f(p.A, p.a32, ao[j] + k * sAk) : 0.f;
+    }
+    if (bnc) {
+      const long long k = k0 + bk;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rb[j] = (bo[j] >= 0 && k < kend) ? ld_f(p.B, p.b32, bo[j] + k * sBk) : 0.f;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long k = k0 + bk + j;
+        rb[j] = (bo[0] >= 0 && k < kend) ? ld_f(p.B, p.b32, bo[0] + k * sBk) : 0.f;
+      }
+    }
+  };
+  auto sstore = [&](int buf) {
+    if (akc) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) As[buf][ak + j][ar] = ra[j];
+    } else {
+      *reinterpret_cast<float4 *>(&As[buf][ak][ar]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+    }
+    if (bnc) {
+      *reinterpret_cast<float4 *>(&Bs[buf][bk][bc]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) Bs[buf][bk + j][bc] = rb[j];
+    }
+  };
+  const int ty = t >> 4, tx = t & 15;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  gload(kbeg);
+  sstore(0);
+  __syncthreads();
+  int cur = 0;
+  for (long long k0 = kbeg; k0 < kend; k0 += GBK) {
+    const bool more = k0 + GBK < kend;
+    if (more) gload(k0 + GBK);
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[cur][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) {
+      sstore(cur ^ 1);
+      __syncthreads();
+      cur ^= 1;
+    }
+  }
+  double *C = p.C + it.offC;
+  long long cn[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+    cn[j] = n < N ? (n / p.N2) * it.sC[2] + (n % p.N2) * it.sC[3] : -1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= M) continue;
+    const long long cm = (m / p.M2) * it.sC[0] + (m % p.M2) * it.sC[1];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (cn[j] < 0) continue;
+      const double v = p.alpha * (double)acc[i][j];
+      if (p.atomic) atomicAdd(C + cm + cn[j], v);
+      else C[cm + cn[j]] += v;
+    }
+  }
+}
+
 // Dot-product form (M = N = 1, large K): one CTA per item reduces over K.
 __global__ void __launch_bounds__(256) bstc_dot_kernel(BstcParams p) {
   __shared__ double red[256];

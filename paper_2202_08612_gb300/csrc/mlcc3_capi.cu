@@ -29,6 +29,7 @@
 namespace mlcc3 {
 __global__ void bstc_kernel(BstcParams p);
 __global__ void bstc_f32_kernel(BstcParams p);
+__global__ void bstc_big_kernel(BstcParams p);
 __global__ void bstc_dot_kernel(BstcParams p);
 __global__ void bstc_gemv_kernel(BstcParams p);
 __global__ void bstc_gemv32_kernel(BstcParams p);
@@ -337,9 +338,32 @@ void mlcc3_ctx::bstc(const double *A, const double *B, double *C, const Shape &s
     check_cuda(cudaGetLastError(), "bstc_gemv launch");
     return;
   }
+  const long long K = sh.K1 * sh.K2 * sh.K3;
+  if (f32 && sh.K2 == 1 && sh.K3 == 1 && bstc_big_from > 0 &&
+      (double)M * (double)N * (double)K * nitems >= (double)bstc_big_from) {
+    // large flat contraction: 128 x 128 tiles, FP32 accumulation over K ranges
+    // of at most 1024 (split over grid.z, FP64 atomic adds when split)
+    const long long tiles = ((N + 127) / 128) * ((M + 127) / 128);
+    long long ks = (K + 1023) / 1024;
+    p.kchunk = ks > 1 ? ((K + ks - 1) / ks + 7) / 8 * 8 : 0;
+    if (ks > 1) {
+      ks = (K + p.kchunk - 1) / p.kchunk;
+      p.atomic = 1;
+    }
+    for (int z0 = 0; z0 < nitems; z0 += 65535) {
+      p.items = it + z0;
+      const int nz = std::min(65535, nitems - z0);
+      dim3 grid((unsigned)tiles, (unsigned)nz, (unsigned)ks);
+      const std::string name = tag.empty() ? std::string("bstc_kernel") : "bstc_kernel:" + tag;
+      launch(name.c_str(), 2.0 * M * N * (double)K * nz, [&] {
+        bstc_big_kernel<<<grid, 256, 0, stream>>>(p);
+      });
+    }
+    check_cuda(cudaGetLastError(), "bstc launch");
+    return;
+  }
   const long long tiles = ((N + 63) / 64) * ((M + 63) / 64);
   // split K when few output tiles face a long reduction
-  const long long K = sh.K1 * sh.K2 * sh.K3;
   long long ksplit = 1;
   if (bstc_fill > 0 && tiles * nitems < 2 * 152 && K >= 1024) {
     ksplit = std::min<long long>((bstc_fill * 152LL + tiles * nitems - 1) / (tiles * nitems), K / 256);
@@ -3225,6 +3249,9 @@ extern "C" int mlcc3_set_param(mlcc3_ctx *c, const char *name, long long value) 
         check_cuda(cudaStreamSynchronize(c->stream), "sync");
         c->release();
       }
+    } else if (n == "bstc_big_from") {
+      if (value < 0) throw Error{MLCC3_ERR_ARG, "bstc_big_from must be >= 0"};
+      c->bstc_big_from = value;
     } else if (n == "finish_fused") {
       if (value != 0 && value != 1) throw Error{MLCC3_ERR_ARG, "finish_fused must be 0 or 1"};
       c->finish_fused = value == 1;

@@ -129,6 +129,24 @@ def test_split_persistent_kernel_everywhere():
         assert rel_err(got[k], ref[k]) < TOL, (k, rel_err(got[k], ref[k]))
 
 
+def test_split_large_flat_contraction_kernel():
+    """bstc_big_from = 1: every flat contraction (one K index) of the split
+    path runs on the 128 x 128 kernel, ragged in M, N and K at these sizes;
+    the whole path still meets its bar."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_common import oracle_all, run_all
+    c = Case(NO=7, NV=30, no=5, nv=13, NJ=40, nstates=1)
+    g = c.context(precision=binding.MLCC3_SPLIT_BF16X3)
+    g.set_param("bstc_big_from", 1)
+    got, ref = run_all(c, g), oracle_all(c)
+    for k in ref:
+        assert rel_err(got[k], ref[k]) < TOL, (k, rel_err(got[k], ref[k]))
+    with pytest.raises(binding.MLCC3Error):
+        g.set_param("bstc_big_from", -1)
+
+
 @pytest.mark.parametrize("chunk_blocks", [0, 7])
 def test_split_unfused_finish(chunk_blocks):
     """finish_fused = 0: the streaming finish followed by the separate
