@@ -543,6 +543,18 @@ constexpr int kC3SJ = 9, kC3SI = 8 * kC3SJ + 1, kC3T = 8 * kC3SI;  // padded til
 __constant__ int kC3P[6][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}};
 }  // namespace
 
+// Positions of the six permutations (in the order of kC3P) of element
+// (l0, l1, l2) in tiles staged at slot s with strides (SI, SJ, 1), TT apart.
+template <int SI, int SJ, int TT>
+__device__ __forceinline__ void c3_pos(int l0, int l1, int l2, const int *slot, int pos[6]) {
+  pos[0] = slot[0] * TT + l0 * SI + l1 * SJ + l2;
+  pos[1] = slot[1] * TT + l2 * SI + l0 * SJ + l1;
+  pos[2] = slot[2] * TT + l1 * SI + l2 * SJ + l0;
+  pos[3] = slot[3] * TT + l1 * SI + l0 * SJ + l2;
+  pos[4] = slot[4] * TT + l2 * SI + l1 * SJ + l0;
+  pos[5] = slot[5] * TT + l0 * SI + l2 * SJ + l1;
+}
+
 // Thread 0 of a block: orbit index o -> tile origins (A, B, C), A <= B <= C,
 // the origins org[p] of the six permuted tiles and, for each, the slot of the
 // first permutation with the same origin (its shared-memory tile).  The orbits
@@ -618,14 +630,11 @@ __global__ void __launch_bounds__(128) contra3_kernel(const T *__restrict__ X,
     const bool own = (A < Bt || li <= lj) && (Bt < C || lj <= lk) && 8 * A + li < nv &&
                      8 * Bt + lj < nv && 8 * C + lk < nv;
     if (!own) continue;
-    const int l[3] = {li, lj, lk};
     T w[6];
     int pos[6];
+    c3_pos<kC3SI, kC3SJ, kC3T>(li, lj, lk, slot, pos);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) {
-      pos[p] = slot[p] * kC3T + l[kC3P[p][0]] * kC3SI + l[kC3P[p][1]] * kC3SJ + l[kC3P[p][2]];
-      w[p] = tile[pos[p]];
-    }
+    for (int p = 0; p < 6; ++p) w[p] = tile[pos[p]];
     const T E = (w[0] + w[1]) + w[2], Od = (w[3] + w[4]) + w[5];
     const T be = fma(T(-2), Od, E), bo = fma(T(-2), E, Od);
 #pragma unroll
@@ -915,8 +924,9 @@ __device__ __forceinline__ int finish_merge(FinishEnt *tab, int n, const FinishE
 // elements per pass over the table.  eps^{abc}_{ijk} - omega is an exact
 // double-float sum of FP32 (hi, lo) pairs (ehl: the virtual energies' pairs),
 // which keeps FP64 accuracy off the FP64 pipe; the quotient of the FP32
-// numerator is taken in FP32 and widened on the integer pipe.  omega is read
-// from omega_p when it is set.
+// numerator is taken in FP32 (a fast division, within two units in the last
+// place of the binary32 result that is stored) and widened on the integer
+// pipe.  omega is read from omega_p when it is set.
 __global__ void __launch_bounds__(256) triples_finish_kernel(
     const float *__restrict__ W, const TripItem *__restrict__ items, int nitems,
     const TripTerms terms, const double *__restrict__ eps, const float2 *__restrict__ ehl, int nv,
@@ -924,7 +934,7 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
     double *__restrict__ out, int out32, int *__restrict__ status) {
   using Ent = FinishEnt;
   __shared__ Ent tab[2 * kMaxTerms * 6];
-  __shared__ float2 ev[1024];
+  __shared__ __align__(16) float2 ev[1024];
   __shared__ float eoh, eol;
   __shared__ int nent;
   if ((int)blockIdx.y >= nitems) return;
@@ -975,26 +985,45 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
         float bh = ev[x0].x, bl = ev[x0].y;
         df_add(bh, bl, ev[x1].x, ev[x1].y);
         df_add(bh, bl, eoh, eol);
+        if (x2 + 3 < nv && (nv & 1) == 0) {
+          // the quad lies in one row and starts at an even x2: its four (hi, lo)
+          // pairs in two 16-byte shared loads
+          const float4 e01 = *reinterpret_cast<const float4 *>(&ev[x2]);
+          const float4 e23 = *reinterpret_cast<const float4 *>(&ev[x2 + 2]);
+          const float eh[4] = {e01.x, e01.z, e23.x, e23.z}, el[4] = {e01.y, e01.w, e23.y, e23.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          float dh = bh, dl = bl;
-          df_add(dh, dl, ev[x2].x, ev[x2].y);
-          const float den = dh + dl;
-          qv[e] = 0.f;
-          if (fabsf(den) < 1e-3f)
-            atomicOr(status, 1);
-          else
-            qv[e] = -wv[e] * __frcp_rn(den);
-          if (++x2 == nv) {  // next element starts a row: carry into x1, x0
-            x2 = 0;
-            if (++x1 == nv) {
-              x1 = 0;
-              ++x0;
+          for (int e = 0; e < 4; ++e) {
+            float dh = bh, dl = bl;
+            df_add(dh, dl, eh[e], el[e]);
+            const float den = dh + dl;
+            qv[e] = 0.f;
+            if (fabsf(den) < 1e-3f)
+              atomicOr(status, 1);
+            else
+              qv[e] = __fdividef(-wv[e], den);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float dh = bh, dl = bl;
+            df_add(dh, dl, ev[x2].x, ev[x2].y);
+            const float den = dh + dl;
+            qv[e] = 0.f;
+            if (fabsf(den) < 1e-3f)
+              atomicOr(status, 1);
+            else
+              qv[e] = __fdividef(-wv[e], den);
+            if (++x2 == nv) {  // next element starts a row: carry into x1, x0
+              x2 = 0;
+              if (++x1 == nv) {
+                x1 = 0;
+                ++x0;
+              }
+              bh = ev[x0].x;
+              bl = ev[x0].y;
+              df_add(bh, bl, ev[x1].x, ev[x1].y);
+              df_add(bh, bl, eoh, eol);
             }
-            bh = ev[x0].x;
-            bl = ev[x0].y;
-            df_add(bh, bl, ev[x1].x, ev[x1].y);
-            df_add(bh, bl, eoh, eol);
           }
         }
         if (out32)
@@ -1047,7 +1076,7 @@ __global__ void __launch_bounds__(256) triples_finish_kernel(
       if (fabsf(den) < 1e-3f)
         atomicOr(status, 1);
       else
-        q = -acc[k] * __frcp_rn(den);
+        q = __fdividef(-acc[k], den);
       if (out32)  // binary32 storage of the split-precision mode
         reinterpret_cast<float *>(out)[it.off + r] = q;
       else
@@ -1173,7 +1202,7 @@ __global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
       if (fabsf(den) < 1e-3f)
         atomicOr(status, 1);
       else
-        q = -acc[r] * __frcp_rn(den);
+        q = __fdividef(-acc[r], den);
       ftile[p * kFT + (l0b + 2 * r) * kFSI + l1 * kFSJ + l2] = q;
       if (out) out[it.off + ((long long)x * nv + y) * nv + z] = q;
     }
@@ -1188,14 +1217,11 @@ __global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
       const bool own = (A < Bt || l0 <= l1) && (Bt < C || l1 <= l2) && kFW * A + l0 < nv &&
                        kFW * Bt + l1 < nv && kFW * C + l2 < nv;
       if (!own) continue;
-      const int l[3] = {l0, l1, l2};
       float v[6];
       int pos[6];
+      c3_pos<kFSI, kFSJ, kFT>(l0, l1, l2, slot, pos);
 #pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        pos[p] = slot[p] * kFT + l[kC3P[p][0]] * kFSI + l[kC3P[p][1]] * kFSJ + l[kC3P[p][2]];
-        v[p] = ftile[pos[p]];
-      }
+      for (int p = 0; p < 6; ++p) v[p] = ftile[pos[p]];
       const float E = (v[0] + v[1]) + v[2], Od = (v[3] + v[4]) + v[5];
       const float be = fmaf(-2.f, Od, E), bo = fmaf(-2.f, E, Od);
 #pragma unroll
