@@ -1596,8 +1596,10 @@ void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const Split
 
 // out[occ o1][occ o2][row][n] += coef sum_{orderings grouped by (o1, o2)}
 //      sum_{x,y at view positions (vk1 < vk2)} X_{pqr}[..] * T_{occ t}[n][(x,y)]
-// Rows: view position vr from XL_{s_vr} (128-row tiles); T: split [occ t][n][(x,y)]
-// in both K orders (T, Ts), map dims (K, n, 1, occ t), box BN = tile_width(nN).
+// T: split [occ t][n][(x,y)] in both K orders (T, Ts), map dims (K, n, 1, occ t).
+// The tile rows are T's n (128-row tiles; n = N_O fills 100 of 128) and the
+// columns the view row of X from XL_{s_vr} (tile_width(n_v) columns, 150 of
+// 160): the other way round, the n_v rows in 128-row tiles filled 150 of 256.
 void tc_xt(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp &T,
            const SplitOp &Ts, long long nN, const std::vector<Ord> &ords, const std::string &okey,
            int vr, int tpos, long long S1, long long S2, long long Srow, double coef, double *out) {
@@ -1605,38 +1607,46 @@ void tc_xt(mlcc3_ctx *c, const double *X, const std::string &xkey, const SplitOp
   if (ords.empty() || s.nv == 0 || nN == 0) return;
   const int vk1 = vr == 0 ? 1 : 0, vk2 = vr == 2 ? 1 : 2;
   const int o1 = tpos == 0 ? 1 : 0, o2 = tpos == 2 ? 1 : 2;
+  const int BX = tc_tile_width(s.nv);
   TcMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int k = 0; k < 3; ++k) {
-    SplitOp &r = layout_XL(c, xkey + ":XL" + std::to_string(k), X, k, 128);
+    SplitOp &r = layout_XL(c, xkey + ":XLB" + std::to_string(k), X, k, (unsigned)BX);
     maps.m[2 * k] = r.mhi;
     maps.m[2 * k + 1] = r.mlo;
   }
-  maps.m[6] = T.mhi;
-  maps.m[7] = T.mlo;
-  maps.m[8] = Ts.mhi;
-  maps.m[9] = Ts.mlo;
-  const int BN = tc_tile_width(nN);
-  const long long ntM = (s.nv + 127) / 128, ntN = (nN + BN - 1) / BN;
+  // T and Ts with 128-row boxes (rows past n read as zeros)
+  const unsigned long long Kp = (unsigned long long)((s.nv * s.nv + 63) / 64 * 64);
+  const unsigned long long dims[4] = {Kp, (unsigned long long)nN, 1ULL, (unsigned long long)s.no};
+  const unsigned long long str[3] = {Kp * 2, Kp * 2 * (unsigned long long)nN, Kp * 2 * (unsigned long long)nN};
+  const unsigned bx[4] = {64, 128, 1, 1};
+  SplitOp ta = T, tsa = Ts;
+  encode_split(ta, "xt:T128", dims, str, bx);
+  encode_split(tsa, "xt:Ts128", dims, str, bx);
+  maps.m[6] = ta.mhi;
+  maps.m[7] = ta.mlo;
+  maps.m[8] = tsa.mhi;
+  maps.m[9] = tsa.mlo;
+  const long long ntM = (nN + 127) / 128, ntN = (s.nv + BX - 1) / BX;
   const int nk = (int)((s.nv * s.nv + 63) / 64);
   const std::string key = "tcX:" + okey + ":" + std::to_string(vr) + std::to_string(tpos) + ":" +
-                          std::to_string(nN);
+                          std::to_string(nN) + ":t";
   TcDev dv = tc_plan(c, key, [&](TcPlan &pl) {
     for (long long x1 = 0; x1 < s.no; ++x1)
       for (long long x2 = 0; x2 < s.no; ++x2)
         for (long long tm = 0; tm < ntM; ++tm)
           for (long long tn = 0; tn < ntN; ++tn) {
-            pl.tile(0, (int)(128 * tm), (int)(BN * tn), x1 * S1 + x2 * S2);
+            pl.tile(0, (int)(128 * tm), (int)(BX * tn), x1 * S1 + x2 * S2);
             for (auto &o : ords) {
               if (occ_of(o, o1) != x1 || occ_of(o, o2) != x2) continue;
-              pl.seg(2 * o.sp[vr], o.sp[vk1] < o.sp[vk2] ? 6 : 8, nk, (int)(128 * tm), 0,
-                     (int)(o.off / s.nv3), (int)(BN * tn), 0, occ_of(o, tpos));
+              pl.seg(o.sp[vk1] < o.sp[vk2] ? 6 : 8, 2 * o.sp[vr], nk, (int)(128 * tm), 0,
+                     occ_of(o, tpos), (int)(BX * tn), 0, (int)(o.off / s.nv3));
             }
             pl.drop_empty_last();
           }
   }, c->tc_kcap);
-  TcEpi epi = make_epi(out, 2, 128, 0, Srow, 1, 1, s.nv, nN, coef);
-  tc_launch(c, "xt", BN, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
+  TcEpi epi = make_epi(out, 2, 128, 0, 1, Srow, 1, nN, s.nv, coef);
+  tc_launch(c, "xt", BX, maps, dv, epi, 2.0 * (double)s.nv3 * (double)nN * (double)ords.size());
 }
 
 // out[c][d] (row stride ld) += alpha sum_{orderings} sum_{ab} X_{pqr}[a][b][c] Y_{pqr}[a][b][d]
