@@ -363,7 +363,6 @@ __global__ void __launch_bounds__(192, 1)
     // ---- MMA issuer ----
     int stage = 0;
     uint32_t phase = 0;
-    int sq = 0, kc = 0;  // segment and chunk of chunk c
     for (int c = 0; c < total; ++c) {
       if (!mbar_wait(full0 + 8 * stage, phase, status, epi.wait)) break;
       tc_fence_after();
@@ -371,10 +370,8 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
       const uint32_t bhi = smem_u32(st + 2 * A_BYTES), blo = smem_u32(st + 2 * A_BYTES + B_BYTES);
       const uint32_t idesc = idesc_n(IDESC, ntile);
-      const int kmax = (kc == seg[sq].nk - 1 && seg[sq].kt > 0) ? seg[sq].kt : 4;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        if (kk >= kmax) break;
         const uint32_t off = kk * 32;
         mma_bf16(tmem, smem_desc(ahi + off), smem_desc(bhi + off), idesc, (c > 0 || kk > 0));
         mma_bf16(tmem, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1u);
@@ -384,10 +381,6 @@ __global__ void __launch_bounds__(192, 1)
       if (++stage == STAGES) {
         stage = 0;
         phase ^= 1u;
-      }
-      if (++kc == seg[sq].nk) {
-        kc = 0;
-        ++sq;
       }
     }
     mma_commit(done);  // arrives once every MMA issued above has completed
@@ -547,7 +540,6 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t acc = tmem + (uint32_t)(u * NCOLS);
       const uint32_t idesc = idesc_n(IDESC, (it.nq > 1 ? it.nq : 1) * qrows);
       bool ok = true;
-      int sq = 0, kc = 0;  // segment and chunk of chunk c
       for (int c = 0; c < total; ++c) {
         if (!mbar_wait(full0 + 8 * stage, phase, status, epi.wait)) {
           *abort_flag = 1;
@@ -558,15 +550,8 @@ __global__ void __launch_bounds__(192, 1)
         unsigned char *st = smem + stage * STAGE;
         const uint32_t ahi = smem_u32(st), alo = smem_u32(st + A_BYTES);
         const uint32_t bhi = smem_u32(st + 2 * A_BYTES), blo = smem_u32(st + 2 * A_BYTES + B_BYTES);
-        const TcSeg &sg = segs[it.seg_begin + sq];
-        const int kmax = (kc == sg.nk - 1 && sg.kt > 0) ? sg.kt : 4;
-        if (++kc == sg.nk) {
-          kc = 0;
-          ++sq;
-        }
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          if (kk >= kmax) break;
           const uint32_t off = kk * 32;
           mma_bf16(acc, smem_desc(ahi + off), smem_desc(bhi + off), idesc, (c > 0 || kk > 0));
           mma_bf16(acc, smem_desc(ahi + off), smem_desc(blo + off), idesc, 1u);

@@ -20,12 +20,8 @@ struct TcMaps {
 // same for B with `bmap` and bc.  A grouped tile (TcItem::nq = nb > 1) stacks
 // nb B boxes of TcEpi::qw rows along N: box 0 at bc, box q at bc with
 // coordinates 2 and 3 replaced by bq[q - 1].
-// kt: 16-wide K steps of the segment's last chunk that hold data (1..3; 0: all
-// four) -- the MMAs over the zero padding of a K that is not a multiple of 64
-// are skipped.
 struct TcSeg {
   int amap, bmap, nk, nb;
-  int kt, pad_;
   int ac[4];
   int bc[4];
   int bq[3][2];

@@ -891,12 +891,6 @@ struct TcPlan {
     segs.push_back(g);
     items.back().seg_count += 1;
   }
-  // the last segment's reduction is K long (nk = ceil(K / 64) chunks): its last
-  // chunk's MMAs stop after the 16-wide steps that hold data
-  void ktail(long long K) {
-    const long long rem = K - 64LL * (segs.back().nk - 1);
-    segs.back().kt = rem > 0 && rem < 64 ? (int)((rem + 15) / 16) : 0;
-  }
   void drop_empty_last() {
     if (!items.empty() && items.back().seg_count == 0) items.pop_back();
   }
@@ -944,7 +938,6 @@ void cap_chains(TcPlan &pl, int cap) {
         h.ac[0] = g.ac[0] + 64 * k0;
         h.bc[0] = g.bc[0] + 64 * k0;
         h.nk = take;
-        h.kt = k0 + take == g.nk ? g.kt : 0;  // the trimmed chunk is the segment's last
         segs.push_back(h);
         items.back().seg_count += 1;
         used += take;
@@ -1196,13 +1189,11 @@ void triples_split(mlcc3_ctx *c, const std::vector<SplitTerm> &terms,
                   if (terms[t].dtype && s0 == o) {
                     pl.seg((int)(6 * t) + (s1 < s2 ? 0 : 2), (int)(6 * t) + 4, (int)NVk,
                            (int)(16 * t2), (int)(8 * t1), I[0][s2], 0, I[0][s1], I[0][s0]);
-                    pl.ktail(s.NV);
                     x = s1;
                     y = s0;
                   } else if (!terms[t].dtype && s2 == o) {
                     pl.seg((int)(6 * t) + (s0 < s1 ? 0 : 2), (int)(6 * t) + 4, (int)NOk,
                            (int)(16 * t2), (int)(8 * t1), I[0][s0], 0, I[0][s2], I[0][s1]);
-                    pl.ktail(s.NO);
                     x = s2;
                     y = s1;
                   }
@@ -1591,7 +1582,6 @@ void tc_pair(mlcc3_ctx *c, const double *X, const std::string &xkey, const Split
                 if (ascending != (cls == 0)) continue;
                 pl.seg(2 * o.sp[vk], 6, nk, (int)(16 * t2), (int)(8 * t1), (int)(o.off / s.nv3),
                        (int)(BN * tn), occ_of(o, b2), occ_of(o, b1));
-                pl.ktail(s.nv);
               }
               pl.drop_empty_last();
             }

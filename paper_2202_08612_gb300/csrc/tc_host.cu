@@ -146,9 +146,6 @@ extern "C" int mlcc3_debug_tc_gemm(const double *A, const double *B, double *C, 
       sg.amap = 0;
       sg.bmap = 2;
       sg.nk = (int)(Kp / 64);
-      // the last chunk's MMAs stop after the 16-wide steps that hold data
-      const int rem = K - 64 * (sg.nk - 1);
-      sg.kt = rem < 64 ? (rem + 15) / 16 : 0;
       sg.ac[1] = m0;
       sg.bc[1] = n0;
       segs.push_back(sg);
