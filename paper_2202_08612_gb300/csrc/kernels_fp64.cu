@@ -1180,10 +1180,23 @@ __global__ void __launch_bounds__(512, 2) triples_finish_contra_kernel(
       const float *pb = e.pb + (y * e.cb[1] + z * e.cb[2]);
       const int a0 = e.ca[0], b0 = e.cb[0];
       const float cf = e.coef;
+      // every rank-1 entry has one factor that does not depend on x (a vector
+      // over y or z, or a matrix over (y, z)): it is read once per column
+      if (a0 == 0 || b0 == 0) {
+        const float *pv = a0 == 0 ? pb : pa;
+        const int v0 = a0 == 0 ? b0 : a0;
+        const float u = cf * (a0 == 0 ? pa[0] : pb[0]);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int x = x0 + 2 * r;
-        if (x < nv) acc[r] = fmaf(cf * pa[x * a0], pb[x * b0], acc[r]);
+        for (int r = 0; r < 8; ++r) {
+          const int x = x0 + 2 * r;
+          if (x < nv) acc[r] = fmaf(u, pv[x * v0], acc[r]);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int x = x0 + 2 * r;
+          if (x < nv) acc[r] = fmaf(cf * pa[x * a0], pb[x * b0], acc[r]);
+        }
       }
     }
     const float2 ey = __ldg(ehl + y), ez = __ldg(ehl + z);
