@@ -1305,6 +1305,50 @@ def run_reference_whole(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_fp64emu(args):
+    """FP64-accurate products on the tensor cores (mlcc3_fp64emu_gemm, 5 and 6
+    digit slices) against cuBLAS DGEMM (the SIMT FP64 rate) on one square
+    product of the Cholesky-index size (M = N = K = 4096): TFLOP/s of each and
+    the normwise error against DGEMM."""
+    import torch
+    from paper_2202_08612_gb300 import binding
+    dev = torch.device("cuda", 0)
+    n = 4096
+    g = torch.Generator(device=dev)
+    g.manual_seed(2022)
+    A = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    B = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    fl = 2.0 * n ** 3
+
+    def timed(f, k):
+        for _ in range(max(1, args.warmup)):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ref = A @ B.T
+    ms_d = timed(lambda: torch.matmul(A, B.T, out=C), args.steps)
+    res = {}
+    for s in (5, 6):
+        ms = timed(lambda: binding.fp64emu_gemm(A, B, C, slices=s), args.steps)
+        err = float(torch.linalg.norm(C - ref) / torch.linalg.norm(ref))
+        res[s] = {"ms": ms, "tflops": fl / ms / 1e9, "normwise_rel_err_vs_dgemm": err}
+    print(json.dumps({"metric": "FP64-accurate GEMM TFLOP/s (tensor-core digit slices vs DGEMM)",
+                      "value": res[5]["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "config": {"workload": f"C = A B^T, M = N = K = {n}, FP64 normal entries",
+                                 "note": "each call allocates and frees its temporaries"},
+                      "slices": {str(k): v for k, v in res.items()},
+                      "dgemm": {"ms": ms_d, "tflops": fl / ms_d / 1e9}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1312,7 +1356,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="betaine_like",
-                    choices=sorted(set(WORKLOADS) | set(WHOLE) | set(LARGE)) + ["uneven_sweep", "nv_scaling"])
+                    choices=sorted(set(WORKLOADS) | set(WHOLE) | set(LARGE)) + ["uneven_sweep", "nv_scaling", "fp64emu_gemm"])
     ap.add_argument("--vectors", type=int, default=4,
                     help="trial vectors per system of the uneven_sweep workload")
     ap.add_argument("--precision", default="split", choices=("split", "fp64"))
@@ -1343,7 +1387,9 @@ def main():
     if world > 1 and args.impl == "ours":
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.impl == "ours" and args.workload == "uneven_sweep":
+    if args.impl == "ours" and args.workload == "fp64emu_gemm":
+        run_fp64emu(args)
+    elif args.impl == "ours" and args.workload == "uneven_sweep":
         run_sweep(args)
     elif args.impl == "ours" and args.workload == "nv_scaling":
         run_nv_scaling(args)

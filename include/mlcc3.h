@@ -307,6 +307,23 @@ int mlcc3_set_param(mlcc3_ctx *ctx, const char *name, long long value);
 int mlcc3_cnto_matrices(int64_t n_occ, int64_t n_vir, const double *R1, const double *R2,
                         double *M, double *N, void *cuda_stream);
 
+/* C = A B^T in FP64 accuracy on the BF16 tensor cores (the contractions of
+ * Sec. 3 at FP64 accuracy, by error-free splitting after Ozaki, Ogita, Oishi
+ * and Rump): every row of A and of B is scaled by a power of two and written
+ * as `slices` balanced base-256 digits (integers in [-128, 128], exact in
+ * bfloat16); the digit slices are multiplied on tcgen05 with FP32 sums that
+ * are exact over K chains of up to 1024, the chains added in FP64; the digit
+ * pairs (t, u) with t + u < slices are kept, so the normwise relative error is
+ * about 2^-(8 slices) (slices = 5: about 1e-12).  A [M][K] with rows lda
+ * apart, B [N][K] rows ldb apart, C [M][N] rows ldc apart, all FP64 device
+ * arrays (MLCC3_ERR_ARG otherwise, and for slices outside 2..6 or a leading
+ * dimension below the row length).  Allocates its temporaries (about
+ * 2 slices (M + N) K bytes), runs on `cuda_stream` and returns when C holds
+ * the product; MLCC3_ERR_OOM when an allocation fails, MLCC3_ERR_TIMEOUT when
+ * a tensor-core pipeline wait ran out (C is then not valid). */
+int mlcc3_fp64emu_gemm(const double *A, long long lda, const double *B, long long ldb, double *C,
+                       long long ldc, int M, int N, int K, int slices, void *cuda_stream);
+
 /* Triples residual without allocating (no counterpart in the paper).
  * Some callers cannot allocate device memory at the moment they call: a
  * solver loop whose host application gives all device memory to its own pool

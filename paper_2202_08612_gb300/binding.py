@@ -30,7 +30,7 @@ EXPORTS = ("mlcc3_create", "mlcc3_destroy", "mlcc3_last_error", "mlcc3_build_int
            "mlcc3_sweep_create", "mlcc3_sweep_set_system", "mlcc3_sweep_run", "mlcc3_sweep_info",
            "mlcc3_sweep_destroy", "mlcc3_rayleigh_quotient", "mlcc3_ground_density",
            "mlcc3_multiplier_transformation", "mlcc3_cnto_matrices", "mlcc3_shard_batches",
-           "mlcc3_transition_densities")
+           "mlcc3_transition_densities", "mlcc3_fp64emu_gemm")
 
 
 class MLCC3Error(RuntimeError):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.mlcc3_ground_density.argtypes = [P, P, P, P]
     lib.mlcc3_multiplier_transformation.argtypes = [P, P, P, P, P]
     lib.mlcc3_cnto_matrices.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]
+    L = ctypes.c_longlong
+    lib.mlcc3_fp64emu_gemm.argtypes = [P, L, P, L, P, L, I, I, I, I, P]
     lib.mlcc3_shard_batches.argtypes = [I, P, I, I, I, P, I]
     lib.mlcc3_transition_densities.argtypes = [P, I, P] + [P] * 10
     lib.mlcc3_debug_kernel_stats.argtypes = [P, I, ctypes.c_char_p, ctypes.c_size_t,
@@ -142,6 +144,18 @@ def tc_gemm(A, B, C):
     M, K = A.shape
     N = B.shape[0]
     rc = lib.mlcc3_debug_tc_gemm(_ptr(A), _ptr(B), _ptr(C), M, N, K)
+    if rc != 0:
+        raise MLCC3Error(rc, lib.mlcc3_last_error().decode())
+
+
+def fp64emu_gemm(A, B, C, slices=5, stream=None):
+    """mlcc3_fp64emu_gemm: C = A B^T (torch CUDA float64 tensors, row-major,
+    unit column stride) to FP64 accuracy on the BF16 tensor cores."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    # contiguous rows (_ptr checks): the leading dimensions are the row lengths
+    rc = lib.mlcc3_fp64emu_gemm(_ptr(A), K, _ptr(B), K, _ptr(C), N, M, N, K, int(slices), stream)
     if rc != 0:
         raise MLCC3Error(rc, lib.mlcc3_last_error().decode())
 
