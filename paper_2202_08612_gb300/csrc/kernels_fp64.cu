@@ -1491,7 +1491,7 @@ namespace mlcc3 {
 // threads take consecutive elements along that view's stride-1 axis, so each
 // load is a run of whole sectors whatever the permutation (with j <= i that
 // axis is b or c, the one of the smaller of j and the view's third index,
-// except for ties: the binary32 form takes TA = 1, TB = 16, rows of 64 bytes),
+// except for ties: the binary32 form takes TA = 2, TB = 16, rows of 64 bytes),
 // and the element is
 // stored at its logical (a,b,c) position of the view's tile in shared memory
 // (padded strides, no bank conflicts along any axis; pads stay zero).  Thread
@@ -1529,12 +1529,7 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
   if (j > i) return;
   const double wij = j < i ? 2.0 : 1.0;
   const int t = threadIdx.x;
-  {
-    unsigned dynz;
-    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dynz));
-    const int nz = dynz >= 4u * (unsigned)no * TS * sizeof(T) ? 4 * no * TS : 2 * no * TS;
-    for (int q = t; q < nz; q += blockDim.x) xs[q] = T(0);  // the pads stay zero
-  }
+  for (int q = t; q < 2 * no * TS; q += blockDim.x) xs[q] = T(0);
   if (t < no) {
     const int v = (i * no + j) * no + t;
     s_have[t] = vhave[v];
@@ -1568,14 +1563,9 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
   const int ta = (nv + TA - 1) / TA, tb = (nv + TB - 1) / TB, tc = (nv + TB - 1) / TB;
   const int ntiles = ta * tb * tc;
-  // two tile buffers when the launch's shared memory holds them: the copies of
-  // tile q + gridDim.x are in flight while tile q is multiplied
-  unsigned dyn;
-  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-  const bool db = dyn >= 4u * (unsigned)no * TS * sizeof(T);
-  auto issue = [&](int q, int buf) {
-    T *bx = xs + (size_t)buf * 2 * no * TS, *by = bx + (size_t)no * TS;
+  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
     const int a0 = TA * (q / (tb * tc)), b0 = TB * ((q / tc) % tb), c0 = TB * (q % tc);
+    __syncthreads();  // the previous tile's reads are done
     for (int r = 0; r < no; ++r) {
       const int f = s_ax[r][0], m = s_ax[r][1];
       // TA and TB are powers of two: the split of e by shifts and masks
@@ -1597,65 +1587,45 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
         // asynchronous global -> shared copies; a missing element is zero-filled
         const unsigned nbytes = ok ? (unsigned)sizeof(T) : 0u;
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(
-                         (unsigned)__cvta_generic_to_shared(bx + sp)),
+                         (unsigned)__cvta_generic_to_shared(xs + sp)),
                      "l"(X + o), "n"(sizeof(T)), "r"(nbytes)
                      : "memory");
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(
-                         (unsigned)__cvta_generic_to_shared(by + sp)),
+                         (unsigned)__cvta_generic_to_shared(ys + sp)),
                      "l"(Y + o), "n"(sizeof(T)), "r"(nbytes)
                      : "memory");
       }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  int buf = 0;
-  if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
-    const int qn = q + gridDim.x;
-    if (db && qn < ntiles) {
-      issue(qn, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    __syncthreads();  // tile q is in shared memory for every thread
-    {
-      const T *bx = xs + (size_t)buf * 2 * no * TS, *by = bx + (size_t)no * TS;
-      if (h < H) {
-        const T *xr[4], *yr[4];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (h < H) {
+      const T *xr[4], *yr[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        xr[d] = xs + min(l0 + d, no - 1) * TS;
+        yr[d] = ys + min(k0 + d, no - 1) * TS;
+      }
+      T p[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) p[x][y] = T(0);
+      for (int e = e0; e < e1; ++e) {
+        T u[4], w[4];
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-          xr[d] = bx + min(l0 + d, no - 1) * TS;
-          yr[d] = by + min(k0 + d, no - 1) * TS;
-        }
-        T p[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 4; ++y) p[x][y] = T(0);
-        for (int e = e0; e < e1; ++e) {
-          T u[4], w[4];
-#pragma unroll
-          for (int d = 0; d < 4; ++d) {
-            u[d] = xr[d][e];
-            w[d] = yr[d][e];
-          }
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) p[x][y] += w[x] * u[y];
+          u[d] = xr[d][e];
+          w[d] = yr[d][e];
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] += (double)p[x][y];
+          for (int y = 0; y < 4; ++y) p[x][y] += w[x] * u[y];
       }
-    }
-    __syncthreads();  // tile q's reads are done before its buffer takes a new tile
-    if (db) {
-      buf ^= 1;
-    } else if (qn < ntiles) {
-      issue(qn, 0);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += (double)p[x][y];
     }
   }
   if (h >= H) return;
@@ -1670,17 +1640,15 @@ __device__ __forceinline__ void pair_dots_body(const T *__restrict__ X,
 }
 
 // Shared-memory bytes of pair_dots_*_kernel for no views.
-// Two tile buffers when they fit (the kernels read the size they were given).
 size_t pair_dots_smem(int no, bool f32) {
-  const int TA = f32 ? 1 : 4, TB = f32 ? 16 : 8;
+  const int TA = f32 ? 2 : 4, TB = f32 ? 16 : 8;
   const int TE = TA * (TB * (TB + 1) + 1), TS = (TE + 31) / 32 * 32 + 1;
-  const size_t one = 2 * (size_t)no * TS * (f32 ? sizeof(float) : sizeof(double));
-  return 2 * one <= 227 * 1024 ? 2 * one : one;
+  return 2 * (size_t)no * TS * (f32 ? sizeof(float) : sizeof(double));
 }
 
 // Tiles of the (a,b,c) cube swept by pair_dots_*_kernel.
 long long pair_dots_tiles(int nv, bool f32) {
-  const int TA = f32 ? 1 : 4, TB = f32 ? 16 : 8;
+  const int TA = f32 ? 2 : 4, TB = f32 ? 16 : 8;
   return (long long)((nv + TA - 1) / TA) * ((nv + TB - 1) / TB) * ((nv + TB - 1) / TB);
 }
 
@@ -1689,7 +1657,7 @@ __global__ void __launch_bounds__(256, 2) pair_dots_f32_kernel(
     const float *__restrict__ X, const float *__restrict__ Y, const long long *__restrict__ voff,
     const int *__restrict__ vstr, const char *__restrict__ vhave, int no, int nv, int p0,
     double *__restrict__ out, long long ldo, int kl, double alpha) {
-  pair_dots_body<float, 1, 16>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
+  pair_dots_body<float, 2, 16>(X, Y, voff, vstr, vhave, no, nv, p0, out, ldo, kl, alpha);
 }
 
 // Physical-order form of pair_dots_f32_kernel for n_v a multiple of 4 (every
