@@ -50,6 +50,15 @@ def test_argument_errors_without_gpu(lib):
     assert L.mlcc3_triples_omega(None, None, None) == -1
     assert L.mlcc3_debug_nbatches(None) == -1
     assert L.mlcc3_set_param(None, b"tc_kcap", 8) == -1
+    # the FP64-accurate GEMM: null operands, bad sizes, leading dimensions below
+    # the row length and slice counts outside 2..6 fail before any CUDA call
+    a = np.zeros((4, 8))
+    P = a.ctypes.data
+    for args in ((None, 8, P, 8, P, 4, 4, 4, 8, 5), (P, 8, P, 8, P, 4, 0, 4, 8, 5),
+                 (P, 7, P, 8, P, 4, 4, 4, 8, 5), (P, 8, P, 8, P, 3, 4, 4, 8, 5),
+                 (P, 8, P, 8, P, 4, 4, 4, 8, 1), (P, 8, P, 8, P, 4, 4, 4, 8, 7)):
+        assert L.mlcc3_fp64emu_gemm(*args, None) == -1, args
+        assert b"fp64emu" in L.mlcc3_last_error()
 
 
 def test_ptr_marshalling():
